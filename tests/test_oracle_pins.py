@@ -1,0 +1,386 @@
+"""Pins of the FP64 oracle against facts fixed outside the oracle itself.
+
+Sources of truth: the printed IsingXX matrix (Eq. 1), Listing 1 semantics,
+Alg. 1 / Alg. 2 brute force, closed forms (RX expectation values, GHZ,
+product states, Hartree-Fock energies, QAOA p=1), matrix exponentials of the
+generators (scipy), and the independent dense Kronecker reference.
+"""
+
+import cmath
+import itertools
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg
+
+import oracle
+from oracle import dense, enumeration
+from workloads import (Circuit, Op, Term, GATE_ARITY, GATE_NPARAMS, layered_circuit,
+                       qaoa_maxcut, random_circuit, random_hamiltonian, random_state,
+                       regular_graph, strongly_entangling, vqe_givens, ry_cz_brick)
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+ONE_ANGLE = [g for g, k in GATE_NPARAMS.items() if k == 1]
+
+
+# ---------------------------------------------------------------------------
+# Alg. 1 / Alg. 2 enumerations (brute force)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n", range(1, 11))
+def test_alg1_pairs_partition_the_state(n):
+    for q in range(n):
+        pairs = list(enumeration.single_qubit_pairs(n, q))
+        assert len(pairs) == 1 << (n - 1)
+        bit = 1 << (n - 1 - q)
+        flat = [i for p in pairs for i in p]
+        assert sorted(flat) == list(range(1 << n))
+        assert all((i0 & bit) == 0 and i1 == i0 | bit for i0, i1 in pairs)
+
+
+def test_alg1_low_mask_reading_at_offset_zero():
+    # q = n-1 gives q_offset = 0: the low mask must be empty (reading of the
+    # printed shift by the full bit width).
+    assert enumeration.gap_masks([0])[0] == 0
+    pairs = list(enumeration.single_qubit_pairs(3, 2))
+    assert pairs == [(0, 1), (2, 3), (4, 5), (6, 7)]
+
+
+@pytest.mark.parametrize("n", range(2, 7))
+def test_alg2_pairs_are_exactly_the_control_matching_pairs(n):
+    rng = np.random.default_rng(n)
+    for target in range(n):
+        others = [w for w in range(n) if w != target]
+        for nc in range(0, min(3, n - 1) + 1):
+            for controls in itertools.combinations(others, nc):
+                vals = [int(v) for v in rng.integers(0, 2, size=nc)]
+                got = list(enumeration.controlled_pairs(n, target, controls, vals))
+                alt = list(enumeration.controlled_pairs_by_insertion(n, target, controls, vals))
+                assert got == alt
+                tb = 1 << (n - 1 - target)
+                want = []
+                for i in range(1 << n):
+                    if i & tb:
+                        continue
+                    if all(((i >> (n - 1 - c)) & 1) == v for c, v in zip(controls, vals)):
+                        want.append((i, i | tb))
+                assert sorted(got) == want
+                assert len(got) == 1 << (n - 1 - nc)   # cost ~ 2^-c of the uncontrolled gate
+
+
+@pytest.mark.parametrize("n", [3, 4, 5])
+def test_alg2_enumeration_applies_the_dense_controlled_gate(n):
+    rng = np.random.default_rng(100 + n)
+    U = scipy.linalg.expm(1j * (lambda a: a + a.conj().T)(rng.normal(size=(2, 2)) + 1j * rng.normal(size=(2, 2))))
+    for target in range(n):
+        controls = [w for w in range(n) if w != target][:2]
+        vals = [1, 0][:len(controls)]
+        psi = random_state(n, 7 + target)
+        out = psi.copy()
+        for i0, i1 in enumeration.controlled_pairs(n, target, controls, vals):
+            a0, a1 = psi[i0], psi[i1]
+            out[i0] = U[0, 0] * a0 + U[0, 1] * a1
+            out[i1] = U[1, 0] * a0 + U[1, 1] * a1
+        want = dense.controlled(n, [target], U, controls, vals) @ psi
+        np.testing.assert_allclose(out, want, atol=1e-14)
+
+
+# ---------------------------------------------------------------------------
+# Gate matrices
+# ---------------------------------------------------------------------------
+def _golden_isingxx(phi):
+    tok = {"c": math.cos(phi / 2), "0": 0.0, "-is": -1j * math.sin(phi / 2)}
+    rows = [ln.split() for ln in open(os.path.join(GOLDEN, "isingxx_eq1.txt"))
+            if ln.strip() and not ln.startswith("#")]
+    return np.array([[tok[t] for t in r] for r in rows], dtype=np.complex128)
+
+
+@pytest.mark.parametrize("phi", [0.0, 0.3, -1.1, math.pi, 2.5, 5.9])
+def test_isingxx_matches_printed_eq1(phi):
+    np.testing.assert_allclose(oracle.gate_matrix("IsingXX", [phi]), _golden_isingxx(phi), atol=1e-15)
+
+
+@pytest.mark.parametrize("name", list(GATE_ARITY))
+def test_every_gate_is_unitary(name):
+    rng = np.random.default_rng(3)
+    for _ in range(5):
+        M = oracle.gate_matrix(name, rng.uniform(-7, 7, size=GATE_NPARAMS[name]))
+        np.testing.assert_allclose(M.conj().T @ M, np.eye(M.shape[0]), atol=1e-14)
+
+
+@pytest.mark.parametrize("name", ONE_ANGLE)
+def test_gate_equals_exponential_of_its_generator(name):
+    G, s = oracle.generator(name)
+    np.testing.assert_allclose(G, G.conj().T, atol=0)          # Hermitian generator
+    for theta in (0.0, 0.4, -2.2, 3.7):
+        np.testing.assert_allclose(oracle.gate_matrix(name, [theta]),
+                                   scipy.linalg.expm(1j * s * theta * G), atol=1e-13)
+
+
+def test_rotations_are_exp_minus_i_theta_p_over_2():
+    # Reading of the RX sign: exp(-i theta/2 P) everywhere (Eq. 1 form).
+    for name, P in (("RX", oracle.PX), ("RY", oracle.PY), ("RZ", oracle.PZ)):
+        for t in (0.1, 1.3, -2.0):
+            np.testing.assert_allclose(oracle.gate_matrix(name, [t]),
+                                       scipy.linalg.expm(-0.5j * t * P), atol=1e-14)
+
+
+def test_rot_closed_form():
+    for (phi, th, om) in [(0.1, 0.2, 0.3), (-1.0, 2.0, 4.0), (3.0, -0.7, 1.9)]:
+        c, s = math.cos(th / 2), math.sin(th / 2)
+        want = np.array([[cmath.exp(-0.5j * (phi + om)) * c, -cmath.exp(0.5j * (phi - om)) * s],
+                         [cmath.exp(-0.5j * (phi - om)) * s, cmath.exp(0.5j * (phi + om)) * c]])
+        np.testing.assert_allclose(oracle.gate_matrix("Rot", [phi, th, om]), want, atol=1e-14)
+
+
+def test_givens_gates_rotate_only_inside_their_subspace():
+    for t in (0.3, -1.7):
+        M = oracle.gate_matrix("SingleExcitation", [t])
+        sub = M[np.ix_([1, 2], [1, 2])]
+        np.testing.assert_allclose(sub, [[math.cos(t / 2), -math.sin(t / 2)], [math.sin(t / 2), math.cos(t / 2)]])
+        rest = [0, 3]
+        np.testing.assert_allclose(M[np.ix_(rest, rest)], np.eye(2))
+        D = oracle.gate_matrix("DoubleExcitation", [t])
+        np.testing.assert_allclose(D[np.ix_([3, 12], [3, 12])],
+                                   [[math.cos(t / 2), -math.sin(t / 2)], [math.sin(t / 2), math.cos(t / 2)]])
+        others = [i for i in range(16) if i not in (3, 12)]
+        np.testing.assert_allclose(D[np.ix_(others, others)], np.eye(14))
+
+
+def _listing1_rows():
+    rows = []
+    for ln in open(os.path.join(GOLDEN, "listing1_semantics.txt")):
+        if ln.strip() and not ln.startswith("#"):
+            rows.append(ln.split())
+    return rows
+
+
+@pytest.mark.parametrize("n", [1, 3, 5])
+def test_listing1_pauli_x_and_phase_shift_semantics(n):
+    angle = 0.83
+    for gate, inv, new0, new1 in _listing1_rows():
+        for q in range(n):
+            psi = random_state(n, 11 * n + q)
+            out = psi.copy()
+            op = Op(gate, (q,), (0,) if gate == "PhaseShift" else (), adjoint=bool(int(inv)))
+            oracle.apply_op(out, op, np.array([angle]))
+            for i0, i1 in enumeration.single_qubit_pairs(n, q):
+                env = {"a0": psi[i0], "a1": psi[i1], "exp": cmath.exp, "i": 1j, "angle": angle}
+                assert abs(out[i0] - eval(new0, env)) < 1e-15
+                assert abs(out[i1] - eval(new1, env)) < 1e-15
+
+
+# ---------------------------------------------------------------------------
+# C loops vs dense reference; invariants
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n,seed", [(2, 0), (3, 1), (4, 2), (5, 3), (6, 4), (7, 5)])
+def test_oracle_forward_matches_dense_kronecker(n, seed):
+    c, p = random_circuit(n, 25, seed, max_controls=2)
+    psi0 = random_state(n, seed + 50)
+    got = oracle.forward(c, p, psi0)
+    want = dense.circuit_unitary(c, p) @ psi0
+    np.testing.assert_allclose(got, want, atol=1e-13)
+
+
+@pytest.mark.parametrize("name", [g for g in GATE_ARITY if g != "Identity"])
+def test_gate_then_inverse_is_identity_and_norm_preserved(name):
+    n = 5
+    k = GATE_ARITY[name]
+    rng = np.random.default_rng(sum(map(ord, name)))
+    for trial in range(4):
+        wires = tuple(int(w) for w in rng.permutation(n)[:k])
+        free = [w for w in range(n) if w not in wires]
+        controls = tuple(free[:trial % 2])
+        op = Op(name, wires, tuple(range(GATE_NPARAMS[name])), controls)
+        params = rng.uniform(-4, 4, size=GATE_NPARAMS[name])
+        psi = random_state(n, trial)
+        out = oracle.apply_op(psi.copy(), op, params)
+        assert abs(oracle.norm2(out) - 1.0) < 1e-14
+        back = oracle.apply_op(out, op, params, dagger=True)
+        np.testing.assert_allclose(back, psi, atol=1e-14)
+
+
+@pytest.mark.parametrize("n", range(1, 11))
+def test_ghz_amplitudes(n):
+    ops = [Op("Hadamard", (0,))] + [Op("PauliX", (i + 1,), controls=(i,)) for i in range(n - 1)]
+    psi = oracle.forward(Circuit(n, ops, 0), np.zeros(0))
+    want = np.zeros(1 << n, dtype=np.complex128)
+    want[0] = want[-1] = 1 / math.sqrt(2)
+    assert np.abs(psi - want).max() < 1e-15
+    assert np.count_nonzero(psi) == 2
+
+
+@pytest.mark.parametrize("theta", [0.0, 0.37, 1.2, -2.5, math.pi])
+def test_rx_expectations_closed_form(theta):
+    c = Circuit(1, [Op("RX", (0,), (0,))], 1,
+                [[Term(1.0, ((0, "Z"),))], [Term(1.0, ((0, "Y"),))], [Term(1.0, ((0, "X"),))]])
+    psi = oracle.forward(c, np.array([theta]))
+    E = oracle.expvals(psi, c.observables)
+    assert abs(E[0] - math.cos(theta)) < 1e-15
+    assert abs(E[1] + math.sin(theta)) < 1e-15
+    assert abs(E[2]) < 1e-15
+    _, J = oracle.adjoint_jacobian(c, np.array([theta]))
+    assert abs(J[0, 0] + math.sin(theta)) < 1e-15     # d<Z>/dtheta = -sin(theta)
+
+
+def _closed_form_pauli(n, paulis, psi):
+    """P|i> = i^{nY} (-1)^{popcount(i & z)} |i ^ x> with bit (n-1-w) for wire w."""
+    x = z = 0
+    for w, l in paulis:
+        b = 1 << (n - 1 - w)
+        if l in "XY":
+            x |= b
+        if l in "YZ":
+            z |= b
+    ny = bin(x & z).count("1")
+    out = np.zeros_like(psi)
+    for i in range(1 << n):
+        out[i ^ x] += (1j ** ny) * (-1) ** bin(i & z).count("1") * psi[i]
+    return out
+
+
+def test_pauli_words_closed_form_all_3q_words():
+    n = 3
+    psi = random_state(n, 5)
+    for letters in itertools.product("IXYZ", repeat=n):
+        paulis = tuple((w, l) for w, l in enumerate(letters) if l != "I")
+        a = oracle.apply_pauli_word(psi, paulis)
+        b = dense.pauli_word(n, paulis) @ psi
+        c = _closed_form_pauli(n, paulis, psi)
+        np.testing.assert_allclose(a, b, atol=1e-15)
+        np.testing.assert_allclose(a, c, atol=1e-15)
+
+
+def test_ry_product_state_closed_form():
+    n, layers = 6, 3
+    rng = np.random.default_rng(9)
+    ops, p = [], 0
+    for _ in range(layers):
+        for w in range(n):
+            ops.append(Op("RY", (w,), (p,)))
+            p += 1
+    params = rng.uniform(0, 2 * math.pi, size=p)
+    obs = [[Term(1.0, ((w, "Z"),))] for w in range(n)]
+    c = Circuit(n, ops, p, obs)
+    E = oracle.expvals(oracle.forward(c, params), obs)
+    for w in range(n):
+        tot = sum(params[l * n + w] for l in range(layers))
+        assert abs(E[w] - math.cos(tot)) < 1e-14
+
+
+def test_hartree_fock_energy_closed_form():
+    c, p = vqe_givens(n=10, electrons=4, n_singles=3, n_doubles=3, n_terms=60, seed=4)
+    H = c.observables[0]
+    psi = oracle.forward(c, np.zeros_like(p))          # zero angles: HF state untouched
+    want = 0.0
+    for t in H:
+        if all(l == "Z" for _, l in t.paulis):
+            occ = sum(1 for w, _ in t.paulis if (c.basis_state >> (c.n - 1 - w)) & 1)
+            want += t.coeff * (-1) ** occ
+    assert abs(oracle.expval(psi, H) - want) < 1e-13
+
+
+def test_givens_circuit_preserves_hamming_weight():
+    c, p = vqe_givens(n=10, electrons=4, n_singles=6, n_doubles=8, n_terms=5, seed=1)
+    psi = oracle.forward(c, p * 10)
+    for i in range(1 << c.n):
+        if bin(i).count("1") != 4:
+            assert psi[i] == 0.0
+
+
+def test_oracle_reductions_do_not_depend_on_thread_count():
+    a, b = random_state(15, 1), random_state(15, 2)
+    t0 = oracle.num_threads()
+    r_many = oracle.inner(a, b)
+    oracle.set_num_threads(1)
+    r_one = oracle.inner(a, b)
+    oracle.set_num_threads(t0)
+    assert r_many == r_one
+    np.testing.assert_allclose(r_one, np.vdot(a, b), rtol=1e-13)
+
+
+# ---------------------------------------------------------------------------
+# Gradients
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n,seed", [(2, 10), (3, 11), (4, 12), (5, 13), (6, 14)])
+def test_adjoint_matches_dense_exact_derivative(n, seed):
+    c, p = random_circuit(n, 18, seed, shared_params=True)
+    rng = np.random.default_rng(seed)
+    obs = [random_hamiltonian(n, 4, rng, weights=(1, 2)), random_hamiltonian(n, 3, rng, weights=(1, 2, 3))]
+    E, J = oracle.adjoint_jacobian(c, p, obs)
+    np.testing.assert_allclose(E, dense.expvals(c, p, obs), atol=1e-13)
+    np.testing.assert_allclose(J, dense.exact_jacobian(c, p, obs), atol=1e-12)
+
+
+@pytest.mark.parametrize("maker", ["layered", "sel", "qaoa", "rycz"])
+def test_adjoint_matches_parameter_shift(maker):
+    if maker == "layered":
+        c, p = layered_circuit(5, 2, seed=1)
+    elif maker == "sel":
+        c, p = strongly_entangling(5, 2, seed=2)
+    elif maker == "qaoa":
+        c = qaoa_maxcut(6, 2, seed=3)
+        p = np.random.default_rng(3).uniform(0, math.pi, size=4)
+    else:
+        c, p = ry_cz_brick(6, 3, seed=4)
+    E, J = oracle.adjoint_jacobian(c, p)
+    Jps = oracle.param_shift_jacobian(c, p)
+    np.testing.assert_allclose(J, Jps, atol=1e-12)
+
+
+def test_adjoint_matches_finite_differences():
+    c, p = random_circuit(4, 14, 77)
+    obs = [[Term(0.7, ((0, "Z"), (2, "X"))), Term(-1.1, ((1, "Y"),))]]
+    _, J = oracle.adjoint_jacobian(c, p, obs)
+    Jfd = oracle.finite_diff_jacobian(c, p, obs)
+    np.testing.assert_allclose(J, Jfd, atol=1e-7)
+
+
+def test_vjp_is_gradient_weighted_jacobian_rows():
+    c, p = strongly_entangling(4, 2, seed=5)
+    g = np.random.default_rng(1).normal(size=len(c.observables))
+    _, J = oracle.adjoint_jacobian(c, p)
+    np.testing.assert_allclose(oracle.adjoint_vjp(c, p, g), g @ J, atol=1e-13)
+
+
+def _qaoa_p1_zz(gamma, beta, du, dv, f):
+    """<Z_u Z_v> after H^n, exp(-i gamma Z_aZ_b) per edge, exp(-i beta X) per wire.
+
+    From the p=1 MaxCut edge expectation of Wang, Hadfield, Jiang and Rieffel
+    (2018) for e^{-i g C} e^{-i b B} with C_uv = (1 - Z_uZ_v)/2; this circuit
+    is g = -2 gamma, b = beta.  du, dv = degree - 1; f = triangles on the edge.
+    """
+    g = -2.0 * gamma
+    b = beta
+    cuv = (0.5 + 0.25 * math.sin(4 * b) * math.sin(g) * (math.cos(g) ** du + math.cos(g) ** dv)
+           - 0.25 * math.sin(2 * b) ** 2 * math.cos(g) ** (du + dv - 2 * f) * (1 - math.cos(2 * g) ** f))
+    return 1.0 - 2.0 * cuv
+
+
+def test_single_edge_qaoa_by_hand():
+    # Heisenberg picture by hand: Z -> cos(2b) Z + sin(2b) Y per wire, so
+    # <Z0Z1> = 2 sin(2b)cos(2b) sin(2 gamma) = sin(4b) sin(2 gamma).
+    for gm, bt in [(0.3, 0.2), (1.1, 2.0), (2.9, 0.7)]:
+        c = qaoa_maxcut(2, 1, edges=[(0, 1)])
+        E = oracle.expvals(oracle.forward(c, np.array([gm, bt])), c.observables)
+        assert abs(E[0] - math.sin(4 * bt) * math.sin(2 * gm)) < 1e-14
+        assert abs(_qaoa_p1_zz(gm, bt, 0, 0, 0) - math.sin(4 * bt) * math.sin(2 * gm)) < 1e-14
+
+
+@pytest.mark.parametrize("n", [8, 10])
+def test_qaoa_p1_closed_form_on_regular_graphs(n):
+    rng = np.random.default_rng(n)
+    edges = regular_graph(n, rng)
+    adj = {v: set() for v in range(n)}
+    for u, v in edges:
+        adj[u].add(v)
+        adj[v].add(u)
+    for gm, bt in [(0.4, 0.3), (1.7, 2.2)]:
+        c = qaoa_maxcut(n, 1, edges=edges)
+        psi = oracle.forward(c, np.array([gm, bt]))
+        for (u, v) in edges:
+            e = oracle.expval(psi, [Term(1.0, ((u, "Z"), (v, "Z")))])
+            f = len(adj[u] & adj[v])
+            want = _qaoa_p1_zz(gm, bt, len(adj[u]) - 1, len(adj[v]) - 1, f)
+            assert abs(e - want) < 1e-13

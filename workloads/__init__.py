@@ -1,0 +1,26 @@
+"""Seeded synthetic workloads shared by the oracle, the tests and the benchmark.
+
+This package describes circuits and observables only as structure (gate names,
+wires, parameter indices) plus seeded random numbers.  It holds none of the
+simulation arithmetic: no gate matrices, no index arithmetic, no reductions.
+"""
+
+from .circuits import (  # noqa: F401
+    Op,
+    Circuit,
+    Term,
+    GATE_ARITY,
+    GATE_NPARAMS,
+    layered_circuit,
+    strongly_entangling,
+    qaoa_maxcut,
+    qaoa_param_sets,
+    qaoa_mixed_instances,
+    regular_graph,
+    vqe_givens,
+    ry_cz_brick,
+    random_circuit,
+    random_hamiltonian,
+    random_state,
+    config_seed,
+)
