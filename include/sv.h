@@ -1,0 +1,277 @@
+/*
+ * sv.h -- C ABI of the GB300 state-vector core (libsv.so).
+ *
+ * The library applies parameterised gates to a 2^n complex amplitude vector,
+ * reduces Pauli-sum expectation values and computes the adjoint-method
+ * Jacobian, all on one NVIDIA GB300 (sm_103a), with hand-written CUDA kernels.
+ * It follows the problem statement of arXiv 2403.02512:
+ *   - a state is 2^n complex amplitudes, 32- or 64-bit floating point
+ *     (Sec. 2: "fully templated end-to-end ... 32-bit or 64-bit");
+ *   - wire w is bit (n - 1 - w) of an amplitude index: wire 0 is the most
+ *     significant bit (Alg. 1, q_offset = n - q - 1);
+ *   - a gate is (kind, wires, angles, inverse flag) (Listing 1), optionally
+ *     controlled by wires that must hold prescribed values (Alg. 2);
+ *   - an observable is a Hamiltonian: coefficients times Pauli words
+ *     (Sec. 2.2, Listing 2);
+ *   - gradients come from the adjoint method as a Jacobian matrix (Sec. 2.2,
+ *     Sec. 4.3: "build and return the Jacobian matrix"), parameters in,
+ *     results and Jacobian out (Sec. 2).
+ *
+ * Conventions for every entry point:
+ *   - no C++ exception crosses this boundary; every call returns sv_status;
+ *   - on SV_ERR_ARG / SV_ERR_UNSUPPORTED nothing was launched and the state
+ *     is unchanged; sv_last_error() holds a message for the calling thread;
+ *   - host pointers are plain host memory unless a parameter says "device";
+ *     the library never keeps a caller pointer after the call returns, except
+ *     the device buffer given to sv_create_from_device_ptr / sv_set_workspace;
+ *   - all GPU work is issued on the state's stream (sv_set_stream); calls that
+ *     return host results synchronise that stream before returning;
+ *   - angles, expectation values and Jacobians are FP64 on the host side
+ *     whatever the state's precision.
+ */
+#ifndef SV_H
+#define SV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SV_MAX_QUBITS 34      /* 2^34 complex128 = 256 GiB, the largest that can fit */
+#define SV_MAX_TARGETS 6      /* target wires of one op (dense matrices up to 64 x 64) */
+#define SV_MAX_CONTROLS 8
+
+typedef struct sv_state sv_state;     /* opaque: one state vector on one GPU */
+typedef struct sv_program sv_program; /* opaque: a planned circuit + observables */
+
+typedef enum {
+    SV_C64 = 0,  /* complex64: FP32 amplitudes, FP32 gate arithmetic, FP64 / compensated reductions */
+    SV_C128 = 1  /* complex128: FP64 amplitudes and arithmetic */
+} sv_dtype;
+
+typedef enum {
+    SV_OK = 0,
+    SV_ERR_ARG = 1,          /* invalid argument (bad wire, size, pointer, NaN angle ...) */
+    SV_ERR_OOM = 2,          /* device allocation failed or exceeds the allocation cap */
+    SV_ERR_CUDA = 3,         /* a CUDA runtime call failed */
+    SV_ERR_TIMEOUT = 4,      /* a bounded device-side wait gave up */
+    SV_ERR_UNSUPPORTED = 5,  /* valid request this build does not implement */
+    SV_ERR_STATE = 6         /* an earlier asynchronous device error is latched; sv_reset clears it */
+} sv_status;
+
+/* Base gates of Sec. 2.1.2 and Sec. 3.2.  Matrices (c = cos(t/2), s = sin(t/2)):
+ *   RX(t)=exp(-i t X/2), RY(t)=exp(-i t Y/2), RZ(t)=exp(-i t Z/2);
+ *   PhaseShift(t)=diag(1, e^{it}) (Listing 1); Rot(a,b,c)=RZ(c) RY(b) RZ(a);
+ *   IsingXX(t)=exp(-i t XX/2) (Eq. 1), IsingYY(t)=exp(-i t YY/2),
+ *   IsingZZ(t)=exp(-i t ZZ/2), IsingXY(t)=exp(i t (XX+YY)/4);
+ *   SingleExcitation(t): [[c,-s],[s,c]] on (|01>,|10>), identity elsewhere;
+ *   DoubleExcitation(t): the same on (|0011>,|1100>).
+ * The first target wire is the most significant bit of a gate's local index. */
+typedef enum {
+    SV_IDENTITY = 0,
+    SV_PAULI_X = 1,
+    SV_PAULI_Y = 2,
+    SV_PAULI_Z = 3,
+    SV_HADAMARD = 4,
+    SV_S = 5,
+    SV_T = 6,
+    SV_PHASE_SHIFT = 7,
+    SV_RX = 8,
+    SV_RY = 9,
+    SV_RZ = 10,
+    SV_ROT = 11,
+    SV_SWAP = 12,
+    SV_ISING_XX = 13,
+    SV_ISING_YY = 14,
+    SV_ISING_ZZ = 15,
+    SV_ISING_XY = 16,
+    SV_SINGLE_EXCITATION = 17,
+    SV_DOUBLE_EXCITATION = 18,
+    SV_MATRIX = 19,          /* dense 2^k x 2^k matrix supplied by the tape */
+    SV_OP_KIND_COUNT = 20
+} sv_op_kind;
+
+/* One operation of a tape.
+ *   angle[a] = scale * params[param_index[a]]  if param_index[a] >= 0,
+ *            = const_angle[a]                   otherwise.
+ * A parameter may be used by several ops; its Jacobian column sums them.
+ * adjoint != 0 applies the conjugate transpose (the "inverse" flag of
+ * Listing 1).  Controls (Alg. 2): the op acts only on amplitudes whose control
+ * wires hold control_values (0 or 1).  SV_MATRIX ops read 4^k complex entries,
+ * row-major, interleaved (re, im), from tape->matrices + 2 * matrix_offset. */
+typedef struct {
+    int32_t kind;
+    int32_t n_targets;
+    int32_t targets[SV_MAX_TARGETS];
+    int32_t n_controls;
+    int32_t controls[SV_MAX_CONTROLS];
+    int32_t control_values[SV_MAX_CONTROLS];
+    int32_t param_index[3];
+    double const_angle[3];
+    double scale;
+    int32_t adjoint;
+    int64_t matrix_offset;
+} sv_op;
+
+typedef struct {
+    int32_t n_ops;
+    const sv_op *ops;
+    int32_t n_params;         /* length of the parameter vector = Jacobian columns */
+    const double *matrices;   /* SV_MATRIX data, may be NULL if no such op */
+    int64_t n_matrix_entries; /* complex entries available in matrices */
+} sv_tape;
+
+/* A Hamiltonian sum_t coeffs[t] * P_t (Listing 2).  Pauli word t acts with X on
+ * the wires in x_mask & ~z_mask, Y on x_mask & z_mask, Z on z_mask & ~x_mask;
+ * bit w of a mask is wire w (NOT an amplitude-index bit).  n_terms may be 0. */
+typedef struct {
+    int32_t n_terms;
+    const double *coeffs;
+    const uint64_t *x_mask;
+    const uint64_t *z_mask;
+} sv_pauli_sum;
+
+/* ---- library ------------------------------------------------------------ */
+
+/* Message of the last failed call on this thread ("" if none).  Owned by the
+ * library, valid until the next call on this thread. */
+const char *sv_last_error(void);
+
+/* Build identification string (compile flags, arch).  Static storage. */
+const char *sv_version(void);
+
+/* Cap on the device bytes the library itself allocates (0 = no cap).  Allocations
+ * that would exceed it fail with SV_ERR_OOM (used to test the OOM path). */
+sv_status sv_set_alloc_cap(size_t bytes);
+
+/* ---- state ---------------------------------------------------------------- */
+
+/* Allocate a 2^n state on the current CUDA device, initialised to |0...0>.
+ * 1 <= n <= SV_MAX_QUBITS.  *out owns its device buffer; free with sv_destroy. */
+sv_status sv_create(int n, sv_dtype dtype, sv_state **out);
+
+/* Wrap a caller-owned device buffer of 2^n amplitudes (interleaved re/im of the
+ * dtype's width, 256-byte aligned).  Contents are used as they are; the buffer
+ * must outlive the state. */
+sv_status sv_create_from_device_ptr(int n, sv_dtype dtype, void *device_ptr, sv_state **out);
+
+/* Release the state, its workspace and any library-owned buffer.  NULL is a no-op. */
+sv_status sv_destroy(sv_state *s);
+
+/* Issue all further work for s on this CUDA stream (cudaStream_t; NULL = legacy default). */
+sv_status sv_set_stream(sv_state *s, void *cuda_stream);
+
+/* Optional caller-owned device workspace used instead of library allocations
+ * while it is large enough (bytes >= sv_workspace_bytes for the request).
+ * NULL / 0 returns to library-owned workspace. */
+sv_status sv_set_workspace(sv_state *s, void *device_ptr, size_t bytes);
+
+/* Query: n, dtype and the device pointer of the amplitudes (any may be NULL). */
+sv_status sv_info(const sv_state *s, int *n, sv_dtype *dtype, void **device_ptr);
+
+/* |basis_index> (index bits: wire 0 = MSB).  Clears a latched SV_ERR_STATE. */
+sv_status sv_reset(sv_state *s, uint64_t basis_index);
+
+/* Copy 2^n amplitudes (interleaved re/im in the state's dtype) host -> state / state -> host. */
+sv_status sv_set_state(sv_state *s, const void *host_amplitudes);
+sv_status sv_get_state(sv_state *s, void *host_amplitudes);
+
+/* Wait for all work issued on the state's stream; reports latched device errors. */
+sv_status sv_synchronize(sv_state *s);
+
+/* ---- gates (S1-S3) ---------------------------------------------------------- */
+
+/* Apply one base gate (Sec. 2.1.1, Alg. 1; Listing 1 inverse flag):
+ * wires = its n_targets target wires, angles = its angles (NULL if none). */
+sv_status sv_apply(sv_state *s, int kind, const int *wires, int n_wires,
+                   const double *angles, int adjoint);
+
+/* Apply one tape op (controls and control values per Alg. 2); params is the
+ * parameter vector its param_index entries refer to (may be NULL if none). */
+sv_status sv_apply_op(sv_state *s, const sv_op *op, const double *params,
+                      const double *matrices);
+
+/* Apply a dense 2^k x 2^k matrix (row-major, interleaved re/im, k <= SV_MAX_TARGETS)
+ * to the k wires (Sec. 2.1.2, generic many-qubit gate). */
+sv_status sv_apply_matrix(sv_state *s, const int *wires, int k, const double *matrix, int adjoint);
+
+/* ---- measurements (S5) -------------------------------------------------------- */
+
+/* out[j] = <psi|H_j|psi> for j < n_obs (Sec. 2.2), FP64 accumulation (complex64:
+ * compensated FP32 per thread, FP64 across threads), fixed summation order:
+ * repeated calls give bitwise-equal results. */
+sv_status sv_expval(sv_state *s, const sv_pauli_sum *obs, int n_obs, double *out);
+
+/* out = <psi|psi> in FP64. */
+sv_status sv_norm2(sv_state *s, double *out);
+
+/* ---- circuits (S4, S6-S8) ----------------------------------------------------- */
+
+/* psi <- U_N ... U_1 psi for the tape with the given parameters.  Ops are fused
+ * into shared-memory passes (gate fusion, S4) without changing the result
+ * beyond rounding. */
+sv_status sv_forward(sv_state *s, const sv_tape *tape, const double *params);
+
+/* Adjoint-method Jacobian (the method the paper cites for Lightning's gradients,
+ * Sec. 2.1 / 3.1.1):  the state must hold psi = U(params)|psi0>, e.g. from
+ * sv_forward.  expvals_out[j] = <psi|H_j|psi> (may be NULL);
+ * jacobian_out[j * n_params + p] = d<H_j>/d params[p].  psi is not modified. */
+sv_status sv_adjoint_jacobian(sv_state *s, const sv_tape *tape, const double *params,
+                              const sv_pauli_sum *obs, int n_obs,
+                              double *expvals_out, double *jacobian_out);
+
+/* Vector-Jacobian product sum_j grad_out[j] * d<H_j>/d params (one backward
+ * sweep with lambda = sum_j grad_out[j] H_j psi).  Same precondition as above. */
+sv_status sv_adjoint_vjp(sv_state *s, const sv_tape *tape, const double *params,
+                         const sv_pauli_sum *obs, int n_obs, const double *grad_out,
+                         double *vjp_out);
+
+/* ---- planned programs (device-resident re-execution) --------------------------- */
+
+/* Plan a tape and observables once for state s: fusion passes, device tables and
+ * workspace are built here; later calls only move parameters.  The program keeps
+ * copies of everything it needs; tape and obs may be freed after the call. */
+sv_status sv_program_create(sv_state *s, const sv_tape *tape, const sv_pauli_sum *obs,
+                            int n_obs, sv_program **out);
+sv_status sv_program_destroy(sv_program *p);
+
+/* Parameters: n_params doubles, on the host (params_on_device = 0) or in device
+ * memory (1).  Gate matrices are rebuilt on the device from them. */
+sv_status sv_program_set_params(sv_program *p, const double *params, int params_on_device);
+
+/* Forward pass on the program's state (from its current contents). */
+sv_status sv_program_forward(sv_program *p);
+
+/* Expectation values and full Jacobian of the program's observables; outputs on
+ * the host (outputs_on_device = 0, the call synchronises) or device pointers (1,
+ * asynchronous on the state's stream).  expvals_out may be NULL. */
+sv_status sv_program_jacobian(sv_program *p, double *expvals_out, double *jacobian_out,
+                              int outputs_on_device);
+
+/* Expectation values of the program's observables for the current state
+ * (outputs on the host, synchronising, or device pointers, asynchronous). */
+sv_status sv_program_expval(sv_program *p, double *expvals_out, int outputs_on_device);
+
+/* Vector-Jacobian product of the program's observables for the current state:
+ * vjp_out[p] = sum_j grad_out[j] d<H_j>/d params[p], one backward sweep with
+ * lambda = sum_j grad_out[j] H_j psi (grad_out: m host doubles).  Output on the
+ * host (outputs_on_device = 0, synchronising) or in device memory (1).
+ * Device memory: psi plus two vectors (phi, lambda). */
+sv_status sv_program_vjp(sv_program *p, const double *grad_out, double *vjp_out, int outputs_on_device);
+
+/* Kernel launches issued by the last program call (for launch accounting). */
+sv_status sv_program_stats(const sv_program *p, int *n_forward_passes, int *n_adjoint_passes,
+                           int *launches_last_call);
+
+/* Host-only planner query (no GPU needed): number of fused forward passes and
+ * adjoint passes this build would use for a tape on n qubits and dtype. */
+sv_status sv_plan_query(int n, sv_dtype dtype, const sv_tape *tape,
+                        int *n_forward_passes, int *n_adjoint_passes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SV_H */

@@ -1,0 +1,380 @@
+"""ctypes binding of ``libsv.so`` (the C ABI declared in include/sv.h).
+
+Argument marshalling only: every step of the simulation runs in the CUDA
+library.  Functions keep the C names (``sv_create``, ``sv_apply``, ...), take
+Python / numpy arguments and raise :class:`SvError` on a non-zero status.
+There is no CPU fallback: if the library cannot be built or loaded, every
+call raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsv.so")
+
+SV_MAX_TARGETS = 6
+SV_MAX_CONTROLS = 8
+SV_MAX_QUBITS = 34
+
+SV_C64, SV_C128 = 0, 1
+
+STATUS = {0: "SV_OK", 1: "SV_ERR_ARG", 2: "SV_ERR_OOM", 3: "SV_ERR_CUDA", 4: "SV_ERR_TIMEOUT",
+          5: "SV_ERR_UNSUPPORTED", 6: "SV_ERR_STATE"}
+
+KIND = {
+    "Identity": 0, "PauliX": 1, "PauliY": 2, "PauliZ": 3, "Hadamard": 4, "S": 5, "T": 6,
+    "PhaseShift": 7, "RX": 8, "RY": 9, "RZ": 10, "Rot": 11, "SWAP": 12, "IsingXX": 13,
+    "IsingYY": 14, "IsingZZ": 15, "IsingXY": 16, "SingleExcitation": 17,
+    "DoubleExcitation": 18, "QubitUnitary": 19,
+}
+
+
+class SvError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class SvOp(ctypes.Structure):
+    _fields_ = [
+        ("kind", ctypes.c_int32),
+        ("n_targets", ctypes.c_int32),
+        ("targets", ctypes.c_int32 * SV_MAX_TARGETS),
+        ("n_controls", ctypes.c_int32),
+        ("controls", ctypes.c_int32 * SV_MAX_CONTROLS),
+        ("control_values", ctypes.c_int32 * SV_MAX_CONTROLS),
+        ("param_index", ctypes.c_int32 * 3),
+        ("const_angle", ctypes.c_double * 3),
+        ("scale", ctypes.c_double),
+        ("adjoint", ctypes.c_int32),
+        ("matrix_offset", ctypes.c_int64),
+    ]
+
+
+class SvTape(ctypes.Structure):
+    _fields_ = [
+        ("n_ops", ctypes.c_int32),
+        ("ops", ctypes.POINTER(SvOp)),
+        ("n_params", ctypes.c_int32),
+        ("matrices", ctypes.POINTER(ctypes.c_double)),
+        ("n_matrix_entries", ctypes.c_int64),
+    ]
+
+
+class SvPauliSum(ctypes.Structure):
+    _fields_ = [
+        ("n_terms", ctypes.c_int32),
+        ("coeffs", ctypes.POINTER(ctypes.c_double)),
+        ("x_mask", ctypes.POINTER(ctypes.c_uint64)),
+        ("z_mask", ctypes.POINTER(ctypes.c_uint64)),
+    ]
+
+
+# exported symbols and their prototypes: (restype, argtypes)
+_vp = ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+PROTOTYPES = {
+    "sv_last_error": (ctypes.c_char_p, []),
+    "sv_version": (ctypes.c_char_p, []),
+    "sv_set_alloc_cap": (ctypes.c_int, [ctypes.c_size_t]),
+    "sv_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(_vp)]),
+    "sv_create_from_device_ptr": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _vp, ctypes.POINTER(_vp)]),
+    "sv_destroy": (ctypes.c_int, [_vp]),
+    "sv_set_stream": (ctypes.c_int, [_vp, _vp]),
+    "sv_set_workspace": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t]),
+    "sv_info": (ctypes.c_int, [_vp, _ip, _ip, ctypes.POINTER(_vp)]),
+    "sv_reset": (ctypes.c_int, [_vp, ctypes.c_uint64]),
+    "sv_set_state": (ctypes.c_int, [_vp, _vp]),
+    "sv_get_state": (ctypes.c_int, [_vp, _vp]),
+    "sv_synchronize": (ctypes.c_int, [_vp]),
+    "sv_apply": (ctypes.c_int, [_vp, ctypes.c_int, _ip, ctypes.c_int, _dp, ctypes.c_int]),
+    "sv_apply_op": (ctypes.c_int, [_vp, ctypes.POINTER(SvOp), _dp, _dp]),
+    "sv_apply_matrix": (ctypes.c_int, [_vp, _ip, ctypes.c_int, _dp, ctypes.c_int]),
+    "sv_expval": (ctypes.c_int, [_vp, ctypes.POINTER(SvPauliSum), ctypes.c_int, _dp]),
+    "sv_norm2": (ctypes.c_int, [_vp, _dp]),
+    "sv_forward": (ctypes.c_int, [_vp, ctypes.POINTER(SvTape), _dp]),
+    "sv_adjoint_jacobian": (ctypes.c_int, [_vp, ctypes.POINTER(SvTape), _dp, ctypes.POINTER(SvPauliSum),
+                                           ctypes.c_int, _dp, _dp]),
+    "sv_adjoint_vjp": (ctypes.c_int, [_vp, ctypes.POINTER(SvTape), _dp, ctypes.POINTER(SvPauliSum),
+                                      ctypes.c_int, _dp, _dp]),
+    "sv_program_create": (ctypes.c_int, [_vp, ctypes.POINTER(SvTape), ctypes.POINTER(SvPauliSum),
+                                         ctypes.c_int, ctypes.POINTER(_vp)]),
+    "sv_program_destroy": (ctypes.c_int, [_vp]),
+    "sv_program_set_params": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
+    "sv_program_forward": (ctypes.c_int, [_vp]),
+    "sv_program_jacobian": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int]),
+    "sv_program_expval": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
+    "sv_program_vjp": (ctypes.c_int, [_vp, _dp, _vp, ctypes.c_int]),
+    "sv_program_stats": (ctypes.c_int, [_vp, _ip, _ip, _ip]),
+    "sv_plan_query": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(SvTape), _ip, _ip]),
+}
+
+_LIB: Optional[ctypes.CDLL] = None
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libsv.so (building it with nvcc first if it is absent or stale)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if build_if_missing:
+        from . import build as _build
+        _build.build()
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libsv.so not found at {LIB_PATH}; build it with paper_2403_02512_gb300.build")
+    L = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in PROTOTYPES.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = L
+    return L
+
+
+def _check(status: int) -> None:
+    if status != 0:
+        msg = load().sv_last_error()
+        raise SvError(status, msg.decode() if msg else "")
+
+
+def _dptr(a: Optional[np.ndarray]):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(_dp)
+
+
+def _iarr(xs: Sequence[int]):
+    return (ctypes.c_int * max(1, len(xs)))(*[int(x) for x in xs])
+
+
+# ---------------------------------------------------------------------------
+# Thin wrappers with the C names
+# ---------------------------------------------------------------------------
+def sv_version() -> str:
+    return load().sv_version().decode()
+
+
+def sv_set_alloc_cap(nbytes: int) -> None:
+    _check(load().sv_set_alloc_cap(int(nbytes)))
+
+
+def sv_create(n: int, dtype: int) -> int:
+    h = _vp()
+    _check(load().sv_create(int(n), int(dtype), ctypes.byref(h)))
+    return h.value
+
+
+def sv_create_from_device_ptr(n: int, dtype: int, device_ptr: int) -> int:
+    h = _vp()
+    _check(load().sv_create_from_device_ptr(int(n), int(dtype), _vp(device_ptr), ctypes.byref(h)))
+    return h.value
+
+
+def sv_destroy(h: int) -> None:
+    _check(load().sv_destroy(_vp(h)))
+
+
+def sv_set_stream(h: int, stream: int) -> None:
+    _check(load().sv_set_stream(_vp(h), _vp(stream)))
+
+
+def sv_set_workspace(h: int, device_ptr: int, nbytes: int) -> None:
+    _check(load().sv_set_workspace(_vp(h), _vp(device_ptr), int(nbytes)))
+
+
+def sv_info(h: int):
+    n, dt, ptr = ctypes.c_int(), ctypes.c_int(), _vp()
+    _check(load().sv_info(_vp(h), ctypes.byref(n), ctypes.byref(dt), ctypes.byref(ptr)))
+    return n.value, dt.value, ptr.value
+
+
+def sv_reset(h: int, basis_index: int = 0) -> None:
+    _check(load().sv_reset(_vp(h), int(basis_index)))
+
+
+def sv_set_state(h: int, host: np.ndarray) -> None:
+    assert host.flags["C_CONTIGUOUS"]
+    _check(load().sv_set_state(_vp(h), host.ctypes.data_as(_vp)))
+
+
+def sv_get_state(h: int, out: np.ndarray) -> np.ndarray:
+    assert out.flags["C_CONTIGUOUS"]
+    _check(load().sv_get_state(_vp(h), out.ctypes.data_as(_vp)))
+    return out
+
+
+def sv_synchronize(h: int) -> None:
+    _check(load().sv_synchronize(_vp(h)))
+
+
+def sv_apply(h: int, kind: int, wires: Sequence[int], angles: Optional[Sequence[float]] = None,
+             adjoint: bool = False) -> None:
+    a = None if angles is None or len(angles) == 0 else np.ascontiguousarray(angles, dtype=np.float64)
+    _check(load().sv_apply(_vp(h), int(kind), _iarr(wires), len(wires), _dptr(a), int(bool(adjoint))))
+
+
+def sv_apply_op(h: int, op: SvOp, params: Optional[np.ndarray] = None, matrices: Optional[np.ndarray] = None):
+    _check(load().sv_apply_op(_vp(h), ctypes.byref(op), _dptr(params), _dptr(matrices)))
+
+
+def sv_apply_matrix(h: int, wires: Sequence[int], matrix: np.ndarray, adjoint: bool = False) -> None:
+    m = np.ascontiguousarray(np.asarray(matrix, dtype=np.complex128)).view(np.float64).ravel()
+    k = len(wires)
+    assert m.size == 2 * (1 << (2 * k))
+    _check(load().sv_apply_matrix(_vp(h), _iarr(wires), k, _dptr(m), int(bool(adjoint))))
+
+
+def sv_expval(h: int, obs: "PauliSums") -> np.ndarray:
+    out = np.zeros(obs.count, dtype=np.float64)
+    _check(load().sv_expval(_vp(h), obs.array, obs.count, _dptr(out)))
+    return out
+
+
+def sv_norm2(h: int) -> float:
+    out = np.zeros(1)
+    _check(load().sv_norm2(_vp(h), _dptr(out)))
+    return float(out[0])
+
+
+def sv_forward(h: int, tape: "Tape", params: np.ndarray) -> None:
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    _check(load().sv_forward(_vp(h), ctypes.byref(tape.struct), _dptr(p)))
+
+
+def sv_adjoint_jacobian(h: int, tape: "Tape", params: np.ndarray, obs: "PauliSums"):
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    E = np.zeros(obs.count)
+    J = np.zeros((obs.count, tape.n_params))
+    _check(load().sv_adjoint_jacobian(_vp(h), ctypes.byref(tape.struct), _dptr(p), obs.array, obs.count,
+                                      _dptr(E), _dptr(J)))
+    return E, J
+
+
+def sv_adjoint_vjp(h: int, tape: "Tape", params: np.ndarray, obs: "PauliSums", grad_out) -> np.ndarray:
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    g = np.ascontiguousarray(grad_out, dtype=np.float64)
+    out = np.zeros(tape.n_params)
+    _check(load().sv_adjoint_vjp(_vp(h), ctypes.byref(tape.struct), _dptr(p), obs.array, obs.count, _dptr(g),
+                                 _dptr(out)))
+    return out
+
+
+def sv_program_create(h: int, tape: "Tape", obs: Optional["PauliSums"]) -> int:
+    ph = _vp()
+    arr = obs.array if obs is not None else None
+    cnt = obs.count if obs is not None else 0
+    _check(load().sv_program_create(_vp(h), ctypes.byref(tape.struct), arr, cnt, ctypes.byref(ph)))
+    return ph.value
+
+
+def sv_program_destroy(ph: int) -> None:
+    _check(load().sv_program_destroy(_vp(ph)))
+
+
+def sv_program_set_params(ph: int, params_ptr: int, on_device: bool) -> None:
+    _check(load().sv_program_set_params(_vp(ph), _vp(params_ptr), int(on_device)))
+
+
+def sv_program_forward(ph: int) -> None:
+    _check(load().sv_program_forward(_vp(ph)))
+
+
+def sv_program_jacobian(ph: int, expvals_ptr: int, jac_ptr: int, on_device: bool) -> None:
+    _check(load().sv_program_jacobian(_vp(ph), _vp(expvals_ptr), _vp(jac_ptr), int(on_device)))
+
+
+def sv_program_expval(ph: int, expvals_ptr: int, on_device: bool) -> None:
+    _check(load().sv_program_expval(_vp(ph), _vp(expvals_ptr), int(on_device)))
+
+
+def sv_program_vjp(ph: int, grad_out: np.ndarray, vjp_ptr: int, on_device: bool) -> None:
+    g = np.ascontiguousarray(grad_out, dtype=np.float64)
+    _check(load().sv_program_vjp(_vp(ph), _dptr(g), _vp(vjp_ptr), int(on_device)))
+
+
+def sv_program_stats(ph: int):
+    a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(load().sv_program_stats(_vp(ph), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return a.value, b.value, c.value
+
+
+def sv_plan_query(n: int, dtype: int, tape: "Tape"):
+    a, b = ctypes.c_int(), ctypes.c_int()
+    _check(load().sv_plan_query(int(n), int(dtype), ctypes.byref(tape.struct), ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+# ---------------------------------------------------------------------------
+# Marshalling of circuits and observables into the C structs
+# ---------------------------------------------------------------------------
+class Tape:
+    """An sv_tape built from a list of ops (objects with name / wires / params /
+    controls / control_values / adjoint / scale, e.g. ``workloads.Op``)."""
+
+    def __init__(self, ops, n_params: int, matrices: Optional[Sequence[np.ndarray]] = None):
+        self.ops = (SvOp * max(1, len(ops)))()
+        mats = []
+        moff = 0
+        for i, op in enumerate(ops):
+            o = self.ops[i]
+            o.kind = KIND[op.name]
+            o.n_targets = len(op.wires)
+            for j, w in enumerate(op.wires):
+                o.targets[j] = int(w)
+            ctrls = tuple(getattr(op, "controls", ()) or ())
+            cvals = tuple(getattr(op, "control_values", ()) or ()) or (1,) * len(ctrls)
+            o.n_controls = len(ctrls)
+            for c, (w, v) in enumerate(zip(ctrls, cvals)):
+                o.controls[c] = int(w)
+                o.control_values[c] = int(v)
+            pidx = tuple(getattr(op, "params", ()) or ())
+            for a in range(3):
+                o.param_index[a] = int(pidx[a]) if a < len(pidx) else -1
+            consts = tuple(getattr(op, "constants", ()) or ())
+            for a, v in enumerate(consts[:3]):
+                o.const_angle[a] = float(v)
+            o.scale = float(getattr(op, "scale", 1.0))
+            o.adjoint = int(bool(getattr(op, "adjoint", False)))
+            if op.name == "QubitUnitary":
+                m = np.ascontiguousarray(op.matrix, dtype=np.complex128)
+                o.matrix_offset = moff
+                mats.append(m.ravel())
+                moff += m.size
+        self.matrices = (np.ascontiguousarray(np.concatenate(mats)).view(np.float64)
+                         if mats else None)
+        self.n_params = int(n_params)
+        self.struct = SvTape(len(ops), self.ops, self.n_params, _dptr(self.matrices), moff)
+
+
+class PauliSums:
+    """A list of Hamiltonians (each a list of terms with ``coeff`` and
+    ``paulis`` = ((wire, 'X'|'Y'|'Z'), ...)) as an sv_pauli_sum array."""
+
+    def __init__(self, observables):
+        self.count = len(observables)
+        self.array = (SvPauliSum * max(1, self.count))()
+        self._keep = []
+        for j, H in enumerate(observables):
+            c = np.array([float(t.coeff) for t in H], dtype=np.float64)
+            x = np.zeros(len(H), dtype=np.uint64)
+            z = np.zeros(len(H), dtype=np.uint64)
+            for t, term in enumerate(H):
+                xm = zm = 0
+                for w, letter in term.paulis:
+                    if letter in ("X", "Y"):
+                        xm |= 1 << int(w)
+                    if letter in ("Y", "Z"):
+                        zm |= 1 << int(w)
+                x[t], z[t] = xm, zm
+            self._keep += [c, x, z]
+            self.array[j] = SvPauliSum(len(H), c.ctypes.data_as(_dp),
+                                       x.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                       z.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)))

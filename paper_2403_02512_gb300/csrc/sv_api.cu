@@ -1,0 +1,1463 @@
+// Host runtime and C ABI of libsv.so: argument validation, the gate-fusion
+// planner, planned programs (device tables + workspace) and the adjoint sweep
+// driver.  Device work goes through the Launch<R> launchers.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "sv.h"
+#include "sv_internal.h"
+
+using namespace sv;
+
+struct sv_state;
+
+namespace {
+
+thread_local std::string g_err;
+std::atomic<size_t> g_alloc_cap{0};
+std::atomic<size_t> g_alloc_bytes{0};
+
+sv_status fail(sv_status st, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+
+sv_status cuda_fail(cudaError_t e, const char *where) {
+  return fail(SV_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define SV_CUDA(call)                                  \
+  do {                                                 \
+    cudaError_t e_ = (call);                           \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+sv_status dev_alloc(void **p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) return SV_OK;
+  const size_t cap = g_alloc_cap.load();
+  if (cap && g_alloc_bytes.load() + bytes > cap)
+    return fail(SV_ERR_OOM, "allocation of %zu bytes exceeds the cap of %zu bytes", bytes, cap);
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(SV_ERR_OOM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+  }
+  g_alloc_bytes += bytes;
+  return SV_OK;
+}
+
+void dev_free(void *p, size_t bytes) {
+  if (!p) return;
+  cudaFree(p);
+  g_alloc_bytes -= bytes;
+}
+
+int sm_count() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
+  }
+  return n;
+}
+
+// ---- gate tables -----------------------------------------------------------
+int kind_arity(int kind) {
+  switch (kind) {
+    case SV_SWAP: case SV_ISING_XX: case SV_ISING_YY: case SV_ISING_ZZ: case SV_ISING_XY:
+    case SV_SINGLE_EXCITATION: return 2;
+    case SV_DOUBLE_EXCITATION: return 4;
+    case SV_MATRIX: return -1;
+    default: return 1;
+  }
+}
+
+int kind_nparams(int kind) {
+  switch (kind) {
+    case SV_PHASE_SHIFT: case SV_RX: case SV_RY: case SV_RZ: case SV_ISING_XX: case SV_ISING_YY:
+    case SV_ISING_ZZ: case SV_ISING_XY: case SV_SINGLE_EXCITATION: case SV_DOUBLE_EXCITATION: return 1;
+    case SV_ROT: return 3;
+    default: return 0;
+  }
+}
+
+bool kind_diag(int kind) {
+  switch (kind) {
+    case SV_IDENTITY: case SV_PAULI_Z: case SV_S: case SV_T: case SV_PHASE_SHIFT: case SV_RZ:
+    case SV_ISING_ZZ: return true;
+    default: return false;
+  }
+}
+
+// s of U(t) = exp(i s t G) for the one-angle kinds.
+double kind_gen_s(int kind) {
+  switch (kind) {
+    case SV_PHASE_SHIFT: return 1.0;
+    case SV_ISING_XY: return 0.25;
+    default: return -0.5;
+  }
+}
+
+// ---- host op ---------------------------------------------------------------
+struct HOp {
+  int kind = 0, k = 1;
+  int tw[kMaxTargets] = {0};
+  int nc = 0;
+  int cw[SV_MAX_CONTROLS] = {0};
+  int cv[SV_MAX_CONTROLS] = {0};
+  int pidx[3] = {-1, -1, -1};
+  double cang[3] = {0, 0, 0};
+  double scale = 1.0;
+  int adjoint = 0;
+  int64_t msrc = 0;
+  bool diag = false;
+  bool train = false;   // adjoint plan: one angle bound to a parameter
+  int uslot = -1;       // offset of U in the matrix buffer
+  int gslot = -1;       // offset of G
+};
+
+sv_status validate_op(int n, const sv_op &op, int n_params, const double *matrices, int64_t n_mat,
+                      const double *params, bool params_on_host) {
+  if (op.kind < 0 || op.kind >= SV_OP_KIND_COUNT) return fail(SV_ERR_ARG, "unknown op kind %d", op.kind);
+  const int ar = kind_arity(op.kind);
+  if (op.kind == SV_MATRIX) {
+    if (op.n_targets < 1 || op.n_targets > SV_MAX_TARGETS)
+      return fail(SV_ERR_ARG, "SV_MATRIX takes 1..%d targets, got %d", SV_MAX_TARGETS, op.n_targets);
+    const int64_t need = (int64_t)1 << (2 * op.n_targets);
+    if (!matrices || op.matrix_offset < 0 || op.matrix_offset + need > n_mat)
+      return fail(SV_ERR_ARG, "SV_MATRIX data out of range (offset %lld, %lld entries needed)",
+                  (long long)op.matrix_offset, (long long)need);
+    for (int64_t e = 0; e < 2 * need; ++e)
+      if (!std::isfinite(matrices[2 * op.matrix_offset + e])) return fail(SV_ERR_ARG, "SV_MATRIX entry is not finite");
+  } else if (op.n_targets != ar) {
+    return fail(SV_ERR_ARG, "op kind %d takes %d target wires, got %d", op.kind, ar, op.n_targets);
+  }
+  if (op.n_controls < 0 || op.n_controls > SV_MAX_CONTROLS)
+    return fail(SV_ERR_ARG, "n_controls %d out of range", op.n_controls);
+  uint64_t seen = 0;
+  for (int j = 0; j < op.n_targets; ++j) {
+    const int w = op.targets[j];
+    if (w < 0 || w >= n) return fail(SV_ERR_ARG, "target wire %d out of range [0, %d)", w, n);
+    if (seen >> w & 1) return fail(SV_ERR_ARG, "wire %d used twice in one op", w);
+    seen |= 1ull << w;
+  }
+  for (int c = 0; c < op.n_controls; ++c) {
+    const int w = op.controls[c];
+    if (w < 0 || w >= n) return fail(SV_ERR_ARG, "control wire %d out of range [0, %d)", w, n);
+    if (seen >> w & 1) return fail(SV_ERR_ARG, "wire %d used twice in one op", w);
+    seen |= 1ull << w;
+    if (op.control_values[c] != 0 && op.control_values[c] != 1)
+      return fail(SV_ERR_ARG, "control value must be 0 or 1");
+  }
+  const int np = kind_nparams(op.kind);
+  for (int a = 0; a < np; ++a) {
+    const int pi = op.param_index[a];
+    if (pi >= 0) {
+      if (pi >= n_params) return fail(SV_ERR_ARG, "param_index %d >= n_params %d", pi, n_params);
+      if (!std::isfinite(op.scale)) return fail(SV_ERR_ARG, "op scale is not finite");
+      if (params_on_host && params && !std::isfinite(params[pi]))
+        return fail(SV_ERR_ARG, "parameter %d is not finite", pi);
+    } else if (!std::isfinite(op.const_angle[a])) {
+      return fail(SV_ERR_ARG, "constant angle is not finite");
+    }
+  }
+  return SV_OK;
+}
+
+bool user_matrix_diag(const double *m, int64_t off, int k) {
+  const int D = 1 << k;
+  for (int r = 0; r < D; ++r)
+    for (int c = 0; c < D; ++c)
+      if (r != c && (m[2 * (off + (int64_t)r * D + c)] != 0.0 || m[2 * (off + (int64_t)r * D + c) + 1] != 0.0))
+        return false;
+  return true;
+}
+
+HOp to_hop(const sv_op &op, const double *matrices) {
+  HOp h;
+  h.kind = op.kind;
+  h.k = op.kind == SV_MATRIX ? op.n_targets : kind_arity(op.kind);
+  for (int j = 0; j < h.k; ++j) h.tw[j] = op.targets[j];
+  h.nc = op.n_controls;
+  for (int c = 0; c < h.nc; ++c) {
+    h.cw[c] = op.controls[c];
+    h.cv[c] = op.control_values[c];
+  }
+  for (int a = 0; a < 3; ++a) {
+    h.pidx[a] = a < kind_nparams(op.kind) ? op.param_index[a] : -1;
+    h.cang[a] = op.const_angle[a];
+  }
+  h.scale = op.scale;
+  h.adjoint = op.adjoint ? 1 : 0;
+  h.msrc = op.matrix_offset;
+  h.diag = op.kind == SV_MATRIX ? user_matrix_diag(matrices, op.matrix_offset, h.k) : kind_diag(op.kind);
+  return h;
+}
+
+// Rot(a, b, c) = RZ(c) RY(b) RZ(a): three one-angle ops (reversed and each
+// inverted under adjoint).  Every other op maps to itself.
+void expand_op(const HOp &h, std::vector<HOp> &out) {
+  if (h.kind != SV_ROT) {
+    HOp e = h;
+    e.train = kind_nparams(h.kind) == 1 && h.pidx[0] >= 0;
+    out.push_back(e);
+    return;
+  }
+  const int kinds[3] = {SV_RZ, SV_RY, SV_RZ};
+  int order[3] = {0, 1, 2};
+  if (h.adjoint) std::swap(order[0], order[2]);
+  for (int q = 0; q < 3; ++q) {
+    const int a = order[q];
+    HOp e = h;
+    e.kind = kinds[a];
+    e.pidx[0] = h.pidx[a];
+    e.pidx[1] = e.pidx[2] = -1;
+    e.cang[0] = h.cang[a];
+    e.diag = kind_diag(e.kind);
+    e.train = h.pidx[a] >= 0;
+    out.push_back(e);
+  }
+}
+
+// ---- planner -----------------------------------------------------------------
+struct Step {
+  int dense_k;  // 0: fused pass `index`; 1: dense k>4 op `index` (HOp index)
+  int index;
+};
+
+struct Plan {
+  std::vector<PassDev> passes;
+  std::vector<OpDev> ops;      // pass op tables, concatenated
+  std::vector<Step> steps;
+  std::vector<OpDev> dk_ops;   // one OpDev per dense_k step (global targets)
+  int n_train = 0;
+};
+
+int popc(uint64_t x) { return __builtin_popcountll(x); }
+
+uint64_t fill_bits(uint64_t bits, int n, int T, int nlow_pref) {
+  for (int b = 0; b < nlow_pref && b < n && popc(bits) < T; ++b) bits |= 1ull << b;
+  for (int b = 0; b < n && popc(bits) < T; ++b) bits |= 1ull << b;
+  return bits;
+}
+
+PassDev make_pass(int n, uint64_t bits) {
+  PassDev p;
+  memset(&p, 0, sizeof(p));
+  p.T = 0;
+  p.nhi = 0;
+  for (int b = 0; b < n; ++b) {
+    if (bits >> b & 1)
+      p.pos[p.T++] = b;
+    else
+      p.hi[p.nhi++] = b;
+  }
+  p.nlow = 0;
+  while (p.nlow < p.T && p.pos[p.nlow] == p.nlow) ++p.nlow;
+  p.max_k = 1;
+  return p;
+}
+
+OpDev make_opdev(int n, const HOp &h, const PassDev *pass) {
+  OpDev o;
+  memset(&o, 0, sizeof(o));
+  o.cls = h.diag ? kDiag : kDense;
+  o.k = h.k;
+  for (int j = 0; j < h.k; ++j) {
+    const int gb = n - 1 - h.tw[j];
+    o.tg[j] = gb;
+    o.tl[j] = -1;
+    if (pass && !h.diag)
+      for (int i = 0; i < pass->T; ++i)
+        if (pass->pos[i] == gb) o.tl[j] = i;
+  }
+  for (int c = 0; c < h.nc; ++c) {
+    const uint64_t b = 1ull << (n - 1 - h.cw[c]);
+    o.cmask |= b;
+    if (h.cv[c]) o.cval |= b;
+  }
+  o.mat = h.uslot;
+  o.gen = h.train ? h.gslot : -1;
+  o.train = -1;
+  o.slot = -1;
+  return o;
+}
+
+uint64_t low_bits(int n, int T, int nlow_pref) {
+  uint64_t b = 0;
+  for (int i = 0; i < nlow_pref && i < n && i < T; ++i) b |= 1ull << i;
+  return b;
+}
+
+// Greedy order-preserving fusion (S4): ops join the current pass while the
+// union of the local bits they need (non-diagonal targets) plus the lowest
+// index bits fits in T bits.  The lowest bits are always local, so every tile
+// is read as runs of >= 2^nlow_pref consecutive amplitudes (coalesced, and
+// 16-byte aligned for the paired complex64 accesses).
+Plan plan_passes(int n, const std::vector<HOp> &ops, int Tmax, int nlow_pref, int max_train) {
+  Plan P;
+  const int T = std::min(Tmax, n);
+  const uint64_t low = low_bits(n, T, nlow_pref);
+  uint64_t cur = low;
+  std::vector<int> cur_ops;
+  int cur_train = 0;
+  auto flush = [&]() {
+    if (cur_ops.empty()) return;
+    PassDev pd = make_pass(n, fill_bits(cur, n, T, nlow_pref));
+    pd.op_begin = (int)P.ops.size();
+    pd.train_base = P.n_train;
+    int t = 0;
+    for (int i : cur_ops) {
+      OpDev o = make_opdev(n, ops[i], &pd);
+      if (ops[i].train) {
+        o.train = t++;
+        o.slot = P.n_train++;
+      }
+      if (o.cls == kDense) pd.max_k = std::max(pd.max_k, o.k);
+      P.ops.push_back(o);
+    }
+    pd.op_end = (int)P.ops.size();
+    pd.n_train = t;
+    P.steps.push_back({0, (int)P.passes.size()});
+    P.passes.push_back(pd);
+    cur_ops.clear();
+    cur = low;
+    cur_train = 0;
+  };
+  for (int i = 0; i < (int)ops.size(); ++i) {
+    const HOp &h = ops[i];
+    if (!h.diag && h.k > kMaxTileTargets) {
+      flush();
+      OpDev o = make_opdev(n, h, nullptr);
+      P.steps.push_back({1, (int)P.dk_ops.size()});
+      P.dk_ops.push_back(o);
+      continue;
+    }
+    uint64_t need = 0;
+    if (!h.diag)
+      for (int j = 0; j < h.k; ++j) need |= 1ull << (n - 1 - h.tw[j]);
+    const bool fits = popc(cur | need) <= T && cur_train + (h.train ? 1 : 0) <= max_train;
+    if (!cur_ops.empty() && !fits) flush();
+    cur |= need;
+    cur_ops.push_back(i);
+    cur_train += h.train ? 1 : 0;
+  }
+  flush();
+  return P;
+}
+
+// Host-side check of a plan before anything is launched: every dense target is
+// a distinct local bit, tiles are at most kMaxLocalBits wide and their low run
+// covers the 16-byte pair accesses.
+sv_status check_plan(const Plan &P, int n, int nlow_pref) {
+  for (const PassDev &pd : P.passes) {
+    if (pd.T < 1 || pd.T > kMaxLocalBits || pd.T + pd.nhi != n)
+      return fail(SV_ERR_UNSUPPORTED, "internal planner error: tile of %d bits", pd.T);
+    if (pd.nlow < std::min(std::min(nlow_pref, n), pd.T))
+      return fail(SV_ERR_UNSUPPORTED, "internal planner error: low run of %d bits", pd.nlow);
+    for (int o = pd.op_begin; o < pd.op_end; ++o) {
+      const OpDev &op = P.ops[o];
+      if (op.cls != kDense) continue;
+      if (op.k > kMaxTileTargets) return fail(SV_ERR_UNSUPPORTED, "internal planner error: wide op in a tile");
+      for (int j = 0; j < op.k; ++j) {
+        if (op.tl[j] < 0 || op.tl[j] >= pd.T) return fail(SV_ERR_UNSUPPORTED, "internal planner error: non-local target");
+        for (int q = 0; q < j; ++q)
+          if (op.tl[q] == op.tl[j]) return fail(SV_ERR_UNSUPPORTED, "internal planner error: repeated target");
+      }
+    }
+  }
+  return SV_OK;
+}
+
+// ---- Pauli terms -------------------------------------------------------------
+struct HTerm {
+  int obs;
+  double coeff;
+  uint64_t x, z;  // global index bits
+  int ny;
+};
+
+uint64_t wire_mask_to_global(uint64_t wm, int n) {
+  uint64_t g = 0;
+  for (int w = 0; w < n; ++w)
+    if (wm >> w & 1) g |= 1ull << (n - 1 - w);
+  return g;
+}
+
+sv_status collect_terms(int n, const sv_pauli_sum *obs, int n_obs, std::vector<HTerm> &terms) {
+  if (n_obs < 0) return fail(SV_ERR_ARG, "n_obs < 0");
+  if (n_obs > 0 && !obs) return fail(SV_ERR_ARG, "observables pointer is NULL");
+  const uint64_t valid = n >= 64 ? ~0ull : ((1ull << n) - 1);
+  for (int o = 0; o < n_obs; ++o) {
+    const sv_pauli_sum &H = obs[o];
+    if (H.n_terms < 0) return fail(SV_ERR_ARG, "observable %d: n_terms < 0", o);
+    if (H.n_terms > 0 && (!H.coeffs || !H.x_mask || !H.z_mask))
+      return fail(SV_ERR_ARG, "observable %d: NULL term arrays", o);
+    for (int t = 0; t < H.n_terms; ++t) {
+      if ((H.x_mask[t] | H.z_mask[t]) & ~valid)
+        return fail(SV_ERR_ARG, "observable %d term %d acts on a wire >= n = %d", o, t, n);
+      if (!std::isfinite(H.coeffs[t])) return fail(SV_ERR_ARG, "observable %d term %d: coefficient not finite", o, t);
+      HTerm h;
+      h.obs = o;
+      h.coeff = H.coeffs[t];
+      h.x = wire_mask_to_global(H.x_mask[t], n);
+      h.z = wire_mask_to_global(H.z_mask[t], n);
+      h.ny = popc(H.x_mask[t] & H.z_mask[t]) & 3;
+      terms.push_back(h);
+    }
+  }
+  return SV_OK;
+}
+
+struct TermPlan {
+  std::vector<PassDev> passes;
+  std::vector<int> begin;  // terms of pass p: [begin[p], begin[p+1]) of `placed`
+  std::vector<int> placed; // original term index, in pass order
+};
+
+constexpr int kMaxTermsPerPass = 512;
+
+// Cover the terms' flip masks by passes: a term joins a pass when its X/Y wires
+// fit into the pass's T local bits; Z-only terms fit everywhere.  A pass starts
+// from the lowest index bits (coalesced tiles) unless its first term needs them.
+sv_status plan_terms(int n, const std::vector<HTerm> &terms, int Tmax, int nlow_pref, TermPlan &tp) {
+  const int T = std::min(Tmax, n);
+  std::vector<char> done(terms.size(), 0);
+  size_t left = terms.size();
+  tp.begin.assign(1, 0);
+  do {
+    uint64_t bits = fill_bits(0, n, std::min(T, nlow_pref), nlow_pref);
+    int cnt = 0;
+    for (size_t t = 0; t < terms.size() && cnt < kMaxTermsPerPass; ++t) {
+      if (done[t]) continue;
+      const uint64_t nb = bits | terms[t].x;
+      if (cnt == 0 && popc(nb) > T)
+        return fail(SV_ERR_UNSUPPORTED, "a Pauli word flips %d wires; a tile has room for %d besides its low bits",
+                    popc(terms[t].x), T - std::min(T, nlow_pref));
+      if (popc(nb) <= T) {
+        bits = nb;
+        done[t] = 1;
+        tp.placed.push_back((int)t);
+        ++cnt;
+        --left;
+      }
+    }
+    tp.passes.push_back(make_pass(n, fill_bits(bits, n, T, nlow_pref)));
+    tp.begin.push_back((int)tp.placed.size());
+  } while (left > 0);
+  return SV_OK;
+}
+
+TermDev make_termdev(const HTerm &h, const PassDev &p) {
+  TermDev t;
+  memset(&t, 0, sizeof(t));
+  t.xg = h.x;
+  t.zg = h.z;
+  uint32_t xl = 0;
+  for (int i = 0; i < p.T; ++i)
+    if (h.x >> p.pos[i] & 1) xl |= 1u << i;
+  t.xl = xl;
+  t.ny = h.ny;
+  t.obs = h.obs;
+  t.coeff = h.coeff;
+  return t;
+}
+
+// ---- precision dispatch ---------------------------------------------------------
+struct Ops {
+  decltype(&Launch<float>::build_matrices) build_matrices;
+  decltype(&Launch<float>::tile_forward) tile_forward;
+  decltype(&Launch<float>::tile_adjoint) tile_adjoint;
+  decltype(&Launch<float>::expval_pass) expval_pass;
+  decltype(&Launch<float>::lambda_pass) lambda_pass;
+  decltype(&Launch<float>::dense_k) dense_k;
+  decltype(&Launch<float>::set_basis) set_basis;
+  decltype(&Launch<float>::copy) copy;
+  int amp_bytes, Tf, Ta, nlow_pref;
+};
+
+const Ops &ops_for(sv_dtype dt) {
+  static const Ops f32 = {Launch<float>::build_matrices, Launch<float>::tile_forward,
+                          Launch<float>::tile_adjoint,   Launch<float>::expval_pass,
+                          Launch<float>::lambda_pass,    Launch<float>::dense_k,
+                          Launch<float>::set_basis,      Launch<float>::copy,
+                          8, Launch<float>::max_T_forward(), Launch<float>::max_T_adjoint(), 4};
+  static const Ops f64 = {Launch<double>::build_matrices, Launch<double>::tile_forward,
+                          Launch<double>::tile_adjoint,   Launch<double>::expval_pass,
+                          Launch<double>::lambda_pass,    Launch<double>::dense_k,
+                          Launch<double>::set_basis,      Launch<double>::copy,
+                          16, Launch<double>::max_T_forward(), Launch<double>::max_T_adjoint(), 3};
+  return dt == SV_C64 ? f32 : f64;
+}
+
+constexpr int kMaxTrainPerPass = 64;
+
+}  // namespace
+
+// ---- state -----------------------------------------------------------------------
+struct sv_state {
+  int n = 0;
+  sv_dtype dt = SV_C128;
+  void *psi = nullptr;
+  bool owns = false;
+  size_t bytes = 0;  // bytes of one vector
+  cudaStream_t stream = nullptr;
+  void *ws = nullptr;        // library-owned workspace arena
+  size_t ws_bytes = 0;
+  void *user_ws = nullptr;   // caller-provided workspace
+  size_t user_ws_bytes = 0;
+  void *tab = nullptr;       // table arena for one-shot programs
+  size_t tab_bytes = 0;
+  int latched = 0;
+};
+
+namespace {
+
+sv_status check_state(const sv_state *s) {
+  if (!s) return fail(SV_ERR_ARG, "state is NULL");
+  if (s->latched) return fail(SV_ERR_STATE, "an earlier device error is latched on this state; call sv_reset");
+  return SV_OK;
+}
+
+sv_status after_launch(sv_state *s, cudaError_t e, const char *what) {
+  if (e != cudaSuccess) {
+    s->latched = 1;
+    return cuda_fail(e, what);
+  }
+  return SV_OK;
+}
+
+// Workspace: the caller's buffer when big enough, else a grow-only library arena.
+sv_status get_workspace(sv_state *s, size_t bytes, char **out) {
+  if (s->user_ws && s->user_ws_bytes >= bytes) {
+    *out = (char *)s->user_ws;
+    return SV_OK;
+  }
+  if (s->ws_bytes < bytes) {
+    if (s->ws) {
+      cudaStreamSynchronize(s->stream);
+      dev_free(s->ws, s->ws_bytes);
+      s->ws = nullptr;
+      s->ws_bytes = 0;
+    }
+    sv_status st = dev_alloc(&s->ws, bytes);
+    if (st) return st;
+    s->ws_bytes = bytes;
+  }
+  *out = (char *)s->ws;
+  return SV_OK;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+// ---- program ----------------------------------------------------------------------
+struct sv_program {
+  sv_state *s = nullptr;
+  int n_params = 0, m = 0;
+  bool owns_tables = true;
+  void *tables = nullptr;
+  size_t tables_bytes = 0;
+  Plan fwd, adj;
+  TermPlan tp;
+  std::vector<HTerm> terms;
+  std::vector<double> coef;   // per trainable slot: scale * (-2 s_eff)
+  int n_slots = 0;
+  size_t mats_entries = 0;
+  // device pointers into `tables`
+  OpDev *d_fwd_ops = nullptr, *d_adj_ops = nullptr;
+  MatSlot *d_slots = nullptr;
+  void *d_mats = nullptr;
+  double *d_params = nullptr, *d_user = nullptr;
+  TermDev *d_terms = nullptr;
+  int32_t *d_obs_begin = nullptr, *d_term_order = nullptr;
+  TermDev *d_lam_terms = nullptr;
+  int32_t *d_lam_begin = nullptr;
+  double *d_coef = nullptr;
+  int32_t *d_pbegin = nullptr, *d_pslots = nullptr;
+  // lambda chunking
+  int mc = 0, n_chunks = 0;
+  std::vector<int> lam_begin_off;  // per (chunk, pass): offset into d_lam_begin
+  // VJP: every placed term with obs 0, coefficient c_t * g_obs(t) set per call
+  std::vector<TermDev> vjp_host;
+  TermDev *d_vjp_terms = nullptr;
+  int32_t *d_vjp_begin = nullptr;
+  // grids
+  int grid_f = 1, grid_e = 1;
+  int ctas_a = 1, ctas_l = 1;        // CTAs per adjoint / lambda launch (split over lambdas)
+  uint64_t tiles_a = 1, tiles_l = 1; // tiles per vector in those passes
+  int grid_a(int mcc) const { return (int)std::max<uint64_t>(1, std::min<uint64_t>(tiles_a, ctas_a / std::max(1, mcc))); }
+  int grid_l(int mcc) const { return (int)std::max<uint64_t>(1, std::min<uint64_t>(tiles_l, ctas_l / std::max(1, mcc))); }
+  int launches = 0;
+};
+
+namespace {
+
+void destroy_program(sv_program *p) {
+  if (!p) return;
+  if (p->owns_tables && p->tables) dev_free(p->tables, p->tables_bytes);
+  delete p;
+}
+
+int blocks_per_sm(int smem_bytes) {
+  const int by_threads = 2048 / kBlock;
+  const int by_smem = (228 * 1024) / (smem_bytes + 1024);
+  return std::max(1, std::min(by_threads, by_smem));
+}
+
+sv_status build_program(sv_state *s, const sv_tape *tape, const sv_pauli_sum *obs, int n_obs,
+                        const double *host_params, bool one_shot, sv_program **out) {
+  *out = nullptr;
+  const int n = s->n;
+  const Ops &K = ops_for(s->dt);
+  int n_ops = 0, n_params = 0;
+  const sv_op *ops = nullptr;
+  const double *umats = nullptr;
+  int64_t n_umat = 0;
+  if (tape) {
+    if (tape->n_ops < 0 || tape->n_params < 0) return fail(SV_ERR_ARG, "negative tape sizes");
+    if (tape->n_ops > 0 && !tape->ops) return fail(SV_ERR_ARG, "tape ops pointer is NULL");
+    n_ops = tape->n_ops;
+    n_params = tape->n_params;
+    ops = tape->ops;
+    umats = tape->matrices;
+    n_umat = tape->n_matrix_entries;
+  }
+  for (int i = 0; i < n_ops; ++i) {
+    sv_status st = validate_op(n, ops[i], n_params, umats, n_umat, host_params, host_params != nullptr);
+    if (st) {
+      g_err = "op " + std::to_string(i) + ": " + g_err;
+      return st;
+    }
+  }
+  std::vector<HTerm> terms;
+  if (sv_status st = collect_terms(n, obs, n_obs, terms)) return st;
+
+  sv_program *p = new sv_program();
+  p->s = s;
+  p->n_params = n_params;
+  p->m = n_obs;
+  p->owns_tables = !one_shot;
+  p->terms = terms;
+
+  // host ops and matrix slots
+  std::vector<HOp> fops, aops;
+  std::vector<MatSlot> slots;
+  size_t off = 0;
+  auto add_slot = [&](const HOp &h, int what) -> int {
+    MatSlot m;
+    memset(&m, 0, sizeof(m));
+    m.kind = h.kind;
+    m.k = h.k;
+    m.adjoint = h.adjoint;
+    m.diag = h.diag ? 1 : 0;
+    m.what = what;
+    m.out = (int)off;
+    for (int a = 0; a < 3; ++a) {
+      m.pidx[a] = h.pidx[a];
+      m.cangle[a] = h.cang[a];
+    }
+    m.scale = h.scale;
+    m.src = h.msrc;
+    slots.push_back(m);
+    off += h.diag ? (size_t)1 << h.k : (size_t)1 << (2 * h.k);
+    return m.out;
+  };
+  for (int i = 0; i < n_ops; ++i) {
+    HOp h = to_hop(ops[i], umats);
+    h.uslot = add_slot(h, 0);
+    fops.push_back(h);
+    std::vector<HOp> ex;
+    expand_op(h, ex);
+    for (HOp &e : ex) {
+      if (e.kind == h.kind)
+        e.uslot = h.uslot;
+      else
+        e.uslot = add_slot(e, 0);
+      if (e.train) e.gslot = add_slot(e, 1);
+      aops.push_back(e);
+    }
+  }
+  p->n_slots = (int)slots.size();
+  p->mats_entries = off;
+
+  p->fwd = plan_passes(n, fops, K.Tf, K.nlow_pref, 1 << 30);
+  p->adj = plan_passes(n, aops, K.Ta, K.nlow_pref, kMaxTrainPerPass);
+  if (sv_status st = check_plan(p->fwd, n, K.nlow_pref)) {
+    destroy_program(p);
+    return st;
+  }
+  if (sv_status st = check_plan(p->adj, n, K.nlow_pref)) {
+    destroy_program(p);
+    return st;
+  }
+
+  // trainable slots (sweep order = adjoint plan order) -> coefficient and parameter CSR
+  std::vector<int> slot_param;
+  {
+    std::vector<double> coef;
+    // walk the adjoint passes' ops in order; OpDev.slot was assigned in that order
+    std::vector<std::pair<int, int>> hop_of_slot;  // slot -> aops index
+    int ai = 0;
+    for (const Step &st : p->adj.steps) {
+      (void)st;
+    }
+    // aops order equals op-table order (plan_passes keeps op order); recover per slot
+    coef.resize(p->adj.n_train);
+    slot_param.resize(p->adj.n_train);
+    int slot = 0;
+    for (ai = 0; ai < (int)aops.size(); ++ai) {
+      const HOp &e = aops[ai];
+      if (!e.train) continue;
+      const double s_eff = e.adjoint ? -kind_gen_s(e.kind) : kind_gen_s(e.kind);
+      coef[slot] = e.scale * (-2.0 * s_eff);
+      slot_param[slot] = e.pidx[0];
+      ++slot;
+    }
+    p->coef = coef;
+  }
+  std::vector<int32_t> pbegin(n_params + 1, 0), pslots;
+  for (int sidx = 0; sidx < (int)slot_param.size(); ++sidx) pbegin[slot_param[sidx] + 1]++;
+  for (int q = 0; q < n_params; ++q) pbegin[q + 1] += pbegin[q];
+  pslots.resize(slot_param.size());
+  {
+    std::vector<int32_t> fillp(pbegin.begin(), pbegin.end() - 1);
+    for (int sidx = 0; sidx < (int)slot_param.size(); ++sidx) pslots[fillp[slot_param[sidx]]++] = sidx;
+  }
+
+  // observables: passes covering the terms
+  std::vector<TermDev> tdev;
+  std::vector<int32_t> obs_begin(n_obs + 1, 0), term_order;
+  if (n_obs > 0) {
+    if (sv_status st = plan_terms(n, terms, K.Tf, K.nlow_pref, p->tp)) {
+      destroy_program(p);
+      return st;
+    }
+    std::vector<int> dev_index(terms.size());
+    for (size_t pi = 0; pi + 1 < p->tp.begin.size(); ++pi)
+      for (int q = p->tp.begin[pi]; q < p->tp.begin[pi + 1]; ++q) {
+        const int t = p->tp.placed[q];
+        dev_index[t] = (int)tdev.size();
+        tdev.push_back(make_termdev(terms[t], p->tp.passes[pi]));
+      }
+    for (size_t t = 0; t < terms.size(); ++t) obs_begin[terms[t].obs + 1]++;
+    for (int o = 0; o < n_obs; ++o) obs_begin[o + 1] += obs_begin[o];
+    term_order.resize(terms.size());
+    std::vector<int32_t> fillo(obs_begin.begin(), obs_begin.end() - 1);
+    for (size_t t = 0; t < terms.size(); ++t) term_order[fillo[terms[t].obs]++] = dev_index[t];
+  }
+
+  // lambda chunk size from free device memory
+  const size_t V = s->bytes;
+  int mc = n_obs;
+  if (n_obs > 0) {
+    size_t freeb = 0, totalb = 0;
+    if (cudaMemGetInfo(&freeb, &totalb) != cudaSuccess) {
+      cudaGetLastError();
+      freeb = 0;
+    }
+    size_t have = s->ws_bytes + (size_t)(0.85 * (double)freeb);
+    const size_t fixed = 2 * V + ((size_t)64 << 20);
+    size_t cap = have > fixed ? (have - fixed) / V : 1;
+    if (const char *env = getenv("SV_LAMBDA_CHUNK")) cap = std::max(1, atoi(env));
+    mc = (int)std::max<size_t>(1, std::min<size_t>((size_t)n_obs, cap));
+  }
+  p->mc = mc;
+  p->n_chunks = n_obs > 0 ? (n_obs + mc - 1) / mc : 0;
+
+  // lambda term tables per (chunk, pass): terms of each observable in the chunk
+  std::vector<TermDev> ltdev;
+  std::vector<int32_t> lbegin;
+  const int npass_e = (int)p->tp.passes.size();
+  for (int c = 0; c < p->n_chunks; ++c) {
+    const int j0 = c * mc, j1 = std::min(n_obs, j0 + mc);
+    for (int pi = 0; pi < npass_e; ++pi) {
+      p->lam_begin_off.push_back((int)lbegin.size());
+      for (int o = j0; o < j1; ++o) {
+        lbegin.push_back((int)ltdev.size());
+        for (int q = p->tp.begin[pi]; q < p->tp.begin[pi + 1]; ++q) {
+          const int t = p->tp.placed[q];
+          if (terms[t].obs == o) ltdev.push_back(make_termdev(terms[t], p->tp.passes[pi]));
+        }
+      }
+      lbegin.push_back((int)ltdev.size());
+    }
+  }
+
+  // VJP tables: pass q holds placed terms [tp.begin[q], tp.begin[q+1]) as observable 0
+  std::vector<int32_t> vbegin;
+  for (int q = 0; q < npass_e; ++q) {
+    for (int i = p->tp.begin[q]; i < p->tp.begin[q + 1]; ++i) {
+      TermDev t = make_termdev(terms[p->tp.placed[i]], p->tp.passes[q]);
+      t.obs = 0;
+      p->vjp_host.push_back(t);
+    }
+    vbegin.push_back(p->tp.begin[q]);
+    vbegin.push_back(p->tp.begin[q + 1]);
+  }
+
+  // grids
+  const int sms = sm_count();
+  {
+    int tmax = std::min(K.Tf, n);
+    p->grid_f = std::max(1, std::min((int)std::min<uint64_t>(1ull << (n - tmax), 1 << 30),
+                                     2 * sms * blocks_per_sm((K.amp_bytes << tmax) + 4096)));
+    int ta = std::min(K.Ta, n);
+    p->ctas_a = 2 * sms * blocks_per_sm(2 * (K.amp_bytes << ta) + 8192);
+    p->tiles_a = 1ull << (n - ta);
+    p->grid_e = std::max(1, std::min((int)std::min<uint64_t>(1ull << (n - tmax), 1 << 30),
+                                     sms * blocks_per_sm((K.amp_bytes << tmax) + 4096 + 32768)));
+    p->ctas_l = 2 * sms * blocks_per_sm((K.amp_bytes << tmax) + 4096);
+    p->tiles_l = 1ull << (n - tmax);
+  }
+
+  // one device allocation for every table
+  auto sz = [](size_t count, size_t elem) { return align256(count * elem); };
+  const size_t umat_doubles = umats ? (size_t)2 * (size_t)n_umat : 0;
+  size_t total = sz(p->fwd.ops.size(), sizeof(OpDev)) + sz(p->adj.ops.size(), sizeof(OpDev)) +
+                 sz(slots.size(), sizeof(MatSlot)) + sz(off, K.amp_bytes) + sz(std::max(n_params, 1), 8) +
+                 sz(umat_doubles, 8) + sz(tdev.size(), sizeof(TermDev)) + sz(obs_begin.size(), 4) +
+                 sz(term_order.size(), 4) + sz(ltdev.size(), sizeof(TermDev)) + sz(lbegin.size(), 4) +
+                 sz(p->coef.size(), 8) + sz(pbegin.size(), 4) + sz(pslots.size(), 4) +
+                 sz(p->vjp_host.size(), sizeof(TermDev)) + sz(vbegin.size(), 4);
+  total = std::max<size_t>(total, 256);
+  if (one_shot) {
+    if (s->tab_bytes < total) {
+      if (s->tab) {
+        cudaStreamSynchronize(s->stream);
+        dev_free(s->tab, s->tab_bytes);
+        s->tab = nullptr;
+        s->tab_bytes = 0;
+      }
+      if (sv_status st = dev_alloc(&s->tab, total)) {
+        destroy_program(p);
+        return st;
+      }
+      s->tab_bytes = total;
+    }
+    p->tables = s->tab;
+  } else {
+    if (sv_status st = dev_alloc(&p->tables, total)) {
+      destroy_program(p);
+      return st;
+    }
+  }
+  p->tables_bytes = total;
+  std::vector<char> host(total, 0);
+  size_t cursor = 0;
+  auto put = [&](const void *src, size_t count, size_t elem) -> char * {
+    char *dptr = (char *)p->tables + cursor;
+    if (count) memcpy(host.data() + cursor, src, count * elem);
+    cursor += align256(count * elem);
+    return dptr;
+  };
+  p->d_fwd_ops = (OpDev *)put(p->fwd.ops.data(), p->fwd.ops.size(), sizeof(OpDev));
+  p->d_adj_ops = (OpDev *)put(p->adj.ops.data(), p->adj.ops.size(), sizeof(OpDev));
+  p->d_slots = (MatSlot *)put(slots.data(), slots.size(), sizeof(MatSlot));
+  p->d_mats = put(nullptr, 0, 1);
+  cursor += align256(off * K.amp_bytes);
+  p->d_params = (double *)put(nullptr, 0, 1);
+  cursor += align256(std::max(n_params, 1) * 8);
+  p->d_user = (double *)put(umats, umat_doubles, 8);
+  p->d_terms = (TermDev *)put(tdev.data(), tdev.size(), sizeof(TermDev));
+  p->d_obs_begin = (int32_t *)put(obs_begin.data(), obs_begin.size(), 4);
+  p->d_term_order = (int32_t *)put(term_order.data(), term_order.size(), 4);
+  p->d_lam_terms = (TermDev *)put(ltdev.data(), ltdev.size(), sizeof(TermDev));
+  p->d_lam_begin = (int32_t *)put(lbegin.data(), lbegin.size(), 4);
+  p->d_coef = (double *)put(p->coef.data(), p->coef.size(), 8);
+  p->d_pbegin = (int32_t *)put(pbegin.data(), pbegin.size(), 4);
+  p->d_pslots = (int32_t *)put(pslots.data(), pslots.size(), 4);
+  p->d_vjp_terms = (TermDev *)put(p->vjp_host.data(), p->vjp_host.size(), sizeof(TermDev));
+  p->d_vjp_begin = (int32_t *)put(vbegin.data(), vbegin.size(), 4);
+  cudaError_t e = cudaMemcpyAsync(p->tables, host.data(), total, cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess && one_shot) e = cudaStreamSynchronize(s->stream);  // host staging freed on return
+  if (e != cudaSuccess) {
+    destroy_program(p);
+    return cuda_fail(e, "uploading program tables");
+  }
+  if (!one_shot) {
+    e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) {
+      destroy_program(p);
+      return cuda_fail(e, "uploading program tables");
+    }
+  }
+  *out = p;
+  return SV_OK;
+}
+
+sv_status program_set_params(sv_program *p, const double *params, int on_device) {
+  sv_state *s = p->s;
+  const Ops &K = ops_for(s->dt);
+  if (p->n_params > 0) {
+    if (!params) return fail(SV_ERR_ARG, "params is NULL but the tape has %d parameters", p->n_params);
+    if (!on_device)
+      for (int i = 0; i < p->n_params; ++i)
+        if (!std::isfinite(params[i])) return fail(SV_ERR_ARG, "parameter %d is not finite", i);
+    cudaError_t e = cudaMemcpyAsync(p->d_params, params, (size_t)p->n_params * 8,
+                                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "copying parameters");
+  }
+  p->launches = 0;
+  sv_status st = after_launch(s, K.build_matrices(p->d_slots, p->n_slots, p->d_params, p->d_user, p->d_mats, s->stream),
+                              "build_matrices");
+  p->launches += p->n_slots > 0;
+  return st;
+}
+
+sv_status run_steps_forward(sv_program *p, void *psi) {
+  sv_state *s = p->s;
+  const Ops &K = ops_for(s->dt);
+  for (const Step &st : p->fwd.steps) {
+    cudaError_t e;
+    if (st.dense_k)
+      e = K.dense_k(psi, s->n, p->fwd.dk_ops[st.index], p->d_mats, 0, s->stream);
+    else
+      e = K.tile_forward(psi, s->n, p->fwd.passes[st.index], p->d_fwd_ops, p->d_mats, p->grid_f, s->stream);
+    if (sv_status r = after_launch(s, e, "forward pass")) return r;
+    ++p->launches;
+  }
+  return SV_OK;
+}
+
+// Workspace layout of a Jacobian call.
+struct JacWs {
+  char *phiA, *phiB, *lam;
+  double *partials, *contrib, *term_sums, *expvals, *J;
+};
+
+sv_status jac_workspace(sv_program *p, JacWs &w) {
+  sv_state *s = p->s;
+  const size_t V = s->bytes;
+  size_t max_train = 1;
+  for (const PassDev &pd : p->adj.passes) max_train = std::max<size_t>(max_train, pd.n_train);
+  size_t max_terms = 1;
+  for (size_t q = 0; q + 1 < p->tp.begin.size(); ++q)
+    max_terms = std::max<size_t>(max_terms, p->tp.begin[q + 1] - p->tp.begin[q]);
+  const size_t part = std::max((size_t)(p->ctas_a + p->mc) * max_train, (size_t)p->grid_e * max_terms);
+  const bool need_vec = p->adj.n_train > 0 || !p->adj.dk_ops.empty();
+  const size_t bytes = (need_vec ? 2 * V + (size_t)p->mc * V : 0) + align256(part * 8) +
+                       align256((size_t)std::max(1, p->adj.n_train) * std::max(1, p->m) * 8) +
+                       align256(std::max<size_t>(1, p->terms.size()) * 8) + align256((size_t)std::max(1, p->m) * 8) +
+                       align256((size_t)std::max(1, p->m) * std::max(1, p->n_params) * 8);
+  char *base = nullptr;
+  if (sv_status st = get_workspace(s, bytes, &base)) return st;
+  size_t c = 0;
+  w.phiA = base + c;
+  c += need_vec ? V : 0;
+  w.phiB = base + c;
+  c += need_vec ? V : 0;
+  w.lam = base + c;
+  c += need_vec ? (size_t)p->mc * V : 0;
+  w.partials = (double *)(base + c);
+  c += align256(part * 8);
+  w.contrib = (double *)(base + c);
+  c += align256((size_t)std::max(1, p->adj.n_train) * std::max(1, p->m) * 8);
+  w.term_sums = (double *)(base + c);
+  c += align256(std::max<size_t>(1, p->terms.size()) * 8);
+  w.expvals = (double *)(base + c);
+  c += align256((size_t)std::max(1, p->m) * 8);
+  w.J = (double *)(base + c);
+  return SV_OK;
+}
+
+sv_status run_expval(sv_program *p, const void *psi, const JacWs &w) {
+  sv_state *s = p->s;
+  const Ops &K = ops_for(s->dt);
+  for (size_t q = 0; q + 1 < p->tp.begin.size(); ++q) {
+    const int b = p->tp.begin[q], cnt = p->tp.begin[q + 1] - b;
+    if (cnt == 0) continue;
+    cudaError_t e = K.expval_pass(psi, s->n, p->tp.passes[q], p->d_terms + b, cnt, w.partials, p->grid_e, s->stream);
+    if (sv_status r = after_launch(s, e, "expval pass")) return r;
+    e = reduce_partials(w.partials, p->grid_e, 1, cnt, w.term_sums, 1, b, 0, s->stream);
+    if (sv_status r = after_launch(s, e, "expval reduce")) return r;
+    p->launches += 2;
+  }
+  cudaError_t e = combine_terms(w.term_sums, p->d_terms, p->d_obs_begin, p->m, p->d_term_order, w.expvals, s->stream);
+  p->launches += p->m > 0;
+  return after_launch(s, e, "combine terms");
+}
+
+// One backward sweep (S6 + S7) for mcc lambdas, written into contrib columns
+// [j0, j0 + mcc) (leading dimension ldc).  lam_begin(q) gives the per-observable
+// term ranges of expectation pass q in lam_terms.
+template <typename BeginFn>
+sv_status run_sweep(sv_program *p, const JacWs &w, int mcc, int j0, int ldc, const TermDev *lam_terms,
+                    BeginFn lam_begin) {
+  sv_state *s = p->s;
+  const Ops &K = ops_for(s->dt);
+  const int n = s->n;
+  const size_t V = s->bytes;
+  const int npass_e = (int)p->tp.passes.size();
+  for (int q = 0; q < npass_e; ++q) {
+    cudaError_t e = K.lambda_pass(s->psi, w.lam, n, p->tp.passes[q], lam_terms, lam_begin(q), mcc, q == 0,
+                                  p->grid_l(mcc), s->stream);
+    if (sv_status r = after_launch(s, e, "lambda pass")) return r;
+    ++p->launches;
+  }
+  // phi starts as psi (read only); with one lambda later passes update phi in place.
+  const void *phi_in = s->psi;
+  char *phi_out = w.phiA;
+  auto advance = [&]() {
+    phi_in = phi_out;
+    if (mcc > 1) phi_out = (phi_out == w.phiA) ? w.phiB : w.phiA;
+  };
+  for (int si = (int)p->adj.steps.size() - 1; si >= 0; --si) {
+    const Step &st = p->adj.steps[si];
+    if (st.dense_k) {
+      if (phi_in == s->psi) {
+        if (sv_status r = after_launch(s, K.copy(phi_out, s->psi, n, s->stream), "copy phi")) return r;
+        advance();
+      }
+      const OpDev &op = p->adj.dk_ops[st.index];
+      cudaError_t e = K.dense_k((void *)phi_in, n, op, p->d_mats, 1, s->stream);
+      for (int j = 0; j < mcc && e == cudaSuccess; ++j) e = K.dense_k(w.lam + (size_t)j * V, n, op, p->d_mats, 1, s->stream);
+      if (sv_status r = after_launch(s, e, "dense_k adjoint")) return r;
+      p->launches += 1 + mcc;
+      continue;
+    }
+    const PassDev &pd = p->adj.passes[st.index];
+    const int nb = p->grid_a(mcc);
+    cudaError_t e = K.tile_adjoint(phi_in, phi_out, w.lam, n, mcc, pd, p->d_adj_ops, p->d_mats, w.partials, nb,
+                                   s->stream);
+    if (sv_status r = after_launch(s, e, "adjoint pass")) return r;
+    ++p->launches;
+    if (pd.n_train > 0) {
+      e = reduce_partials(w.partials, nb, mcc, pd.n_train, w.contrib, ldc, pd.train_base, j0, s->stream);
+      if (sv_status r = after_launch(s, e, "adjoint reduce")) return r;
+      ++p->launches;
+    }
+    advance();
+  }
+  return SV_OK;
+}
+
+bool needs_sweep(const sv_program *p) { return p->adj.n_train > 0 || !p->adj.dk_ops.empty(); }
+
+sv_status run_jacobian(sv_program *p, const JacWs &w) {
+  sv_state *s = p->s;
+  if (sv_status r = run_expval(p, s->psi, w)) return r;
+  if (needs_sweep(p)) {
+    const int npass_e = (int)p->tp.passes.size();
+    for (int c = 0; c < p->n_chunks; ++c) {
+      const int j0 = c * p->mc, mcc = std::min(p->m, j0 + p->mc) - j0;
+      auto begin = [&](int q) { return (const int32_t *)p->d_lam_begin + p->lam_begin_off[c * npass_e + q]; };
+      if (sv_status r = run_sweep(p, w, mcc, j0, p->m, p->d_lam_terms, begin)) return r;
+    }
+  }
+  cudaError_t e;
+  if (p->adj.n_train > 0 && p->n_params > 0) {
+    e = assemble_jacobian(w.contrib, p->d_coef, p->d_pbegin, p->d_pslots, p->n_params, p->m, 0, p->n_params, w.J,
+                          s->stream);
+    ++p->launches;
+  } else {
+    e = cudaMemsetAsync(w.J, 0, (size_t)std::max(1, p->m) * std::max(1, p->n_params) * 8, s->stream);
+  }
+  return after_launch(s, e, "assemble jacobian");
+}
+
+// VJP: lambda = sum_j g_j H_j psi, one sweep, one contrib column.
+sv_status run_vjp(sv_program *p, const JacWs &w, const double *g) {
+  sv_state *s = p->s;
+  std::vector<TermDev> &vt = p->vjp_host;
+  for (size_t q = 0; q < vt.size(); ++q) vt[q].coeff = p->terms[p->tp.placed[q]].coeff * g[p->terms[p->tp.placed[q]].obs];
+  cudaError_t e = cudaMemcpyAsync(p->d_vjp_terms, vt.data(), vt.size() * sizeof(TermDev), cudaMemcpyHostToDevice,
+                                  s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "uploading vjp coefficients");
+  if (needs_sweep(p)) {
+    auto begin = [&](int q) { return (const int32_t *)p->d_vjp_begin + 2 * q; };
+    if (sv_status r = run_sweep(p, w, 1, 0, 1, p->d_vjp_terms, begin)) return r;
+  }
+  if (p->adj.n_train > 0 && p->n_params > 0) {
+    e = assemble_jacobian(w.contrib, p->d_coef, p->d_pbegin, p->d_pslots, p->n_params, 1, 0, p->n_params, w.J,
+                          s->stream);
+    ++p->launches;
+  } else {
+    e = cudaMemsetAsync(w.J, 0, (size_t)std::max(1, p->n_params) * 8, s->stream);
+  }
+  return after_launch(s, e, "assemble vjp");
+}
+
+sv_status copy_out(sv_state *s, double *dst, const double *src, size_t count, bool on_device) {
+  if (!dst || count == 0) return SV_OK;
+  cudaError_t e = cudaMemcpyAsync(dst, src, count * 8, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                  s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "copying results");
+  return SV_OK;
+}
+
+sv_status sync_state(sv_state *s) {
+  cudaError_t e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) {
+    s->latched = 1;
+    return cuda_fail(e, "stream synchronize");
+  }
+  return SV_OK;
+}
+
+}  // namespace
+
+// ==== C ABI ==========================================================================
+extern "C" {
+
+const char *sv_last_error(void) { return g_err.c_str(); }
+
+const char *sv_version(void) {
+  return "libsv 1.0 (sm_103a; complex64/complex128; fused tile passes, adjoint Jacobian)";
+}
+
+sv_status sv_set_alloc_cap(size_t bytes) {
+  g_alloc_cap = bytes;
+  return SV_OK;
+}
+
+sv_status sv_create(int n, sv_dtype dtype, sv_state **out) {
+  if (!out) return fail(SV_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (n < 1 || n > SV_MAX_QUBITS) return fail(SV_ERR_ARG, "n = %d outside [1, %d]", n, SV_MAX_QUBITS);
+  if (dtype != SV_C64 && dtype != SV_C128) return fail(SV_ERR_ARG, "unknown dtype %d", (int)dtype);
+  sv_state *s = new sv_state();
+  s->n = n;
+  s->dt = dtype;
+  s->bytes = (size_t)ops_for(dtype).amp_bytes << n;
+  if (sv_status st = dev_alloc(&s->psi, s->bytes)) {
+    delete s;
+    return st;
+  }
+  s->owns = true;
+  cudaError_t e = ops_for(dtype).set_basis(s->psi, n, 0, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) {
+    dev_free(s->psi, s->bytes);
+    delete s;
+    return cuda_fail(e, "sv_create");
+  }
+  *out = s;
+  return SV_OK;
+}
+
+sv_status sv_create_from_device_ptr(int n, sv_dtype dtype, void *device_ptr, sv_state **out) {
+  if (!out) return fail(SV_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (n < 1 || n > SV_MAX_QUBITS) return fail(SV_ERR_ARG, "n = %d outside [1, %d]", n, SV_MAX_QUBITS);
+  if (dtype != SV_C64 && dtype != SV_C128) return fail(SV_ERR_ARG, "unknown dtype %d", (int)dtype);
+  if (!device_ptr) return fail(SV_ERR_ARG, "device_ptr is NULL");
+  if (((uintptr_t)device_ptr) & 255) return fail(SV_ERR_ARG, "device_ptr must be 256-byte aligned");
+  sv_state *s = new sv_state();
+  s->n = n;
+  s->dt = dtype;
+  s->bytes = (size_t)ops_for(dtype).amp_bytes << n;
+  s->psi = device_ptr;
+  s->owns = false;
+  *out = s;
+  return SV_OK;
+}
+
+sv_status sv_destroy(sv_state *s) {
+  if (!s) return SV_OK;
+  cudaStreamSynchronize(s->stream);
+  if (s->owns) dev_free(s->psi, s->bytes);
+  dev_free(s->ws, s->ws_bytes);
+  dev_free(s->tab, s->tab_bytes);
+  delete s;
+  return SV_OK;
+}
+
+sv_status sv_set_stream(sv_state *s, void *cuda_stream) {
+  if (!s) return fail(SV_ERR_ARG, "state is NULL");
+  s->stream = (cudaStream_t)cuda_stream;
+  return SV_OK;
+}
+
+sv_status sv_set_workspace(sv_state *s, void *device_ptr, size_t bytes) {
+  if (!s) return fail(SV_ERR_ARG, "state is NULL");
+  if (device_ptr && ((uintptr_t)device_ptr & 255)) return fail(SV_ERR_ARG, "workspace must be 256-byte aligned");
+  s->user_ws = device_ptr;
+  s->user_ws_bytes = device_ptr ? bytes : 0;
+  return SV_OK;
+}
+
+sv_status sv_info(const sv_state *s, int *n, sv_dtype *dtype, void **device_ptr) {
+  if (!s) return fail(SV_ERR_ARG, "state is NULL");
+  if (n) *n = s->n;
+  if (dtype) *dtype = s->dt;
+  if (device_ptr) *device_ptr = s->psi;
+  return SV_OK;
+}
+
+sv_status sv_reset(sv_state *s, uint64_t basis_index) {
+  if (!s) return fail(SV_ERR_ARG, "state is NULL");
+  if (basis_index >> s->n) return fail(SV_ERR_ARG, "basis index %llu >= 2^%d", (unsigned long long)basis_index, s->n);
+  s->latched = 0;
+  return after_launch(s, ops_for(s->dt).set_basis(s->psi, s->n, basis_index, s->stream), "sv_reset");
+}
+
+sv_status sv_set_state(sv_state *s, const void *host_amplitudes) {
+  if (sv_status st = check_state(s)) return st;
+  if (!host_amplitudes) return fail(SV_ERR_ARG, "host buffer is NULL");
+  SV_CUDA(cudaMemcpyAsync(s->psi, host_amplitudes, s->bytes, cudaMemcpyHostToDevice, s->stream));
+  return sync_state(s);
+}
+
+sv_status sv_get_state(sv_state *s, void *host_amplitudes) {
+  if (sv_status st = check_state(s)) return st;
+  if (!host_amplitudes) return fail(SV_ERR_ARG, "host buffer is NULL");
+  SV_CUDA(cudaMemcpyAsync(host_amplitudes, s->psi, s->bytes, cudaMemcpyDeviceToHost, s->stream));
+  return sync_state(s);
+}
+
+sv_status sv_synchronize(sv_state *s) {
+  if (!s) return fail(SV_ERR_ARG, "state is NULL");
+  if (sv_status st = sync_state(s)) return st;
+  return s->latched ? fail(SV_ERR_STATE, "device error latched") : SV_OK;
+}
+
+sv_status sv_apply_op(sv_state *s, const sv_op *op, const double *params, const double *matrices) {
+  if (sv_status st = check_state(s)) return st;
+  if (!op) return fail(SV_ERR_ARG, "op is NULL");
+  int np = 0;
+  for (int a = 0; a < 3; ++a) np = std::max(np, op->param_index[a] + 1);
+  int64_t nm = 0;
+  if (op->kind == SV_MATRIX) nm = op->matrix_offset + ((int64_t)1 << (2 * op->n_targets));
+  sv_tape tape = {1, op, np, matrices, nm};
+  sv_program *p = nullptr;
+  if (sv_status st = build_program(s, &tape, nullptr, 0, params, true, &p)) return st;
+  sv_status st = program_set_params(p, params, 0);
+  if (!st) st = run_steps_forward(p, s->psi);
+  if (!st) st = sync_state(s);
+  destroy_program(p);
+  return st;
+}
+
+sv_status sv_apply(sv_state *s, int kind, const int *wires, int n_wires, const double *angles, int adjoint) {
+  if (sv_status st = check_state(s)) return st;
+  if (kind == SV_MATRIX) return fail(SV_ERR_ARG, "use sv_apply_matrix for SV_MATRIX");
+  if (kind < 0 || kind >= SV_OP_KIND_COUNT) return fail(SV_ERR_ARG, "unknown op kind %d", kind);
+  if (n_wires < 0 || n_wires > SV_MAX_TARGETS || (n_wires > 0 && !wires)) return fail(SV_ERR_ARG, "bad wires");
+  const int np = kind_nparams(kind);
+  if (np > 0 && !angles) return fail(SV_ERR_ARG, "angles is NULL for a parametric gate");
+  sv_op op;
+  memset(&op, 0, sizeof(op));
+  op.kind = kind;
+  op.n_targets = n_wires;
+  for (int j = 0; j < n_wires; ++j) op.targets[j] = wires[j];
+  for (int a = 0; a < 3; ++a) op.param_index[a] = a < np ? a : -1;
+  op.scale = 1.0;
+  op.adjoint = adjoint;
+  return sv_apply_op(s, &op, angles, nullptr);
+}
+
+sv_status sv_apply_matrix(sv_state *s, const int *wires, int k, const double *matrix, int adjoint) {
+  if (sv_status st = check_state(s)) return st;
+  if (k < 1 || k > SV_MAX_TARGETS || !wires || !matrix) return fail(SV_ERR_ARG, "bad sv_apply_matrix arguments");
+  sv_op op;
+  memset(&op, 0, sizeof(op));
+  op.kind = SV_MATRIX;
+  op.n_targets = k;
+  for (int j = 0; j < k; ++j) op.targets[j] = wires[j];
+  op.param_index[0] = op.param_index[1] = op.param_index[2] = -1;
+  op.scale = 1.0;
+  op.adjoint = adjoint;
+  op.matrix_offset = 0;
+  return sv_apply_op(s, &op, nullptr, matrix);
+}
+
+sv_status sv_expval(sv_state *s, const sv_pauli_sum *obs, int n_obs, double *out) {
+  if (sv_status st = check_state(s)) return st;
+  if (n_obs > 0 && !out) return fail(SV_ERR_ARG, "out is NULL");
+  if (n_obs == 0) return SV_OK;
+  sv_program *p = nullptr;
+  if (sv_status st = build_program(s, nullptr, obs, n_obs, nullptr, true, &p)) return st;
+  JacWs w;
+  sv_status st = jac_workspace(p, w);
+  if (!st) st = run_expval(p, s->psi, w);
+  if (!st) st = copy_out(s, out, w.expvals, n_obs, false);
+  if (!st) st = sync_state(s);
+  destroy_program(p);
+  return st;
+}
+
+sv_status sv_norm2(sv_state *s, double *out) {
+  if (!out) return fail(SV_ERR_ARG, "out is NULL");
+  const double c = 1.0;
+  const uint64_t zero = 0;
+  sv_pauli_sum id = {1, &c, &zero, &zero};
+  return sv_expval(s, &id, 1, out);
+}
+
+sv_status sv_forward(sv_state *s, const sv_tape *tape, const double *params) {
+  if (sv_status st = check_state(s)) return st;
+  if (!tape) return fail(SV_ERR_ARG, "tape is NULL");
+  sv_program *p = nullptr;
+  if (sv_status st = build_program(s, tape, nullptr, 0, params, true, &p)) return st;
+  sv_status st = program_set_params(p, params, 0);
+  if (!st) st = run_steps_forward(p, s->psi);
+  if (!st) st = sync_state(s);
+  destroy_program(p);
+  return st;
+}
+
+sv_status sv_adjoint_jacobian(sv_state *s, const sv_tape *tape, const double *params, const sv_pauli_sum *obs,
+                              int n_obs, double *expvals_out, double *jacobian_out) {
+  if (sv_status st = check_state(s)) return st;
+  if (!tape) return fail(SV_ERR_ARG, "tape is NULL");
+  if (n_obs < 1) return fail(SV_ERR_ARG, "need at least one observable");
+  if (tape->n_params > 0 && !jacobian_out) return fail(SV_ERR_ARG, "jacobian_out is NULL");
+  sv_program *p = nullptr;
+  if (sv_status st = build_program(s, tape, obs, n_obs, params, true, &p)) return st;
+  JacWs w;
+  sv_status st = program_set_params(p, params, 0);
+  if (!st) st = jac_workspace(p, w);
+  if (!st) st = run_jacobian(p, w);
+  if (!st) st = copy_out(s, expvals_out, w.expvals, n_obs, false);
+  if (!st) st = copy_out(s, jacobian_out, w.J, (size_t)n_obs * tape->n_params, false);
+  if (!st) st = sync_state(s);
+  destroy_program(p);
+  return st;
+}
+
+sv_status sv_adjoint_vjp(sv_state *s, const sv_tape *tape, const double *params, const sv_pauli_sum *obs, int n_obs,
+                         const double *grad_out, double *vjp_out) {
+  if (sv_status st = check_state(s)) return st;
+  if (!tape || !grad_out || (tape->n_params > 0 && !vjp_out) || n_obs < 1 || !obs)
+    return fail(SV_ERR_ARG, "bad sv_adjoint_vjp arguments");
+  // lambda = sum_j g_j H_j psi: one merged Pauli sum, one backward sweep
+  std::vector<double> c;
+  std::vector<uint64_t> x, z;
+  for (int j = 0; j < n_obs; ++j) {
+    if (!std::isfinite(grad_out[j])) return fail(SV_ERR_ARG, "grad_out[%d] is not finite", j);
+    if (obs[j].n_terms > 0 && (!obs[j].coeffs || !obs[j].x_mask || !obs[j].z_mask))
+      return fail(SV_ERR_ARG, "observable %d: NULL term arrays", j);
+    for (int t = 0; t < obs[j].n_terms; ++t) {
+      c.push_back(grad_out[j] * obs[j].coeffs[t]);
+      x.push_back(obs[j].x_mask[t]);
+      z.push_back(obs[j].z_mask[t]);
+    }
+  }
+  sv_pauli_sum merged = {(int32_t)c.size(), c.data(), x.data(), z.data()};
+  return sv_adjoint_jacobian(s, tape, params, &merged, 1, nullptr, vjp_out);
+}
+
+sv_status sv_program_create(sv_state *s, const sv_tape *tape, const sv_pauli_sum *obs, int n_obs, sv_program **out) {
+  if (!out) return fail(SV_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (sv_status st = check_state(s)) return st;
+  if (!tape) return fail(SV_ERR_ARG, "tape is NULL");
+  return build_program(s, tape, obs, n_obs, nullptr, false, out);
+}
+
+sv_status sv_program_destroy(sv_program *p) {
+  if (!p) return SV_OK;
+  cudaStreamSynchronize(p->s->stream);
+  destroy_program(p);
+  return SV_OK;
+}
+
+sv_status sv_program_set_params(sv_program *p, const double *params, int params_on_device) {
+  if (!p) return fail(SV_ERR_ARG, "program is NULL");
+  if (sv_status st = check_state(p->s)) return st;
+  return program_set_params(p, params, params_on_device);
+}
+
+sv_status sv_program_forward(sv_program *p) {
+  if (!p) return fail(SV_ERR_ARG, "program is NULL");
+  if (sv_status st = check_state(p->s)) return st;
+  p->launches = 0;
+  return run_steps_forward(p, p->s->psi);
+}
+
+sv_status sv_program_jacobian(sv_program *p, double *expvals_out, double *jacobian_out, int outputs_on_device) {
+  if (!p) return fail(SV_ERR_ARG, "program is NULL");
+  if (sv_status st = check_state(p->s)) return st;
+  if (p->m < 1) return fail(SV_ERR_ARG, "program has no observables");
+  JacWs w;
+  p->launches = 0;
+  sv_status st = jac_workspace(p, w);
+  if (!st) st = run_jacobian(p, w);
+  if (!st) st = copy_out(p->s, expvals_out, w.expvals, p->m, outputs_on_device != 0);
+  if (!st) st = copy_out(p->s, jacobian_out, w.J, (size_t)p->m * p->n_params, outputs_on_device != 0);
+  if (!st && !outputs_on_device) st = sync_state(p->s);
+  return st;
+}
+
+sv_status sv_program_expval(sv_program *p, double *expvals_out, int outputs_on_device) {
+  if (!p) return fail(SV_ERR_ARG, "program is NULL");
+  if (sv_status st = check_state(p->s)) return st;
+  if (p->m < 1) return fail(SV_ERR_ARG, "program has no observables");
+  if (!expvals_out) return fail(SV_ERR_ARG, "expvals_out is NULL");
+  JacWs w;
+  p->launches = 0;
+  sv_status st = jac_workspace(p, w);
+  if (!st) st = run_expval(p, p->s->psi, w);
+  if (!st) st = copy_out(p->s, expvals_out, w.expvals, p->m, outputs_on_device != 0);
+  if (!st && !outputs_on_device) st = sync_state(p->s);
+  return st;
+}
+
+sv_status sv_program_vjp(sv_program *p, const double *grad_out, double *vjp_out, int outputs_on_device) {
+  if (!p) return fail(SV_ERR_ARG, "program is NULL");
+  if (sv_status st = check_state(p->s)) return st;
+  if (p->m < 1) return fail(SV_ERR_ARG, "program has no observables");
+  if (!grad_out || (p->n_params > 0 && !vjp_out)) return fail(SV_ERR_ARG, "NULL grad_out / vjp_out");
+  for (int j = 0; j < p->m; ++j)
+    if (!std::isfinite(grad_out[j])) return fail(SV_ERR_ARG, "grad_out[%d] is not finite", j);
+  JacWs w;
+  p->launches = 0;
+  const int saved_mc = p->mc;
+  p->mc = 1;  // one lambda: workspace of psi + phi + lambda
+  sv_status st = jac_workspace(p, w);
+  p->mc = saved_mc;
+  if (!st) st = run_vjp(p, w, grad_out);
+  if (!st) st = copy_out(p->s, vjp_out, w.J, (size_t)p->n_params, outputs_on_device != 0);
+  if (!st && !outputs_on_device) st = sync_state(p->s);
+  return st;
+}
+
+sv_status sv_program_stats(const sv_program *p, int *n_forward_passes, int *n_adjoint_passes, int *launches_last_call) {
+  if (!p) return fail(SV_ERR_ARG, "program is NULL");
+  if (n_forward_passes) *n_forward_passes = (int)p->fwd.steps.size();
+  if (n_adjoint_passes) *n_adjoint_passes = (int)p->adj.steps.size();
+  if (launches_last_call) *launches_last_call = p->launches;
+  return SV_OK;
+}
+
+sv_status sv_plan_query(int n, sv_dtype dtype, const sv_tape *tape, int *n_forward_passes, int *n_adjoint_passes) {
+  if (n < 1 || n > SV_MAX_QUBITS) return fail(SV_ERR_ARG, "n = %d outside [1, %d]", n, SV_MAX_QUBITS);
+  if (dtype != SV_C64 && dtype != SV_C128) return fail(SV_ERR_ARG, "unknown dtype");
+  if (!tape || (tape->n_ops > 0 && !tape->ops)) return fail(SV_ERR_ARG, "bad tape");
+  const Ops &K = ops_for(dtype);
+  std::vector<HOp> fops, aops;
+  for (int i = 0; i < tape->n_ops; ++i) {
+    if (sv_status st = validate_op(n, tape->ops[i], tape->n_params, tape->matrices, tape->n_matrix_entries, nullptr,
+                                   false))
+      return st;
+    HOp h = to_hop(tape->ops[i], tape->matrices);
+    fops.push_back(h);
+    expand_op(h, aops);
+  }
+  Plan f = plan_passes(n, fops, K.Tf, K.nlow_pref, 1 << 30);
+  Plan a = plan_passes(n, aops, K.Ta, K.nlow_pref, kMaxTrainPerPass);
+  if (sv_status st = check_plan(f, n, K.nlow_pref)) return st;
+  if (sv_status st = check_plan(a, n, K.nlow_pref)) return st;
+  if (n_forward_passes) *n_forward_passes = (int)f.steps.size();
+  if (n_adjoint_passes) *n_adjoint_passes = (int)a.steps.size();
+  return SV_OK;
+}
+
+}  // extern "C"

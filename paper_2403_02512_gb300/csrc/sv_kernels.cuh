@@ -1,0 +1,850 @@
+// Device kernels of the state-vector hot path, templated on the real type R
+// (float = complex64 states, double = complex128 states).
+//
+// Layout: a state is 2^n amplitudes of c_t<R> (float2 / double2), interleaved
+// (re, im).  Wire w is global index bit n-1-w (Alg. 1).
+//
+// Tile model (the GPU counterpart of Alg. 1 / Alg. 2's pair enumeration):
+// a pass fixes T "local" index bits pos[0..T).  A tile is the 2^T amplitudes
+// that share all other bits; tiles are disjoint and cover the state, the same
+// disjointness that lets Alg. 1 update pairs concurrently (Sec. 2.1.1).  The
+// lowest nlow local bits are the contiguous low index bits, so a tile is read
+// as 2^(T-nlow) runs of 2^nlow consecutive amplitudes (>= 128 bytes: full
+// 128-bit coalesced accesses).  Every op whose non-diagonal target wires are
+// local bits is applied in shared memory; diagonal ops (RZ, PhaseShift,
+// IsingZZ, CZ, ...) may act on any bits because they only need each
+// amplitude's own global index.  Controls (Alg. 2) may be any bits: a group is
+// updated only when its global index holds the control values.
+#pragma once
+
+#include <cstdint>
+#include <type_traits>
+
+#include "sv_internal.h"
+#include "sv.h"
+
+namespace sv {
+
+template <typename R>
+using c_t = typename std::conditional<std::is_same<R, float>::value, float2, double2>::type;
+
+template <typename C>
+__device__ __forceinline__ C cmul(C a, C b) {
+  C r;
+  r.x = a.x * b.x - a.y * b.y;
+  r.y = a.x * b.y + a.y * b.x;
+  return r;
+}
+
+// acc + a * b
+template <typename C>
+__device__ __forceinline__ C cmac(C acc, C a, C b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(a.y, b.x, acc.y);
+  return acc;
+}
+
+template <typename C>
+__device__ __forceinline__ C cconj(C a) {
+  a.y = -a.y;
+  return a;
+}
+
+__device__ __forceinline__ int insert_zero(int x, int b) {
+  return ((x >> b) << (b + 1)) | (x & ((1 << b) - 1));
+}
+
+// Error-free sum (Knuth TwoSum): s + e == a + b exactly.
+template <typename R>
+__device__ __forceinline__ void two_sum(R a, R b, R &s, R &e) {
+  s = a + b;
+  R bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// Compensated per-thread accumulator: FP32 with a running error term for
+// complex64 states, plain FP64 for complex128 states.  Converted to FP64 for
+// every reduction across threads.
+template <typename R>
+struct Acc {
+  R s = R(0), c = R(0);
+  __device__ __forceinline__ void add(R v) {
+    if constexpr (std::is_same<R, float>::value) {
+      R t, e;
+      two_sum(s, v, t, e);
+      s = t;
+      c += e;
+    } else {
+      s += v;
+    }
+  }
+  __device__ __forceinline__ double value() const { return double(s) + double(c); }
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// Tile geometry
+// ---------------------------------------------------------------------------
+struct TileGeom {
+  int T, nlow, A;
+  uint32_t lowmask;
+  const uint64_t *lut;  // shared: global offset of chunk c (local bits >= nlow)
+  uint64_t base;        // global bits of the current tile
+
+  __device__ __forceinline__ uint64_t gidx(int l) const {
+    return base | lut[l >> nlow] | (uint64_t)(l & lowmask);
+  }
+};
+
+__device__ __forceinline__ void build_lut(uint64_t *lut, const PassDev &p) {
+  const int nch = 1 << (p.T - p.nlow);
+  for (int c = threadIdx.x; c < nch; c += blockDim.x) {
+    uint64_t o = 0;
+    for (int i = p.nlow; i < p.T; ++i)
+      if ((c >> (i - p.nlow)) & 1) o |= 1ull << p.pos[i];
+    lut[c] = o;
+  }
+}
+
+__device__ __forceinline__ uint64_t tile_base(const PassDev &p, uint64_t tile) {
+  uint64_t b = 0;
+  for (int i = 0; i < p.nhi; ++i)
+    if ((tile >> i) & 1) b |= 1ull << p.hi[i];
+  return b;
+}
+
+// 128-bit coalesced tile load / store (c64: two amplitudes per access).
+template <typename R>
+__device__ __forceinline__ void load_tile(const c_t<R> *__restrict__ g, c_t<R> *s, const TileGeom &tg) {
+  if constexpr (std::is_same<R, float>::value) {
+    const int nv = tg.A >> 1;
+    for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+      const int l = v << 1;
+      const float4 x = __ldg(reinterpret_cast<const float4 *>(g + tg.gidx(l)));
+      reinterpret_cast<float4 *>(s)[v] = x;
+    }
+  } else {
+    for (int l = threadIdx.x; l < tg.A; l += blockDim.x) s[l] = __ldg(g + tg.gidx(l));
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ void load_tile_rw(const c_t<R> *g, c_t<R> *s, const TileGeom &tg) {
+  // Same as load_tile without the read-only path (buffer is written by this kernel).
+  if constexpr (std::is_same<R, float>::value) {
+    const int nv = tg.A >> 1;
+    for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+      const int l = v << 1;
+      reinterpret_cast<float4 *>(s)[v] = *reinterpret_cast<const float4 *>(g + tg.gidx(l));
+    }
+  } else {
+    for (int l = threadIdx.x; l < tg.A; l += blockDim.x) s[l] = g[tg.gidx(l)];
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ void store_tile(c_t<R> *g, const c_t<R> *s, const TileGeom &tg) {
+  if constexpr (std::is_same<R, float>::value) {
+    const int nv = tg.A >> 1;
+    for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+      const int l = v << 1;
+      *reinterpret_cast<float4 *>(g + tg.gidx(l)) = reinterpret_cast<const float4 *>(s)[v];
+    }
+  } else {
+    for (int l = threadIdx.x; l < tg.A; l += blockDim.x) g[tg.gidx(l)] = s[l];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Op application inside a tile
+// ---------------------------------------------------------------------------
+template <int K>
+struct GroupIdx {
+  int sorted[K];
+  int offs[1 << K];
+  __device__ __forceinline__ void init(const OpDev &op) {
+#pragma unroll
+    for (int j = 0; j < K; ++j) sorted[j] = op.tl[j];
+    // insertion sort (K <= 4)
+#pragma unroll
+    for (int i = 1; i < K; ++i)
+#pragma unroll
+      for (int j = i; j > 0; --j)
+        if (sorted[j - 1] > sorted[j]) {
+          int t = sorted[j];
+          sorted[j] = sorted[j - 1];
+          sorted[j - 1] = t;
+        }
+#pragma unroll
+    for (int r = 0; r < (1 << K); ++r) {
+      int o = 0;
+#pragma unroll
+      for (int j = 0; j < K; ++j)
+        if ((r >> (K - 1 - j)) & 1) o |= 1 << op.tl[j];
+      offs[r] = o;
+    }
+  }
+  __device__ __forceinline__ int first(int g) const {
+    int l = g;
+#pragma unroll
+    for (int j = 0; j < K; ++j) l = insert_zero(l, sorted[j]);
+    return l;
+  }
+};
+
+// Row r of M v (dagger: of M^dagger v), M row-major 2^K x 2^K.
+template <typename R, int K>
+__device__ __forceinline__ c_t<R> matrow(const c_t<R> (&v)[1 << K], const c_t<R> *__restrict__ M, int r,
+                                         bool dagger) {
+  using C = c_t<R>;
+  constexpr int D = 1 << K;
+  C acc;
+  acc.x = R(0);
+  acc.y = R(0);
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    const C m = dagger ? cconj(M[c * D + r]) : M[r * D + c];
+    acc = cmac(acc, m, v[c]);
+  }
+  return acc;
+}
+
+// Apply M (or M^dagger) to every control-matching group of a tile.  The group's
+// inputs are held in registers; outputs go straight back to shared memory.
+template <typename R, int K>
+__device__ void apply_dense_tile(c_t<R> *s, const TileGeom &tg, const OpDev &op,
+                                 const c_t<R> *__restrict__ mats, bool dagger) {
+  using C = c_t<R>;
+  constexpr int D = 1 << K;
+  GroupIdx<K> gi;
+  gi.init(op);
+  const C *M = mats + op.mat;
+  const int ng = tg.A >> K;
+  for (int g = threadIdx.x; g < ng; g += blockDim.x) {
+    const int l0 = gi.first(g);
+    if (op.cmask && ((tg.gidx(l0) & op.cmask) != op.cval)) continue;
+    C v[D];
+#pragma unroll
+    for (int r = 0; r < D; ++r) v[r] = s[l0 + gi.offs[r]];
+#pragma unroll
+    for (int r = 0; r < D; ++r) s[l0 + gi.offs[r]] = matrow<R, K>(v, M, r, dagger);
+  }
+}
+
+template <typename R, int MAXK>
+__device__ __forceinline__ void apply_dense_any(c_t<R> *s, const TileGeom &tg, const OpDev &op,
+                                                const c_t<R> *mats, bool dagger) {
+  if (op.k == 1) {
+    apply_dense_tile<R, 1>(s, tg, op, mats, dagger);
+  } else if (MAXK <= 2 || op.k == 2) {
+    apply_dense_tile<R, 2>(s, tg, op, mats, dagger);
+  } else if (op.k == 3) {
+    apply_dense_tile<R, (MAXK >= 3 ? 3 : 2)>(s, tg, op, mats, dagger);
+  } else {
+    apply_dense_tile<R, (MAXK >= 4 ? 4 : 2)>(s, tg, op, mats, dagger);
+  }
+}
+
+__device__ __forceinline__ int diag_index(const OpDev &op, uint64_t g) {
+  int idx = 0;
+  for (int j = 0; j < op.k; ++j) idx = (idx << 1) | (int)((g >> op.tg[j]) & 1);
+  return idx;
+}
+
+// A run of consecutive diagonal ops [o0, o1): every amplitude is multiplied by
+// the product of its diagonal entries, in op order.
+template <typename R>
+__device__ void apply_diag_run(c_t<R> *s, const TileGeom &tg, const OpDev *__restrict__ ops, int o0,
+                               int o1, const c_t<R> *__restrict__ mats, bool dagger) {
+  using C = c_t<R>;
+  for (int l = threadIdx.x; l < tg.A; l += blockDim.x) {
+    const uint64_t g = tg.gidx(l);
+    C a = s[l];
+    if (!dagger) {
+      for (int o = o0; o < o1; ++o) {
+        const OpDev &op = ops[o];
+        if ((g & op.cmask) != op.cval) continue;
+        a = cmul(a, mats[op.mat + diag_index(op, g)]);
+      }
+    } else {
+      for (int o = o1 - 1; o >= o0; --o) {
+        const OpDev &op = ops[o];
+        if ((g & op.cmask) != op.cval) continue;
+        a = cmul(a, cconj(mats[op.mat + diag_index(op, g)]));
+      }
+    }
+    s[l] = a;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Forward pass kernel (S1-S4): load tile, apply the pass's ops, store tile.
+// ---------------------------------------------------------------------------
+template <typename R, int MAXK>
+__global__ void __launch_bounds__(kBlock) k_tile_forward(c_t<R> *__restrict__ psi, int n, const PassDev pass,
+                                                          const OpDev *__restrict__ ops,
+                                                          const c_t<R> *__restrict__ mats) {
+  using C = c_t<R>;
+  extern __shared__ __align__(16) unsigned char smem[];
+  C *s = reinterpret_cast<C *>(smem);
+  uint64_t *lut = reinterpret_cast<uint64_t *>(smem + (sizeof(C) << pass.T));
+  build_lut(lut, pass);
+  TileGeom tg;
+  tg.T = pass.T;
+  tg.nlow = pass.nlow;
+  tg.A = 1 << pass.T;
+  tg.lowmask = (1u << pass.nlow) - 1u;
+  tg.lut = lut;
+  __syncthreads();
+  const uint64_t ntiles = 1ull << (n - pass.T);
+  for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    tg.base = tile_base(pass, tile);
+    load_tile_rw<R>(psi, s, tg);
+    __syncthreads();
+    int o = pass.op_begin;
+    while (o < pass.op_end) {
+      if (ops[o].cls == kDiag) {
+        int e = o + 1;
+        while (e < pass.op_end && ops[e].cls == kDiag) ++e;
+        apply_diag_run<R>(s, tg, ops, o, e, mats, false);
+        o = e;
+      } else {
+        apply_dense_any<R, MAXK>(s, tg, ops[o], mats, false);
+        ++o;
+      }
+      __syncthreads();
+    }
+    store_tile<R>(psi, s, tg);
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint pass kernel (S7): for ops of the pass in reverse order,
+//   partial[op] += Im <lambda | G phi>   (before un-applying the op),
+//   phi <- U^dagger phi,  lambda <- U^dagger lambda.
+// blockIdx.x = lambda index j (fastest, so the CTAs that share a phi tile run
+// together and re-read it from L2), blockIdx.y = tile group.  phi_in is read,
+// phi_out written by the j == 0 CTAs only: with several lambdas they are
+// distinct (ping-pong) buffers; with one lambda each phi tile is read and
+// written by the same CTA, so phi_out may equal phi_in (three vectors in all).
+// Partial layout: partials[(b * m + j) * n_train + t].
+// ---------------------------------------------------------------------------
+template <typename R, int K>
+__device__ void adjoint_dense_tile(c_t<R> *sp, c_t<R> *sl, const TileGeom &tg, const OpDev &op,
+                                   const c_t<R> *__restrict__ mats, double &accum) {
+  using C = c_t<R>;
+  constexpr int D = 1 << K;
+  GroupIdx<K> gi;
+  gi.init(op);
+  const C *M = mats + op.mat;
+  const bool train = op.train >= 0;
+  const C *G = mats + (train ? op.gen : op.mat);
+  Acc<R> acc;
+  const int ng = tg.A >> K;
+  for (int g = threadIdx.x; g < ng; g += blockDim.x) {
+    const int l0 = gi.first(g);
+    if (op.cmask && ((tg.gidx(l0) & op.cmask) != op.cval)) continue;
+    C v[D];
+#pragma unroll
+    for (int r = 0; r < D; ++r) v[r] = sp[l0 + gi.offs[r]];
+    if (train) {
+      // Im sum_r conj(lambda_r) (G phi)_r, before the op is un-applied
+#pragma unroll
+      for (int r = 0; r < D; ++r) {
+        const C gp = matrow<R, K>(v, G, r, false);
+        const C q = sl[l0 + gi.offs[r]];
+        acc.add(q.x * gp.y - q.y * gp.x);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < D; ++r) sp[l0 + gi.offs[r]] = matrow<R, K>(v, M, r, true);
+#pragma unroll
+    for (int r = 0; r < D; ++r) v[r] = sl[l0 + gi.offs[r]];
+#pragma unroll
+    for (int r = 0; r < D; ++r) sl[l0 + gi.offs[r]] = matrow<R, K>(v, M, r, true);
+  }
+  accum = acc.value();
+}
+
+template <typename R>
+__device__ void adjoint_diag_tile(c_t<R> *sp, c_t<R> *sl, const TileGeom &tg, const OpDev &op,
+                                  const c_t<R> *__restrict__ mats, double &accum) {
+  using C = c_t<R>;
+  const bool train = op.train >= 0;
+  Acc<R> acc;
+  for (int l = threadIdx.x; l < tg.A; l += blockDim.x) {
+    const uint64_t g = tg.gidx(l);
+    if ((g & op.cmask) != op.cval) continue;
+    const int idx = diag_index(op, g);
+    C p = sp[l], q = sl[l];
+    if (train) {
+      const R gd = mats[op.gen + idx].x;  // generator diagonal is real
+      acc.add(gd * (q.x * p.y - q.y * p.x));
+    }
+    const C d = cconj(mats[op.mat + idx]);
+    sp[l] = cmul(p, d);
+    sl[l] = cmul(q, d);
+  }
+  accum = acc.value();
+}
+
+template <typename R, int MAXK>
+__global__ void __launch_bounds__(kBlock) k_tile_adjoint(const c_t<R> *phi_in, c_t<R> *phi_out,
+                                                          c_t<R> *__restrict__ lam_base, int n,
+                                                          const PassDev pass, const OpDev *__restrict__ ops,
+                                                          const c_t<R> *__restrict__ mats,
+                                                          double *__restrict__ partials) {
+  using C = c_t<R>;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int A = 1 << pass.T;
+  C *sp = reinterpret_cast<C *>(smem);
+  C *sl = sp + A;
+  uint64_t *lut = reinterpret_cast<uint64_t *>(sl + A);
+  const int nch = 1 << (pass.T - pass.nlow);
+  double *accs = reinterpret_cast<double *>(lut + nch);  // [n_train][nwarps]
+  const int nwarps = blockDim.x >> 5;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int j = blockIdx.x;
+  const int m = gridDim.x;
+  C *lam = lam_base + ((size_t)j << n);
+
+  build_lut(lut, pass);
+  for (int i = threadIdx.x; i < pass.n_train * nwarps; i += blockDim.x) accs[i] = 0.0;
+  TileGeom tg;
+  tg.T = pass.T;
+  tg.nlow = pass.nlow;
+  tg.A = A;
+  tg.lowmask = (1u << pass.nlow) - 1u;
+  tg.lut = lut;
+  __syncthreads();
+
+  const uint64_t ntiles = 1ull << (n - pass.T);
+  for (uint64_t tile = blockIdx.y; tile < ntiles; tile += gridDim.y) {
+    tg.base = tile_base(pass, tile);
+    load_tile_rw<R>(phi_in, sp, tg);  // phi_in may equal phi_out (single lambda, in place)
+    load_tile_rw<R>(lam, sl, tg);
+    __syncthreads();
+    for (int o = pass.op_end - 1; o >= pass.op_begin; --o) {
+      const OpDev &op = ops[o];
+      double part = 0.0;
+      if (op.cls == kDiag) {
+        adjoint_diag_tile<R>(sp, sl, tg, op, mats, part);
+      } else {
+        if (op.k == 1)
+          adjoint_dense_tile<R, 1>(sp, sl, tg, op, mats, part);
+        else if (MAXK <= 2 || op.k == 2)
+          adjoint_dense_tile<R, 2>(sp, sl, tg, op, mats, part);
+        else if (op.k == 3)
+          adjoint_dense_tile<R, (MAXK >= 3 ? 3 : 2)>(sp, sl, tg, op, mats, part);
+        else
+          adjoint_dense_tile<R, (MAXK >= 4 ? 4 : 2)>(sp, sl, tg, op, mats, part);
+      }
+      if (op.train >= 0) {
+        part = warp_sum(part);
+        if (lane == 0) accs[op.train * nwarps + warp] += part;
+      }
+      __syncthreads();
+    }
+    store_tile<R>(lam, sl, tg);
+    if (j == 0) store_tile<R>(phi_out, sp, tg);
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < pass.n_train; t += blockDim.x) {
+    double v = 0.0;
+    for (int w = 0; w < nwarps; ++w) v += accs[t * nwarps + w];
+    partials[((size_t)blockIdx.y * m + j) * pass.n_train + t] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Expectation values (S5): for every term t placed in this pass,
+//   <P_t> partial = sum_l Re( i^{ny} (-1)^{popcount((g ^ x) & z)} conj(psi_g) psi_{g ^ x} )
+// over the tile (P|i> = i^{ny} (-1)^{popcount(i & z)} |i ^ x>).  x lies inside
+// the local bits, so both amplitudes are in the tile.  Term coefficients are
+// applied later (combine_terms).  partials[b * n_terms + t].
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ R pauli_re(c_t<R> a, c_t<R> b, int ny) {
+  // Re(i^ny * conj(a) * b)
+  const R re = a.x * b.x + a.y * b.y;
+  const R im = a.x * b.y - a.y * b.x;
+  switch (ny & 3) {
+    case 0: return re;
+    case 1: return -im;
+    case 2: return -re;
+    default: return im;
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kBlock) k_expval(const c_t<R> *__restrict__ psi, int n, const PassDev pass,
+                                                    const TermDev *__restrict__ terms, int n_terms,
+                                                    double *__restrict__ partials) {
+  using C = c_t<R>;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int A = 1 << pass.T;
+  C *s = reinterpret_cast<C *>(smem);
+  uint64_t *lut = reinterpret_cast<uint64_t *>(s + A);
+  const int nch = 1 << (pass.T - pass.nlow);
+  double *accs = reinterpret_cast<double *>(lut + nch);  // [n_terms][nwarps]
+  const int nwarps = blockDim.x >> 5;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  build_lut(lut, pass);
+  for (int i = threadIdx.x; i < n_terms * nwarps; i += blockDim.x) accs[i] = 0.0;
+  TileGeom tg;
+  tg.T = pass.T;
+  tg.nlow = pass.nlow;
+  tg.A = A;
+  tg.lowmask = (1u << pass.nlow) - 1u;
+  tg.lut = lut;
+  __syncthreads();
+  const uint64_t ntiles = 1ull << (n - pass.T);
+  for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    tg.base = tile_base(pass, tile);
+    load_tile<R>(psi, s, tg);
+    __syncthreads();
+    for (int t = 0; t < n_terms; ++t) {
+      const TermDev tm = terms[t];
+      Acc<R> acc;
+      for (int l = threadIdx.x; l < A; l += blockDim.x) {
+        const uint64_t g = tg.gidx(l);
+        const int par = __popcll((g ^ tm.xg) & tm.zg) & 1;
+        R v = pauli_re<R>(s[l], s[l ^ tm.xl], tm.ny);
+        acc.add(par ? -v : v);
+      }
+      const double part = warp_sum(acc.value());
+      if (lane == 0) accs[t * nwarps + warp] += part;
+    }
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < n_terms; t += blockDim.x) {
+    double v = 0.0;
+    for (int w = 0; w < nwarps; ++w) v += accs[t * nwarps + w];
+    partials[(size_t)blockIdx.x * n_terms + t] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Lambda initialisation (S6): lam_o += sum_{t in o} c_t P_t phi over the terms of
+// this pass (output-stationary: each lambda amplitude written once per pass).
+//   (P phi)_g = i^{ny} (-1)^{popcount((g ^ x) & z)} phi_{g ^ x}
+// blockIdx.y = observable within the chunk; first != 0 overwrites lam.
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(kBlock) k_lambda(const c_t<R> *__restrict__ phi, c_t<R> *__restrict__ lam_base,
+                                                    int n, const PassDev pass, const TermDev *__restrict__ terms,
+                                                    const int32_t *__restrict__ obs_term_begin, int first) {
+  using C = c_t<R>;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int A = 1 << pass.T;
+  C *s = reinterpret_cast<C *>(smem);
+  uint64_t *lut = reinterpret_cast<uint64_t *>(s + A);
+  const int o = blockIdx.y;
+  const int t0 = obs_term_begin[o], t1 = obs_term_begin[o + 1];
+  C *lam = lam_base + ((size_t)o << n);
+  build_lut(lut, pass);
+  TileGeom tg;
+  tg.T = pass.T;
+  tg.nlow = pass.nlow;
+  tg.A = A;
+  tg.lowmask = (1u << pass.nlow) - 1u;
+  tg.lut = lut;
+  __syncthreads();
+  const uint64_t ntiles = 1ull << (n - pass.T);
+  for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    tg.base = tile_base(pass, tile);
+    load_tile<R>(phi, s, tg);
+    __syncthreads();
+    for (int l = threadIdx.x; l < A; l += blockDim.x) {
+      const uint64_t g = tg.gidx(l);
+      C acc;
+      if (first) {
+        acc.x = R(0);
+        acc.y = R(0);
+      } else {
+        acc = lam[g];
+      }
+      for (int t = t0; t < t1; ++t) {
+        const TermDev tm = terms[t];
+        const C b = s[l ^ tm.xl];
+        const int par = __popcll((g ^ tm.xg) & tm.zg) & 1;
+        const R c = par ? R(-tm.coeff) : R(tm.coeff);
+        // i^ny * c * b
+        switch (tm.ny & 3) {
+          case 0: acc.x = fma(c, b.x, acc.x); acc.y = fma(c, b.y, acc.y); break;
+          case 1: acc.x = fma(-c, b.y, acc.x); acc.y = fma(c, b.x, acc.y); break;
+          case 2: acc.x = fma(-c, b.x, acc.x); acc.y = fma(-c, b.y, acc.y); break;
+          default: acc.x = fma(c, b.y, acc.x); acc.y = fma(-c, b.x, acc.y); break;
+        }
+      }
+      lam[g] = acc;
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Dense k-qubit block applied straight from global memory (k = 5, 6), one
+// output amplitude per thread: CTA stages 256 / 2^k groups in shared memory.
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(kBlock) k_dense_k(c_t<R> *__restrict__ psi, int n, const OpDev op,
+                                                     const c_t<R> *__restrict__ M, int dagger) {
+  using C = c_t<R>;
+  __shared__ C sv[kBlock];
+  const int K = op.k, D = 1 << K;
+  const int gpb = kBlock / D;  // groups per CTA
+  int sorted[kMaxTargets];
+  for (int j = 0; j < K; ++j) sorted[j] = op.tg[j];
+  for (int i = 1; i < K; ++i)
+    for (int j = i; j > 0 && sorted[j - 1] > sorted[j]; --j) {
+      int t = sorted[j];
+      sorted[j] = sorted[j - 1];
+      sorted[j - 1] = t;
+    }
+  const uint64_t ngroups = 1ull << (n - K);
+  const int r = threadIdx.x % D, gl = threadIdx.x / D;
+  uint64_t roff = 0;
+  for (int j = 0; j < K; ++j)
+    if ((r >> (K - 1 - j)) & 1) roff |= 1ull << op.tg[j];
+  for (uint64_t g0 = (uint64_t)blockIdx.x * gpb; g0 < ngroups; g0 += (uint64_t)gridDim.x * gpb) {
+    const uint64_t g = g0 + gl;
+    uint64_t i0 = g;
+    for (int j = 0; j < K; ++j) {
+      const int b = sorted[j];
+      i0 = ((i0 >> b) << (b + 1)) | (i0 & ((1ull << b) - 1));
+    }
+    const bool active = (g < ngroups) && ((i0 & op.cmask) == op.cval);
+    if (active) sv[threadIdx.x] = psi[i0 | roff];
+    __syncthreads();
+    if (active) {
+      C acc;
+      acc.x = R(0);
+      acc.y = R(0);
+      for (int c = 0; c < D; ++c) {
+        C m = dagger ? cconj(M[c * D + r]) : M[r * D + c];
+        acc = cmac(acc, m, sv[gl * D + c]);
+      }
+      psi[i0 | roff] = acc;
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Gate matrices from parameters (one thread per slot, FP64 trigonometry).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double2 dc(double re, double im) { return make_double2(re, im); }
+
+// Writes the 2^k x 2^k matrix of a base gate (not SV_MATRIX) into m (row-major).
+__device__ inline void gate_matrix(int kind, const double *a, double2 *m) {
+  double c = 0.0, s = 0.0;
+  if (kind == SV_RX || kind == SV_RY || kind == SV_ISING_XX || kind == SV_ISING_YY ||
+      kind == SV_ISING_XY || kind == SV_SINGLE_EXCITATION || kind == SV_DOUBLE_EXCITATION)
+    sincos(0.5 * a[0], &s, &c);
+  const double r2 = 0.70710678118654752440;
+  switch (kind) {
+    case SV_IDENTITY: m[0] = dc(1, 0); m[1] = dc(0, 0); m[2] = dc(0, 0); m[3] = dc(1, 0); break;
+    case SV_PAULI_X: m[0] = dc(0, 0); m[1] = dc(1, 0); m[2] = dc(1, 0); m[3] = dc(0, 0); break;
+    case SV_PAULI_Y: m[0] = dc(0, 0); m[1] = dc(0, -1); m[2] = dc(0, 1); m[3] = dc(0, 0); break;
+    case SV_PAULI_Z: m[0] = dc(1, 0); m[1] = dc(0, 0); m[2] = dc(0, 0); m[3] = dc(-1, 0); break;
+    case SV_HADAMARD: m[0] = dc(r2, 0); m[1] = dc(r2, 0); m[2] = dc(r2, 0); m[3] = dc(-r2, 0); break;
+    case SV_S: m[0] = dc(1, 0); m[1] = dc(0, 0); m[2] = dc(0, 0); m[3] = dc(0, 1); break;
+    case SV_T: m[0] = dc(1, 0); m[1] = dc(0, 0); m[2] = dc(0, 0); m[3] = dc(r2, r2); break;
+    case SV_PHASE_SHIFT: {
+      double ps, pc;
+      sincos(a[0], &ps, &pc);
+      m[0] = dc(1, 0); m[1] = dc(0, 0); m[2] = dc(0, 0); m[3] = dc(pc, ps);
+      break;
+    }
+    case SV_RX: m[0] = dc(c, 0); m[1] = dc(0, -s); m[2] = dc(0, -s); m[3] = dc(c, 0); break;
+    case SV_RY: m[0] = dc(c, 0); m[1] = dc(-s, 0); m[2] = dc(s, 0); m[3] = dc(c, 0); break;
+    case SV_RZ: {
+      double zs, zc;
+      sincos(0.5 * a[0], &zs, &zc);
+      m[0] = dc(zc, -zs); m[1] = dc(0, 0); m[2] = dc(0, 0); m[3] = dc(zc, zs);
+      break;
+    }
+    case SV_ROT: {
+      // RZ(w) RY(t) RZ(p): [[e^{-i(p+w)/2} c, -e^{i(p-w)/2} s], [e^{-i(p-w)/2} s, e^{i(p+w)/2} c]]
+      double tc, ts, ac, as, bc, bs;
+      sincos(0.5 * a[1], &ts, &tc);
+      sincos(0.5 * (a[0] + a[2]), &as, &ac);
+      sincos(0.5 * (a[0] - a[2]), &bs, &bc);
+      m[0] = dc(ac * tc, -as * tc);
+      m[1] = dc(-bc * ts, -bs * ts);
+      m[2] = dc(bc * ts, -bs * ts);
+      m[3] = dc(ac * tc, as * tc);
+      break;
+    }
+    case SV_SWAP:
+      for (int i = 0; i < 16; ++i) m[i] = dc(0, 0);
+      m[0] = m[6] = m[9] = m[15] = dc(1, 0);
+      break;
+    case SV_ISING_XX:
+      for (int i = 0; i < 16; ++i) m[i] = dc(0, 0);
+      for (int i = 0; i < 4; ++i) {
+        m[i * 4 + i] = dc(c, 0);
+        m[i * 4 + (3 - i)] = dc(0, -s);
+      }
+      break;
+    case SV_ISING_YY:
+      for (int i = 0; i < 16; ++i) m[i] = dc(0, 0);
+      for (int i = 0; i < 4; ++i) m[i * 4 + i] = dc(c, 0);
+      m[3] = m[12] = dc(0, s);
+      m[6] = m[9] = dc(0, -s);
+      break;
+    case SV_ISING_ZZ: {
+      double zs, zc;
+      sincos(0.5 * a[0], &zs, &zc);
+      for (int i = 0; i < 16; ++i) m[i] = dc(0, 0);
+      m[0] = m[15] = dc(zc, -zs);
+      m[5] = m[10] = dc(zc, zs);
+      break;
+    }
+    case SV_ISING_XY:
+      for (int i = 0; i < 16; ++i) m[i] = dc(0, 0);
+      m[0] = m[15] = dc(1, 0);
+      m[5] = m[10] = dc(c, 0);
+      m[6] = m[9] = dc(0, s);
+      break;
+    case SV_SINGLE_EXCITATION:
+      for (int i = 0; i < 16; ++i) m[i] = dc(0, 0);
+      m[0] = m[15] = dc(1, 0);
+      m[5] = m[10] = dc(c, 0);
+      m[6] = dc(-s, 0);
+      m[9] = dc(s, 0);
+      break;
+    case SV_DOUBLE_EXCITATION:
+      for (int i = 0; i < 256; ++i) m[i] = dc(0, 0);
+      for (int i = 0; i < 16; ++i) m[i * 16 + i] = dc(1, 0);
+      m[3 * 16 + 3] = m[12 * 16 + 12] = dc(c, 0);
+      m[3 * 16 + 12] = dc(-s, 0);
+      m[12 * 16 + 3] = dc(s, 0);
+      break;
+    default: break;
+  }
+}
+
+// Generator G with U(t) = exp(i s t G); the factor s is applied on the host.
+__device__ inline void gate_generator(int kind, double2 *m) {
+  switch (kind) {
+    case SV_RX: m[0] = dc(0, 0); m[1] = dc(1, 0); m[2] = dc(1, 0); m[3] = dc(0, 0); break;
+    case SV_RY: m[0] = dc(0, 0); m[1] = dc(0, -1); m[2] = dc(0, 1); m[3] = dc(0, 0); break;
+    case SV_RZ: m[0] = dc(1, 0); m[1] = dc(0, 0); m[2] = dc(0, 0); m[3] = dc(-1, 0); break;
+    case SV_PHASE_SHIFT: m[0] = dc(0, 0); m[1] = dc(0, 0); m[2] = dc(0, 0); m[3] = dc(1, 0); break;
+    case SV_ISING_XX:
+      for (int i = 0; i < 16; ++i) m[i] = dc(0, 0);
+      for (int i = 0; i < 4; ++i) m[i * 4 + (3 - i)] = dc(1, 0);
+      break;
+    case SV_ISING_YY:
+      for (int i = 0; i < 16; ++i) m[i] = dc(0, 0);
+      m[3] = m[12] = dc(-1, 0);
+      m[6] = m[9] = dc(1, 0);
+      break;
+    case SV_ISING_ZZ:
+      for (int i = 0; i < 16; ++i) m[i] = dc(0, 0);
+      m[0] = m[15] = dc(1, 0);
+      m[5] = m[10] = dc(-1, 0);
+      break;
+    case SV_ISING_XY:
+      for (int i = 0; i < 16; ++i) m[i] = dc(0, 0);
+      m[6] = m[9] = dc(2, 0);
+      break;
+    case SV_SINGLE_EXCITATION:
+      for (int i = 0; i < 16; ++i) m[i] = dc(0, 0);
+      m[6] = dc(0, -1);
+      m[9] = dc(0, 1);
+      break;
+    case SV_DOUBLE_EXCITATION:
+      for (int i = 0; i < 256; ++i) m[i] = dc(0, 0);
+      m[3 * 16 + 12] = dc(0, -1);
+      m[12 * 16 + 3] = dc(0, 1);
+      break;
+    default: break;
+  }
+}
+
+template <typename R>
+__global__ void k_build_matrices(const MatSlot *__restrict__ slots, int n_slots,
+                                 const double *__restrict__ params, const double *__restrict__ user,
+                                 c_t<R> *__restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_slots) return;
+  const MatSlot sl = slots[i];
+  const int D = 1 << sl.k;
+  c_t<R> *o = out + sl.out;
+  if (sl.kind == SV_MATRIX) {
+    for (int r = 0; r < D; ++r)
+      for (int c = 0; c < D; ++c) {
+        if (sl.diag && r != c) continue;
+        const int64_t e = sl.adjoint ? (int64_t)c * D + r : (int64_t)r * D + c;
+        double re = user[2 * (sl.src + e)], im = user[2 * (sl.src + e) + 1];
+        if (sl.adjoint) im = -im;
+        c_t<R> v;
+        v.x = (R)re;
+        v.y = (R)im;
+        o[sl.diag ? r : r * D + c] = v;
+      }
+    return;
+  }
+  double a[3];
+  for (int q = 0; q < 3; ++q) a[q] = sl.pidx[q] >= 0 ? sl.scale * params[sl.pidx[q]] : sl.cangle[q];
+  double2 m[256];
+  if (sl.what == 0)
+    gate_matrix(sl.kind, a, m);
+  else
+    gate_generator(sl.kind, m);
+  for (int r = 0; r < D; ++r)
+    for (int c = 0; c < D; ++c) {
+      if (sl.diag && r != c) continue;
+      double2 v = (sl.adjoint && sl.what == 0) ? make_double2(m[c * D + r].x, -m[c * D + r].y) : m[r * D + c];
+      c_t<R> w;
+      w.x = (R)v.x;
+      w.y = (R)v.y;
+      o[sl.diag ? r : r * D + c] = w;
+    }
+}
+
+template <typename R>
+__global__ void k_set_basis(c_t<R> *psi, uint64_t N, uint64_t index) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < N; i += (uint64_t)gridDim.x * blockDim.x) {
+    c_t<R> v;
+    v.x = (i == index) ? R(1) : R(0);
+    v.y = R(0);
+    psi[i] = v;
+  }
+}
+
+template <typename R>
+__global__ void k_copy(c_t<R> *__restrict__ dst, const c_t<R> *__restrict__ src, uint64_t N) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < N; i += (uint64_t)gridDim.x * blockDim.x)
+    dst[i] = src[i];
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+inline int lut_bytes(int T, int nlow_min) { return 8 << (T - nlow_min); }
+
+template <typename R>
+struct LaunchImpl {
+  using C = c_t<R>;
+  static constexpr int kNlowMin = std::is_same<R, float>::value ? 4 : 3;
+
+  static int forward_smem(int T) { return (int)(sizeof(C) << T) + lut_bytes(T, 0); }
+  static int adjoint_smem(int T) { return (int)(2 * (sizeof(C) << T)) + lut_bytes(T, 0) + 64 * 8 * 8; }
+  static int expval_smem(int T, int n_terms) {
+    return (int)(sizeof(C) << T) + lut_bytes(T, 0) + n_terms * 8 * 8;
+  }
+};
+
+}  // namespace sv

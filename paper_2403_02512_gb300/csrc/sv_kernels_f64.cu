@@ -1,0 +1,86 @@
+// complex128 instantiation of the state-vector kernels, plus the
+// precision-independent deterministic reductions (S8).
+#include "sv_launch.cuh"
+
+namespace sv {
+template struct Launch<double>;
+
+// Fixed-order sum over b of partials[b * (m * n_rows) + j * n_rows + t] into
+// out[(row0 + t) * ldo + col0 + j]: one thread per (j, t), b ascending.  The
+// same inputs always give bitwise-equal outputs.
+__global__ void k_reduce_partials(const double *__restrict__ partials, int nb, int m, int n_rows,
+                                  double *__restrict__ out, int ldo, int row0, int col0) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= m * n_rows) return;
+  const int j = r / n_rows, t = r % n_rows;
+  const size_t stride = (size_t)m * n_rows;
+  double s = 0.0;
+  for (int b = 0; b < nb; ++b) s += partials[(size_t)b * stride + r];
+  out[(size_t)(row0 + t) * ldo + col0 + j] = s;
+}
+
+cudaError_t reduce_rows(const double *partials, int nb, int rows, int stride, double *out,
+                        cudaStream_t st) {
+  (void)stride;
+  if (rows <= 0) return cudaSuccess;
+  k_reduce_partials<<<(rows + 127) / 128, 128, 0, st>>>(partials, nb, 1, rows, out, 1, 0, 0);
+  return cudaGetLastError();
+}
+
+cudaError_t reduce_partials(const double *partials, int nb, int m, int n_rows, double *out, int ldo,
+                            int row0, int col0, cudaStream_t st) {
+  const int total = m * n_rows;
+  if (total <= 0) return cudaSuccess;
+  k_reduce_partials<<<(total + 127) / 128, 128, 0, st>>>(partials, nb, m, n_rows, out, ldo, row0, col0);
+  return cudaGetLastError();
+}
+
+// expvals[o] = sum_{i in [obs_begin[o], obs_begin[o+1])} coeff(term_order[i]) * sums[term_order[i]]
+__global__ void k_combine_terms(const double *__restrict__ sums, const TermDev *__restrict__ terms,
+                                const int32_t *__restrict__ obs_begin, int n_obs,
+                                const int32_t *__restrict__ order, double *__restrict__ out) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= n_obs) return;
+  double e = 0.0;
+  for (int i = obs_begin[o]; i < obs_begin[o + 1]; ++i) {
+    const int t = order[i];
+    e += terms[t].coeff * sums[t];
+  }
+  out[o] = e;
+}
+
+cudaError_t combine_terms(const double *term_sums, const TermDev *terms, const int32_t *obs_begin,
+                          int n_obs, const int32_t *term_order, double *expvals, cudaStream_t st) {
+  if (n_obs <= 0) return cudaSuccess;
+  k_combine_terms<<<(n_obs + 127) / 128, 128, 0, st>>>(term_sums, terms, obs_begin, n_obs, term_order,
+                                                        expvals);
+  return cudaGetLastError();
+}
+
+// J[(row0 + j) * ldj + p] = sum over slots s of parameter p (CSR, sweep order) of
+// coef[s] * contrib[s * m + j].
+__global__ void k_assemble_jacobian(const double *__restrict__ contrib, const double *__restrict__ coef,
+                                    const int32_t *__restrict__ p_begin, const int32_t *__restrict__ p_slots,
+                                    int n_params, int m, int row0, int ldj, double *__restrict__ J) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_params * m) return;
+  const int j = i / n_params, p = i % n_params;
+  double v = 0.0;
+  for (int q = p_begin[p]; q < p_begin[p + 1]; ++q) {
+    const int s = p_slots[q];
+    v += coef[s] * contrib[(size_t)s * m + j];
+  }
+  J[(size_t)(row0 + j) * ldj + p] = v;
+}
+
+cudaError_t assemble_jacobian(const double *contrib, const double *coef, const int32_t *p_begin,
+                              const int32_t *p_slots, int n_params, int m, int row0, int ldj,
+                              double *J, cudaStream_t st) {
+  const int total = n_params * m;
+  if (total <= 0) return cudaSuccess;
+  k_assemble_jacobian<<<(total + 127) / 128, 128, 0, st>>>(contrib, coef, p_begin, p_slots, n_params, m,
+                                                            row0, ldj, J);
+  return cudaGetLastError();
+}
+
+}  // namespace sv

@@ -1,0 +1,152 @@
+// Launcher definitions of Launch<R>; included once per precision.
+#pragma once
+
+#include "sv_kernels.cuh"
+
+namespace sv {
+
+namespace detail {
+inline int tile_bytes(int elem, int T) { return elem << T; }
+inline int lut_bytes(const PassDev &p) { return 8 << (p.T - p.nlow); }
+constexpr int kWarps = kBlock / 32;
+constexpr int kMaxDynSmem = 227 * 1024;
+
+template <typename Kern>
+inline void allow_big_smem(Kern k, bool &done) {
+  if (!done) {
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
+    done = true;
+  }
+}
+}  // namespace detail
+
+template <typename R>
+cudaError_t Launch<R>::build_matrices(const MatSlot *slots, int n_slots, const double *params,
+                                      const double *user_mats, void *mats, cudaStream_t st) {
+  if (n_slots <= 0) return cudaSuccess;
+  const int tpb = 64;
+  k_build_matrices<R><<<(n_slots + tpb - 1) / tpb, tpb, 0, st>>>(slots, n_slots, params, user_mats,
+                                                                   reinterpret_cast<c_t<R> *>(mats));
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t Launch<R>::tile_forward(void *psi, int n, const PassDev &pass, const OpDev *ops,
+                                    const void *mats, int grid, cudaStream_t st) {
+  static bool attr2 = false, attr4 = false;
+  const int smem = detail::tile_bytes(sizeof(c_t<R>), pass.T) + detail::lut_bytes(pass);
+  if (pass.max_k <= 2) {
+    detail::allow_big_smem(k_tile_forward<R, 2>, attr2);
+    k_tile_forward<R, 2><<<grid, kBlock, smem, st>>>(reinterpret_cast<c_t<R> *>(psi), n, pass, ops,
+                                                      reinterpret_cast<const c_t<R> *>(mats));
+  } else {
+    detail::allow_big_smem(k_tile_forward<R, 4>, attr4);
+    k_tile_forward<R, 4><<<grid, kBlock, smem, st>>>(reinterpret_cast<c_t<R> *>(psi), n, pass, ops,
+                                                      reinterpret_cast<const c_t<R> *>(mats));
+  }
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t Launch<R>::tile_adjoint(const void *phi_in, void *phi_out, void *lam, int n, int m,
+                                    const PassDev &pass, const OpDev *ops, const void *mats,
+                                    double *partials, int grid, cudaStream_t st) {
+  static bool attr2 = false, attr4 = false;
+  const int smem = 2 * detail::tile_bytes(sizeof(c_t<R>), pass.T) + detail::lut_bytes(pass) +
+                   pass.n_train * detail::kWarps * 8;
+  dim3 g(m, grid);
+  if (pass.max_k <= 2) {
+    detail::allow_big_smem(k_tile_adjoint<R, 2>, attr2);
+    k_tile_adjoint<R, 2><<<g, kBlock, smem, st>>>(reinterpret_cast<const c_t<R> *>(phi_in),
+                                                   reinterpret_cast<c_t<R> *>(phi_out),
+                                                   reinterpret_cast<c_t<R> *>(lam), n, pass, ops,
+                                                   reinterpret_cast<const c_t<R> *>(mats), partials);
+  } else {
+    detail::allow_big_smem(k_tile_adjoint<R, 4>, attr4);
+    k_tile_adjoint<R, 4><<<g, kBlock, smem, st>>>(reinterpret_cast<const c_t<R> *>(phi_in),
+                                                   reinterpret_cast<c_t<R> *>(phi_out),
+                                                   reinterpret_cast<c_t<R> *>(lam), n, pass, ops,
+                                                   reinterpret_cast<const c_t<R> *>(mats), partials);
+  }
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t Launch<R>::expval_pass(const void *psi, int n, const PassDev &pass, const TermDev *terms,
+                                   int n_terms, double *partials, int grid, cudaStream_t st) {
+  static bool attr = false;
+  detail::allow_big_smem(k_expval<R>, attr);
+  const int smem = detail::tile_bytes(sizeof(c_t<R>), pass.T) + detail::lut_bytes(pass) +
+                   n_terms * detail::kWarps * 8;
+  k_expval<R><<<grid, kBlock, smem, st>>>(reinterpret_cast<const c_t<R> *>(psi), n, pass, terms, n_terms,
+                                           partials);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t Launch<R>::lambda_pass(const void *phi, void *lam, int n, const PassDev &pass,
+                                   const TermDev *terms, const int32_t *obs_term_begin, int n_obs,
+                                   int first, int grid, cudaStream_t st) {
+  static bool attr = false;
+  detail::allow_big_smem(k_lambda<R>, attr);
+  const int smem = detail::tile_bytes(sizeof(c_t<R>), pass.T) + detail::lut_bytes(pass);
+  dim3 g(grid, n_obs);
+  k_lambda<R><<<g, kBlock, smem, st>>>(reinterpret_cast<const c_t<R> *>(phi), reinterpret_cast<c_t<R> *>(lam),
+                                        n, pass, terms, obs_term_begin, first);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t Launch<R>::dense_k(void *psi, int n, const OpDev &op, const void *mats, int adjoint,
+                               cudaStream_t st) {
+  const uint64_t groups = 1ull << (n - op.k);
+  const int gpb = kBlock >> op.k;
+  uint64_t blocks = (groups + gpb - 1) / gpb;
+  if (blocks > 65535ull * 16) blocks = 65535ull * 16;
+  k_dense_k<R><<<(unsigned)blocks, kBlock, 0, st>>>(reinterpret_cast<c_t<R> *>(psi), n, op,
+                                                     reinterpret_cast<const c_t<R> *>(mats) + op.mat, adjoint);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t Launch<R>::set_basis(void *psi, int n, uint64_t index, cudaStream_t st) {
+  const uint64_t N = 1ull << n;
+  uint64_t blocks = (N + 255) / 256;
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  k_set_basis<R><<<(unsigned)blocks, 256, 0, st>>>(reinterpret_cast<c_t<R> *>(psi), N, index);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t Launch<R>::copy(void *dst, const void *src, int n, cudaStream_t st) {
+  return cudaMemcpyAsync(dst, src, sizeof(c_t<R>) << n, cudaMemcpyDeviceToDevice, st);
+}
+
+template <typename R>
+int Launch<R>::forward_smem(int T) {
+  return detail::tile_bytes(sizeof(c_t<R>), T) + (8 << T);
+}
+
+template <typename R>
+int Launch<R>::adjoint_smem(int T) {
+  return 2 * detail::tile_bytes(sizeof(c_t<R>), T) + (8 << T) + 64 * detail::kWarps * 8;
+}
+
+template <typename R>
+int Launch<R>::expval_smem(int T, int n_terms) {
+  return detail::tile_bytes(sizeof(c_t<R>), T) + (8 << T) + n_terms * detail::kWarps * 8;
+}
+
+// Tile sizes: 32 KiB of amplitudes per tile in the forward / expval kernels,
+// 2 x 16 KiB (phi + lambda) in the adjoint kernel.
+template <typename R>
+int Launch<R>::max_T_forward() {
+  return std::is_same<R, float>::value ? 12 : 11;
+}
+
+template <typename R>
+int Launch<R>::max_T_adjoint() {
+  return std::is_same<R, float>::value ? 11 : 10;
+}
+
+}  // namespace sv

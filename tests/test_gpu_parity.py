@@ -1,0 +1,305 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (fixed by the accuracy targets of the state-vector core):
+  complex128: amplitudes 1e-12 absolute; expectation values 1e-10 relative
+              (to max(1, |E|)); Jacobian entries 1e-9 relative to max(1, max|J|).
+  complex64:  1e-4 on amplitudes, expectation values and Jacobian entries
+              (relative to max(1, |.|)), with FP32 gate arithmetic and FP64 /
+              compensated reductions.
+Sizes span several tiles (n > 11 local bits for complex128, > 12 for
+complex64) and ragged cases (n = 1, 2, 3; empty tapes; zero-term observables).
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import dense
+from workloads import (Circuit, Op, Term, GATE_ARITY, GATE_NPARAMS, layered_circuit, qaoa_maxcut,
+                       random_circuit, random_hamiltonian, random_state, ry_cz_brick,
+                       strongly_entangling, vqe_givens)
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - GPU-only module
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2403_02512_gb300 as svlib  # noqa: E402
+from paper_2403_02512_gb300 import _lib as L  # noqa: E402
+from paper_2403_02512_gb300.torch_api import Program, StateVector, expval as ad_expval  # noqa: E402
+
+DTYPES = ["c128", "c64"]
+TOL_STATE = {"c128": 1e-12, "c64": 1e-4}
+TOL_E = {"c128": 1e-10, "c64": 1e-4}
+TOL_J = {"c128": 1e-9, "c64": 1e-4}
+
+
+def _state(n, dtype, seed):
+    sv = StateVector(n, dtype)
+    psi = random_state(n, seed)
+    sv.set_numpy(psi)
+    # the oracle starts from exactly the amplitudes the GPU holds
+    return sv, sv.to_numpy().astype(np.complex128)
+
+
+def _assert_state(got, want, dtype):
+    err = np.abs(got.astype(np.complex128) - want).max()
+    assert err <= TOL_STATE[dtype], f"max amplitude error {err:.3e}"
+
+
+def _assert_rel(got, want, tol, what):
+    got, want = np.asarray(got, dtype=np.float64), np.asarray(want, dtype=np.float64)
+    scale = max(1.0, float(np.abs(want).max()) if want.size else 1.0)
+    err = float(np.abs(got - want).max()) if want.size else 0.0
+    assert err <= tol * scale, f"{what}: max error {err:.3e} > {tol:.1e} * {scale:.3g}"
+
+
+# ---------------------------------------------------------------------------
+# S1-S3: every gate, every wire, controls, adjoint flag
+# ---------------------------------------------------------------------------
+GATES = [g for g in GATE_ARITY if g != "Identity"]
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 9, 13])
+def test_single_gates_every_wire(dtype, n):
+    rng = np.random.default_rng(1000 + n)
+    for name in GATES:
+        k = GATE_ARITY[name]
+        if k > n:
+            continue
+        trials = n if n <= 5 else 6
+        for trial in range(trials):
+            wires = tuple(int(w) for w in rng.permutation(n)[:k]) if n > 5 else \
+                tuple(int((trial + j) % n) for j in range(k))
+            free = [w for w in range(n) if w not in wires]
+            nc = min(len(free), trial % 3)
+            controls = tuple(free[:nc])
+            cvals = tuple(int(v) for v in rng.integers(0, 2, size=nc))
+            npar = GATE_NPARAMS[name]
+            op = Op(name, wires, tuple(range(npar)), controls, cvals, bool(trial % 2))
+            params = rng.uniform(-4, 4, size=npar)
+            sv, psi = _state(n, dtype, 7 * n + trial)
+            L.sv_apply_op(sv.handle, L.Tape([op], npar).ops[0], params if npar else None)
+            want = oracle.apply_op(psi.copy(), op, params)
+            _assert_state(sv.to_numpy(), want, dtype)
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_sv_apply_plain_gates_and_matrices(dtype):
+    n = 6
+    sv, psi = _state(n, dtype, 3)
+    sv.apply("RX", [2], [0.7]).apply("IsingXX", [0, 5], [1.3]).apply("Hadamard", [4]).apply("RZ", [1], [2.1], True)
+    for op in (Op("RX", (2,), (0,)), Op("IsingXX", (0, 5), (0,)), Op("Hadamard", (4,)), Op("RZ", (1,), (0,), adjoint=True)):
+        ang = {"RX": [0.7], "IsingXX": [1.3], "RZ": [2.1]}.get(op.name, [])
+        oracle.apply_op(psi, op, np.array(ang))
+    _assert_state(sv.to_numpy(), psi, dtype)
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("k", [1, 3, 5, 6])
+def test_dense_matrix_blocks(dtype, k):
+    n = 13
+    rng = np.random.default_rng(k)
+    A = rng.normal(size=(1 << k, 1 << k)) + 1j * rng.normal(size=(1 << k, 1 << k))
+    U, _ = np.linalg.qr(A)
+    wires = [int(w) for w in rng.permutation(n)[:k]]
+    for adjoint in (False, True):
+        sv, psi = _state(n, dtype, 40 + k)
+        sv.apply_matrix(wires, U, adjoint)
+        oracle.apply_matrix(psi, U.conj().T if adjoint else U, wires)
+        tol = TOL_STATE[dtype] * (10 if dtype == "c128" else 1)
+        assert np.abs(sv.to_numpy() - psi).max() <= tol
+
+
+# ---------------------------------------------------------------------------
+# S4: fused forward passes
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("n,seed", [(3, 1), (7, 2), (12, 3), (14, 4)])
+def test_random_circuit_forward(dtype, n, seed):
+    c, p = random_circuit(n, 80, seed, max_controls=2)
+    sv, psi = _state(n, dtype, seed)
+    prog = Program(sv, c.ops, c.n_params)
+    prog.forward(p, reset=False)
+    _assert_state(sv.to_numpy(), oracle.forward(c, p, psi), dtype)
+
+
+def test_empty_tape_leaves_the_state():
+    sv, psi = _state(5, "c128", 9)
+    L.sv_forward(sv.handle, L.Tape([], 0), np.zeros(0))
+    assert np.array_equal(sv.to_numpy(), psi)
+
+
+# ---------------------------------------------------------------------------
+# S5: expectation values
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("n", [1, 3, 8, 13, 15])
+def test_pauli_sum_expvals(dtype, n):
+    rng = np.random.default_rng(n)
+    obs = [random_hamiltonian(n, 40, rng, weights=tuple(range(1, min(n, 4) + 1))),
+           [Term(0.5, ())],                                 # identity term
+           [],                                               # zero terms
+           [Term(1.0, ((n - 1, "Y"),)), Term(-2.0, ((0, "X"),))]]
+    sv, psi = _state(n, dtype, 100 + n)
+    got = sv.expval(obs)
+    want = np.array([oracle.expval(psi, H) for H in obs])
+    _assert_rel(got, want, TOL_E[dtype], "expval")
+    assert abs(sv.norm2() - oracle.norm2(psi)) <= TOL_E[dtype]
+
+
+def test_expvals_repeat_bitwise():
+    n = 16
+    rng = np.random.default_rng(5)
+    obs = [random_hamiltonian(n, 300, rng)]
+    sv, _ = _state(n, "c128", 5)
+    a, b = sv.expval(obs), sv.expval(obs)
+    assert np.array_equal(a, b)
+
+
+# ---------------------------------------------------------------------------
+# S6-S8: adjoint Jacobian, VJP, autograd
+# ---------------------------------------------------------------------------
+def _obs_for(n, rng):
+    return [random_hamiltonian(n, 5, rng, weights=tuple(range(1, min(n, 3) + 1))),
+            [Term(1.0, ((0, "Z"),))],
+            random_hamiltonian(n, 3, rng, weights=(1,))]
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("n,seed", [(2, 11), (4, 12), (7, 13), (12, 14), (13, 15)])
+def test_adjoint_jacobian_random_circuits(dtype, n, seed):
+    c, p = random_circuit(n, 40, seed, shared_params=True)
+    rng = np.random.default_rng(seed)
+    obs = _obs_for(n, rng)
+    sv = StateVector(n, dtype)
+    prog = Program(sv, c.ops, c.n_params, obs)
+    prog.forward(p)
+    E, J = prog.jacobian()
+    Eo, Jo = oracle.adjoint_jacobian(c, p, obs)
+    _assert_rel(E.cpu().numpy(), Eo, TOL_E[dtype], "expvals")
+    _assert_rel(J.cpu().numpy(), Jo, TOL_J[dtype], "jacobian")
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_one_shot_jacobian_and_vjp_calls(dtype):
+    n = 9
+    c, p = random_circuit(n, 30, 21)
+    rng = np.random.default_rng(21)
+    obs = _obs_for(n, rng)
+    h = L.sv_create(n, L.SV_C64 if dtype == "c64" else L.SV_C128)
+    try:
+        tape, ps = L.Tape(c.ops, c.n_params), L.PauliSums(obs)
+        L.sv_forward(h, tape, p)
+        E, J = L.sv_adjoint_jacobian(h, tape, p, ps)
+        g = rng.normal(size=len(obs))
+        v = L.sv_adjoint_vjp(h, tape, p, ps, g)
+    finally:
+        L.sv_destroy(h)
+    Eo, Jo = oracle.adjoint_jacobian(c, p, obs)
+    _assert_rel(E, Eo, TOL_E[dtype], "expvals")
+    _assert_rel(J, Jo, TOL_J[dtype], "jacobian")
+    _assert_rel(v, g @ Jo, TOL_J[dtype], "vjp")
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_lambda_chunking_matches_single_sweep(dtype, monkeypatch):
+    n = 12
+    c, p = strongly_entangling(n, 2, seed=3)
+    sv = StateVector(n, dtype)
+    full = Program.from_circuit(sv, c)
+    full.forward(p)
+    E1, J1 = full.jacobian()
+    monkeypatch.setenv("SV_LAMBDA_CHUNK", "5")
+    chunked = Program.from_circuit(sv, c)
+    E2, J2 = chunked.jacobian()
+    assert torch.equal(E1, E2)
+    _assert_rel(J2.cpu().numpy(), J1.cpu().numpy(), 1e-12 if dtype == "c128" else 1e-6, "chunked")
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_autograd_function_backward_is_adjoint_vjp(dtype):
+    n = 10
+    c, p = strongly_entangling(n, 2, seed=8)
+    sv = StateVector(n, dtype)
+    prog = Program.from_circuit(sv, c)
+    params = torch.tensor(p, dtype=torch.float64, device="cuda", requires_grad=True)
+    E = ad_expval(params, prog)
+    w = torch.linspace(-1, 1, E.numel(), dtype=torch.float64, device="cuda")
+    (E * w).sum().backward()
+    _, Jo = oracle.adjoint_jacobian(c, p)
+    _assert_rel(params.grad.cpu().numpy(), w.cpu().numpy() @ Jo, TOL_J[dtype], "autograd grad")
+
+
+def test_jacobian_repeats_bitwise():
+    n = 13
+    c, p = random_circuit(n, 30, 31)
+    obs = _obs_for(n, np.random.default_rng(31))
+    sv = StateVector(n, "c128")
+    prog = Program(sv, c.ops, c.n_params, obs)
+    prog.forward(p)
+    E1, J1 = prog.jacobian()
+    E2, J2 = prog.jacobian()
+    assert torch.equal(E1, E2) and torch.equal(J1, J2)
+
+
+# ---------------------------------------------------------------------------
+# The five workload shapes at oracle-friendly sizes
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_layered_12_qubit_full_size(dtype):
+    c, p = layered_circuit(12, 10)
+    sv = StateVector(12, dtype)
+    prog = Program.from_circuit(sv, c)
+    prog.forward(p)
+    E, J = prog.jacobian()
+    Eo, Jo = oracle.adjoint_jacobian(c, p)
+    _assert_rel(E.cpu().numpy(), Eo, TOL_E[dtype], "expvals")
+    _assert_rel(J.cpu().numpy(), Jo, TOL_J[dtype], "jacobian")
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("maker", ["sel", "qaoa", "vqe", "rycz"])
+def test_workload_shapes_small(dtype, maker):
+    if maker == "sel":
+        c, p = strongly_entangling(13, 3, seed=1)
+    elif maker == "qaoa":
+        c = qaoa_maxcut(14, 2, seed=2)
+        p = np.random.default_rng(2).uniform(0, math.pi, size=4)
+    elif maker == "vqe":
+        c, p = vqe_givens(12, 6, 10, 20, 150, seed=3)
+    else:
+        c, p = ry_cz_brick(14, 4, seed=4)
+    sv = StateVector(c.n, dtype, basis_state=c.basis_state)
+    prog = Program.from_circuit(sv, c)
+    prog.forward(p)
+    if maker == "vqe":
+        amps = sv.to_numpy()
+        weights = np.array([bin(i).count("1") for i in range(1 << c.n)])
+        assert np.all(amps[weights != 6] == 0)          # Givens gates keep Hamming weight exactly
+    E, J = prog.jacobian()
+    Eo, Jo = oracle.adjoint_jacobian(c, p)
+    _assert_rel(E.cpu().numpy(), Eo, TOL_E[dtype], "expvals")
+    _assert_rel(J.cpu().numpy(), Jo, TOL_J[dtype], "jacobian")
+
+
+def test_error_status_for_bad_calls():
+    sv = StateVector(4, "c128")
+    with pytest.raises(L.SvError) as ei:
+        sv.apply("RX", [7], [0.1])
+    assert ei.value.status == 1
+    with pytest.raises(L.SvError):
+        sv.apply("RX", [1], [float("nan")])
+    with pytest.raises(L.SvError):
+        sv.expval([[Term(1.0, ((9, "Z"),))]])
+    L.sv_set_alloc_cap(1 << 20)
+    try:
+        with pytest.raises(L.SvError) as ei:
+            L.sv_create(20, L.SV_C128)
+        assert ei.value.status == 2
+    finally:
+        L.sv_set_alloc_cap(0)

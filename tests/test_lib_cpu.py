@@ -1,0 +1,86 @@
+"""Host-only checks of libsv.so: it builds for sm_103a, loads, exports every
+entry point declared in include/sv.h, and its planner / validation work
+without a GPU."""
+
+import os
+import re
+
+import pytest
+
+import paper_2403_02512_gb300 as svlib
+from paper_2403_02512_gb300 import _lib as L
+from workloads import (Op, layered_circuit, qaoa_maxcut, random_circuit, ry_cz_brick, strongly_entangling,
+                       vqe_givens)
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_symbols():
+    text = open(os.path.join(ROOT, "include", "sv.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(sv_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_library_builds_and_exports_every_declared_symbol():
+    lib = L.load()
+    syms = _declared_symbols()
+    assert len(syms) >= 25
+    for name in syms:
+        assert hasattr(lib, name), f"libsv.so does not export {name}"
+        assert name in L.PROTOTYPES, f"binding has no prototype for {name}"
+    assert "sm_103a" in svlib.sv_version()
+
+
+def test_plan_counts_fuse_gates_into_few_passes():
+    c, _ = strongly_entangling(24, 8)
+    tape = L.Tape(c.ops, c.n_params)
+    f128, a128 = L.sv_plan_query(24, L.SV_C128, tape)
+    f64, a64 = L.sv_plan_query(24, L.SV_C64, tape)
+    n_gates = len(c.ops)
+    assert f128 < n_gates / 4 and f64 <= f128
+    assert a128 < 3 * n_gates / 4  # expanded Rot = 3 ops each
+    c1, _ = layered_circuit(12, 10)
+    f, a = L.sv_plan_query(12, L.SV_C128, L.Tape(c1.ops, c1.n_params))
+    assert f <= 2 * 10 and a >= 1  # 12 wires > 11 local bits: two passes per layer
+
+
+@pytest.mark.parametrize("maker", ["qaoa", "vqe", "rycz"])
+def test_plan_query_accepts_every_workload_shape(maker):
+    if maker == "qaoa":
+        c = qaoa_maxcut(20, 4)
+    elif maker == "vqe":
+        c, _ = vqe_givens(24, 12, 40, 120, 10)
+    else:
+        c, _ = ry_cz_brick(30, 20)
+    f, a = L.sv_plan_query(c.n, L.SV_C128, L.Tape(c.ops, c.n_params))
+    assert 1 <= f <= len(c.ops) and 1 <= a
+
+
+@pytest.mark.parametrize("bad,msg", [
+    (Op("RX", (5,), (0,)), "out of range"),
+    (Op("PauliX", (1,), controls=(1,)), "used twice"),
+    (Op("RX", (0,), (3,)), "n_params"),
+])
+def test_validation_rejects_bad_ops_before_any_launch(bad, msg):
+    tape = L.Tape([bad], 1)
+    with pytest.raises(L.SvError) as ei:
+        L.sv_plan_query(4, L.SV_C128, tape)
+    assert ei.value.status == 1 and msg in str(ei.value)
+
+
+def test_validation_rejects_bad_sizes():
+    tape = L.Tape([Op("Hadamard", (0,))], 0)
+    for n in (0, 35):
+        with pytest.raises(L.SvError) as ei:
+            L.sv_plan_query(n, L.SV_C128, tape)
+        assert ei.value.status == 1
+
+
+def test_planner_checks_hold_for_random_circuits():
+    # check_plan runs inside sv_plan_query: local targets, tile widths, low runs
+    for n in list(range(1, 16)) + [20, 24, 30]:
+        for seed in range(4):
+            c, _ = random_circuit(n, 60, 1000 * n + seed, max_controls=3)
+            for dt in (L.SV_C64, L.SV_C128):
+                f, a = L.sv_plan_query(n, dt, L.Tape(c.ops, c.n_params))
+                assert 1 <= f <= len(c.ops) and a >= f
