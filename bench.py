@@ -1,0 +1,334 @@
+#!/usr/bin/env python
+"""Benchmark of the state-vector hot path on one GB300 (or N replicas).
+
+Step = forward pass + expectation values + full adjoint Jacobian of the
+24-qubit strongly-entangling-layers workload (8 layers of Rot per wire plus a
+CNOT ring of range r = l mod 23 + 1; 576 parameters; 24 single-Z observables)
+in complex128, all kernels of the library on the GPU.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the baseline arm) on the host cores.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "adjoint-Jacobian ms & gate HBM GB/s (% peak) at 24-30 qubits; batched circuits/s"
+WORKLOAD = ("sel24: 24-qubit StronglyEntanglingLayers, 8 layers of Rot(phi,theta,omega) per wire + CNOT ring "
+            "range l mod 23 + 1, 576 parameters, 24 single-Z observables; step = forward + expvals + full "
+            "adjoint Jacobian (24 x 576)")
+N_QUBITS, LAYERS = 24, 8
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--dtype", choices=["c128", "c64"], default="c128")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the complex64 and per-gate side measurements")
+    return ap.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for ln in open(self.path):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) >= 9 and f[1].replace(".", "").isdigit():
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]), "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())}
+
+
+# ---------------------------------------------------------------------------
+# oracle (CPU baseline / reference arm) on a bounded sample
+# ---------------------------------------------------------------------------
+def oracle_sample(sweep_steps: int = 6):
+    """Time the FP64 oracle on the sel24 workload and scale to one full step.
+
+    Sample: the full forward pass (all 384 ops), lambda_j = Z_j psi for the 24
+    observables, and `sweep_steps` steps of the adjoint sweep (each step: 24
+    generator inner products and 25 un-applied vectors).  The full step is
+    estimated as forward + lambda + (sweep time per step) x (1152 sweep steps).
+    """
+    import oracle
+    from workloads import strongly_entangling
+
+    c, p = strongly_entangling(N_QUBITS, LAYERS)
+    steps = oracle.expand(c.ops)
+    t0 = time.perf_counter()
+    psi = oracle.forward(c, p)
+    t1 = time.perf_counter()
+    lams = [oracle.apply_hamiltonian(psi, H) for H in c.observables]
+    t2 = time.perf_counter()
+    phi = psi
+    for st in list(reversed(steps))[:sweep_steps]:
+        M = oracle.core._step_matrix(st, p)
+        if st.param is not None:
+            G, _ = oracle.generator(st.name)
+            mu = oracle.copy(phi)
+            oracle.apply_matrix(mu, G, st.wires, st.controls, st.cvals)
+            for lam in lams:
+                oracle.inner(lam, mu)
+        Md = M.conj().T.copy()
+        oracle.apply_matrix(phi, Md, st.wires, st.controls, st.cvals)
+        for lam in lams:
+            oracle.apply_matrix(lam, Md, st.wires, st.controls, st.cvals)
+    t3 = time.perf_counter()
+    est_ms = 1e3 * ((t1 - t0) + (t2 - t1) + (t3 - t2) / sweep_steps * len(steps))
+    sample = (f"oracle FP64 on sel24 at full size: forward (384 ops) + 24 lambdas + {sweep_steps} of "
+              f"{len(steps)} adjoint-sweep steps, scaled to the full sweep")
+    return est_ms, sample, oracle.num_threads(), (t3 - t0)
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    times = []
+    sample = cores = None
+    for i in range(args.warmup + args.steps):
+        est, sample, cores, _ = oracle_sample(sweep_steps=3)
+        if i >= args.warmup:
+            times.append(est)
+    value = statistics.mean(times)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "ms", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": value, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_qubits": N_QUBITS, "n_params": 576, "n_observables": 24},
+            "cpu_baseline": {"value": value, "unit": "ms", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2403_02512_gb300 import _lib as L
+    from paper_2403_02512_gb300.torch_api import Program, StateVector
+    from workloads import strongly_entangling
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    hbm_peak, peak_kind = peaks()
+    c, p = strongly_entangling(N_QUBITS, LAYERS)
+    m, P = len(c.observables), c.n_params
+
+    def measure(dtype, steps, warmup, timing):
+        sv = StateVector(N_QUBITS, dtype)
+        prog = Program.from_circuit(sv, c)
+        params = torch.tensor(p, dtype=torch.float64, device="cuda")
+        stream = torch.cuda.current_stream()
+
+        def step():
+            prog.set_params(params)
+            prog.forward()
+            return prog.jacobian()
+
+        for _ in range(warmup):
+            step()
+        torch.cuda.synchronize()
+        launches_fwd = prog.stats()[2]
+        if timing:
+            L.sv_kernel_timing_reset()
+            L.sv_kernel_timing_enable(True)
+        barrier()
+        torch.cuda.synchronize()
+        clocks = ClockSampler(local)
+        if timing:
+            clocks.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        launches = 0
+        for _ in range(steps):
+            prog.set_params(params)
+            launches += prog.stats()[2]
+            prog.forward()
+            launches += prog.stats()[2]
+            E, J = prog.jacobian()
+            launches += prog.stats()[2]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        clk = clocks.stop() if timing else None
+        ms = e0.elapsed_time(e1) / steps
+        kt = None
+        if timing:
+            L.sv_kernel_timing_enable(False)
+            kt = L.sv_kernel_timing_read()
+        fp, ap, _ = prog.stats()
+        out = {"ms": ms, "launches": launches, "kt": kt, "clocks": clk, "fwd_passes": fp, "adj_passes": ap,
+               "J": J, "E": E, "vec_bytes": (16 if dtype == "c128" else 8) << N_QUBITS}
+        prog.close()
+        sv.close()
+        del params
+        torch.cuda.empty_cache()
+        return out
+
+    main = measure(args.dtype, args.steps, args.warmup, timing=True)
+    ms = main["ms"]
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # roofline of the dominant kernel (tile_adjoint): algorithmic bytes 2V(1 + m) per launch
+    kt = main["kt"]
+    V = main["vec_bytes"]
+    adj_ms, adj_n = kt["tile_adjoint"]
+    bytes_per_launch = 2.0 * V * (1 + m)
+    achieved = bytes_per_launch * adj_n / (adj_ms * 1e-3) / 1e9 if adj_ms > 0 else None
+    total_kernel_ms = sum(v[0] for v in kt.values())
+    shares = {k: round(v[0] / total_kernel_ms, 4) for k, v in kt.items() if v[1] > 0}
+    roofline = {"kernel": "k_tile_adjoint", "bound": "hbm", "achieved": achieved, "peak": hbm_peak,
+                "unit": "GB/s", "frac": (achieved / hbm_peak) if achieved else None, "traffic": None,
+                "peak_kind": peak_kind, "avg_launch_ms": adj_ms / max(1, adj_n),
+                "algorithmic_bytes_per_launch": bytes_per_launch, "kernel_time_shares": shares}
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    e2e = None
+    if rank == 0 or True:
+        dt = L.SV_C128 if args.dtype == "c128" else L.SV_C64
+        h = L.sv_create(N_QUBITS, dt)
+        L.sv_set_stream(h, torch.cuda.current_stream().cuda_stream)
+        tape, obs = L.Tape(c.ops, P), L.PauliSums(c.observables)
+        pin = torch.tensor(p, dtype=torch.float64).pin_memory()
+        p_host = pin.numpy()
+        for _ in range(1):
+            L.sv_reset(h, 0)
+            L.sv_forward(h, tape, p_host)
+            L.sv_adjoint_jacobian(h, tape, p_host, obs)
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            L.sv_reset(h, 0)
+            L.sv_forward(h, tape, p_host)
+            E_h, J_h = L.sv_adjoint_jacobian(h, tape, p_host, obs)
+        torch.cuda.synchronize()
+        e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+        barrier()
+        L.sv_destroy(h)
+        err = float(np.abs(J_h - main["J"].cpu().numpy()).max())
+        e2e = {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": 2 * P * 8,
+               "d2h_bytes_per_step": (m + m * P) * 8, "api": "sv_reset + sv_forward + sv_adjoint_jacobian",
+               "max_abs_diff_vs_device_path": err}
+
+    extras = {}
+    if not args.no_extras and rank == 0:
+        other = "c64" if args.dtype == "c128" else "c128"
+        o = measure(other, max(2, args.steps // 2), 2, timing=False)
+        dJ = float(np.abs(o["J"].cpu().numpy() - main["J"].cpu().numpy()).max())
+        extras[other] = {"ms_per_step": o["ms"], "max_abs_jacobian_diff_vs_" + args.dtype: dJ}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        est, sample, cores, wall = oracle_sample()
+        cpu = {"value": est, "unit": "ms", "cores": cores, "kind": "oracle", "sample": sample,
+               "sample_wall_s": wall}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": ms / world if world > 1 else ms, "unit": "ms", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.dtype == "c128" else "f32",
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD, "precision": args.dtype, "n_qubits": N_QUBITS, "layers": LAYERS,
+                           "n_params": P, "n_observables": m, "parallelism": "replicas" if world > 1 else "single",
+                           "l2": "inputs larger than L2: state 268 MB (c128) and 24 lambda vectors 6.4 GB per step",
+                           "forward_passes": main["fwd_passes"], "adjoint_passes": main["adj_passes"]},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": main["launches"],
+                "clocks": main["clocks"], "extras": extras}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

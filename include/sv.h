@@ -265,6 +265,18 @@ sv_status sv_program_vjp(sv_program *p, const double *grad_out, double *vjp_out,
 sv_status sv_program_stats(const sv_program *p, int *n_forward_passes, int *n_adjoint_passes,
                            int *launches_last_call);
 
+/* Kernel timing for roofline accounting.  While enabled, every kernel launch of
+ * the library is bracketed by CUDA events on the stream it runs on, grouped by
+ * kernel class: 0 tile_forward, 1 tile_adjoint, 2 expval, 3 lambda, 4 reduce
+ * (all deterministic reductions), 5 build_matrices, 6 dense_k, 7 other.
+ * sv_kernel_timing_read synchronises the device, adds the elapsed times of the
+ * completed launches to per-class totals and reports them (ms, launches).
+ * SV_KERNEL_CLASSES entries each; NULL outputs are skipped.  Reset clears totals. */
+#define SV_KERNEL_CLASSES 8
+sv_status sv_kernel_timing_enable(int enable);
+sv_status sv_kernel_timing_reset(void);
+sv_status sv_kernel_timing_read(double *total_ms, int64_t *launches);
+
 /* Host-only planner query (no GPU needed): number of fused forward passes and
  * adjoint passes this build would use for a tape on n qubits and dtype. */
 sv_status sv_plan_query(int n, sv_dtype dtype, const sv_tape *tape,

@@ -114,7 +114,13 @@ PROTOTYPES = {
     "sv_program_vjp": (ctypes.c_int, [_vp, _dp, _vp, ctypes.c_int]),
     "sv_program_stats": (ctypes.c_int, [_vp, _ip, _ip, _ip]),
     "sv_plan_query": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(SvTape), _ip, _ip]),
+    "sv_kernel_timing_enable": (ctypes.c_int, [ctypes.c_int]),
+    "sv_kernel_timing_reset": (ctypes.c_int, []),
+    "sv_kernel_timing_read": (ctypes.c_int, [_dp, ctypes.POINTER(ctypes.c_int64)]),
 }
+
+KERNEL_CLASSES = ["tile_forward", "tile_adjoint", "expval", "lambda", "reduce", "build_matrices", "dense_k",
+                  "other"]
 
 _LIB: Optional[ctypes.CDLL] = None
 
@@ -310,6 +316,22 @@ def sv_plan_query(n: int, dtype: int, tape: "Tape"):
     a, b = ctypes.c_int(), ctypes.c_int()
     _check(load().sv_plan_query(int(n), int(dtype), ctypes.byref(tape.struct), ctypes.byref(a), ctypes.byref(b)))
     return a.value, b.value
+
+
+def sv_kernel_timing_enable(enable: bool) -> None:
+    _check(load().sv_kernel_timing_enable(int(bool(enable))))
+
+
+def sv_kernel_timing_reset() -> None:
+    _check(load().sv_kernel_timing_reset())
+
+
+def sv_kernel_timing_read():
+    """{class name: (total ms, launches)} of the launches bracketed so far."""
+    ms = (ctypes.c_double * len(KERNEL_CLASSES))()
+    cnt = (ctypes.c_int64 * len(KERNEL_CLASSES))()
+    _check(load().sv_kernel_timing_read(ms, cnt))
+    return {name: (ms[i], cnt[i]) for i, name in enumerate(KERNEL_CLASSES)}
 
 
 # ---------------------------------------------------------------------------

@@ -76,6 +76,48 @@ int sm_count() {
   return n;
 }
 
+// ---- kernel timing (roofline accounting) -------------------------------------
+struct TimedLaunch {
+  cudaEvent_t a, b;
+  int cls;
+};
+std::atomic<bool> g_timing{false};
+std::vector<TimedLaunch> g_pending;
+std::vector<cudaEvent_t> g_event_pool;
+double g_class_ms[SV_KERNEL_CLASSES] = {0};
+int64_t g_class_n[SV_KERNEL_CLASSES] = {0};
+
+cudaEvent_t take_event() {
+  if (!g_event_pool.empty()) {
+    cudaEvent_t e = g_event_pool.back();
+    g_event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Bracket one launch with events when timing is on.
+struct LaunchTimer {
+  cudaStream_t st;
+  int cls;
+  cudaEvent_t a = nullptr;
+  LaunchTimer(cudaStream_t s_, int c) : st(s_), cls(c) {
+    if (g_timing.load()) {
+      a = take_event();
+      cudaEventRecord(a, st);
+    }
+  }
+  ~LaunchTimer() {
+    if (a) {
+      cudaEvent_t b = take_event();
+      cudaEventRecord(b, st);
+      g_pending.push_back({a, b, cls});
+    }
+  }
+};
+
 // ---- gate tables -----------------------------------------------------------
 int kind_arity(int kind) {
   switch (kind) {
@@ -605,6 +647,7 @@ struct sv_program {
   int grid_a(int mcc) const { return (int)std::max<uint64_t>(1, std::min<uint64_t>(tiles_a, ctas_a / std::max(1, mcc))); }
   int grid_l(int mcc) const { return (int)std::max<uint64_t>(1, std::min<uint64_t>(tiles_l, ctas_l / std::max(1, mcc))); }
   int launches = 0;
+  bool params_set = false;  // gate matrices built at least once
 };
 
 namespace {
@@ -915,10 +958,21 @@ sv_status program_set_params(sv_program *p, const double *params, int on_device)
     if (e != cudaSuccess) return cuda_fail(e, "copying parameters");
   }
   p->launches = 0;
-  sv_status st = after_launch(s, K.build_matrices(p->d_slots, p->n_slots, p->d_params, p->d_user, p->d_mats, s->stream),
-                              "build_matrices");
+  sv_status st;
+  {
+    LaunchTimer t(s->stream, 5);
+    st = after_launch(s, K.build_matrices(p->d_slots, p->n_slots, p->d_params, p->d_user, p->d_mats, s->stream),
+                      "build_matrices");
+  }
   p->launches += p->n_slots > 0;
+  if (!st) p->params_set = true;
   return st;
+}
+
+sv_status require_params(const sv_program *p) {
+  if (p->n_slots > 0 && !p->params_set)
+    return fail(SV_ERR_STATE, "program parameters were never set (call sv_program_set_params first)");
+  return SV_OK;
 }
 
 sv_status run_steps_forward(sv_program *p, void *psi) {
@@ -926,10 +980,13 @@ sv_status run_steps_forward(sv_program *p, void *psi) {
   const Ops &K = ops_for(s->dt);
   for (const Step &st : p->fwd.steps) {
     cudaError_t e;
-    if (st.dense_k)
+    if (st.dense_k) {
+      LaunchTimer t(s->stream, 6);
       e = K.dense_k(psi, s->n, p->fwd.dk_ops[st.index], p->d_mats, 0, s->stream);
-    else
+    } else {
+      LaunchTimer t(s->stream, 0);
       e = K.tile_forward(psi, s->n, p->fwd.passes[st.index], p->d_fwd_ops, p->d_mats, p->grid_f, s->stream);
+    }
     if (sv_status r = after_launch(s, e, "forward pass")) return r;
     ++p->launches;
   }
@@ -983,13 +1040,24 @@ sv_status run_expval(sv_program *p, const void *psi, const JacWs &w) {
   for (size_t q = 0; q + 1 < p->tp.begin.size(); ++q) {
     const int b = p->tp.begin[q], cnt = p->tp.begin[q + 1] - b;
     if (cnt == 0) continue;
-    cudaError_t e = K.expval_pass(psi, s->n, p->tp.passes[q], p->d_terms + b, cnt, w.partials, p->grid_e, s->stream);
+    cudaError_t e;
+    {
+      LaunchTimer t(s->stream, 2);
+      e = K.expval_pass(psi, s->n, p->tp.passes[q], p->d_terms + b, cnt, w.partials, p->grid_e, s->stream);
+    }
     if (sv_status r = after_launch(s, e, "expval pass")) return r;
-    e = reduce_partials(w.partials, p->grid_e, 1, cnt, w.term_sums, 1, b, 0, s->stream);
+    {
+      LaunchTimer t(s->stream, 4);
+      e = reduce_partials(w.partials, p->grid_e, 1, cnt, w.term_sums, 1, b, 0, s->stream);
+    }
     if (sv_status r = after_launch(s, e, "expval reduce")) return r;
     p->launches += 2;
   }
-  cudaError_t e = combine_terms(w.term_sums, p->d_terms, p->d_obs_begin, p->m, p->d_term_order, w.expvals, s->stream);
+  cudaError_t e;
+  {
+    LaunchTimer t(s->stream, 4);
+    e = combine_terms(w.term_sums, p->d_terms, p->d_obs_begin, p->m, p->d_term_order, w.expvals, s->stream);
+  }
   p->launches += p->m > 0;
   return after_launch(s, e, "combine terms");
 }
@@ -1006,8 +1074,12 @@ sv_status run_sweep(sv_program *p, const JacWs &w, int mcc, int j0, int ldc, con
   const size_t V = s->bytes;
   const int npass_e = (int)p->tp.passes.size();
   for (int q = 0; q < npass_e; ++q) {
-    cudaError_t e = K.lambda_pass(s->psi, w.lam, n, p->tp.passes[q], lam_terms, lam_begin(q), mcc, q == 0,
-                                  p->grid_l(mcc), s->stream);
+    cudaError_t e;
+    {
+      LaunchTimer t(s->stream, 3);
+      e = K.lambda_pass(s->psi, w.lam, n, p->tp.passes[q], lam_terms, lam_begin(q), mcc, q == 0, p->grid_l(mcc),
+                        s->stream);
+    }
     if (sv_status r = after_launch(s, e, "lambda pass")) return r;
     ++p->launches;
   }
@@ -1026,6 +1098,7 @@ sv_status run_sweep(sv_program *p, const JacWs &w, int mcc, int j0, int ldc, con
         advance();
       }
       const OpDev &op = p->adj.dk_ops[st.index];
+      LaunchTimer t(s->stream, 6);
       cudaError_t e = K.dense_k((void *)phi_in, n, op, p->d_mats, 1, s->stream);
       for (int j = 0; j < mcc && e == cudaSuccess; ++j) e = K.dense_k(w.lam + (size_t)j * V, n, op, p->d_mats, 1, s->stream);
       if (sv_status r = after_launch(s, e, "dense_k adjoint")) return r;
@@ -1034,11 +1107,15 @@ sv_status run_sweep(sv_program *p, const JacWs &w, int mcc, int j0, int ldc, con
     }
     const PassDev &pd = p->adj.passes[st.index];
     const int nb = p->grid_a(mcc);
-    cudaError_t e = K.tile_adjoint(phi_in, phi_out, w.lam, n, mcc, pd, p->d_adj_ops, p->d_mats, w.partials, nb,
-                                   s->stream);
+    cudaError_t e;
+    {
+      LaunchTimer t(s->stream, 1);
+      e = K.tile_adjoint(phi_in, phi_out, w.lam, n, mcc, pd, p->d_adj_ops, p->d_mats, w.partials, nb, s->stream);
+    }
     if (sv_status r = after_launch(s, e, "adjoint pass")) return r;
     ++p->launches;
     if (pd.n_train > 0) {
+      LaunchTimer t(s->stream, 4);
       e = reduce_partials(w.partials, nb, mcc, pd.n_train, w.contrib, ldc, pd.train_base, j0, s->stream);
       if (sv_status r = after_launch(s, e, "adjoint reduce")) return r;
       ++p->launches;
@@ -1063,6 +1140,7 @@ sv_status run_jacobian(sv_program *p, const JacWs &w) {
   }
   cudaError_t e;
   if (p->adj.n_train > 0 && p->n_params > 0) {
+    LaunchTimer t(s->stream, 4);
     e = assemble_jacobian(w.contrib, p->d_coef, p->d_pbegin, p->d_pslots, p->n_params, p->m, 0, p->n_params, w.J,
                           s->stream);
     ++p->launches;
@@ -1085,6 +1163,7 @@ sv_status run_vjp(sv_program *p, const JacWs &w, const double *g) {
     if (sv_status r = run_sweep(p, w, 1, 0, 1, p->d_vjp_terms, begin)) return r;
   }
   if (p->adj.n_train > 0 && p->n_params > 0) {
+    LaunchTimer t(s->stream, 4);
     e = assemble_jacobian(w.contrib, p->d_coef, p->d_pbegin, p->d_pslots, p->n_params, 1, 0, p->n_params, w.J,
                           s->stream);
     ++p->launches;
@@ -1378,6 +1457,7 @@ sv_status sv_program_set_params(sv_program *p, const double *params, int params_
 sv_status sv_program_forward(sv_program *p) {
   if (!p) return fail(SV_ERR_ARG, "program is NULL");
   if (sv_status st = check_state(p->s)) return st;
+  if (sv_status st = require_params(p)) return st;
   p->launches = 0;
   return run_steps_forward(p, p->s->psi);
 }
@@ -1385,6 +1465,7 @@ sv_status sv_program_forward(sv_program *p) {
 sv_status sv_program_jacobian(sv_program *p, double *expvals_out, double *jacobian_out, int outputs_on_device) {
   if (!p) return fail(SV_ERR_ARG, "program is NULL");
   if (sv_status st = check_state(p->s)) return st;
+  if (sv_status st = require_params(p)) return st;
   if (p->m < 1) return fail(SV_ERR_ARG, "program has no observables");
   JacWs w;
   p->launches = 0;
@@ -1413,6 +1494,7 @@ sv_status sv_program_expval(sv_program *p, double *expvals_out, int outputs_on_d
 sv_status sv_program_vjp(sv_program *p, const double *grad_out, double *vjp_out, int outputs_on_device) {
   if (!p) return fail(SV_ERR_ARG, "program is NULL");
   if (sv_status st = check_state(p->s)) return st;
+  if (sv_status st = require_params(p)) return st;
   if (p->m < 1) return fail(SV_ERR_ARG, "program has no observables");
   if (!grad_out || (p->n_params > 0 && !vjp_out)) return fail(SV_ERR_ARG, "NULL grad_out / vjp_out");
   for (int j = 0; j < p->m; ++j)
@@ -1434,6 +1516,45 @@ sv_status sv_program_stats(const sv_program *p, int *n_forward_passes, int *n_ad
   if (n_forward_passes) *n_forward_passes = (int)p->fwd.steps.size();
   if (n_adjoint_passes) *n_adjoint_passes = (int)p->adj.steps.size();
   if (launches_last_call) *launches_last_call = p->launches;
+  return SV_OK;
+}
+
+sv_status sv_kernel_timing_enable(int enable) {
+  g_timing = enable != 0;
+  return SV_OK;
+}
+
+sv_status sv_kernel_timing_reset(void) {
+  cudaError_t e = cudaDeviceSynchronize();
+  for (TimedLaunch &t : g_pending) {
+    g_event_pool.push_back(t.a);
+    g_event_pool.push_back(t.b);
+  }
+  g_pending.clear();
+  for (int c = 0; c < SV_KERNEL_CLASSES; ++c) {
+    g_class_ms[c] = 0.0;
+    g_class_n[c] = 0;
+  }
+  return e == cudaSuccess ? SV_OK : cuda_fail(e, "sv_kernel_timing_reset");
+}
+
+sv_status sv_kernel_timing_read(double *total_ms, int64_t *launches) {
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "sv_kernel_timing_read");
+  for (TimedLaunch &t : g_pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) {
+      g_class_ms[t.cls] += ms;
+      g_class_n[t.cls] += 1;
+    }
+    g_event_pool.push_back(t.a);
+    g_event_pool.push_back(t.b);
+  }
+  g_pending.clear();
+  for (int c = 0; c < SV_KERNEL_CLASSES; ++c) {
+    if (total_ms) total_ms[c] = g_class_ms[c];
+    if (launches) launches[c] = g_class_n[c];
+  }
   return SV_OK;
 }
 

@@ -216,6 +216,7 @@ def test_lambda_chunking_matches_single_sweep(dtype, monkeypatch):
     E1, J1 = full.jacobian()
     monkeypatch.setenv("SV_LAMBDA_CHUNK", "5")
     chunked = Program.from_circuit(sv, c)
+    chunked.set_params(p)
     E2, J2 = chunked.jacobian()
     assert torch.equal(E1, E2)
     _assert_rel(J2.cpu().numpy(), J1.cpu().numpy(), 1e-12 if dtype == "c128" else 1e-6, "chunked")
@@ -285,6 +286,17 @@ def test_workload_shapes_small(dtype, maker):
     Eo, Jo = oracle.adjoint_jacobian(c, p)
     _assert_rel(E.cpu().numpy(), Eo, TOL_E[dtype], "expvals")
     _assert_rel(J.cpu().numpy(), Jo, TOL_J[dtype], "jacobian")
+
+
+def test_program_refuses_to_run_before_parameters_are_set():
+    c, p = strongly_entangling(4, 1, seed=1)
+    sv = StateVector(4, "c128")
+    prog = Program.from_circuit(sv, c)
+    with pytest.raises(L.SvError) as ei:
+        prog.jacobian()
+    assert ei.value.status == 6
+    prog.set_params(p)
+    prog.jacobian()
 
 
 def test_error_status_for_bad_calls():
