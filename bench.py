@@ -43,6 +43,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--dtype", choices=["c128", "c64"], default="c128")
+    ap.add_argument("--qubits", type=int, default=N_QUBITS, help="smaller sizes are for profiling captures only")
+    ap.add_argument("--layers", type=int, default=LAYERS)
+    ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the complex64 and per-gate side measurements")
     return ap.parse_args()
@@ -113,7 +116,7 @@ def oracle_sample(sweep_steps: int = 6):
     Sample: the full forward pass (all 384 ops), lambda_j = Z_j psi for the 24
     observables, and `sweep_steps` steps of the adjoint sweep (each step: 24
     generator inner products and 25 un-applied vectors).  The full step is
-    estimated as forward + lambda + (sweep time per step) x (1152 sweep steps).
+    estimated as forward + lambda + (sweep time per step) x (768 sweep steps).
     """
     import oracle
     from workloads import strongly_entangling
@@ -188,11 +191,12 @@ def run_ours(args):
             dist.barrier()
 
     hbm_peak, peak_kind = peaks()
-    c, p = strongly_entangling(N_QUBITS, LAYERS)
+    NQ = args.qubits
+    c, p = strongly_entangling(NQ, args.layers)
     m, P = len(c.observables), c.n_params
 
     def measure(dtype, steps, warmup, timing):
-        sv = StateVector(N_QUBITS, dtype)
+        sv = StateVector(NQ, dtype)
         prog = Program.from_circuit(sv, c)
         params = torch.tensor(p, dtype=torch.float64, device="cuda")
         stream = torch.cuda.current_stream()
@@ -235,7 +239,7 @@ def run_ours(args):
             kt = L.sv_kernel_timing_read()
         fp, ap, _ = prog.stats()
         out = {"ms": ms, "launches": launches, "kt": kt, "clocks": clk, "fwd_passes": fp, "adj_passes": ap,
-               "J": J, "E": E, "vec_bytes": (16 if dtype == "c128" else 8) << N_QUBITS}
+               "J": J, "E": E, "vec_bytes": (16 if dtype == "c128" else 8) << NQ}
         prog.close()
         sv.close()
         del params
@@ -264,9 +268,9 @@ def run_ours(args):
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     e2e = None
-    if rank == 0 or True:
+    if not args.no_e2e:
         dt = L.SV_C128 if args.dtype == "c128" else L.SV_C64
-        h = L.sv_create(N_QUBITS, dt)
+        h = L.sv_create(NQ, dt)
         L.sv_set_stream(h, torch.cuda.current_stream().cuda_stream)
         tape, obs = L.Tape(c.ops, P), L.PauliSums(c.observables)
         pin = torch.tensor(p, dtype=torch.float64).pin_memory()
@@ -309,9 +313,11 @@ def run_ours(args):
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.dtype == "c128" else "f32",
                 "data": "synthetic",
-                "config": {"workload": WORKLOAD, "precision": args.dtype, "n_qubits": N_QUBITS, "layers": LAYERS,
+                "config": {"workload": WORKLOAD if (NQ, args.layers) == (N_QUBITS, LAYERS) else
+                           f"sel{NQ} ({args.layers} layers; reduced size for profiling)",
+                           "precision": args.dtype, "n_qubits": NQ, "layers": args.layers,
                            "n_params": P, "n_observables": m, "parallelism": "replicas" if world > 1 else "single",
-                           "l2": "inputs larger than L2: state 268 MB (c128) and 24 lambda vectors 6.4 GB per step",
+                           "l2": "inputs larger than L2 (129 MB): c128 state 268 MB and 24 lambda vectors 6.4 GB per step",
                            "forward_passes": main["fwd_passes"], "adjoint_passes": main["adj_passes"]},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": main["launches"],
                 "clocks": main["clocks"], "extras": extras}

@@ -169,8 +169,6 @@ struct HOp {
   int64_t msrc = 0;
   bool diag = false;
   bool train = false;   // adjoint plan: one angle bound to a parameter
-  int uslot = -1;       // offset of U in the matrix buffer
-  int gslot = -1;       // offset of G
 };
 
 sv_status validate_op(int n, const sv_op &op, int n_params, const double *matrices, int64_t n_mat,
@@ -278,16 +276,43 @@ void expand_op(const HOp &h, std::vector<HOp> &out) {
 
 // ---- planner -----------------------------------------------------------------
 struct Step {
-  int dense_k;  // 0: fused pass `index`; 1: dense k>4 op `index` (HOp index)
+  int dense_k;  // 0: fused pass `index`; 1: dense k>4 op `index` (dk_ops)
   int index;
 };
 
 struct Plan {
   std::vector<PassDev> passes;
-  std::vector<OpDev> ops;      // pass op tables, concatenated
+  std::vector<OpDev> ops;      // micro-op tables of all passes, concatenated
   std::vector<Step> steps;
-  std::vector<OpDev> dk_ops;   // one OpDev per dense_k step (global targets)
+  std::vector<OpDev> dk_ops;   // one op per dense_k step (global targets)
+  std::vector<int> train_hop;  // trainable slot -> HOp index (sweep order)
   int n_train = 0;
+};
+
+// Matrix-slot allocator shared by the forward and adjoint plans of a program.
+struct SlotTable {
+  std::vector<MatSlot> slots;
+  size_t entries = 0;
+  int add(const HOp &h, bool dagger, int mode, int a = 0, int b = 0) {
+    MatSlot m;
+    memset(&m, 0, sizeof(m));
+    m.kind = h.kind;
+    m.k = h.k;
+    m.dagger = dagger ? 1 : 0;
+    m.mode = mode;
+    m.a = a;
+    m.b = b;
+    m.out = (int)entries;
+    for (int q = 0; q < 3; ++q) {
+      m.pidx[q] = h.pidx[q];
+      m.cangle[q] = h.cang[q];
+    }
+    m.scale = h.scale;
+    m.src = h.msrc;
+    slots.push_back(m);
+    entries += mode == 0 ? (size_t)1 << (2 * h.k) : (mode == 1 ? (size_t)1 << h.k : 4);
+    return m.out;
+  }
 };
 
 int popc(uint64_t x) { return __builtin_popcountll(x); }
@@ -301,43 +326,15 @@ uint64_t fill_bits(uint64_t bits, int n, int T, int nlow_pref) {
 PassDev make_pass(int n, uint64_t bits) {
   PassDev p;
   memset(&p, 0, sizeof(p));
-  p.T = 0;
-  p.nhi = 0;
   for (int b = 0; b < n; ++b) {
     if (bits >> b & 1)
       p.pos[p.T++] = b;
     else
       p.hi[p.nhi++] = b;
   }
-  p.nlow = 0;
   while (p.nlow < p.T && p.pos[p.nlow] == p.nlow) ++p.nlow;
   p.max_k = 1;
   return p;
-}
-
-OpDev make_opdev(int n, const HOp &h, const PassDev *pass) {
-  OpDev o;
-  memset(&o, 0, sizeof(o));
-  o.cls = h.diag ? kDiag : kDense;
-  o.k = h.k;
-  for (int j = 0; j < h.k; ++j) {
-    const int gb = n - 1 - h.tw[j];
-    o.tg[j] = gb;
-    o.tl[j] = -1;
-    if (pass && !h.diag)
-      for (int i = 0; i < pass->T; ++i)
-        if (pass->pos[i] == gb) o.tl[j] = i;
-  }
-  for (int c = 0; c < h.nc; ++c) {
-    const uint64_t b = 1ull << (n - 1 - h.cw[c]);
-    o.cmask |= b;
-    if (h.cv[c]) o.cval |= b;
-  }
-  o.mat = h.uslot;
-  o.gen = h.train ? h.gslot : -1;
-  o.train = -1;
-  o.slot = -1;
-  return o;
 }
 
 uint64_t low_bits(int n, int T, int nlow_pref) {
@@ -346,12 +343,143 @@ uint64_t low_bits(int n, int T, int nlow_pref) {
   return b;
 }
 
-// Greedy order-preserving fusion (S4): ops join the current pass while the
+// Gate structure: the 2x2 blocks (member patterns a, b) of a non-diagonal gate,
+// each block's matrix code and its generator restricted to the block.
+struct Block {
+  int a, b;
+  int8_t code, gcode;
+  float gs;
+};
+
+bool gate_blocks(const HOp &h, std::vector<Block> &out) {
+  out.clear();
+  switch (h.kind) {
+    case SV_PAULI_X: out.push_back({0, 1, mSwap, gNone, 0}); return true;
+    case SV_PAULI_Y: out.push_back({0, 1, mY, gNone, 0}); return true;
+    case SV_HADAMARD: out.push_back({0, 1, mReal, gNone, 0}); return true;
+    case SV_RX: out.push_back({0, 1, mImOff, gX, 1}); return true;
+    case SV_RY: out.push_back({0, 1, mReal, gY, 1}); return true;
+    case SV_ROT: out.push_back({0, 1, mGen, gNone, 0}); return true;
+    case SV_SWAP: out.push_back({1, 2, mSwap, gNone, 0}); return true;
+    case SV_ISING_XX:
+      out.push_back({0, 3, mImOff, gX, 1});
+      out.push_back({1, 2, mImOff, gX, 1});
+      return true;
+    case SV_ISING_YY:
+      out.push_back({0, 3, mImOff, gX, -1});
+      out.push_back({1, 2, mImOff, gX, 1});
+      return true;
+    case SV_ISING_XY: out.push_back({1, 2, mImOff, gX, 2}); return true;
+    case SV_SINGLE_EXCITATION: out.push_back({1, 2, mReal, gY, 1}); return true;
+    case SV_DOUBLE_EXCITATION: out.push_back({3, 12, mReal, gY, 1}); return true;
+    case SV_MATRIX:
+      if (h.k == 1) {
+        out.push_back({0, 1, mGen, gNone, 0});
+        return true;
+      }
+      return false;  // dense block
+    default: return false;
+  }
+}
+
+// Diagonal generator restricted to the pattern: g = ga / gb by parity of pattern & zmask.
+void diag_generator(int kind, int &zmask, float &ga, float &gb) {
+  zmask = 1;
+  ga = 1.f;
+  gb = -1.f;
+  if (kind == SV_PHASE_SHIFT) {
+    ga = 0.f;
+    gb = 1.f;
+  } else if (kind == SV_ISING_ZZ) {
+    zmask = 3;
+  }
+}
+
+OpDev blank_op(int n, const HOp &h) {
+  OpDev o;
+  memset(&o, 0, sizeof(o));
+  o.k = (int8_t)h.k;
+  for (int j = 0; j < h.k; ++j) o.tg[j] = (int8_t)(n - 1 - h.tw[j]);
+  for (int c = 0; c < h.nc; ++c) {
+    const uint64_t b = 1ull << (n - 1 - h.cw[c]);
+    o.cmask |= b;
+    if (h.cv[c]) o.cval |= b;
+  }
+  o.train = -1;
+  o.slot = -1;
+  o.sync_prev = 1;
+  return o;
+}
+
+// Lower one gate into micro-ops inside a pass (dagger: store U^dagger blocks).
+void lower_gate(int n, const HOp &h, const PassDev &pd, bool dagger, int train, int slot, SlotTable &st,
+                std::vector<OpDev> &out) {
+  const bool eff_dagger = (h.adjoint != 0) != dagger;
+  OpDev base = blank_op(n, h);
+  base.train = h.train ? train : -1;
+  base.slot = h.train ? slot : -1;
+  if (h.diag) {
+    OpDev o = base;
+    o.kind = kDiag;
+    o.code = (h.kind == SV_PAULI_Z) ? dNeg : dGen;
+    if (o.code == dGen) o.mat = st.add(h, eff_dagger, 1);
+    if (h.train) {
+      o.gcode = gDiag;
+      diag_generator(h.kind, o.zmask, o.ga, o.gb);
+    }
+    out.push_back(o);
+    return;
+  }
+  int tl[kMaxTargets];
+  for (int j = 0; j < h.k; ++j) {
+    tl[j] = -1;
+    for (int i = 0; i < pd.T; ++i)
+      if (pd.pos[i] == n - 1 - h.tw[j]) tl[j] = i;
+  }
+  int ts[4] = {0, 0, 0, 0};
+  for (int j = 0; j < h.k && j < 4; ++j) ts[j] = tl[j];
+  std::sort(ts, ts + std::min(h.k, 4));
+  std::vector<Block> blocks;
+  if (gate_blocks(h, blocks)) {
+    bool first = true;
+    for (const Block &bl : blocks) {
+      OpDev o = base;
+      o.kind = kPair;
+      o.code = bl.code;
+      for (int j = 0; j < 4; ++j) o.ts[j] = (int8_t)ts[j];
+      for (int j = 0; j < h.k; ++j) o.tl[j] = (int8_t)tl[j];
+      o.oa = o.ob = 0;
+      for (int j = 0; j < h.k; ++j) {
+        if ((bl.a >> (h.k - 1 - j)) & 1) o.oa += 1 << tl[j];
+        if ((bl.b >> (h.k - 1 - j)) & 1) o.ob += 1 << tl[j];
+      }
+      if (bl.code == mGen || bl.code == mReal || bl.code == mImOff) o.mat = st.add(h, eff_dagger, 2, bl.a, bl.b);
+      if (h.train) {
+        o.gcode = bl.gcode;
+        o.gs = bl.gs;
+      }
+      o.sync_prev = first ? 1 : 0;  // blocks of one gate are disjoint
+      first = false;
+      out.push_back(o);
+    }
+    return;
+  }
+  OpDev o = base;  // dense user block on 2-4 local wires
+  o.kind = kDense;
+  for (int j = 0; j < 4; ++j) o.ts[j] = (int8_t)ts[j];
+  for (int j = 0; j < h.k; ++j) o.tl[j] = (int8_t)tl[j];
+  o.mat = st.add(h, eff_dagger, 0);
+  out.push_back(o);
+}
+
+// Greedy order-preserving fusion (S4): gates join the current pass while the
 // union of the local bits they need (non-diagonal targets) plus the lowest
 // index bits fits in T bits.  The lowest bits are always local, so every tile
 // is read as runs of >= 2^nlow_pref consecutive amplitudes (coalesced, and
-// 16-byte aligned for the paired complex64 accesses).
-Plan plan_passes(int n, const std::vector<HOp> &ops, int Tmax, int nlow_pref, int max_train) {
+// 16-byte aligned for the paired complex64 accesses).  Each pass is then
+// lowered into micro-ops; dagger selects the adjoint sweep's U^dagger blocks.
+Plan plan_passes(int n, const std::vector<HOp> &ops, int Tmax, int nlow_pref, int max_train, bool dagger,
+                 SlotTable &st) {
   Plan P;
   const int T = std::min(Tmax, n);
   const uint64_t low = low_bits(n, T, nlow_pref);
@@ -364,14 +492,24 @@ Plan plan_passes(int n, const std::vector<HOp> &ops, int Tmax, int nlow_pref, in
     pd.op_begin = (int)P.ops.size();
     pd.train_base = P.n_train;
     int t = 0;
+    bool prev_diag = false;
     for (int i : cur_ops) {
-      OpDev o = make_opdev(n, ops[i], &pd);
-      if (ops[i].train) {
-        o.train = t++;
-        o.slot = P.n_train++;
+      const HOp &h = ops[i];
+      const size_t before = P.ops.size();
+      const int slot = h.train ? P.n_train : -1;
+      lower_gate(n, h, pd, dagger, t, slot, st, P.ops);
+      if (h.train) {
+        ++t;
+        ++P.n_train;
+        P.train_hop.push_back(i);
       }
-      if (o.cls == kDense) pd.max_k = std::max(pd.max_k, o.k);
-      P.ops.push_back(o);
+      if (P.ops.size() > before) {
+        OpDev &first = P.ops[before];
+        if (first.kind == kDiag && prev_diag) first.sync_prev = 0;  // same thread-to-amplitude map
+        prev_diag = P.ops.back().kind == kDiag;
+      }
+      for (size_t q = before; q < P.ops.size(); ++q)
+        if (P.ops[q].kind == kDense) pd.max_k = std::max(pd.max_k, (int)P.ops[q].k);
     }
     pd.op_end = (int)P.ops.size();
     pd.n_train = t;
@@ -383,9 +521,12 @@ Plan plan_passes(int n, const std::vector<HOp> &ops, int Tmax, int nlow_pref, in
   };
   for (int i = 0; i < (int)ops.size(); ++i) {
     const HOp &h = ops[i];
+    if (h.kind == SV_IDENTITY) continue;
     if (!h.diag && h.k > kMaxTileTargets) {
       flush();
-      OpDev o = make_opdev(n, h, nullptr);
+      OpDev o = blank_op(n, h);
+      o.kind = kDense;
+      o.mat = st.add(h, (h.adjoint != 0) != dagger, 0);
       P.steps.push_back({1, (int)P.dk_ops.size()});
       P.dk_ops.push_back(o);
       continue;
@@ -403,24 +544,28 @@ Plan plan_passes(int n, const std::vector<HOp> &ops, int Tmax, int nlow_pref, in
   return P;
 }
 
-// Host-side check of a plan before anything is launched: every dense target is
-// a distinct local bit, tiles are at most kMaxLocalBits wide and their low run
-// covers the 16-byte pair accesses.
+// Host-side check of a plan before anything is launched: every non-diagonal
+// target is a distinct local bit, pair members lie in the tile, tiles are at
+// most kMaxLocalBits wide and their low run covers the 16-byte pair accesses.
 sv_status check_plan(const Plan &P, int n, int nlow_pref) {
   for (const PassDev &pd : P.passes) {
     if (pd.T < 1 || pd.T > kMaxLocalBits || pd.T + pd.nhi != n)
       return fail(SV_ERR_UNSUPPORTED, "internal planner error: tile of %d bits", pd.T);
     if (pd.nlow < std::min(std::min(nlow_pref, n), pd.T))
       return fail(SV_ERR_UNSUPPORTED, "internal planner error: low run of %d bits", pd.nlow);
+    if (pd.n_train > kMaxTrainPerPass) return fail(SV_ERR_UNSUPPORTED, "internal planner error: trainable ops");
     for (int o = pd.op_begin; o < pd.op_end; ++o) {
       const OpDev &op = P.ops[o];
-      if (op.cls != kDense) continue;
+      if (op.kind == kDiag) continue;
       if (op.k > kMaxTileTargets) return fail(SV_ERR_UNSUPPORTED, "internal planner error: wide op in a tile");
       for (int j = 0; j < op.k; ++j) {
         if (op.tl[j] < 0 || op.tl[j] >= pd.T) return fail(SV_ERR_UNSUPPORTED, "internal planner error: non-local target");
         for (int q = 0; q < j; ++q)
           if (op.tl[q] == op.tl[j]) return fail(SV_ERR_UNSUPPORTED, "internal planner error: repeated target");
+        if (j > 0 && op.ts[j] <= op.ts[j - 1]) return fail(SV_ERR_UNSUPPORTED, "internal planner error: target order");
       }
+      if (op.kind == kPair && (op.oa < 0 || op.ob < 0 || op.oa >= (1 << pd.T) || op.ob >= (1 << pd.T) || op.oa == op.ob))
+        return fail(SV_ERR_UNSUPPORTED, "internal planner error: pair members");
     }
   }
   return SV_OK;
@@ -547,7 +692,6 @@ const Ops &ops_for(sv_dtype dt) {
   return dt == SV_C64 ? f32 : f64;
 }
 
-constexpr int kMaxTrainPerPass = 64;
 
 }  // namespace
 
@@ -644,7 +788,11 @@ struct sv_program {
   int grid_f = 1, grid_e = 1;
   int ctas_a = 1, ctas_l = 1;        // CTAs per adjoint / lambda launch (split over lambdas)
   uint64_t tiles_a = 1, tiles_l = 1; // tiles per vector in those passes
-  int grid_a(int mcc) const { return (int)std::max<uint64_t>(1, std::min<uint64_t>(tiles_a, ctas_a / std::max(1, mcc))); }
+  int lam_per_cta = 1;               // lambdas sharing one phi tile in the adjoint kernel
+  int groups_a(int mcc) const { return (mcc + lam_per_cta - 1) / lam_per_cta; }
+  int grid_a(int mcc) const {
+    return (int)std::max<uint64_t>(1, std::min<uint64_t>(tiles_a, ctas_a / std::max(1, groups_a(mcc))));
+  }
   int grid_l(int mcc) const { return (int)std::max<uint64_t>(1, std::min<uint64_t>(tiles_l, ctas_l / std::max(1, mcc))); }
   int launches = 0;
   bool params_set = false;  // gate matrices built at least once
@@ -699,49 +847,16 @@ sv_status build_program(sv_state *s, const sv_tape *tape, const sv_pauli_sum *ob
   p->owns_tables = !one_shot;
   p->terms = terms;
 
-  // host ops and matrix slots
+  // host ops, fused passes lowered to micro-ops, and their matrix slots
   std::vector<HOp> fops, aops;
-  std::vector<MatSlot> slots;
-  size_t off = 0;
-  auto add_slot = [&](const HOp &h, int what) -> int {
-    MatSlot m;
-    memset(&m, 0, sizeof(m));
-    m.kind = h.kind;
-    m.k = h.k;
-    m.adjoint = h.adjoint;
-    m.diag = h.diag ? 1 : 0;
-    m.what = what;
-    m.out = (int)off;
-    for (int a = 0; a < 3; ++a) {
-      m.pidx[a] = h.pidx[a];
-      m.cangle[a] = h.cang[a];
-    }
-    m.scale = h.scale;
-    m.src = h.msrc;
-    slots.push_back(m);
-    off += h.diag ? (size_t)1 << h.k : (size_t)1 << (2 * h.k);
-    return m.out;
-  };
   for (int i = 0; i < n_ops; ++i) {
     HOp h = to_hop(ops[i], umats);
-    h.uslot = add_slot(h, 0);
     fops.push_back(h);
-    std::vector<HOp> ex;
-    expand_op(h, ex);
-    for (HOp &e : ex) {
-      if (e.kind == h.kind)
-        e.uslot = h.uslot;
-      else
-        e.uslot = add_slot(e, 0);
-      if (e.train) e.gslot = add_slot(e, 1);
-      aops.push_back(e);
-    }
+    expand_op(h, aops);
   }
-  p->n_slots = (int)slots.size();
-  p->mats_entries = off;
-
-  p->fwd = plan_passes(n, fops, K.Tf, K.nlow_pref, 1 << 30);
-  p->adj = plan_passes(n, aops, K.Ta, K.nlow_pref, kMaxTrainPerPass);
+  SlotTable st_tab;
+  p->fwd = plan_passes(n, fops, K.Tf, K.nlow_pref, 1 << 30, false, st_tab);
+  p->adj = plan_passes(n, aops, K.Ta, K.nlow_pref, kMaxTrainPerPass, true, st_tab);
   if (sv_status st = check_plan(p->fwd, n, K.nlow_pref)) {
     destroy_program(p);
     return st;
@@ -750,30 +865,19 @@ sv_status build_program(sv_state *s, const sv_tape *tape, const sv_pauli_sum *ob
     destroy_program(p);
     return st;
   }
+  std::vector<MatSlot> &slots = st_tab.slots;
+  const size_t off = st_tab.entries;
+  p->n_slots = (int)slots.size();
+  p->mats_entries = off;
 
-  // trainable slots (sweep order = adjoint plan order) -> coefficient and parameter CSR
-  std::vector<int> slot_param;
-  {
-    std::vector<double> coef;
-    // walk the adjoint passes' ops in order; OpDev.slot was assigned in that order
-    std::vector<std::pair<int, int>> hop_of_slot;  // slot -> aops index
-    int ai = 0;
-    for (const Step &st : p->adj.steps) {
-      (void)st;
-    }
-    // aops order equals op-table order (plan_passes keeps op order); recover per slot
-    coef.resize(p->adj.n_train);
-    slot_param.resize(p->adj.n_train);
-    int slot = 0;
-    for (ai = 0; ai < (int)aops.size(); ++ai) {
-      const HOp &e = aops[ai];
-      if (!e.train) continue;
-      const double s_eff = e.adjoint ? -kind_gen_s(e.kind) : kind_gen_s(e.kind);
-      coef[slot] = e.scale * (-2.0 * s_eff);
-      slot_param[slot] = e.pidx[0];
-      ++slot;
-    }
-    p->coef = coef;
+  // trainable slots (sweep order) -> coefficient scale * (-2 s_eff) and parameter CSR
+  std::vector<int> slot_param(p->adj.n_train);
+  p->coef.assign(p->adj.n_train, 0.0);
+  for (int sidx = 0; sidx < p->adj.n_train; ++sidx) {
+    const HOp &e = aops[p->adj.train_hop[sidx]];
+    const double s_eff = e.adjoint ? -kind_gen_s(e.kind) : kind_gen_s(e.kind);
+    p->coef[sidx] = e.scale * (-2.0 * s_eff);
+    slot_param[sidx] = e.pidx[0];
   }
   std::vector<int32_t> pbegin(n_params + 1, 0), pslots;
   for (int sidx = 0; sidx < (int)slot_param.size(); ++sidx) pbegin[slot_param[sidx] + 1]++;
@@ -862,7 +966,12 @@ sv_status build_program(sv_state *s, const sv_tape *tape, const sv_pauli_sum *ob
     p->grid_f = std::max(1, std::min((int)std::min<uint64_t>(1ull << (n - tmax), 1 << 30),
                                      2 * sms * blocks_per_sm((K.amp_bytes << tmax) + 4096)));
     int ta = std::min(K.Ta, n);
-    p->ctas_a = 2 * sms * blocks_per_sm(2 * (K.amp_bytes << ta) + 8192);
+    const int tile_b = K.amp_bytes << ta;
+    const int budget = 112 * 1024 - tile_b - (8 << ta);
+    p->lam_per_cta = std::max(1, std::min({kMaxLambdaPerCta, std::max(1, mc),
+                                            budget / (tile_b + kMaxTrainPerPass * 8 * (kBlock / 32))}));
+    const int smem_a = tile_b * (1 + p->lam_per_cta) + (8 << ta) + kMaxTrainPerPass * 8 * (kBlock / 32) * p->lam_per_cta;
+    p->ctas_a = 2 * sms * blocks_per_sm(smem_a);
     p->tiles_a = 1ull << (n - ta);
     p->grid_e = std::max(1, std::min((int)std::min<uint64_t>(1ull << (n - tmax), 1 << 30),
                                      sms * blocks_per_sm((K.amp_bytes << tmax) + 4096 + 32768)));
@@ -1007,7 +1116,10 @@ sv_status jac_workspace(sv_program *p, JacWs &w) {
   size_t max_terms = 1;
   for (size_t q = 0; q + 1 < p->tp.begin.size(); ++q)
     max_terms = std::max<size_t>(max_terms, p->tp.begin[q + 1] - p->tp.begin[q]);
-  const size_t part = std::max((size_t)(p->ctas_a + p->mc) * max_train, (size_t)p->grid_e * max_terms);
+  size_t lam_rows = 1;
+  for (int mcc : {p->mc, p->m % std::max(1, p->mc), 1})
+    if (mcc > 0) lam_rows = std::max(lam_rows, (size_t)p->grid_a(mcc) * mcc);
+  const size_t part = std::max(lam_rows * max_train, (size_t)p->grid_e * max_terms);
   const bool need_vec = p->adj.n_train > 0 || !p->adj.dk_ops.empty();
   const size_t bytes = (need_vec ? 2 * V + (size_t)p->mc * V : 0) + align256(part * 8) +
                        align256((size_t)std::max(1, p->adj.n_train) * std::max(1, p->m) * 8) +
@@ -1083,12 +1195,13 @@ sv_status run_sweep(sv_program *p, const JacWs &w, int mcc, int j0, int ldc, con
     if (sv_status r = after_launch(s, e, "lambda pass")) return r;
     ++p->launches;
   }
-  // phi starts as psi (read only); with one lambda later passes update phi in place.
+  // phi starts as psi (read only); with one lambda group later passes update phi in place.
   const void *phi_in = s->psi;
   char *phi_out = w.phiA;
+  const bool in_place = p->groups_a(mcc) == 1;
   auto advance = [&]() {
     phi_in = phi_out;
-    if (mcc > 1) phi_out = (phi_out == w.phiA) ? w.phiB : w.phiA;
+    if (!in_place) phi_out = (phi_out == w.phiA) ? w.phiB : w.phiA;
   };
   for (int si = (int)p->adj.steps.size() - 1; si >= 0; --si) {
     const Step &st = p->adj.steps[si];
@@ -1110,7 +1223,8 @@ sv_status run_sweep(sv_program *p, const JacWs &w, int mcc, int j0, int ldc, con
     cudaError_t e;
     {
       LaunchTimer t(s->stream, 1);
-      e = K.tile_adjoint(phi_in, phi_out, w.lam, n, mcc, pd, p->d_adj_ops, p->d_mats, w.partials, nb, s->stream);
+      e = K.tile_adjoint(phi_in, phi_out, w.lam, n, mcc, p->lam_per_cta, pd, p->d_adj_ops, p->d_mats, w.partials, nb,
+                         s->stream);
     }
     if (sv_status r = after_launch(s, e, "adjoint pass")) return r;
     ++p->launches;
@@ -1572,8 +1686,9 @@ sv_status sv_plan_query(int n, sv_dtype dtype, const sv_tape *tape, int *n_forwa
     fops.push_back(h);
     expand_op(h, aops);
   }
-  Plan f = plan_passes(n, fops, K.Tf, K.nlow_pref, 1 << 30);
-  Plan a = plan_passes(n, aops, K.Ta, K.nlow_pref, kMaxTrainPerPass);
+  SlotTable st_tab;
+  Plan f = plan_passes(n, fops, K.Tf, K.nlow_pref, 1 << 30, false, st_tab);
+  Plan a = plan_passes(n, aops, K.Ta, K.nlow_pref, kMaxTrainPerPass, true, st_tab);
   if (sv_status st = check_plan(f, n, K.nlow_pref)) return st;
   if (sv_status st = check_plan(a, n, K.nlow_pref)) return st;
   if (n_forward_passes) *n_forward_passes = (int)f.steps.size();

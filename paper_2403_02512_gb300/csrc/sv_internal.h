@@ -16,26 +16,47 @@ constexpr int kMaxTargets = 6;      // dense ops inside a tile: k <= 4; dense_k 
 constexpr int kMaxTileTargets = 4;
 constexpr int kMaxQubits = 34;
 constexpr int kBlock = 256;         // threads per CTA in the tile kernels
+constexpr int kMaxLambdaPerCta = 8; // lambdas sharing one phi tile in the adjoint kernel
+constexpr int kMaxTrainPerPass = 32;
 
-// Op classes inside a pass.
-enum OpClass : int32_t {
-  kDense = 0,  // 2^k x 2^k matrix on k local target bits
-  kDiag = 1,   // 2^k diagonal on k target bits anywhere in the index
+// Micro-op kinds.  Every structured gate is a set of independent 2x2 blocks on
+// amplitude pairs (kPair: e.g. IsingXX = blocks on |00>,|11> and |01>,|10>;
+// DoubleExcitation = one block on |0011>,|1100>), or a diagonal (kDiag), or,
+// for a user matrix on 2-4 wires, a dense block (kDense).
+enum OpKind : int8_t { kPair = 0, kDiag = 1, kDense = 2 };
+// 2x2 block structure (of the stored, already adjoint-resolved block).
+enum MatCode : int8_t {
+  mGen = 0,    // general complex
+  mReal = 1,   // real entries (RY, Hadamard, Givens rotations)
+  mImOff = 2,  // real diagonal, imaginary off-diagonal (RX, IsingXX/YY/XY blocks)
+  mSwap = 3,   // [[0,1],[1,0]] (PauliX, CNOT target, SWAP block)
+  mY = 4       // [[0,-i],[i,0]]
+};
+enum DiagCode : int8_t { dGen = 0, dNeg = 1 /* -1 on the all-ones pattern (Z, CZ) */ };
+// Generator block of a trainable op, restricted to the op's pair or diagonal.
+enum GenCode : int8_t {
+  gNone = 0,
+  gX = 1,    // gs * [[0,1],[1,0]] on the pair
+  gY = 2,    // gs * [[0,-i],[i,0]] on the pair
+  gDiag = 3  // g = ga (even) / gb (odd) by the parity of pattern & zmask
 };
 
-// One op of one pass.  Matrices live in the program's matrix buffer, indexed in
-// complex entries of the state's precision.
+// One micro-op of one pass.
 struct OpDev {
-  int32_t cls;
-  int32_t k;
-  int32_t tl[kMaxTargets];  // kDense: local bit of target j (j = 0 is the op's local MSB)
-  int32_t tg[kMaxTargets];  // kDiag:  global bit of target j
-  uint64_t cmask;           // control bits (global)
-  uint64_t cval;            // required values of the control bits
-  int32_t mat;              // U: 4^k (dense) or 2^k (diag) entries
-  int32_t gen;              // generator G (same shape as U) or -1
-  int32_t train;            // index among the pass's trainable ops, or -1
-  int32_t slot;             // contribution slot (expanded-op index), or -1
+  int8_t kind, code, gcode, k;
+  int8_t ts[4];          // kPair / kDense: local target bits, ascending
+  int8_t tl[4];          // kDense: local bit of target j (j = 0 is the op's local MSB)
+  int8_t tg[kMaxTargets];// kDiag / dense_k: global bit of target j
+  int8_t sync_prev;      // barrier needed between the previous micro-op and this one
+  int8_t pad0;
+  int32_t oa, ob;        // kPair: local offsets of the two members within a group
+  int32_t zmask;         // gDiag: target-pattern bits whose parity selects gb
+  int32_t train;         // trainable index within the pass, or -1
+  int32_t mat;           // matrix entries: kPair 4 (2x2 block), kDiag 2^k, kDense / dense_k 4^k
+  int32_t slot;          // global trainable slot, or -1
+  float gs, ga, gb;
+  int32_t pad1;
+  uint64_t cmask, cval;  // control bits (global) and their required values
 };
 
 // One fused pass: a tile is the set of 2^T amplitudes that share every index
@@ -49,7 +70,7 @@ struct PassDev {
   int32_t op_begin, op_end;        // ops [op_begin, op_end) of the program's op table
   int32_t n_train;                 // trainable ops in this pass
   int32_t train_base;              // row of the first trainable op in the pass's partial block
-  int32_t max_k;                   // widest dense op in the pass (selects the kernel variant)
+  int32_t max_k;                   // widest kDense op in the pass (selects the kernel variant)
 };
 
 // One Pauli term placed in an expectation / lambda pass.
@@ -62,16 +83,18 @@ struct TermDev {
   double coeff;
 };
 
-// Gate-matrix slot built on the device from the parameter vector.
+// Gate-matrix slot built on the device from the parameter vector: the op's
+// matrix E = U, or U^dagger when `dagger` (op's own adjoint flag XOR the
+// adjoint sweep), written whole (mode 0), as its diagonal (1) or as the 2x2
+// block on members (a, b) (2).
 struct MatSlot {
   int32_t kind;        // sv_op_kind
   int32_t k;
-  int32_t adjoint;
-  int32_t diag;        // write the 2^k diagonal only
-  int32_t what;        // 0 = U, 1 = generator G
+  int32_t dagger;
+  int32_t mode;
+  int32_t a, b;
   int32_t out;         // offset (complex entries) in the matrix buffer
   int32_t pidx[3];
-  int32_t pad;
   double scale;
   double cangle[3];
   int64_t src;         // SV_MATRIX: offset (complex entries) of the user matrix
@@ -86,7 +109,8 @@ struct Launch {
                                     const double *user_mats, void *mats, cudaStream_t st);
   static cudaError_t tile_forward(void *psi, int n, const PassDev &pass, const OpDev *ops,
                                   const void *mats, int grid, cudaStream_t st);
-  static cudaError_t tile_adjoint(const void *phi_in, void *phi_out, void *lam, int n, int m,
+  // m lambdas, b of them per CTA (grid.x = ceil(m / b) lambda groups).
+  static cudaError_t tile_adjoint(const void *phi_in, void *phi_out, void *lam, int n, int m, int b,
                                   const PassDev &pass, const OpDev *ops, const void *mats,
                                   double *partials, int grid, cudaStream_t st);
   static cudaError_t expval_pass(const void *psi, int n, const PassDev &pass, const TermDev *terms,

@@ -64,24 +64,48 @@ __device__ __forceinline__ void two_sum(R a, R b, R &s, R &e) {
   e = (a - (s - bb)) + (b - bb);
 }
 
-// Compensated per-thread accumulator: FP32 with a running error term for
-// complex64 states, plain FP64 for complex128 states.  Converted to FP64 for
-// every reduction across threads.
+// Per-thread partial sum inside one tile: FP32 for complex64 states (a
+// handful of terms), FP64 for complex128.  Tile partials are combined across
+// warps and tiles in compensated form (see WarpAcc).
 template <typename R>
 struct Acc {
-  R s = R(0), c = R(0);
-  __device__ __forceinline__ void add(R v) {
-    if constexpr (std::is_same<R, float>::value) {
-      R t, e;
-      two_sum(s, v, t, e);
-      s = t;
-      c += e;
-    } else {
-      s += v;
-    }
-  }
-  __device__ __forceinline__ double value() const { return double(s) + double(c); }
+  R s = R(0);
+  __device__ __forceinline__ void add(R v) { s += v; }
+  __device__ __forceinline__ R value() const { return s; }
 };
+
+// Per-warp accumulator slot in shared memory, summed over tiles: a
+// double-float pair (hi, lo) updated with TwoSum for complex64 (no FP64
+// instruction in the hot loop), a plain double for complex128.
+template <typename R>
+struct WarpAcc;
+template <>
+struct WarpAcc<float> {
+  static __device__ __forceinline__ void add(double *slot, float v) {
+    float2 *p = reinterpret_cast<float2 *>(slot);
+    float2 a = *p;
+    float s, e;
+    two_sum(a.x, v, s, e);
+    a.y += e;
+    a.x = s;
+    *p = a;
+  }
+  static __device__ __forceinline__ double read(const double *slot) {
+    const float2 a = *reinterpret_cast<const float2 *>(slot);
+    return (double)a.x + (double)a.y;
+  }
+};
+template <>
+struct WarpAcc<double> {
+  static __device__ __forceinline__ void add(double *slot, double v) { *slot += v; }
+  static __device__ __forceinline__ double read(const double *slot) { return *slot; }
+};
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -163,25 +187,158 @@ __device__ __forceinline__ void store_tile(c_t<R> *g, const c_t<R> *s, const Til
 }
 
 // ---------------------------------------------------------------------------
-// Op application inside a tile
+// Micro-op application inside a tile
 // ---------------------------------------------------------------------------
+// First member of group g of a k-target micro-op: g with a zero inserted at
+// every target bit (Alg. 1 / Alg. 2 enumeration, on local bits).
+__device__ __forceinline__ int group_base(const OpDev &op, int g) {
+  int l = g;
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+    if (j < op.k) l = insert_zero(l, op.ts[j]);
+  return l;
+}
+
+// (va, vb) <- E (va, vb) for a 2x2 block E stored row-major in M.
+template <typename R>
+__device__ __forceinline__ void pair_apply(int code, const c_t<R> *M, c_t<R> &va, c_t<R> &vb) {
+  using C = c_t<R>;
+  C na, nb;
+  switch (code) {
+    case mSwap:
+      na = vb;
+      nb = va;
+      break;
+    case mY:
+      na.x = vb.y;
+      na.y = -vb.x;
+      nb.x = -va.y;
+      nb.y = va.x;
+      break;
+    case mReal: {
+      const R m00 = M[0].x, m01 = M[1].x, m10 = M[2].x, m11 = M[3].x;
+      na.x = fma(m00, va.x, m01 * vb.x);
+      na.y = fma(m00, va.y, m01 * vb.y);
+      nb.x = fma(m10, va.x, m11 * vb.x);
+      nb.y = fma(m10, va.y, m11 * vb.y);
+      break;
+    }
+    case mImOff: {
+      const R d0 = M[0].x, o01 = M[1].y, o10 = M[2].y, d1 = M[3].x;
+      na.x = fma(d0, va.x, -o01 * vb.y);
+      na.y = fma(d0, va.y, o01 * vb.x);
+      nb.x = fma(d1, vb.x, -o10 * va.y);
+      nb.y = fma(d1, vb.y, o10 * va.x);
+      break;
+    }
+    default: {
+      na.x = R(0);
+      na.y = R(0);
+      nb = na;
+      na = cmac(cmac(na, M[0], va), M[1], vb);
+      nb = cmac(cmac(nb, M[2], va), M[3], vb);
+      break;
+    }
+  }
+  va = na;
+  vb = nb;
+}
+
+// Im(conj(x) y) and Re(conj(x) y)
+template <typename C>
+__device__ __forceinline__ auto im_cx(C x, C y) -> decltype(x.x) { return x.x * y.y - x.y * y.x; }
+template <typename C>
+__device__ __forceinline__ auto re_cx(C x, C y) -> decltype(x.x) { return x.x * y.x + x.y * y.y; }
+
+// Im <l | G p> over one pair for the generator codes gX / gY.
+template <typename R>
+__device__ __forceinline__ R pair_ip(int gcode, R gs, c_t<R> pa, c_t<R> pb, c_t<R> la, c_t<R> lb) {
+  if (gcode == gX) return gs * (im_cx(la, pb) + im_cx(lb, pa));
+  return gs * (re_cx(lb, pa) - re_cx(la, pb));  // gY: (G p)_a = -i gs pb, (G p)_b = i gs pa
+}
+
+__device__ __forceinline__ int diag_index(const OpDev &op, uint64_t g) {
+  int idx = 0;
+  for (int j = 0; j < op.k; ++j) idx = (idx << 1) | (int)((g >> op.tg[j]) & 1);
+  return idx;
+}
+
+template <typename R>
+__device__ __forceinline__ c_t<R> diag_mul(const OpDev &op, const c_t<R> *__restrict__ mats, int idx, c_t<R> v) {
+  if (op.code == dNeg) {
+    if (idx == (1 << op.k) - 1) {
+      v.x = -v.x;
+      v.y = -v.y;
+    }
+    return v;
+  }
+  return cmul(v, mats[op.mat + idx]);
+}
+
+template <typename R, int CODE>
+__device__ void fwd_pair_t(c_t<R> *s, const TileGeom &tg, const OpDev &op, const c_t<R> *__restrict__ mats) {
+  using C = c_t<R>;
+  const C *M = mats + op.mat;
+  C Mr[4];
+  if (CODE == mGen || CODE == mReal || CODE == mImOff)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) Mr[q] = M[q];
+  const int ng = tg.A >> op.k;
+  const bool ctl = op.cmask != 0;
+  for (int g = threadIdx.x; g < ng; g += blockDim.x) {
+    const int l0 = group_base(op, g);
+    if (ctl && ((tg.gidx(l0) & op.cmask) != op.cval)) continue;
+    C va = s[l0 + op.oa], vb = s[l0 + op.ob];
+    pair_apply<R>(CODE, Mr, va, vb);
+    s[l0 + op.oa] = va;
+    s[l0 + op.ob] = vb;
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ void fwd_pair(c_t<R> *s, const TileGeom &tg, const OpDev &op, const c_t<R> *mats) {
+  switch (op.code) {
+    case mSwap: fwd_pair_t<R, mSwap>(s, tg, op, mats); break;
+    case mY: fwd_pair_t<R, mY>(s, tg, op, mats); break;
+    case mReal: fwd_pair_t<R, mReal>(s, tg, op, mats); break;
+    case mImOff: fwd_pair_t<R, mImOff>(s, tg, op, mats); break;
+    default: fwd_pair_t<R, mGen>(s, tg, op, mats); break;
+  }
+}
+
+template <typename R>
+__device__ void fwd_diag(c_t<R> *s, const TileGeom &tg, const OpDev &op, const c_t<R> *__restrict__ mats) {
+  using C = c_t<R>;
+  if (op.k <= 2 && op.code == dGen) {
+    C d[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) d[q] = q < (1 << op.k) ? mats[op.mat + q] : C();
+    const int b0 = op.tg[0], b1 = op.k == 2 ? op.tg[1] : 0;
+    const bool two = op.k == 2;
+    for (int l = threadIdx.x; l < tg.A; l += blockDim.x) {
+      const uint64_t g = tg.gidx(l);
+      if ((g & op.cmask) != op.cval) continue;
+      const int idx = two ? (int)(((g >> b0) & 1) << 1 | ((g >> b1) & 1)) : (int)((g >> b0) & 1);
+      C dv = d[0];
+#pragma unroll
+      for (int q = 1; q < 4; ++q)
+        if (idx == q) dv = d[q];
+      s[l] = cmul(s[l], dv);
+    }
+    return;
+  }
+  for (int l = threadIdx.x; l < tg.A; l += blockDim.x) {
+    const uint64_t g = tg.gidx(l);
+    if ((g & op.cmask) != op.cval) continue;
+    s[l] = diag_mul<R>(op, mats, diag_index(op, g), s[l]);
+  }
+}
+
+// Dense 2^K x 2^K block of a user matrix (not trainable), inputs in registers.
 template <int K>
 struct GroupIdx {
-  int sorted[K];
   int offs[1 << K];
   __device__ __forceinline__ void init(const OpDev &op) {
-#pragma unroll
-    for (int j = 0; j < K; ++j) sorted[j] = op.tl[j];
-    // insertion sort (K <= 4)
-#pragma unroll
-    for (int i = 1; i < K; ++i)
-#pragma unroll
-      for (int j = i; j > 0; --j)
-        if (sorted[j - 1] > sorted[j]) {
-          int t = sorted[j];
-          sorted[j] = sorted[j - 1];
-          sorted[j - 1] = t;
-        }
 #pragma unroll
     for (int r = 0; r < (1 << K); ++r) {
       int o = 0;
@@ -191,36 +348,22 @@ struct GroupIdx {
       offs[r] = o;
     }
   }
-  __device__ __forceinline__ int first(int g) const {
-    int l = g;
-#pragma unroll
-    for (int j = 0; j < K; ++j) l = insert_zero(l, sorted[j]);
-    return l;
-  }
 };
 
-// Row r of M v (dagger: of M^dagger v), M row-major 2^K x 2^K.
 template <typename R, int K>
-__device__ __forceinline__ c_t<R> matrow(const c_t<R> (&v)[1 << K], const c_t<R> *__restrict__ M, int r,
-                                         bool dagger) {
+__device__ __forceinline__ c_t<R> matrow(const c_t<R> (&v)[1 << K], const c_t<R> *__restrict__ M, int r) {
   using C = c_t<R>;
   constexpr int D = 1 << K;
   C acc;
   acc.x = R(0);
   acc.y = R(0);
 #pragma unroll
-  for (int c = 0; c < D; ++c) {
-    const C m = dagger ? cconj(M[c * D + r]) : M[r * D + c];
-    acc = cmac(acc, m, v[c]);
-  }
+  for (int c = 0; c < D; ++c) acc = cmac(acc, M[r * D + c], v[c]);
   return acc;
 }
 
-// Apply M (or M^dagger) to every control-matching group of a tile.  The group's
-// inputs are held in registers; outputs go straight back to shared memory.
 template <typename R, int K>
-__device__ void apply_dense_tile(c_t<R> *s, const TileGeom &tg, const OpDev &op,
-                                 const c_t<R> *__restrict__ mats, bool dagger) {
+__device__ void dense_vec(c_t<R> *s, const TileGeom &tg, const OpDev &op, const c_t<R> *__restrict__ mats) {
   using C = c_t<R>;
   constexpr int D = 1 << K;
   GroupIdx<K> gi;
@@ -228,64 +371,42 @@ __device__ void apply_dense_tile(c_t<R> *s, const TileGeom &tg, const OpDev &op,
   const C *M = mats + op.mat;
   const int ng = tg.A >> K;
   for (int g = threadIdx.x; g < ng; g += blockDim.x) {
-    const int l0 = gi.first(g);
+    const int l0 = group_base(op, g);
     if (op.cmask && ((tg.gidx(l0) & op.cmask) != op.cval)) continue;
     C v[D];
 #pragma unroll
     for (int r = 0; r < D; ++r) v[r] = s[l0 + gi.offs[r]];
 #pragma unroll
-    for (int r = 0; r < D; ++r) s[l0 + gi.offs[r]] = matrow<R, K>(v, M, r, dagger);
+    for (int r = 0; r < D; ++r) s[l0 + gi.offs[r]] = matrow<R, K>(v, M, r);
   }
 }
 
 template <typename R, int MAXK>
-__device__ __forceinline__ void apply_dense_any(c_t<R> *s, const TileGeom &tg, const OpDev &op,
-                                                const c_t<R> *mats, bool dagger) {
-  if (op.k == 1) {
-    apply_dense_tile<R, 1>(s, tg, op, mats, dagger);
-  } else if (MAXK <= 2 || op.k == 2) {
-    apply_dense_tile<R, 2>(s, tg, op, mats, dagger);
+__device__ __forceinline__ void dense_any(c_t<R> *s, const TileGeom &tg, const OpDev &op, const c_t<R> *mats) {
+  if (MAXK <= 2 || op.k == 2) {
+    dense_vec<R, 2>(s, tg, op, mats);
   } else if (op.k == 3) {
-    apply_dense_tile<R, (MAXK >= 3 ? 3 : 2)>(s, tg, op, mats, dagger);
+    dense_vec<R, (MAXK >= 3 ? 3 : 2)>(s, tg, op, mats);
   } else {
-    apply_dense_tile<R, (MAXK >= 4 ? 4 : 2)>(s, tg, op, mats, dagger);
+    dense_vec<R, (MAXK >= 4 ? 4 : 2)>(s, tg, op, mats);
   }
 }
 
-__device__ __forceinline__ int diag_index(const OpDev &op, uint64_t g) {
-  int idx = 0;
-  for (int j = 0; j < op.k; ++j) idx = (idx << 1) | (int)((g >> op.tg[j]) & 1);
-  return idx;
-}
-
-// A run of consecutive diagonal ops [o0, o1): every amplitude is multiplied by
-// the product of its diagonal entries, in op order.
-template <typename R>
-__device__ void apply_diag_run(c_t<R> *s, const TileGeom &tg, const OpDev *__restrict__ ops, int o0,
-                               int o1, const c_t<R> *__restrict__ mats, bool dagger) {
-  using C = c_t<R>;
-  for (int l = threadIdx.x; l < tg.A; l += blockDim.x) {
-    const uint64_t g = tg.gidx(l);
-    C a = s[l];
-    if (!dagger) {
-      for (int o = o0; o < o1; ++o) {
-        const OpDev &op = ops[o];
-        if ((g & op.cmask) != op.cval) continue;
-        a = cmul(a, mats[op.mat + diag_index(op, g)]);
-      }
-    } else {
-      for (int o = o1 - 1; o >= o0; --o) {
-        const OpDev &op = ops[o];
-        if ((g & op.cmask) != op.cval) continue;
-        a = cmul(a, cconj(mats[op.mat + diag_index(op, g)]));
-      }
-    }
-    s[l] = a;
-  }
+template <typename R, int MAXK>
+__device__ __forceinline__ void apply_op(c_t<R> *s, const TileGeom &tg, const OpDev &op, const c_t<R> *mats) {
+  if (op.kind == kPair)
+    fwd_pair<R>(s, tg, op, mats);
+  else if (op.kind == kDiag)
+    fwd_diag<R>(s, tg, op, mats);
+  else
+    dense_any<R, MAXK>(s, tg, op, mats);
 }
 
 // ---------------------------------------------------------------------------
-// Forward pass kernel (S1-S4): load tile, apply the pass's ops, store tile.
+// Forward pass kernel (S1-S4): load tile, apply the pass's micro-ops, store.
+// A barrier separates micro-ops whose thread-to-amplitude maps differ; runs of
+// diagonal micro-ops and the blocks of one gate need none (each thread keeps
+// the same amplitudes, or the blocks are disjoint).
 // ---------------------------------------------------------------------------
 template <typename R, int MAXK>
 __global__ void __launch_bounds__(kBlock) k_tile_forward(c_t<R> *__restrict__ psi, int n, const PassDev pass,
@@ -308,116 +429,164 @@ __global__ void __launch_bounds__(kBlock) k_tile_forward(c_t<R> *__restrict__ ps
     tg.base = tile_base(pass, tile);
     load_tile_rw<R>(psi, s, tg);
     __syncthreads();
-    int o = pass.op_begin;
-    while (o < pass.op_end) {
-      if (ops[o].cls == kDiag) {
-        int e = o + 1;
-        while (e < pass.op_end && ops[e].cls == kDiag) ++e;
-        apply_diag_run<R>(s, tg, ops, o, e, mats, false);
-        o = e;
-      } else {
-        apply_dense_any<R, MAXK>(s, tg, ops[o], mats, false);
-        ++o;
-      }
-      __syncthreads();
+    for (int o = pass.op_begin; o < pass.op_end; ++o) {
+      const OpDev &op = ops[o];
+      if (op.sync_prev && o > pass.op_begin) __syncthreads();
+      apply_op<R, MAXK>(s, tg, op, mats);
     }
+    __syncthreads();
     store_tile<R>(psi, s, tg);
     __syncthreads();
   }
 }
 
 // ---------------------------------------------------------------------------
-// Adjoint pass kernel (S7): for ops of the pass in reverse order,
-//   partial[op] += Im <lambda | G phi>   (before un-applying the op),
-//   phi <- U^dagger phi,  lambda <- U^dagger lambda.
-// blockIdx.x = lambda index j (fastest, so the CTAs that share a phi tile run
-// together and re-read it from L2), blockIdx.y = tile group.  phi_in is read,
-// phi_out written by the j == 0 CTAs only: with several lambdas they are
-// distinct (ping-pong) buffers; with one lambda each phi tile is read and
-// written by the same CTA, so phi_out may equal phi_in (three vectors in all).
-// Partial layout: partials[(b * m + j) * n_train + t].
+// Adjoint pass kernel (S7).  For the pass's micro-ops in reverse order:
+//   acc[op, j] += Im <lambda_j | G phi>   (before the op is un-applied),
+//   phi <- E phi, lambda_j <- E lambda_j   (E = U^dagger, stored by the builder).
+// One CTA holds a phi tile and b lambda tiles in shared memory, so phi is
+// un-applied once per b lambdas.  blockIdx.x = lambda group (fastest, so the
+// CTAs sharing a phi tile run together and re-read it from L2), blockIdx.y =
+// tile group.  phi_out is written by lambda group 0 only: with several groups
+// phi_in / phi_out are distinct buffers; with one group each phi tile is read
+// and written by one CTA and phi_out may equal phi_in.
+// Partial layout: partials[(blockIdx.y * m + j) * n_train + t].
 // ---------------------------------------------------------------------------
-template <typename R, int K>
-__device__ void adjoint_dense_tile(c_t<R> *sp, c_t<R> *sl, const TileGeom &tg, const OpDev &op,
-                                   const c_t<R> *__restrict__ mats, double &accum) {
+template <typename R>
+__device__ __forceinline__ void flush_acc(Acc<R> (&acc)[kMaxLambdaPerCta], int bb, int b, int train, double *accs,
+                                          int nwarps, int warp, int lane) {
+#pragma unroll
+  for (int jj = 0; jj < kMaxLambdaPerCta; ++jj) {
+    if (jj < bb) {
+      const R v = warp_sum(acc[jj].value());
+      if (lane == 0) WarpAcc<R>::add(&accs[(train * b + jj) * nwarps + warp], v);
+    }
+  }
+}
+
+template <typename R, int CODE, int GCODE>
+__device__ void adj_pair_t(c_t<R> *sp, c_t<R> *sl, int bb, const TileGeom &tg, const OpDev &op,
+                           const c_t<R> *__restrict__ mats, Acc<R> (&acc)[kMaxLambdaPerCta]) {
   using C = c_t<R>;
-  constexpr int D = 1 << K;
-  GroupIdx<K> gi;
-  gi.init(op);
-  const C *M = mats + op.mat;
-  const bool train = op.train >= 0;
-  const C *G = mats + (train ? op.gen : op.mat);
-  Acc<R> acc;
-  const int ng = tg.A >> K;
+  C Mr[4];
+  if (CODE == mGen || CODE == mReal || CODE == mImOff)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) Mr[q] = mats[op.mat + q];
+  const R gs = (R)op.gs;
+  const int ng = tg.A >> op.k;
+  const bool ctl = op.cmask != 0;
   for (int g = threadIdx.x; g < ng; g += blockDim.x) {
-    const int l0 = gi.first(g);
-    if (op.cmask && ((tg.gidx(l0) & op.cmask) != op.cval)) continue;
-    C v[D];
+    const int l0 = group_base(op, g);
+    if (ctl && ((tg.gidx(l0) & op.cmask) != op.cval)) continue;
+    const int ia = l0 + op.oa, ib = l0 + op.ob;
+    C pa = sp[ia], pb = sp[ib];
+    const C qa = pa, qb = pb;  // phi before the un-apply
+    pair_apply<R>(CODE, Mr, pa, pb);
+    sp[ia] = pa;
+    sp[ib] = pb;
 #pragma unroll
-    for (int r = 0; r < D; ++r) v[r] = sp[l0 + gi.offs[r]];
-    if (train) {
-      // Im sum_r conj(lambda_r) (G phi)_r, before the op is un-applied
-#pragma unroll
-      for (int r = 0; r < D; ++r) {
-        const C gp = matrow<R, K>(v, G, r, false);
-        const C q = sl[l0 + gi.offs[r]];
-        acc.add(q.x * gp.y - q.y * gp.x);
+    for (int jj = 0; jj < kMaxLambdaPerCta; ++jj) {
+      if (jj < bb) {
+        C la = sl[jj * tg.A + ia], lb = sl[jj * tg.A + ib];
+        if (GCODE != gNone) acc[jj].add(pair_ip<R>(GCODE, gs, qa, qb, la, lb));
+        pair_apply<R>(CODE, Mr, la, lb);
+        sl[jj * tg.A + ia] = la;
+        sl[jj * tg.A + ib] = lb;
       }
     }
-#pragma unroll
-    for (int r = 0; r < D; ++r) sp[l0 + gi.offs[r]] = matrow<R, K>(v, M, r, true);
-#pragma unroll
-    for (int r = 0; r < D; ++r) v[r] = sl[l0 + gi.offs[r]];
-#pragma unroll
-    for (int r = 0; r < D; ++r) sl[l0 + gi.offs[r]] = matrow<R, K>(v, M, r, true);
   }
-  accum = acc.value();
+}
+
+template <typename R, int CODE>
+__device__ __forceinline__ void adj_pair_g(c_t<R> *sp, c_t<R> *sl, int bb, const TileGeom &tg, const OpDev &op,
+                                           const c_t<R> *mats, Acc<R> (&acc)[kMaxLambdaPerCta]) {
+  const int gcode = op.train >= 0 ? op.gcode : gNone;
+  if (gcode == gX)
+    adj_pair_t<R, CODE, gX>(sp, sl, bb, tg, op, mats, acc);
+  else if (gcode == gY)
+    adj_pair_t<R, CODE, gY>(sp, sl, bb, tg, op, mats, acc);
+  else
+    adj_pair_t<R, CODE, gNone>(sp, sl, bb, tg, op, mats, acc);
 }
 
 template <typename R>
-__device__ void adjoint_diag_tile(c_t<R> *sp, c_t<R> *sl, const TileGeom &tg, const OpDev &op,
-                                  const c_t<R> *__restrict__ mats, double &accum) {
+__device__ __forceinline__ void adj_pair(c_t<R> *sp, c_t<R> *sl, int bb, const TileGeom &tg, const OpDev &op,
+                                         const c_t<R> *mats, Acc<R> (&acc)[kMaxLambdaPerCta]) {
+  switch (op.code) {
+    case mSwap: adj_pair_g<R, mSwap>(sp, sl, bb, tg, op, mats, acc); break;
+    case mY: adj_pair_g<R, mY>(sp, sl, bb, tg, op, mats, acc); break;
+    case mReal: adj_pair_g<R, mReal>(sp, sl, bb, tg, op, mats, acc); break;
+    case mImOff: adj_pair_g<R, mImOff>(sp, sl, bb, tg, op, mats, acc); break;
+    default: adj_pair_g<R, mGen>(sp, sl, bb, tg, op, mats, acc); break;
+  }
+}
+
+template <typename R, bool TRAIN>
+__device__ void adj_diag_t(c_t<R> *sp, c_t<R> *sl, int bb, const TileGeom &tg, const OpDev &op,
+                           const c_t<R> *__restrict__ mats, Acc<R> (&acc)[kMaxLambdaPerCta]) {
   using C = c_t<R>;
-  const bool train = op.train >= 0;
-  Acc<R> acc;
+  C d[4];
+  const bool small = op.k <= 2 && op.code == dGen;
+  if (small)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) d[q] = q < (1 << op.k) ? mats[op.mat + q] : C();
+  const R ga = (R)op.ga, gb = (R)op.gb;
   for (int l = threadIdx.x; l < tg.A; l += blockDim.x) {
     const uint64_t g = tg.gidx(l);
     if ((g & op.cmask) != op.cval) continue;
     const int idx = diag_index(op, g);
-    C p = sp[l], q = sl[l];
-    if (train) {
-      const R gd = mats[op.gen + idx].x;  // generator diagonal is real
-      acc.add(gd * (q.x * p.y - q.y * p.x));
+    C dv;
+    if (small) {
+      dv = d[0];
+#pragma unroll
+      for (int q = 1; q < 4; ++q)
+        if (idx == q) dv = d[q];
     }
-    const C d = cconj(mats[op.mat + idx]);
-    sp[l] = cmul(p, d);
-    sl[l] = cmul(q, d);
+    const C p = sp[l];
+    R gd = R(0);
+    if (TRAIN) gd = (__popc(idx & op.zmask) & 1) ? gb : ga;
+    sp[l] = small ? cmul(p, dv) : diag_mul<R>(op, mats, idx, p);
+#pragma unroll
+    for (int jj = 0; jj < kMaxLambdaPerCta; ++jj) {
+      if (jj < bb) {
+        const C q = sl[jj * tg.A + l];
+        if (TRAIN) acc[jj].add(gd * im_cx(q, p));
+        sl[jj * tg.A + l] = small ? cmul(q, dv) : diag_mul<R>(op, mats, idx, q);
+      }
+    }
   }
-  accum = acc.value();
+}
+
+template <typename R>
+__device__ __forceinline__ void adj_diag(c_t<R> *sp, c_t<R> *sl, int bb, const TileGeom &tg, const OpDev &op,
+                                         const c_t<R> *mats, Acc<R> (&acc)[kMaxLambdaPerCta]) {
+  if (op.train >= 0)
+    adj_diag_t<R, true>(sp, sl, bb, tg, op, mats, acc);
+  else
+    adj_diag_t<R, false>(sp, sl, bb, tg, op, mats, acc);
 }
 
 template <typename R, int MAXK>
-__global__ void __launch_bounds__(kBlock) k_tile_adjoint(const c_t<R> *phi_in, c_t<R> *phi_out,
-                                                          c_t<R> *__restrict__ lam_base, int n,
+__global__ void __launch_bounds__(kBlock, 2) k_tile_adjoint(const c_t<R> *phi_in, c_t<R> *phi_out,
+                                                          c_t<R> *__restrict__ lam_base, int n, int m, int b,
                                                           const PassDev pass, const OpDev *__restrict__ ops,
                                                           const c_t<R> *__restrict__ mats,
                                                           double *__restrict__ partials) {
   using C = c_t<R>;
   extern __shared__ __align__(16) unsigned char smem[];
   const int A = 1 << pass.T;
+  const int j0 = blockIdx.x * b;
+  const int bb = min(b, m - j0);
   C *sp = reinterpret_cast<C *>(smem);
-  C *sl = sp + A;
-  uint64_t *lut = reinterpret_cast<uint64_t *>(sl + A);
+  C *sl = sp + A;  // b lambda tiles
+  uint64_t *lut = reinterpret_cast<uint64_t *>(sl + (size_t)b * A);
   const int nch = 1 << (pass.T - pass.nlow);
-  double *accs = reinterpret_cast<double *>(lut + nch);  // [n_train][nwarps]
+  double *accs = reinterpret_cast<double *>(lut + nch);  // [n_train][b][nwarps]
   const int nwarps = blockDim.x >> 5;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int j = blockIdx.x;
-  const int m = gridDim.x;
-  C *lam = lam_base + ((size_t)j << n);
 
   build_lut(lut, pass);
-  for (int i = threadIdx.x; i < pass.n_train * nwarps; i += blockDim.x) accs[i] = 0.0;
+  for (int i = threadIdx.x; i < pass.n_train * b * nwarps; i += blockDim.x) accs[i] = 0.0;
   TileGeom tg;
   tg.T = pass.T;
   tg.nlow = pass.nlow;
@@ -429,38 +598,34 @@ __global__ void __launch_bounds__(kBlock) k_tile_adjoint(const c_t<R> *phi_in, c
   const uint64_t ntiles = 1ull << (n - pass.T);
   for (uint64_t tile = blockIdx.y; tile < ntiles; tile += gridDim.y) {
     tg.base = tile_base(pass, tile);
-    load_tile_rw<R>(phi_in, sp, tg);  // phi_in may equal phi_out (single lambda, in place)
-    load_tile_rw<R>(lam, sl, tg);
+    load_tile_rw<R>(phi_in, sp, tg);  // phi_in may equal phi_out (one lambda group, in place)
+    for (int jj = 0; jj < bb; ++jj) load_tile_rw<R>(lam_base + ((size_t)(j0 + jj) << n), sl + (size_t)jj * A, tg);
     __syncthreads();
     for (int o = pass.op_end - 1; o >= pass.op_begin; --o) {
       const OpDev &op = ops[o];
-      double part = 0.0;
-      if (op.cls == kDiag) {
-        adjoint_diag_tile<R>(sp, sl, tg, op, mats, part);
+      if (op.kind == kDense) {
+        dense_any<R, MAXK>(sp, tg, op, mats);
+        for (int jj = 0; jj < bb; ++jj) dense_any<R, MAXK>(sl + (size_t)jj * A, tg, op, mats);
       } else {
-        if (op.k == 1)
-          adjoint_dense_tile<R, 1>(sp, sl, tg, op, mats, part);
-        else if (MAXK <= 2 || op.k == 2)
-          adjoint_dense_tile<R, 2>(sp, sl, tg, op, mats, part);
-        else if (op.k == 3)
-          adjoint_dense_tile<R, (MAXK >= 3 ? 3 : 2)>(sp, sl, tg, op, mats, part);
+        Acc<R> acc[kMaxLambdaPerCta];
+        if (op.kind == kPair)
+          adj_pair<R>(sp, sl, bb, tg, op, mats, acc);
         else
-          adjoint_dense_tile<R, (MAXK >= 4 ? 4 : 2)>(sp, sl, tg, op, mats, part);
+          adj_diag<R>(sp, sl, bb, tg, op, mats, acc);
+        if (op.train >= 0) flush_acc<R>(acc, bb, b, op.train, accs, nwarps, warp, lane);
       }
-      if (op.train >= 0) {
-        part = warp_sum(part);
-        if (lane == 0) accs[op.train * nwarps + warp] += part;
-      }
-      __syncthreads();
+      if (op.sync_prev && o > pass.op_begin) __syncthreads();
     }
-    store_tile<R>(lam, sl, tg);
-    if (j == 0) store_tile<R>(phi_out, sp, tg);
+    __syncthreads();
+    for (int jj = 0; jj < bb; ++jj) store_tile<R>(lam_base + ((size_t)(j0 + jj) << n), sl + (size_t)jj * A, tg);
+    if (blockIdx.x == 0) store_tile<R>(phi_out, sp, tg);
     __syncthreads();
   }
-  for (int t = threadIdx.x; t < pass.n_train; t += blockDim.x) {
+  for (int i = threadIdx.x; i < pass.n_train * bb; i += blockDim.x) {
+    const int t = i / bb, jj = i % bb;
     double v = 0.0;
-    for (int w = 0; w < nwarps; ++w) v += accs[t * nwarps + w];
-    partials[((size_t)blockIdx.y * m + j) * pass.n_train + t] = v;
+    for (int w = 0; w < nwarps; ++w) v += WarpAcc<R>::read(&accs[(t * b + jj) * nwarps + w]);
+    partials[((size_t)blockIdx.y * m + j0 + jj) * pass.n_train + t] = v;
   }
 }
 
@@ -520,14 +685,14 @@ __global__ void __launch_bounds__(kBlock) k_expval(const c_t<R> *__restrict__ ps
         R v = pauli_re<R>(s[l], s[l ^ tm.xl], tm.ny);
         acc.add(par ? -v : v);
       }
-      const double part = warp_sum(acc.value());
-      if (lane == 0) accs[t * nwarps + warp] += part;
+      const R part = warp_sum(acc.value());
+      if (lane == 0) WarpAcc<R>::add(&accs[t * nwarps + warp], part);
     }
     __syncthreads();
   }
   for (int t = threadIdx.x; t < n_terms; t += blockDim.x) {
     double v = 0.0;
-    for (int w = 0; w < nwarps; ++w) v += accs[t * nwarps + w];
+    for (int w = 0; w < nwarps; ++w) v += WarpAcc<R>::read(&accs[t * nwarps + w]);
     partials[(size_t)blockIdx.x * n_terms + t] = v;
   }
 }
@@ -734,45 +899,25 @@ __device__ inline void gate_matrix(int kind, const double *a, double2 *m) {
   }
 }
 
-// Generator G with U(t) = exp(i s t G); the factor s is applied on the host.
-__device__ inline void gate_generator(int kind, double2 *m) {
-  switch (kind) {
-    case SV_RX: m[0] = dc(0, 0); m[1] = dc(1, 0); m[2] = dc(1, 0); m[3] = dc(0, 0); break;
-    case SV_RY: m[0] = dc(0, 0); m[1] = dc(0, -1); m[2] = dc(0, 1); m[3] = dc(0, 0); break;
-    case SV_RZ: m[0] = dc(1, 0); m[1] = dc(0, 0); m[2] = dc(0, 0); m[3] = dc(-1, 0); break;
-    case SV_PHASE_SHIFT: m[0] = dc(0, 0); m[1] = dc(0, 0); m[2] = dc(0, 0); m[3] = dc(1, 0); break;
-    case SV_ISING_XX:
-      for (int i = 0; i < 16; ++i) m[i] = dc(0, 0);
-      for (int i = 0; i < 4; ++i) m[i * 4 + (3 - i)] = dc(1, 0);
-      break;
-    case SV_ISING_YY:
-      for (int i = 0; i < 16; ++i) m[i] = dc(0, 0);
-      m[3] = m[12] = dc(-1, 0);
-      m[6] = m[9] = dc(1, 0);
-      break;
-    case SV_ISING_ZZ:
-      for (int i = 0; i < 16; ++i) m[i] = dc(0, 0);
-      m[0] = m[15] = dc(1, 0);
-      m[5] = m[10] = dc(-1, 0);
-      break;
-    case SV_ISING_XY:
-      for (int i = 0; i < 16; ++i) m[i] = dc(0, 0);
-      m[6] = m[9] = dc(2, 0);
-      break;
-    case SV_SINGLE_EXCITATION:
-      for (int i = 0; i < 16; ++i) m[i] = dc(0, 0);
-      m[6] = dc(0, -1);
-      m[9] = dc(0, 1);
-      break;
-    case SV_DOUBLE_EXCITATION:
-      for (int i = 0; i < 256; ++i) m[i] = dc(0, 0);
-      m[3 * 16 + 12] = dc(0, -1);
-      m[12 * 16 + 3] = dc(0, 1);
-      break;
-    default: break;
+template <typename R>
+__device__ __forceinline__ void put_entry(const MatSlot &sl, c_t<R> *o, int r, int c, double re, double im) {
+  c_t<R> v;
+  v.x = (R)re;
+  v.y = (R)im;
+  const int D = 1 << sl.k;
+  if (sl.mode == 0) {
+    o[r * D + c] = v;
+  } else if (sl.mode == 1) {
+    if (r == c) o[r] = v;
+  } else {
+    const int rr = r == sl.a ? 0 : (r == sl.b ? 1 : -1);
+    const int cc = c == sl.a ? 0 : (c == sl.b ? 1 : -1);
+    if (rr >= 0 && cc >= 0) o[rr * 2 + cc] = v;
   }
 }
 
+// One thread per slot: E = U (or U^dagger) from FP64 trigonometry, written
+// whole, as its diagonal, or as one 2x2 block.
 template <typename R>
 __global__ void k_build_matrices(const MatSlot *__restrict__ slots, int n_slots,
                                  const double *__restrict__ params, const double *__restrict__ user,
@@ -785,32 +930,24 @@ __global__ void k_build_matrices(const MatSlot *__restrict__ slots, int n_slots,
   if (sl.kind == SV_MATRIX) {
     for (int r = 0; r < D; ++r)
       for (int c = 0; c < D; ++c) {
-        if (sl.diag && r != c) continue;
-        const int64_t e = sl.adjoint ? (int64_t)c * D + r : (int64_t)r * D + c;
-        double re = user[2 * (sl.src + e)], im = user[2 * (sl.src + e) + 1];
-        if (sl.adjoint) im = -im;
-        c_t<R> v;
-        v.x = (R)re;
-        v.y = (R)im;
-        o[sl.diag ? r : r * D + c] = v;
+        if (sl.mode == 1 && r != c) continue;
+        const int64_t e = sl.dagger ? (int64_t)c * D + r : (int64_t)r * D + c;
+        const double re = user[2 * (sl.src + e)];
+        const double im = sl.dagger ? -user[2 * (sl.src + e) + 1] : user[2 * (sl.src + e) + 1];
+        put_entry<R>(sl, o, r, c, re, im);
       }
     return;
   }
   double a[3];
   for (int q = 0; q < 3; ++q) a[q] = sl.pidx[q] >= 0 ? sl.scale * params[sl.pidx[q]] : sl.cangle[q];
   double2 m[256];
-  if (sl.what == 0)
-    gate_matrix(sl.kind, a, m);
-  else
-    gate_generator(sl.kind, m);
+  gate_matrix(sl.kind, a, m);
   for (int r = 0; r < D; ++r)
     for (int c = 0; c < D; ++c) {
-      if (sl.diag && r != c) continue;
-      double2 v = (sl.adjoint && sl.what == 0) ? make_double2(m[c * D + r].x, -m[c * D + r].y) : m[r * D + c];
-      c_t<R> w;
-      w.x = (R)v.x;
-      w.y = (R)v.y;
-      o[sl.diag ? r : r * D + c] = w;
+      if (sl.mode == 1 && r != c) continue;
+      if (sl.mode == 2 && !((r == sl.a || r == sl.b) && (c == sl.a || c == sl.b))) continue;
+      const double2 v = sl.dagger ? make_double2(m[c * D + r].x, -m[c * D + r].y) : m[r * D + c];
+      put_entry<R>(sl, o, r, c, v.x, v.y);
     }
 }
 

@@ -48,24 +48,24 @@ cudaError_t Launch<R>::tile_forward(void *psi, int n, const PassDev &pass, const
 }
 
 template <typename R>
-cudaError_t Launch<R>::tile_adjoint(const void *phi_in, void *phi_out, void *lam, int n, int m,
-                                    const PassDev &pass, const OpDev *ops, const void *mats,
-                                    double *partials, int grid, cudaStream_t st) {
+cudaError_t Launch<R>::tile_adjoint(const void *phi_in, void *phi_out, void *lam, int n, int m, int b,
+                                    const PassDev &pass, const OpDev *ops, const void *mats, double *partials,
+                                    int grid, cudaStream_t st) {
   static bool attr2 = false, attr4 = false;
-  const int smem = 2 * detail::tile_bytes(sizeof(c_t<R>), pass.T) + detail::lut_bytes(pass) +
-                   pass.n_train * detail::kWarps * 8;
-  dim3 g(m, grid);
+  const int smem = (1 + b) * detail::tile_bytes(sizeof(c_t<R>), pass.T) + detail::lut_bytes(pass) +
+                   pass.n_train * b * detail::kWarps * 8;
+  dim3 g((m + b - 1) / b, grid);
   if (pass.max_k <= 2) {
     detail::allow_big_smem(k_tile_adjoint<R, 2>, attr2);
     k_tile_adjoint<R, 2><<<g, kBlock, smem, st>>>(reinterpret_cast<const c_t<R> *>(phi_in),
                                                    reinterpret_cast<c_t<R> *>(phi_out),
-                                                   reinterpret_cast<c_t<R> *>(lam), n, pass, ops,
+                                                   reinterpret_cast<c_t<R> *>(lam), n, m, b, pass, ops,
                                                    reinterpret_cast<const c_t<R> *>(mats), partials);
   } else {
     detail::allow_big_smem(k_tile_adjoint<R, 4>, attr4);
     k_tile_adjoint<R, 4><<<g, kBlock, smem, st>>>(reinterpret_cast<const c_t<R> *>(phi_in),
                                                    reinterpret_cast<c_t<R> *>(phi_out),
-                                                   reinterpret_cast<c_t<R> *>(lam), n, pass, ops,
+                                                   reinterpret_cast<c_t<R> *>(lam), n, m, b, pass, ops,
                                                    reinterpret_cast<const c_t<R> *>(mats), partials);
   }
   return cudaGetLastError();
