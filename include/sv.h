@@ -282,6 +282,37 @@ sv_status sv_kernel_timing_read(double *total_ms, int64_t *launches);
 sv_status sv_plan_query(int n, sv_dtype dtype, const sv_tape *tape,
                         int *n_forward_passes, int *n_adjoint_passes);
 
+/* ---- expectation values without device allocation ------------------------------ */
+
+/* The paper has no counterpart to this call; it exists for callers that cannot
+ * allocate device memory when they need a measurement (an application that
+ * reserved all GPU memory up front, code where cudaMalloc / cudaFree and the
+ * device synchronisation of cudaFree are not allowed, or a framework whose
+ * allocator must not see foreign allocations).
+ *
+ * Same values as sv_expval (same kernels and summation order), computed for a
+ * state given by its device pointer psi (2^n amplitudes of dtype, 16-byte
+ * aligned, read only) on cuda_stream (NULL = legacy default stream); results go
+ * to the host array out[n_obs] and the call synchronises the stream.  Every
+ * temporary lives in one array compiled into the library
+ * (SV_STATIC_SCRATCH_BYTES on every GPU that loads it, until exit); the call
+ * makes no cudaMalloc / cudaFree or other allocation.
+ *
+ * Limits, rejected with SV_ERR_ARG and a message in sv_last_error(): at most
+ * SV_STATIC_MAX_OBSERVABLES observables and SV_STATIC_MAX_TERMS Pauli terms in
+ * total per call.
+ *
+ * The first call on each device looks up the array's device address (with
+ * that device current) and keeps it: make that first call before any stream
+ * capture.  All calls share the array; calls whose GPU work overlaps race and
+ * must be serialised by the caller.  The per-term totals are cleared at the
+ * start of every call. */
+#define SV_STATIC_SCRATCH_BYTES (2u << 20)
+#define SV_STATIC_MAX_TERMS 4096
+#define SV_STATIC_MAX_OBSERVABLES 1024
+sv_status sv_expval_static(const void *psi, int n, sv_dtype dtype, const sv_pauli_sum *obs, int n_obs,
+                           double *out, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

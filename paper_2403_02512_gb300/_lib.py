@@ -117,6 +117,8 @@ PROTOTYPES = {
     "sv_kernel_timing_enable": (ctypes.c_int, [ctypes.c_int]),
     "sv_kernel_timing_reset": (ctypes.c_int, []),
     "sv_kernel_timing_read": (ctypes.c_int, [_dp, ctypes.POINTER(ctypes.c_int64)]),
+    "sv_expval_static": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(SvPauliSum), ctypes.c_int,
+                                        _dp, _vp]),
 }
 
 KERNEL_CLASSES = ["tile_forward", "tile_adjoint", "expval", "lambda", "reduce", "build_matrices", "dense_k",
@@ -332,6 +334,15 @@ def sv_kernel_timing_read():
     cnt = (ctypes.c_int64 * len(KERNEL_CLASSES))()
     _check(load().sv_kernel_timing_read(ms, cnt))
     return {name: (ms[i], cnt[i]) for i, name in enumerate(KERNEL_CLASSES)}
+
+
+def sv_expval_static(device_ptr: int, n: int, dtype: int, obs: "PauliSums", stream: int = 0) -> np.ndarray:
+    """sv_expval for a state given by device pointer, with no device allocation
+    (all temporaries in the library's fixed scratch array)."""
+    out = np.zeros(obs.count, dtype=np.float64)
+    _check(load().sv_expval_static(_vp(device_ptr), int(n), int(dtype), obs.array, obs.count, _dptr(out),
+                                   _vp(stream)))
+    return out
 
 
 # ---------------------------------------------------------------------------

@@ -1306,6 +1306,10 @@ sv_status sync_state(sv_state *s) {
 
 }  // namespace
 
+namespace sv {
+void set_error_message(const char *msg) { g_err = msg ? msg : ""; }
+}  // namespace sv
+
 // ==== C ABI ==========================================================================
 extern "C" {
 

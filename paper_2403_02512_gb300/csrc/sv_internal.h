@@ -129,6 +129,9 @@ struct Launch {
   static int max_T_adjoint();
 };
 
+// Message returned by sv_last_error() on the calling thread (defined in sv_api.cu).
+void set_error_message(const char *msg);
+
 // Deterministic reductions (precision independent, sv_kernels_f64.cu).
 // out[r] = sum_{b < nb} partials[b * stride + r] for r < rows, fixed order.
 cudaError_t reduce_rows(const double *partials, int nb, int rows, int stride, double *out,
