@@ -277,6 +277,41 @@ sv_status sv_kernel_timing_enable(int enable);
 sv_status sv_kernel_timing_reset(void);
 sv_status sv_kernel_timing_read(double *total_ms, int64_t *launches);
 
+/* ---- batched circuits (S9) ---------------------------------------------------------- */
+
+typedef struct sv_batch sv_batch; /* opaque: many circuits in one persistent launch */
+
+/* Plan n_circuits circuits for one persistent, CUDA-graph-captured launch
+ * (many independent circuits on one device, as in the paper's batched
+ * execution of cut-circuit fragments of mixed sizes, Sec. 4.1).  Circuit i acts
+ * on n_qubits[i] wires (1..30), runs tapes[i] from |basis_states[i]> (NULL = all
+ * |0>) and measures obs[i], one Pauli sum of Z-only words (x_mask = 0;
+ * otherwise SV_ERR_UNSUPPORTED), giving one expectation value per circuit.
+ * Parameters of circuit i are the next tapes[i].n_params entries of the
+ * concatenated parameter vector.  Tapes may repeat (one tape, many parameter
+ * sets).  The batch owns its device memory (states of all circuits, tables).
+ * SV_MATRIX ops wider than 4 wires are not supported in a batch. */
+sv_status sv_batch_create(sv_dtype dtype, int n_circuits, const int *n_qubits, const sv_tape *tapes,
+                          const sv_pauli_sum *obs, const uint64_t *basis_states, sv_batch **out);
+sv_status sv_batch_destroy(sv_batch *b);
+/* Stream for all batch work (NULL: a stream the batch creates; graph capture
+ * needs a non-default stream). */
+sv_status sv_batch_set_stream(sv_batch *b, void *cuda_stream);
+/* Concatenated parameters (sum of tapes[i].n_params doubles), host or device. */
+sv_status sv_batch_set_params(sv_batch *b, const double *params, int params_on_device);
+/* Run every circuit: expvals_out[i] = <H_i> of circuit i.  Host outputs
+ * synchronise and report SV_ERR_TIMEOUT if a bounded inter-CTA wait gave up;
+ * device outputs are asynchronous (then check with sv_batch_status). */
+sv_status sv_batch_run(sv_batch *b, double *expvals_out, int outputs_on_device);
+/* SV_ERR_TIMEOUT if the last run's bounded waits gave up, else SV_OK (synchronises). */
+sv_status sv_batch_status(sv_batch *b);
+/* Time candidate tile widths and circuit-wave sizes on this device and keep the
+ * fastest (the batch's autotuner); *best_ms gets the chosen run time. */
+sv_status sv_batch_autotune(sv_batch *b, double *best_ms);
+/* Plan facts: work items, persistent CTAs, tile bits, wave bytes, graph in use (0/1). */
+sv_status sv_batch_info(const sv_batch *b, int64_t *work_items, int *ctas, int *tile_bits, int64_t *wave_bytes,
+                        int *graph);
+
 /* Host-only planner query (no GPU needed): number of fused forward passes and
  * adjoint passes this build would use for a tape on n qubits and dtype. */
 sv_status sv_plan_query(int n, sv_dtype dtype, const sv_tape *tape,

@@ -117,6 +117,17 @@ PROTOTYPES = {
     "sv_kernel_timing_enable": (ctypes.c_int, [ctypes.c_int]),
     "sv_kernel_timing_reset": (ctypes.c_int, []),
     "sv_kernel_timing_read": (ctypes.c_int, [_dp, ctypes.POINTER(ctypes.c_int64)]),
+    "sv_batch_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _ip, ctypes.POINTER(SvTape),
+                                       ctypes.POINTER(SvPauliSum), ctypes.POINTER(ctypes.c_uint64),
+                                       ctypes.POINTER(_vp)]),
+    "sv_batch_destroy": (ctypes.c_int, [_vp]),
+    "sv_batch_set_stream": (ctypes.c_int, [_vp, _vp]),
+    "sv_batch_set_params": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
+    "sv_batch_run": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
+    "sv_batch_status": (ctypes.c_int, [_vp]),
+    "sv_batch_autotune": (ctypes.c_int, [_vp, _dp]),
+    "sv_batch_info": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int64), _ip, _ip, ctypes.POINTER(ctypes.c_int64),
+                                     _ip]),
     "sv_expval_static": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(SvPauliSum), ctypes.c_int,
                                         _dp, _vp]),
 }
@@ -334,6 +345,83 @@ def sv_kernel_timing_read():
     cnt = (ctypes.c_int64 * len(KERNEL_CLASSES))()
     _check(load().sv_kernel_timing_read(ms, cnt))
     return {name: (ms[i], cnt[i]) for i, name in enumerate(KERNEL_CLASSES)}
+
+
+class Batch:
+    """Many circuits in one persistent, graph-captured launch (sv_batch_*).
+
+    ``circuits``: objects with ``n``, ``ops``, ``n_params``, ``observables``
+    (the first observable is measured; Z-only words) and ``basis_state``.
+    Circuits that share a structure may pass the same object repeatedly.
+    """
+
+    def __init__(self, circuits, dtype: int = SV_C64):
+        self.count = len(circuits)
+        cache = {}
+        tapes = (SvTape * self.count)()
+        obs = []
+        self._keep = []
+        for i, c in enumerate(circuits):
+            key = id(c)
+            if key not in cache:
+                cache[key] = Tape(c.ops, c.n_params)
+            t = cache[key]
+            self._keep.append(t)
+            tapes[i] = t.struct
+            obs.append(c.observables[0] if c.observables else [])
+        self._tapes = tapes
+        self._obs = PauliSums(obs)
+        nq = (ctypes.c_int * self.count)(*[int(c.n) for c in circuits])
+        basis = (ctypes.c_uint64 * self.count)(*[int(getattr(c, "basis_state", 0)) for c in circuits])
+        self.n_params = sum(int(c.n_params) for c in circuits)
+        h = _vp()
+        _check(load().sv_batch_create(int(dtype), self.count, nq, tapes, self._obs.array, basis, ctypes.byref(h)))
+        self.handle = h.value
+
+    def set_params(self, params, on_device: bool = False) -> None:
+        if on_device:
+            _check(load().sv_batch_set_params(_vp(self.handle), _vp(params), 1))
+        else:
+            p = np.ascontiguousarray(params, dtype=np.float64).ravel()
+            assert p.size == self.n_params
+            _check(load().sv_batch_set_params(_vp(self.handle), p.ctypes.data_as(_vp), 0))
+
+    def run(self) -> np.ndarray:
+        out = np.zeros(self.count, dtype=np.float64)
+        _check(load().sv_batch_run(_vp(self.handle), out.ctypes.data_as(_vp), 0))
+        return out
+
+    def run_device(self, out_ptr: int) -> None:
+        _check(load().sv_batch_run(_vp(self.handle), _vp(out_ptr), 1))
+
+    def status(self) -> None:
+        _check(load().sv_batch_status(_vp(self.handle)))
+
+    def set_stream(self, stream: int) -> None:
+        _check(load().sv_batch_set_stream(_vp(self.handle), _vp(stream)))
+
+    def autotune(self) -> float:
+        ms = ctypes.c_double()
+        _check(load().sv_batch_autotune(_vp(self.handle), ctypes.byref(ms)))
+        return ms.value
+
+    def info(self):
+        items, ctas, tbits, wave, graph = ctypes.c_int64(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int64(), ctypes.c_int()
+        _check(load().sv_batch_info(_vp(self.handle), ctypes.byref(items), ctypes.byref(ctas), ctypes.byref(tbits),
+                                    ctypes.byref(wave), ctypes.byref(graph)))
+        return {"work_items": items.value, "ctas": ctas.value, "tile_bits": tbits.value,
+                "wave_bytes": wave.value, "graph": bool(graph.value)}
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            _check(load().sv_batch_destroy(_vp(self.handle)))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def sv_expval_static(device_ptr: int, n: int, dtype: int, obs: "PauliSums", stream: int = 0) -> np.ndarray:

@@ -1306,6 +1306,285 @@ sv_status sync_state(sv_state *s) {
 
 }  // namespace
 
+
+// ---- batched circuits (S9) ----------------------------------------------------------
+struct sv_batch {
+  sv_dtype dt = SV_C64;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int n_circ = 0;
+  // inputs, kept for re-planning by the autotuner
+  std::vector<int> nq;
+  std::vector<std::vector<sv_op>> ops;
+  std::vector<int> np;
+  std::vector<std::vector<double>> umat;
+  std::vector<std::vector<ZTerm>> zterms_wire;  // z as wire masks until planned
+  std::vector<uint64_t> basis;
+  int total_params = 0;
+  // plan
+  int tile_cap = 0;          // tile bits cap (autotuned)
+  int64_t wave_bytes = 64ll << 20;
+  int n_segs = 0, n_pass = 0, n_slots = 0, max_T = 1, max_terms = 1, max_k = 1, grid = 1;
+  int64_t total_items = 0, n_partials = 0;
+  int no_publish = -1;
+  unsigned long long timeout_ns = 2000000000ull;
+  // device memory
+  void *tables = nullptr;
+  size_t tables_bytes = 0;
+  void *states = nullptr;
+  size_t states_bytes = 0;
+  void *work = nullptr;
+  size_t work_bytes = 0;
+  BatchCircuit *d_circs = nullptr;
+  PassDev *d_passes = nullptr;
+  OpDev *d_ops = nullptr;
+  MatSlot *d_slots = nullptr;
+  void *d_mats = nullptr;
+  double *d_params = nullptr, *d_user = nullptr;
+  BatchSeg *d_segs = nullptr;
+  ZTerm *d_terms = nullptr;
+  double *d_partials = nullptr, *d_out = nullptr;
+  int *d_done = nullptr, *d_err = nullptr;
+  unsigned long long *d_head = nullptr;
+  bool params_set = false;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  bool use_graph = true;
+};
+
+namespace {
+
+void batch_free_plan(sv_batch *b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+  dev_free(b->tables, b->tables_bytes);
+  dev_free(b->work, b->work_bytes);
+  b->tables = b->work = nullptr;
+  b->tables_bytes = b->work_bytes = 0;
+}
+
+// Plan every circuit with tile cap `tcap` and L2 waves of `wave` bytes; upload tables.
+sv_status batch_plan(sv_batch *b, int tcap, int64_t wave) {
+  const Ops &K = ops_for(b->dt);
+  std::vector<BatchCircuit> circs(b->n_circ);
+  std::vector<PassDev> passes;
+  std::vector<OpDev> dops;
+  std::vector<ZTerm> terms;
+  SlotTable st;
+  std::vector<double> user;
+  int param_off = 0;
+  uint64_t state_off = 0;
+  int64_t part_off = 0;
+  int max_T = 1, max_terms = 1, max_k = 1;
+  for (int i = 0; i < b->n_circ; ++i) {
+    const int n = b->nq[i];
+    const int64_t uoff = (int64_t)user.size() / 2;
+    user.insert(user.end(), b->umat[i].begin(), b->umat[i].end());
+    std::vector<HOp> hops;
+    for (const sv_op &o : b->ops[i]) {
+      HOp h = to_hop(o, b->umat[i].empty() ? nullptr : b->umat[i].data());
+      for (int a = 0; a < 3; ++a)
+        if (h.pidx[a] >= 0) h.pidx[a] += param_off;
+      h.msrc += uoff;
+      if (!h.diag && h.k > kMaxTileTargets)
+        return fail(SV_ERR_UNSUPPORTED, "batch circuit %d: dense matrix on more than %d wires", i, kMaxTileTargets);
+      hops.push_back(h);
+    }
+    const int T = std::min(std::min(tcap, K.Tf), n);
+    Plan P = plan_passes(n, hops, T, K.nlow_pref, 1 << 30, false, st);
+    if (sv_status e = check_plan(P, n, K.nlow_pref)) return e;
+    BatchCircuit &c = circs[i];
+    memset(&c, 0, sizeof(c));
+    c.n = n;
+    c.pass_begin = (int)passes.size();
+    const int op_base = (int)dops.size();
+    for (PassDev pd : P.passes) {
+      pd.op_begin += op_base;
+      pd.op_end += op_base;
+      max_k = std::max(max_k, pd.max_k);
+      passes.push_back(pd);
+    }
+    if (P.passes.empty()) {  // empty tape: one pass without ops carries the measurement
+      PassDev pd = make_pass(n, fill_bits(low_bits(n, T, K.nlow_pref), n, T, K.nlow_pref));
+      pd.op_begin = pd.op_end = op_base;
+      passes.push_back(pd);
+    }
+    dops.insert(dops.end(), P.ops.begin(), P.ops.end());
+    c.n_pass = (int)passes.size() - c.pass_begin;
+    c.tiles = 1 << (n - T);
+    c.term_begin = (int)terms.size();
+    for (const ZTerm &z : b->zterms_wire[i]) terms.push_back({wire_mask_to_global(z.z, n), z.coeff});
+    c.n_terms = (int)terms.size() - c.term_begin;
+    c.out = i;
+    c.part_begin = part_off;
+    part_off += (int64_t)c.n_terms * c.tiles;
+    c.state_off = state_off;
+    state_off += 1ull << n;
+    c.basis = b->basis[i];
+    max_T = std::max(max_T, T);
+    max_terms = std::max(max_terms, c.n_terms);
+    param_off += b->np[i];
+  }
+  if (max_terms > 2048) return fail(SV_ERR_UNSUPPORTED, "batch: more than 2048 Z words in one observable");
+  // segments: waves of circuits whose states fit in `wave` bytes; inside a wave
+  // pass p of every circuit precedes pass p + 1 of any circuit
+  std::vector<BatchSeg> segs;
+  int64_t items = 0;
+  int c0 = 0;
+  while (c0 < b->n_circ) {
+    int c1 = c0;
+    int64_t bytes = 0;
+    while (c1 < b->n_circ && (c1 == c0 || bytes + ((int64_t)K.amp_bytes << circs[c1].n) <= wave)) {
+      bytes += (int64_t)K.amp_bytes << circs[c1].n;
+      ++c1;
+    }
+    int maxp = 0;
+    for (int c = c0; c < c1; ++c) maxp = std::max(maxp, circs[c].n_pass);
+    for (int pp = 0; pp < maxp; ++pp)
+      for (int c = c0; c < c1; ++c) {
+        if (pp >= circs[c].n_pass) continue;
+        BatchSeg sg;
+        memset(&sg, 0, sizeof(sg));
+        sg.first_item = items;
+        sg.circ = c;
+        sg.pass = pp;
+        sg.ntiles = circs[c].tiles;
+        segs.push_back(sg);
+        items += sg.ntiles;
+      }
+    c0 = c1;
+  }
+
+  batch_free_plan(b);
+  b->tile_cap = tcap;
+  b->wave_bytes = wave;
+  b->n_segs = (int)segs.size();
+  b->n_pass = (int)passes.size();
+  b->n_slots = (int)st.slots.size();
+  b->max_T = max_T;
+  b->max_terms = max_terms;
+  b->max_k = max_k;
+  b->total_items = items;
+  b->n_partials = part_off;
+  const int sms = sm_count();
+  const int per_sm = b->dt == SV_C64 ? Launch<float>::batch_blocks_per_sm(max_T, max_terms, max_k)
+                                     : Launch<double>::batch_blocks_per_sm(max_T, max_terms, max_k);
+  b->grid = (int)std::max<int64_t>(1, std::min<int64_t>(items, (int64_t)sms * per_sm));
+  if (const char *e = getenv("SV_BATCH_DEBUG_NO_PUBLISH")) b->no_publish = atoi(e);
+  if (const char *e = getenv("SV_BATCH_TIMEOUT_MS")) b->timeout_ns = 1000000ull * (unsigned long long)atoll(e);
+
+  auto sz = [](size_t count, size_t elem) { return align256(count * elem); };
+  size_t total = sz(circs.size(), sizeof(BatchCircuit)) + sz(passes.size(), sizeof(PassDev)) +
+                 sz(dops.size(), sizeof(OpDev)) + sz(st.slots.size(), sizeof(MatSlot)) + sz(st.entries, K.amp_bytes) +
+                 sz(std::max(b->total_params, 1), 8) + sz(std::max<size_t>(user.size(), 1), 8) +
+                 sz(segs.size(), sizeof(BatchSeg)) + sz(std::max<size_t>(terms.size(), 1), sizeof(ZTerm));
+  if (sv_status e = dev_alloc(&b->tables, total)) return e;
+  b->tables_bytes = total;
+  std::vector<char> host(total, 0);
+  size_t cur = 0;
+  auto put = [&](const void *src, size_t count, size_t elem) -> char * {
+    char *d = (char *)b->tables + cur;
+    if (count && src) memcpy(host.data() + cur, src, count * elem);
+    cur += align256(count * elem);
+    return d;
+  };
+  b->d_circs = (BatchCircuit *)put(circs.data(), circs.size(), sizeof(BatchCircuit));
+  b->d_passes = (PassDev *)put(passes.data(), passes.size(), sizeof(PassDev));
+  b->d_ops = (OpDev *)put(dops.data(), dops.size(), sizeof(OpDev));
+  b->d_slots = (MatSlot *)put(st.slots.data(), st.slots.size(), sizeof(MatSlot));
+  b->d_mats = put(nullptr, st.entries, K.amp_bytes);
+  b->d_params = (double *)put(nullptr, std::max(b->total_params, 1), 8);
+  b->d_user = (double *)put(user.data(), std::max<size_t>(user.size(), 1), 8);
+  b->d_segs = (BatchSeg *)put(segs.data(), segs.size(), sizeof(BatchSeg));
+  b->d_terms = (ZTerm *)put(terms.data(), std::max<size_t>(terms.size(), 1), sizeof(ZTerm));
+  // the parameters survive re-planning: keep the previous values on the host side
+  cudaError_t e = cudaMemcpyAsync(b->tables, host.data(), total, cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "uploading batch tables");
+
+  const size_t wtotal = align256((size_t)std::max<int64_t>(part_off, 1) * 8) + align256((size_t)b->n_circ * 8) +
+                        align256((size_t)b->n_pass * 4) + 256 + 256;
+  if (sv_status e2 = dev_alloc(&b->work, wtotal)) return e2;
+  b->work_bytes = wtotal;
+  char *w = (char *)b->work;
+  b->d_partials = (double *)w;
+  w += align256((size_t)std::max<int64_t>(part_off, 1) * 8);
+  b->d_out = (double *)w;
+  w += align256((size_t)b->n_circ * 8);
+  b->d_done = (int *)w;
+  w += align256((size_t)b->n_pass * 4);
+  b->d_head = (unsigned long long *)w;
+  w += 256;
+  b->d_err = (int *)w;
+  if (!b->states) {
+    b->states_bytes = (size_t)state_off * K.amp_bytes;
+    if (sv_status e3 = dev_alloc(&b->states, b->states_bytes)) return e3;
+  }
+  return SV_OK;
+}
+
+// The launches of one run, in stream order (captured into the graph).
+sv_status batch_enqueue(sv_batch *b) {
+  const Ops &K = ops_for(b->dt);
+  cudaStream_t s = b->stream;
+  cudaError_t e = cudaMemsetAsync(b->d_done, 0, (size_t)b->n_pass * 4, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_head, 0, 8, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_err, 0, 4, s);
+  if (e == cudaSuccess) e = K.build_matrices(b->d_slots, b->n_slots, b->d_params, b->d_user, b->d_mats, s);
+  if (e == cudaSuccess)
+    e = b->dt == SV_C64
+            ? Launch<float>::batch(b->states, b->d_circs, b->d_passes, b->d_ops, b->d_mats, b->d_segs, b->n_segs,
+                                   b->total_items, b->d_terms, b->d_partials, b->d_done, b->d_head, b->d_err, 0,
+                                   b->timeout_ns, b->max_T, b->max_terms, b->max_k, b->no_publish, b->grid, s)
+            : Launch<double>::batch(b->states, b->d_circs, b->d_passes, b->d_ops, b->d_mats, b->d_segs, b->n_segs,
+                                    b->total_items, b->d_terms, b->d_partials, b->d_done, b->d_head, b->d_err, 0,
+                                    b->timeout_ns, b->max_T, b->max_terms, b->max_k, b->no_publish, b->grid, s);
+  if (e == cudaSuccess) e = batch_reduce(b->d_circs, b->n_circ, b->d_terms, b->d_partials, b->d_out, s);
+  return e == cudaSuccess ? SV_OK : cuda_fail(e, "batch launch");
+}
+
+sv_status batch_launch(sv_batch *b) {
+  if (!b->use_graph) return batch_enqueue(b);
+  if (!b->exec) {
+    // one plain run first (sets kernel attributes outside the capture), then capture
+    if (sv_status st = batch_enqueue(b)) return st;
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "batch warm-up");
+    e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      b->use_graph = false;  // e.g. the legacy default stream: launch directly
+      return batch_enqueue(b);
+    }
+    sv_status st = batch_enqueue(b);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(b->stream, &g);
+    if (st) return st;
+    if (e != cudaSuccess) return cuda_fail(e, "batch graph capture");
+    e = cudaGraphInstantiate(&b->exec, g, 0);
+    if (e != cudaSuccess) {
+      cudaGraphDestroy(g);
+      return cuda_fail(e, "batch graph instantiate");
+    }
+    b->graph = g;
+  }
+  cudaError_t e = cudaGraphLaunch(b->exec, b->stream);
+  return e == cudaSuccess ? SV_OK : cuda_fail(e, "batch graph launch");
+}
+
+sv_status batch_check(sv_batch *b) {
+  int err = 0;
+  cudaError_t e = cudaMemcpyAsync(&err, b->d_err, 4, cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "batch run");
+  if (err) return fail(SV_ERR_TIMEOUT, "batch: a bounded wait for a previous pass gave up");
+  return SV_OK;
+}
+
+}  // namespace
+
 namespace sv {
 void set_error_message(const char *msg) { g_err = msg ? msg : ""; }
 }  // namespace sv
@@ -1673,6 +1952,202 @@ sv_status sv_kernel_timing_read(double *total_ms, int64_t *launches) {
     if (total_ms) total_ms[c] = g_class_ms[c];
     if (launches) launches[c] = g_class_n[c];
   }
+  return SV_OK;
+}
+
+
+sv_status sv_batch_create(sv_dtype dtype, int n_circuits, const int *n_qubits, const sv_tape *tapes,
+                          const sv_pauli_sum *obs, const uint64_t *basis_states, sv_batch **out) {
+  if (!out) return fail(SV_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (dtype != SV_C64 && dtype != SV_C128) return fail(SV_ERR_ARG, "unknown dtype");
+  if (n_circuits < 1 || !n_qubits || !tapes || !obs) return fail(SV_ERR_ARG, "bad batch arguments");
+  sv_batch *b = new sv_batch();
+  b->dt = dtype;
+  b->n_circ = n_circuits;
+  for (int i = 0; i < n_circuits; ++i) {
+    const int n = n_qubits[i];
+    if (n < 1 || n > 30) {
+      delete b;
+      return fail(SV_ERR_ARG, "batch circuit %d: n = %d outside [1, 30]", i, n);
+    }
+    const sv_tape &t = tapes[i];
+    if (t.n_ops < 0 || t.n_params < 0 || (t.n_ops > 0 && !t.ops)) {
+      delete b;
+      return fail(SV_ERR_ARG, "batch circuit %d: bad tape", i);
+    }
+    for (int k = 0; k < t.n_ops; ++k)
+      if (sv_status st = validate_op(n, t.ops[k], t.n_params, t.matrices, t.n_matrix_entries, nullptr, false)) {
+        delete b;
+        g_err = "batch circuit " + std::to_string(i) + " op " + std::to_string(k) + ": " + g_err;
+        return st;
+      }
+    b->nq.push_back(n);
+    b->ops.emplace_back(t.ops, t.ops + t.n_ops);
+    b->np.push_back(t.n_params);
+    b->umat.emplace_back();
+    if (t.matrices && t.n_matrix_entries > 0) b->umat.back().assign(t.matrices, t.matrices + 2 * t.n_matrix_entries);
+    b->total_params += t.n_params;
+    const sv_pauli_sum &H = obs[i];
+    if (H.n_terms < 0 || (H.n_terms > 0 && (!H.coeffs || !H.x_mask || !H.z_mask))) {
+      delete b;
+      return fail(SV_ERR_ARG, "batch circuit %d: bad observable", i);
+    }
+    std::vector<ZTerm> zt;
+    for (int k = 0; k < H.n_terms; ++k) {
+      if (H.x_mask[k]) {
+        delete b;
+        return fail(SV_ERR_UNSUPPORTED, "batch circuit %d: observables must be Z-only Pauli words", i);
+      }
+      if ((H.z_mask[k] >> n) || !std::isfinite(H.coeffs[k])) {
+        delete b;
+        return fail(SV_ERR_ARG, "batch circuit %d: bad Z word", i);
+      }
+      zt.push_back({H.z_mask[k], H.coeffs[k]});
+    }
+    b->zterms_wire.push_back(zt);
+    const uint64_t basis = basis_states ? basis_states[i] : 0;
+    if (basis >> n) {
+      delete b;
+      return fail(SV_ERR_ARG, "batch circuit %d: basis state out of range", i);
+    }
+    b->basis.push_back(basis);
+  }
+  cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    delete b;
+    return cuda_fail(e, "batch stream");
+  }
+  b->own_stream = true;
+  const Ops &K = ops_for(dtype);
+  if (sv_status st = batch_plan(b, K.Tf, 64ll << 20)) {
+    sv_batch_destroy(b);
+    return st;
+  }
+  *out = b;
+  return SV_OK;
+}
+
+sv_status sv_batch_destroy(sv_batch *b) {
+  if (!b) return SV_OK;
+  cudaStreamSynchronize(b->stream);
+  batch_free_plan(b);
+  dev_free(b->states, b->states_bytes);
+  if (b->own_stream) cudaStreamDestroy(b->stream);
+  delete b;
+  return SV_OK;
+}
+
+sv_status sv_batch_set_stream(sv_batch *b, void *cuda_stream) {
+  if (!b) return fail(SV_ERR_ARG, "batch is NULL");
+  cudaStreamSynchronize(b->stream);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+  b->use_graph = true;
+  if (cuda_stream) {
+    if (b->own_stream) cudaStreamDestroy(b->stream);
+    b->own_stream = false;
+    b->stream = (cudaStream_t)cuda_stream;
+  } else if (!b->own_stream) {
+    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess)
+      return fail(SV_ERR_CUDA, "batch stream");
+    b->own_stream = true;
+  }
+  return SV_OK;
+}
+
+sv_status sv_batch_set_params(sv_batch *b, const double *params, int params_on_device) {
+  if (!b) return fail(SV_ERR_ARG, "batch is NULL");
+  if (b->total_params > 0) {
+    if (!params) return fail(SV_ERR_ARG, "params is NULL");
+    if (!params_on_device)
+      for (int i = 0; i < b->total_params; ++i)
+        if (!std::isfinite(params[i])) return fail(SV_ERR_ARG, "parameter %d is not finite", i);
+    cudaError_t e = cudaMemcpyAsync(b->d_params, params, (size_t)b->total_params * 8,
+                                    params_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, b->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "batch parameters");
+  }
+  b->params_set = true;
+  return SV_OK;
+}
+
+sv_status sv_batch_run(sv_batch *b, double *expvals_out, int outputs_on_device) {
+  if (!b) return fail(SV_ERR_ARG, "batch is NULL");
+  if (b->total_params > 0 && !b->params_set) return fail(SV_ERR_STATE, "batch parameters were never set");
+  if (sv_status st = batch_launch(b)) return st;
+  if (expvals_out) {
+    cudaError_t e = cudaMemcpyAsync(expvals_out, b->d_out, (size_t)b->n_circ * 8,
+                                    outputs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, b->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "batch results");
+  }
+  return outputs_on_device ? SV_OK : batch_check(b);
+}
+
+sv_status sv_batch_status(sv_batch *b) {
+  if (!b) return fail(SV_ERR_ARG, "batch is NULL");
+  return batch_check(b);
+}
+
+sv_status sv_batch_autotune(sv_batch *b, double *best_ms) {
+  if (!b) return fail(SV_ERR_ARG, "batch is NULL");
+  if (b->total_params > 0 && !b->params_set) return fail(SV_ERR_STATE, "batch parameters were never set");
+  const Ops &K = ops_for(b->dt);
+  // parameters live in the table block: keep them across re-planning
+  std::vector<double> params(std::max(b->total_params, 1));
+  if (b->total_params > 0) {
+    cudaError_t e = cudaMemcpyAsync(params.data(), b->d_params, (size_t)b->total_params * 8, cudaMemcpyDeviceToHost,
+                                    b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "autotune");
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  double best = 1e300;
+  int best_t = K.Tf;
+  int64_t best_w = b->wave_bytes;
+  const int64_t waves[4] = {16ll << 20, 32ll << 20, 64ll << 20, 128ll << 20};
+  sv_status result = SV_OK;
+  for (int t = K.Tf - 2; t <= K.Tf && !result; ++t) {
+    for (int64_t w : waves) {
+      if ((result = batch_plan(b, t, w))) break;
+      if ((result = sv_batch_set_params(b, params.data(), 0))) break;
+      b->use_graph = false;
+      if ((result = batch_enqueue(b)) || (result = batch_check(b))) break;  // warm-up
+      cudaEventRecord(e0, b->stream);
+      for (int r = 0; r < 2 && !result; ++r) result = batch_enqueue(b);
+      cudaEventRecord(e1, b->stream);
+      if (!result) result = batch_check(b);
+      if (result) break;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms / 2 < best) {
+        best = ms / 2;
+        best_t = t;
+        best_w = w;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (result) return result;
+  if (sv_status st = batch_plan(b, best_t, best_w)) return st;
+  b->use_graph = true;
+  if (sv_status st = sv_batch_set_params(b, params.data(), 0)) return st;
+  if (best_ms) *best_ms = best;
+  return SV_OK;
+}
+
+sv_status sv_batch_info(const sv_batch *b, int64_t *work_items, int *ctas, int *tile_bits, int64_t *wave_bytes,
+                        int *graph) {
+  if (!b) return fail(SV_ERR_ARG, "batch is NULL");
+  if (work_items) *work_items = b->total_items;
+  if (ctas) *ctas = b->grid;
+  if (tile_bits) *tile_bits = b->max_T;
+  if (wave_bytes) *wave_bytes = b->wave_bytes;
+  if (graph) *graph = (b->exec != nullptr) ? 1 : 0;
   return SV_OK;
 }
 

@@ -100,6 +100,32 @@ struct MatSlot {
   int64_t src;         // SV_MATRIX: offset (complex entries) of the user matrix
 };
 
+// ---- batched circuits (S9) --------------------------------------------------
+// One circuit of a batch: its passes, its Z-only observable and its state slice.
+struct BatchCircuit {
+  int32_t n;
+  int32_t pass_begin, n_pass;   // passes [pass_begin, pass_begin + n_pass) of the batch pass table
+  int32_t term_begin, n_terms;  // Z words of its observable in the batch term table
+  int32_t out;                  // index of its expectation value
+  int32_t tiles;                // tiles per pass (2^(n - T); the same T for all its passes)
+  int32_t pad;
+  int64_t part_begin;           // partials [part_begin, + n_terms * tiles): one per (term, tile)
+  uint64_t state_off;           // amplitude offset of its state in the state pool
+  uint64_t basis;               // initial basis state
+};
+
+// A run of consecutive work items: every tile of pass `pass` of circuit `circ`.
+struct BatchSeg {
+  int64_t first_item;
+  int32_t circ, pass;
+  int32_t ntiles, pad;
+};
+
+struct ZTerm {
+  uint64_t z;     // amplitude-index bits of the Z word
+  double coeff;
+};
+
 // Launchers (defined once per precision in sv_kernels_f32.cu / sv_kernels_f64.cu).
 // R = float (complex64) or double (complex128).  Every launcher returns the
 // cudaError_t of its launch.
@@ -121,6 +147,13 @@ struct Launch {
   static cudaError_t dense_k(void *psi, int n, const OpDev &op, const void *mats, int adjoint,
                              cudaStream_t st);
   static cudaError_t set_basis(void *psi, int n, uint64_t index, cudaStream_t st);
+  // Persistent batch launch: `grid` CTAs drain the work items of all segments.
+  static cudaError_t batch(void *states, const BatchCircuit *circs, const PassDev *passes, const OpDev *ops,
+                           const void *mats, const BatchSeg *segs, int n_segs, int64_t total_items,
+                           const ZTerm *terms, double *partials, int *done, unsigned long long *head, int *err,
+                           int store_final, unsigned long long timeout_ns, int max_T, int max_terms, int max_k,
+                           int no_publish, int grid, cudaStream_t st);
+  static int batch_blocks_per_sm(int max_T, int max_terms, int max_k);
   static cudaError_t copy(void *dst, const void *src, int n, cudaStream_t st);
   static int forward_smem(int T);
   static int adjoint_smem(int T);
@@ -128,6 +161,10 @@ struct Launch {
   static int max_T_forward();
   static int max_T_adjoint();
 };
+
+// Batch: out[c.out] = sum_term coeff * sum_tile partials (fixed order), one thread per circuit.
+cudaError_t batch_reduce(const BatchCircuit *circs, int n_circ, const ZTerm *terms, const double *partials,
+                         double *out, cudaStream_t st);
 
 // Message returned by sv_last_error() on the calling thread (defined in sv_api.cu).
 void set_error_message(const char *msg);

@@ -968,6 +968,163 @@ __global__ void k_copy(c_t<R> *__restrict__ dst, const c_t<R> *__restrict__ src,
 }
 
 // ---------------------------------------------------------------------------
+// Batched circuits (S9): one persistent launch drains a queue of work items
+// (circuit, pass, tile).  Items are numbered so that every tile of pass p of a
+// circuit precedes every tile of its pass p + 1; a CTA holding an item of pass
+// p + 1 waits (bounded, %globaltimer) until all tiles of pass p are done.  An
+// item is only ever taken by a running CTA, so the oldest unfinished item
+// always has its inputs and the queue cannot deadlock.  States live in L2-sized
+// waves of circuits (the item order interleaves the circuits of a wave).
+// Loads bypass L1 (ld.global.cg): another SM may have written the amplitudes
+// in the previous pass.  The first pass writes the basis state straight into
+// shared memory; the last pass adds the Z-word expectation partials of its
+// tile (one slot per term and tile, summed later in fixed order) and stores
+// the final state only when asked.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int ld_acquire(const int *p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+template <typename R>
+__device__ __forceinline__ void load_tile_cg(const c_t<R> *g, c_t<R> *s, const TileGeom &tg) {
+  if constexpr (std::is_same<R, float>::value) {
+    const int nv = tg.A >> 1;
+    for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+      const int l = v << 1;
+      reinterpret_cast<float4 *>(s)[v] = __ldcg(reinterpret_cast<const float4 *>(g + tg.gidx(l)));
+    }
+  } else {
+    for (int l = threadIdx.x; l < tg.A; l += blockDim.x) s[l] = __ldcg(g + tg.gidx(l));
+  }
+}
+
+template <typename R, int MAXK>
+__global__ void __launch_bounds__(kBlock) k_batch(c_t<R> *__restrict__ states, const BatchCircuit *__restrict__ circs,
+                                                   const PassDev *__restrict__ passes, const OpDev *__restrict__ ops,
+                                                   const c_t<R> *__restrict__ mats, const BatchSeg *__restrict__ segs,
+                                                   int n_segs, long long total_items, const ZTerm *__restrict__ terms,
+                                                   double *__restrict__ partials, int *done,
+                                                   unsigned long long *head, int *err, int store_final,
+                                                   unsigned long long timeout_ns, int max_T, int max_terms,
+                                                   int no_publish) {
+  using C = c_t<R>;
+  extern __shared__ __align__(16) unsigned char smem[];
+  C *s = reinterpret_cast<C *>(smem);
+  uint64_t *lut = reinterpret_cast<uint64_t *>(s + (1 << max_T));
+  double *accs = reinterpret_cast<double *>(lut + (1 << max_T));  // [max_terms][nwarps]
+  __shared__ long long s_item;
+  __shared__ int s_seg, s_abort;
+  __shared__ PassDev s_pass;
+  const int nwarps = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  for (;;) {
+    if (threadIdx.x == 0) {
+      s_abort = *reinterpret_cast<volatile int *>(err);
+      s_item = (long long)atomicAdd(head, 1ull);
+      // segment holding the item: last segment with first_item <= item
+      int lo = 0, hi = n_segs - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (segs[mid].first_item <= s_item)
+          lo = mid;
+        else
+          hi = mid - 1;
+      }
+      s_seg = lo;
+    }
+    __syncthreads();
+    const long long item = s_item;
+    if (item >= total_items || s_abort) break;
+    const BatchSeg sg = segs[s_seg];
+    const BatchCircuit cc = circs[sg.circ];
+    const int pidx = cc.pass_begin + sg.pass;
+    const uint64_t tile = (uint64_t)(item - sg.first_item);
+    if (threadIdx.x == 0) {
+      s_pass = passes[pidx];
+      if (sg.pass > 0) {  // all tiles of the previous pass of this circuit must be done
+        const unsigned long long t0 = global_ns();
+        while (ld_acquire(&done[pidx - 1]) < sg.ntiles) {
+          if (*reinterpret_cast<volatile int *>(err) || global_ns() - t0 > timeout_ns) {
+            atomicExch(err, 1);
+            s_abort = 1;
+            break;
+          }
+          __nanosleep(64);
+        }
+        __threadfence();
+      }
+    }
+    __syncthreads();
+    if (s_abort) break;
+    const PassDev &pass = s_pass;
+    build_lut(lut, pass);
+    TileGeom tg;
+    tg.T = pass.T;
+    tg.nlow = pass.nlow;
+    tg.A = 1 << pass.T;
+    tg.lowmask = (1u << pass.nlow) - 1u;
+    tg.lut = lut;
+    tg.base = tile_base(pass, tile);
+    C *psi = states + cc.state_off;
+    __syncthreads();
+    if (sg.pass == 0) {
+      for (int l = threadIdx.x; l < tg.A; l += blockDim.x) {
+        C v;
+        v.x = tg.gidx(l) == cc.basis ? R(1) : R(0);
+        v.y = R(0);
+        s[l] = v;
+      }
+    } else {
+      load_tile_cg<R>(psi, s, tg);
+    }
+    __syncthreads();
+    for (int o = pass.op_begin; o < pass.op_end; ++o) {
+      const OpDev &op = ops[o];
+      if (op.sync_prev && o > pass.op_begin) __syncthreads();
+      apply_op<R, MAXK>(s, tg, op, mats);
+    }
+    __syncthreads();
+    const bool last = sg.pass == cc.n_pass - 1;
+    if (last && cc.n_terms > 0) {
+      // <Z word> partial of this tile: sum_l (-1)^popcount(g & z) |psi_l|^2
+      for (int i = threadIdx.x; i < cc.n_terms * nwarps; i += blockDim.x) accs[i] = 0.0;
+      __syncthreads();
+      for (int t = 0; t < cc.n_terms; ++t) {
+        const uint64_t z = terms[cc.term_begin + t].z;
+        R acc = R(0);
+        for (int l = threadIdx.x; l < tg.A; l += blockDim.x) {
+          const C a = s[l];
+          const R pr = a.x * a.x + a.y * a.y;
+          acc += (__popcll(tg.gidx(l) & z) & 1) ? -pr : pr;
+        }
+        acc = warp_sum(acc);
+        if (lane == 0) accs[t * nwarps + warp] = (double)acc;
+      }
+      __syncthreads();
+      for (int t = threadIdx.x; t < cc.n_terms; t += blockDim.x) {
+        double v = 0.0;
+        for (int w = 0; w < nwarps; ++w) v += accs[t * nwarps + w];
+        partials[cc.part_begin + (int64_t)t * sg.ntiles + (int64_t)tile] = v;
+      }
+    }
+    if (!last || store_final) store_tile<R>(psi, s, tg);
+    __syncthreads();
+    if (threadIdx.x == 0 && pidx != no_publish) {  // no_publish >= 0 only in failure-path tests
+      __threadfence();
+      atomicAdd(&done[pidx], 1);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
 inline int lut_bytes(int T, int nlow_min) { return 8 << (T - nlow_min); }

@@ -11,10 +11,16 @@ inline int lut_bytes(const PassDev &p) { return 8 << (p.T - p.nlow); }
 constexpr int kWarps = kBlock / 32;
 constexpr int kMaxDynSmem = 227 * 1024;
 
+// Opt in to large dynamic shared memory: the per-block limit minus the
+// kernel's own static shared memory.
 template <typename Kern>
 inline void allow_big_smem(Kern k, bool &done) {
   if (!done) {
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
+    cudaFuncAttributes fa;
+    int stat = 0;
+    if (cudaFuncGetAttributes(&fa, k) == cudaSuccess) stat = (int)fa.sharedSizeBytes;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem - stat);
+    cudaGetLastError();
     done = true;
   }
 }
@@ -114,6 +120,43 @@ cudaError_t Launch<R>::set_basis(void *psi, int n, uint64_t index, cudaStream_t 
   uint64_t blocks = (N + 255) / 256;
   if (blocks > 152 * 64) blocks = 152 * 64;
   k_set_basis<R><<<(unsigned)blocks, 256, 0, st>>>(reinterpret_cast<c_t<R> *>(psi), N, index);
+  return cudaGetLastError();
+}
+
+template <typename R>
+int Launch<R>::batch_blocks_per_sm(int max_T, int max_terms, int max_k) {
+  const int smem = (int)((sizeof(c_t<R>) + 8) << max_T) + max_terms * detail::kWarps * 8;
+  int nb = 0;
+  cudaError_t e = max_k <= 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<R, 2>, kBlock, smem)
+                             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<R, 4>, kBlock, smem);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  return nb > 0 ? nb : 1;
+}
+
+template <typename R>
+cudaError_t Launch<R>::batch(void *states, const BatchCircuit *circs, const PassDev *passes, const OpDev *ops,
+                             const void *mats, const BatchSeg *segs, int n_segs, int64_t total_items,
+                             const ZTerm *terms, double *partials, int *done, unsigned long long *head, int *err,
+                             int store_final, unsigned long long timeout_ns, int max_T, int max_terms, int max_k,
+                             int no_publish, int grid, cudaStream_t st) {
+  static bool attr2 = false, attr4 = false;
+  const int smem = (int)((sizeof(c_t<R>) + 8) << max_T) + max_terms * detail::kWarps * 8;
+  if (max_k <= 2) {
+    detail::allow_big_smem(k_batch<R, 2>, attr2);
+    k_batch<R, 2><<<grid, kBlock, smem, st>>>(reinterpret_cast<c_t<R> *>(states), circs, passes, ops,
+                                               reinterpret_cast<const c_t<R> *>(mats), segs, n_segs,
+                                               (long long)total_items, terms, partials, done, head, err, store_final,
+                                               timeout_ns, max_T, max_terms, no_publish);
+  } else {
+    detail::allow_big_smem(k_batch<R, 4>, attr4);
+    k_batch<R, 4><<<grid, kBlock, smem, st>>>(reinterpret_cast<c_t<R> *>(states), circs, passes, ops,
+                                               reinterpret_cast<const c_t<R> *>(mats), segs, n_segs,
+                                               (long long)total_items, terms, partials, done, head, err, store_final,
+                                               timeout_ns, max_T, max_terms, no_publish);
+  }
   return cudaGetLastError();
 }
 
