@@ -42,7 +42,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--dtype", choices=["c128", "c64"], default="c128")
+    ap.add_argument("--dtype", choices=["c128", "c64", "c128df"], default="c128",
+                    help="c128: FP64 arithmetic; c128df: complex128 storage, double-float arithmetic")
     ap.add_argument("--qubits", type=int, default=N_QUBITS, help="smaller sizes are for profiling captures only")
     ap.add_argument("--layers", type=int, default=LAYERS)
     ap.add_argument("--no-e2e", action="store_true")
@@ -169,6 +170,157 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
+# side measurements of the other workload shapes (rank 0, untimed by the contract)
+# ---------------------------------------------------------------------------
+def _timed(fn, reps, stream):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    fn()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def extra_gates(hbm_peak):
+    """Per-gate pass at 30 qubits (RX, Hadamard, CNOT on several target wires)."""
+    import torch
+    from paper_2403_02512_gb300.torch_api import Program, StateVector
+    from workloads import Op
+    out = {}
+    for dtype in ("c128", "c64"):
+        n = 30
+        sv = StateVector(n, dtype)
+        V = (16 if dtype == "c128" else 8) << n
+        rows = []
+        for name, wires in (("RX", [0]), ("RX", [15]), ("RX", [29]), ("Hadamard", [29]), ("PauliX", [0]),
+                            ("PauliX", [29])):
+            ctrl = () if name != "PauliX" else ((wires[0] + 1) % n,)
+            op = Op(name, tuple(wires), (0,) if name == "RX" else (), ctrl)
+            prog = Program(sv, [op], 1 if name == "RX" else 0)
+            prog.set_params([0.3] if name == "RX" else [])
+            ms = _timed(lambda: prog.forward(reset=False), 5, torch.cuda.current_stream())
+            moved = 2.0 * V
+            alg = moved / 2 if ctrl else moved  # Alg. 2: a controlled gate touches half the pairs
+            rows.append({"gate": ("CNOT" if ctrl else name), "target_wire": wires[0], "ms": ms,
+                         "gbs_moved": moved / ms / 1e6, "frac_moved": moved / ms / 1e6 / hbm_peak,
+                         "gbs_algorithmic": alg / ms / 1e6})
+            prog.close()
+        out[dtype] = rows
+        sv.close()
+        torch.cuda.empty_cache()
+    return out
+
+
+def extra_qaoa():
+    """Batched QAOA MaxCut: 512 parameter sets of one 20-node circuit and 256
+    mixed 14-22-qubit instances, complex64 with FP64 reductions, one persistent
+    graph-captured launch each; beside it the plain per-circuit complex128 form."""
+    import torch
+    from paper_2403_02512_gb300 import _lib as L
+    from paper_2403_02512_gb300.torch_api import Program, StateVector
+    from workloads import qaoa_maxcut, qaoa_mixed_instances, qaoa_param_sets
+    res = {}
+    c = qaoa_maxcut(20, 4)
+    sets = qaoa_param_sets(512, 4)
+    b = L.Batch([c] * len(sets), L.SV_C64)
+    b.set_params(sets.ravel())
+    b.autotune()
+    b.run()
+    t0 = time.perf_counter()
+    reps = 5
+    for _ in range(reps):
+        e64 = b.run()
+    dt = (time.perf_counter() - t0) / reps
+    res["qaoa20_x512_c64_batch"] = {"circuits_per_s": len(sets) / dt, "ms_per_batch": dt * 1e3, **b.info()}
+    b.close()
+    # plain per-circuit complex128 form on a sample of the same parameter sets
+    sv = StateVector(20, "c128")
+    prog = Program.from_circuit(sv, c)
+    k = 32
+    e128 = np.zeros(k)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(k):
+        prog.forward(sets[i])
+        e128[i] = float(prog.expval()[0])
+    dt128 = (time.perf_counter() - t0) / k
+    res["qaoa20_per_circuit_c128"] = {"circuits_per_s": 1.0 / dt128, "sample": k,
+                                      "max_abs_diff_c64_batch_vs_c128": float(np.abs(e64[:k] - e128).max())}
+    prog.close()
+    sv.close()
+    inst = qaoa_mixed_instances(256, 14, 22, 4)
+    b = L.Batch([ci for ci, _ in inst], L.SV_C64)
+    b.set_params(np.concatenate([pi for _, pi in inst]))
+    b.autotune()
+    b.run()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        b.run()
+    dt = (time.perf_counter() - t0) / reps
+    res["qaoa_mixed14to22_x256_c64_batch"] = {"circuits_per_s": 256 / dt, "ms_per_batch": dt * 1e3, **b.info()}
+    b.close()
+    torch.cuda.empty_cache()
+    return res
+
+
+def extra_vqe():
+    """24-qubit Givens ansatz, 2000-term Hamiltonian: forward + energy + adjoint gradient (one lambda)."""
+    import torch
+    from paper_2403_02512_gb300.torch_api import Program, StateVector
+    from workloads import vqe_givens
+    c, p = vqe_givens(24, 12, 40, 120, 2000)
+    out = {}
+    grads = {}
+    for dtype in ("c128", "c64"):
+        sv = StateVector(24, dtype, basis_state=c.basis_state)
+        prog = Program.from_circuit(sv, c)
+
+        def step():
+            prog.forward(p)
+            prog.expval()
+            return prog.vjp(np.ones(1))
+
+        ms = _timed(step, 2, torch.cuda.current_stream())
+        grads[dtype] = step().cpu().numpy()
+        out[dtype] = {"ms_energy_and_gradient": ms, "forward_passes": prog.stats()[0],
+                      "adjoint_passes": prog.stats()[1]}
+        prog.close()
+        sv.close()
+        torch.cuda.empty_cache()
+    out["c64_max_abs_gradient_diff_vs_c128"] = float(np.abs(grads["c64"] - grads["c128"]).max())
+    return out
+
+
+def extra_rycz30():
+    """30-qubit RY layers + CZ brick, <Z0 Z29>: forward + full adjoint Jacobian (600 params)."""
+    import torch
+    from paper_2403_02512_gb300.torch_api import Program, StateVector
+    from workloads import ry_cz_brick
+    c, p = ry_cz_brick(30, 20)
+    out = {}
+    for dtype in ("c128", "c64"):
+        sv = StateVector(30, dtype)
+        prog = Program.from_circuit(sv, c)
+
+        def step():
+            prog.forward(p)
+            return prog.jacobian()
+
+        ms = _timed(step, 1, torch.cuda.current_stream())
+        E, J = step()
+        out[dtype] = {"ms_forward_and_jacobian": ms, "expval": float(E[0]), "forward_passes": prog.stats()[0],
+                      "adjoint_passes": prog.stats()[1], "J_sum": float(J.sum())}
+        prog.close()
+        sv.close()
+        torch.cuda.empty_cache()
+    return out
+
+
+# ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
 def run_ours(args):
@@ -239,7 +391,7 @@ def run_ours(args):
             kt = L.sv_kernel_timing_read()
         fp, ap, _ = prog.stats()
         out = {"ms": ms, "launches": launches, "kt": kt, "clocks": clk, "fwd_passes": fp, "adj_passes": ap,
-               "J": J, "E": E, "vec_bytes": (16 if dtype == "c128" else 8) << NQ}
+               "J": J, "E": E, "vec_bytes": (8 if dtype == "c64" else 16) << NQ}
         prog.close()
         sv.close()
         del params
@@ -269,8 +421,10 @@ def run_ours(args):
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     e2e = None
     if not args.no_e2e:
-        dt = L.SV_C128 if args.dtype == "c128" else L.SV_C64
+        dt = L.SV_C64 if args.dtype == "c64" else L.SV_C128
         h = L.sv_create(NQ, dt)
+        if args.dtype == "c128df":
+            L.sv_set_compute(h, L.SV_COMPUTE_DOUBLE_FLOAT)
         L.sv_set_stream(h, torch.cuda.current_stream().cuda_stream)
         tape, obs = L.Tape(c.ops, P), L.PauliSums(c.observables)
         pin = torch.tensor(p, dtype=torch.float64).pin_memory()
@@ -297,10 +451,17 @@ def run_ours(args):
 
     extras = {}
     if not args.no_extras and rank == 0:
-        other = "c64" if args.dtype == "c128" else "c128"
-        o = measure(other, max(2, args.steps // 2), 2, timing=False)
-        dJ = float(np.abs(o["J"].cpu().numpy() - main["J"].cpu().numpy()).max())
-        extras[other] = {"ms_per_step": o["ms"], "max_abs_jacobian_diff_vs_" + args.dtype: dJ}
+        for other in [d for d in ("c128", "c128df", "c64") if d != args.dtype]:
+            o = measure(other, max(2, args.steps // 2), 2, timing=False)
+            dJ = float(np.abs(o["J"].cpu().numpy() - main["J"].cpu().numpy()).max())
+            extras[other] = {"ms_per_step": o["ms"], "max_abs_jacobian_diff_vs_" + args.dtype: dJ}
+            del o
+            torch.cuda.empty_cache()
+        if NQ == N_QUBITS:
+            extras["gate_pass_n30"] = extra_gates(hbm_peak)
+            extras["qaoa_batched"] = extra_qaoa()
+            extras["vqe24_2000_terms"] = extra_vqe()
+            extras["rycz30"] = extra_rycz30()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -311,7 +472,7 @@ def run_ours(args):
     if rank == 0:
         line = {"metric": METRIC, "value": ms / world if world > 1 else ms, "unit": "ms", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.dtype == "c128" else "f32",
+                "scaling": "weak", "vs_baseline": None, "dtype": {"c128": "f64", "c64": "f32", "c128df": "df64 (f32 pairs; complex128 storage)"}[args.dtype],
                 "data": "synthetic",
                 "config": {"workload": WORKLOAD if (NQ, args.layers) == (N_QUBITS, LAYERS) else
                            f"sel{NQ} ({args.layers} layers; reduced size for profiling)",

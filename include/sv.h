@@ -168,6 +168,17 @@ sv_status sv_set_stream(sv_state *s, void *cuda_stream);
  * NULL / 0 returns to library-owned workspace. */
 sv_status sv_set_workspace(sv_state *s, void *device_ptr, size_t bytes);
 
+/* Arithmetic of a complex128 state (its storage stays IEEE complex128):
+ *   SV_COMPUTE_NATIVE (default) -- FP64;
+ *   SV_COMPUTE_DOUBLE_FLOAT     -- double-float: each real as an unevaluated sum of two
+ *     FP32 values (~48 significant bits, errors ~1e-14 relative per operation), run on the
+ *     FP32 pipe, which is 62x the FP64 rate on a GB300; expectation values and Jacobians
+ *     are still reduced in FP64.
+ * complex64 states accept only SV_COMPUTE_NATIVE.  Planned programs follow the state's
+ * current mode (their gate matrices are rebuilt when it changes). */
+typedef enum { SV_COMPUTE_NATIVE = 0, SV_COMPUTE_DOUBLE_FLOAT = 1 } sv_compute;
+sv_status sv_set_compute(sv_state *s, int compute);
+
 /* Query: n, dtype and the device pointer of the amplitudes (any may be NULL). */
 sv_status sv_info(const sv_state *s, int *n, sv_dtype *dtype, void **device_ptr);
 

@@ -23,6 +23,7 @@ SV_MAX_CONTROLS = 8
 SV_MAX_QUBITS = 34
 
 SV_C64, SV_C128 = 0, 1
+SV_COMPUTE_NATIVE, SV_COMPUTE_DOUBLE_FLOAT = 0, 1
 
 STATUS = {0: "SV_OK", 1: "SV_ERR_ARG", 2: "SV_ERR_OOM", 3: "SV_ERR_CUDA", 4: "SV_ERR_TIMEOUT",
           5: "SV_ERR_UNSUPPORTED", 6: "SV_ERR_STATE"}
@@ -90,6 +91,7 @@ PROTOTYPES = {
     "sv_set_stream": (ctypes.c_int, [_vp, _vp]),
     "sv_set_workspace": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t]),
     "sv_info": (ctypes.c_int, [_vp, _ip, _ip, ctypes.POINTER(_vp)]),
+    "sv_set_compute": (ctypes.c_int, [_vp, ctypes.c_int]),
     "sv_reset": (ctypes.c_int, [_vp, ctypes.c_uint64]),
     "sv_set_state": (ctypes.c_int, [_vp, _vp]),
     "sv_get_state": (ctypes.c_int, [_vp, _vp]),
@@ -207,6 +209,10 @@ def sv_set_stream(h: int, stream: int) -> None:
 
 def sv_set_workspace(h: int, device_ptr: int, nbytes: int) -> None:
     _check(load().sv_set_workspace(_vp(h), _vp(device_ptr), int(nbytes)))
+
+
+def sv_set_compute(h: int, compute: int) -> None:
+    _check(load().sv_set_compute(_vp(h), int(compute)))
 
 
 def sv_info(h: int):

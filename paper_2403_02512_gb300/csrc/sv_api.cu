@@ -11,6 +11,7 @@
 #include <string>
 #include <vector>
 
+#include "df64.cuh"
 #include "sv.h"
 #include "sv_internal.h"
 
@@ -678,6 +679,14 @@ struct Ops {
   int amp_bytes, Tf, Ta, nlow_pref;
 };
 
+const Ops &ops_df() {
+  static const Ops d = {Launch<df>::build_matrices, Launch<df>::tile_forward, Launch<df>::tile_adjoint,
+                        Launch<df>::expval_pass,    Launch<df>::lambda_pass,  Launch<df>::dense_k,
+                        Launch<df>::set_basis,      Launch<df>::copy,
+                        16, Launch<df>::max_T_forward(), Launch<df>::max_T_adjoint(), 3};
+  return d;
+}
+
 const Ops &ops_for(sv_dtype dt) {
   static const Ops f32 = {Launch<float>::build_matrices, Launch<float>::tile_forward,
                           Launch<float>::tile_adjoint,   Launch<float>::expval_pass,
@@ -710,7 +719,14 @@ struct sv_state {
   void *tab = nullptr;       // table arena for one-shot programs
   size_t tab_bytes = 0;
   int latched = 0;
+  int compute = SV_COMPUTE_NATIVE;
 };
+
+namespace {
+const Ops &ops_of(const sv_state *s) {
+  return (s->dt == SV_C128 && s->compute == SV_COMPUTE_DOUBLE_FLOAT) ? ops_df() : ops_for(s->dt);
+}
+}  // namespace
 
 namespace {
 
@@ -796,6 +812,7 @@ struct sv_program {
   int grid_l(int mcc) const { return (int)std::max<uint64_t>(1, std::min<uint64_t>(tiles_l, ctas_l / std::max(1, mcc))); }
   int launches = 0;
   bool params_set = false;  // gate matrices built at least once
+  int mats_compute = SV_COMPUTE_NATIVE;
 };
 
 namespace {
@@ -816,7 +833,7 @@ sv_status build_program(sv_state *s, const sv_tape *tape, const sv_pauli_sum *ob
                         const double *host_params, bool one_shot, sv_program **out) {
   *out = nullptr;
   const int n = s->n;
-  const Ops &K = ops_for(s->dt);
+  const Ops &K = ops_of(s);
   int n_ops = 0, n_params = 0;
   const sv_op *ops = nullptr;
   const double *umats = nullptr;
@@ -1056,7 +1073,7 @@ sv_status build_program(sv_state *s, const sv_tape *tape, const sv_pauli_sum *ob
 
 sv_status program_set_params(sv_program *p, const double *params, int on_device) {
   sv_state *s = p->s;
-  const Ops &K = ops_for(s->dt);
+  const Ops &K = ops_of(s);
   if (p->n_params > 0) {
     if (!params) return fail(SV_ERR_ARG, "params is NULL but the tape has %d parameters", p->n_params);
     if (!on_device)
@@ -1074,7 +1091,23 @@ sv_status program_set_params(sv_program *p, const double *params, int on_device)
                       "build_matrices");
   }
   p->launches += p->n_slots > 0;
-  if (!st) p->params_set = true;
+  if (!st) {
+    p->params_set = true;
+    p->mats_compute = s->compute;
+  }
+  return st;
+}
+
+// Gate matrices are stored in the compute type: rebuild them if the state's
+// arithmetic mode changed since the parameters were set.
+sv_status ensure_mats(sv_program *p) {
+  sv_state *s = p->s;
+  if (!p->params_set || p->mats_compute == s->compute || p->n_slots == 0) return SV_OK;
+  LaunchTimer t(s->stream, 5);
+  sv_status st = after_launch(s, ops_of(s).build_matrices(p->d_slots, p->n_slots, p->d_params, p->d_user, p->d_mats,
+                                                           s->stream),
+                              "build_matrices");
+  if (!st) p->mats_compute = s->compute;
   return st;
 }
 
@@ -1086,7 +1119,8 @@ sv_status require_params(const sv_program *p) {
 
 sv_status run_steps_forward(sv_program *p, void *psi) {
   sv_state *s = p->s;
-  const Ops &K = ops_for(s->dt);
+  if (sv_status r = ensure_mats(p)) return r;
+  const Ops &K = ops_of(s);
   for (const Step &st : p->fwd.steps) {
     cudaError_t e;
     if (st.dense_k) {
@@ -1148,7 +1182,7 @@ sv_status jac_workspace(sv_program *p, JacWs &w) {
 
 sv_status run_expval(sv_program *p, const void *psi, const JacWs &w) {
   sv_state *s = p->s;
-  const Ops &K = ops_for(s->dt);
+  const Ops &K = ops_of(s);
   for (size_t q = 0; q + 1 < p->tp.begin.size(); ++q) {
     const int b = p->tp.begin[q], cnt = p->tp.begin[q + 1] - b;
     if (cnt == 0) continue;
@@ -1181,7 +1215,7 @@ template <typename BeginFn>
 sv_status run_sweep(sv_program *p, const JacWs &w, int mcc, int j0, int ldc, const TermDev *lam_terms,
                     BeginFn lam_begin) {
   sv_state *s = p->s;
-  const Ops &K = ops_for(s->dt);
+  const Ops &K = ops_of(s);
   const int n = s->n;
   const size_t V = s->bytes;
   const int npass_e = (int)p->tp.passes.size();
@@ -1243,6 +1277,7 @@ bool needs_sweep(const sv_program *p) { return p->adj.n_train > 0 || !p->adj.dk_
 
 sv_status run_jacobian(sv_program *p, const JacWs &w) {
   sv_state *s = p->s;
+  if (sv_status r = ensure_mats(p)) return r;
   if (sv_status r = run_expval(p, s->psi, w)) return r;
   if (needs_sweep(p)) {
     const int npass_e = (int)p->tp.passes.size();
@@ -1267,6 +1302,7 @@ sv_status run_jacobian(sv_program *p, const JacWs &w) {
 // VJP: lambda = sum_j g_j H_j psi, one sweep, one contrib column.
 sv_status run_vjp(sv_program *p, const JacWs &w, const double *g) {
   sv_state *s = p->s;
+  if (sv_status r = ensure_mats(p)) return r;
   std::vector<TermDev> &vt = p->vjp_host;
   for (size_t q = 0; q < vt.size(); ++q) vt[q].coeff = p->terms[p->tp.placed[q]].coeff * g[p->terms[p->tp.placed[q]].obs];
   cudaError_t e = cudaMemcpyAsync(p->d_vjp_terms, vt.data(), vt.size() * sizeof(TermDev), cudaMemcpyHostToDevice,
@@ -1666,6 +1702,16 @@ sv_status sv_set_workspace(sv_state *s, void *device_ptr, size_t bytes) {
   if (device_ptr && ((uintptr_t)device_ptr & 255)) return fail(SV_ERR_ARG, "workspace must be 256-byte aligned");
   s->user_ws = device_ptr;
   s->user_ws_bytes = device_ptr ? bytes : 0;
+  return SV_OK;
+}
+
+sv_status sv_set_compute(sv_state *s, int compute) {
+  if (!s) return fail(SV_ERR_ARG, "state is NULL");
+  if (compute != SV_COMPUTE_NATIVE && compute != SV_COMPUTE_DOUBLE_FLOAT)
+    return fail(SV_ERR_ARG, "unknown compute mode %d", compute);
+  if (compute == SV_COMPUTE_DOUBLE_FLOAT && s->dt != SV_C128)
+    return fail(SV_ERR_ARG, "double-float arithmetic applies to complex128 states only");
+  s->compute = compute;
   return SV_OK;
 }
 

@@ -20,13 +20,57 @@
 #include <cstdint>
 #include <type_traits>
 
+#include "df64.cuh"
 #include "sv_internal.h"
 #include "sv.h"
 
 namespace sv {
 
+// Compute type R -> complex type in registers / shared memory (c_t) and the
+// amplitude type in global memory (g_t).  R = df computes complex128 states in
+// double-float arithmetic: global double2, converted on tile load / store.
 template <typename R>
-using c_t = typename std::conditional<std::is_same<R, float>::value, float2, double2>::type;
+struct Types;
+template <>
+struct Types<float> {
+  using C = float2;
+  using G = float2;
+};
+template <>
+struct Types<double> {
+  using C = double2;
+  using G = double2;
+};
+template <>
+struct Types<df> {
+  using C = dfc;
+  using G = double2;
+};
+template <typename R>
+using c_t = typename Types<R>::C;
+template <typename R>
+using g_t = typename Types<R>::G;
+
+template <typename R>
+__device__ __forceinline__ c_t<R> to_c(g_t<R> v) {
+  if constexpr (std::is_same<R, df>::value) {
+    dfc r;
+    r.x = df(v.x);
+    r.y = df(v.y);
+    return r;
+  } else {
+    return v;
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ g_t<R> to_g(c_t<R> v) {
+  if constexpr (std::is_same<R, df>::value) {
+    return make_double2((double)v.x, (double)v.y);
+  } else {
+    return v;
+  }
+}
 
 template <typename C>
 __device__ __forceinline__ C cmul(C a, C b) {
@@ -74,6 +118,9 @@ struct Acc {
   __device__ __forceinline__ R value() const { return s; }
 };
 
+__device__ __forceinline__ float to_r(float v, float) { return v; }
+__device__ __forceinline__ double to_r(float v, double) { return (double)v; }
+
 // Per-warp accumulator slot in shared memory, summed over tiles: a
 // double-float pair (hi, lo) updated with TwoSum for complex64 (no FP64
 // instruction in the hot loop), a plain double for complex128.
@@ -99,6 +146,22 @@ template <>
 struct WarpAcc<double> {
   static __device__ __forceinline__ void add(double *slot, double v) { *slot += v; }
   static __device__ __forceinline__ double read(const double *slot) { return *slot; }
+};
+
+__device__ __forceinline__ df warp_sum(df v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+    v = v + df_make(__shfl_xor_sync(0xffffffffu, v.h, o), __shfl_xor_sync(0xffffffffu, v.l, o));
+  return v;
+}
+
+template <>
+struct WarpAcc<df> {
+  static __device__ __forceinline__ void add(double *slot, df v) {
+    df *p = reinterpret_cast<df *>(slot);
+    *p = *p + v;
+  }
+  static __device__ __forceinline__ double read(const double *slot) { return (double)*reinterpret_cast<const df *>(slot); }
 };
 
 __device__ __forceinline__ float warp_sum(float v) {
@@ -146,7 +209,7 @@ __device__ __forceinline__ uint64_t tile_base(const PassDev &p, uint64_t tile) {
 
 // 128-bit coalesced tile load / store (c64: two amplitudes per access).
 template <typename R>
-__device__ __forceinline__ void load_tile(const c_t<R> *__restrict__ g, c_t<R> *s, const TileGeom &tg) {
+__device__ __forceinline__ void load_tile(const g_t<R> *__restrict__ g, c_t<R> *s, const TileGeom &tg) {
   if constexpr (std::is_same<R, float>::value) {
     const int nv = tg.A >> 1;
     for (int v = threadIdx.x; v < nv; v += blockDim.x) {
@@ -155,12 +218,12 @@ __device__ __forceinline__ void load_tile(const c_t<R> *__restrict__ g, c_t<R> *
       reinterpret_cast<float4 *>(s)[v] = x;
     }
   } else {
-    for (int l = threadIdx.x; l < tg.A; l += blockDim.x) s[l] = __ldg(g + tg.gidx(l));
+    for (int l = threadIdx.x; l < tg.A; l += blockDim.x) s[l] = to_c<R>(__ldg(g + tg.gidx(l)));
   }
 }
 
 template <typename R>
-__device__ __forceinline__ void load_tile_rw(const c_t<R> *g, c_t<R> *s, const TileGeom &tg) {
+__device__ __forceinline__ void load_tile_rw(const g_t<R> *g, c_t<R> *s, const TileGeom &tg) {
   // Same as load_tile without the read-only path (buffer is written by this kernel).
   if constexpr (std::is_same<R, float>::value) {
     const int nv = tg.A >> 1;
@@ -169,12 +232,12 @@ __device__ __forceinline__ void load_tile_rw(const c_t<R> *g, c_t<R> *s, const T
       reinterpret_cast<float4 *>(s)[v] = *reinterpret_cast<const float4 *>(g + tg.gidx(l));
     }
   } else {
-    for (int l = threadIdx.x; l < tg.A; l += blockDim.x) s[l] = g[tg.gidx(l)];
+    for (int l = threadIdx.x; l < tg.A; l += blockDim.x) s[l] = to_c<R>(g[tg.gidx(l)]);
   }
 }
 
 template <typename R>
-__device__ __forceinline__ void store_tile(c_t<R> *g, const c_t<R> *s, const TileGeom &tg) {
+__device__ __forceinline__ void store_tile(g_t<R> *g, const c_t<R> *s, const TileGeom &tg) {
   if constexpr (std::is_same<R, float>::value) {
     const int nv = tg.A >> 1;
     for (int v = threadIdx.x; v < nv; v += blockDim.x) {
@@ -182,7 +245,7 @@ __device__ __forceinline__ void store_tile(c_t<R> *g, const c_t<R> *s, const Til
       *reinterpret_cast<float4 *>(g + tg.gidx(l)) = reinterpret_cast<const float4 *>(s)[v];
     }
   } else {
-    for (int l = threadIdx.x; l < tg.A; l += blockDim.x) g[tg.gidx(l)] = s[l];
+    for (int l = threadIdx.x; l < tg.A; l += blockDim.x) g[tg.gidx(l)] = to_g<R>(s[l]);
   }
 }
 
@@ -250,11 +313,24 @@ __device__ __forceinline__ auto im_cx(C x, C y) -> decltype(x.x) { return x.x * 
 template <typename C>
 __device__ __forceinline__ auto re_cx(C x, C y) -> decltype(x.x) { return x.x * y.x + x.y * y.y; }
 
-// Im <l | G p> over one pair for the generator codes gX / gY.
-template <typename R>
-__device__ __forceinline__ R pair_ip(int gcode, R gs, c_t<R> pa, c_t<R> pb, c_t<R> la, c_t<R> lb) {
-  if (gcode == gX) return gs * (im_cx(la, pb) + im_cx(lb, pa));
-  return gs * (re_cx(lb, pa) - re_cx(la, pb));  // gY: (G p)_a = -i gs pb, (G p)_b = i gs pa
+// acc += Im <l | G p> / gs over one pair for the generator codes gX / gY (the
+// block scale gs is applied once per tile when the partial is flushed).
+//   gX: Im(conj(la) pb) + Im(conj(lb) pa)
+//   gY: (G p)_a = -i pb, (G p)_b = i pa  ->  Re(conj(lb) pa) - Re(conj(la) pb)
+template <typename R, int GCODE>
+__device__ __forceinline__ R pair_ip_acc(R acc, c_t<R> pa, c_t<R> pb, c_t<R> la, c_t<R> lb) {
+  if (GCODE == gX) {
+    acc = fma(la.x, pb.y, acc);
+    acc = fma(-la.y, pb.x, acc);
+    acc = fma(lb.x, pa.y, acc);
+    acc = fma(-lb.y, pa.x, acc);
+  } else {
+    acc = fma(lb.x, pa.x, acc);
+    acc = fma(lb.y, pa.y, acc);
+    acc = fma(-la.x, pb.x, acc);
+    acc = fma(-la.y, pb.y, acc);
+  }
+  return acc;
 }
 
 __device__ __forceinline__ int diag_index(const OpDev &op, uint64_t g) {
@@ -409,7 +485,7 @@ __device__ __forceinline__ void apply_op(c_t<R> *s, const TileGeom &tg, const Op
 // the same amplitudes, or the blocks are disjoint).
 // ---------------------------------------------------------------------------
 template <typename R, int MAXK>
-__global__ void __launch_bounds__(kBlock) k_tile_forward(c_t<R> *__restrict__ psi, int n, const PassDev pass,
+__global__ void __launch_bounds__(kBlock) k_tile_forward(g_t<R> *__restrict__ psi, int n, const PassDev pass,
                                                           const OpDev *__restrict__ ops,
                                                           const c_t<R> *__restrict__ mats) {
   using C = c_t<R>;
@@ -454,11 +530,11 @@ __global__ void __launch_bounds__(kBlock) k_tile_forward(c_t<R> *__restrict__ ps
 // ---------------------------------------------------------------------------
 template <typename R>
 __device__ __forceinline__ void flush_acc(Acc<R> (&acc)[kMaxLambdaPerCta], int bb, int b, int train, double *accs,
-                                          int nwarps, int warp, int lane) {
+                                          int nwarps, int warp, int lane, R scale) {
 #pragma unroll
   for (int jj = 0; jj < kMaxLambdaPerCta; ++jj) {
     if (jj < bb) {
-      const R v = warp_sum(acc[jj].value());
+      const R v = scale * warp_sum(acc[jj].value());
       if (lane == 0) WarpAcc<R>::add(&accs[(train * b + jj) * nwarps + warp], v);
     }
   }
@@ -472,7 +548,6 @@ __device__ void adj_pair_t(c_t<R> *sp, c_t<R> *sl, int bb, const TileGeom &tg, c
   if (CODE == mGen || CODE == mReal || CODE == mImOff)
 #pragma unroll
     for (int q = 0; q < 4; ++q) Mr[q] = mats[op.mat + q];
-  const R gs = (R)op.gs;
   const int ng = tg.A >> op.k;
   const bool ctl = op.cmask != 0;
   for (int g = threadIdx.x; g < ng; g += blockDim.x) {
@@ -488,7 +563,7 @@ __device__ void adj_pair_t(c_t<R> *sp, c_t<R> *sl, int bb, const TileGeom &tg, c
     for (int jj = 0; jj < kMaxLambdaPerCta; ++jj) {
       if (jj < bb) {
         C la = sl[jj * tg.A + ia], lb = sl[jj * tg.A + ib];
-        if (GCODE != gNone) acc[jj].add(pair_ip<R>(GCODE, gs, qa, qb, la, lb));
+        if (GCODE != gNone) acc[jj].s = pair_ip_acc<R, GCODE>(acc[jj].s, qa, qb, la, lb);
         pair_apply<R>(CODE, Mr, la, lb);
         sl[jj * tg.A + ia] = la;
         sl[jj * tg.A + ib] = lb;
@@ -545,12 +620,13 @@ __device__ void adj_diag_t(c_t<R> *sp, c_t<R> *sl, int bb, const TileGeom &tg, c
     const C p = sp[l];
     R gd = R(0);
     if (TRAIN) gd = (__popc(idx & op.zmask) & 1) ? gb : ga;
+    const R gpy = gd * p.y, gpx = gd * p.x;
     sp[l] = small ? cmul(p, dv) : diag_mul<R>(op, mats, idx, p);
 #pragma unroll
     for (int jj = 0; jj < kMaxLambdaPerCta; ++jj) {
       if (jj < bb) {
         const C q = sl[jj * tg.A + l];
-        if (TRAIN) acc[jj].add(gd * im_cx(q, p));
+        if (TRAIN) acc[jj].s = fma(q.x, gpy, fma(-q.y, gpx, acc[jj].s));
         sl[jj * tg.A + l] = small ? cmul(q, dv) : diag_mul<R>(op, mats, idx, q);
       }
     }
@@ -567,8 +643,8 @@ __device__ __forceinline__ void adj_diag(c_t<R> *sp, c_t<R> *sl, int bb, const T
 }
 
 template <typename R, int MAXK>
-__global__ void __launch_bounds__(kBlock, 2) k_tile_adjoint(const c_t<R> *phi_in, c_t<R> *phi_out,
-                                                          c_t<R> *__restrict__ lam_base, int n, int m, int b,
+__global__ void __launch_bounds__(kBlock, 2) k_tile_adjoint(const g_t<R> *phi_in, g_t<R> *phi_out,
+                                                          g_t<R> *__restrict__ lam_base, int n, int m, int b,
                                                           const PassDev pass, const OpDev *__restrict__ ops,
                                                           const c_t<R> *__restrict__ mats,
                                                           double *__restrict__ partials) {
@@ -612,7 +688,8 @@ __global__ void __launch_bounds__(kBlock, 2) k_tile_adjoint(const c_t<R> *phi_in
           adj_pair<R>(sp, sl, bb, tg, op, mats, acc);
         else
           adj_diag<R>(sp, sl, bb, tg, op, mats, acc);
-        if (op.train >= 0) flush_acc<R>(acc, bb, b, op.train, accs, nwarps, warp, lane);
+        if (op.train >= 0)
+          flush_acc<R>(acc, bb, b, op.train, accs, nwarps, warp, lane, op.kind == kPair ? (R)op.gs : R(1));
       }
       if (op.sync_prev && o > pass.op_begin) __syncthreads();
     }
@@ -650,7 +727,7 @@ __device__ __forceinline__ R pauli_re(c_t<R> a, c_t<R> b, int ny) {
 }
 
 template <typename R>
-__global__ void __launch_bounds__(kBlock) k_expval(const c_t<R> *__restrict__ psi, int n, const PassDev pass,
+__global__ void __launch_bounds__(kBlock) k_expval(const g_t<R> *__restrict__ psi, int n, const PassDev pass,
                                                     const TermDev *__restrict__ terms, int n_terms,
                                                     double *__restrict__ partials) {
   using C = c_t<R>;
@@ -704,7 +781,7 @@ __global__ void __launch_bounds__(kBlock) k_expval(const c_t<R> *__restrict__ ps
 // blockIdx.y = observable within the chunk; first != 0 overwrites lam.
 // ---------------------------------------------------------------------------
 template <typename R>
-__global__ void __launch_bounds__(kBlock) k_lambda(const c_t<R> *__restrict__ phi, c_t<R> *__restrict__ lam_base,
+__global__ void __launch_bounds__(kBlock) k_lambda(const g_t<R> *__restrict__ phi, g_t<R> *__restrict__ lam_base,
                                                     int n, const PassDev pass, const TermDev *__restrict__ terms,
                                                     const int32_t *__restrict__ obs_term_begin, int first) {
   using C = c_t<R>;
@@ -714,7 +791,7 @@ __global__ void __launch_bounds__(kBlock) k_lambda(const c_t<R> *__restrict__ ph
   uint64_t *lut = reinterpret_cast<uint64_t *>(s + A);
   const int o = blockIdx.y;
   const int t0 = obs_term_begin[o], t1 = obs_term_begin[o + 1];
-  C *lam = lam_base + ((size_t)o << n);
+  g_t<R> *lam = lam_base + ((size_t)o << n);
   build_lut(lut, pass);
   TileGeom tg;
   tg.T = pass.T;
@@ -735,7 +812,7 @@ __global__ void __launch_bounds__(kBlock) k_lambda(const c_t<R> *__restrict__ ph
         acc.x = R(0);
         acc.y = R(0);
       } else {
-        acc = lam[g];
+        acc = to_c<R>(lam[g]);
       }
       for (int t = t0; t < t1; ++t) {
         const TermDev tm = terms[t];
@@ -750,7 +827,7 @@ __global__ void __launch_bounds__(kBlock) k_lambda(const c_t<R> *__restrict__ ph
           default: acc.x = fma(c, b.y, acc.x); acc.y = fma(-c, b.x, acc.y); break;
         }
       }
-      lam[g] = acc;
+      lam[g] = to_g<R>(acc);
     }
     __syncthreads();
   }
@@ -761,7 +838,7 @@ __global__ void __launch_bounds__(kBlock) k_lambda(const c_t<R> *__restrict__ ph
 // output amplitude per thread: CTA stages 256 / 2^k groups in shared memory.
 // ---------------------------------------------------------------------------
 template <typename R>
-__global__ void __launch_bounds__(kBlock) k_dense_k(c_t<R> *__restrict__ psi, int n, const OpDev op,
+__global__ void __launch_bounds__(kBlock) k_dense_k(g_t<R> *__restrict__ psi, int n, const OpDev op,
                                                      const c_t<R> *__restrict__ M, int dagger) {
   using C = c_t<R>;
   __shared__ C sv[kBlock];
@@ -788,7 +865,7 @@ __global__ void __launch_bounds__(kBlock) k_dense_k(c_t<R> *__restrict__ psi, in
       i0 = ((i0 >> b) << (b + 1)) | (i0 & ((1ull << b) - 1));
     }
     const bool active = (g < ngroups) && ((i0 & op.cmask) == op.cval);
-    if (active) sv[threadIdx.x] = psi[i0 | roff];
+    if (active) sv[threadIdx.x] = to_c<R>(psi[i0 | roff]);
     __syncthreads();
     if (active) {
       C acc;
@@ -798,7 +875,7 @@ __global__ void __launch_bounds__(kBlock) k_dense_k(c_t<R> *__restrict__ psi, in
         C m = dagger ? cconj(M[c * D + r]) : M[r * D + c];
         acc = cmac(acc, m, sv[gl * D + c]);
       }
-      psi[i0 | roff] = acc;
+      psi[i0 | roff] = to_g<R>(acc);
     }
     __syncthreads();
   }
@@ -952,19 +1029,13 @@ __global__ void k_build_matrices(const MatSlot *__restrict__ slots, int n_slots,
 }
 
 template <typename R>
-__global__ void k_set_basis(c_t<R> *psi, uint64_t N, uint64_t index) {
+__global__ void k_set_basis(g_t<R> *psi, uint64_t N, uint64_t index) {
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < N; i += (uint64_t)gridDim.x * blockDim.x) {
-    c_t<R> v;
-    v.x = (i == index) ? R(1) : R(0);
-    v.y = R(0);
+    g_t<R> v;
+    v.x = (i == index) ? 1 : 0;
+    v.y = 0;
     psi[i] = v;
   }
-}
-
-template <typename R>
-__global__ void k_copy(c_t<R> *__restrict__ dst, const c_t<R> *__restrict__ src, uint64_t N) {
-  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < N; i += (uint64_t)gridDim.x * blockDim.x)
-    dst[i] = src[i];
 }
 
 // ---------------------------------------------------------------------------
@@ -994,7 +1065,7 @@ __device__ __forceinline__ unsigned long long global_ns() {
 }
 
 template <typename R>
-__device__ __forceinline__ void load_tile_cg(const c_t<R> *g, c_t<R> *s, const TileGeom &tg) {
+__device__ __forceinline__ void load_tile_cg(const g_t<R> *g, c_t<R> *s, const TileGeom &tg) {
   if constexpr (std::is_same<R, float>::value) {
     const int nv = tg.A >> 1;
     for (int v = threadIdx.x; v < nv; v += blockDim.x) {
@@ -1002,12 +1073,14 @@ __device__ __forceinline__ void load_tile_cg(const c_t<R> *g, c_t<R> *s, const T
       reinterpret_cast<float4 *>(s)[v] = __ldcg(reinterpret_cast<const float4 *>(g + tg.gidx(l)));
     }
   } else {
-    for (int l = threadIdx.x; l < tg.A; l += blockDim.x) s[l] = __ldcg(g + tg.gidx(l));
+    for (int l = threadIdx.x; l < tg.A; l += blockDim.x) s[l] = to_c<R>(__ldcg(g + tg.gidx(l)));
   }
 }
 
+constexpr int kBatchChunk = 8;  // work items a CTA takes from the queue at once
+
 template <typename R, int MAXK>
-__global__ void __launch_bounds__(kBlock) k_batch(c_t<R> *__restrict__ states, const BatchCircuit *__restrict__ circs,
+__global__ void __launch_bounds__(kBlock) k_batch(g_t<R> *__restrict__ states, const BatchCircuit *__restrict__ circs,
                                                    const PassDev *__restrict__ passes, const OpDev *__restrict__ ops,
                                                    const c_t<R> *__restrict__ mats, const BatchSeg *__restrict__ segs,
                                                    int n_segs, long long total_items, const ZTerm *__restrict__ terms,
@@ -1020,107 +1093,123 @@ __global__ void __launch_bounds__(kBlock) k_batch(c_t<R> *__restrict__ states, c
   C *s = reinterpret_cast<C *>(smem);
   uint64_t *lut = reinterpret_cast<uint64_t *>(s + (1 << max_T));
   double *accs = reinterpret_cast<double *>(lut + (1 << max_T));  // [max_terms][nwarps]
-  __shared__ long long s_item;
-  __shared__ int s_seg, s_abort;
+  __shared__ long long s_first;
+  __shared__ int s_seg, s_abort, s_new_seg;
   __shared__ PassDev s_pass;
   const int nwarps = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int cur_seg = -1;  // segment whose pass / LUT / dependency are in place
 
   for (;;) {
     if (threadIdx.x == 0) {
       s_abort = *reinterpret_cast<volatile int *>(err);
-      s_item = (long long)atomicAdd(head, 1ull);
-      // segment holding the item: last segment with first_item <= item
+      s_first = (long long)atomicAdd(head, (unsigned long long)kBatchChunk);
+    }
+    __syncthreads();
+    const long long first = s_first;
+    if (first >= total_items || s_abort) break;
+    const long long last_item = min(first + (long long)kBatchChunk, total_items);
+    if (threadIdx.x == 0) {  // segment of the chunk's first item: last segment with first_item <= item
       int lo = 0, hi = n_segs - 1;
       while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (segs[mid].first_item <= s_item)
+        if (segs[mid].first_item <= first)
           lo = mid;
         else
           hi = mid - 1;
       }
       s_seg = lo;
     }
-    __syncthreads();
-    const long long item = s_item;
-    if (item >= total_items || s_abort) break;
-    const BatchSeg sg = segs[s_seg];
-    const BatchCircuit cc = circs[sg.circ];
-    const int pidx = cc.pass_begin + sg.pass;
-    const uint64_t tile = (uint64_t)(item - sg.first_item);
-    if (threadIdx.x == 0) {
-      s_pass = passes[pidx];
-      if (sg.pass > 0) {  // all tiles of the previous pass of this circuit must be done
-        const unsigned long long t0 = global_ns();
-        while (ld_acquire(&done[pidx - 1]) < sg.ntiles) {
-          if (*reinterpret_cast<volatile int *>(err) || global_ns() - t0 > timeout_ns) {
-            atomicExch(err, 1);
-            s_abort = 1;
-            break;
+    for (long long item = first; item < last_item; ++item) {
+      if (threadIdx.x == 0) {
+        int sg_i = (item == first) ? s_seg : cur_seg;
+        while (sg_i + 1 < n_segs && segs[sg_i + 1].first_item <= item) ++sg_i;
+        s_seg = sg_i;
+        s_new_seg = sg_i != cur_seg;
+        if (s_new_seg) {
+          const BatchSeg sg = segs[sg_i];
+          const int pidx = circs[sg.circ].pass_begin + sg.pass;
+          s_pass = passes[pidx];
+          if (sg.pass > 0) {  // all tiles of the previous pass of this circuit must be done
+            const unsigned long long t0 = global_ns();
+            while (ld_acquire(&done[pidx - 1]) < sg.ntiles) {
+              if (*reinterpret_cast<volatile int *>(err) || global_ns() - t0 > timeout_ns) {
+                atomicExch(err, 1);
+                s_abort = 1;
+                break;
+              }
+              __nanosleep(64);
+            }
+            __threadfence();
           }
-          __nanosleep(64);
         }
-        __threadfence();
       }
-    }
-    __syncthreads();
-    if (s_abort) break;
-    const PassDev &pass = s_pass;
-    build_lut(lut, pass);
-    TileGeom tg;
-    tg.T = pass.T;
-    tg.nlow = pass.nlow;
-    tg.A = 1 << pass.T;
-    tg.lowmask = (1u << pass.nlow) - 1u;
-    tg.lut = lut;
-    tg.base = tile_base(pass, tile);
-    C *psi = states + cc.state_off;
-    __syncthreads();
-    if (sg.pass == 0) {
-      for (int l = threadIdx.x; l < tg.A; l += blockDim.x) {
-        C v;
-        v.x = tg.gidx(l) == cc.basis ? R(1) : R(0);
-        v.y = R(0);
-        s[l] = v;
-      }
-    } else {
-      load_tile_cg<R>(psi, s, tg);
-    }
-    __syncthreads();
-    for (int o = pass.op_begin; o < pass.op_end; ++o) {
-      const OpDev &op = ops[o];
-      if (op.sync_prev && o > pass.op_begin) __syncthreads();
-      apply_op<R, MAXK>(s, tg, op, mats);
-    }
-    __syncthreads();
-    const bool last = sg.pass == cc.n_pass - 1;
-    if (last && cc.n_terms > 0) {
-      // <Z word> partial of this tile: sum_l (-1)^popcount(g & z) |psi_l|^2
-      for (int i = threadIdx.x; i < cc.n_terms * nwarps; i += blockDim.x) accs[i] = 0.0;
       __syncthreads();
-      for (int t = 0; t < cc.n_terms; ++t) {
-        const uint64_t z = terms[cc.term_begin + t].z;
-        R acc = R(0);
+      if (s_abort) break;
+      const int seg_i = s_seg;
+      const BatchSeg sg = segs[seg_i];
+      const BatchCircuit cc = circs[sg.circ];
+      const int pidx = cc.pass_begin + sg.pass;
+      const PassDev &pass = s_pass;
+      if (s_new_seg) {
+        build_lut(lut, pass);
+        __syncthreads();
+      }
+      cur_seg = seg_i;
+      const uint64_t tile = (uint64_t)(item - sg.first_item);
+      TileGeom tg;
+      tg.T = pass.T;
+      tg.nlow = pass.nlow;
+      tg.A = 1 << pass.T;
+      tg.lowmask = (1u << pass.nlow) - 1u;
+      tg.lut = lut;
+      tg.base = tile_base(pass, tile);
+      g_t<R> *psi = states + cc.state_off;
+      if (sg.pass == 0) {
         for (int l = threadIdx.x; l < tg.A; l += blockDim.x) {
-          const C a = s[l];
-          const R pr = a.x * a.x + a.y * a.y;
-          acc += (__popcll(tg.gidx(l) & z) & 1) ? -pr : pr;
+          C v;
+          v.x = tg.gidx(l) == cc.basis ? R(1) : R(0);
+          v.y = R(0);
+          s[l] = v;
         }
-        acc = warp_sum(acc);
-        if (lane == 0) accs[t * nwarps + warp] = (double)acc;
+      } else {
+        load_tile_cg<R>(psi, s, tg);
       }
       __syncthreads();
-      for (int t = threadIdx.x; t < cc.n_terms; t += blockDim.x) {
-        double v = 0.0;
-        for (int w = 0; w < nwarps; ++w) v += accs[t * nwarps + w];
-        partials[cc.part_begin + (int64_t)t * sg.ntiles + (int64_t)tile] = v;
+      for (int o = pass.op_begin; o < pass.op_end; ++o) {
+        const OpDev &op = ops[o];
+        if (op.sync_prev && o > pass.op_begin) __syncthreads();
+        apply_op<R, MAXK>(s, tg, op, mats);
+      }
+      __syncthreads();
+      const bool last = sg.pass == cc.n_pass - 1;
+      if (last && cc.n_terms > 0) {
+        // <Z word> partial of this tile: sum_l (-1)^popcount(g & z) |psi_l|^2
+        for (int t = 0; t < cc.n_terms; ++t) {
+          const uint64_t z = terms[cc.term_begin + t].z;
+          R acc = R(0);
+          for (int l = threadIdx.x; l < tg.A; l += blockDim.x) {
+            const C a = s[l];
+            const R pr = a.x * a.x + a.y * a.y;
+            acc += (__popcll(tg.gidx(l) & z) & 1) ? -pr : pr;
+          }
+          acc = warp_sum(acc);
+          if (lane == 0) accs[t * nwarps + warp] = (double)acc;
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < cc.n_terms; t += blockDim.x) {
+          double v = 0.0;
+          for (int w = 0; w < nwarps; ++w) v += accs[t * nwarps + w];
+          partials[cc.part_begin + (int64_t)t * sg.ntiles + (int64_t)tile] = v;
+        }
+      }
+      if (!last || store_final) store_tile<R>(psi, s, tg);
+      __syncthreads();
+      if (threadIdx.x == 0 && pidx != no_publish) {  // no_publish >= 0 only in failure-path tests
+        __threadfence();
+        atomicAdd(&done[pidx], 1);
       }
     }
-    if (!last || store_final) store_tile<R>(psi, s, tg);
-    __syncthreads();
-    if (threadIdx.x == 0 && pidx != no_publish) {  // no_publish >= 0 only in failure-path tests
-      __threadfence();
-      atomicAdd(&done[pidx], 1);
-    }
+    if (s_abort) break;
   }
 }
 

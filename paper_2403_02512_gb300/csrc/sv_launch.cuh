@@ -43,11 +43,11 @@ cudaError_t Launch<R>::tile_forward(void *psi, int n, const PassDev &pass, const
   const int smem = detail::tile_bytes(sizeof(c_t<R>), pass.T) + detail::lut_bytes(pass);
   if (pass.max_k <= 2) {
     detail::allow_big_smem(k_tile_forward<R, 2>, attr2);
-    k_tile_forward<R, 2><<<grid, kBlock, smem, st>>>(reinterpret_cast<c_t<R> *>(psi), n, pass, ops,
+    k_tile_forward<R, 2><<<grid, kBlock, smem, st>>>(reinterpret_cast<g_t<R> *>(psi), n, pass, ops,
                                                       reinterpret_cast<const c_t<R> *>(mats));
   } else {
     detail::allow_big_smem(k_tile_forward<R, 4>, attr4);
-    k_tile_forward<R, 4><<<grid, kBlock, smem, st>>>(reinterpret_cast<c_t<R> *>(psi), n, pass, ops,
+    k_tile_forward<R, 4><<<grid, kBlock, smem, st>>>(reinterpret_cast<g_t<R> *>(psi), n, pass, ops,
                                                       reinterpret_cast<const c_t<R> *>(mats));
   }
   return cudaGetLastError();
@@ -63,15 +63,15 @@ cudaError_t Launch<R>::tile_adjoint(const void *phi_in, void *phi_out, void *lam
   dim3 g((m + b - 1) / b, grid);
   if (pass.max_k <= 2) {
     detail::allow_big_smem(k_tile_adjoint<R, 2>, attr2);
-    k_tile_adjoint<R, 2><<<g, kBlock, smem, st>>>(reinterpret_cast<const c_t<R> *>(phi_in),
-                                                   reinterpret_cast<c_t<R> *>(phi_out),
-                                                   reinterpret_cast<c_t<R> *>(lam), n, m, b, pass, ops,
+    k_tile_adjoint<R, 2><<<g, kBlock, smem, st>>>(reinterpret_cast<const g_t<R> *>(phi_in),
+                                                   reinterpret_cast<g_t<R> *>(phi_out),
+                                                   reinterpret_cast<g_t<R> *>(lam), n, m, b, pass, ops,
                                                    reinterpret_cast<const c_t<R> *>(mats), partials);
   } else {
     detail::allow_big_smem(k_tile_adjoint<R, 4>, attr4);
-    k_tile_adjoint<R, 4><<<g, kBlock, smem, st>>>(reinterpret_cast<const c_t<R> *>(phi_in),
-                                                   reinterpret_cast<c_t<R> *>(phi_out),
-                                                   reinterpret_cast<c_t<R> *>(lam), n, m, b, pass, ops,
+    k_tile_adjoint<R, 4><<<g, kBlock, smem, st>>>(reinterpret_cast<const g_t<R> *>(phi_in),
+                                                   reinterpret_cast<g_t<R> *>(phi_out),
+                                                   reinterpret_cast<g_t<R> *>(lam), n, m, b, pass, ops,
                                                    reinterpret_cast<const c_t<R> *>(mats), partials);
   }
   return cudaGetLastError();
@@ -84,7 +84,7 @@ cudaError_t Launch<R>::expval_pass(const void *psi, int n, const PassDev &pass, 
   detail::allow_big_smem(k_expval<R>, attr);
   const int smem = detail::tile_bytes(sizeof(c_t<R>), pass.T) + detail::lut_bytes(pass) +
                    n_terms * detail::kWarps * 8;
-  k_expval<R><<<grid, kBlock, smem, st>>>(reinterpret_cast<const c_t<R> *>(psi), n, pass, terms, n_terms,
+  k_expval<R><<<grid, kBlock, smem, st>>>(reinterpret_cast<const g_t<R> *>(psi), n, pass, terms, n_terms,
                                            partials);
   return cudaGetLastError();
 }
@@ -97,7 +97,7 @@ cudaError_t Launch<R>::lambda_pass(const void *phi, void *lam, int n, const Pass
   detail::allow_big_smem(k_lambda<R>, attr);
   const int smem = detail::tile_bytes(sizeof(c_t<R>), pass.T) + detail::lut_bytes(pass);
   dim3 g(grid, n_obs);
-  k_lambda<R><<<g, kBlock, smem, st>>>(reinterpret_cast<const c_t<R> *>(phi), reinterpret_cast<c_t<R> *>(lam),
+  k_lambda<R><<<g, kBlock, smem, st>>>(reinterpret_cast<const g_t<R> *>(phi), reinterpret_cast<g_t<R> *>(lam),
                                         n, pass, terms, obs_term_begin, first);
   return cudaGetLastError();
 }
@@ -109,7 +109,7 @@ cudaError_t Launch<R>::dense_k(void *psi, int n, const OpDev &op, const void *ma
   const int gpb = kBlock >> op.k;
   uint64_t blocks = (groups + gpb - 1) / gpb;
   if (blocks > 65535ull * 16) blocks = 65535ull * 16;
-  k_dense_k<R><<<(unsigned)blocks, kBlock, 0, st>>>(reinterpret_cast<c_t<R> *>(psi), n, op,
+  k_dense_k<R><<<(unsigned)blocks, kBlock, 0, st>>>(reinterpret_cast<g_t<R> *>(psi), n, op,
                                                      reinterpret_cast<const c_t<R> *>(mats) + op.mat, adjoint);
   return cudaGetLastError();
 }
@@ -119,7 +119,7 @@ cudaError_t Launch<R>::set_basis(void *psi, int n, uint64_t index, cudaStream_t 
   const uint64_t N = 1ull << n;
   uint64_t blocks = (N + 255) / 256;
   if (blocks > 152 * 64) blocks = 152 * 64;
-  k_set_basis<R><<<(unsigned)blocks, 256, 0, st>>>(reinterpret_cast<c_t<R> *>(psi), N, index);
+  k_set_basis<R><<<(unsigned)blocks, 256, 0, st>>>(reinterpret_cast<g_t<R> *>(psi), N, index);
   return cudaGetLastError();
 }
 
@@ -146,13 +146,13 @@ cudaError_t Launch<R>::batch(void *states, const BatchCircuit *circs, const Pass
   const int smem = (int)((sizeof(c_t<R>) + 8) << max_T) + max_terms * detail::kWarps * 8;
   if (max_k <= 2) {
     detail::allow_big_smem(k_batch<R, 2>, attr2);
-    k_batch<R, 2><<<grid, kBlock, smem, st>>>(reinterpret_cast<c_t<R> *>(states), circs, passes, ops,
+    k_batch<R, 2><<<grid, kBlock, smem, st>>>(reinterpret_cast<g_t<R> *>(states), circs, passes, ops,
                                                reinterpret_cast<const c_t<R> *>(mats), segs, n_segs,
                                                (long long)total_items, terms, partials, done, head, err, store_final,
                                                timeout_ns, max_T, max_terms, no_publish);
   } else {
     detail::allow_big_smem(k_batch<R, 4>, attr4);
-    k_batch<R, 4><<<grid, kBlock, smem, st>>>(reinterpret_cast<c_t<R> *>(states), circs, passes, ops,
+    k_batch<R, 4><<<grid, kBlock, smem, st>>>(reinterpret_cast<g_t<R> *>(states), circs, passes, ops,
                                                reinterpret_cast<const c_t<R> *>(mats), segs, n_segs,
                                                (long long)total_items, terms, partials, done, head, err, store_final,
                                                timeout_ns, max_T, max_terms, no_publish);
@@ -162,7 +162,7 @@ cudaError_t Launch<R>::batch(void *states, const BatchCircuit *circs, const Pass
 
 template <typename R>
 cudaError_t Launch<R>::copy(void *dst, const void *src, int n, cudaStream_t st) {
-  return cudaMemcpyAsync(dst, src, sizeof(c_t<R>) << n, cudaMemcpyDeviceToDevice, st);
+  return cudaMemcpyAsync(dst, src, sizeof(g_t<R>) << n, cudaMemcpyDeviceToDevice, st);
 }
 
 template <typename R>
@@ -184,12 +184,12 @@ int Launch<R>::expval_smem(int T, int n_terms) {
 // 2 x 16 KiB (phi + lambda) in the adjoint kernel.
 template <typename R>
 int Launch<R>::max_T_forward() {
-  return std::is_same<R, float>::value ? 12 : 11;
+  return sizeof(c_t<R>) == 8 ? 12 : 11;
 }
 
 template <typename R>
 int Launch<R>::max_T_adjoint() {
-  return std::is_same<R, float>::value ? 11 : 10;
+  return sizeof(c_t<R>) == 8 ? 11 : 10;
 }
 
 }  // namespace sv

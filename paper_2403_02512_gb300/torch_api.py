@@ -22,6 +22,7 @@ import torch
 from . import _lib as L
 
 _DT = {"c64": (L.SV_C64, torch.complex64), "c128": (L.SV_C128, torch.complex128),
+       "c128df": (L.SV_C128, torch.complex128),
        torch.complex64: (L.SV_C64, torch.complex64), torch.complex128: (L.SV_C128, torch.complex128)}
 
 
@@ -35,7 +36,10 @@ def _require_cuda(device) -> torch.device:
 
 
 class StateVector:
-    """A 2^n-amplitude state held in a torch tensor on the GPU (wire 0 = MSB)."""
+    """A 2^n-amplitude state held in a torch tensor on the GPU (wire 0 = MSB).
+
+    dtype "c64" / "c128" (IEEE FP64 arithmetic) / "c128df" (complex128 storage,
+    double-float arithmetic on the FP32 pipe)."""
 
     def __init__(self, n: int, dtype="c128", device="cuda", basis_state: int = 0):
         dev = _require_cuda(device)
@@ -46,6 +50,8 @@ class StateVector:
             self.handle = L.sv_create_from_device_ptr(self.n, self.sv_dtype, self.tensor.data_ptr())
         self.device = dev
         self.generation = 0
+        if dtype == "c128df":
+            L.sv_set_compute(self.handle, L.SV_COMPUTE_DOUBLE_FLOAT)
         self.sync_stream()
         self.reset(basis_state)
 

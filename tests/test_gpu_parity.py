@@ -31,10 +31,11 @@ import paper_2403_02512_gb300 as svlib  # noqa: E402
 from paper_2403_02512_gb300 import _lib as L  # noqa: E402
 from paper_2403_02512_gb300.torch_api import Program, StateVector, expval as ad_expval  # noqa: E402
 
-DTYPES = ["c128", "c64"]
-TOL_STATE = {"c128": 1e-12, "c64": 1e-4}
-TOL_E = {"c128": 1e-10, "c64": 1e-4}
-TOL_J = {"c128": 1e-9, "c64": 1e-4}
+# "c128df": complex128 storage, double-float arithmetic -- held to the complex128 bars
+DTYPES = ["c128", "c64", "c128df"]
+TOL_STATE = {"c128": 1e-12, "c64": 1e-4, "c128df": 1e-12}
+TOL_E = {"c128": 1e-10, "c64": 1e-4, "c128df": 1e-10}
+TOL_J = {"c128": 1e-9, "c64": 1e-4, "c128df": 1e-9}
 
 
 def _state(n, dtype, seed):
@@ -111,7 +112,7 @@ def test_dense_matrix_blocks(dtype, k):
         sv, psi = _state(n, dtype, 40 + k)
         sv.apply_matrix(wires, U, adjoint)
         oracle.apply_matrix(psi, U.conj().T if adjoint else U, wires)
-        tol = TOL_STATE[dtype] * (10 if dtype == "c128" else 1)
+        tol = TOL_STATE[dtype] * (10 if dtype != "c64" else 1)
         assert np.abs(sv.to_numpy() - psi).max() <= tol
 
 
@@ -192,6 +193,8 @@ def test_one_shot_jacobian_and_vjp_calls(dtype):
     rng = np.random.default_rng(21)
     obs = _obs_for(n, rng)
     h = L.sv_create(n, L.SV_C64 if dtype == "c64" else L.SV_C128)
+    if dtype == "c128df":
+        L.sv_set_compute(h, L.SV_COMPUTE_DOUBLE_FLOAT)
     try:
         tape, ps = L.Tape(c.ops, c.n_params), L.PauliSums(obs)
         L.sv_forward(h, tape, p)
@@ -219,7 +222,7 @@ def test_lambda_chunking_matches_single_sweep(dtype, monkeypatch):
     chunked.set_params(p)
     E2, J2 = chunked.jacobian()
     assert torch.equal(E1, E2)
-    _assert_rel(J2.cpu().numpy(), J1.cpu().numpy(), 1e-12 if dtype == "c128" else 1e-6, "chunked")
+    _assert_rel(J2.cpu().numpy(), J1.cpu().numpy(), 1e-6 if dtype == "c64" else 1e-12, "chunked")
 
 
 @pytest.mark.parametrize("dtype", DTYPES)
@@ -286,6 +289,22 @@ def test_workload_shapes_small(dtype, maker):
     Eo, Jo = oracle.adjoint_jacobian(c, p)
     _assert_rel(E.cpu().numpy(), Eo, TOL_E[dtype], "expvals")
     _assert_rel(J.cpu().numpy(), Jo, TOL_J[dtype], "jacobian")
+
+
+def test_compute_mode_switch_rebuilds_matrices():
+    n = 11
+    c, p = strongly_entangling(n, 2, seed=4)
+    sv = StateVector(n, "c128")
+    prog = Program.from_circuit(sv, c)
+    prog.forward(p)
+    E1, J1 = prog.jacobian()
+    L.sv_set_compute(sv.handle, L.SV_COMPUTE_DOUBLE_FLOAT)
+    prog.forward(p)
+    E2, J2 = prog.jacobian()
+    _assert_rel(E2.cpu().numpy(), E1.cpu().numpy(), 1e-10, "expvals")
+    _assert_rel(J2.cpu().numpy(), J1.cpu().numpy(), 1e-9, "jacobian")
+    with pytest.raises(L.SvError):
+        L.sv_set_compute(StateVector(3, "c64").handle, L.SV_COMPUTE_DOUBLE_FLOAT)
 
 
 def test_program_refuses_to_run_before_parameters_are_set():
