@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the complex64 and per-gate side measurements")
+    ap.add_argument("--quick-extras", action="store_true", help="only the other precisions of the same step")
     return ap.parse_args()
 
 
@@ -457,7 +458,7 @@ def run_ours(args):
             extras[other] = {"ms_per_step": o["ms"], "max_abs_jacobian_diff_vs_" + args.dtype: dJ}
             del o
             torch.cuda.empty_cache()
-        if NQ == N_QUBITS:
+        if NQ == N_QUBITS and not args.quick_extras:
             extras["gate_pass_n30"] = extra_gates(hbm_peak)
             extras["qaoa_batched"] = extra_qaoa()
             extras["vqe24_2000_terms"] = extra_vqe()

@@ -412,9 +412,45 @@ OpDev blank_op(int n, const HOp &h) {
   return o;
 }
 
+// Split an op's controls into the pass's local bits and fixed tile bits; for
+// diagonal ops record which targets are local (tl[j], else -1).
+void localise(OpDev &o, const PassDev &pd) {
+  o.lcmask = o.lcval = 0;
+  o.hcmask = o.hcval = 0;
+  for (int b = 0; b < 64; ++b) {
+    if (!((o.cmask >> b) & 1)) continue;
+    const bool v = (o.cval >> b) & 1;
+    int li = -1;
+    for (int i = 0; i < pd.T; ++i)
+      if (pd.pos[i] == b) li = i;
+    if (li >= 0) {
+      o.lcmask |= 1u << li;
+      if (v) o.lcval |= 1u << li;
+    } else {
+      o.hcmask |= 1ull << b;
+      if (v) o.hcval |= 1ull << b;
+    }
+  }
+  if (o.kind == kDiag)
+    for (int j = 0; j < o.k && j < 4; ++j) {
+      o.tl[j] = -1;
+      for (int i = 0; i < pd.T; ++i)
+        if (pd.pos[i] == o.tg[j]) o.tl[j] = (int8_t)i;
+    }
+}
+
 // Lower one gate into micro-ops inside a pass (dagger: store U^dagger blocks).
 void lower_gate(int n, const HOp &h, const PassDev &pd, bool dagger, int train, int slot, SlotTable &st,
                 std::vector<OpDev> &out) {
+  const size_t first_out = out.size();
+  struct Fin {
+    std::vector<OpDev> &v;
+    size_t f;
+    const PassDev &pd;
+    ~Fin() {
+      for (size_t i = f; i < v.size(); ++i) localise(v[i], pd);
+    }
+  } fin{out, first_out, pd};
   const bool eff_dagger = (h.adjoint != 0) != dagger;
   OpDev base = blank_op(n, h);
   base.train = h.train ? train : -1;
@@ -985,8 +1021,9 @@ sv_status build_program(sv_state *s, const sv_tape *tape, const sv_pauli_sum *ob
     int ta = std::min(K.Ta, n);
     const int tile_b = K.amp_bytes << ta;
     const int budget = 112 * 1024 - tile_b - (8 << ta);
-    p->lam_per_cta = std::max(1, std::min({kMaxLambdaPerCta, std::max(1, mc),
-                                            budget / (tile_b + kMaxTrainPerPass * 8 * (kBlock / 32))}));
+    int lpc = std::max(1, std::min({kMaxLambdaPerCta, std::max(1, mc),
+                                    budget / (tile_b + kMaxTrainPerPass * 8 * (kBlock / 32))}));
+    p->lam_per_cta = lpc >= 4 ? 4 : lpc >= 2 ? 2 : 1;  // the adjoint kernel is compiled for 1, 2 and 4
     const int smem_a = tile_b * (1 + p->lam_per_cta) + (8 << ta) + kMaxTrainPerPass * 8 * (kBlock / 32) * p->lam_per_cta;
     p->ctas_a = 2 * sms * blocks_per_sm(smem_a);
     p->tiles_a = 1ull << (n - ta);

@@ -16,7 +16,7 @@ constexpr int kMaxTargets = 6;      // dense ops inside a tile: k <= 4; dense_k 
 constexpr int kMaxTileTargets = 4;
 constexpr int kMaxQubits = 34;
 constexpr int kBlock = 256;         // threads per CTA in the tile kernels
-constexpr int kMaxLambdaPerCta = 8; // lambdas sharing one phi tile in the adjoint kernel
+constexpr int kMaxLambdaPerCta = 4; // lambdas sharing one phi tile in the adjoint kernel
 constexpr int kMaxTrainPerPass = 32;
 
 // Micro-op kinds.  Every structured gate is a set of independent 2x2 blocks on
@@ -57,6 +57,10 @@ struct OpDev {
   float gs, ga, gb;
   int32_t pad1;
   uint64_t cmask, cval;  // control bits (global) and their required values
+  // The same controls split by the pass's tiles: local bits (as local-index
+  // bits) vary inside a tile; the others are fixed per tile.
+  uint32_t lcmask, lcval;
+  uint64_t hcmask, hcval;
 };
 
 // One fused pass: a tile is the set of 2^T amplitudes that share every index

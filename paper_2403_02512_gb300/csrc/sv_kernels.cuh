@@ -262,6 +262,66 @@ __device__ __forceinline__ int group_base(const OpDev &op, int g) {
   return l;
 }
 
+// The fields of a micro-op that the per-amplitude loops use, copied into
+// registers once per op: reading them through the descriptor pointer inside a
+// loop that stores to shared memory forces a reload on every iteration.
+struct OpRegs {
+  int k, ts0, ts1, ts2, ts3, oa, ob;
+  uint64_t cmask, cval;
+  __device__ __forceinline__ explicit OpRegs(const OpDev &op)
+      : k(op.k), ts0(op.ts[0]), ts1(op.ts[1]), ts2(op.ts[2]), ts3(op.ts[3]), oa(op.oa), ob(op.ob),
+        cmask(op.cmask), cval(op.cval) {}
+  __device__ __forceinline__ int base(int g) const {
+    int l = insert_zero(g, ts0);
+    if (k > 1) l = insert_zero(l, ts1);
+    if (k > 2) l = insert_zero(l, ts2);
+    if (k > 3) l = insert_zero(l, ts3);
+    return l;
+  }
+};
+
+// Diagonal micro-op fields in registers (targets anywhere, entries up to 2^2
+// held directly; wider diagonals read their entries from the matrix buffer).
+template <typename R>
+struct DiagRegs {
+  int k, b0, b1, mat, code;
+  uint64_t cmask, cval;
+  c_t<R> d[4];
+  bool small;
+  __device__ __forceinline__ DiagRegs(const OpDev &op, const c_t<R> *__restrict__ mats)
+      : k(op.k), b0(op.tg[0]), b1(op.k > 1 ? op.tg[1] : 0), mat(op.mat), code(op.code), cmask(op.cmask),
+        cval(op.cval) {
+    small = k <= 2 && code == dGen;
+    if (small)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) d[e] = e < (1 << k) ? mats[mat + e] : c_t<R>();
+  }
+  __device__ __forceinline__ int index(const OpDev &op, uint64_t g) const {
+    if (k == 1) return (int)((g >> b0) & 1);
+    if (k == 2) return (int)(((g >> b0) & 1) << 1 | ((g >> b1) & 1));
+    int idx = 0;
+    for (int j = 0; j < op.k; ++j) idx = (idx << 1) | (int)((g >> op.tg[j]) & 1);
+    return idx;
+  }
+  __device__ __forceinline__ c_t<R> mul(const c_t<R> *__restrict__ mats, int idx, c_t<R> v) const {
+    if (code == dNeg) {
+      if (idx == (1 << k) - 1) {
+        v.x = -v.x;
+        v.y = -v.y;
+      }
+      return v;
+    }
+    if (small) {
+      c_t<R> dv = d[0];
+#pragma unroll
+      for (int e = 1; e < 4; ++e)
+        if (idx == e) dv = d[e];
+      return cmul(v, dv);
+    }
+    return cmul(v, mats[mat + idx]);
+  }
+};
+
 // (va, vb) <- E (va, vb) for a 2x2 block E stored row-major in M.
 template <typename R>
 __device__ __forceinline__ void pair_apply(int code, const c_t<R> *M, c_t<R> &va, c_t<R> &vb) {
@@ -351,62 +411,136 @@ __device__ __forceinline__ c_t<R> diag_mul(const OpDev &op, const c_t<R> *__rest
   return cmul(v, mats[op.mat + idx]);
 }
 
-template <typename R, int CODE>
+// Controls on bits outside the tile decide per tile whether an op acts at all.
+__device__ __forceinline__ bool op_active(const OpDev &op, uint64_t base) {
+  return (base & op.hcmask) == op.hcval;
+}
+
+template <typename R, int CODE, bool CTL>
 __device__ void fwd_pair_t(c_t<R> *s, const TileGeom &tg, const OpDev &op, const c_t<R> *__restrict__ mats) {
   using C = c_t<R>;
-  const C *M = mats + op.mat;
   C Mr[4];
   if (CODE == mGen || CODE == mReal || CODE == mImOff)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) Mr[q] = M[q];
-  const int ng = tg.A >> op.k;
-  const bool ctl = op.cmask != 0;
+    for (int q = 0; q < 4; ++q) Mr[q] = mats[op.mat + q];
+  const OpRegs o(op);
+  const uint32_t lcm = op.lcmask, lcv = op.lcval;
+  const int ng = tg.A >> o.k;
   for (int g = threadIdx.x; g < ng; g += blockDim.x) {
-    const int l0 = group_base(op, g);
-    if (ctl && ((tg.gidx(l0) & op.cmask) != op.cval)) continue;
-    C va = s[l0 + op.oa], vb = s[l0 + op.ob];
+    const int l0 = o.base(g);
+    if (CTL && (((uint32_t)l0 & lcm) != lcv)) continue;
+    C va = s[l0 + o.oa], vb = s[l0 + o.ob];
     pair_apply<R>(CODE, Mr, va, vb);
-    s[l0 + op.oa] = va;
-    s[l0 + op.ob] = vb;
+    s[l0 + o.oa] = va;
+    s[l0 + o.ob] = vb;
   }
+}
+
+template <typename R, int CODE>
+__device__ __forceinline__ void fwd_pair_c(c_t<R> *s, const TileGeom &tg, const OpDev &op, const c_t<R> *mats) {
+  if (op.lcmask)
+    fwd_pair_t<R, CODE, true>(s, tg, op, mats);
+  else
+    fwd_pair_t<R, CODE, false>(s, tg, op, mats);
 }
 
 template <typename R>
 __device__ __forceinline__ void fwd_pair(c_t<R> *s, const TileGeom &tg, const OpDev &op, const c_t<R> *mats) {
   switch (op.code) {
-    case mSwap: fwd_pair_t<R, mSwap>(s, tg, op, mats); break;
-    case mY: fwd_pair_t<R, mY>(s, tg, op, mats); break;
-    case mReal: fwd_pair_t<R, mReal>(s, tg, op, mats); break;
-    case mImOff: fwd_pair_t<R, mImOff>(s, tg, op, mats); break;
-    default: fwd_pair_t<R, mGen>(s, tg, op, mats); break;
+    case mSwap: fwd_pair_c<R, mSwap>(s, tg, op, mats); break;
+    case mY: fwd_pair_c<R, mY>(s, tg, op, mats); break;
+    case mReal: fwd_pair_c<R, mReal>(s, tg, op, mats); break;
+    case mImOff: fwd_pair_c<R, mImOff>(s, tg, op, mats); break;
+    default: fwd_pair_c<R, mGen>(s, tg, op, mats); break;
   }
+}
+
+// Diagonal index of local element l for a 1- or 2-target diagonal: targets in
+// the tile come from l, the others are fixed for the tile.
+struct DiagIdx {
+  int fixed, sh0, sh1;
+  __device__ __forceinline__ DiagIdx(const OpDev &op, uint64_t base, int kd) {
+    fixed = 0;
+    sh0 = op.tl[0] >= 0 ? op.tl[0] : 31;  // l < 2^13: (l >> 31) == 0
+    if (op.tl[0] < 0) fixed |= (int)((base >> op.tg[0]) & 1) << (kd - 1);
+    sh1 = 31;
+    if (kd == 2) {
+      sh1 = op.tl[1] >= 0 ? op.tl[1] : 31;
+      if (op.tl[1] < 0) fixed |= (int)((base >> op.tg[1]) & 1);
+    }
+  }
+  template <int KD>
+  __device__ __forceinline__ int of(int l) const {
+    if (KD == 1) return fixed | ((l >> sh0) & 1);
+    return fixed | (((l >> sh0) & 1) << 1) | ((l >> sh1) & 1);
+  }
+};
+
+template <typename C, int KD>
+__device__ __forceinline__ C pick(const C (&d)[4], int idx) {
+  if (KD == 1) return idx ? d[1] : d[0];
+  C v = d[0];
+  v = idx == 1 ? d[1] : v;
+  v = idx == 2 ? d[2] : v;
+  v = idx == 3 ? d[3] : v;
+  return v;
+}
+
+template <typename C>
+__device__ __forceinline__ C negate_if(C v, bool neg) {
+  if (neg) {
+    v.x = -v.x;
+    v.y = -v.y;
+  }
+  return v;
+}
+
+template <typename R, int KD, bool NEG, bool CTL>
+__device__ void fwd_diag_t(c_t<R> *s, const TileGeom &tg, const OpDev &op, const c_t<R> *__restrict__ mats) {
+  using C = c_t<R>;
+  C d[4];
+  if (!NEG)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) d[e] = e < (1 << KD) ? mats[op.mat + e] : C();
+  const DiagIdx di(op, tg.base, KD);
+  const uint32_t lcm = op.lcmask, lcv = op.lcval;
+  constexpr int full = (1 << KD) - 1;
+  for (int l = threadIdx.x; l < tg.A; l += blockDim.x) {
+    if (CTL && (((uint32_t)l & lcm) != lcv)) continue;
+    const int idx = di.of<KD>(l);
+    s[l] = NEG ? negate_if(s[l], idx == full) : cmul(s[l], pick<C, KD>(d, idx));
+  }
+}
+
+template <typename R, int KD, bool NEG>
+__device__ __forceinline__ void fwd_diag_c(c_t<R> *s, const TileGeom &tg, const OpDev &op, const c_t<R> *mats) {
+  if (op.lcmask)
+    fwd_diag_t<R, KD, NEG, true>(s, tg, op, mats);
+  else
+    fwd_diag_t<R, KD, NEG, false>(s, tg, op, mats);
 }
 
 template <typename R>
 __device__ void fwd_diag(c_t<R> *s, const TileGeom &tg, const OpDev &op, const c_t<R> *__restrict__ mats) {
-  using C = c_t<R>;
-  if (op.k <= 2 && op.code == dGen) {
-    C d[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) d[q] = q < (1 << op.k) ? mats[op.mat + q] : C();
-    const int b0 = op.tg[0], b1 = op.k == 2 ? op.tg[1] : 0;
-    const bool two = op.k == 2;
-    for (int l = threadIdx.x; l < tg.A; l += blockDim.x) {
-      const uint64_t g = tg.gidx(l);
-      if ((g & op.cmask) != op.cval) continue;
-      const int idx = two ? (int)(((g >> b0) & 1) << 1 | ((g >> b1) & 1)) : (int)((g >> b0) & 1);
-      C dv = d[0];
-#pragma unroll
-      for (int q = 1; q < 4; ++q)
-        if (idx == q) dv = d[q];
-      s[l] = cmul(s[l], dv);
-    }
+  if (op.k == 1) {
+    if (op.code == dNeg)
+      fwd_diag_c<R, 1, true>(s, tg, op, mats);
+    else
+      fwd_diag_c<R, 1, false>(s, tg, op, mats);
     return;
   }
+  if (op.k == 2) {
+    if (op.code == dNeg)
+      fwd_diag_c<R, 2, true>(s, tg, op, mats);
+    else
+      fwd_diag_c<R, 2, false>(s, tg, op, mats);
+    return;
+  }
+  const DiagRegs<R> dr(op, mats);  // wider diagonals: entries from the matrix buffer
   for (int l = threadIdx.x; l < tg.A; l += blockDim.x) {
     const uint64_t g = tg.gidx(l);
-    if ((g & op.cmask) != op.cval) continue;
-    s[l] = diag_mul<R>(op, mats, diag_index(op, g), s[l]);
+    if ((g & dr.cmask) != dr.cval) continue;
+    s[l] = dr.mul(mats, dr.index(op, g), s[l]);
   }
 }
 
@@ -470,6 +604,7 @@ __device__ __forceinline__ void dense_any(c_t<R> *s, const TileGeom &tg, const O
 
 template <typename R, int MAXK>
 __device__ __forceinline__ void apply_op(c_t<R> *s, const TileGeom &tg, const OpDev &op, const c_t<R> *mats) {
+  if (op.kind != kDense && !op_active(op, tg.base)) return;
   if (op.kind == kPair)
     fwd_pair<R>(s, tg, op, mats);
   else if (op.kind == kDiag)
@@ -528,141 +663,199 @@ __global__ void __launch_bounds__(kBlock) k_tile_forward(g_t<R> *__restrict__ ps
 // and written by one CTA and phi_out may equal phi_in.
 // Partial layout: partials[(blockIdx.y * m + j) * n_train + t].
 // ---------------------------------------------------------------------------
-template <typename R>
-__device__ __forceinline__ void flush_acc(Acc<R> (&acc)[kMaxLambdaPerCta], int bb, int b, int train, double *accs,
-                                          int nwarps, int warp, int lane, R scale) {
+template <typename R, int B>
+__device__ __forceinline__ void flush_acc(const R (&acc)[B], int bb, int train, double *accs, int nwarps, int warp,
+                                          int lane, R scale) {
 #pragma unroll
-  for (int jj = 0; jj < kMaxLambdaPerCta; ++jj) {
+  for (int jj = 0; jj < B; ++jj) {
     if (jj < bb) {
-      const R v = scale * warp_sum(acc[jj].value());
-      if (lane == 0) WarpAcc<R>::add(&accs[(train * b + jj) * nwarps + warp], v);
+      const R v = scale * warp_sum(acc[jj]);
+      if (lane == 0) WarpAcc<R>::add(&accs[(train * B + jj) * nwarps + warp], v);
     }
   }
 }
 
-template <typename R, int CODE, int GCODE>
-__device__ void adj_pair_t(c_t<R> *sp, c_t<R> *sl, int bb, const TileGeom &tg, const OpDev &op,
-                           const c_t<R> *__restrict__ mats, Acc<R> (&acc)[kMaxLambdaPerCta]) {
+// Adjoint pair micro-op on phi and B lambda tiles (slots past the CTA's last
+// lambda are zero and never stored).  acc[j] += Im <lambda_j | G phi> / gs.
+template <typename R, int B, int CODE, int GCODE, bool CTL>
+__device__ void adj_pair_t(c_t<R> *sp, c_t<R> *sl, const TileGeom &tg, const OpDev &op,
+                           const c_t<R> *__restrict__ mats, R (&acc)[B]) {
   using C = c_t<R>;
   C Mr[4];
   if (CODE == mGen || CODE == mReal || CODE == mImOff)
 #pragma unroll
     for (int q = 0; q < 4; ++q) Mr[q] = mats[op.mat + q];
-  const int ng = tg.A >> op.k;
-  const bool ctl = op.cmask != 0;
+  const OpRegs o(op);
+  const uint32_t lcm = op.lcmask, lcv = op.lcval;
+  const int ng = tg.A >> o.k;
   for (int g = threadIdx.x; g < ng; g += blockDim.x) {
-    const int l0 = group_base(op, g);
-    if (ctl && ((tg.gidx(l0) & op.cmask) != op.cval)) continue;
-    const int ia = l0 + op.oa, ib = l0 + op.ob;
+    const int l0 = o.base(g);
+    if (CTL && (((uint32_t)l0 & lcm) != lcv)) continue;
+    const int ia = l0 + o.oa, ib = l0 + o.ob;
     C pa = sp[ia], pb = sp[ib];
     const C qa = pa, qb = pb;  // phi before the un-apply
     pair_apply<R>(CODE, Mr, pa, pb);
     sp[ia] = pa;
     sp[ib] = pb;
 #pragma unroll
-    for (int jj = 0; jj < kMaxLambdaPerCta; ++jj) {
-      if (jj < bb) {
-        C la = sl[jj * tg.A + ia], lb = sl[jj * tg.A + ib];
-        if (GCODE != gNone) acc[jj].s = pair_ip_acc<R, GCODE>(acc[jj].s, qa, qb, la, lb);
-        pair_apply<R>(CODE, Mr, la, lb);
-        sl[jj * tg.A + ia] = la;
-        sl[jj * tg.A + ib] = lb;
-      }
+    for (int jj = 0; jj < B; ++jj) {
+      C la = sl[jj * tg.A + ia], lb = sl[jj * tg.A + ib];
+      if (GCODE != gNone) acc[jj] = pair_ip_acc<R, GCODE>(acc[jj], qa, qb, la, lb);
+      pair_apply<R>(CODE, Mr, la, lb);
+      sl[jj * tg.A + ia] = la;
+      sl[jj * tg.A + ib] = lb;
     }
   }
 }
 
-template <typename R, int CODE>
-__device__ __forceinline__ void adj_pair_g(c_t<R> *sp, c_t<R> *sl, int bb, const TileGeom &tg, const OpDev &op,
-                                           const c_t<R> *mats, Acc<R> (&acc)[kMaxLambdaPerCta]) {
+template <typename R, int B, int CODE, int GCODE>
+__device__ __forceinline__ void adj_pair_c(c_t<R> *sp, c_t<R> *sl, const TileGeom &tg, const OpDev &op,
+                                           const c_t<R> *mats, R (&acc)[B]) {
+  if (op.lcmask)
+    adj_pair_t<R, B, CODE, GCODE, true>(sp, sl, tg, op, mats, acc);
+  else
+    adj_pair_t<R, B, CODE, GCODE, false>(sp, sl, tg, op, mats, acc);
+}
+
+template <typename R, int B, int CODE>
+__device__ __forceinline__ void adj_pair_g(c_t<R> *sp, c_t<R> *sl, const TileGeom &tg, const OpDev &op,
+                                           const c_t<R> *mats, R (&acc)[B]) {
   const int gcode = op.train >= 0 ? op.gcode : gNone;
   if (gcode == gX)
-    adj_pair_t<R, CODE, gX>(sp, sl, bb, tg, op, mats, acc);
+    adj_pair_c<R, B, CODE, gX>(sp, sl, tg, op, mats, acc);
   else if (gcode == gY)
-    adj_pair_t<R, CODE, gY>(sp, sl, bb, tg, op, mats, acc);
+    adj_pair_c<R, B, CODE, gY>(sp, sl, tg, op, mats, acc);
   else
-    adj_pair_t<R, CODE, gNone>(sp, sl, bb, tg, op, mats, acc);
+    adj_pair_c<R, B, CODE, gNone>(sp, sl, tg, op, mats, acc);
 }
 
-template <typename R>
-__device__ __forceinline__ void adj_pair(c_t<R> *sp, c_t<R> *sl, int bb, const TileGeom &tg, const OpDev &op,
-                                         const c_t<R> *mats, Acc<R> (&acc)[kMaxLambdaPerCta]) {
+template <typename R, int B>
+__device__ __forceinline__ void adj_pair(c_t<R> *sp, c_t<R> *sl, const TileGeom &tg, const OpDev &op,
+                                         const c_t<R> *mats, R (&acc)[B]) {
   switch (op.code) {
-    case mSwap: adj_pair_g<R, mSwap>(sp, sl, bb, tg, op, mats, acc); break;
-    case mY: adj_pair_g<R, mY>(sp, sl, bb, tg, op, mats, acc); break;
-    case mReal: adj_pair_g<R, mReal>(sp, sl, bb, tg, op, mats, acc); break;
-    case mImOff: adj_pair_g<R, mImOff>(sp, sl, bb, tg, op, mats, acc); break;
-    default: adj_pair_g<R, mGen>(sp, sl, bb, tg, op, mats, acc); break;
+    case mSwap: adj_pair_g<R, B, mSwap>(sp, sl, tg, op, mats, acc); break;
+    case mY: adj_pair_g<R, B, mY>(sp, sl, tg, op, mats, acc); break;
+    case mReal: adj_pair_g<R, B, mReal>(sp, sl, tg, op, mats, acc); break;
+    case mImOff: adj_pair_g<R, B, mImOff>(sp, sl, tg, op, mats, acc); break;
+    default: adj_pair_g<R, B, mGen>(sp, sl, tg, op, mats, acc); break;
   }
 }
 
-template <typename R, bool TRAIN>
-__device__ void adj_diag_t(c_t<R> *sp, c_t<R> *sl, int bb, const TileGeom &tg, const OpDev &op,
-                           const c_t<R> *__restrict__ mats, Acc<R> (&acc)[kMaxLambdaPerCta]) {
+// Adjoint diagonal micro-op: acc[j] += g(idx) Im(conj(lambda_j) phi) before
+// multiplying phi and every lambda by the stored (adjoint) entry.
+template <typename R, int B, int KD, bool NEG, bool CTL, bool TRAIN>
+__device__ void adj_diag_t(c_t<R> *sp, c_t<R> *sl, const TileGeom &tg, const OpDev &op,
+                           const c_t<R> *__restrict__ mats, R (&acc)[B]) {
   using C = c_t<R>;
   C d[4];
-  const bool small = op.k <= 2 && op.code == dGen;
-  if (small)
+  if (!NEG)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) d[q] = q < (1 << op.k) ? mats[op.mat + q] : C();
+    for (int e = 0; e < 4; ++e) d[e] = e < (1 << KD) ? mats[op.mat + e] : C();
+  const DiagIdx di(op, tg.base, KD);
+  const uint32_t lcm = op.lcmask, lcv = op.lcval;
   const R ga = (R)op.ga, gb = (R)op.gb;
+  const int zmask = op.zmask;
+  constexpr int full = (1 << KD) - 1;
   for (int l = threadIdx.x; l < tg.A; l += blockDim.x) {
-    const uint64_t g = tg.gidx(l);
-    if ((g & op.cmask) != op.cval) continue;
-    const int idx = diag_index(op, g);
-    C dv;
-    if (small) {
-      dv = d[0];
-#pragma unroll
-      for (int q = 1; q < 4; ++q)
-        if (idx == q) dv = d[q];
-    }
+    if (CTL && (((uint32_t)l & lcm) != lcv)) continue;
+    const int idx = di.of<KD>(l);
     const C p = sp[l];
-    R gd = R(0);
-    if (TRAIN) gd = (__popc(idx & op.zmask) & 1) ? gb : ga;
-    const R gpy = gd * p.y, gpx = gd * p.x;
-    sp[l] = small ? cmul(p, dv) : diag_mul<R>(op, mats, idx, p);
+    R gpy = R(0), gpx = R(0);
+    if (TRAIN) {
+      const R gd = (__popc(idx & zmask) & 1) ? gb : ga;
+      gpy = gd * p.y;
+      gpx = gd * p.x;
+    }
+    C dv;
+    if (!NEG) dv = pick<C, KD>(d, idx);
+    const bool neg = idx == full;
+    sp[l] = NEG ? negate_if(p, neg) : cmul(p, dv);
 #pragma unroll
-    for (int jj = 0; jj < kMaxLambdaPerCta; ++jj) {
-      if (jj < bb) {
-        const C q = sl[jj * tg.A + l];
-        if (TRAIN) acc[jj].s = fma(q.x, gpy, fma(-q.y, gpx, acc[jj].s));
-        sl[jj * tg.A + l] = small ? cmul(q, dv) : diag_mul<R>(op, mats, idx, q);
-      }
+    for (int jj = 0; jj < B; ++jj) {
+      const C q = sl[jj * tg.A + l];
+      if (TRAIN) acc[jj] = fma(q.x, gpy, fma(-q.y, gpx, acc[jj]));
+      sl[jj * tg.A + l] = NEG ? negate_if(q, neg) : cmul(q, dv);
     }
   }
 }
 
-template <typename R>
-__device__ __forceinline__ void adj_diag(c_t<R> *sp, c_t<R> *sl, int bb, const TileGeom &tg, const OpDev &op,
-                                         const c_t<R> *mats, Acc<R> (&acc)[kMaxLambdaPerCta]) {
-  if (op.train >= 0)
-    adj_diag_t<R, true>(sp, sl, bb, tg, op, mats, acc);
-  else
-    adj_diag_t<R, false>(sp, sl, bb, tg, op, mats, acc);
+template <typename R, int B, int KD, bool NEG>
+__device__ __forceinline__ void adj_diag_c(c_t<R> *sp, c_t<R> *sl, const TileGeom &tg, const OpDev &op,
+                                           const c_t<R> *mats, R (&acc)[B]) {
+  const bool tr = op.train >= 0;
+  if (op.lcmask) {
+    if (tr)
+      adj_diag_t<R, B, KD, NEG, true, true>(sp, sl, tg, op, mats, acc);
+    else
+      adj_diag_t<R, B, KD, NEG, true, false>(sp, sl, tg, op, mats, acc);
+  } else {
+    if (tr)
+      adj_diag_t<R, B, KD, NEG, false, true>(sp, sl, tg, op, mats, acc);
+    else
+      adj_diag_t<R, B, KD, NEG, false, false>(sp, sl, tg, op, mats, acc);
+  }
 }
 
-template <typename R, int MAXK>
+// Wider diagonals (user matrices on 3+ wires; never trainable).
+template <typename R, int B>
+__device__ void adj_diag_wide(c_t<R> *sp, c_t<R> *sl, const TileGeom &tg, const OpDev &op,
+                              const c_t<R> *__restrict__ mats) {
+  const DiagRegs<R> dr(op, mats);
+  for (int l = threadIdx.x; l < tg.A; l += blockDim.x) {
+    const uint64_t g = tg.gidx(l);
+    if ((g & dr.cmask) != dr.cval) continue;
+    const int idx = dr.index(op, g);
+    sp[l] = dr.mul(mats, idx, sp[l]);
+#pragma unroll
+    for (int jj = 0; jj < B; ++jj) sl[jj * tg.A + l] = dr.mul(mats, idx, sl[jj * tg.A + l]);
+  }
+}
+
+template <typename R, int B>
+__device__ __forceinline__ void adj_diag(c_t<R> *sp, c_t<R> *sl, const TileGeom &tg, const OpDev &op,
+                                         const c_t<R> *mats, R (&acc)[B]) {
+  if (op.k == 1) {
+    if (op.code == dNeg)
+      adj_diag_c<R, B, 1, true>(sp, sl, tg, op, mats, acc);
+    else
+      adj_diag_c<R, B, 1, false>(sp, sl, tg, op, mats, acc);
+  } else if (op.k == 2) {
+    if (op.code == dNeg)
+      adj_diag_c<R, B, 2, true>(sp, sl, tg, op, mats, acc);
+    else
+      adj_diag_c<R, B, 2, false>(sp, sl, tg, op, mats, acc);
+  } else {
+    adj_diag_wide<R, B>(sp, sl, tg, op, mats);
+  }
+}
+
+template <typename R, int MAXK, int B>
 __global__ void __launch_bounds__(kBlock, 2) k_tile_adjoint(const g_t<R> *phi_in, g_t<R> *phi_out,
-                                                          g_t<R> *__restrict__ lam_base, int n, int m, int b,
-                                                          const PassDev pass, const OpDev *__restrict__ ops,
-                                                          const c_t<R> *__restrict__ mats,
-                                                          double *__restrict__ partials) {
+                                                             g_t<R> *__restrict__ lam_base, int n, int m,
+                                                             const PassDev pass, const OpDev *__restrict__ ops,
+                                                             const c_t<R> *__restrict__ mats,
+                                                             double *__restrict__ partials) {
   using C = c_t<R>;
   extern __shared__ __align__(16) unsigned char smem[];
   const int A = 1 << pass.T;
-  const int j0 = blockIdx.x * b;
-  const int bb = min(b, m - j0);
+  const int j0 = blockIdx.x * B;
+  const int bb = min(B, m - j0);
   C *sp = reinterpret_cast<C *>(smem);
-  C *sl = sp + A;  // b lambda tiles
-  uint64_t *lut = reinterpret_cast<uint64_t *>(sl + (size_t)b * A);
+  C *sl = sp + A;  // B lambda tiles; slots bb..B-1 stay zero
+  uint64_t *lut = reinterpret_cast<uint64_t *>(sl + (size_t)B * A);
   const int nch = 1 << (pass.T - pass.nlow);
-  double *accs = reinterpret_cast<double *>(lut + nch);  // [n_train][b][nwarps]
+  double *accs = reinterpret_cast<double *>(lut + nch);  // [n_train][B][nwarps]
   const int nwarps = blockDim.x >> 5;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   build_lut(lut, pass);
-  for (int i = threadIdx.x; i < pass.n_train * b * nwarps; i += blockDim.x) accs[i] = 0.0;
+  for (int i = threadIdx.x; i < pass.n_train * B * nwarps; i += blockDim.x) accs[i] = 0.0;
+  for (int i = threadIdx.x + bb * A; i < B * A; i += blockDim.x) {
+    C z;
+    z.x = R(0);
+    z.y = R(0);
+    sl[i] = z;
+  }
   TileGeom tg;
   tg.T = pass.T;
   tg.nlow = pass.nlow;
@@ -682,14 +875,15 @@ __global__ void __launch_bounds__(kBlock, 2) k_tile_adjoint(const g_t<R> *phi_in
       if (op.kind == kDense) {
         dense_any<R, MAXK>(sp, tg, op, mats);
         for (int jj = 0; jj < bb; ++jj) dense_any<R, MAXK>(sl + (size_t)jj * A, tg, op, mats);
-      } else {
-        Acc<R> acc[kMaxLambdaPerCta];
+      } else if (op_active(op, tg.base)) {
+        R acc[B];
+#pragma unroll
+        for (int jj = 0; jj < B; ++jj) acc[jj] = R(0);
         if (op.kind == kPair)
-          adj_pair<R>(sp, sl, bb, tg, op, mats, acc);
+          adj_pair<R, B>(sp, sl, tg, op, mats, acc);
         else
-          adj_diag<R>(sp, sl, bb, tg, op, mats, acc);
-        if (op.train >= 0)
-          flush_acc<R>(acc, bb, b, op.train, accs, nwarps, warp, lane, op.kind == kPair ? (R)op.gs : R(1));
+          adj_diag<R, B>(sp, sl, tg, op, mats, acc);
+        if (op.train >= 0) flush_acc<R, B>(acc, bb, op.train, accs, nwarps, warp, lane, op.kind == kPair ? (R)op.gs : R(1));
       }
       if (op.sync_prev && o > pass.op_begin) __syncthreads();
     }
@@ -701,7 +895,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_tile_adjoint(const g_t<R> *phi_in
   for (int i = threadIdx.x; i < pass.n_train * bb; i += blockDim.x) {
     const int t = i / bb, jj = i % bb;
     double v = 0.0;
-    for (int w = 0; w < nwarps; ++w) v += WarpAcc<R>::read(&accs[(t * b + jj) * nwarps + w]);
+    for (int w = 0; w < nwarps; ++w) v += WarpAcc<R>::read(&accs[(t * B + jj) * nwarps + w]);
     partials[((size_t)blockIdx.y * m + j0 + jj) * pass.n_train + t] = v;
   }
 }

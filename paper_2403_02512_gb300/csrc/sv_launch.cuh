@@ -53,28 +53,39 @@ cudaError_t Launch<R>::tile_forward(void *psi, int n, const PassDev &pass, const
   return cudaGetLastError();
 }
 
+namespace detail {
+template <typename R, int MAXK, int B>
+cudaError_t adjoint_b(const void *phi_in, void *phi_out, void *lam, int n, int m, const PassDev &pass,
+                      const OpDev *ops, const void *mats, double *partials, int grid, cudaStream_t st) {
+  static bool attr = false;
+  const int smem = (1 + B) * tile_bytes(sizeof(c_t<R>), pass.T) + lut_bytes(pass) + pass.n_train * B * kWarps * 8;
+  allow_big_smem(k_tile_adjoint<R, MAXK, B>, attr);
+  dim3 g((m + B - 1) / B, grid);
+  k_tile_adjoint<R, MAXK, B><<<g, kBlock, smem, st>>>(
+      reinterpret_cast<const g_t<R> *>(phi_in), reinterpret_cast<g_t<R> *>(phi_out), reinterpret_cast<g_t<R> *>(lam),
+      n, m, pass, ops, reinterpret_cast<const c_t<R> *>(mats), partials);
+  return cudaGetLastError();
+}
+
+template <typename R, int MAXK>
+cudaError_t adjoint_k(const void *phi_in, void *phi_out, void *lam, int n, int m, int b, const PassDev &pass,
+                      const OpDev *ops, const void *mats, double *partials, int grid, cudaStream_t st) {
+  switch (b) {
+    case 1: return adjoint_b<R, MAXK, 1>(phi_in, phi_out, lam, n, m, pass, ops, mats, partials, grid, st);
+    case 2: return adjoint_b<R, MAXK, 2>(phi_in, phi_out, lam, n, m, pass, ops, mats, partials, grid, st);
+    case 4: return adjoint_b<R, MAXK, 4>(phi_in, phi_out, lam, n, m, pass, ops, mats, partials, grid, st);
+    default: return cudaErrorInvalidValue;  // lambdas per CTA: 1, 2 or 4
+  }
+}
+}  // namespace detail
+
 template <typename R>
 cudaError_t Launch<R>::tile_adjoint(const void *phi_in, void *phi_out, void *lam, int n, int m, int b,
                                     const PassDev &pass, const OpDev *ops, const void *mats, double *partials,
                                     int grid, cudaStream_t st) {
-  static bool attr2 = false, attr4 = false;
-  const int smem = (1 + b) * detail::tile_bytes(sizeof(c_t<R>), pass.T) + detail::lut_bytes(pass) +
-                   pass.n_train * b * detail::kWarps * 8;
-  dim3 g((m + b - 1) / b, grid);
-  if (pass.max_k <= 2) {
-    detail::allow_big_smem(k_tile_adjoint<R, 2>, attr2);
-    k_tile_adjoint<R, 2><<<g, kBlock, smem, st>>>(reinterpret_cast<const g_t<R> *>(phi_in),
-                                                   reinterpret_cast<g_t<R> *>(phi_out),
-                                                   reinterpret_cast<g_t<R> *>(lam), n, m, b, pass, ops,
-                                                   reinterpret_cast<const c_t<R> *>(mats), partials);
-  } else {
-    detail::allow_big_smem(k_tile_adjoint<R, 4>, attr4);
-    k_tile_adjoint<R, 4><<<g, kBlock, smem, st>>>(reinterpret_cast<const g_t<R> *>(phi_in),
-                                                   reinterpret_cast<g_t<R> *>(phi_out),
-                                                   reinterpret_cast<g_t<R> *>(lam), n, m, b, pass, ops,
-                                                   reinterpret_cast<const c_t<R> *>(mats), partials);
-  }
-  return cudaGetLastError();
+  if (pass.max_k <= 2)
+    return detail::adjoint_k<R, 2>(phi_in, phi_out, lam, n, m, b, pass, ops, mats, partials, grid, st);
+  return detail::adjoint_k<R, 4>(phi_in, phi_out, lam, n, m, b, pass, ops, mats, partials, grid, st);
 }
 
 template <typename R>
