@@ -314,6 +314,51 @@ struct SlotTable {
     entries += mode == 0 ? (size_t)1 << (2 * h.k) : (mode == 1 ? (size_t)1 << h.k : 4);
     return m.out;
   }
+  // Fused run: a head slot (the run's 2x2 product) followed by its members;
+  // gens[i] is member i's generator (code, g0, g1) or code gNone.  Returns the
+  // product's offset; gmat = first generator output (consecutive, 4 each).
+  struct Gen {
+    int code;
+    double g0, g1;
+  };
+  int add_run(const std::vector<const HOp *> &mem, const std::vector<Gen> &gens, bool dagger, int &gmat) {
+    MatSlot hd;
+    memset(&hd, 0, sizeof(hd));
+    hd.kind = SV_MATRIX;
+    hd.k = 1;
+    hd.dagger = dagger ? 1 : 0;
+    hd.mode = 3;
+    hd.a = (int)slots.size() + 1;
+    hd.b = (int)mem.size();
+    hd.out = (int)entries;
+    entries += 4;
+    slots.push_back(hd);
+    gmat = (int)entries;
+    for (size_t i = 0; i < mem.size(); ++i) {
+      const HOp &h = *mem[i];
+      MatSlot m;
+      memset(&m, 0, sizeof(m));
+      m.kind = h.kind;
+      m.k = 1;
+      m.dagger = h.adjoint ? 1 : 0;
+      m.mode = 4;
+      m.a = gens[i].code;
+      m.g0 = gens[i].g0;
+      m.g1 = gens[i].g1;
+      for (int q = 0; q < 3; ++q) {
+        m.pidx[q] = h.pidx[q];
+        m.cangle[q] = h.cang[q];
+      }
+      m.scale = h.scale;
+      m.src = h.msrc;
+      if (gens[i].code != gNone) {
+        m.out = (int)entries;
+        entries += 4;
+      }
+      slots.push_back(m);
+    }
+    return hd.out;
+  }
 };
 
 int popc(uint64_t x) { return __builtin_popcountll(x); }
@@ -509,6 +554,116 @@ void lower_gate(int n, const HOp &h, const PassDev &pd, bool dagger, int train, 
   out.push_back(o);
 }
 
+// Generator of a trainable single-wire gate as the kernels accumulate it:
+// gs X or gs Y on the pair, diag(ga, gb) for a diagonal.
+bool single_wire_generator(const HOp &h, SlotTable::Gen &g) {
+  g = {gNone, 0.0, 0.0};
+  if (!h.train) return true;
+  if (h.diag) {
+    int zm;
+    float ga, gb;
+    diag_generator(h.kind, zm, ga, gb);
+    g = {gDiag, ga, gb};
+    return true;
+  }
+  std::vector<Block> bl;
+  if (!gate_blocks(h, bl) || bl.size() != 1 || bl[0].gcode == gNone) return false;
+  g = {bl[0].gcode, bl[0].gs, 0.0};
+  return true;
+}
+
+bool fusable(const HOp &h) {
+  if (h.kind == SV_IDENTITY || h.k != 1 || h.nc != 0) return false;
+  SlotTable::Gen g;
+  return single_wire_generator(h, g);
+}
+
+// Runs of single-wire gates: op i joins the open run on its wire when no gate
+// since the run's first member touched that wire (the ops in between act on
+// other wires and commute with it).  A run is kept when it has >= 2 members,
+// one of them non-diagonal, and at most kMaxFuseGen trainable members; it is
+// emitted at its first member's position.  Other ops keep their order.
+std::vector<std::vector<int>> fuse_groups(int n, const std::vector<HOp> &ops, bool fuse) {
+  std::vector<std::vector<int>> runs;
+  std::vector<int> run_of(ops.size(), -1);
+  if (fuse) {
+    std::vector<int> open(n, -1);
+    std::vector<int> gens;
+    for (int i = 0; i < (int)ops.size(); ++i) {
+      const HOp &h = ops[i];
+      if (h.kind == SV_IDENTITY) continue;
+      if (fusable(h)) {
+        const int w = h.tw[0];
+        const int r = open[w];
+        if (r >= 0 && (int)runs[r].size() < kMaxFuseMembers && gens[r] + (h.train ? 1 : 0) <= kMaxFuseGen) {
+          runs[r].push_back(i);
+          gens[r] += h.train ? 1 : 0;
+          run_of[i] = r;
+          continue;
+        }
+        open[w] = (int)runs.size();
+        run_of[i] = (int)runs.size();
+        runs.push_back({i});
+        gens.push_back(h.train ? 1 : 0);
+        continue;
+      }
+      for (int j = 0; j < h.k; ++j) open[h.tw[j]] = -1;
+      for (int c = 0; c < h.nc; ++c) open[h.cw[c]] = -1;
+    }
+    for (size_t r = 0; r < runs.size(); ++r) {
+      bool any_pair = false;
+      for (int i : runs[r]) any_pair |= !ops[i].diag;
+      if (runs[r].size() < 2 || !any_pair)
+        for (int i : runs[r]) run_of[i] = -1;
+    }
+  }
+  std::vector<std::vector<int>> out;
+  for (int i = 0; i < (int)ops.size(); ++i) {
+    const int r = run_of[i];
+    if (r < 0)
+      out.push_back({i});
+    else if (runs[r][0] == i)
+      out.push_back(runs[r]);
+  }
+  return out;
+}
+
+// Lower a fused run into one pair micro-op on its wire's local bit.
+void lower_fused(int n, const std::vector<HOp> &ops, const std::vector<int> &mem, const PassDev &pd, bool dagger,
+                 int train, int slot, SlotTable &st, std::vector<OpDev> &out) {
+  const HOp &h0 = ops[mem[0]];
+  OpDev o = blank_op(n, h0);
+  o.kind = kPair;
+  o.code = mGen;
+  int tl = -1;
+  for (int i = 0; i < pd.T; ++i)
+    if (pd.pos[i] == n - 1 - h0.tw[0]) tl = i;
+  o.ts[0] = o.tl[0] = (int8_t)tl;
+  o.oa = 0;
+  o.ob = 1 << tl;
+  std::vector<const HOp *> hs;
+  std::vector<SlotTable::Gen> gens;
+  int ngen = 0;
+  for (int i : mem) {
+    hs.push_back(&ops[i]);
+    SlotTable::Gen g;
+    single_wire_generator(ops[i], g);
+    gens.push_back(g);
+    ngen += g.code != gNone;
+  }
+  int gmat = 0;
+  o.mat = st.add_run(hs, gens, dagger, gmat);
+  if (ngen > 0) {
+    o.gcode = gHerm;
+    o.ngen = (int8_t)ngen;
+    o.gmat = gmat;
+    o.train = train;
+    o.slot = slot;
+  }
+  localise(o, pd);
+  out.push_back(o);
+}
+
 // Greedy order-preserving fusion (S4): gates join the current pass while the
 // union of the local bits they need (non-diagonal targets) plus the lowest
 // index bits fits in T bits.  The lowest bits are always local, so every tile
@@ -516,8 +671,9 @@ void lower_gate(int n, const HOp &h, const PassDev &pd, bool dagger, int train, 
 // 16-byte aligned for the paired complex64 accesses).  Each pass is then
 // lowered into micro-ops; dagger selects the adjoint sweep's U^dagger blocks.
 Plan plan_passes(int n, const std::vector<HOp> &ops, int Tmax, int nlow_pref, int max_train, bool dagger,
-                 SlotTable &st) {
+                 SlotTable &st, bool fuse = false) {
   Plan P;
+  const std::vector<std::vector<int>> groups = fuse_groups(n, ops, fuse);
   const int T = std::min(Tmax, n);
   const uint64_t low = low_bits(n, T, nlow_pref);
   uint64_t cur = low;
@@ -530,15 +686,27 @@ Plan plan_passes(int n, const std::vector<HOp> &ops, int Tmax, int nlow_pref, in
     pd.train_base = P.n_train;
     int t = 0;
     bool prev_diag = false;
-    for (int i : cur_ops) {
-      const HOp &h = ops[i];
+    for (int gi : cur_ops) {
+      const std::vector<int> &grp = groups[gi];
       const size_t before = P.ops.size();
-      const int slot = h.train ? P.n_train : -1;
-      lower_gate(n, h, pd, dagger, t, slot, st, P.ops);
-      if (h.train) {
-        ++t;
-        ++P.n_train;
-        P.train_hop.push_back(i);
+      if (grp.size() > 1) {
+        lower_fused(n, ops, grp, pd, dagger, t, P.n_train, st, P.ops);
+        for (int i : grp)
+          if (ops[i].train) {
+            ++t;
+            ++P.n_train;
+            P.train_hop.push_back(i);
+          }
+      } else {
+        const int i = grp[0];
+        const HOp &h = ops[i];
+        const int slot = h.train ? P.n_train : -1;
+        lower_gate(n, h, pd, dagger, t, slot, st, P.ops);
+        if (h.train) {
+          ++t;
+          ++P.n_train;
+          P.train_hop.push_back(i);
+        }
       }
       if (P.ops.size() > before) {
         OpDev &first = P.ops[before];
@@ -556,8 +724,20 @@ Plan plan_passes(int n, const std::vector<HOp> &ops, int Tmax, int nlow_pref, in
     cur = low;
     cur_train = 0;
   };
-  for (int i = 0; i < (int)ops.size(); ++i) {
-    const HOp &h = ops[i];
+  for (int gi = 0; gi < (int)groups.size(); ++gi) {
+    const std::vector<int> &grp = groups[gi];
+    if (grp.size() > 1) {
+      const uint64_t need = 1ull << (n - 1 - ops[grp[0]].tw[0]);
+      int gt = 0;
+      for (int i : grp) gt += ops[i].train ? 1 : 0;
+      const bool fits = popc(cur | need) <= T && cur_train + gt <= max_train;
+      if (!cur_ops.empty() && !fits) flush();
+      cur |= need;
+      cur_ops.push_back(gi);
+      cur_train += gt;
+      continue;
+    }
+    const HOp &h = ops[grp[0]];
     if (h.kind == SV_IDENTITY) continue;
     if (!h.diag && h.k > kMaxTileTargets) {
       flush();
@@ -574,7 +754,7 @@ Plan plan_passes(int n, const std::vector<HOp> &ops, int Tmax, int nlow_pref, in
     const bool fits = popc(cur | need) <= T && cur_train + (h.train ? 1 : 0) <= max_train;
     if (!cur_ops.empty() && !fits) flush();
     cur |= need;
-    cur_ops.push_back(i);
+    cur_ops.push_back(gi);
     cur_train += h.train ? 1 : 0;
   }
   flush();
@@ -908,8 +1088,8 @@ sv_status build_program(sv_state *s, const sv_tape *tape, const sv_pauli_sum *ob
     expand_op(h, aops);
   }
   SlotTable st_tab;
-  p->fwd = plan_passes(n, fops, K.Tf, K.nlow_pref, 1 << 30, false, st_tab);
-  p->adj = plan_passes(n, aops, K.Ta, K.nlow_pref, kMaxTrainPerPass, true, st_tab);
+  p->fwd = plan_passes(n, fops, K.Tf, K.nlow_pref, 1 << 30, false, st_tab, true);
+  p->adj = plan_passes(n, aops, K.Ta, K.nlow_pref, kMaxTrainPerPass, true, st_tab, true);
   if (sv_status st = check_plan(p->fwd, n, K.nlow_pref)) {
     destroy_program(p);
     return st;
@@ -2249,8 +2429,8 @@ sv_status sv_plan_query(int n, sv_dtype dtype, const sv_tape *tape, int *n_forwa
     expand_op(h, aops);
   }
   SlotTable st_tab;
-  Plan f = plan_passes(n, fops, K.Tf, K.nlow_pref, 1 << 30, false, st_tab);
-  Plan a = plan_passes(n, aops, K.Ta, K.nlow_pref, kMaxTrainPerPass, true, st_tab);
+  Plan f = plan_passes(n, fops, K.Tf, K.nlow_pref, 1 << 30, false, st_tab, true);
+  Plan a = plan_passes(n, aops, K.Ta, K.nlow_pref, kMaxTrainPerPass, true, st_tab, true);
   if (sv_status st = check_plan(f, n, K.nlow_pref)) return st;
   if (sv_status st = check_plan(a, n, K.nlow_pref)) return st;
   if (n_forward_passes) *n_forward_passes = (int)f.steps.size();

@@ -38,8 +38,14 @@ enum GenCode : int8_t {
   gNone = 0,
   gX = 1,    // gs * [[0,1],[1,0]] on the pair
   gY = 2,    // gs * [[0,-i],[i,0]] on the pair
-  gDiag = 3  // g = ga (even) / gb (odd) by the parity of pattern & zmask
+  gDiag = 3, // g = ga (even) / gb (odd) by the parity of pattern & zmask
+  gHerm = 4  // fused run: ngen general Hermitian 2x2 generators (entries at gmat)
 };
+// A run of single-wire gates on one wire (no other gate touching the wire in
+// between) is applied as one 2x2 block; its trainable members' generators are
+// carried to the run's end by conjugation with the members that follow them.
+constexpr int kMaxFuseGen = 3;      // trainable members per fused run
+constexpr int kMaxFuseMembers = 8;  // members per fused run
 
 // One micro-op of one pass.
 struct OpDev {
@@ -48,14 +54,14 @@ struct OpDev {
   int8_t tl[4];          // kDense: local bit of target j (j = 0 is the op's local MSB)
   int8_t tg[kMaxTargets];// kDiag / dense_k: global bit of target j
   int8_t sync_prev;      // barrier needed between the previous micro-op and this one
-  int8_t pad0;
+  int8_t ngen;           // gHerm: generators (trainable indices train .. train + ngen - 1)
   int32_t oa, ob;        // kPair: local offsets of the two members within a group
   int32_t zmask;         // gDiag: target-pattern bits whose parity selects gb
   int32_t train;         // trainable index within the pass, or -1
   int32_t mat;           // matrix entries: kPair 4 (2x2 block), kDiag 2^k, kDense / dense_k 4^k
   int32_t slot;          // global trainable slot, or -1
   float gs, ga, gb;
-  int32_t pad1;
+  int32_t gmat;          // gHerm: first generator (4 entries each, row-major)
   uint64_t cmask, cval;  // control bits (global) and their required values
   // The same controls split by the pass's tiles: local bits (as local-index
   // bits) vary inside a tile; the others are fixed per tile.
@@ -90,7 +96,11 @@ struct TermDev {
 // Gate-matrix slot built on the device from the parameter vector: the op's
 // matrix E = U, or U^dagger when `dagger` (op's own adjoint flag XOR the
 // adjoint sweep), written whole (mode 0), as its diagonal (1) or as the 2x2
-// block on members (a, b) (2).
+// block on members (a, b) (2).  A fused run (mode 3) takes its members from
+// slots [a, a + b) (mode 4, forward order, `dagger` = the member's own adjoint
+// flag) and writes the run's product (adjoint when `dagger`) plus, for each
+// trainable member (a = generator code gX / gY / gDiag with g0, g1 = gs or
+// ga, gb), the conjugated generator at the member's `out`.
 struct MatSlot {
   int32_t kind;        // sv_op_kind
   int32_t k;
@@ -102,6 +112,7 @@ struct MatSlot {
   double scale;
   double cangle[3];
   int64_t src;         // SV_MATRIX: offset (complex entries) of the user matrix
+  double g0, g1;       // mode 4: generator parameters
 };
 
 // ---- batched circuits (S9) --------------------------------------------------

@@ -741,6 +741,92 @@ __device__ __forceinline__ void adj_pair(c_t<R> *sp, c_t<R> *sl, const TileGeom 
   }
 }
 
+// Fused run in the adjoint sweep: phi and B lambdas on pairs (a, b); for each
+// of NG generators G' (Hermitian: G00, G11 real, G10 = conj(G01)) the phi-side
+// products w = G' phi are formed once per pair and every lambda adds
+// Im(conj(l_a) w_a + conj(l_b) w_b) before the run's U^dagger is applied.
+template <typename R, int B, int NG, bool CTL>
+__device__ void adj_fused_t(c_t<R> *sp, c_t<R> *sl, const TileGeom &tg, const OpDev &op,
+                            const c_t<R> *__restrict__ mats, int bb, double *accs, int nwarps, int warp, int lane) {
+  using C = c_t<R>;
+  C Mr[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) Mr[q] = mats[op.mat + q];
+  R g00[NG], g11[NG];
+  C g01[NG];
+#pragma unroll
+  for (int g = 0; g < NG; ++g) {
+    g00[g] = mats[op.gmat + 4 * g].x;
+    g01[g] = mats[op.gmat + 4 * g + 1];
+    g11[g] = mats[op.gmat + 4 * g + 3].x;
+  }
+  R acc[NG][B];
+#pragma unroll
+  for (int g = 0; g < NG; ++g)
+#pragma unroll
+    for (int jj = 0; jj < B; ++jj) acc[g][jj] = R(0);
+  const OpRegs o(op);
+  const uint32_t lcm = op.lcmask, lcv = op.lcval;
+  const int ng = tg.A >> 1;
+  for (int gi = threadIdx.x; gi < ng; gi += blockDim.x) {
+    const int l0 = o.base(gi);
+    if (CTL && (((uint32_t)l0 & lcm) != lcv)) continue;
+    const int ia = l0 + o.oa, ib = l0 + o.ob;
+    C pa = sp[ia], pb = sp[ib];
+    C wa[NG], wb[NG];
+#pragma unroll
+    for (int g = 0; g < NG; ++g) {
+      // wa = g00 pa + g01 pb ; wb = conj(g01) pa + g11 pb
+      wa[g].x = fma(g01[g].x, pb.x, fma(-g01[g].y, pb.y, g00[g] * pa.x));
+      wa[g].y = fma(g01[g].x, pb.y, fma(g01[g].y, pb.x, g00[g] * pa.y));
+      wb[g].x = fma(g01[g].x, pa.x, fma(g01[g].y, pa.y, g11[g] * pb.x));
+      wb[g].y = fma(g01[g].x, pa.y, fma(-g01[g].y, pa.x, g11[g] * pb.y));
+    }
+    pair_apply<R>(mGen, Mr, pa, pb);
+    sp[ia] = pa;
+    sp[ib] = pb;
+#pragma unroll
+    for (int jj = 0; jj < B; ++jj) {
+      C la = sl[jj * tg.A + ia], lb = sl[jj * tg.A + ib];
+#pragma unroll
+      for (int g = 0; g < NG; ++g) {
+        R a = acc[g][jj];
+        a = fma(la.x, wa[g].y, a);
+        a = fma(-la.y, wa[g].x, a);
+        a = fma(lb.x, wb[g].y, a);
+        a = fma(-lb.y, wb[g].x, a);
+        acc[g][jj] = a;
+      }
+      pair_apply<R>(mGen, Mr, la, lb);
+      sl[jj * tg.A + ia] = la;
+      sl[jj * tg.A + ib] = lb;
+    }
+  }
+#pragma unroll
+  for (int g = 0; g < NG; ++g) flush_acc<R, B>(acc[g], bb, op.train + g, accs, nwarps, warp, lane, R(1));
+}
+
+template <typename R, int B, int NG>
+__device__ __forceinline__ void adj_fused_c(c_t<R> *sp, c_t<R> *sl, const TileGeom &tg, const OpDev &op,
+                                            const c_t<R> *mats, int bb, double *accs, int nwarps, int warp,
+                                            int lane) {
+  if (op.lcmask)
+    adj_fused_t<R, B, NG, true>(sp, sl, tg, op, mats, bb, accs, nwarps, warp, lane);
+  else
+    adj_fused_t<R, B, NG, false>(sp, sl, tg, op, mats, bb, accs, nwarps, warp, lane);
+}
+
+template <typename R, int B>
+__device__ __forceinline__ void adj_fused(c_t<R> *sp, c_t<R> *sl, const TileGeom &tg, const OpDev &op,
+                                          const c_t<R> *mats, int bb, double *accs, int nwarps, int warp, int lane) {
+  if (op.ngen == 1)
+    adj_fused_c<R, B, 1>(sp, sl, tg, op, mats, bb, accs, nwarps, warp, lane);
+  else if (op.ngen == 2)
+    adj_fused_c<R, B, 2>(sp, sl, tg, op, mats, bb, accs, nwarps, warp, lane);
+  else
+    adj_fused_c<R, B, 3>(sp, sl, tg, op, mats, bb, accs, nwarps, warp, lane);
+}
+
 // Adjoint diagonal micro-op: acc[j] += g(idx) Im(conj(lambda_j) phi) before
 // multiplying phi and every lambda by the stored (adjoint) entry.
 template <typename R, int B, int KD, bool NEG, bool CTL, bool TRAIN>
@@ -875,6 +961,8 @@ __global__ void __launch_bounds__(kBlock, 2) k_tile_adjoint(const g_t<R> *phi_in
       if (op.kind == kDense) {
         dense_any<R, MAXK>(sp, tg, op, mats);
         for (int jj = 0; jj < bb; ++jj) dense_any<R, MAXK>(sl + (size_t)jj * A, tg, op, mats);
+      } else if (op.gcode == gHerm && op.train >= 0) {
+        if (op_active(op, tg.base)) adj_fused<R, B>(sp, sl, tg, op, mats, bb, accs, nwarps, warp, lane);
       } else if (op_active(op, tg.base)) {
         R acc[B];
 #pragma unroll
@@ -1189,6 +1277,76 @@ __device__ __forceinline__ void put_entry(const MatSlot &sl, c_t<R> *o, int r, i
 
 // One thread per slot: E = U (or U^dagger) from FP64 trigonometry, written
 // whole, as its diagonal, or as one 2x2 block.
+__device__ __forceinline__ double2 zmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 zadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 zconj(double2 a) { return make_double2(a.x, -a.y); }
+
+// 2x2 matrix of a single-wire member of a fused run (its own adjoint applied).
+__device__ inline void member_matrix(const MatSlot &m, const double *__restrict__ params, const double *__restrict__ user,
+                              double2 (&u)[4]) {
+  if (m.kind == SV_MATRIX) {
+    for (int e = 0; e < 4; ++e) u[e] = make_double2(user[2 * (m.src + e)], user[2 * (m.src + e) + 1]);
+  } else {
+    double a[3];
+    for (int q = 0; q < 3; ++q) a[q] = m.pidx[q] >= 0 ? m.scale * params[m.pidx[q]] : m.cangle[q];
+    double2 g[256];
+    gate_matrix(m.kind, a, g);
+    for (int e = 0; e < 4; ++e) u[e] = g[e];
+  }
+  if (m.dagger) {
+    const double2 t = u[1];
+    u[0] = zconj(u[0]);
+    u[1] = zconj(u[2]);
+    u[2] = zconj(t);
+    u[3] = zconj(u[3]);
+  }
+}
+
+// Fused run: V = U_r ... U_1 built from the last member backwards; a trainable
+// member i gets G_i' = W G_i W^dagger with W = U_r ... U_{i+1}, the generator
+// seen from the run's end (Im<lambda|G_i' phi> there equals Im<lambda|G_i phi>
+// right after member i).
+template <typename R>
+__device__ void build_run(const MatSlot *__restrict__ slots, const MatSlot &head, const double *__restrict__ params,
+                          const double *__restrict__ user, c_t<R> *__restrict__ out) {
+  double2 V[4] = {make_double2(1, 0), make_double2(0, 0), make_double2(0, 0), make_double2(1, 0)};
+  auto put = [&](int off, int e, double2 v) {
+    c_t<R> c;
+    c.x = (R)v.x;
+    c.y = (R)v.y;
+    out[off + e] = c;
+  };
+  for (int q = head.b - 1; q >= 0; --q) {
+    const MatSlot m = slots[head.a + q];
+    if (m.a != gNone) {
+      double2 G[4];
+      if (m.a == gX) {
+        G[0] = make_double2(0, 0); G[1] = make_double2(m.g0, 0); G[2] = make_double2(m.g0, 0); G[3] = make_double2(0, 0);
+      } else if (m.a == gY) {
+        G[0] = make_double2(0, 0); G[1] = make_double2(0, -m.g0); G[2] = make_double2(0, m.g0); G[3] = make_double2(0, 0);
+      } else {
+        G[0] = make_double2(m.g0, 0); G[1] = make_double2(0, 0); G[2] = make_double2(0, 0); G[3] = make_double2(m.g1, 0);
+      }
+      double2 T[4];  // V G
+      for (int r = 0; r < 2; ++r)
+        for (int c = 0; c < 2; ++c) T[r * 2 + c] = zadd(zmul(V[r * 2], G[c]), zmul(V[r * 2 + 1], G[2 + c]));
+      for (int r = 0; r < 2; ++r)  // (V G) V^dagger
+        for (int c = 0; c < 2; ++c)
+          put(m.out, r * 2 + c, zadd(zmul(T[r * 2], zconj(V[c * 2])), zmul(T[r * 2 + 1], zconj(V[c * 2 + 1]))));
+    }
+    double2 U[4];
+    member_matrix(m, params, user, U);
+    double2 W[4];
+    for (int r = 0; r < 2; ++r)
+      for (int c = 0; c < 2; ++c) W[r * 2 + c] = zadd(zmul(V[r * 2], U[c]), zmul(V[r * 2 + 1], U[2 + c]));
+    for (int e = 0; e < 4; ++e) V[e] = W[e];
+  }
+  for (int r = 0; r < 2; ++r)
+    for (int c = 0; c < 2; ++c) put(head.out, r * 2 + c, head.dagger ? zconj(V[c * 2 + r]) : V[r * 2 + c]);
+}
+
 template <typename R>
 __global__ void k_build_matrices(const MatSlot *__restrict__ slots, int n_slots,
                                  const double *__restrict__ params, const double *__restrict__ user,
@@ -1196,6 +1354,11 @@ __global__ void k_build_matrices(const MatSlot *__restrict__ slots, int n_slots,
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_slots) return;
   const MatSlot sl = slots[i];
+  if (sl.mode == 4) return;  // member of a fused run: built by its head
+  if (sl.mode == 3) {
+    build_run<R>(slots, sl, params, user, out);
+    return;
+  }
   const int D = 1 << sl.k;
   c_t<R> *o = out + sl.out;
   if (sl.kind == SV_MATRIX) {
