@@ -186,31 +186,37 @@ def _timed(fn, reps, stream):
     return e0.elapsed_time(e1) / reps
 
 
-def extra_gates(hbm_peak):
-    """Per-gate pass at 30 qubits (RX, Hadamard, CNOT on several target wires)."""
+def extra_gates(hbm_peak, wires_step=1):
+    """Per-gate pass at 30 qubits for every target wire (the per-index study):
+    RX, Hadamard, CNOT (control wire t+1 mod n).  Reported per wire as GB/s of
+    algorithmic bytes (2V, or V for a one-control gate: half the pairs) and as
+    a fraction of the measured HBM peak."""
     import torch
     from paper_2403_02512_gb300.torch_api import Program, StateVector
     from workloads import Op
     out = {}
-    for dtype in ("c128", "c64"):
+    for dtype in ("c128", "c128df", "c64"):
         n = 30
         sv = StateVector(n, dtype)
-        V = (16 if dtype == "c128" else 8) << n
-        rows = []
-        for name, wires in (("RX", [0]), ("RX", [15]), ("RX", [29]), ("Hadamard", [29]), ("PauliX", [0]),
-                            ("PauliX", [29])):
-            ctrl = () if name != "PauliX" else ((wires[0] + 1) % n,)
-            op = Op(name, tuple(wires), (0,) if name == "RX" else (), ctrl)
-            prog = Program(sv, [op], 1 if name == "RX" else 0)
-            prog.set_params([0.3] if name == "RX" else [])
-            ms = _timed(lambda: prog.forward(reset=False), 5, torch.cuda.current_stream())
-            moved = 2.0 * V
-            alg = moved / 2 if ctrl else moved  # Alg. 2: a controlled gate touches half the pairs
-            rows.append({"gate": ("CNOT" if ctrl else name), "target_wire": wires[0], "ms": ms,
-                         "gbs_moved": moved / ms / 1e6, "frac_moved": moved / ms / 1e6 / hbm_peak,
-                         "gbs_algorithmic": alg / ms / 1e6})
-            prog.close()
-        out[dtype] = rows
+        V = (8 if dtype == "c64" else 16) << n
+        res = {}
+        for name in ("RX", "Hadamard", "CNOT"):
+            fr, ms_l = [], []
+            for t in range(0, n, wires_step):
+                if name == "CNOT":
+                    op = Op("PauliX", (t,), (), ((t + 1) % n,))
+                else:
+                    op = Op(name, (t,), (0,) if name == "RX" else ())
+                prog = Program(sv, [op], 1 if name == "RX" else 0)
+                prog.set_params([0.3] if name == "RX" else [])
+                ms = _timed(lambda: prog.forward(reset=False), 5, torch.cuda.current_stream())
+                alg = (V if name == "CNOT" else 2.0 * V)
+                fr.append(round(alg / ms / 1e6 / hbm_peak, 4))
+                ms_l.append(round(ms, 3))
+                prog.close()
+            res[name] = {"wires": list(range(0, n, wires_step)), "ms": ms_l, "frac_of_hbm": fr,
+                         "frac_min": min(fr), "frac_median": float(np.median(fr)), "frac_max": max(fr)}
+        out[dtype] = res
         sv.close()
         torch.cuda.empty_cache()
     return out

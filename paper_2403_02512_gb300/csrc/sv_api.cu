@@ -892,14 +892,18 @@ struct Ops {
   decltype(&Launch<float>::dense_k) dense_k;
   decltype(&Launch<float>::set_basis) set_basis;
   decltype(&Launch<float>::copy) copy;
+  decltype(&Launch<float>::stream_op) stream_op;
   int amp_bytes, Tf, Ta, nlow_pref;
+  int adj_bmax, adj_cps;  // lambdas per adjoint CTA (largest variant), adjoint CTAs per SM
 };
 
 const Ops &ops_df() {
   static const Ops d = {Launch<df>::build_matrices, Launch<df>::tile_forward, Launch<df>::tile_adjoint,
                         Launch<df>::expval_pass,    Launch<df>::lambda_pass,  Launch<df>::dense_k,
                         Launch<df>::set_basis,      Launch<df>::copy,
-                        16, Launch<df>::max_T_forward(), Launch<df>::max_T_adjoint(), 3};
+                        Launch<df>::stream_op,
+                        16, Launch<df>::max_T_forward(), Launch<df>::max_T_adjoint(), 3,
+                        Launch<df>::adj_lambdas_max(), Launch<df>::adj_ctas_per_sm()};
   return d;
 }
 
@@ -908,12 +912,16 @@ const Ops &ops_for(sv_dtype dt) {
                           Launch<float>::tile_adjoint,   Launch<float>::expval_pass,
                           Launch<float>::lambda_pass,    Launch<float>::dense_k,
                           Launch<float>::set_basis,      Launch<float>::copy,
-                          8, Launch<float>::max_T_forward(), Launch<float>::max_T_adjoint(), 4};
+                          Launch<float>::stream_op,
+                          8, Launch<float>::max_T_forward(), Launch<float>::max_T_adjoint(), 4,
+                          Launch<float>::adj_lambdas_max(), Launch<float>::adj_ctas_per_sm()};
   static const Ops f64 = {Launch<double>::build_matrices, Launch<double>::tile_forward,
                           Launch<double>::tile_adjoint,   Launch<double>::expval_pass,
                           Launch<double>::lambda_pass,    Launch<double>::dense_k,
                           Launch<double>::set_basis,      Launch<double>::copy,
-                          16, Launch<double>::max_T_forward(), Launch<double>::max_T_adjoint(), 3};
+                          Launch<double>::stream_op,
+                          16, Launch<double>::max_T_forward(), Launch<double>::max_T_adjoint(), 3,
+                          Launch<double>::adj_lambdas_max(), Launch<double>::adj_ctas_per_sm()};
   return dt == SV_C64 ? f32 : f64;
 }
 
@@ -1021,6 +1029,7 @@ struct sv_program {
   int ctas_a = 1, ctas_l = 1;        // CTAs per adjoint / lambda launch (split over lambdas)
   uint64_t tiles_a = 1, tiles_l = 1; // tiles per vector in those passes
   int lam_per_cta = 1;               // lambdas sharing one phi tile in the adjoint kernel
+  int cfg_compute = -1;              // compute mode the adjoint launch shape was made for
   int groups_a(int mcc) const { return (mcc + lam_per_cta - 1) / lam_per_cta; }
   int grid_a(int mcc) const {
     return (int)std::max<uint64_t>(1, std::min<uint64_t>(tiles_a, ctas_a / std::max(1, groups_a(mcc))));
@@ -1043,6 +1052,27 @@ int blocks_per_sm(int smem_bytes) {
   const int by_threads = 2048 / kBlock;
   const int by_smem = (228 * 1024) / (smem_bytes + 1024);
   return std::max(1, std::min(by_threads, by_smem));
+}
+
+// Adjoint launch shape for the state's current compute mode: lambdas per CTA
+// (a compiled power of two that fits the shared-memory budget) and CTAs.
+void adj_config(sv_program *p, const Ops &K, int n) {
+  const int ta = std::min(K.Ta, n);
+  const int tile_b = K.amp_bytes << ta;
+  const int budget = (224 / K.adj_cps) * 1024 - tile_b - (8 << ta);
+  const int lpc = std::max(1, std::min({K.adj_bmax, std::max(1, p->mc),
+                                        budget / (tile_b + kMaxTrainPerPass * 8 * (kBlock / 32))}));
+  int b = 1;
+  while (2 * b <= lpc) b *= 2;
+  p->lam_per_cta = b;
+  const int smem_a = tile_b * (1 + b) + (8 << ta) + kMaxTrainPerPass * 8 * (kBlock / 32) * b;
+  p->ctas_a = 2 * sm_count() * std::min(K.adj_cps, blocks_per_sm(smem_a));
+  p->tiles_a = 1ull << (n - ta);
+  p->cfg_compute = p->s->compute;
+}
+
+void sync_adj_config(sv_program *p) {
+  if (p->cfg_compute != p->s->compute) adj_config(p, ops_of(p->s), p->s->n);
 }
 
 sv_status build_program(sv_state *s, const sv_tape *tape, const sv_pauli_sum *obs, int n_obs,
@@ -1198,15 +1228,7 @@ sv_status build_program(sv_state *s, const sv_tape *tape, const sv_pauli_sum *ob
     int tmax = std::min(K.Tf, n);
     p->grid_f = std::max(1, std::min((int)std::min<uint64_t>(1ull << (n - tmax), 1 << 30),
                                      2 * sms * blocks_per_sm((K.amp_bytes << tmax) + 4096)));
-    int ta = std::min(K.Ta, n);
-    const int tile_b = K.amp_bytes << ta;
-    const int budget = 112 * 1024 - tile_b - (8 << ta);
-    int lpc = std::max(1, std::min({kMaxLambdaPerCta, std::max(1, mc),
-                                    budget / (tile_b + kMaxTrainPerPass * 8 * (kBlock / 32))}));
-    p->lam_per_cta = lpc >= 4 ? 4 : lpc >= 2 ? 2 : 1;  // the adjoint kernel is compiled for 1, 2 and 4
-    const int smem_a = tile_b * (1 + p->lam_per_cta) + (8 << ta) + kMaxTrainPerPass * 8 * (kBlock / 32) * p->lam_per_cta;
-    p->ctas_a = 2 * sms * blocks_per_sm(smem_a);
-    p->tiles_a = 1ull << (n - ta);
+    adj_config(p, K, n);
     p->grid_e = std::max(1, std::min((int)std::min<uint64_t>(1ull << (n - tmax), 1 << 30),
                                      sms * blocks_per_sm((K.amp_bytes << tmax) + 4096 + 32768)));
     p->ctas_l = 2 * sms * blocks_per_sm((K.amp_bytes << tmax) + 4096);
@@ -1319,6 +1341,7 @@ sv_status program_set_params(sv_program *p, const double *params, int on_device)
 // arithmetic mode changed since the parameters were set.
 sv_status ensure_mats(sv_program *p) {
   sv_state *s = p->s;
+  sync_adj_config(p);
   if (!p->params_set || p->mats_compute == s->compute || p->n_slots == 0) return SV_OK;
   LaunchTimer t(s->stream, 5);
   sv_status st = after_launch(s, ops_of(s).build_matrices(p->d_slots, p->n_slots, p->d_params, p->d_user, p->d_mats,
@@ -1334,6 +1357,40 @@ sv_status require_params(const sv_program *p) {
   return SV_OK;
 }
 
+// A pass of one pair op, or one diagonal op on <= 2 targets, runs as a stream
+// over the amplitudes it touches (no tile, no shared memory).
+bool make_stream(int n, const PassDev &pd, const OpDev &o, bool c64, StreamDev &sd) {
+  memset(&sd, 0, sizeof(sd));
+  if (o.kind == kDense || (o.kind == kDiag && o.k > 2)) return false;
+  uint64_t fixed = o.cmask, val = o.cval;
+  if (o.kind == kPair) {
+    for (int j = 0; j < o.k; ++j) fixed |= 1ull << o.tg[j];
+    for (int i = 0; i < pd.T; ++i) {
+      if ((o.oa >> i) & 1) sd.oa |= 1ull << pd.pos[i];
+      if ((o.ob >> i) & 1) sd.ob |= 1ull << pd.pos[i];
+    }
+  } else {
+    sd.tg0 = o.tg[0];
+    sd.tg1 = o.k > 1 ? o.tg[1] : 0;
+    if (o.code == dNeg)
+      for (int j = 0; j < o.k; ++j) {
+        fixed |= 1ull << o.tg[j];
+        val |= 1ull << o.tg[j];
+      }
+  }
+  if (popc(fixed) > 16 || popc(fixed) > n) return false;
+  for (int b = 0; b < n; ++b)
+    if ((fixed >> b) & 1) sd.fix[sd.nfix++] = (int8_t)b;
+  sd.kind = o.kind;
+  sd.code = o.code;
+  sd.k = o.k;
+  sd.fixval = val;
+  sd.mat = o.mat;
+  sd.vec2 = c64 && !(fixed & 1) && n - sd.nfix >= 1;
+  sd.pair16 = c64 && o.kind == kPair && sd.oa == 0 && sd.ob == 1;
+  return true;
+}
+
 sv_status run_steps_forward(sv_program *p, void *psi) {
   sv_state *s = p->s;
   if (sv_status r = ensure_mats(p)) return r;
@@ -1345,7 +1402,13 @@ sv_status run_steps_forward(sv_program *p, void *psi) {
       e = K.dense_k(psi, s->n, p->fwd.dk_ops[st.index], p->d_mats, 0, s->stream);
     } else {
       LaunchTimer t(s->stream, 0);
-      e = K.tile_forward(psi, s->n, p->fwd.passes[st.index], p->d_fwd_ops, p->d_mats, p->grid_f, s->stream);
+      const PassDev &pd = p->fwd.passes[st.index];
+      StreamDev sd;
+      if (pd.op_end - pd.op_begin == 1 &&
+          make_stream(s->n, pd, p->fwd.ops[pd.op_begin], s->dt == SV_C64, sd))
+        e = K.stream_op(psi, s->n, sd, p->d_mats, s->stream);
+      else
+        e = K.tile_forward(psi, s->n, pd, p->d_fwd_ops, p->d_mats, p->grid_f, s->stream);
     }
     if (sv_status r = after_launch(s, e, "forward pass")) return r;
     ++p->launches;
@@ -1361,6 +1424,7 @@ struct JacWs {
 
 sv_status jac_workspace(sv_program *p, JacWs &w) {
   sv_state *s = p->s;
+  sync_adj_config(p);
   const size_t V = s->bytes;
   size_t max_train = 1;
   for (const PassDev &pd : p->adj.passes) max_train = std::max<size_t>(max_train, pd.n_train);

@@ -16,7 +16,7 @@ constexpr int kMaxTargets = 6;      // dense ops inside a tile: k <= 4; dense_k 
 constexpr int kMaxTileTargets = 4;
 constexpr int kMaxQubits = 34;
 constexpr int kBlock = 256;         // threads per CTA in the tile kernels
-constexpr int kMaxLambdaPerCta = 4; // lambdas sharing one phi tile in the adjoint kernel
+constexpr int kMaxLambdaPerCta = 8; // lambdas sharing one phi tile in the adjoint kernel (at most)
 constexpr int kMaxTrainPerPass = 32;
 
 // Micro-op kinds.  Every structured gate is a set of independent 2x2 blocks on
@@ -115,6 +115,22 @@ struct MatSlot {
   double g0, g1;       // mode 4: generator parameters
 };
 
+// A pass that holds one pair or diagonal micro-op runs straight from HBM
+// (Alg. 2's enumeration: the unit index gets a zero inserted at every fixed
+// bit, then the fixed values are or-ed in).  Pair units are the op's amplitude
+// pairs; diagonal units are the amplitudes it scales.
+struct StreamDev {
+  int32_t kind, code, k;  // kPair (code) or kDiag (code, k <= 2 targets)
+  int32_t nfix;           // fixed index bits (targets of a pair, controls, dNeg targets), ascending
+  int8_t fix[16];
+  uint64_t fixval;        // required values of the fixed bits
+  uint64_t oa, ob;        // kPair: global offsets of the two members
+  int32_t tg0, tg1;       // kDiag: global bits of the targets (entry = bit(tg0) [, bit(tg1)])
+  int32_t mat;            // entries in the matrix buffer
+  int32_t vec2;           // complex64: bit 0 is free, two adjacent units per 16-byte access
+  int32_t pair16;         // complex64 pair on bit 0 alone: both members in one 16-byte access
+};
+
 // ---- batched circuits (S9) --------------------------------------------------
 // One circuit of a batch: its passes, its Z-only observable and its state slice.
 struct BatchCircuit {
@@ -162,6 +178,7 @@ struct Launch {
   static cudaError_t dense_k(void *psi, int n, const OpDev &op, const void *mats, int adjoint,
                              cudaStream_t st);
   static cudaError_t set_basis(void *psi, int n, uint64_t index, cudaStream_t st);
+  static cudaError_t stream_op(void *psi, int n, const StreamDev &sd, const void *mats, cudaStream_t st);
   // Persistent batch launch: `grid` CTAs drain the work items of all segments.
   static cudaError_t batch(void *states, const BatchCircuit *circs, const PassDev *passes, const OpDev *ops,
                            const void *mats, const BatchSeg *segs, int n_segs, int64_t total_items,
@@ -175,6 +192,9 @@ struct Launch {
   static int expval_smem(int T, int n_terms);
   static int max_T_forward();
   static int max_T_adjoint();
+  // lambdas per adjoint CTA (largest compiled variant) and resident adjoint CTAs per SM
+  static int adj_lambdas_max();
+  static int adj_ctas_per_sm();
 };
 
 // Batch: out[c.out] = sum_term coeff * sum_tile partials (fixed order), one thread per circuit.

@@ -916,7 +916,7 @@ __device__ __forceinline__ void adj_diag(c_t<R> *sp, c_t<R> *sl, const TileGeom 
 }
 
 template <typename R, int MAXK, int B>
-__global__ void __launch_bounds__(kBlock, 2) k_tile_adjoint(const g_t<R> *phi_in, g_t<R> *phi_out,
+__global__ void __launch_bounds__(kBlock, std::is_same<R, double>::value ? 1 : 2) k_tile_adjoint(const g_t<R> *phi_in, g_t<R> *phi_out,
                                                              g_t<R> *__restrict__ lam_base, int n, int m,
                                                              const PassDev pass, const OpDev *__restrict__ ops,
                                                              const c_t<R> *__restrict__ mats,
@@ -1383,6 +1383,183 @@ __global__ void k_build_matrices(const MatSlot *__restrict__ slots, int n_slots,
       const double2 v = sl.dagger ? make_double2(m[c * D + r].x, -m[c * D + r].y) : m[r * D + c];
       put_entry<R>(sl, o, r, c, v.x, v.y);
     }
+}
+
+// ---------------------------------------------------------------------------
+// Single-op passes straight from HBM: every thread takes kStreamUnroll units
+// per step, issues all their loads before any store (several 128-bit accesses
+// in flight per thread), and the grid strides over the units.
+// ---------------------------------------------------------------------------
+constexpr int kStreamUnroll = 4;
+
+__device__ __forceinline__ uint64_t stream_index(const StreamDev &sd, uint64_t u) {
+  for (int j = 0; j < sd.nfix; ++j) {
+    const int b = sd.fix[j];
+    u = ((u >> b) << (b + 1)) | (u & ((1ull << b) - 1));
+  }
+  return u | sd.fixval;
+}
+
+// Streams of a double-float state use FP64 arithmetic on the stored complex128
+// amplitudes: one pass does a few operations per amplitude, fewer than the
+// conversions to and from double-float would cost.
+template <typename R>
+using stream_t = typename std::conditional<std::is_same<R, df>::value, double, R>::type;
+
+template <typename R>
+__device__ __forceinline__ c_t<stream_t<R>> stream_entry(const c_t<R> &e) {
+  if constexpr (std::is_same<R, df>::value)
+    return make_double2((double)e.x, (double)e.y);
+  else
+    return e;
+}
+
+template <typename R0, int CODE>
+__global__ void __launch_bounds__(kBlock) k_stream_pair(g_t<R0> *__restrict__ psi, uint64_t units, const StreamDev sd,
+                                                        const c_t<R0> *__restrict__ mats) {
+  using R = stream_t<R0>;
+  using C = c_t<R>;
+  C M[4];
+  if (CODE == mGen || CODE == mReal || CODE == mImOff)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) M[q] = stream_entry<R0>(mats[sd.mat + q]);
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  if constexpr (std::is_same<R, float>::value) {
+    if (sd.vec2) {  // units 2v, 2v + 1 are adjacent amplitudes in both members
+      float4 *p4 = reinterpret_cast<float4 *>(psi);
+      const uint64_t nv = units >> 1;
+      for (uint64_t v0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v0 < nv; v0 += stride * kStreamUnroll) {
+        uint64_t ia[kStreamUnroll];
+        float4 a[kStreamUnroll], b[kStreamUnroll];
+#pragma unroll
+        for (int r = 0; r < kStreamUnroll; ++r) {
+          const uint64_t v = v0 + r * stride;
+          ia[r] = v < nv ? stream_index(sd, v << 1) : 0;
+          if (v < nv) {
+            a[r] = __ldcs(p4 + ((ia[r] + sd.oa) >> 1));
+            b[r] = __ldcs(p4 + ((ia[r] + sd.ob) >> 1));
+          }
+        }
+#pragma unroll
+        for (int r = 0; r < kStreamUnroll; ++r) {
+          if (v0 + r * stride >= nv) break;
+          C a0 = make_float2(a[r].x, a[r].y), a1 = make_float2(a[r].z, a[r].w);
+          C b0 = make_float2(b[r].x, b[r].y), b1 = make_float2(b[r].z, b[r].w);
+          pair_apply<R>(CODE, M, a0, b0);
+          pair_apply<R>(CODE, M, a1, b1);
+          __stcs(p4 + ((ia[r] + sd.oa) >> 1), make_float4(a0.x, a0.y, a1.x, a1.y));
+          __stcs(p4 + ((ia[r] + sd.ob) >> 1), make_float4(b0.x, b0.y, b1.x, b1.y));
+        }
+      }
+      return;
+    }
+    if (sd.pair16) {  // members 2v, 2v + 1; twice the units per step (one access each)
+      constexpr int U2 = 2 * kStreamUnroll;
+      float4 *p4 = reinterpret_cast<float4 *>(psi);
+      for (uint64_t u0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; u0 < units; u0 += stride * U2) {
+        uint64_t ia[U2];
+        float4 a[U2];
+#pragma unroll
+        for (int r = 0; r < U2; ++r) {
+          const uint64_t u = u0 + r * stride;
+          ia[r] = u < units ? stream_index(sd, u) >> 1 : 0;
+          if (u < units) a[r] = __ldcs(p4 + ia[r]);
+        }
+#pragma unroll
+        for (int r = 0; r < U2; ++r) {
+          if (u0 + r * stride >= units) break;
+          C va = make_float2(a[r].x, a[r].y), vb = make_float2(a[r].z, a[r].w);
+          pair_apply<R>(CODE, M, va, vb);
+          __stcs(p4 + ia[r], make_float4(va.x, va.y, vb.x, vb.y));
+        }
+      }
+      return;
+    }
+  }
+  for (uint64_t u0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; u0 < units; u0 += stride * kStreamUnroll) {
+    uint64_t ia[kStreamUnroll];
+    g_t<R> a[kStreamUnroll], b[kStreamUnroll];
+#pragma unroll
+    for (int r = 0; r < kStreamUnroll; ++r) {
+      const uint64_t u = u0 + r * stride;
+      ia[r] = u < units ? stream_index(sd, u) : 0;
+      if (u < units) {
+        a[r] = __ldcs(psi + ia[r] + sd.oa);
+        b[r] = __ldcs(psi + ia[r] + sd.ob);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < kStreamUnroll; ++r) {
+      if (u0 + r * stride >= units) break;
+      C va = to_c<R>(a[r]), vb = to_c<R>(b[r]);
+      pair_apply<R>(CODE, M, va, vb);
+      __stcs(psi + ia[r] + sd.oa, to_g<R>(va));
+      __stcs(psi + ia[r] + sd.ob, to_g<R>(vb));
+    }
+  }
+}
+
+template <typename R, int KD, bool NEG>
+__device__ __forceinline__ c_t<R> stream_diag_mul(const StreamDev &sd, const c_t<R> (&d)[4], uint64_t i, c_t<R> v) {
+  if (NEG) {
+    v.x = -v.x;  // every unit is on the all-ones target pattern
+    v.y = -v.y;
+    return v;
+  }
+  int idx = (int)((i >> sd.tg0) & 1);
+  if (KD == 2) idx = (idx << 1) | (int)((i >> sd.tg1) & 1);
+  return cmul(v, pick<c_t<R>, KD>(d, idx));
+}
+
+template <typename R0, int KD, bool NEG>
+__global__ void __launch_bounds__(kBlock) k_stream_diag(g_t<R0> *__restrict__ psi, uint64_t units, const StreamDev sd,
+                                                        const c_t<R0> *__restrict__ mats) {
+  using R = stream_t<R0>;
+  using C = c_t<R>;
+  C d[4];
+  if (!NEG)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) d[e] = e < (1 << KD) ? stream_entry<R0>(mats[sd.mat + e]) : C();
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  if constexpr (std::is_same<R, float>::value) {
+    if (sd.vec2) {
+      float4 *p4 = reinterpret_cast<float4 *>(psi);
+      const uint64_t nv = units >> 1;
+      for (uint64_t v0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v0 < nv; v0 += stride * kStreamUnroll) {
+        uint64_t ia[kStreamUnroll];
+        float4 a[kStreamUnroll];
+#pragma unroll
+        for (int r = 0; r < kStreamUnroll; ++r) {
+          const uint64_t v = v0 + r * stride;
+          ia[r] = v < nv ? stream_index(sd, v << 1) : 0;
+          if (v < nv) a[r] = __ldcs(p4 + (ia[r] >> 1));
+        }
+#pragma unroll
+        for (int r = 0; r < kStreamUnroll; ++r) {
+          if (v0 + r * stride >= nv) break;
+          const C a0 = stream_diag_mul<R, KD, NEG>(sd, d, ia[r], make_float2(a[r].x, a[r].y));
+          const C a1 = stream_diag_mul<R, KD, NEG>(sd, d, ia[r] | 1, make_float2(a[r].z, a[r].w));
+          __stcs(p4 + (ia[r] >> 1), make_float4(a0.x, a0.y, a1.x, a1.y));
+        }
+      }
+      return;
+    }
+  }
+  for (uint64_t u0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; u0 < units; u0 += stride * kStreamUnroll) {
+    uint64_t ia[kStreamUnroll];
+    g_t<R> a[kStreamUnroll];
+#pragma unroll
+    for (int r = 0; r < kStreamUnroll; ++r) {
+      const uint64_t u = u0 + r * stride;
+      ia[r] = u < units ? stream_index(sd, u) : 0;
+      if (u < units) a[r] = __ldcs(psi + ia[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < kStreamUnroll; ++r) {
+      if (u0 + r * stride >= units) break;
+      __stcs(psi + ia[r], to_g<R>(stream_diag_mul<R, KD, NEG>(sd, d, ia[r], to_c<R>(a[r]))));
+    }
+  }
 }
 
 template <typename R>

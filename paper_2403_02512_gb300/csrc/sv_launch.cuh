@@ -74,7 +74,11 @@ cudaError_t adjoint_k(const void *phi_in, void *phi_out, void *lam, int n, int m
     case 1: return adjoint_b<R, MAXK, 1>(phi_in, phi_out, lam, n, m, pass, ops, mats, partials, grid, st);
     case 2: return adjoint_b<R, MAXK, 2>(phi_in, phi_out, lam, n, m, pass, ops, mats, partials, grid, st);
     case 4: return adjoint_b<R, MAXK, 4>(phi_in, phi_out, lam, n, m, pass, ops, mats, partials, grid, st);
-    default: return cudaErrorInvalidValue;  // lambdas per CTA: 1, 2 or 4
+    case 8:
+      if constexpr (std::is_same<R, double>::value)
+        return adjoint_b<R, MAXK, 8>(phi_in, phi_out, lam, n, m, pass, ops, mats, partials, grid, st);
+      return cudaErrorInvalidValue;
+    default: return cudaErrorInvalidValue;  // lambdas per CTA: 1, 2, 4 (8: complex128)
   }
 }
 }  // namespace detail
@@ -86,6 +90,39 @@ cudaError_t Launch<R>::tile_adjoint(const void *phi_in, void *phi_out, void *lam
   if (pass.max_k <= 2)
     return detail::adjoint_k<R, 2>(phi_in, phi_out, lam, n, m, b, pass, ops, mats, partials, grid, st);
   return detail::adjoint_k<R, 4>(phi_in, phi_out, lam, n, m, b, pass, ops, mats, partials, grid, st);
+}
+
+template <typename R>
+cudaError_t Launch<R>::stream_op(void *psi, int n, const StreamDev &sd, const void *mats, cudaStream_t st) {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  const uint64_t units = 1ull << (n - sd.nfix);
+  const uint64_t per_thread = (sd.vec2 ? 2 : 1) * kStreamUnroll;
+  const uint64_t want = (units + per_thread * kBlock - 1) / (per_thread * kBlock);
+  const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)sms * (2048 / kBlock)));
+  g_t<R> *p = reinterpret_cast<g_t<R> *>(psi);
+  const c_t<R> *m = reinterpret_cast<const c_t<R> *>(mats);
+  if (sd.kind == kPair) {
+    switch (sd.code) {
+      case mSwap: k_stream_pair<R, mSwap><<<grid, kBlock, 0, st>>>(p, units, sd, m); break;
+      case mY: k_stream_pair<R, mY><<<grid, kBlock, 0, st>>>(p, units, sd, m); break;
+      case mReal: k_stream_pair<R, mReal><<<grid, kBlock, 0, st>>>(p, units, sd, m); break;
+      case mImOff: k_stream_pair<R, mImOff><<<grid, kBlock, 0, st>>>(p, units, sd, m); break;
+      default: k_stream_pair<R, mGen><<<grid, kBlock, 0, st>>>(p, units, sd, m); break;
+    }
+  } else if (sd.code == dNeg) {
+    k_stream_diag<R, 1, true><<<grid, kBlock, 0, st>>>(p, units, sd, m);
+  } else if (sd.k == 1) {
+    k_stream_diag<R, 1, false><<<grid, kBlock, 0, st>>>(p, units, sd, m);
+  } else {
+    k_stream_diag<R, 2, false><<<grid, kBlock, 0, st>>>(p, units, sd, m);
+  }
+  return cudaGetLastError();
 }
 
 template <typename R>
@@ -201,6 +238,19 @@ int Launch<R>::max_T_forward() {
 template <typename R>
 int Launch<R>::max_T_adjoint() {
   return sizeof(c_t<R>) == 8 ? 11 : 10;
+}
+
+// FP64 arithmetic runs at a small fraction of the FP32 rate, so eight warps
+// per SM keep its pipe busy: the complex128 adjoint kernel runs one CTA per SM
+// with up to 255 registers and 8 lambdas per phi tile (less phi work per lambda).
+template <typename R>
+int Launch<R>::adj_lambdas_max() {
+  return std::is_same<R, double>::value ? 8 : 4;
+}
+
+template <typename R>
+int Launch<R>::adj_ctas_per_sm() {
+  return std::is_same<R, double>::value ? 1 : 2;
 }
 
 }  // namespace sv
