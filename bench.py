@@ -53,6 +53,35 @@ def parse():
     return ap.parse_args()
 
 
+# FP64 pipe of a GB300: 152 SMs x 2 FMA lanes/clk x 2 flops x 2.07 GHz.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+
+# Algorithmic flops per amplitude of one gate application (the unfused method,
+# each gate a pass): complex multiply 6, real 2x2 rotation 6, RX 6, general
+# 2x2 14, Hadamard 4; permutations and sign flips 0.  PhaseShift touches half
+# the amplitudes.  A trainable gate adds Im<lambda|G phi>: 4 flops per
+# amplitude per lambda (G a Pauli word: a permutation with signs).
+_GATE_FLOPS = {"RZ": 6.0, "RY": 6.0, "RX": 6.0, "PhaseShift": 3.0, "Hadamard": 4.0, "Rot": 14.0,
+               "IsingZZ": 6.0, "IsingXX": 6.0, "IsingYY": 6.0, "SingleExcitation": 3.0,
+               "DoubleExcitation": 6.0 / 8.0}
+
+
+def adjoint_flops(circ, m):
+    """Algorithmic flops of one adjoint sweep with m lambdas (Rot expanded to
+    RZ, RY, RZ as the sweep differentiates it)."""
+    amps = float(1 << circ.n)
+    total = 0.0
+    for op in circ.ops:
+        parts = ["RZ", "RY", "RZ"] if op.name == "Rot" else [op.name]
+        for name in parts:
+            f = _GATE_FLOPS.get(name, 0.0)
+            ctrl = 0.5 ** len(op.controls)
+            total += amps * ctrl * f * (1 + m)
+            if op.params:
+                total += amps * ctrl * 4.0 * m
+    return total
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -412,18 +441,32 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
 
-    # roofline of the dominant kernel (tile_adjoint): algorithmic bytes 2V(1 + m) per launch
+    # roofline of the dominant kernel (tile_adjoint).  HBM: algorithmic bytes
+    # 2V(1 + m) per launch.  Arithmetic: the sweep's algorithmic flops
+    # (adjoint_flops) over all launches.  Native complex128 is bound by the FP64
+    # pipe and reports "alu"; complex64 and double-float report HBM.
     kt = main["kt"]
     V = main["vec_bytes"]
     adj_ms, adj_n = kt["tile_adjoint"]
     bytes_per_launch = 2.0 * V * (1 + m)
-    achieved = bytes_per_launch * adj_n / (adj_ms * 1e-3) / 1e9 if adj_ms > 0 else None
+    hbm_achieved = bytes_per_launch * adj_n / (adj_ms * 1e-3) / 1e9 if adj_ms > 0 else None
+    flops_per_launch = adjoint_flops(c, m) / max(1, main["adj_passes"])  # one sweep = adj_passes launches
+    flops_achieved = flops_per_launch * adj_n / (adj_ms * 1e-3) / 1e12 if adj_ms > 0 else None
     total_kernel_ms = sum(v[0] for v in kt.values())
     shares = {k: round(v[0] / total_kernel_ms, 4) for k, v in kt.items() if v[1] > 0}
-    roofline = {"kernel": "k_tile_adjoint", "bound": "hbm", "achieved": achieved, "peak": hbm_peak,
-                "unit": "GB/s", "frac": (achieved / hbm_peak) if achieved else None, "traffic": None,
-                "peak_kind": peak_kind, "avg_launch_ms": adj_ms / max(1, adj_n),
-                "algorithmic_bytes_per_launch": bytes_per_launch, "kernel_time_shares": shares}
+    common = {"kernel": "k_tile_adjoint", "avg_launch_ms": adj_ms / max(1, adj_n), "launches": adj_n,
+              "algorithmic_bytes_per_launch": bytes_per_launch,
+              "algorithmic_flops_per_launch": flops_per_launch,
+              "hbm_achieved_gbs": hbm_achieved, "hbm_frac": (hbm_achieved / hbm_peak) if hbm_achieved else None,
+              "kernel_time_shares": shares, "traffic": None}
+    if args.dtype == "c128":
+        roofline = {"bound": "alu", "achieved": flops_achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": flops_achieved / FP64_PEAK_TFLOPS if flops_achieved else None,
+                    "peak_kind": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2070 MHz (FP64 pipe)", **common}
+    else:
+        roofline = {"bound": "hbm", "achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": (hbm_achieved / hbm_peak) if hbm_achieved else None, "peak_kind": peak_kind,
+                    "fp_tflops_algorithmic": flops_achieved, **common}
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     e2e = None

@@ -236,6 +236,43 @@ __device__ __forceinline__ void load_tile_rw(const g_t<R> *g, c_t<R> *s, const T
   }
 }
 
+// Asynchronous tile load: every thread issues all of its 16-byte copies
+// global -> shared (cp.async, L2 only) before waiting, so a whole tile is in
+// flight at once.  Complete with tile_async_wait; double-float tiles then need
+// tile_async_convert (the copies land as IEEE doubles in the same bytes).
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+template <typename R>
+__device__ __forceinline__ void load_tile_async(const g_t<R> *g, c_t<R> *s, const TileGeom &tg) {
+  static_assert(sizeof(c_t<R>) == sizeof(g_t<R>), "tile bytes land unchanged");
+  if constexpr (std::is_same<R, float>::value) {
+    const int nv = tg.A >> 1;
+    for (int v = threadIdx.x; v < nv; v += blockDim.x) cp_async16(s + 2 * v, g + tg.gidx(v << 1));
+  } else {
+    for (int l = threadIdx.x; l < tg.A; l += blockDim.x) cp_async16(s + l, g + tg.gidx(l));
+  }
+}
+
+__device__ __forceinline__ void tile_async_wait() {
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+  __syncthreads();
+}
+
+// In-place IEEE double -> double-float conversion of n amplitudes (after the wait).
+template <typename R>
+__device__ __forceinline__ void tile_async_convert(c_t<R> *s, int n) {
+  if constexpr (std::is_same<R, df>::value) {
+    for (int l = threadIdx.x; l < n; l += blockDim.x) {
+      const double2 v = *reinterpret_cast<const double2 *>(s + l);
+      s[l] = to_c<R>(v);
+    }
+    __syncthreads();
+  }
+}
+
 template <typename R>
 __device__ __forceinline__ void store_tile(g_t<R> *g, const c_t<R> *s, const TileGeom &tg) {
   if constexpr (std::is_same<R, float>::value) {
@@ -638,8 +675,9 @@ __global__ void __launch_bounds__(kBlock) k_tile_forward(g_t<R> *__restrict__ ps
   const uint64_t ntiles = 1ull << (n - pass.T);
   for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     tg.base = tile_base(pass, tile);
-    load_tile_rw<R>(psi, s, tg);
-    __syncthreads();
+    load_tile_async<R>(psi, s, tg);
+    tile_async_wait();
+    tile_async_convert<R>(s, tg.A);
     for (int o = pass.op_begin; o < pass.op_end; ++o) {
       const OpDev &op = ops[o];
       if (op.sync_prev && o > pass.op_begin) __syncthreads();
@@ -953,9 +991,10 @@ __global__ void __launch_bounds__(kBlock, std::is_same<R, double>::value ? 1 : 2
   const uint64_t ntiles = 1ull << (n - pass.T);
   for (uint64_t tile = blockIdx.y; tile < ntiles; tile += gridDim.y) {
     tg.base = tile_base(pass, tile);
-    load_tile_rw<R>(phi_in, sp, tg);  // phi_in may equal phi_out (one lambda group, in place)
-    for (int jj = 0; jj < bb; ++jj) load_tile_rw<R>(lam_base + ((size_t)(j0 + jj) << n), sl + (size_t)jj * A, tg);
-    __syncthreads();
+    load_tile_async<R>(phi_in, sp, tg);  // phi_in may equal phi_out (one lambda group, in place)
+    for (int jj = 0; jj < bb; ++jj) load_tile_async<R>(lam_base + ((size_t)(j0 + jj) << n), sl + (size_t)jj * A, tg);
+    tile_async_wait();
+    tile_async_convert<R>(sp, A * (1 + bb));  // sp and the lambda tiles are contiguous
     for (int o = pass.op_end - 1; o >= pass.op_begin; --o) {
       const OpDev &op = ops[o];
       if (op.kind == kDense) {
