@@ -179,6 +179,16 @@ sv_status sv_set_workspace(sv_state *s, void *device_ptr, size_t bytes);
 typedef enum { SV_COMPUTE_NATIVE = 0, SV_COMPUTE_DOUBLE_FLOAT = 1 } sv_compute;
 sv_status sv_set_compute(sv_state *s, int compute);
 
+/* Renormalisation after a circuit's forward pass (the complex64 precision
+ * reading of the method: only norms, expectation values and adjoint inner
+ * products are reduced in FP64).  When on, sv_forward and sv_program_forward
+ * end with psi <- psi / ||psi||, ||psi||^2 summed in FP64 in a fixed order, all
+ * on the device (no host synchronisation).  Single-gate calls (sv_apply,
+ * sv_apply_op, sv_apply_matrix) never renormalise.  Default: on for complex64
+ * states, off for complex128 states (their drift from 1 is what sv_norm2
+ * reports).  on: 0 or 1; SV_ERR_ARG for a NULL state or another value. */
+sv_status sv_set_renormalize(sv_state *s, int on);
+
 /* Query: n, dtype and the device pointer of the amplitudes (any may be NULL). */
 sv_status sv_info(const sv_state *s, int *n, sv_dtype *dtype, void **device_ptr);
 

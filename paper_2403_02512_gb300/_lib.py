@@ -92,6 +92,7 @@ PROTOTYPES = {
     "sv_set_workspace": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t]),
     "sv_info": (ctypes.c_int, [_vp, _ip, _ip, ctypes.POINTER(_vp)]),
     "sv_set_compute": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "sv_set_renormalize": (ctypes.c_int, [_vp, ctypes.c_int]),
     "sv_reset": (ctypes.c_int, [_vp, ctypes.c_uint64]),
     "sv_set_state": (ctypes.c_int, [_vp, _vp]),
     "sv_get_state": (ctypes.c_int, [_vp, _vp]),
@@ -213,6 +214,10 @@ def sv_set_workspace(h: int, device_ptr: int, nbytes: int) -> None:
 
 def sv_set_compute(h: int, compute: int) -> None:
     _check(load().sv_set_compute(_vp(h), int(compute)))
+
+
+def sv_set_renormalize(h: int, on: bool) -> None:
+    _check(load().sv_set_renormalize(_vp(h), 1 if on else 0))
 
 
 def sv_info(h: int):

@@ -944,6 +944,8 @@ struct sv_state {
   size_t tab_bytes = 0;
   int latched = 0;
   int compute = SV_COMPUTE_NATIVE;
+  int renorm = 0;            // renormalise after circuit forward passes
+  double *d_norm = nullptr;  // kNormBlocks FP64 partials
 };
 
 namespace {
@@ -1389,6 +1391,16 @@ bool make_stream(int n, const PassDev &pd, const OpDev &o, bool c64, StreamDev &
   sd.vec2 = c64 && !(fixed & 1) && n - sd.nfix >= 1;
   sd.pair16 = c64 && o.kind == kPair && sd.oa == 0 && sd.ob == 1;
   return true;
+}
+
+// End of a circuit's forward pass: psi <- psi / ||psi|| when the state asks for it.
+sv_status finish_forward(sv_state *s) {
+  if (!s->renorm) return SV_OK;
+  if (!s->d_norm)
+    if (sv_status st = dev_alloc((void **)&s->d_norm, kNormBlocks * sizeof(double))) return st;
+  const cudaError_t e = s->dt == SV_C64 ? Launch<float>::renormalize(s->psi, s->n, s->d_norm, s->stream)
+                                        : Launch<double>::renormalize(s->psi, s->n, s->d_norm, s->stream);
+  return after_launch(s, e, "renormalize");
 }
 
 sv_status run_steps_forward(sv_program *p, void *psi) {
@@ -1934,6 +1946,7 @@ sv_status sv_create(int n, sv_dtype dtype, sv_state **out) {
     return st;
   }
   s->owns = true;
+  s->renorm = dtype == SV_C64;
   cudaError_t e = ops_for(dtype).set_basis(s->psi, n, 0, s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) {
@@ -1958,6 +1971,7 @@ sv_status sv_create_from_device_ptr(int n, sv_dtype dtype, void *device_ptr, sv_
   s->bytes = (size_t)ops_for(dtype).amp_bytes << n;
   s->psi = device_ptr;
   s->owns = false;
+  s->renorm = dtype == SV_C64;
   *out = s;
   return SV_OK;
 }
@@ -1968,6 +1982,7 @@ sv_status sv_destroy(sv_state *s) {
   if (s->owns) dev_free(s->psi, s->bytes);
   dev_free(s->ws, s->ws_bytes);
   dev_free(s->tab, s->tab_bytes);
+  dev_free(s->d_norm, s->d_norm ? kNormBlocks * sizeof(double) : 0);
   delete s;
   return SV_OK;
 }
@@ -1993,6 +2008,13 @@ sv_status sv_set_compute(sv_state *s, int compute) {
   if (compute == SV_COMPUTE_DOUBLE_FLOAT && s->dt != SV_C128)
     return fail(SV_ERR_ARG, "double-float arithmetic applies to complex128 states only");
   s->compute = compute;
+  return SV_OK;
+}
+
+sv_status sv_set_renormalize(sv_state *s, int on) {
+  if (!s) return fail(SV_ERR_ARG, "state is NULL");
+  if (on != 0 && on != 1) return fail(SV_ERR_ARG, "renormalize flag must be 0 or 1, got %d", on);
+  s->renorm = on;
   return SV_OK;
 }
 
@@ -2111,6 +2133,7 @@ sv_status sv_forward(sv_state *s, const sv_tape *tape, const double *params) {
   if (sv_status st = build_program(s, tape, nullptr, 0, params, true, &p)) return st;
   sv_status st = program_set_params(p, params, 0);
   if (!st) st = run_steps_forward(p, s->psi);
+  if (!st) st = finish_forward(s);
   if (!st) st = sync_state(s);
   destroy_program(p);
   return st;
@@ -2183,7 +2206,9 @@ sv_status sv_program_forward(sv_program *p) {
   if (sv_status st = check_state(p->s)) return st;
   if (sv_status st = require_params(p)) return st;
   p->launches = 0;
-  return run_steps_forward(p, p->s->psi);
+  if (sv_status st = run_steps_forward(p, p->s->psi)) return st;
+  if (p->s->renorm) p->launches += 2;
+  return finish_forward(p->s);
 }
 
 sv_status sv_program_jacobian(sv_program *p, double *expvals_out, double *jacobian_out, int outputs_on_device) {

@@ -18,6 +18,7 @@ constexpr int kMaxQubits = 34;
 constexpr int kBlock = 256;         // threads per CTA in the tile kernels
 constexpr int kMaxLambdaPerCta = 8; // lambdas sharing one phi tile in the adjoint kernel (at most)
 constexpr int kMaxTrainPerPass = 32;
+constexpr int kNormBlocks = 304;    // partial sums of a renormalisation (fixed count: same order every call)
 
 // Micro-op kinds.  Every structured gate is a set of independent 2x2 blocks on
 // amplitude pairs (kPair: e.g. IsingXX = blocks on |00>,|11> and |01>,|10>;
@@ -179,6 +180,8 @@ struct Launch {
                              cudaStream_t st);
   static cudaError_t set_basis(void *psi, int n, uint64_t index, cudaStream_t st);
   static cudaError_t stream_op(void *psi, int n, const StreamDev &sd, const void *mats, cudaStream_t st);
+  // psi <- psi / ||psi|| (||psi||^2 in FP64 over kNormBlocks fixed partials in `scratch`).
+  static cudaError_t renormalize(void *psi, int n, double *scratch, cudaStream_t st);
   // Persistent batch launch: `grid` CTAs drain the work items of all segments.
   static cudaError_t batch(void *states, const BatchCircuit *circs, const PassDev *passes, const OpDev *ops,
                            const void *mats, const BatchSeg *segs, int n_segs, int64_t total_items,

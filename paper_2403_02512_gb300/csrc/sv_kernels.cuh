@@ -1601,6 +1601,81 @@ __global__ void __launch_bounds__(kBlock) k_stream_diag(g_t<R0> *__restrict__ ps
   }
 }
 
+// ---------------------------------------------------------------------------
+// Renormalisation: ||psi||^2 as kNormBlocks FP64 partials (each thread sums
+// |a|^2 of two amplitudes in the state's precision, then adds in FP64; fixed
+// thread-to-element map and tree order), then one scaling pass whose blocks
+// all sum the partials in the same order.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double block_sum_fixed(double v, double *red) {
+  v += __shfl_down_sync(0xffffffffu, v, 16);
+  v += __shfl_down_sync(0xffffffffu, v, 8);
+  v += __shfl_down_sync(0xffffffffu, v, 4);
+  v += __shfl_down_sync(0xffffffffu, v, 2);
+  v += __shfl_down_sync(0xffffffffu, v, 1);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+  return t;  // valid in thread 0
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kBlock) k_norm_partials(const g_t<R> *__restrict__ psi, uint64_t N,
+                                                          double *__restrict__ partials) {
+  __shared__ double red[kBlock / 32];
+  double acc = 0.0;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  if constexpr (std::is_same<R, float>::value) {
+    const float4 *p4 = reinterpret_cast<const float4 *>(psi);
+    for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < (N >> 1); v += stride) {
+      const float4 a = __ldcs(p4 + v);
+      acc += (double)fmaf(a.x, a.x, fmaf(a.y, a.y, fmaf(a.z, a.z, a.w * a.w)));
+    }
+  } else {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < N; i += stride) {
+      const g_t<R> a = __ldcs(psi + i);
+      acc = fma(a.x, a.x, fma(a.y, a.y, acc));
+    }
+  }
+  const double t = block_sum_fixed(acc, red);
+  if (threadIdx.x == 0) partials[blockIdx.x] = t;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kBlock) k_norm_scale(g_t<R> *__restrict__ psi, uint64_t N,
+                                                       const double *__restrict__ partials, int nb) {
+  __shared__ double sc;
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int b = 0; b < nb; ++b) t += partials[b];
+    sc = t > 0.0 ? 1.0 / sqrt(t) : 1.0;
+  }
+  __syncthreads();
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  if constexpr (std::is_same<R, float>::value) {
+    const float f = (float)sc;
+    float4 *p4 = reinterpret_cast<float4 *>(psi);
+    for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < (N >> 1); v += stride) {
+      float4 a = __ldcs(p4 + v);
+      a.x *= f;
+      a.y *= f;
+      a.z *= f;
+      a.w *= f;
+      __stcs(p4 + v, a);
+    }
+  } else {
+    const double f = sc;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < N; i += stride) {
+      g_t<R> a = __ldcs(psi + i);
+      a.x *= f;
+      a.y *= f;
+      __stcs(psi + i, a);
+    }
+  }
+}
+
 template <typename R>
 __global__ void k_set_basis(g_t<R> *psi, uint64_t N, uint64_t index) {
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < N; i += (uint64_t)gridDim.x * blockDim.x) {

@@ -172,6 +172,15 @@ cudaError_t Launch<R>::set_basis(void *psi, int n, uint64_t index, cudaStream_t 
 }
 
 template <typename R>
+cudaError_t Launch<R>::renormalize(void *psi, int n, double *scratch, cudaStream_t st) {
+  const uint64_t N = 1ull << n;
+  g_t<R> *p = reinterpret_cast<g_t<R> *>(psi);
+  k_norm_partials<R><<<kNormBlocks, kBlock, 0, st>>>(p, N, scratch);
+  k_norm_scale<R><<<kNormBlocks, kBlock, 0, st>>>(p, N, scratch, kNormBlocks);
+  return cudaGetLastError();
+}
+
+template <typename R>
 int Launch<R>::batch_blocks_per_sm(int max_T, int max_terms, int max_k) {
   const int smem = (int)((sizeof(c_t<R>) + 8) << max_T) + max_terms * detail::kWarps * 8;
   int nb = 0;

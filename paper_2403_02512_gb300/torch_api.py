@@ -39,9 +39,12 @@ class StateVector:
     """A 2^n-amplitude state held in a torch tensor on the GPU (wire 0 = MSB).
 
     dtype "c64" / "c128" (IEEE FP64 arithmetic) / "c128df" (complex128 storage,
-    double-float arithmetic on the FP32 pipe)."""
+    double-float arithmetic on the FP32 pipe).  renormalize: scale the state to
+    unit norm (FP64 norm) after each circuit forward pass; None = the library
+    default (on for c64, off for c128)."""
 
-    def __init__(self, n: int, dtype="c128", device="cuda", basis_state: int = 0):
+    def __init__(self, n: int, dtype="c128", device="cuda", basis_state: int = 0,
+                 renormalize: Optional[bool] = None):
         dev = _require_cuda(device)
         self.n = int(n)
         self.sv_dtype, self.torch_dtype = _DT[dtype]
@@ -52,6 +55,8 @@ class StateVector:
         self.generation = 0
         if dtype == "c128df":
             L.sv_set_compute(self.handle, L.SV_COMPUTE_DOUBLE_FLOAT)
+        if renormalize is not None:
+            L.sv_set_renormalize(self.handle, bool(renormalize))
         self.sync_stream()
         self.reset(basis_state)
 

@@ -334,3 +334,43 @@ def test_error_status_for_bad_calls():
         assert ei.value.status == 2
     finally:
         L.sv_set_alloc_cap(0)
+
+
+# ---- renormalisation after a forward pass (complex64 precision reading) ------
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_renormalize_divides_by_the_fp64_norm(dtype):
+    n = 13
+    sv = StateVector(n, dtype, renormalize=True)
+    psi = 2.0 * random_state(n, 71)  # ||psi||^2 = 4
+    sv.set_numpy(psi)
+    start = sv.to_numpy().astype(np.complex128)
+    prog = Program(sv, [Op("PauliX", (0,))], 0)
+    prog.set_params([])
+    prog.forward(reset=False)
+    want = oracle.forward(Circuit(n, [Op("PauliX", (0,))], 0, []), np.zeros(0), psi0=start)
+    want = want / np.linalg.norm(want)
+    _assert_state(sv.to_numpy(), want, dtype)
+    assert abs(sv.norm2() - 1.0) <= (1e-6 if dtype == "c64" else 1e-14)
+
+
+def test_renormalize_keeps_a_deep_complex64_circuit_on_the_unit_sphere():
+    n = 14
+    c, params = random_circuit(n, 600, 72)
+    want = oracle.forward(c, params)
+    drift = {}
+    for on in (False, True):
+        sv = StateVector(n, "c64", renormalize=on)
+        prog = Program(sv, c.ops, c.n_params)
+        prog.forward(params)
+        got = sv.to_numpy()
+        _assert_state(got, want, "c64")
+        drift[on] = abs(sv.norm2() - 1.0)
+    assert drift[True] <= 1e-6
+    assert drift[True] <= drift[False] + 1e-7
+
+
+def test_renormalize_flag_is_checked():
+    import ctypes
+    sv = StateVector(3, "c64")
+    assert L.load().sv_set_renormalize(ctypes.c_void_p(sv.handle), 2) == 1  # SV_ERR_ARG
+    assert L.load().sv_set_renormalize(None, 1) == 1
