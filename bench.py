@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the complex64 and per-gate side measurements")
     ap.add_argument("--quick-extras", action="store_true", help="only the other precisions of the same step")
+    ap.add_argument("--profile-gate", default=None, metavar="GATE:WIRE",
+                    help="profiling aid: time --steps passes of one gate (RX, Hadamard or CNOT, control "
+                         "wire+1) on a --qubits state of --dtype and print one JSON line (not the bench line)")
     return ap.parse_args()
 
 
@@ -226,7 +229,7 @@ def extra_gates(hbm_peak, wires_step=1):
     out = {}
     for dtype in ("c128", "c128df", "c64"):
         n = 30
-        sv = StateVector(n, dtype)
+        sv = StateVector(n, dtype, renormalize=False)  # time the gate pass alone
         V = (8 if dtype == "c64" else 16) << n
         res = {}
         for name in ("RX", "Hadamard", "CNOT"):
@@ -537,11 +540,35 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_profile_gate(args):
+    import torch
+    from paper_2403_02512_gb300.torch_api import Program, StateVector
+    from workloads import Op
+    name, wire = args.profile_gate.split(":")
+    t, n = int(wire), args.qubits
+    sv = StateVector(n, args.dtype, renormalize=False)  # time the gate pass alone
+    if name == "CNOT":
+        op = Op("PauliX", (t,), (), ((t + 1) % n,))
+    else:
+        op = Op(name, (t,), (0,) if name == "RX" else ())
+    prog = Program(sv, [op], 1 if name == "RX" else 0)
+    prog.set_params([0.3] if name == "RX" else [])
+    for _ in range(args.warmup):
+        prog.forward(reset=False)
+    ms = _timed(lambda: prog.forward(reset=False), args.steps, torch.cuda.current_stream())
+    V = (8 if args.dtype == "c64" else 16) << n
+    alg = V if name == "CNOT" else 2.0 * V
+    print(json.dumps({"profile_gate": args.profile_gate, "dtype": args.dtype, "n": n, "ms": ms,
+                      "gbs_algorithmic": alg / ms / 1e6}))
+
+
 def main():
     args = parse()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
-    if args.impl == "reference":
+    if args.profile_gate:
+        run_profile_gate(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
