@@ -56,6 +56,14 @@ def parse():
     return ap.parse_args()
 
 
+# DRAM bytes (read + write) per adjoint launch from one ncu capture of the
+# current kernel on sel22 (22 observables), scaled to sel24 by the state size
+# (x4) and the vector count (25 / 23).  Must be re-taken when the kernel changes.
+PROFILED_TRAFFIC = {
+    "c128": (3.037110e9 * 4 * 25 / 23, "profiles/k_tile_adjoint_sel22_c128.md, scaled x4 x25/23"),
+    "c64": (1.487835e9 * 4 * 25 / 23, "profiles/k_tile_adjoint_sel22_c64.md, scaled x4 x25/23"),
+}
+
 # FP64 pipe of a GB300: 152 SMs x 2 FMA lanes/clk x 2 flops x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 
@@ -462,6 +470,8 @@ def run_ours(args):
               "algorithmic_flops_per_launch": flops_per_launch,
               "hbm_achieved_gbs": hbm_achieved, "hbm_frac": (hbm_achieved / hbm_peak) if hbm_achieved else None,
               "kernel_time_shares": shares, "traffic": None}
+    if (NQ, args.layers) == (N_QUBITS, LAYERS) and args.dtype in PROFILED_TRAFFIC:
+        common["traffic"], common["traffic_source"] = PROFILED_TRAFFIC[args.dtype]
     if args.dtype == "c128":
         roofline = {"bound": "alu", "achieved": flops_achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                     "frac": flops_achieved / FP64_PEAK_TFLOPS if flops_achieved else None,
