@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the complex64 and per-gate side measurements")
     ap.add_argument("--quick-extras", action="store_true", help="only the other precisions of the same step")
+    ap.add_argument("--profile-batch", type=int, default=0, metavar="N",
+                    help="profiling aid: time --steps runs of one batch of N 20-qubit QAOA p=4 parameter sets "
+                         "(complex64, default launch shape, no autotuning) and print one JSON line")
     ap.add_argument("--profile-gate", default=None, metavar="GATE:WIRE",
                     help="profiling aid: time --steps passes of one gate (RX, Hadamard or CNOT, control "
                          "wire+1) on a --qubits state of --dtype and print one JSON line (not the bench line)")
@@ -572,12 +575,34 @@ def run_profile_gate(args):
                       "gbs_algorithmic": alg / ms / 1e6}))
 
 
+def run_profile_batch(args):
+    import torch
+    from paper_2403_02512_gb300 import _lib as L
+    from workloads import qaoa_maxcut, qaoa_param_sets
+    c = qaoa_maxcut(20, 4)
+    sets = qaoa_param_sets(args.profile_batch, 4)
+    b = L.Batch([c] * len(sets), L.SV_C64)
+    b.set_params(sets.ravel())
+    for _ in range(args.warmup):
+        b.run()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        b.run()
+    dt = (time.perf_counter() - t0) / args.steps
+    print(json.dumps({"profile_batch": len(sets), "ms_per_batch": dt * 1e3, "circuits_per_s": len(sets) / dt,
+                      **b.info()}))
+    b.close()
+
+
 def main():
     args = parse()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.profile_gate:
         run_profile_gate(args)
+    elif args.profile_batch:
+        run_profile_batch(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -1694,7 +1694,7 @@ __global__ void k_set_basis(g_t<R> *psi, uint64_t N, uint64_t index) {
 // item is only ever taken by a running CTA, so the oldest unfinished item
 // always has its inputs and the queue cannot deadlock.  States live in L2-sized
 // waves of circuits (the item order interleaves the circuits of a wave).
-// Loads bypass L1 (ld.global.cg): another SM may have written the amplitudes
+// Loads bypass L1 (cp.async.cg): another SM may have written the amplitudes
 // in the previous pass.  The first pass writes the basis state straight into
 // shared memory; the last pass adds the Z-word expectation partials of its
 // tile (one slot per term and tile, summed later in fixed order) and stores
@@ -1710,19 +1710,6 @@ __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
-}
-
-template <typename R>
-__device__ __forceinline__ void load_tile_cg(const g_t<R> *g, c_t<R> *s, const TileGeom &tg) {
-  if constexpr (std::is_same<R, float>::value) {
-    const int nv = tg.A >> 1;
-    for (int v = threadIdx.x; v < nv; v += blockDim.x) {
-      const int l = v << 1;
-      reinterpret_cast<float4 *>(s)[v] = __ldcg(reinterpret_cast<const float4 *>(g + tg.gidx(l)));
-    }
-  } else {
-    for (int l = threadIdx.x; l < tg.A; l += blockDim.x) s[l] = to_c<R>(__ldcg(g + tg.gidx(l)));
-  }
 }
 
 constexpr int kBatchChunk = 8;  // work items a CTA takes from the queue at once
@@ -1820,7 +1807,9 @@ __global__ void __launch_bounds__(kBlock) k_batch(g_t<R> *__restrict__ states, c
           s[l] = v;
         }
       } else {
-        load_tile_cg<R>(psi, s, tg);
+        load_tile_async<R>(psi, s, tg);  // cp.async.cg: L2 only, as the previous pass ran on other SMs
+        tile_async_wait();
+        tile_async_convert<R>(s, tg.A);
       }
       __syncthreads();
       for (int o = pass.op_begin; o < pass.op_end; ++o) {

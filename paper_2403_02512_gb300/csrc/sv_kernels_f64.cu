@@ -83,27 +83,30 @@ cudaError_t assemble_jacobian(const double *contrib, const double *coef, const i
   return cudaGetLastError();
 }
 
-// Batch: out[c.out] = sum_t coeff_t * sum_tile partials[part_begin + t * tiles + tile],
-// tiles ascending then terms ascending (fixed order).
+// Batch: out[c.out] = sum_t coeff_t * sum_tile partials[part_begin + t * tiles + tile].
+// One warp per circuit: lane l sums tiles l, l + 32, ... in ascending order,
+// a fixed shuffle tree combines the lanes, terms are added in ascending order.
 __global__ void k_batch_reduce(const BatchCircuit *__restrict__ circs, int n_circ, const ZTerm *__restrict__ terms,
                                const double *__restrict__ partials, double *__restrict__ out) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
   if (c >= n_circ) return;
   const BatchCircuit cc = circs[c];
   double e = 0.0;
   for (int t = 0; t < cc.n_terms; ++t) {
     double v = 0.0;
     const double *p = partials + cc.part_begin + (int64_t)t * cc.tiles;
-    for (int i = 0; i < cc.tiles; ++i) v += p[i];
-    e += terms[cc.term_begin + t].coeff * v;
+    for (int i = lane; i < cc.tiles; i += 32) v += p[i];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    e += terms[cc.term_begin + t].coeff * v;  // lane 0 holds the tile sum
   }
-  out[cc.out] = e;
+  if (lane == 0) out[cc.out] = e;
 }
 
 cudaError_t batch_reduce(const BatchCircuit *circs, int n_circ, const ZTerm *terms, const double *partials,
                          double *out, cudaStream_t st) {
   if (n_circ <= 0) return cudaSuccess;
-  k_batch_reduce<<<(n_circ + 127) / 128, 128, 0, st>>>(circs, n_circ, terms, partials, out);
+  k_batch_reduce<<<(n_circ + 3) / 4, 128, 0, st>>>(circs, n_circ, terms, partials, out);
   return cudaGetLastError();
 }
 

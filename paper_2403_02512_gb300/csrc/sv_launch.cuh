@@ -183,6 +183,12 @@ cudaError_t Launch<R>::renormalize(void *psi, int n, double *scratch, cudaStream
 template <typename R>
 int Launch<R>::batch_blocks_per_sm(int max_T, int max_terms, int max_k) {
   const int smem = (int)((sizeof(c_t<R>) + 8) << max_T) + max_terms * detail::kWarps * 8;
+  // the occupancy query honours the dynamic shared-memory opt-in: set it first
+  static bool attr2 = false, attr4 = false;
+  if (max_k <= 2)
+    detail::allow_big_smem(k_batch<R, 2>, attr2);
+  else
+    detail::allow_big_smem(k_batch<R, 4>, attr4);
   int nb = 0;
   cudaError_t e = max_k <= 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<R, 2>, kBlock, smem)
                              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<R, 4>, kBlock, smem);
