@@ -288,6 +288,7 @@ struct Plan {
   std::vector<OpDev> dk_ops;   // one op per dense_k step (global targets)
   std::vector<int> train_hop;  // trainable slot -> HOp index (sweep order)
   int n_train = 0;
+  std::vector<uint64_t> aux;   // phase-run member records (two words each)
 };
 
 // Matrix-slot allocator shared by the forward and adjoint plans of a program.
@@ -358,6 +359,25 @@ struct SlotTable {
       slots.push_back(m);
     }
     return hd.out;
+  }
+  // Phase run of r members sharing h's angle: entries E[0..r].
+  int add_phase(const HOp &h, int r, bool dagger) {
+    MatSlot m;
+    memset(&m, 0, sizeof(m));
+    m.kind = h.kind;
+    m.k = h.k;
+    m.dagger = dagger ? 1 : 0;
+    m.mode = 5;
+    m.b = r;
+    m.out = (int)entries;
+    for (int q = 0; q < 3; ++q) {
+      m.pidx[q] = h.pidx[q];
+      m.cangle[q] = h.cang[q];
+    }
+    m.scale = h.scale;
+    slots.push_back(m);
+    entries += (size_t)r + 1;
+    return m.out;
   }
 };
 
@@ -578,12 +598,51 @@ bool fusable(const HOp &h) {
   return single_wire_generator(h, g);
 }
 
+// Phase runs: adjacent uncontrolled RZ / IsingZZ ops with one angle source
+// (same parameter and scale, or the same constant, and the same adjoint flag)
+// multiply by exp(-i theta/2 sum_j (-1)^p_j): one diagonal pass.
+bool phase_member(const HOp &h) {
+  return h.diag && h.nc == 0 && !h.train && (h.kind == SV_RZ || h.kind == SV_ISING_ZZ);
+}
+
+bool same_angle(const HOp &a, const HOp &b) {
+  if (a.adjoint != b.adjoint || a.pidx[0] != b.pidx[0]) return false;
+  return a.pidx[0] >= 0 ? a.scale == b.scale : a.cang[0] == b.cang[0];
+}
+
+enum GroupKind { gSingle = 0, gRun = 1, gPhaseRun = 2 };
+struct Group {
+  GroupKind kind;
+  std::vector<int> m;  // member op indices, forward order
+};
+
 // Runs of single-wire gates: op i joins the open run on its wire when no gate
 // since the run's first member touched that wire (the ops in between act on
 // other wires and commute with it).  A run is kept when it has >= 2 members,
 // one of them non-diagonal, and at most kMaxFuseGen trainable members; it is
-// emitted at its first member's position.  Other ops keep their order.
-std::vector<std::vector<int>> fuse_groups(int n, const std::vector<HOp> &ops, bool fuse) {
+// emitted at its first member's position.  Phase runs (when asked) are taken
+// first, from adjacent ops.  Other ops keep their order.
+std::vector<Group> fuse_groups(int n, const std::vector<HOp> &ops, bool fuse, bool phase) {
+  std::vector<int> phase_of(ops.size(), -1);
+  std::vector<std::vector<int>> pruns;
+  if (phase) {
+    for (int i = 0; i < (int)ops.size();) {
+      if (!phase_member(ops[i])) {
+        ++i;
+        continue;
+      }
+      int j = i + 1;
+      while (j < (int)ops.size() && j - i < kMaxPhaseMembers && phase_member(ops[j]) && same_angle(ops[i], ops[j])) ++j;
+      if (j - i >= 2) {
+        pruns.emplace_back();
+        for (int q = i; q < j; ++q) {
+          phase_of[q] = (int)pruns.size() - 1;
+          pruns.back().push_back(q);
+        }
+      }
+      i = j;
+    }
+  }
   std::vector<std::vector<int>> runs;
   std::vector<int> run_of(ops.size(), -1);
   if (fuse) {
@@ -592,7 +651,7 @@ std::vector<std::vector<int>> fuse_groups(int n, const std::vector<HOp> &ops, bo
     for (int i = 0; i < (int)ops.size(); ++i) {
       const HOp &h = ops[i];
       if (h.kind == SV_IDENTITY) continue;
-      if (fusable(h)) {
+      if (phase_of[i] < 0 && fusable(h)) {
         const int w = h.tw[0];
         const int r = open[w];
         if (r >= 0 && (int)runs[r].size() < kMaxFuseMembers && gens[r] + (h.train ? 1 : 0) <= kMaxFuseGen) {
@@ -617,15 +676,60 @@ std::vector<std::vector<int>> fuse_groups(int n, const std::vector<HOp> &ops, bo
         for (int i : runs[r]) run_of[i] = -1;
     }
   }
-  std::vector<std::vector<int>> out;
+  std::vector<Group> out;
   for (int i = 0; i < (int)ops.size(); ++i) {
+    if (phase_of[i] >= 0) {
+      if (pruns[phase_of[i]][0] == i) out.push_back({gPhaseRun, pruns[phase_of[i]]});
+      continue;
+    }
     const int r = run_of[i];
     if (r < 0)
-      out.push_back({i});
+      out.push_back({gSingle, {i}});
     else if (runs[r][0] == i)
-      out.push_back(runs[r]);
+      out.push_back({gRun, runs[r]});
   }
   return out;
+}
+
+// Lower a phase run into one kPhase micro-op: member records (local-bit parity
+// mask, tile-bit parity mask) in P.aux, members with local bits first.
+void lower_phase(int n, const std::vector<HOp> &ops, const std::vector<int> &mem, const PassDev &pd, bool dagger,
+                 SlotTable &st, std::vector<OpDev> &out, std::vector<uint64_t> &aux) {
+  const HOp &h0 = ops[mem[0]];
+  OpDev o;
+  memset(&o, 0, sizeof(o));
+  o.kind = kPhase;
+  o.k = 1;
+  o.train = -1;
+  o.slot = -1;
+  o.sync_prev = 1;
+  o.mat = st.add_phase(h0, (int)mem.size(), (h0.adjoint != 0) != dagger);
+  std::vector<std::pair<uint32_t, uint64_t>> loc, far;
+  for (int i : mem) {
+    const HOp &h = ops[i];
+    uint32_t lm = 0;
+    uint64_t hm = 0;
+    for (int j = 0; j < h.k; ++j) {
+      const int b = n - 1 - h.tw[j];
+      int li = -1;
+      for (int q = 0; q < pd.T; ++q)
+        if (pd.pos[q] == b) li = q;
+      if (li >= 0)
+        lm |= 1u << li;
+      else
+        hm |= 1ull << b;
+    }
+    (lm ? loc : far).push_back({lm, hm});
+  }
+  o.oa = (int32_t)(aux.size() / 2);
+  o.ob = (int32_t)mem.size();
+  o.zmask = (int32_t)loc.size();
+  for (auto *v : {&loc, &far})
+    for (auto &rec : *v) {
+      aux.push_back(rec.first);
+      aux.push_back(rec.second);
+    }
+  out.push_back(o);
 }
 
 // Lower a fused run into one pair micro-op on its wire's local bit.
@@ -671,9 +775,9 @@ void lower_fused(int n, const std::vector<HOp> &ops, const std::vector<int> &mem
 // 16-byte aligned for the paired complex64 accesses).  Each pass is then
 // lowered into micro-ops; dagger selects the adjoint sweep's U^dagger blocks.
 Plan plan_passes(int n, const std::vector<HOp> &ops, int Tmax, int nlow_pref, int max_train, bool dagger,
-                 SlotTable &st, bool fuse = false) {
+                 SlotTable &st, bool fuse = false, bool phase = false) {
   Plan P;
-  const std::vector<std::vector<int>> groups = fuse_groups(n, ops, fuse);
+  const std::vector<Group> groups = fuse_groups(n, ops, fuse, phase);
   const int T = std::min(Tmax, n);
   const uint64_t low = low_bits(n, T, nlow_pref);
   uint64_t cur = low;
@@ -687,9 +791,11 @@ Plan plan_passes(int n, const std::vector<HOp> &ops, int Tmax, int nlow_pref, in
     int t = 0;
     bool prev_diag = false;
     for (int gi : cur_ops) {
-      const std::vector<int> &grp = groups[gi];
+      const std::vector<int> &grp = groups[gi].m;
       const size_t before = P.ops.size();
-      if (grp.size() > 1) {
+      if (groups[gi].kind == gPhaseRun) {
+        lower_phase(n, ops, grp, pd, dagger, st, P.ops, P.aux);
+      } else if (groups[gi].kind == gRun) {
         lower_fused(n, ops, grp, pd, dagger, t, P.n_train, st, P.ops);
         for (int i : grp)
           if (ops[i].train) {
@@ -710,8 +816,9 @@ Plan plan_passes(int n, const std::vector<HOp> &ops, int Tmax, int nlow_pref, in
       }
       if (P.ops.size() > before) {
         OpDev &first = P.ops[before];
-        if (first.kind == kDiag && prev_diag) first.sync_prev = 0;  // same thread-to-amplitude map
-        prev_diag = P.ops.back().kind == kDiag;
+        const bool first_diag = first.kind == kDiag || first.kind == kPhase;
+        if (first_diag && prev_diag) first.sync_prev = 0;  // same thread-to-amplitude map
+        prev_diag = P.ops.back().kind == kDiag || P.ops.back().kind == kPhase;
       }
       for (size_t q = before; q < P.ops.size(); ++q)
         if (P.ops[q].kind == kDense) pd.max_k = std::max(pd.max_k, (int)P.ops[q].k);
@@ -725,8 +832,13 @@ Plan plan_passes(int n, const std::vector<HOp> &ops, int Tmax, int nlow_pref, in
     cur_train = 0;
   };
   for (int gi = 0; gi < (int)groups.size(); ++gi) {
-    const std::vector<int> &grp = groups[gi];
-    if (grp.size() > 1) {
+    const std::vector<int> &grp = groups[gi].m;
+    if (groups[gi].kind == gPhaseRun) {  // diagonal: needs no local bits
+      if (!cur_ops.empty() && cur_train > max_train) flush();
+      cur_ops.push_back(gi);
+      continue;
+    }
+    if (groups[gi].kind == gRun) {
       const uint64_t need = 1ull << (n - 1 - ops[grp[0]].tw[0]);
       int gt = 0;
       for (int i : grp) gt += ops[i].train ? 1 : 0;
@@ -774,6 +886,12 @@ sv_status check_plan(const Plan &P, int n, int nlow_pref) {
     for (int o = pd.op_begin; o < pd.op_end; ++o) {
       const OpDev &op = P.ops[o];
       if (op.kind == kDiag) continue;
+      if (op.kind == kPhase) {
+        if (op.ob < 2 || op.ob > kMaxPhaseMembers || op.zmask < 0 || op.zmask > op.ob || op.oa < 0 ||
+            2 * (size_t)(op.oa + op.ob) > P.aux.size())
+          return fail(SV_ERR_UNSUPPORTED, "internal planner error: phase run");
+        continue;
+      }
       if (op.k > kMaxTileTargets) return fail(SV_ERR_UNSUPPORTED, "internal planner error: wide op in a tile");
       for (int j = 0; j < op.k; ++j) {
         if (op.tl[j] < 0 || op.tl[j] >= pd.T) return fail(SV_ERR_UNSUPPORTED, "internal planner error: non-local target");
@@ -1010,6 +1128,7 @@ struct sv_program {
   size_t mats_entries = 0;
   // device pointers into `tables`
   OpDev *d_fwd_ops = nullptr, *d_adj_ops = nullptr;
+  uint64_t *d_aux = nullptr;  // phase-run member records of the forward plan
   MatSlot *d_slots = nullptr;
   void *d_mats = nullptr;
   double *d_params = nullptr, *d_user = nullptr;
@@ -1120,7 +1239,7 @@ sv_status build_program(sv_state *s, const sv_tape *tape, const sv_pauli_sum *ob
     expand_op(h, aops);
   }
   SlotTable st_tab;
-  p->fwd = plan_passes(n, fops, K.Tf, K.nlow_pref, 1 << 30, false, st_tab, true);
+  p->fwd = plan_passes(n, fops, K.Tf, K.nlow_pref, 1 << 30, false, st_tab, true, true);
   p->adj = plan_passes(n, aops, K.Ta, K.nlow_pref, kMaxTrainPerPass, true, st_tab, true);
   if (sv_status st = check_plan(p->fwd, n, K.nlow_pref)) {
     destroy_program(p);
@@ -1245,7 +1364,7 @@ sv_status build_program(sv_state *s, const sv_tape *tape, const sv_pauli_sum *ob
                  sz(umat_doubles, 8) + sz(tdev.size(), sizeof(TermDev)) + sz(obs_begin.size(), 4) +
                  sz(term_order.size(), 4) + sz(ltdev.size(), sizeof(TermDev)) + sz(lbegin.size(), 4) +
                  sz(p->coef.size(), 8) + sz(pbegin.size(), 4) + sz(pslots.size(), 4) +
-                 sz(p->vjp_host.size(), sizeof(TermDev)) + sz(vbegin.size(), 4);
+                 sz(p->vjp_host.size(), sizeof(TermDev)) + sz(vbegin.size(), 4) + sz(p->fwd.aux.size(), 8);
   total = std::max<size_t>(total, 256);
   if (one_shot) {
     if (s->tab_bytes < total) {
@@ -1278,6 +1397,7 @@ sv_status build_program(sv_state *s, const sv_tape *tape, const sv_pauli_sum *ob
     return dptr;
   };
   p->d_fwd_ops = (OpDev *)put(p->fwd.ops.data(), p->fwd.ops.size(), sizeof(OpDev));
+  p->d_aux = (uint64_t *)put(p->fwd.aux.data(), p->fwd.aux.size(), 8);
   p->d_adj_ops = (OpDev *)put(p->adj.ops.data(), p->adj.ops.size(), sizeof(OpDev));
   p->d_slots = (MatSlot *)put(slots.data(), slots.size(), sizeof(MatSlot));
   p->d_mats = put(nullptr, 0, 1);
@@ -1363,7 +1483,7 @@ sv_status require_params(const sv_program *p) {
 // over the amplitudes it touches (no tile, no shared memory).
 bool make_stream(int n, const PassDev &pd, const OpDev &o, bool c64, StreamDev &sd) {
   memset(&sd, 0, sizeof(sd));
-  if (o.kind == kDense || (o.kind == kDiag && o.k > 2)) return false;
+  if (o.kind == kDense || o.kind == kPhase || (o.kind == kDiag && o.k > 2)) return false;
   uint64_t fixed = o.cmask, val = o.cval;
   if (o.kind == kPair) {
     for (int j = 0; j < o.k; ++j) fixed |= 1ull << o.tg[j];
@@ -1420,7 +1540,7 @@ sv_status run_steps_forward(sv_program *p, void *psi) {
           make_stream(s->n, pd, p->fwd.ops[pd.op_begin], s->dt == SV_C64, sd))
         e = K.stream_op(psi, s->n, sd, p->d_mats, s->stream);
       else
-        e = K.tile_forward(psi, s->n, pd, p->d_fwd_ops, p->d_mats, p->grid_f, s->stream);
+        e = K.tile_forward(psi, s->n, pd, p->d_fwd_ops, p->d_mats, p->d_aux, p->grid_f, s->stream);
     }
     if (sv_status r = after_launch(s, e, "forward pass")) return r;
     ++p->launches;
@@ -1672,6 +1792,7 @@ struct sv_batch {
   double *d_params = nullptr, *d_user = nullptr;
   BatchSeg *d_segs = nullptr;
   ZTerm *d_terms = nullptr;
+  uint64_t *d_aux = nullptr;  // phase-run member records
   double *d_partials = nullptr, *d_out = nullptr;
   int *d_done = nullptr, *d_err = nullptr;
   unsigned long long *d_head = nullptr;
@@ -1703,6 +1824,7 @@ sv_status batch_plan(sv_batch *b, int tcap, int64_t wave) {
   std::vector<ZTerm> terms;
   SlotTable st;
   std::vector<double> user;
+  std::vector<uint64_t> aux;
   int param_off = 0;
   uint64_t state_off = 0;
   int64_t part_off = 0;
@@ -1722,8 +1844,12 @@ sv_status batch_plan(sv_batch *b, int tcap, int64_t wave) {
       hops.push_back(h);
     }
     const int T = std::min(std::min(tcap, K.Tf), n);
-    Plan P = plan_passes(n, hops, T, K.nlow_pref, 1 << 30, false, st);
+    Plan P = plan_passes(n, hops, T, K.nlow_pref, 1 << 30, false, st, true, true);
     if (sv_status e = check_plan(P, n, K.nlow_pref)) return e;
+    const int aux_base = (int)(aux.size() / 2);
+    for (OpDev &o : P.ops)
+      if (o.kind == kPhase) o.oa += aux_base;
+    aux.insert(aux.end(), P.aux.begin(), P.aux.end());
     BatchCircuit &c = circs[i];
     memset(&c, 0, sizeof(c));
     c.n = n;
@@ -1808,7 +1934,8 @@ sv_status batch_plan(sv_batch *b, int tcap, int64_t wave) {
   size_t total = sz(circs.size(), sizeof(BatchCircuit)) + sz(passes.size(), sizeof(PassDev)) +
                  sz(dops.size(), sizeof(OpDev)) + sz(st.slots.size(), sizeof(MatSlot)) + sz(st.entries, K.amp_bytes) +
                  sz(std::max(b->total_params, 1), 8) + sz(std::max<size_t>(user.size(), 1), 8) +
-                 sz(segs.size(), sizeof(BatchSeg)) + sz(std::max<size_t>(terms.size(), 1), sizeof(ZTerm));
+                 sz(segs.size(), sizeof(BatchSeg)) + sz(std::max<size_t>(terms.size(), 1), sizeof(ZTerm)) +
+                 sz(aux.size(), 8);
   if (sv_status e = dev_alloc(&b->tables, total)) return e;
   b->tables_bytes = total;
   std::vector<char> host(total, 0);
@@ -1828,6 +1955,7 @@ sv_status batch_plan(sv_batch *b, int tcap, int64_t wave) {
   b->d_user = (double *)put(user.data(), std::max<size_t>(user.size(), 1), 8);
   b->d_segs = (BatchSeg *)put(segs.data(), segs.size(), sizeof(BatchSeg));
   b->d_terms = (ZTerm *)put(terms.data(), std::max<size_t>(terms.size(), 1), sizeof(ZTerm));
+  b->d_aux = (uint64_t *)put(aux.data(), aux.size(), 8);
   // the parameters survive re-planning: keep the previous values on the host side
   cudaError_t e = cudaMemcpyAsync(b->tables, host.data(), total, cudaMemcpyHostToDevice, b->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
@@ -1864,10 +1992,10 @@ sv_status batch_enqueue(sv_batch *b) {
   if (e == cudaSuccess) e = K.build_matrices(b->d_slots, b->n_slots, b->d_params, b->d_user, b->d_mats, s);
   if (e == cudaSuccess)
     e = b->dt == SV_C64
-            ? Launch<float>::batch(b->states, b->d_circs, b->d_passes, b->d_ops, b->d_mats, b->d_segs, b->n_segs,
+            ? Launch<float>::batch(b->states, b->d_circs, b->d_passes, b->d_ops, b->d_mats, b->d_aux, b->d_segs, b->n_segs,
                                    b->total_items, b->d_terms, b->d_partials, b->d_done, b->d_head, b->d_err, 0,
                                    b->timeout_ns, b->max_T, b->max_terms, b->max_k, b->no_publish, b->grid, s)
-            : Launch<double>::batch(b->states, b->d_circs, b->d_passes, b->d_ops, b->d_mats, b->d_segs, b->n_segs,
+            : Launch<double>::batch(b->states, b->d_circs, b->d_passes, b->d_ops, b->d_mats, b->d_aux, b->d_segs, b->n_segs,
                                     b->total_items, b->d_terms, b->d_partials, b->d_done, b->d_head, b->d_err, 0,
                                     b->timeout_ns, b->max_T, b->max_terms, b->max_k, b->no_publish, b->grid, s);
   if (e == cudaSuccess) e = batch_reduce(b->d_circs, b->n_circ, b->d_terms, b->d_partials, b->d_out, s);
@@ -2518,7 +2646,7 @@ sv_status sv_plan_query(int n, sv_dtype dtype, const sv_tape *tape, int *n_forwa
     expand_op(h, aops);
   }
   SlotTable st_tab;
-  Plan f = plan_passes(n, fops, K.Tf, K.nlow_pref, 1 << 30, false, st_tab, true);
+  Plan f = plan_passes(n, fops, K.Tf, K.nlow_pref, 1 << 30, false, st_tab, true, true);
   Plan a = plan_passes(n, aops, K.Ta, K.nlow_pref, kMaxTrainPerPass, true, st_tab, true);
   if (sv_status st = check_plan(f, n, K.nlow_pref)) return st;
   if (sv_status st = check_plan(a, n, K.nlow_pref)) return st;

@@ -24,7 +24,15 @@ constexpr int kNormBlocks = 304;    // partial sums of a renormalisation (fixed 
 // amplitude pairs (kPair: e.g. IsingXX = blocks on |00>,|11> and |01>,|10>;
 // DoubleExcitation = one block on |0011>,|1100>), or a diagonal (kDiag), or,
 // for a user matrix on 2-4 wires, a dense block (kDense).
-enum OpKind : int8_t { kPair = 0, kDiag = 1, kDense = 2 };
+enum OpKind : int8_t { kPair = 0, kDiag = 1, kDense = 2, kPhase = 3 };
+// kPhase: a run of r adjacent Z-parity rotations sharing one angle (RZ,
+// IsingZZ; e.g. a QAOA cost layer) as one diagonal.  Member j multiplies by
+// exp(-i theta/2 (-1)^p_j) with p_j the parity of the index bits it acts on,
+// so the run multiplies by E[k] = exp(-i theta/2 (r - 2k)), k = sum_j p_j.
+// Fields: mat = E[0..r]; oa = first member record in the plan's aux table
+// (two words each: parity mask over local bits, parity mask over tile bits;
+// members with local bits come first); ob = r; zmask = members with local bits.
+constexpr int kMaxPhaseMembers = 64;
 // 2x2 block structure (of the stored, already adjoint-resolved block).
 enum MatCode : int8_t {
   mGen = 0,    // general complex
@@ -101,7 +109,8 @@ struct TermDev {
 // slots [a, a + b) (mode 4, forward order, `dagger` = the member's own adjoint
 // flag) and writes the run's product (adjoint when `dagger`) plus, for each
 // trainable member (a = generator code gX / gY / gDiag with g0, g1 = gs or
-// ga, gb), the conjugated generator at the member's `out`.
+// ga, gb), the conjugated generator at the member's `out`.  A phase run
+// (mode 5, b = r members sharing this slot's angle) writes E[0..r].
 struct MatSlot {
   int32_t kind;        // sv_op_kind
   int32_t k;
@@ -166,7 +175,7 @@ struct Launch {
   static cudaError_t build_matrices(const MatSlot *slots, int n_slots, const double *params,
                                     const double *user_mats, void *mats, cudaStream_t st);
   static cudaError_t tile_forward(void *psi, int n, const PassDev &pass, const OpDev *ops,
-                                  const void *mats, int grid, cudaStream_t st);
+                                  const void *mats, const uint64_t *aux, int grid, cudaStream_t st);
   // m lambdas, b of them per CTA (grid.x = ceil(m / b) lambda groups).
   static cudaError_t tile_adjoint(const void *phi_in, void *phi_out, void *lam, int n, int m, int b,
                                   const PassDev &pass, const OpDev *ops, const void *mats,
@@ -184,7 +193,7 @@ struct Launch {
   static cudaError_t renormalize(void *psi, int n, double *scratch, cudaStream_t st);
   // Persistent batch launch: `grid` CTAs drain the work items of all segments.
   static cudaError_t batch(void *states, const BatchCircuit *circs, const PassDev *passes, const OpDev *ops,
-                           const void *mats, const BatchSeg *segs, int n_segs, int64_t total_items,
+                           const void *mats, const uint64_t *aux, const BatchSeg *segs, int n_segs, int64_t total_items,
                            const ZTerm *terms, double *partials, int *done, unsigned long long *head, int *err,
                            int store_final, unsigned long long timeout_ns, int max_T, int max_terms, int max_k,
                            int no_publish, int grid, cudaStream_t st);

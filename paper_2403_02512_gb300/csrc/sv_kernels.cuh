@@ -639,13 +639,40 @@ __device__ __forceinline__ void dense_any(c_t<R> *s, const TileGeom &tg, const O
   }
 }
 
+// Phase run: k(l) = parities of the members over the tile's fixed bits (once
+// per tile) plus their parities over the local bits of l; then one table entry.
+template <typename R>
+__device__ void fwd_phase(c_t<R> *s, const TileGeom &tg, const OpDev &op, const c_t<R> *__restrict__ mats,
+                          const uint64_t *__restrict__ aux) {
+  const uint64_t *m = aux + 2 * op.oa;
+  const int r = op.ob, rl = op.zmask;
+  uint64_t flip = 0;  // member j's parity over the tile bits (j < rl)
+  int k0 = 0;         // members without local bits: constant for the tile
+  for (int j = 0; j < r; ++j) {
+    const int f = __popcll(tg.base & __ldg(m + 2 * j + 1)) & 1;
+    if (j < rl)
+      flip |= (uint64_t)f << j;
+    else
+      k0 += f;
+  }
+  for (int l = threadIdx.x; l < tg.A; l += blockDim.x) {
+    int k = k0;
+    for (int j = 0; j < rl; ++j)
+      k += (__popc((uint32_t)l & (uint32_t)__ldg(m + 2 * j)) + (int)(flip >> j)) & 1;
+    s[l] = cmul(s[l], mats[op.mat + k]);
+  }
+}
+
 template <typename R, int MAXK>
-__device__ __forceinline__ void apply_op(c_t<R> *s, const TileGeom &tg, const OpDev &op, const c_t<R> *mats) {
+__device__ __forceinline__ void apply_op(c_t<R> *s, const TileGeom &tg, const OpDev &op, const c_t<R> *mats,
+                                         const uint64_t *aux) {
   if (op.kind != kDense && !op_active(op, tg.base)) return;
   if (op.kind == kPair)
     fwd_pair<R>(s, tg, op, mats);
   else if (op.kind == kDiag)
     fwd_diag<R>(s, tg, op, mats);
+  else if (op.kind == kPhase)
+    fwd_phase<R>(s, tg, op, mats, aux);
   else
     dense_any<R, MAXK>(s, tg, op, mats);
 }
@@ -659,7 +686,8 @@ __device__ __forceinline__ void apply_op(c_t<R> *s, const TileGeom &tg, const Op
 template <typename R, int MAXK>
 __global__ void __launch_bounds__(kBlock) k_tile_forward(g_t<R> *__restrict__ psi, int n, const PassDev pass,
                                                           const OpDev *__restrict__ ops,
-                                                          const c_t<R> *__restrict__ mats) {
+                                                          const c_t<R> *__restrict__ mats,
+                                                          const uint64_t *__restrict__ aux) {
   using C = c_t<R>;
   extern __shared__ __align__(16) unsigned char smem[];
   C *s = reinterpret_cast<C *>(smem);
@@ -681,7 +709,7 @@ __global__ void __launch_bounds__(kBlock) k_tile_forward(g_t<R> *__restrict__ ps
     for (int o = pass.op_begin; o < pass.op_end; ++o) {
       const OpDev &op = ops[o];
       if (op.sync_prev && o > pass.op_begin) __syncthreads();
-      apply_op<R, MAXK>(s, tg, op, mats);
+      apply_op<R, MAXK>(s, tg, op, mats, aux);
     }
     __syncthreads();
     store_tile<R>(psi, s, tg);
@@ -1398,6 +1426,18 @@ __global__ void k_build_matrices(const MatSlot *__restrict__ slots, int n_slots,
     build_run<R>(slots, sl, params, user, out);
     return;
   }
+  if (sl.mode == 5) {  // phase run: E[k] = exp(-i theta/2 (r - 2k)), conjugated when dagger
+    const double th = sl.pidx[0] >= 0 ? sl.scale * params[sl.pidx[0]] : sl.cangle[0];
+    for (int k = 0; k <= sl.b; ++k) {
+      double sn, cs;
+      sincos(-0.5 * th * (double)(sl.b - 2 * k), &sn, &cs);
+      c_t<R> v;
+      v.x = (R)cs;
+      v.y = (R)(sl.dagger ? -sn : sn);
+      out[sl.out + k] = v;
+    }
+    return;
+  }
   const int D = 1 << sl.k;
   c_t<R> *o = out + sl.out;
   if (sl.kind == SV_MATRIX) {
@@ -1717,7 +1757,8 @@ constexpr int kBatchChunk = 8;  // work items a CTA takes from the queue at once
 template <typename R, int MAXK>
 __global__ void __launch_bounds__(kBlock) k_batch(g_t<R> *__restrict__ states, const BatchCircuit *__restrict__ circs,
                                                    const PassDev *__restrict__ passes, const OpDev *__restrict__ ops,
-                                                   const c_t<R> *__restrict__ mats, const BatchSeg *__restrict__ segs,
+                                                   const c_t<R> *__restrict__ mats, const uint64_t *__restrict__ aux,
+                                                   const BatchSeg *__restrict__ segs,
                                                    int n_segs, long long total_items, const ZTerm *__restrict__ terms,
                                                    double *__restrict__ partials, int *done,
                                                    unsigned long long *head, int *err, int store_final,
@@ -1815,7 +1856,7 @@ __global__ void __launch_bounds__(kBlock) k_batch(g_t<R> *__restrict__ states, c
       for (int o = pass.op_begin; o < pass.op_end; ++o) {
         const OpDev &op = ops[o];
         if (op.sync_prev && o > pass.op_begin) __syncthreads();
-        apply_op<R, MAXK>(s, tg, op, mats);
+        apply_op<R, MAXK>(s, tg, op, mats, aux);
       }
       __syncthreads();
       const bool last = sg.pass == cc.n_pass - 1;

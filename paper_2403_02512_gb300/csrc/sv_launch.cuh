@@ -38,17 +38,17 @@ cudaError_t Launch<R>::build_matrices(const MatSlot *slots, int n_slots, const d
 
 template <typename R>
 cudaError_t Launch<R>::tile_forward(void *psi, int n, const PassDev &pass, const OpDev *ops,
-                                    const void *mats, int grid, cudaStream_t st) {
+                                    const void *mats, const uint64_t *aux, int grid, cudaStream_t st) {
   static bool attr2 = false, attr4 = false;
   const int smem = detail::tile_bytes(sizeof(c_t<R>), pass.T) + detail::lut_bytes(pass);
   if (pass.max_k <= 2) {
     detail::allow_big_smem(k_tile_forward<R, 2>, attr2);
     k_tile_forward<R, 2><<<grid, kBlock, smem, st>>>(reinterpret_cast<g_t<R> *>(psi), n, pass, ops,
-                                                      reinterpret_cast<const c_t<R> *>(mats));
+                                                      reinterpret_cast<const c_t<R> *>(mats), aux);
   } else {
     detail::allow_big_smem(k_tile_forward<R, 4>, attr4);
     k_tile_forward<R, 4><<<grid, kBlock, smem, st>>>(reinterpret_cast<g_t<R> *>(psi), n, pass, ops,
-                                                      reinterpret_cast<const c_t<R> *>(mats));
+                                                      reinterpret_cast<const c_t<R> *>(mats), aux);
   }
   return cudaGetLastError();
 }
@@ -201,7 +201,7 @@ int Launch<R>::batch_blocks_per_sm(int max_T, int max_terms, int max_k) {
 
 template <typename R>
 cudaError_t Launch<R>::batch(void *states, const BatchCircuit *circs, const PassDev *passes, const OpDev *ops,
-                             const void *mats, const BatchSeg *segs, int n_segs, int64_t total_items,
+                             const void *mats, const uint64_t *aux, const BatchSeg *segs, int n_segs, int64_t total_items,
                              const ZTerm *terms, double *partials, int *done, unsigned long long *head, int *err,
                              int store_final, unsigned long long timeout_ns, int max_T, int max_terms, int max_k,
                              int no_publish, int grid, cudaStream_t st) {
@@ -210,13 +210,13 @@ cudaError_t Launch<R>::batch(void *states, const BatchCircuit *circs, const Pass
   if (max_k <= 2) {
     detail::allow_big_smem(k_batch<R, 2>, attr2);
     k_batch<R, 2><<<grid, kBlock, smem, st>>>(reinterpret_cast<g_t<R> *>(states), circs, passes, ops,
-                                               reinterpret_cast<const c_t<R> *>(mats), segs, n_segs,
+                                               reinterpret_cast<const c_t<R> *>(mats), aux, segs, n_segs,
                                                (long long)total_items, terms, partials, done, head, err, store_final,
                                                timeout_ns, max_T, max_terms, no_publish);
   } else {
     detail::allow_big_smem(k_batch<R, 4>, attr4);
     k_batch<R, 4><<<grid, kBlock, smem, st>>>(reinterpret_cast<g_t<R> *>(states), circs, passes, ops,
-                                               reinterpret_cast<const c_t<R> *>(mats), segs, n_segs,
+                                               reinterpret_cast<const c_t<R> *>(mats), aux, segs, n_segs,
                                                (long long)total_items, terms, partials, done, head, err, store_final,
                                                timeout_ns, max_T, max_terms, no_publish);
   }

@@ -374,3 +374,52 @@ def test_renormalize_flag_is_checked():
     sv = StateVector(3, "c64")
     assert L.load().sv_set_renormalize(ctypes.c_void_p(sv.handle), 2) == 1  # SV_ERR_ARG
     assert L.load().sv_set_renormalize(None, 1) == 1
+
+
+# ---- phase runs: adjacent RZ / IsingZZ with one angle as one diagonal --------
+def _phase_run_circuit(n, seed):
+    rng = np.random.default_rng(seed)
+    ops = [Op("Hadamard", (w,)) for w in range(n)]
+    # 40 IsingZZ on random wire pairs sharing parameter 0 (local and tile bits mixed)
+    for _ in range(40):
+        a, b = rng.choice(n, 2, replace=False)
+        ops.append(Op("IsingZZ", (int(a), int(b)), (0,), scale=2.0))
+    ops += [Op("RX", (w,), (1,)) for w in range(n)]
+    # RZ run on a constant-free shared parameter, with the adjoint flag
+    ops += [Op("RZ", (w,), (2,), adjoint=True) for w in range(0, n, 2)]
+    # a run broken by a parameter change, then a 64-member run
+    ops += [Op("RZ", (1,), (3,)), Op("RZ", (2,), (4,))]
+    for _ in range(70):
+        a, b = rng.choice(n, 2, replace=False)
+        ops.append(Op("IsingZZ", (int(a), int(b)), (3,)))
+    ops += [Op("RY", (w,), (4,)) for w in range(n)]
+    return Circuit(n, ops, 5, [[Term(1.0, ((0, "Z"), (n - 1, "Z")))]]), rng.uniform(0, 2 * np.pi, 5)
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("n", [5, 16])
+def test_phase_runs_forward_and_jacobian(dtype, n):
+    c, p = _phase_run_circuit(n, 80 + n)
+    sv = StateVector(n, dtype)
+    prog = Program.from_circuit(sv, c)
+    prog.forward(p)
+    want = oracle.forward(c, p)
+    _assert_state(sv.to_numpy(), want, dtype)
+    E, J = prog.jacobian()
+    _assert_rel(E.cpu().numpy(), oracle.expvals(want, c.observables), TOL_E[dtype], "expval")
+    _assert_rel(J.cpu().numpy(), oracle.adjoint_jacobian(c, p)[1], TOL_J[dtype], "jacobian")
+
+
+def test_phase_runs_in_a_batch():
+    circs, params = [], []
+    for i, n in enumerate((5, 12, 16)):
+        c, p = _phase_run_circuit(n, 90 + i)
+        circs.append(c)
+        params.append(p)
+    b = L.Batch(circs, L.SV_C64)
+    b.set_params(np.concatenate(params))
+    got = b.run()
+    b.close()
+    for c, p, g in zip(circs, params, got):
+        want = oracle.expvals(oracle.forward(c, p), c.observables)[0]
+        assert abs(g - want) <= 1e-4, (c.n, g, want)
