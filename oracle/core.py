@@ -327,6 +327,15 @@ def expval(psi: np.ndarray, terms) -> float:
     return e
 
 
+def variance(psi: np.ndarray, terms) -> float:
+    """Var(H) = <psi|H^2|psi> - <psi|H|psi>^2, the variance measurement of the
+    GPU device (Sec. 2.2), with H^2 psi formed as H applied twice."""
+    h = apply_hamiltonian(psi, terms)
+    h2 = apply_hamiltonian(h, terms)
+    e = inner(psi, h).real
+    return inner(psi, h2).real - e * e
+
+
 def expvals(psi: np.ndarray, observables) -> np.ndarray:
     return np.array([expval(psi, H) for H in observables])
 

@@ -384,3 +384,38 @@ def test_qaoa_p1_closed_form_on_regular_graphs(n):
             f = len(adj[u] & adj[v])
             want = _qaoa_p1_zz(gm, bt, len(adj[u]) - 1, len(adj[v]) - 1, f)
             assert abs(e - want) < 1e-13
+
+
+# ---- variance: closed forms, eigenstates, dense reference -------------------
+def test_variance_after_rx_closed_form():
+    # RX(t)|0> = cos(t/2)|0> - i sin(t/2)|1>: <Z> = cos t, <Y> = -sin t, <X> = 0,
+    # and every Pauli word squares to I, so Var(P) = 1 - <P>^2.
+    for t in (0.0, 0.37, 1.9, 3.0):
+        psi = oracle.forward(Circuit(1, [Op("RX", (0,), (0,))], 1, []), np.array([t]))
+        assert abs(oracle.variance(psi, [Term(1.0, ((0, "Z"),))]) - math.sin(t) ** 2) < 1e-14
+        assert abs(oracle.variance(psi, [Term(1.0, ((0, "Y"),))]) - math.cos(t) ** 2) < 1e-14
+        assert abs(oracle.variance(psi, [Term(1.0, ((0, "X"),))]) - 1.0) < 1e-14
+        # Var(a Z + b) = a^2 Var(Z): the identity term only shifts
+        v = oracle.variance(psi, [Term(-2.5, ((0, "Z"),)), Term(0.75, ())])
+        assert abs(v - 6.25 * math.sin(t) ** 2) < 1e-13
+
+
+def test_variance_vanishes_on_eigenstates():
+    n = 4
+    ops = [Op("Hadamard", (0,))] + [Op("PauliX", (w + 1,), controls=(w,)) for w in range(n - 1)]
+    psi = oracle.forward(Circuit(n, ops, 0, []), np.zeros(0))  # GHZ: eigenstate of Z_i Z_j and X^n
+    H = [Term(0.7, ((0, "Z"), (3, "Z"))), Term(-1.3, ((0, "X"), (1, "X"), (2, "X"), (3, "X")))]
+    assert abs(oracle.variance(psi, H)) < 1e-13
+    assert abs(oracle.expval(psi, H) - (0.7 - 1.3)) < 1e-13
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_variance_matches_dense_hamiltonian(seed):
+    n = 5
+    rng = np.random.default_rng(seed)
+    psi = random_state(n, seed)
+    H = random_hamiltonian(n, 12, rng, weights=(1, 2, 3))
+    Hd = dense.hamiltonian(n, H)
+    e = np.vdot(psi, Hd @ psi).real
+    want = np.vdot(psi, Hd @ (Hd @ psi)).real - e * e
+    assert abs(oracle.variance(psi, H) - want) < 1e-12 * max(1.0, abs(want))
