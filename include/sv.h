@@ -228,6 +228,16 @@ sv_status sv_expval(sv_state *s, const sv_pauli_sum *obs, int n_obs, double *out
 /* out = <psi|psi> in FP64. */
 sv_status sv_norm2(sv_state *s, double *out);
 
+/* Variances (the GPU device's variance measurement, Sec. 2.2):
+ *   out[j] = <psi|H_j^2|psi> - <psi|H_j|psi>^2 = ||H_j psi||^2 - <H_j>^2
+ * (real coefficients make H_j Hermitian).  lambda_j = H_j psi is formed by the
+ * same passes as the adjoint method's lambda vectors; ||lambda_j||^2 is summed
+ * in FP64 over a fixed set of partial sums, so results repeat bitwise.  out is
+ * a host array of n_obs doubles.  Device workspace: min(n_obs, what fits) state
+ * vectors (the rest in chunks).  Same argument errors as sv_expval; the state
+ * is not modified. */
+sv_status sv_var(sv_state *s, const sv_pauli_sum *obs, int n_obs, double *out);
+
 /* ---- circuits (S4, S6-S8) ----------------------------------------------------- */
 
 /* psi <- U_N ... U_1 psi for the tape with the given parameters.  Ops are fused

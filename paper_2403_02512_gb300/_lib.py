@@ -102,6 +102,7 @@ PROTOTYPES = {
     "sv_apply_matrix": (ctypes.c_int, [_vp, _ip, ctypes.c_int, _dp, ctypes.c_int]),
     "sv_expval": (ctypes.c_int, [_vp, ctypes.POINTER(SvPauliSum), ctypes.c_int, _dp]),
     "sv_norm2": (ctypes.c_int, [_vp, _dp]),
+    "sv_var": (ctypes.c_int, [_vp, ctypes.POINTER(SvPauliSum), ctypes.c_int, _dp]),
     "sv_forward": (ctypes.c_int, [_vp, ctypes.POINTER(SvTape), _dp]),
     "sv_adjoint_jacobian": (ctypes.c_int, [_vp, ctypes.POINTER(SvTape), _dp, ctypes.POINTER(SvPauliSum),
                                            ctypes.c_int, _dp, _dp]),
@@ -265,6 +266,12 @@ def sv_apply_matrix(h: int, wires: Sequence[int], matrix: np.ndarray, adjoint: b
 def sv_expval(h: int, obs: "PauliSums") -> np.ndarray:
     out = np.zeros(obs.count, dtype=np.float64)
     _check(load().sv_expval(_vp(h), obs.array, obs.count, _dptr(out)))
+    return out
+
+
+def sv_var(h: int, obs: "PauliSums") -> np.ndarray:
+    out = np.zeros(obs.count, dtype=np.float64)
+    _check(load().sv_var(_vp(h), obs.array, obs.count, _dptr(out)))
     return out
 
 

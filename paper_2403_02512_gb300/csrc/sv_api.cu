@@ -1151,6 +1151,7 @@ struct sv_program {
   uint64_t tiles_a = 1, tiles_l = 1; // tiles per vector in those passes
   int lam_per_cta = 1;               // lambdas sharing one phi tile in the adjoint kernel
   int cfg_compute = -1;              // compute mode the adjoint launch shape was made for
+  bool want_lam = false;             // workspace holds lambda vectors without a sweep (variance)
   int groups_a(int mcc) const { return (mcc + lam_per_cta - 1) / lam_per_cta; }
   int grid_a(int mcc) const {
     return (int)std::max<uint64_t>(1, std::min<uint64_t>(tiles_a, ctas_a / std::max(1, groups_a(mcc))));
@@ -1566,9 +1567,11 @@ sv_status jac_workspace(sv_program *p, JacWs &w) {
   size_t lam_rows = 1;
   for (int mcc : {p->mc, p->m % std::max(1, p->mc), 1})
     if (mcc > 0) lam_rows = std::max(lam_rows, (size_t)p->grid_a(mcc) * mcc);
-  const size_t part = std::max(lam_rows * max_train, (size_t)p->grid_e * max_terms);
-  const bool need_vec = p->adj.n_train > 0 || !p->adj.dk_ops.empty();
-  const size_t bytes = (need_vec ? 2 * V + (size_t)p->mc * V : 0) + align256(part * 8) +
+  size_t part = std::max(lam_rows * max_train, (size_t)p->grid_e * max_terms);
+  if (p->want_lam) part = std::max(part, (size_t)p->mc * kNormBlocks);
+  const bool need_vec = p->adj.n_train > 0 || !p->adj.dk_ops.empty();  // phi buffers for a sweep
+  const bool need_lam = need_vec || p->want_lam;
+  const size_t bytes = (need_vec ? 2 * V : 0) + (need_lam ? (size_t)p->mc * V : 0) + align256(part * 8) +
                        align256((size_t)std::max(1, p->adj.n_train) * std::max(1, p->m) * 8) +
                        align256(std::max<size_t>(1, p->terms.size()) * 8) + align256((size_t)std::max(1, p->m) * 8) +
                        align256((size_t)std::max(1, p->m) * std::max(1, p->n_params) * 8);
@@ -1580,7 +1583,7 @@ sv_status jac_workspace(sv_program *p, JacWs &w) {
   w.phiB = base + c;
   c += need_vec ? V : 0;
   w.lam = base + c;
-  c += need_vec ? (size_t)p->mc * V : 0;
+  c += need_lam ? (size_t)p->mc * V : 0;
   w.partials = (double *)(base + c);
   c += align256(part * 8);
   w.contrib = (double *)(base + c);
@@ -1710,6 +1713,47 @@ sv_status run_jacobian(sv_program *p, const JacWs &w) {
     e = cudaMemsetAsync(w.J, 0, (size_t)std::max(1, p->m) * std::max(1, p->n_params) * 8, s->stream);
   }
   return after_launch(s, e, "assemble jacobian");
+}
+
+// Variances: Var_j = ||H_j psi||^2 - <H_j>^2 (H_j Hermitian), with lambda_j =
+// H_j psi from the lambda passes and ||lambda_j||^2 as fixed FP64 partials.
+// Output in w.J[0..m).
+sv_status run_var(sv_program *p, const JacWs &w) {
+  sv_state *s = p->s;
+  if (sv_status r = run_expval(p, s->psi, w)) return r;
+  const Ops &K = ops_of(s);
+  const int npass_e = (int)p->tp.passes.size();
+  for (int c = 0; c < p->n_chunks; ++c) {
+    const int j0 = c * p->mc, mcc = std::min(p->m, j0 + p->mc) - j0;
+    for (int q = 0; q < npass_e; ++q) {
+      const int32_t *begin = (const int32_t *)p->d_lam_begin + p->lam_begin_off[c * npass_e + q];
+      cudaError_t e;
+      {
+        LaunchTimer t(s->stream, 3);
+        e = K.lambda_pass(s->psi, w.lam, s->n, p->tp.passes[q], p->d_lam_terms, begin, mcc, q == 0, p->grid_l(mcc),
+                          s->stream);
+      }
+      if (sv_status r = after_launch(s, e, "lambda pass")) return r;
+      ++p->launches;
+    }
+    if (npass_e == 0) {  // observables without terms: lambda = 0
+      if (sv_status r = after_launch(s, cudaMemsetAsync(w.lam, 0, (size_t)mcc * s->bytes, s->stream), "lambda"))
+        return r;
+    }
+    for (int j = 0; j < mcc; ++j) {
+      const void *lam = w.lam + (size_t)j * s->bytes;
+      const cudaError_t e = s->dt == SV_C64
+                                ? Launch<float>::norm_partials(lam, s->n, w.partials + (size_t)j * kNormBlocks, s->stream)
+                                : Launch<double>::norm_partials(lam, s->n, w.partials + (size_t)j * kNormBlocks, s->stream);
+      if (sv_status r = after_launch(s, e, "variance norm")) return r;
+      ++p->launches;
+    }
+    if (sv_status r = after_launch(s, var_combine(w.partials, kNormBlocks, mcc, w.expvals, j0, w.J, s->stream),
+                                   "variance combine"))
+      return r;
+    ++p->launches;
+  }
+  return SV_OK;
 }
 
 // VJP: lambda = sum_j g_j H_j psi, one sweep, one contrib column.
@@ -2241,6 +2285,22 @@ sv_status sv_expval(sv_state *s, const sv_pauli_sum *obs, int n_obs, double *out
   sv_status st = jac_workspace(p, w);
   if (!st) st = run_expval(p, s->psi, w);
   if (!st) st = copy_out(s, out, w.expvals, n_obs, false);
+  if (!st) st = sync_state(s);
+  destroy_program(p);
+  return st;
+}
+
+sv_status sv_var(sv_state *s, const sv_pauli_sum *obs, int n_obs, double *out) {
+  if (sv_status st = check_state(s)) return st;
+  if (n_obs > 0 && !out) return fail(SV_ERR_ARG, "out is NULL");
+  if (n_obs == 0) return SV_OK;
+  sv_program *p = nullptr;
+  if (sv_status st = build_program(s, nullptr, obs, n_obs, nullptr, true, &p)) return st;
+  p->want_lam = true;
+  JacWs w;
+  sv_status st = jac_workspace(p, w);
+  if (!st) st = run_var(p, w);
+  if (!st) st = copy_out(s, out, w.J, n_obs, false);
   if (!st) st = sync_state(s);
   destroy_program(p);
   return st;

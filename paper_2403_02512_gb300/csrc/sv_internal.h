@@ -191,6 +191,8 @@ struct Launch {
   static cudaError_t stream_op(void *psi, int n, const StreamDev &sd, const void *mats, cudaStream_t st);
   // psi <- psi / ||psi|| (||psi||^2 in FP64 over kNormBlocks fixed partials in `scratch`).
   static cudaError_t renormalize(void *psi, int n, double *scratch, cudaStream_t st);
+  // kNormBlocks FP64 partials of ||psi||^2 (fixed order).
+  static cudaError_t norm_partials(const void *psi, int n, double *partials, cudaStream_t st);
   // Persistent batch launch: `grid` CTAs drain the work items of all segments.
   static cudaError_t batch(void *states, const BatchCircuit *circs, const PassDev *passes, const OpDev *ops,
                            const void *mats, const uint64_t *aux, const BatchSeg *segs, int n_segs, int64_t total_items,
@@ -210,6 +212,8 @@ struct Launch {
 };
 
 // Batch: out[c.out] = sum_term coeff * sum_tile partials (fixed order), one thread per circuit.
+// out[j0 + j] = sum_b partials[j * nb + b] - E[j0 + j]^2, j < m (variances).
+cudaError_t var_combine(const double *partials, int nb, int m, const double *E, int j0, double *out, cudaStream_t st);
 cudaError_t batch_reduce(const BatchCircuit *circs, int n_circ, const ZTerm *terms, const double *partials,
                          double *out, cudaStream_t st);
 

@@ -83,6 +83,23 @@ cudaError_t assemble_jacobian(const double *contrib, const double *coef, const i
   return cudaGetLastError();
 }
 
+// Variances: one thread per observable, partials summed in ascending order.
+__global__ void k_var_combine(const double *__restrict__ partials, int nb, int m, const double *__restrict__ E, int j0,
+                              double *__restrict__ out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= m) return;
+  double t = 0.0;
+  for (int b = 0; b < nb; ++b) t += partials[(size_t)j * nb + b];
+  const double e = E[j0 + j];
+  out[j0 + j] = t - e * e;
+}
+
+cudaError_t var_combine(const double *partials, int nb, int m, const double *E, int j0, double *out, cudaStream_t st) {
+  if (m <= 0) return cudaSuccess;
+  k_var_combine<<<(m + 127) / 128, 128, 0, st>>>(partials, nb, m, E, j0, out);
+  return cudaGetLastError();
+}
+
 // Batch: out[c.out] = sum_t coeff_t * sum_tile partials[part_begin + t * tiles + tile].
 // One warp per circuit: lane l sums tiles l, l + 32, ... in ascending order,
 // a fixed shuffle tree combines the lanes, terms are added in ascending order.

@@ -181,6 +181,12 @@ cudaError_t Launch<R>::renormalize(void *psi, int n, double *scratch, cudaStream
 }
 
 template <typename R>
+cudaError_t Launch<R>::norm_partials(const void *psi, int n, double *partials, cudaStream_t st) {
+  k_norm_partials<R><<<kNormBlocks, kBlock, 0, st>>>(reinterpret_cast<const g_t<R> *>(psi), 1ull << n, partials);
+  return cudaGetLastError();
+}
+
+template <typename R>
 int Launch<R>::batch_blocks_per_sm(int max_T, int max_terms, int max_k) {
   const int smem = (int)((sizeof(c_t<R>) + 8) << max_T) + max_terms * detail::kWarps * 8;
   // the occupancy query honours the dynamic shared-memory opt-in: set it first

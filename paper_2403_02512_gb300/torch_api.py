@@ -81,6 +81,9 @@ class StateVector:
     def expval(self, observables) -> np.ndarray:
         return L.sv_expval(self.handle, L.PauliSums(observables))
 
+    def var(self, observables) -> np.ndarray:
+        return L.sv_var(self.handle, L.PauliSums(observables))
+
     def norm2(self) -> float:
         return L.sv_norm2(self.handle)
 

@@ -423,3 +423,20 @@ def test_phase_runs_in_a_batch():
     for c, p, g in zip(circs, params, got):
         want = oracle.expvals(oracle.forward(c, p), c.observables)[0]
         assert abs(g - want) <= 1e-4, (c.n, g, want)
+
+
+# ---- variances ---------------------------------------------------------------
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("n", [1, 3, 13, 18])
+def test_variance_matches_oracle(dtype, n):
+    sv, psi = _state(n, dtype, 300 + n)
+    rng = np.random.default_rng(300 + n)
+    obs = [random_hamiltonian(n, 25, rng, weights=tuple(range(1, min(n, 4) + 1))) for _ in range(3)]
+    obs.append([Term(1.0, ((0, "Z"),))])          # single word: 1 - <Z>^2
+    obs.append([Term(0.5, ())])                   # identity: variance 0
+    obs.append([])                                # no terms: 0
+    got = sv.var(obs)
+    want = np.array([oracle.variance(psi, H) for H in obs])
+    _assert_rel(got, want, TOL_E[dtype] * 10, "variance")
+    again = sv.var(obs)
+    assert np.array_equal(got, again)             # fixed-order reductions repeat bitwise
