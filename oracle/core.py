@@ -336,6 +336,31 @@ def variance(psi: np.ndarray, terms) -> float:
     return inner(psi, h2).real - e * e
 
 
+def probabilities(psi: np.ndarray, wires: Sequence[int]) -> np.ndarray:
+    """Marginal probabilities of measuring `wires` in the computational basis
+    (the device's probability measurement, Sec. 2.2; Listing 3 reads them out):
+    p[b] = sum over indices i whose bits at `wires` spell b of |psi_i|^2, with
+    wires[0] the most significant bit of b and wire w at index bit n-1-w."""
+    n = _nqubits(psi)
+    k = len(wires)
+    idx = np.arange(psi.size, dtype=np.int64)
+    b = np.zeros(psi.size, dtype=np.int64)
+    for j, w in enumerate(wires):
+        b |= ((idx >> (n - 1 - w)) & 1) << (k - 1 - j)
+    p = np.zeros(1 << k)
+    np.add.at(p, b, psi.real ** 2 + psi.imag ** 2)
+    return p
+
+
+def sample(psi: np.ndarray, wires: Sequence[int], uniforms: Sequence[float]) -> np.ndarray:
+    """Outcomes for given uniforms u in [0, 1): the first b whose cumulative
+    probability (summed in ascending b) exceeds u * total (inverse transform)."""
+    p = probabilities(psi, wires)
+    cdf = np.cumsum(p)
+    u = np.asarray(uniforms, dtype=np.float64) * cdf[-1]
+    return np.minimum(np.searchsorted(cdf, u, side="right"), p.size - 1).astype(np.uint64)
+
+
 def expvals(psi: np.ndarray, observables) -> np.ndarray:
     return np.array([expval(psi, H) for H in observables])
 

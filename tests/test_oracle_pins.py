@@ -419,3 +419,52 @@ def test_variance_matches_dense_hamiltonian(seed):
     e = np.vdot(psi, Hd @ psi).real
     want = np.vdot(psi, Hd @ (Hd @ psi)).real - e * e
     assert abs(oracle.variance(psi, H) - want) < 1e-12 * max(1.0, abs(want))
+
+
+# ---- probabilities and samples ----------------------------------------------
+def test_probabilities_of_a_product_state_closed_form():
+    th = np.array([0.3, 1.1, 2.5, 0.9])
+    c = Circuit(4, [Op("RY", (w,), (w,)) for w in range(4)], 4, [])
+    psi = oracle.forward(c, th)
+    for w in range(4):
+        p = oracle.probabilities(psi, [w])
+        assert abs(p[1] - math.sin(th[w] / 2) ** 2) < 1e-15 and abs(p.sum() - 1) < 1e-15
+    p = oracle.probabilities(psi, [3, 1])  # wires[0] is the most significant outcome bit
+    for b3 in (0, 1):
+        for b1 in (0, 1):
+            want = ((math.sin(th[3] / 2) ** 2) if b3 else (math.cos(th[3] / 2) ** 2)) * \
+                   ((math.sin(th[1] / 2) ** 2) if b1 else (math.cos(th[1] / 2) ** 2))
+            assert abs(p[2 * b3 + b1] - want) < 1e-15
+
+
+def test_probabilities_brute_force_and_wire_order():
+    n = 4
+    psi = random_state(n, 5)
+    for wires in ([0], [3], [2, 0], [1, 3, 2], [0, 1, 2, 3], []):
+        want = np.zeros(1 << len(wires))
+        for i in range(1 << n):
+            bits = [(i >> (n - 1 - w)) & 1 for w in wires]
+            b = 0
+            for x in bits:
+                b = 2 * b + x
+            want[b] += abs(psi[i]) ** 2
+        assert np.abs(oracle.probabilities(psi, wires) - want).max() < 1e-15
+    # a basis state |i> is one-hot on its own bits
+    e = oracle.basis_state(n, 0b1011)
+    assert list(oracle.probabilities(e, [2, 0])) == [0.0, 0.0, 0.0, 1.0]
+
+
+def test_sampling_by_inverse_transform():
+    n = 3
+    ghz = oracle.forward(Circuit(n, [Op("Hadamard", (0,))] + [Op("PauliX", (w + 1,), controls=(w,))
+                                                              for w in range(n - 1)], 0, []), np.zeros(0))
+    u = np.array([0.0, 0.2, 0.4999999, 0.5, 0.75, 0.9999999])
+    assert list(oracle.sample(ghz, [0, 1, 2], u)) == [0, 0, 0, 7, 7, 7]
+    assert list(oracle.sample(oracle.basis_state(n, 5), [0, 1, 2], u)) == [5] * 6
+    # empirical frequencies of seeded uniforms: within 5 sigma of the probabilities
+    psi = random_state(n, 9)
+    p = oracle.probabilities(psi, [2, 0])
+    shots = 20000
+    s = oracle.sample(psi, [2, 0], np.random.default_rng(9).random(shots))
+    freq = np.bincount(s.astype(np.int64), minlength=4) / shots
+    assert np.all(np.abs(freq - p) <= 5 * np.sqrt(p * (1 - p) / shots) + 1e-12)
