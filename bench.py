@@ -345,6 +345,45 @@ def extra_vqe():
     return out
 
 
+def extra_measurements(hbm_peak):
+    """Measurement processes on the sel24 output state: expectation values and
+    variances of the 24 single-Z observables, marginal probabilities of all 24
+    wires, 10^4 samples.  Algorithmic bytes: expval V; variance V + 2 m V
+    (lambda passes write m vectors, the norms read them); probabilities V;
+    samples V plus the 2^24-entry CDF."""
+    import torch
+    from paper_2403_02512_gb300.torch_api import Program, StateVector
+    from workloads import strongly_entangling
+    c, p = strongly_entangling(N_QUBITS, LAYERS)
+    m = len(c.observables)
+    out = {}
+    u = np.random.default_rng(7).random(10000)
+    wires = list(range(N_QUBITS))
+    for dtype in ("c128", "c64"):
+        sv = StateVector(N_QUBITS, dtype)
+        prog = Program.from_circuit(sv, c)
+        prog.forward(p)
+        V = (8 if dtype == "c64" else 16) << N_QUBITS
+        res = {}
+        for name, fn, alg in (("expval", lambda: sv.expval(c.observables), V),
+                              ("variance", lambda: sv.var(c.observables), V + 2 * m * V),
+                              ("probs_all_wires", lambda: sv.probs(wires), V + 8 * (1 << N_QUBITS)),
+                              ("sample_1e4_all_wires", lambda: sv.sample(wires, u), V + 3 * 8 * (1 << N_QUBITS))):
+            fn()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            reps = 3
+            for _ in range(reps):
+                fn()
+            ms = (time.perf_counter() - t0) / reps * 1e3
+            res[name] = {"ms": ms, "frac_of_hbm": alg / ms / 1e6 / hbm_peak}
+        out[dtype] = res
+        prog.close()
+        sv.close()
+        torch.cuda.empty_cache()
+    return out
+
+
 def extra_rycz30():
     """30-qubit RY layers + CZ brick, <Z0 Z29>: forward + full adjoint Jacobian (600 params)."""
     import torch
@@ -528,6 +567,7 @@ def run_ours(args):
             extras["qaoa_batched"] = extra_qaoa()
             extras["vqe24_2000_terms"] = extra_vqe()
             extras["rycz30"] = extra_rycz30()
+            extras["measurements_sel24"] = extra_measurements(hbm_peak)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

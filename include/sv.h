@@ -238,6 +238,26 @@ sv_status sv_norm2(sv_state *s, double *out);
  * is not modified. */
 sv_status sv_var(sv_state *s, const sv_pauli_sum *obs, int n_obs, double *out);
 
+/* Marginal probabilities of k wires (the device's probability measurement,
+ * Sec. 2.2; Listing 3 reads probabilities out of a circuit):
+ *   out[b] = sum of |psi_i|^2 over indices i whose bits at wires[0..k) spell b,
+ * with wires[0] the most significant bit of b (wire w = index bit n-1-w).
+ * 0 <= k <= min(n, SV_MAX_PROB_WIRES); wires distinct and in [0, n); out is a
+ * host array of 2^k doubles.  FP64 sums in a fixed order (bitwise repeatable).
+ * k = 0 gives out[0] = <psi|psi>.  SV_ERR_ARG on bad wires; the state is not
+ * modified. */
+#define SV_MAX_PROB_WIRES 24
+sv_status sv_probs(sv_state *s, const int *wires, int k, double *out);
+
+/* Samples of k wires by inverse transform: for each caller-drawn uniform
+ * u[t] in [0, 1) (host array of `shots`), out[t] (host, uint64) is the first
+ * outcome b whose cumulative probability -- the marginal probabilities of
+ * sv_probs summed in ascending b by a fixed-order scan -- exceeds u[t] times
+ * their total.  The caller owns the random numbers (seeded, reproducible);
+ * the same uniforms give the same samples.  SV_ERR_ARG for a uniform outside
+ * [0, 1), bad wires or shots < 0; the state is not modified. */
+sv_status sv_sample(sv_state *s, const int *wires, int k, const double *uniforms, int64_t shots, uint64_t *out);
+
 /* ---- circuits (S4, S6-S8) ----------------------------------------------------- */
 
 /* psi <- U_N ... U_1 psi for the tape with the given parameters.  Ops are fused

@@ -103,6 +103,8 @@ PROTOTYPES = {
     "sv_expval": (ctypes.c_int, [_vp, ctypes.POINTER(SvPauliSum), ctypes.c_int, _dp]),
     "sv_norm2": (ctypes.c_int, [_vp, _dp]),
     "sv_var": (ctypes.c_int, [_vp, ctypes.POINTER(SvPauliSum), ctypes.c_int, _dp]),
+    "sv_probs": (ctypes.c_int, [_vp, _ip, ctypes.c_int, _dp]),
+    "sv_sample": (ctypes.c_int, [_vp, _ip, ctypes.c_int, _dp, ctypes.c_int64, ctypes.POINTER(ctypes.c_uint64)]),
     "sv_forward": (ctypes.c_int, [_vp, ctypes.POINTER(SvTape), _dp]),
     "sv_adjoint_jacobian": (ctypes.c_int, [_vp, ctypes.POINTER(SvTape), _dp, ctypes.POINTER(SvPauliSum),
                                            ctypes.c_int, _dp, _dp]),
@@ -272,6 +274,26 @@ def sv_expval(h: int, obs: "PauliSums") -> np.ndarray:
 def sv_var(h: int, obs: "PauliSums") -> np.ndarray:
     out = np.zeros(obs.count, dtype=np.float64)
     _check(load().sv_var(_vp(h), obs.array, obs.count, _dptr(out)))
+    return out
+
+
+def _wires(wires):
+    arr = (ctypes.c_int * max(1, len(wires)))(*[int(w) for w in wires])
+    return arr, len(wires)
+
+
+def sv_probs(h: int, wires) -> np.ndarray:
+    arr, k = _wires(wires)
+    out = np.zeros(1 << k, dtype=np.float64)
+    _check(load().sv_probs(_vp(h), arr, k, _dptr(out)))
+    return out
+
+
+def sv_sample(h: int, wires, uniforms) -> np.ndarray:
+    arr, k = _wires(wires)
+    u = np.ascontiguousarray(uniforms, dtype=np.float64)
+    out = np.zeros(u.size, dtype=np.uint64)
+    _check(load().sv_sample(_vp(h), arr, k, _dptr(u), u.size, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))))
     return out
 
 

@@ -2306,6 +2306,101 @@ sv_status sv_var(sv_state *s, const sv_pauli_sum *obs, int n_obs, double *out) {
   return st;
 }
 
+namespace {
+// Marginal probabilities of `wires` into dev_probs (2^k doubles, device).
+sv_status probs_device(sv_state *s, const int *wires, int k, double *dev_probs, double *partials) {
+  ProbsDev pd;
+  memset(&pd, 0, sizeof(pd));
+  pd.n = s->n;
+  pd.k = k;
+  pd.chunk_log = std::min(s->n - k, 12);
+  uint64_t mask = 0;
+  for (int j = 0; j < k; ++j) {
+    pd.bitpos[j] = (int8_t)(s->n - 1 - wires[j]);
+    mask |= 1ull << (s->n - 1 - wires[j]);
+  }
+  int q = 0;
+  for (int b = 0; b < s->n; ++b)
+    if ((mask >> b) & 1) pd.pos[q++] = (int8_t)b;
+  cudaError_t e;
+  if (s->n - k <= kProbsSmallLog) {
+    e = s->dt == SV_C64 ? Launch<float>::probs_small(s->psi, pd, dev_probs, s->stream)
+                        : Launch<double>::probs_small(s->psi, pd, dev_probs, s->stream);
+  } else {
+    e = s->dt == SV_C64 ? Launch<float>::probs_partials(s->psi, pd, partials, s->stream)
+                        : Launch<double>::probs_partials(s->psi, pd, partials, s->stream);
+    if (e == cudaSuccess) e = probs_combine(partials, 1ll << k, 1 << (s->n - k - pd.chunk_log), dev_probs, s->stream);
+  }
+  return after_launch(s, e, "probabilities");
+}
+
+sv_status check_wires(const sv_state *s, const int *wires, int k) {
+  if (k < 0 || k > std::min(s->n, kMaxProbWires))
+    return fail(SV_ERR_ARG, "k = %d wires outside [0, %d]", k, std::min(s->n, kMaxProbWires));
+  if (k > 0 && !wires) return fail(SV_ERR_ARG, "wires is NULL");
+  uint64_t seen = 0;
+  for (int j = 0; j < k; ++j) {
+    if (wires[j] < 0 || wires[j] >= s->n) return fail(SV_ERR_ARG, "wire %d outside [0, %d)", wires[j], s->n);
+    if ((seen >> wires[j]) & 1) return fail(SV_ERR_ARG, "wire %d repeated", wires[j]);
+    seen |= 1ull << wires[j];
+  }
+  return SV_OK;
+}
+
+size_t probs_partials_count(int n, int k) {
+  return n - k <= kProbsSmallLog ? 1 : (size_t)1 << (n - std::min(n - k, 12));
+}
+}  // namespace
+
+sv_status sv_probs(sv_state *s, const int *wires, int k, double *out) {
+  if (sv_status st = check_state(s)) return st;
+  if (sv_status st = check_wires(s, wires, k)) return st;
+  if (!out) return fail(SV_ERR_ARG, "out is NULL");
+  const size_t bins = (size_t)1 << k, parts = probs_partials_count(s->n, k);
+  char *base = nullptr;
+  if (sv_status st = get_workspace(s, align256(bins * 8) + align256(parts * 8), &base)) return st;
+  double *probs = (double *)base, *partials = (double *)(base + align256(bins * 8));
+  sv_status st = probs_device(s, wires, k, probs, partials);
+  if (!st) st = copy_out(s, out, probs, bins, false);
+  if (!st) st = sync_state(s);
+  return st;
+}
+
+sv_status sv_sample(sv_state *s, const int *wires, int k, const double *uniforms, int64_t shots, uint64_t *out) {
+  if (sv_status st = check_state(s)) return st;
+  if (sv_status st = check_wires(s, wires, k)) return st;
+  if (shots < 0) return fail(SV_ERR_ARG, "shots < 0");
+  if (shots == 0) return SV_OK;
+  if (!uniforms || !out) return fail(SV_ERR_ARG, "uniforms / out is NULL");
+  for (int64_t t = 0; t < shots; ++t)
+    if (!(uniforms[t] >= 0.0 && uniforms[t] < 1.0)) return fail(SV_ERR_ARG, "uniforms[%lld] not in [0, 1)", (long long)t);
+  const size_t bins = (size_t)1 << k, parts = probs_partials_count(s->n, k);
+  const size_t scan = (bins + 4095) / 4096;
+  const size_t bytes = align256(bins * 8) + align256(parts * 8) + align256(scan * 8) + align256((size_t)shots * 8) +
+                       align256((size_t)shots * 8);
+  char *base = nullptr;
+  if (sv_status st = get_workspace(s, bytes, &base)) return st;
+  size_t c = 0;
+  double *cdf = (double *)(base + c);
+  c += align256(bins * 8);
+  double *partials = (double *)(base + c);
+  c += align256(parts * 8);
+  double *scratch = (double *)(base + c);
+  c += align256(scan * 8);
+  double *u = (double *)(base + c);
+  c += align256((size_t)shots * 8);
+  uint64_t *dout = (uint64_t *)(base + c);
+  cudaError_t e = cudaMemcpyAsync(u, uniforms, (size_t)shots * 8, cudaMemcpyHostToDevice, s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "copying uniforms");
+  if (sv_status st = probs_device(s, wires, k, cdf, partials)) return st;
+  e = inclusive_scan(cdf, (int64_t)bins, scratch, s->stream);
+  if (e == cudaSuccess) e = sample_cdf(cdf, (int64_t)bins, u, shots, dout, s->stream);
+  if (sv_status st = after_launch(s, e, "sampling")) return st;
+  e = cudaMemcpyAsync(out, dout, (size_t)shots * 8, cudaMemcpyDeviceToHost, s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "copying samples");
+  return sync_state(s);
+}
+
 sv_status sv_norm2(sv_state *s, double *out) {
   if (!out) return fail(SV_ERR_ARG, "out is NULL");
   const double c = 1.0;

@@ -141,6 +141,25 @@ struct StreamDev {
   int32_t pair16;         // complex64 pair on bit 0 alone: both members in one 16-byte access
 };
 
+// Marginal probabilities of k wires: enumeration index j = bin * 2^(n-k) + other,
+// amplitude index = `other` with zeros inserted at the wires' bits (ascending
+// pos) or-ed with bin's bits placed at bitpos[0..k) (bitpos[0] = most
+// significant bin bit).
+struct ProbsDev {
+  int32_t n, k, chunk_log;
+  int32_t pad;
+  int8_t pos[kMaxQubits];     // the wires' global bits, ascending
+  int8_t bitpos[kMaxQubits];  // global bit of bin bit k-1-j for j = 0..k-1 (wires order)
+};
+constexpr int kMaxProbWires = 24;   // 2^24 bins at most
+constexpr int kProbsSmallLog = 6;   // bins of <= 64 amplitudes: one thread per bin
+
+// Deterministic inclusive prefix sum of m doubles in place (three fixed levels,
+// `scratch` >= ceil(m / 4096) doubles), and inverse-transform sampling.
+cudaError_t inclusive_scan(double *x, int64_t m, double *scratch, cudaStream_t st);
+cudaError_t probs_combine(const double *partials, int64_t bins, int per_bin, double *out, cudaStream_t st);
+cudaError_t sample_cdf(const double *cdf, int64_t m, const double *u, int64_t shots, uint64_t *out, cudaStream_t st);
+
 // ---- batched circuits (S9) --------------------------------------------------
 // One circuit of a batch: its passes, its Z-only observable and its state slice.
 struct BatchCircuit {
@@ -193,6 +212,11 @@ struct Launch {
   static cudaError_t renormalize(void *psi, int n, double *scratch, cudaStream_t st);
   // kNormBlocks FP64 partials of ||psi||^2 (fixed order).
   static cudaError_t norm_partials(const void *psi, int n, double *partials, cudaStream_t st);
+  // Marginal-probability partials: partials[c] = sum of |psi_i|^2 over chunk c of 2^chunk_log
+  // consecutive (bin, other) indices, bin = the bits at the wires (see ProbsDev).
+  static cudaError_t probs_partials(const void *psi, const ProbsDev &pd, double *partials, cudaStream_t st);
+  // Bins of <= 2^kProbsSmallLog amplitudes: out[bin] directly, one thread per bin.
+  static cudaError_t probs_small(const void *psi, const ProbsDev &pd, double *out, cudaStream_t st);
   // Persistent batch launch: `grid` CTAs drain the work items of all segments.
   static cudaError_t batch(void *states, const BatchCircuit *circs, const PassDev *passes, const OpDev *ops,
                            const void *mats, const uint64_t *aux, const BatchSeg *segs, int n_segs, int64_t total_items,

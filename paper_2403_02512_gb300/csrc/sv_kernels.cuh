@@ -1716,6 +1716,57 @@ __global__ void __launch_bounds__(kBlock) k_norm_scale(g_t<R> *__restrict__ psi,
   }
 }
 
+// Marginal probabilities: block c sums |psi_i|^2 over enumeration indices
+// [c L, (c + 1) L), L = 2^chunk_log <= 2^(n-k), so one bin per block; per-thread
+// strided FP64 sums, fixed tree (bitwise repeatable).
+template <typename R>
+__global__ void __launch_bounds__(kBlock) k_probs_partials(const g_t<R> *__restrict__ psi, const ProbsDev pd,
+                                                           double *__restrict__ partials) {
+  __shared__ double red[kBlock / 32];
+  const uint64_t L = 1ull << pd.chunk_log;
+  const uint64_t j0 = (uint64_t)blockIdx.x * L;
+  const uint64_t bin = j0 >> (pd.n - pd.k);
+  uint64_t binmask = 0;
+  for (int j = 0; j < pd.k; ++j)
+    if ((bin >> (pd.k - 1 - j)) & 1) binmask |= 1ull << pd.bitpos[j];
+  const uint64_t other0 = j0 & ((1ull << (pd.n - pd.k)) - 1);
+  double acc = 0.0;
+  for (uint64_t t = threadIdx.x; t < L; t += blockDim.x) {
+    uint64_t i = other0 + t;
+    for (int q = 0; q < pd.k; ++q) {
+      const int b = pd.pos[q];
+      i = ((i >> b) << (b + 1)) | (i & ((1ull << b) - 1));
+    }
+    const g_t<R> a = __ldcs(psi + (i | binmask));
+    acc += (double)a.x * (double)a.x + (double)a.y * (double)a.y;
+  }
+  const double t = block_sum_fixed(acc, red);
+  if (threadIdx.x == 0) partials[blockIdx.x] = t;
+}
+
+// Marginal probabilities with small bins (2^(n-k) <= 64 amplitudes each): one
+// thread per bin sums its amplitudes in ascending order and writes the bin.
+template <typename R>
+__global__ void __launch_bounds__(kBlock) k_probs_small(const g_t<R> *__restrict__ psi, const ProbsDev pd,
+                                                        double *__restrict__ out) {
+  const uint64_t bin = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (bin >> pd.k) return;
+  uint64_t binmask = 0;
+  for (int j = 0; j < pd.k; ++j)
+    if ((bin >> (pd.k - 1 - j)) & 1) binmask |= 1ull << pd.bitpos[j];
+  double acc = 0.0;
+  for (uint64_t o = 0; o < (1ull << (pd.n - pd.k)); ++o) {
+    uint64_t i = o;
+    for (int q = 0; q < pd.k; ++q) {
+      const int b = pd.pos[q];
+      i = ((i >> b) << (b + 1)) | (i & ((1ull << b) - 1));
+    }
+    const g_t<R> a = __ldcs(psi + (i | binmask));
+    acc += (double)a.x * (double)a.x + (double)a.y * (double)a.y;
+  }
+  out[bin] = acc;
+}
+
 template <typename R>
 __global__ void k_set_basis(g_t<R> *psi, uint64_t N, uint64_t index) {
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < N; i += (uint64_t)gridDim.x * blockDim.x) {

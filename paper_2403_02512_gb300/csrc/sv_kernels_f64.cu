@@ -100,6 +100,99 @@ cudaError_t var_combine(const double *partials, int nb, int m, const double *E, 
   return cudaGetLastError();
 }
 
+// Probabilities: out[bin] = its per_bin consecutive partials, ascending.
+__global__ void k_probs_combine(const double *__restrict__ partials, int64_t bins, int per_bin, double *__restrict__ out) {
+  const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (b >= bins) return;
+  double t = 0.0;
+  for (int c = 0; c < per_bin; ++c) t += partials[b * per_bin + c];
+  out[b] = t;
+}
+
+cudaError_t probs_combine(const double *partials, int64_t bins, int per_bin, double *out, cudaStream_t st) {
+  if (bins <= 0) return cudaSuccess;
+  k_probs_combine<<<(unsigned)((bins + 255) / 256), 256, 0, st>>>(partials, bins, per_bin, out);
+  return cudaGetLastError();
+}
+
+// Inclusive scan of one 4096-element segment per 1024-thread block: each
+// thread sums its 4 elements in order, a Hillis-Steele scan over the 1024
+// thread sums (fixed steps), then each thread writes its 4 running sums.
+// totals[block] = the segment's sum.
+constexpr int kScanThreads = 1024, kScanPer = 4, kScanSeg = kScanThreads * kScanPer;
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_segments(double *__restrict__ x, int64_t m,
+                                                                double *__restrict__ totals) {
+  __shared__ double sh[2][kScanThreads];
+  const int64_t base = (int64_t)blockIdx.x * kScanSeg + (int64_t)threadIdx.x * kScanPer;
+  double v[kScanPer];
+  double run = 0.0;
+  for (int e = 0; e < kScanPer; ++e) {
+    v[e] = base + e < m ? x[base + e] : 0.0;
+    run += v[e];
+  }
+  int cur = 0;
+  sh[0][threadIdx.x] = run;
+  __syncthreads();
+  for (int d = 1; d < kScanThreads; d <<= 1) {
+    const double a = sh[cur][threadIdx.x];
+    const double b = threadIdx.x >= (unsigned)d ? sh[cur][threadIdx.x - d] : 0.0;
+    sh[cur ^ 1][threadIdx.x] = threadIdx.x >= (unsigned)d ? b + a : a;
+    cur ^= 1;
+    __syncthreads();
+  }
+  double pre = threadIdx.x > 0 ? sh[cur][threadIdx.x - 1] : 0.0;  // exclusive prefix of this thread
+  for (int e = 0; e < kScanPer; ++e) {
+    pre += v[e];
+    if (base + e < m) x[base + e] = pre;
+  }
+  if (threadIdx.x == kScanThreads - 1 && totals) totals[blockIdx.x] = sh[cur][threadIdx.x];
+}
+
+__global__ void k_scan_add(double *__restrict__ x, int64_t m, const double *__restrict__ offsets) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  const int64_t seg = i / kScanSeg;
+  if (seg > 0) x[i] += offsets[seg - 1];
+}
+
+// Three fixed levels: segments of 4096, their totals (<= 4096 segments, one
+// block), offsets added back.  m <= 2^24.
+cudaError_t inclusive_scan(double *x, int64_t m, double *scratch, cudaStream_t st) {
+  if (m <= 0) return cudaSuccess;
+  const int64_t segs = (m + kScanSeg - 1) / kScanSeg;
+  if (segs > kScanSeg) return cudaErrorInvalidValue;
+  k_scan_segments<<<(unsigned)segs, kScanThreads, 0, st>>>(x, m, segs > 1 ? scratch : nullptr);
+  if (segs > 1) {
+    k_scan_segments<<<1, kScanThreads, 0, st>>>(scratch, segs, nullptr);
+    k_scan_add<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(x, m, scratch);
+  }
+  return cudaGetLastError();
+}
+
+// out[t] = first b with cdf[b] > u[t] * cdf[m - 1] (clamped to m - 1).
+__global__ void k_sample_cdf(const double *__restrict__ cdf, int64_t m, const double *__restrict__ u, int64_t shots,
+                             uint64_t *__restrict__ out) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= shots) return;
+  const double target = u[t] * cdf[m - 1];
+  int64_t lo = 0, hi = m - 1;  // answer in [lo, hi]
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (cdf[mid] > target)
+      hi = mid;
+    else
+      lo = mid + 1;
+  }
+  out[t] = (uint64_t)lo;
+}
+
+cudaError_t sample_cdf(const double *cdf, int64_t m, const double *u, int64_t shots, uint64_t *out, cudaStream_t st) {
+  if (shots <= 0) return cudaSuccess;
+  k_sample_cdf<<<(unsigned)((shots + 255) / 256), 256, 0, st>>>(cdf, m, u, shots, out);
+  return cudaGetLastError();
+}
+
 // Batch: out[c.out] = sum_t coeff_t * sum_tile partials[part_begin + t * tiles + tile].
 // One warp per circuit: lane l sums tiles l, l + 32, ... in ascending order,
 // a fixed shuffle tree combines the lanes, terms are added in ascending order.

@@ -187,6 +187,21 @@ cudaError_t Launch<R>::norm_partials(const void *psi, int n, double *partials, c
 }
 
 template <typename R>
+cudaError_t Launch<R>::probs_partials(const void *psi, const ProbsDev &pd, double *partials, cudaStream_t st) {
+  const uint64_t blocks = 1ull << (pd.n - pd.chunk_log);
+  k_probs_partials<R><<<(unsigned)blocks, kBlock, 0, st>>>(reinterpret_cast<const g_t<R> *>(psi), pd, partials);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t Launch<R>::probs_small(const void *psi, const ProbsDev &pd, double *out, cudaStream_t st) {
+  const uint64_t bins = 1ull << pd.k;
+  k_probs_small<R><<<(unsigned)((bins + kBlock - 1) / kBlock), kBlock, 0, st>>>(reinterpret_cast<const g_t<R> *>(psi),
+                                                                               pd, out);
+  return cudaGetLastError();
+}
+
+template <typename R>
 int Launch<R>::batch_blocks_per_sm(int max_T, int max_terms, int max_k) {
   const int smem = (int)((sizeof(c_t<R>) + 8) << max_T) + max_terms * detail::kWarps * 8;
   // the occupancy query honours the dynamic shared-memory opt-in: set it first

@@ -84,6 +84,12 @@ class StateVector:
     def var(self, observables) -> np.ndarray:
         return L.sv_var(self.handle, L.PauliSums(observables))
 
+    def probs(self, wires) -> np.ndarray:
+        return L.sv_probs(self.handle, list(wires))
+
+    def sample(self, wires, uniforms) -> np.ndarray:
+        return L.sv_sample(self.handle, list(wires), uniforms)
+
     def norm2(self) -> float:
         return L.sv_norm2(self.handle)
 

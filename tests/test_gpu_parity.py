@@ -440,3 +440,58 @@ def test_variance_matches_oracle(dtype, n):
     _assert_rel(got, want, TOL_E[dtype] * 10, "variance")
     again = sv.var(obs)
     assert np.array_equal(got, again)             # fixed-order reductions repeat bitwise
+
+
+# ---- probabilities and samples -----------------------------------------------
+def _wire_sets(n, rng):
+    sets = [[], [0], [n - 1], list(range(n)), list(range(n))[::-1]]
+    for k in (2, 3, min(n, 6)):
+        if k <= n:
+            sets.append([int(w) for w in rng.permutation(n)[:k]])
+    return sets
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("n", [1, 3, 13, 20])
+def test_probabilities_match_oracle(dtype, n):
+    sv, psi = _state(n, dtype, 400 + n)
+    rng = np.random.default_rng(400 + n)
+    for wires in _wire_sets(n, rng):
+        got = sv.probs(wires)
+        want = oracle.probabilities(psi, wires)
+        assert got.shape == want.shape
+        assert np.abs(got - want).max() <= 1e-12, wires
+        assert np.array_equal(got, sv.probs(wires))  # fixed-order sums repeat bitwise
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("n", [3, 13, 20])
+def test_samples_match_oracle_inverse_transform(dtype, n):
+    sv, psi = _state(n, dtype, 500 + n)
+    rng = np.random.default_rng(500 + n)
+    for wires in _wire_sets(n, rng):
+        u = rng.random(4000)
+        got = sv.sample(wires, u)
+        want = oracle.sample(psi, wires, u)
+        # equal except where u * total lies within rounding of a CDF boundary
+        # (the device's scan and the oracle's running sum round differently)
+        cdf = np.cumsum(oracle.probabilities(psi, wires))
+        target = u * cdf[-1]
+        g = got.astype(np.int64)
+        lo = np.where(g > 0, cdf[np.maximum(g - 1, 0)], 0.0)
+        assert np.all(lo <= target + 1e-12) and np.all(cdf[g] > target - 1e-12), wires
+        assert np.count_nonzero(got != want) <= 2, wires
+        assert np.array_equal(got, sv.sample(wires, u))
+
+
+def test_probabilities_and_samples_reject_bad_arguments():
+    sv = StateVector(4, "c128")
+    for wires in ([0, 0], [4], [-1]):
+        with pytest.raises(L.SvError) as ei:
+            sv.probs(wires)
+        assert ei.value.status == 1
+    for u in ([1.0], [-0.1], [float("nan")]):
+        with pytest.raises(L.SvError) as ei:
+            sv.sample([0], u)
+        assert ei.value.status == 1
+    assert sv.sample([0, 1], []).size == 0
