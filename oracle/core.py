@@ -432,6 +432,33 @@ def adjoint_jacobian(circuit, params: np.ndarray, observables=None, psi_final=No
     return E, J
 
 
+def jvp(circuit, params: np.ndarray, tangent: Sequence[float], observables=None) -> np.ndarray:
+    """Forward-mode derivative along `tangent` (the Jacobian-vector product the
+    paper names as future work in Sec. 5): psi and dpsi = d psi(params + t
+    tangent)/dt at t = 0 go through the expanded tape together.  A step
+    U = exp(i s theta G) with theta = scale * params[p] gives
+    dpsi <- U dpsi + i s scale tangent[p] G (U psi); then
+    d<H_j>/dt = 2 Re <psi|H_j|dpsi>."""
+    obs = circuit.observables if observables is None else observables
+    v = np.asarray(tangent, dtype=np.float64)
+    psi = initial_state(circuit)
+    dpsi = np.zeros_like(psi)
+    for st in expand(circuit.ops):
+        M = _step_matrix(st, params)
+        apply_matrix(psi, M, st.wires, st.controls, st.cvals)
+        apply_matrix(dpsi, M, st.wires, st.controls, st.cvals)
+        if st.param is not None and v[st.param] != 0.0:
+            G, s = generator(st.name)
+            if st.adjoint:
+                s = -s
+            mu = copy(psi)
+            apply_matrix(mu, G, st.wires, st.controls, st.cvals)
+            if st.controls:
+                project_controls(mu, st.controls, st.cvals)
+            axpy(dpsi, mu, 1j * s * st.scale * v[st.param])
+    return np.array([2.0 * inner(psi, apply_hamiltonian(dpsi, H)).real for H in obs])
+
+
 def adjoint_vjp(circuit, params: np.ndarray, grad_out: Sequence[float], observables=None):
     """sum_j grad_out[j] * J[j, :] with one lambda = sum_j grad_out[j] O_j phi."""
     obs = circuit.observables if observables is None else observables

@@ -468,3 +468,33 @@ def test_sampling_by_inverse_transform():
     s = oracle.sample(psi, [2, 0], np.random.default_rng(9).random(shots))
     freq = np.bincount(s.astype(np.int64), minlength=4) / shots
     assert np.all(np.abs(freq - p) <= 5 * np.sqrt(p * (1 - p) / shots) + 1e-12)
+
+
+# ---- forward-mode Jacobian-vector product -----------------------------------
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_jvp_matches_dense_exact_jacobian(seed):
+    n = 4
+    c, p = random_circuit(n, 30, seed, max_controls=1, shared_params=(seed == 2))
+    rng = np.random.default_rng(seed)
+    obs = [random_hamiltonian(n, 6, rng, weights=(1, 2)) for _ in range(3)]
+    v = rng.normal(size=c.n_params)
+    want = dense.exact_jacobian(c, p, obs) @ v
+    assert np.abs(oracle.jvp(c, p, v, obs) - want).max() < 1e-11
+
+
+def test_jvp_matches_central_differences_along_the_tangent():
+    c, p = layered_circuit(4, 3, seed=5)
+    v = np.random.default_rng(5).normal(size=c.n_params)
+    h = 1e-5
+    ep = oracle.expvals(oracle.forward(c, p + h * v), c.observables)
+    em = oracle.expvals(oracle.forward(c, p - h * v), c.observables)
+    assert np.abs(oracle.jvp(c, p, v) - (ep - em) / (2 * h)).max() < 1e-7
+
+
+def test_jvp_of_unit_tangents_is_the_parameter_shift_column():
+    c, p = layered_circuit(3, 2, seed=6)
+    Js = oracle.param_shift_jacobian(c, p)
+    for q in (0, 5, c.n_params - 1):
+        e = np.zeros(c.n_params)
+        e[q] = 1.0
+        assert np.abs(oracle.jvp(c, p, e) - Js[:, q]).max() < 1e-12
