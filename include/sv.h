@@ -312,6 +312,22 @@ sv_status sv_program_expval(sv_program *p, double *expvals_out, int outputs_on_d
  * Device memory: psi plus two vectors (phi, lambda). */
 sv_status sv_program_vjp(sv_program *p, const double *grad_out, double *vjp_out, int outputs_on_device);
 
+/* Jacobian-vector product in forward mode (the JVP integration the paper
+ * names as future work, Sec. 5): jvp_out[j] = sum_p d<H_j>/d params[p]
+ * tangent[p] (tangent: n_params host doubles, finite).  One tangent pass runs
+ * the tape from the state's CURRENT contents (as sv_program_forward does)
+ * while carrying d psi / dt, starting at 0; each trainable gate
+ * U = exp(i s theta G) adds i s scale tangent[p] G psi after it; then
+ * jvp_out[j] = 2 Re <H_j psi | d psi> with FP64 fixed-order sums.  The state
+ * ends holding the forward output (not renormalised).  Cost: one pass over two
+ * vectors plus one lambda per observable, whatever the number of parameters
+ * (the full Jacobian by forward mode is n_params such calls; by reverse mode,
+ * sv_program_jacobian, one sweep per observable).  Output m doubles on the host
+ * (synchronising) or in device memory (outputs_on_device = 1).
+ * SV_ERR_ARG: no observables, NULL or non-finite tangent; SV_ERR_STATE:
+ * parameters never set. */
+sv_status sv_program_jvp(sv_program *p, const double *tangent, double *jvp_out, int outputs_on_device);
+
 /* Kernel launches issued by the last program call (for launch accounting). */
 sv_status sv_program_stats(const sv_program *p, int *n_forward_passes, int *n_adjoint_passes,
                            int *launches_last_call);

@@ -118,6 +118,7 @@ PROTOTYPES = {
     "sv_program_jacobian": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int]),
     "sv_program_expval": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
     "sv_program_vjp": (ctypes.c_int, [_vp, _dp, _vp, ctypes.c_int]),
+    "sv_program_jvp": (ctypes.c_int, [_vp, _dp, _vp, ctypes.c_int]),
     "sv_program_stats": (ctypes.c_int, [_vp, _ip, _ip, _ip]),
     "sv_plan_query": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(SvTape), _ip, _ip]),
     "sv_kernel_timing_enable": (ctypes.c_int, [ctypes.c_int]),
@@ -357,6 +358,11 @@ def sv_program_expval(ph: int, expvals_ptr: int, on_device: bool) -> None:
 def sv_program_vjp(ph: int, grad_out: np.ndarray, vjp_ptr: int, on_device: bool) -> None:
     g = np.ascontiguousarray(grad_out, dtype=np.float64)
     _check(load().sv_program_vjp(_vp(ph), _dptr(g), _vp(vjp_ptr), int(on_device)))
+
+
+def sv_program_jvp(ph: int, tangent: np.ndarray, out_ptr: int, on_device: bool) -> None:
+    t = np.ascontiguousarray(tangent, dtype=np.float64)
+    _check(load().sv_program_jvp(_vp(ph), _dptr(t), _vp(out_ptr), int(on_device)))
 
 
 def sv_program_stats(ph: int):

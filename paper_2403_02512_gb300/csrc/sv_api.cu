@@ -1011,6 +1011,7 @@ struct Ops {
   decltype(&Launch<float>::set_basis) set_basis;
   decltype(&Launch<float>::copy) copy;
   decltype(&Launch<float>::stream_op) stream_op;
+  decltype(&Launch<float>::tile_tangent) tile_tangent;
   int amp_bytes, Tf, Ta, nlow_pref;
   int adj_bmax, adj_cps;  // lambdas per adjoint CTA (largest variant), adjoint CTAs per SM
 };
@@ -1019,7 +1020,7 @@ const Ops &ops_df() {
   static const Ops d = {Launch<df>::build_matrices, Launch<df>::tile_forward, Launch<df>::tile_adjoint,
                         Launch<df>::expval_pass,    Launch<df>::lambda_pass,  Launch<df>::dense_k,
                         Launch<df>::set_basis,      Launch<df>::copy,
-                        Launch<df>::stream_op,
+                        Launch<df>::stream_op, Launch<df>::tile_tangent,
                         16, Launch<df>::max_T_forward(), Launch<df>::max_T_adjoint(), 3,
                         Launch<df>::adj_lambdas_max(), Launch<df>::adj_ctas_per_sm()};
   return d;
@@ -1030,14 +1031,14 @@ const Ops &ops_for(sv_dtype dt) {
                           Launch<float>::tile_adjoint,   Launch<float>::expval_pass,
                           Launch<float>::lambda_pass,    Launch<float>::dense_k,
                           Launch<float>::set_basis,      Launch<float>::copy,
-                          Launch<float>::stream_op,
+                          Launch<float>::stream_op, Launch<float>::tile_tangent,
                           8, Launch<float>::max_T_forward(), Launch<float>::max_T_adjoint(), 4,
                           Launch<float>::adj_lambdas_max(), Launch<float>::adj_ctas_per_sm()};
   static const Ops f64 = {Launch<double>::build_matrices, Launch<double>::tile_forward,
                           Launch<double>::tile_adjoint,   Launch<double>::expval_pass,
                           Launch<double>::lambda_pass,    Launch<double>::dense_k,
                           Launch<double>::set_basis,      Launch<double>::copy,
-                          Launch<double>::stream_op,
+                          Launch<double>::stream_op, Launch<double>::tile_tangent,
                           16, Launch<double>::max_T_forward(), Launch<double>::max_T_adjoint(), 3,
                           Launch<double>::adj_lambdas_max(), Launch<double>::adj_ctas_per_sm()};
   return dt == SV_C64 ? f32 : f64;
@@ -1127,7 +1128,7 @@ struct sv_program {
   int n_slots = 0;
   size_t mats_entries = 0;
   // device pointers into `tables`
-  OpDev *d_fwd_ops = nullptr, *d_adj_ops = nullptr;
+  OpDev *d_fwd_ops = nullptr, *d_adj_ops = nullptr, *d_tan_ops = nullptr;
   uint64_t *d_aux = nullptr;  // phase-run member records of the forward plan
   MatSlot *d_slots = nullptr;
   void *d_mats = nullptr;
@@ -1152,6 +1153,10 @@ struct sv_program {
   int lam_per_cta = 1;               // lambdas sharing one phi tile in the adjoint kernel
   int cfg_compute = -1;              // compute mode the adjoint launch shape was made for
   bool want_lam = false;             // workspace holds lambda vectors without a sweep (variance)
+  bool want_tan = false;             // workspace holds the tangent vector and coefficients (JVP)
+  Plan tan;                          // forward plan of the expanded tape with trainable micro-ops (JVP)
+  std::vector<int> tan_pidx;         // tangent slot -> parameter
+  std::vector<double> tan_factor;    // tangent slot -> s_eff * scale (coefficient i * factor * tangent[p])
   int groups_a(int mcc) const { return (mcc + lam_per_cta - 1) / lam_per_cta; }
   int grid_a(int mcc) const {
     return (int)std::max<uint64_t>(1, std::min<uint64_t>(tiles_a, ctas_a / std::max(1, groups_a(mcc))));
@@ -1249,6 +1254,18 @@ sv_status build_program(sv_state *s, const sv_tape *tape, const sv_pauli_sum *ob
   if (sv_status st = check_plan(p->adj, n, K.nlow_pref)) {
     destroy_program(p);
     return st;
+  }
+  if (n_params > 0) {
+    p->tan = plan_passes(n, aops, K.Tf, K.nlow_pref, kMaxTrainPerPass, false, st_tab, false, false);
+    if (sv_status st = check_plan(p->tan, n, K.nlow_pref)) {
+      destroy_program(p);
+      return st;
+    }
+    for (int sidx = 0; sidx < p->tan.n_train; ++sidx) {
+      const HOp &e = aops[p->tan.train_hop[sidx]];
+      p->tan_pidx.push_back(e.pidx[0]);
+      p->tan_factor.push_back((e.adjoint ? -kind_gen_s(e.kind) : kind_gen_s(e.kind)) * e.scale);
+    }
   }
   std::vector<MatSlot> &slots = st_tab.slots;
   const size_t off = st_tab.entries;
@@ -1361,6 +1378,7 @@ sv_status build_program(sv_state *s, const sv_tape *tape, const sv_pauli_sum *ob
   auto sz = [](size_t count, size_t elem) { return align256(count * elem); };
   const size_t umat_doubles = umats ? (size_t)2 * (size_t)n_umat : 0;
   size_t total = sz(p->fwd.ops.size(), sizeof(OpDev)) + sz(p->adj.ops.size(), sizeof(OpDev)) +
+                 sz(p->tan.ops.size(), sizeof(OpDev)) +
                  sz(slots.size(), sizeof(MatSlot)) + sz(off, K.amp_bytes) + sz(std::max(n_params, 1), 8) +
                  sz(umat_doubles, 8) + sz(tdev.size(), sizeof(TermDev)) + sz(obs_begin.size(), 4) +
                  sz(term_order.size(), 4) + sz(ltdev.size(), sizeof(TermDev)) + sz(lbegin.size(), 4) +
@@ -1399,6 +1417,7 @@ sv_status build_program(sv_state *s, const sv_tape *tape, const sv_pauli_sum *ob
   };
   p->d_fwd_ops = (OpDev *)put(p->fwd.ops.data(), p->fwd.ops.size(), sizeof(OpDev));
   p->d_aux = (uint64_t *)put(p->fwd.aux.data(), p->fwd.aux.size(), 8);
+  p->d_tan_ops = (OpDev *)put(p->tan.ops.data(), p->tan.ops.size(), sizeof(OpDev));
   p->d_adj_ops = (OpDev *)put(p->adj.ops.data(), p->adj.ops.size(), sizeof(OpDev));
   p->d_slots = (MatSlot *)put(slots.data(), slots.size(), sizeof(MatSlot));
   p->d_mats = put(nullptr, 0, 1);
@@ -1553,6 +1572,7 @@ sv_status run_steps_forward(sv_program *p, void *psi) {
 struct JacWs {
   char *phiA, *phiB, *lam;
   double *partials, *contrib, *term_sums, *expvals, *J;
+  double2 *tan_coefs;  // JVP: complex coefficient per tangent slot
 };
 
 sv_status jac_workspace(sv_program *p, JacWs &w) {
@@ -1569,15 +1589,19 @@ sv_status jac_workspace(sv_program *p, JacWs &w) {
     if (mcc > 0) lam_rows = std::max(lam_rows, (size_t)p->grid_a(mcc) * mcc);
   size_t part = std::max(lam_rows * max_train, (size_t)p->grid_e * max_terms);
   if (p->want_lam) part = std::max(part, (size_t)p->mc * kNormBlocks);
-  const bool need_vec = p->adj.n_train > 0 || !p->adj.dk_ops.empty();  // phi buffers for a sweep
+  if (p->want_tan) part = std::max(part, (size_t)p->mc * kNormBlocks);
+  const bool need_vec = p->adj.n_train > 0 || !p->adj.dk_ops.empty() || p->want_tan;  // phi buffers / dpsi
   const bool need_lam = need_vec || p->want_lam;
-  const size_t bytes = (need_vec ? 2 * V : 0) + (need_lam ? (size_t)p->mc * V : 0) + align256(part * 8) +
+  const size_t tan_bytes = p->want_tan ? align256((size_t)std::max(1, p->tan.n_train) * 16) : 0;
+  const size_t bytes = tan_bytes + (need_vec ? 2 * V : 0) + (need_lam ? (size_t)p->mc * V : 0) + align256(part * 8) +
                        align256((size_t)std::max(1, p->adj.n_train) * std::max(1, p->m) * 8) +
                        align256(std::max<size_t>(1, p->terms.size()) * 8) + align256((size_t)std::max(1, p->m) * 8) +
                        align256((size_t)std::max(1, p->m) * std::max(1, p->n_params) * 8);
   char *base = nullptr;
   if (sv_status st = get_workspace(s, bytes, &base)) return st;
   size_t c = 0;
+  w.tan_coefs = (double2 *)(base + c);
+  c += tan_bytes;
   w.phiA = base + c;
   c += need_vec ? V : 0;
   w.phiB = base + c;
@@ -1750,6 +1774,66 @@ sv_status run_var(sv_program *p, const JacWs &w) {
     }
     if (sv_status r = after_launch(s, var_combine(w.partials, kNormBlocks, mcc, w.expvals, j0, w.J, s->stream),
                                    "variance combine"))
+      return r;
+    ++p->launches;
+  }
+  return SV_OK;
+}
+
+// Jacobian-vector product along `tangent` (forward mode): one tangent pass
+// from the state's current contents carries psi and dpsi (dpsi starts at 0);
+// then out_j = 2 Re <H_j psi | dpsi> from the lambda passes and FP64 dots.
+// Output in w.J[0..m); the state ends as the forward output.
+sv_status run_jvp(sv_program *p, const JacWs &w, const double *tangent) {
+  sv_state *s = p->s;
+  if (sv_status r = ensure_mats(p)) return r;
+  const Ops &K = ops_of(s);
+  std::vector<double2> coefs(std::max(1, p->tan.n_train));
+  for (int sidx = 0; sidx < p->tan.n_train; ++sidx) {
+    const int q = p->tan_pidx[sidx];
+    coefs[sidx] = make_double2(0.0, q >= 0 ? p->tan_factor[sidx] * tangent[q] : 0.0);  // i s scale tangent[q]
+  }
+  cudaError_t e = cudaMemcpyAsync(w.tan_coefs, coefs.data(), coefs.size() * sizeof(double2), cudaMemcpyHostToDevice,
+                                  s->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(w.phiA, 0, s->bytes, s->stream);
+  if (sv_status r = after_launch(s, e, "tangent setup")) return r;
+  for (const Step &st : p->tan.steps) {
+    if (st.dense_k) {
+      LaunchTimer t(s->stream, 6);
+      e = K.dense_k(s->psi, s->n, p->tan.dk_ops[st.index], p->d_mats, 0, s->stream);
+      if (e == cudaSuccess) e = K.dense_k(w.phiA, s->n, p->tan.dk_ops[st.index], p->d_mats, 0, s->stream);
+      p->launches += 2;
+    } else {
+      LaunchTimer t(s->stream, 0);
+      e = K.tile_tangent(s->psi, w.phiA, s->n, p->tan.passes[st.index], p->d_tan_ops, p->d_mats, w.tan_coefs,
+                         p->grid_f, s->stream);
+      ++p->launches;
+    }
+    if (sv_status r = after_launch(s, e, "tangent pass")) return r;
+  }
+  const int npass_e = (int)p->tp.passes.size();
+  for (int c = 0; c < p->n_chunks; ++c) {
+    const int j0 = c * p->mc, mcc = std::min(p->m, j0 + p->mc) - j0;
+    for (int q = 0; q < npass_e; ++q) {
+      const int32_t *begin = (const int32_t *)p->d_lam_begin + p->lam_begin_off[c * npass_e + q];
+      LaunchTimer t(s->stream, 3);
+      e = K.lambda_pass(s->psi, w.lam, s->n, p->tp.passes[q], p->d_lam_terms, begin, mcc, q == 0, p->grid_l(mcc),
+                        s->stream);
+      if (sv_status r = after_launch(s, e, "lambda pass")) return r;
+      ++p->launches;
+    }
+    if (npass_e == 0) {
+      if (sv_status r = after_launch(s, cudaMemsetAsync(w.lam, 0, (size_t)mcc * s->bytes, s->stream), "lambda"))
+        return r;
+    }
+    for (int j = 0; j < mcc; ++j) {
+      const void *lam = w.lam + (size_t)j * s->bytes;
+      e = s->dt == SV_C64 ? Launch<float>::dot_partials(lam, w.phiA, s->n, w.partials + (size_t)j * kNormBlocks, s->stream)
+                          : Launch<double>::dot_partials(lam, w.phiA, s->n, w.partials + (size_t)j * kNormBlocks, s->stream);
+      if (sv_status r = after_launch(s, e, "jvp dot")) return r;
+      ++p->launches;
+    }
+    if (sv_status r = after_launch(s, jvp_combine(w.partials, kNormBlocks, mcc, j0, w.J, s->stream), "jvp combine"))
       return r;
     ++p->launches;
   }
@@ -2540,6 +2624,26 @@ sv_status sv_program_vjp(sv_program *p, const double *grad_out, double *vjp_out,
   if (!st) st = run_vjp(p, w, grad_out);
   if (!st) st = copy_out(p->s, vjp_out, w.J, (size_t)p->n_params, outputs_on_device != 0);
   if (!st && !outputs_on_device) st = sync_state(p->s);
+  return st;
+}
+
+sv_status sv_program_jvp(sv_program *p, const double *tangent, double *jvp_out, int outputs_on_device) {
+  if (!p) return fail(SV_ERR_ARG, "program is NULL");
+  if (sv_status st = check_state(p->s)) return st;
+  if (sv_status st = require_params(p)) return st;
+  if (p->m < 1) return fail(SV_ERR_ARG, "the program has no observables");
+  if (!jvp_out || (p->n_params > 0 && !tangent)) return fail(SV_ERR_ARG, "NULL tangent / jvp_out");
+  for (int q = 0; q < p->n_params; ++q)
+    if (!std::isfinite(tangent[q])) return fail(SV_ERR_ARG, "tangent[%d] is not finite", q);
+  sv_state *s = p->s;
+  JacWs w;
+  p->launches = 0;
+  p->want_tan = true;
+  sv_status st = jac_workspace(p, w);
+  p->want_tan = false;
+  if (!st) st = run_jvp(p, w, tangent);
+  if (!st) st = copy_out(s, jvp_out, w.J, p->m, outputs_on_device != 0);
+  if (!st && !outputs_on_device) st = sync_state(s);
   return st;
 }
 

@@ -215,6 +215,11 @@ struct Launch {
   // Marginal-probability partials: partials[c] = sum of |psi_i|^2 over chunk c of 2^chunk_log
   // consecutive (bin, other) indices, bin = the bits at the wires (see ProbsDev).
   static cudaError_t probs_partials(const void *psi, const ProbsDev &pd, double *partials, cudaStream_t st);
+  // Tangent pass (forward-mode JVP): psi and dpsi through one pass; coefs[slot] complex.
+  static cudaError_t tile_tangent(void *psi, void *dpsi, int n, const PassDev &pass, const OpDev *ops,
+                                  const void *mats, const double2 *coefs, int grid, cudaStream_t st);
+  // kNormBlocks FP64 partials of Re <a|b> (fixed order).
+  static cudaError_t dot_partials(const void *a, const void *b, int n, double *partials, cudaStream_t st);
   // Bins of <= 2^kProbsSmallLog amplitudes: out[bin] directly, one thread per bin.
   static cudaError_t probs_small(const void *psi, const ProbsDev &pd, double *out, cudaStream_t st);
   // Persistent batch launch: `grid` CTAs drain the work items of all segments.
@@ -236,6 +241,8 @@ struct Launch {
 };
 
 // Batch: out[c.out] = sum_term coeff * sum_tile partials (fixed order), one thread per circuit.
+// out[j0 + j] = 2 sum_b partials[j * nb + b], j < m (Jacobian-vector products).
+cudaError_t jvp_combine(const double *partials, int nb, int m, int j0, double *out, cudaStream_t st);
 // out[j0 + j] = sum_b partials[j * nb + b] - E[j0 + j]^2, j < m (variances).
 cudaError_t var_combine(const double *partials, int nb, int m, const double *E, int j0, double *out, cudaStream_t st);
 cudaError_t batch_reduce(const BatchCircuit *circs, int n_circ, const ZTerm *terms, const double *partials,

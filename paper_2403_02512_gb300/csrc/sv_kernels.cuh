@@ -718,6 +718,145 @@ __global__ void __launch_bounds__(kBlock) k_tile_forward(g_t<R> *__restrict__ ps
 }
 
 // ---------------------------------------------------------------------------
+// Tangent pass (forward-mode Jacobian-vector product): psi and dpsi tiles go
+// through the pass's micro-ops together; a trainable micro-op (generator G on
+// its pair or diagonal) then adds coef[slot] * G psi_new to dpsi, with
+// coef = i s scale tangent[p] for U = exp(i s theta G).
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ c_t<R> tan_coef(const double2 *coefs, int slot) {
+  const double2 c = coefs[slot];
+  c_t<R> r;
+  r.x = (R)c.x;
+  r.y = (R)c.y;
+  return r;
+}
+
+template <typename R>
+__device__ void tan_pair(c_t<R> *sp, c_t<R> *sd, const TileGeom &tg, const OpDev &op, const c_t<R> *__restrict__ mats,
+                         const double2 *__restrict__ coefs) {
+  using C = c_t<R>;
+  C Mr[4];
+  if (op.code == mGen || op.code == mReal || op.code == mImOff)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) Mr[q] = mats[op.mat + q];
+  const bool tr = op.train >= 0 && op.slot >= 0 && (op.gcode == gX || op.gcode == gY);
+  C c;
+  c.x = R(0);
+  c.y = R(0);
+  if (tr) {
+    c = tan_coef<R>(coefs, op.slot);
+    const R gs = (R)op.gs;
+    c.x = c.x * gs;
+    c.y = c.y * gs;
+  }
+  const OpRegs o(op);
+  const uint32_t lcm = op.lcmask, lcv = op.lcval;
+  const int ng = tg.A >> o.k;
+  for (int g = threadIdx.x; g < ng; g += blockDim.x) {
+    const int l0 = o.base(g);
+    if (((uint32_t)l0 & lcm) != lcv) continue;
+    const int ia = l0 + o.oa, ib = l0 + o.ob;
+    C va = sp[ia], vb = sp[ib];
+    pair_apply<R>(op.code, Mr, va, vb);
+    sp[ia] = va;
+    sp[ib] = vb;
+    C da = sd[ia], db = sd[ib];
+    pair_apply<R>(op.code, Mr, da, db);
+    if (tr) {
+      C ga, gb;  // G psi on the pair: X -> (b, a), Y -> (-i b, i a)
+      if (op.gcode == gX) {
+        ga = vb;
+        gb = va;
+      } else {
+        ga.x = vb.y;
+        ga.y = -vb.x;
+        gb.x = -va.y;
+        gb.y = va.x;
+      }
+      const C ca = cmul(c, ga), cb = cmul(c, gb);
+      da.x = da.x + ca.x;
+      da.y = da.y + ca.y;
+      db.x = db.x + cb.x;
+      db.y = db.y + cb.y;
+    }
+    sd[ia] = da;
+    sd[ib] = db;
+  }
+}
+
+template <typename R>
+__device__ void tan_diag(c_t<R> *sp, c_t<R> *sd, const TileGeom &tg, const OpDev &op, const c_t<R> *__restrict__ mats,
+                         const double2 *__restrict__ coefs) {
+  using C = c_t<R>;
+  const DiagRegs<R> dr(op, mats);
+  const bool tr = op.train >= 0 && op.slot >= 0 && op.gcode == gDiag;
+  const C c = tr ? tan_coef<R>(coefs, op.slot) : C();
+  const R ga = (R)op.ga, gb = (R)op.gb;
+  for (int l = threadIdx.x; l < tg.A; l += blockDim.x) {
+    const uint64_t g = tg.gidx(l);
+    if ((g & dr.cmask) != dr.cval) continue;
+    const int idx = dr.index(op, g);
+    const C v = dr.mul(mats, idx, sp[l]);
+    sp[l] = v;
+    C d = dr.mul(mats, idx, sd[l]);
+    if (tr) {
+      const R gd = (__popc(idx & op.zmask) & 1) ? gb : ga;
+      const C cv = cmul(c, v);
+      d.x = d.x + gd * cv.x;
+      d.y = d.y + gd * cv.y;
+    }
+    sd[l] = d;
+  }
+}
+
+template <typename R, int MAXK>
+__global__ void __launch_bounds__(kBlock) k_tile_tangent(g_t<R> *__restrict__ psi, g_t<R> *__restrict__ dpsi, int n,
+                                                          const PassDev pass, const OpDev *__restrict__ ops,
+                                                          const c_t<R> *__restrict__ mats,
+                                                          const double2 *__restrict__ coefs) {
+  using C = c_t<R>;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int A = 1 << pass.T;
+  C *sp = reinterpret_cast<C *>(smem);
+  C *sd = sp + A;
+  uint64_t *lut = reinterpret_cast<uint64_t *>(sd + A);
+  build_lut(lut, pass);
+  TileGeom tg;
+  tg.T = pass.T;
+  tg.nlow = pass.nlow;
+  tg.A = A;
+  tg.lowmask = (1u << pass.nlow) - 1u;
+  tg.lut = lut;
+  __syncthreads();
+  const uint64_t ntiles = 1ull << (n - pass.T);
+  for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    tg.base = tile_base(pass, tile);
+    load_tile_async<R>(psi, sp, tg);
+    load_tile_async<R>(dpsi, sd, tg);
+    tile_async_wait();
+    tile_async_convert<R>(sp, 2 * A);
+    for (int o = pass.op_begin; o < pass.op_end; ++o) {
+      const OpDev &op = ops[o];
+      if (op.sync_prev && o > pass.op_begin) __syncthreads();
+      if (op.kind == kDense) {
+        dense_any<R, MAXK>(sp, tg, op, mats);
+        dense_any<R, MAXK>(sd, tg, op, mats);
+      } else if (op_active(op, tg.base)) {
+        if (op.kind == kPair)
+          tan_pair<R>(sp, sd, tg, op, mats, coefs);
+        else
+          tan_diag<R>(sp, sd, tg, op, mats, coefs);
+      }
+    }
+    __syncthreads();
+    store_tile<R>(psi, sp, tg);
+    store_tile<R>(dpsi, sd, tg);
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Adjoint pass kernel (S7).  For the pass's micro-ops in reverse order:
 //   acc[op, j] += Im <lambda_j | G phi>   (before the op is un-applied),
 //   phi <- E phi, lambda_j <- E lambda_j   (E = U^dagger, stored by the builder).
@@ -1678,6 +1817,21 @@ __global__ void __launch_bounds__(kBlock) k_norm_partials(const g_t<R> *__restri
       const g_t<R> a = __ldcs(psi + i);
       acc = fma(a.x, a.x, fma(a.y, a.y, acc));
     }
+  }
+  const double t = block_sum_fixed(acc, red);
+  if (threadIdx.x == 0) partials[blockIdx.x] = t;
+}
+
+// Jacobian-vector product: partials of Re <a|b> (kNormBlocks blocks, fixed order).
+template <typename R>
+__global__ void __launch_bounds__(kBlock) k_dot_partials(const g_t<R> *__restrict__ a, const g_t<R> *__restrict__ b,
+                                                         uint64_t N, double *__restrict__ partials) {
+  __shared__ double red[kBlock / 32];
+  double acc = 0.0;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < N; i += stride) {
+    const g_t<R> x = __ldcs(a + i), y = __ldcs(b + i);
+    acc += (double)x.x * (double)y.x + (double)x.y * (double)y.y;
   }
   const double t = block_sum_fixed(acc, red);
   if (threadIdx.x == 0) partials[blockIdx.x] = t;

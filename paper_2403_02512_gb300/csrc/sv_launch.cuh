@@ -194,6 +194,30 @@ cudaError_t Launch<R>::probs_partials(const void *psi, const ProbsDev &pd, doubl
 }
 
 template <typename R>
+cudaError_t Launch<R>::tile_tangent(void *psi, void *dpsi, int n, const PassDev &pass, const OpDev *ops,
+                                    const void *mats, const double2 *coefs, int grid, cudaStream_t st) {
+  static bool attr2 = false, attr4 = false;
+  const int smem = 2 * detail::tile_bytes(sizeof(c_t<R>), pass.T) + detail::lut_bytes(pass);
+  g_t<R> *p = reinterpret_cast<g_t<R> *>(psi), *d = reinterpret_cast<g_t<R> *>(dpsi);
+  const c_t<R> *m = reinterpret_cast<const c_t<R> *>(mats);
+  if (pass.max_k <= 2) {
+    detail::allow_big_smem(k_tile_tangent<R, 2>, attr2);
+    k_tile_tangent<R, 2><<<grid, kBlock, smem, st>>>(p, d, n, pass, ops, m, coefs);
+  } else {
+    detail::allow_big_smem(k_tile_tangent<R, 4>, attr4);
+    k_tile_tangent<R, 4><<<grid, kBlock, smem, st>>>(p, d, n, pass, ops, m, coefs);
+  }
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t Launch<R>::dot_partials(const void *a, const void *b, int n, double *partials, cudaStream_t st) {
+  k_dot_partials<R><<<kNormBlocks, kBlock, 0, st>>>(reinterpret_cast<const g_t<R> *>(a),
+                                                    reinterpret_cast<const g_t<R> *>(b), 1ull << n, partials);
+  return cudaGetLastError();
+}
+
+template <typename R>
 cudaError_t Launch<R>::probs_small(const void *psi, const ProbsDev &pd, double *out, cudaStream_t st) {
   const uint64_t bins = 1ull << pd.k;
   k_probs_small<R><<<(unsigned)((bins + kBlock - 1) / kBlock), kBlock, 0, st>>>(reinterpret_cast<const g_t<R> *>(psi),

@@ -176,6 +176,34 @@ class Program:
         L.sv_program_vjp(self.handle, g, out.data_ptr(), True)
         return out[: self.n_params]
 
+    def jvp(self, tangent, reset: bool = True) -> torch.Tensor:
+        """Forward-mode J @ tangent (one tangent pass from the basis state, or from
+        the current state if reset=False); the state ends as the forward output."""
+        t = np.ascontiguousarray(torch.as_tensor(tangent).detach().double().cpu().numpy().ravel())
+        if t.size != self.n_params:
+            raise ValueError(f"expected {self.n_params} tangent entries, got {t.size}")
+        out = torch.empty(max(1, self.m), dtype=torch.float64, device=self.sv.device)
+        self.sv.sync_stream()
+        if reset:
+            self.sv.reset(self.basis_state)
+        L.sv_program_jvp(self.handle, t, out.data_ptr(), True)
+        self.sv.generation += 1
+        self._forward_generation = self.sv.generation
+        return out[: self.m]
+
+    def jacobian_by_shape(self):
+        """(E, J) by whichever mode costs fewer passes: reverse mode (one adjoint
+        sweep per observable, `jacobian`) unless there are fewer parameters than
+        observables, then forward mode (one tangent pass per parameter)."""
+        if self.n_params >= self.m:
+            self.forward()
+            return self.jacobian()
+        J = torch.empty((self.m, self.n_params), dtype=torch.float64, device=self.sv.device)
+        eye = np.eye(self.n_params)
+        for q in range(self.n_params):
+            J[:, q] = self.jvp(eye[q])
+        return self.expval(), J
+
     def stats(self):
         return L.sv_program_stats(self.handle)
 

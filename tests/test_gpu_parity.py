@@ -495,3 +495,59 @@ def test_probabilities_and_samples_reject_bad_arguments():
             sv.sample([0], u)
         assert ei.value.status == 1
     assert sv.sample([0, 1], []).size == 0
+
+
+# ---- forward-mode Jacobian-vector products -----------------------------------
+def _jvp_cases():
+    c1, p1 = random_circuit(7, 60, 61, max_controls=2, shared_params=True)
+    c1 = Circuit(c1.n, c1.ops, c1.n_params, [random_hamiltonian(7, 10, np.random.default_rng(61), weights=(1, 2)),
+                                              [Term(1.0, ((3, "Z"),))]])
+    c2, p2 = random_circuit(13, 80, 62, max_controls=1)
+    c2 = Circuit(c2.n, c2.ops, c2.n_params, [[Term(0.5, ((0, "X"), (12, "Y")))], [Term(1.0, ((6, "Z"),))]])
+    c3, p3 = strongly_entangling(12, 2, seed=63)
+    c4, p4 = qaoa_maxcut(12, 2), np.random.default_rng(64).uniform(0, np.pi, 4)
+    return [(c1, p1), (c2, p2), (c3, p3), (c4, p4)]
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("case", range(4))
+def test_jvp_matches_oracle_forward_mode(dtype, case):
+    c, p = _jvp_cases()[case]
+    v = np.random.default_rng(70 + case).normal(size=c.n_params)
+    sv = StateVector(c.n, dtype)
+    prog = Program.from_circuit(sv, c)
+    prog.set_params(p)
+    got = prog.jvp(v).cpu().numpy()
+    want = oracle.jvp(c, p, v)
+    _assert_rel(got, want, TOL_J[dtype] * 10, "jvp")
+    # the state ends as the forward output; the reverse-mode Jacobian agrees
+    _assert_state(sv.to_numpy(), oracle.forward(c, p), dtype)
+    _, J = prog.jacobian()
+    _assert_rel(J.cpu().numpy() @ v, got, TOL_J[dtype] * 10, "J @ v")
+
+
+def test_jacobian_by_shape_uses_forward_mode_when_parameters_are_few():
+    n = 9
+    ops = [Op("RY", (w,), (w % 3,)) for w in range(n)] + [Op("PauliX", (w + 1,), controls=(w,)) for w in range(n - 1)]
+    obs = [[Term(1.0, ((w, "Z"),))] for w in range(n)]
+    c = Circuit(n, ops, 3, obs)
+    p = np.array([0.3, 1.2, 2.2])
+    sv = StateVector(n, "c128")
+    prog = Program.from_circuit(sv, c)
+    prog.set_params(p)
+    E, J = prog.jacobian_by_shape()  # 3 parameters < 9 observables: three tangent passes
+    Eo, Jo = oracle.adjoint_jacobian(c, p)
+    _assert_rel(E.cpu().numpy(), Eo, 1e-10, "expval")
+    _assert_rel(J.cpu().numpy(), Jo, 1e-9, "jacobian")
+
+
+def test_jvp_rejects_bad_tangents():
+    c, p = strongly_entangling(4, 1, seed=65)
+    sv = StateVector(4, "c128")
+    prog = Program.from_circuit(sv, c)
+    prog.set_params(p)
+    bad = np.zeros(c.n_params)
+    bad[2] = np.nan
+    with pytest.raises(L.SvError) as ei:
+        prog.jvp(bad)
+    assert ei.value.status == 1
