@@ -346,11 +346,13 @@ def extra_vqe():
 
 
 def extra_measurements(hbm_peak):
-    """Measurement processes on the sel24 output state: expectation values and
-    variances of the 24 single-Z observables, marginal probabilities of all 24
-    wires, 10^4 samples.  Algorithmic bytes: expval V; variance V + 2 m V
-    (lambda passes write m vectors, the norms read them); probabilities V;
-    samples V plus the 2^24-entry CDF."""
+    """Measurement processes on the sel24 output state: a forward-mode
+    Jacobian-vector product (one tangent pass plus the 24 dots), expectation
+    values and variances of the 24 single-Z observables, marginal probabilities
+    of all 24 wires, 10^4 samples.  Algorithmic bytes: JVP 2 x 2V per forward
+    pass (psi and d psi) + 2 m V; expval V; variance V + 2 m V (lambda passes
+    write m vectors, the norms read them); probabilities V; samples V plus the
+    2^24-entry CDF."""
     import torch
     from paper_2403_02512_gb300.torch_api import Program, StateVector
     from workloads import strongly_entangling
@@ -365,7 +367,10 @@ def extra_measurements(hbm_peak):
         prog.forward(p)
         V = (8 if dtype == "c64" else 16) << N_QUBITS
         res = {}
-        for name, fn, alg in (("expval", lambda: sv.expval(c.observables), V),
+        tangent = np.random.default_rng(8).normal(size=c.n_params)
+        prog.set_params(p)
+        for name, fn, alg in (("jvp_forward_mode", lambda: prog.jvp(tangent), 2 * 2 * V * prog.stats()[0] + 2 * m * V),
+                              ("expval", lambda: sv.expval(c.observables), V),
                               ("variance", lambda: sv.var(c.observables), V + 2 * m * V),
                               ("probs_all_wires", lambda: sv.probs(wires), V + 8 * (1 << N_QUBITS)),
                               ("sample_1e4_all_wires", lambda: sv.sample(wires, u), V + 3 * 8 * (1 << N_QUBITS))):
