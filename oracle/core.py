@@ -311,8 +311,27 @@ def apply_pauli_word(psi: np.ndarray, paulis) -> np.ndarray:
     return out
 
 
+class CSRObservable:
+    """A general sparse observable (the SparseHamiltonian of Sec. 2.2): row
+    pointers, column indices and complex values of a 2^n x 2^n matrix.
+    (H psi)_i = sum over the row's stored entries of value * psi[column]."""
+
+    def __init__(self, indptr, indices, values):
+        self.indptr = np.asarray(indptr, dtype=np.int64)
+        self.indices = np.asarray(indices, dtype=np.int64)
+        self.values = np.asarray(values, dtype=np.complex128)
+
+    def apply(self, psi: np.ndarray) -> np.ndarray:
+        rows = np.repeat(np.arange(self.indptr.size - 1), np.diff(self.indptr))
+        out = np.zeros_like(psi)
+        np.add.at(out, rows, self.values * psi[self.indices])
+        return out
+
+
 def apply_hamiltonian(psi: np.ndarray, terms) -> np.ndarray:
-    """out = sum_t c_t P_t psi."""
+    """out = sum_t c_t P_t psi (or H psi for a sparse observable)."""
+    if hasattr(terms, "apply"):
+        return terms.apply(psi)
     out = np.zeros_like(psi)
     for t in terms:
         axpy(out, apply_pauli_word(psi, t.paulis), t.coeff)
@@ -320,7 +339,10 @@ def apply_hamiltonian(psi: np.ndarray, terms) -> np.ndarray:
 
 
 def expval(psi: np.ndarray, terms) -> float:
-    """<psi|H|psi> = sum_t c_t <psi|P_t|psi> (each term's value is real)."""
+    """<psi|H|psi> = sum_t c_t <psi|P_t|psi> (each term's value is real); for a
+    sparse observable the real part of <psi|H psi>."""
+    if hasattr(terms, "apply"):
+        return inner(psi, terms.apply(psi)).real
     e = 0.0
     for t in terms:
         e += t.coeff * inner(psi, apply_pauli_word(psi, t.paulis)).real
