@@ -328,6 +328,29 @@ sv_status sv_program_vjp(sv_program *p, const double *grad_out, double *vjp_out,
  * parameters never set. */
 sv_status sv_program_jvp(sv_program *p, const double *tangent, double *jvp_out, int outputs_on_device);
 
+/* ---- sparse observables (NEXT-4) ----------------------------------------------
+ * A general sparse observable in CSR form (the SparseHamiltonian the paper's
+ * GPU device accepts for expectation values and the adjoint method, Sec. 2.2):
+ * indptr[0..2^n] (indptr[0] = 0, non-decreasing, indptr[2^n] = nnz), column
+ * indices[0..nnz) in [0, 2^n), values[0..2*nnz) complex (re, im) interleaved.
+ * sv_sparse_create validates and copies the arrays to the current device
+ * (one allocation; SV_ERR_ARG on a malformed matrix, SV_ERR_OOM).  The matrix
+ * is taken as given: Hermitian matrices give real expectation values. */
+typedef struct sv_sparse sv_sparse;
+sv_status sv_sparse_create(int n, const int64_t *indptr, const int64_t *indices, const double *values, int64_t nnz,
+                           sv_sparse **out);
+sv_status sv_sparse_destroy(sv_sparse *h);
+
+/* out = Re <psi|H psi> (one warp per row, FP64 sums in a fixed order). */
+sv_status sv_sparse_expval(sv_state *s, const sv_sparse *h, double *out);
+
+/* Adjoint Jacobian of <H> for a sparse H: the state holds psi = U(params)|.>
+ * (as for sv_adjoint_jacobian); lambda = H psi from the SpMV, then the usual
+ * reverse sweep.  expval_out (may be NULL): 1 double; jacobian_out:
+ * n_params doubles, host. */
+sv_status sv_adjoint_jacobian_sparse(sv_state *s, const sv_tape *tape, const double *params, const sv_sparse *h,
+                                     double *expval_out, double *jacobian_out);
+
 /* Kernel launches issued by the last program call (for launch accounting). */
 sv_status sv_program_stats(const sv_program *p, int *n_forward_passes, int *n_adjoint_passes,
                            int *launches_last_call);

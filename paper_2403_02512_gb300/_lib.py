@@ -119,6 +119,10 @@ PROTOTYPES = {
     "sv_program_expval": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
     "sv_program_vjp": (ctypes.c_int, [_vp, _dp, _vp, ctypes.c_int]),
     "sv_program_jvp": (ctypes.c_int, [_vp, _dp, _vp, ctypes.c_int]),
+    "sv_sparse_create": (ctypes.c_int, [ctypes.c_int, _vp, _vp, _dp, ctypes.c_int64, ctypes.POINTER(_vp)]),
+    "sv_sparse_destroy": (ctypes.c_int, [_vp]),
+    "sv_sparse_expval": (ctypes.c_int, [_vp, _vp, _dp]),
+    "sv_adjoint_jacobian_sparse": (ctypes.c_int, [_vp, ctypes.POINTER(SvTape), _dp, _vp, _dp, _dp]),
     "sv_program_stats": (ctypes.c_int, [_vp, _ip, _ip, _ip]),
     "sv_plan_query": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(SvTape), _ip, _ip]),
     "sv_kernel_timing_enable": (ctypes.c_int, [ctypes.c_int]),
@@ -363,6 +367,46 @@ def sv_program_vjp(ph: int, grad_out: np.ndarray, vjp_ptr: int, on_device: bool)
 def sv_program_jvp(ph: int, tangent: np.ndarray, out_ptr: int, on_device: bool) -> None:
     t = np.ascontiguousarray(tangent, dtype=np.float64)
     _check(load().sv_program_jvp(_vp(ph), _dptr(t), _vp(out_ptr), int(on_device)))
+
+
+class Sparse:
+    """A CSR observable on the device (sv_sparse_create / sv_sparse_destroy)."""
+
+    def __init__(self, n: int, indptr, indices, values):
+        self.n = int(n)
+        ip = np.ascontiguousarray(indptr, dtype=np.int64)
+        ix = np.ascontiguousarray(indices, dtype=np.int64)
+        v = np.ascontiguousarray(np.asarray(values, dtype=np.complex128).view(np.float64))
+        h = _vp()
+        _check(load().sv_sparse_create(self.n, ip.ctypes.data, ix.ctypes.data if ix.size else None,
+                                       _dptr(v) if v.size else None, ix.size, ctypes.byref(h)))
+        self.handle = h.value
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            load().sv_sparse_destroy(_vp(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def sv_sparse_expval(h: int, sp: Sparse) -> float:
+    out = np.zeros(1)
+    _check(load().sv_sparse_expval(_vp(h), _vp(sp.handle), _dptr(out)))
+    return float(out[0])
+
+
+def sv_adjoint_jacobian_sparse(h: int, tape: "Tape", params, sp: Sparse):
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    e = np.zeros(1)
+    J = np.zeros(max(1, tape.n_params))
+    _check(load().sv_adjoint_jacobian_sparse(_vp(h), ctypes.byref(tape.struct), _dptr(p) if p.size else None,
+                                             _vp(sp.handle), _dptr(e), _dptr(J)))
+    return float(e[0]), J[: tape.n_params]
 
 
 def sv_program_stats(ph: int):

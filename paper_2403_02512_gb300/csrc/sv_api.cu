@@ -1653,12 +1653,12 @@ sv_status run_expval(sv_program *p, const void *psi, const JacWs &w) {
 // term ranges of expectation pass q in lam_terms.
 template <typename BeginFn>
 sv_status run_sweep(sv_program *p, const JacWs &w, int mcc, int j0, int ldc, const TermDev *lam_terms,
-                    BeginFn lam_begin) {
+                    BeginFn lam_begin, bool lam_ready = false) {
   sv_state *s = p->s;
   const Ops &K = ops_of(s);
   const int n = s->n;
   const size_t V = s->bytes;
-  const int npass_e = (int)p->tp.passes.size();
+  const int npass_e = lam_ready ? 0 : (int)p->tp.passes.size();  // lam_ready: lambdas already in w.lam
   for (int q = 0; q < npass_e; ++q) {
     cudaError_t e;
     {
@@ -2483,6 +2483,128 @@ sv_status sv_sample(sv_state *s, const int *wires, int k, const double *uniforms
   e = cudaMemcpyAsync(out, dout, (size_t)shots * 8, cudaMemcpyDeviceToHost, s->stream);
   if (e != cudaSuccess) return cuda_fail(e, "copying samples");
   return sync_state(s);
+}
+
+// ---- sparse observables ----------------------------------------------------------
+struct sv_sparse {
+  int n = 0;
+  int64_t nnz = 0;
+  void *mem = nullptr;
+  size_t bytes = 0;
+  SparseDev dev;
+};
+
+sv_status sv_sparse_create(int n, const int64_t *indptr, const int64_t *indices, const double *values, int64_t nnz,
+                           sv_sparse **out) {
+  if (!out) return fail(SV_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (n < 1 || n > SV_MAX_QUBITS) return fail(SV_ERR_ARG, "n = %d outside [1, %d]", n, SV_MAX_QUBITS);
+  if (nnz < 0) return fail(SV_ERR_ARG, "nnz < 0");
+  if (!indptr || (nnz > 0 && (!indices || !values))) return fail(SV_ERR_ARG, "NULL CSR arrays");
+  const int64_t rows = 1ll << n;
+  if (indptr[0] != 0 || indptr[rows] != nnz) return fail(SV_ERR_ARG, "indptr must run from 0 to nnz");
+  for (int64_t r = 0; r < rows; ++r)
+    if (indptr[r + 1] < indptr[r]) return fail(SV_ERR_ARG, "indptr decreases at row %lld", (long long)r);
+  for (int64_t k = 0; k < nnz; ++k) {
+    if (indices[k] < 0 || indices[k] >= rows) return fail(SV_ERR_ARG, "column index %lld out of range", (long long)k);
+    if (!std::isfinite(values[2 * k]) || !std::isfinite(values[2 * k + 1]))
+      return fail(SV_ERR_ARG, "value %lld is not finite", (long long)k);
+  }
+  sv_sparse *h = new sv_sparse();
+  h->n = n;
+  h->nnz = nnz;
+  const size_t b_ptr = align256((size_t)(rows + 1) * 8), b_idx = align256((size_t)std::max<int64_t>(nnz, 1) * 8);
+  const size_t b_val = align256((size_t)std::max<int64_t>(nnz, 1) * 16);
+  h->bytes = b_ptr + b_idx + b_val;
+  if (sv_status st = dev_alloc(&h->mem, h->bytes)) {
+    delete h;
+    return st;
+  }
+  char *base = (char *)h->mem;
+  cudaError_t e = cudaMemcpy(base, indptr, (size_t)(rows + 1) * 8, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && nnz > 0) e = cudaMemcpy(base + b_ptr, indices, (size_t)nnz * 8, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && nnz > 0) e = cudaMemcpy(base + b_ptr + b_idx, values, (size_t)nnz * 16, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    dev_free(h->mem, h->bytes);
+    delete h;
+    return cuda_fail(e, "sv_sparse_create");
+  }
+  h->dev.n = n;
+  h->dev.indptr = (const int64_t *)base;
+  h->dev.indices = (const int64_t *)(base + b_ptr);
+  h->dev.vals = (const double2 *)(base + b_ptr + b_idx);
+  *out = h;
+  return SV_OK;
+}
+
+sv_status sv_sparse_destroy(sv_sparse *h) {
+  if (!h) return SV_OK;
+  cudaDeviceSynchronize();
+  dev_free(h->mem, h->bytes);
+  delete h;
+  return SV_OK;
+}
+
+namespace {
+sv_status sparse_expval_device(sv_state *s, const sv_sparse *h, double *partials, double *dev_out) {
+  cudaError_t e = s->dt == SV_C64 ? Launch<float>::csr_expval_partials(s->psi, h->dev, partials, s->stream)
+                                  : Launch<double>::csr_expval_partials(s->psi, h->dev, partials, s->stream);
+  if (e == cudaSuccess) e = probs_combine(partials, 1, kNormBlocks, dev_out, s->stream);  // fixed-order sum
+  return after_launch(s, e, "sparse expval");
+}
+}  // namespace
+
+sv_status sv_sparse_expval(sv_state *s, const sv_sparse *h, double *out) {
+  if (sv_status st = check_state(s)) return st;
+  if (!h || !out) return fail(SV_ERR_ARG, "NULL sparse observable / out");
+  if (h->n != s->n) return fail(SV_ERR_ARG, "sparse observable on %d qubits, state on %d", h->n, s->n);
+  char *base = nullptr;
+  if (sv_status st = get_workspace(s, align256(kNormBlocks * 8) + 256, &base)) return st;
+  double *partials = (double *)base, *dv = (double *)(base + align256(kNormBlocks * 8));
+  sv_status st = sparse_expval_device(s, h, partials, dv);
+  if (!st) st = copy_out(s, out, dv, 1, false);
+  if (!st) st = sync_state(s);
+  return st;
+}
+
+sv_status sv_adjoint_jacobian_sparse(sv_state *s, const sv_tape *tape, const double *params, const sv_sparse *h,
+                                     double *expval_out, double *jacobian_out) {
+  if (sv_status st = check_state(s)) return st;
+  if (!tape || !h) return fail(SV_ERR_ARG, "NULL tape / sparse observable");
+  if (h->n != s->n) return fail(SV_ERR_ARG, "sparse observable on %d qubits, state on %d", h->n, s->n);
+  if (tape->n_params > 0 && !jacobian_out) return fail(SV_ERR_ARG, "jacobian_out is NULL");
+  // the program's one observable is a placeholder: lambda = H psi comes from the SpMV
+  const double one = 1.0;
+  const uint64_t zero = 0;
+  sv_pauli_sum placeholder = {1, &one, &zero, &zero};
+  sv_program *p = nullptr;
+  if (sv_status st = build_program(s, tape, &placeholder, 1, params, true, &p)) return st;
+  JacWs w;
+  sv_status st = program_set_params(p, params, 0);
+  if (!st) st = jac_workspace(p, w);
+  if (!st) st = ensure_mats(p);
+  if (!st) st = sparse_expval_device(s, h, w.partials, w.expvals);
+  if (!st && needs_sweep(p)) {  // the workspace holds lambda only when there is a sweep
+    const cudaError_t e = s->dt == SV_C64 ? Launch<float>::csr_spmv(s->psi, h->dev, w.lam, s->stream)
+                                          : Launch<double>::csr_spmv(s->psi, h->dev, w.lam, s->stream);
+    st = after_launch(s, e, "sparse lambda");
+    auto begin = [&](int) { return (const int32_t *)nullptr; };
+    if (!st) st = run_sweep(p, w, 1, 0, 1, p->d_lam_terms, begin, true);
+  }
+  if (!st) {
+    cudaError_t e;
+    if (p->adj.n_train > 0 && p->n_params > 0)
+      e = assemble_jacobian(w.contrib, p->d_coef, p->d_pbegin, p->d_pslots, p->n_params, 1, 0, p->n_params, w.J,
+                            s->stream);
+    else
+      e = cudaMemsetAsync(w.J, 0, (size_t)std::max(1, p->n_params) * 8, s->stream);
+    st = after_launch(s, e, "assemble jacobian");
+  }
+  if (!st) st = copy_out(s, expval_out, w.expvals, 1, false);
+  if (!st) st = copy_out(s, jacobian_out, w.J, (size_t)tape->n_params, false);
+  if (!st) st = sync_state(s);
+  destroy_program(p);
+  return st;
 }
 
 sv_status sv_norm2(sv_state *s, double *out) {

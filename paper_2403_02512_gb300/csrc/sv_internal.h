@@ -141,6 +141,15 @@ struct StreamDev {
   int32_t pair16;         // complex64 pair on bit 0 alone: both members in one 16-byte access
 };
 
+// A sparse observable in device memory (CSR, 2^n rows, complex FP64 values).
+struct SparseDev {
+  int32_t n;
+  int32_t pad;
+  const int64_t *indptr;   // 2^n + 1
+  const int64_t *indices;  // nnz
+  const double2 *vals;     // nnz
+};
+
 // Marginal probabilities of k wires: enumeration index j = bin * 2^(n-k) + other,
 // amplitude index = `other` with zeros inserted at the wires' bits (ascending
 // pos) or-ed with bin's bits placed at bitpos[0..k) (bitpos[0] = most
@@ -220,6 +229,9 @@ struct Launch {
                                   const void *mats, const double2 *coefs, int grid, cudaStream_t st);
   // kNormBlocks FP64 partials of Re <a|b> (fixed order).
   static cudaError_t dot_partials(const void *a, const void *b, int n, double *partials, cudaStream_t st);
+  // Sparse (CSR) observable, 2^n rows: lambda = H psi, or kNormBlocks partials of Re <psi|H psi>.
+  static cudaError_t csr_spmv(const void *psi, const SparseDev &h, void *out, cudaStream_t st);
+  static cudaError_t csr_expval_partials(const void *psi, const SparseDev &h, double *partials, cudaStream_t st);
   // Bins of <= 2^kProbsSmallLog amplitudes: out[bin] directly, one thread per bin.
   static cudaError_t probs_small(const void *psi, const ProbsDev &pd, double *out, cudaStream_t st);
   // Persistent batch launch: `grid` CTAs drain the work items of all segments.

@@ -1837,6 +1837,67 @@ __global__ void __launch_bounds__(kBlock) k_dot_partials(const g_t<R> *__restric
   if (threadIdx.x == 0) partials[blockIdx.x] = t;
 }
 
+// Sparse observable rows: one warp per row (rows strided over all warps of a
+// fixed grid); lanes stride the row's stored entries, FP64 complex sums, a
+// fixed shuffle tree.  The result is valid in lane 0.
+template <typename R>
+__device__ __forceinline__ double2 csr_row(const g_t<R> *__restrict__ psi, const SparseDev &h, int64_t row, int lane) {
+  double yr = 0.0, yi = 0.0;
+  const int64_t e = __ldg(h.indptr + row + 1);
+  for (int64_t k = __ldg(h.indptr + row) + lane; k < e; k += 32) {
+    const double2 v = __ldg(h.vals + k);
+    const g_t<R> x = psi[__ldg(h.indices + k)];
+    yr += v.x * (double)x.x - v.y * (double)x.y;
+    yi += v.x * (double)x.y + v.y * (double)x.x;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    yr += __shfl_down_sync(0xffffffffu, yr, o);
+    yi += __shfl_down_sync(0xffffffffu, yi, o);
+  }
+  return make_double2(yr, yi);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kBlock) k_csr_spmv(const g_t<R> *__restrict__ psi, const SparseDev h,
+                                                     g_t<R> *__restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int64_t rows = 1ll << h.n;
+  for (int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < rows; row += warps) {
+    const double2 y = csr_row<R>(psi, h, row, lane);
+    if (lane == 0) {
+      g_t<R> v;
+      v.x = y.x;
+      v.y = y.y;
+      out[row] = v;
+    }
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kBlock) k_csr_expval_partials(const g_t<R> *__restrict__ psi, const SparseDev h,
+                                                                double *__restrict__ partials) {
+  __shared__ double red[kBlock / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int64_t rows = 1ll << h.n;
+  double acc = 0.0;  // lane 0: sum over this warp's rows of Re(conj(psi_row) (H psi)_row)
+  for (int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; row < rows; row += warps) {
+    const double2 y = csr_row<R>(psi, h, row, lane);
+    if (lane == 0) {
+      const g_t<R> x = psi[row];
+      acc += (double)x.x * y.x + (double)x.y * y.y;
+    }
+  }
+  if (lane == 0) red[warp] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    partials[blockIdx.x] = t;
+  }
+}
+
 template <typename R>
 __global__ void __launch_bounds__(kBlock) k_norm_scale(g_t<R> *__restrict__ psi, uint64_t N,
                                                        const double *__restrict__ partials, int nb) {

@@ -218,6 +218,18 @@ cudaError_t Launch<R>::dot_partials(const void *a, const void *b, int n, double 
 }
 
 template <typename R>
+cudaError_t Launch<R>::csr_spmv(const void *psi, const SparseDev &h, void *out, cudaStream_t st) {
+  k_csr_spmv<R><<<kNormBlocks, kBlock, 0, st>>>(reinterpret_cast<const g_t<R> *>(psi), h, reinterpret_cast<g_t<R> *>(out));
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t Launch<R>::csr_expval_partials(const void *psi, const SparseDev &h, double *partials, cudaStream_t st) {
+  k_csr_expval_partials<R><<<kNormBlocks, kBlock, 0, st>>>(reinterpret_cast<const g_t<R> *>(psi), h, partials);
+  return cudaGetLastError();
+}
+
+template <typename R>
 cudaError_t Launch<R>::probs_small(const void *psi, const ProbsDev &pd, double *out, cudaStream_t st) {
   const uint64_t bins = 1ull << pd.k;
   k_probs_small<R><<<(unsigned)((bins + kBlock - 1) / kBlock), kBlock, 0, st>>>(reinterpret_cast<const g_t<R> *>(psi),
