@@ -354,6 +354,7 @@ def extra_measurements(hbm_peak):
     write m vectors, the norms read them); probabilities V; samples V plus the
     2^24-entry CDF."""
     import torch
+    from paper_2403_02512_gb300 import _lib as L
     from paper_2403_02512_gb300.torch_api import Program, StateVector
     from workloads import strongly_entangling
     c, p = strongly_entangling(N_QUBITS, LAYERS)
@@ -382,6 +383,23 @@ def extra_measurements(hbm_peak):
                 fn()
             ms = (time.perf_counter() - t0) / reps * 1e3
             res[name] = {"ms": ms, "frac_of_hbm": alg / ms / 1e6 / hbm_peak}
+        # sparse observable: 8 stored entries per row (the diagonal plus 7 seeded columns)
+        rows = 1 << N_QUBITS
+        rng = np.random.default_rng(9)
+        cols = np.concatenate([np.arange(rows)[:, None], rng.integers(0, rows, (rows, 7))], axis=1)
+        cols.sort(axis=1)
+        vals = rng.normal(size=cols.shape) + 1j * rng.normal(size=cols.shape)
+        sp = L.Sparse(N_QUBITS, np.arange(0, 8 * rows + 1, 8), cols.ravel(), vals.ravel())
+        alg_sp = 8 * (rows + 1) + 24 * 8 * rows + V + 8 * V  # CSR arrays, psi rows, gathered columns
+        L.sv_sparse_expval(sv.handle, sp)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(3):
+            L.sv_sparse_expval(sv.handle, sp)
+        ms = (time.perf_counter() - t0) / 3 * 1e3
+        res["sparse_expval_8_per_row"] = {"ms": ms, "frac_of_hbm": alg_sp / ms / 1e6 / hbm_peak}
+        sp.close()
+        del cols, vals
         out[dtype] = res
         prog.close()
         sv.close()
