@@ -373,7 +373,7 @@ def extra_measurements(hbm_peak):
         for name, fn, alg in (("jvp_forward_mode", lambda: prog.jvp(tangent), 2 * 2 * V * prog.stats()[0] + 2 * m * V),
                               ("expval", lambda: sv.expval(c.observables), V),
                               ("variance", lambda: sv.var(c.observables), V + 2 * m * V),
-                              ("probs_all_wires", lambda: sv.probs(wires), V + 8 * (1 << N_QUBITS)),
+                              ("probs_all_wires_to_host", lambda: sv.probs(wires), V + 8 * (1 << N_QUBITS)),
                               ("sample_1e4_all_wires", lambda: sv.sample(wires, u), V + 3 * 8 * (1 << N_QUBITS))):
             fn()
             torch.cuda.synchronize()
@@ -381,6 +381,7 @@ def extra_measurements(hbm_peak):
             reps = 3
             for _ in range(reps):
                 fn()
+            torch.cuda.synchronize()  # the JVP leaves its output on the device
             ms = (time.perf_counter() - t0) / reps * 1e3
             res[name] = {"ms": ms, "frac_of_hbm": alg / ms / 1e6 / hbm_peak}
         # sparse observable: 8 stored entries per row (the diagonal plus 7 seeded columns)

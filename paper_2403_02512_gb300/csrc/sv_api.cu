@@ -2530,6 +2530,7 @@ sv_status sv_sparse_create(int n, const int64_t *indptr, const int64_t *indices,
     return cuda_fail(e, "sv_sparse_create");
   }
   h->dev.n = n;
+  h->dev.nnz_per_row = (double)nnz / (double)rows;
   h->dev.indptr = (const int64_t *)base;
   h->dev.indices = (const int64_t *)(base + b_ptr);
   h->dev.vals = (const double2 *)(base + b_ptr + b_idx);

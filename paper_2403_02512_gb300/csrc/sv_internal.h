@@ -145,6 +145,7 @@ struct StreamDev {
 struct SparseDev {
   int32_t n;
   int32_t pad;
+  double nnz_per_row;      // mean stored entries per row (selects the lanes per row)
   const int64_t *indptr;   // 2^n + 1
   const int64_t *indices;  // nnz
   const double2 *vals;     // nnz

@@ -1837,35 +1837,43 @@ __global__ void __launch_bounds__(kBlock) k_dot_partials(const g_t<R> *__restric
   if (threadIdx.x == 0) partials[blockIdx.x] = t;
 }
 
-// Sparse observable rows: one warp per row (rows strided over all warps of a
-// fixed grid); lanes stride the row's stored entries, FP64 complex sums, a
-// fixed shuffle tree.  The result is valid in lane 0.
-template <typename R>
-__device__ __forceinline__ double2 csr_row(const g_t<R> *__restrict__ psi, const SparseDev &h, int64_t row, int lane) {
+// Sparse observable rows: a group of G lanes per row (G a power of two near
+// the mean row length; rows strided over all groups of a fixed grid); lanes
+// stride the row's stored entries, FP64 complex sums, a fixed shuffle tree
+// within the group.  The result is valid in the group's first lane.
+template <typename R, int G>
+__device__ __forceinline__ double2 csr_row(const g_t<R> *__restrict__ psi, const SparseDev &h, int64_t row, int gl,
+                                           bool active) {
   double yr = 0.0, yi = 0.0;
-  const int64_t e = __ldg(h.indptr + row + 1);
-  for (int64_t k = __ldg(h.indptr + row) + lane; k < e; k += 32) {
+  const int64_t e = active ? __ldg(h.indptr + row + 1) : 0;
+  for (int64_t k = active ? __ldg(h.indptr + row) + gl : 0; k < e; k += G) {
     const double2 v = __ldg(h.vals + k);
     const g_t<R> x = psi[__ldg(h.indices + k)];
     yr += v.x * (double)x.x - v.y * (double)x.y;
     yi += v.x * (double)x.y + v.y * (double)x.x;
   }
-  for (int o = 16; o > 0; o >>= 1) {
-    yr += __shfl_down_sync(0xffffffffu, yr, o);
-    yi += __shfl_down_sync(0xffffffffu, yi, o);
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) {
+    yr += __shfl_down_sync(0xffffffffu, yr, o, G);
+    yi += __shfl_down_sync(0xffffffffu, yi, o, G);
   }
   return make_double2(yr, yi);
 }
 
-template <typename R>
+template <typename R, int G>
 __global__ void __launch_bounds__(kBlock) k_csr_spmv(const g_t<R> *__restrict__ psi, const SparseDev h,
                                                      g_t<R> *__restrict__ out) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int gl = threadIdx.x & (G - 1);
+  const int64_t groups = (int64_t)gridDim.x * (blockDim.x / G);
   const int64_t rows = 1ll << h.n;
-  for (int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < rows; row += warps) {
-    const double2 y = csr_row<R>(psi, h, row, lane);
-    if (lane == 0) {
+  const int64_t first = (int64_t)blockIdx.x * (blockDim.x / G) + threadIdx.x / G;
+  // every lane of a warp runs the same number of iterations (shuffles need the whole warp)
+  const int64_t iters = (rows + groups - 1) / groups;
+  for (int64_t it = 0; it < iters; ++it) {
+    const int64_t row = first + it * groups;
+    const bool ok = row < rows;
+    const double2 y = csr_row<R, G>(psi, h, row, gl, ok);  // groups past the last row sum nothing
+    if (ok && gl == 0) {
       g_t<R> v;
       v.x = y.x;
       v.y = y.y;
@@ -1874,26 +1882,30 @@ __global__ void __launch_bounds__(kBlock) k_csr_spmv(const g_t<R> *__restrict__ 
   }
 }
 
-template <typename R>
+template <typename R, int G>
 __global__ void __launch_bounds__(kBlock) k_csr_expval_partials(const g_t<R> *__restrict__ psi, const SparseDev h,
                                                                 double *__restrict__ partials) {
-  __shared__ double red[kBlock / 32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  __shared__ double red[kBlock];
+  const int gl = threadIdx.x & (G - 1);
+  const int64_t groups = (int64_t)gridDim.x * (blockDim.x / G);
   const int64_t rows = 1ll << h.n;
-  double acc = 0.0;  // lane 0: sum over this warp's rows of Re(conj(psi_row) (H psi)_row)
-  for (int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; row < rows; row += warps) {
-    const double2 y = csr_row<R>(psi, h, row, lane);
-    if (lane == 0) {
+  const int64_t first = (int64_t)blockIdx.x * (blockDim.x / G) + threadIdx.x / G;
+  const int64_t iters = (rows + groups - 1) / groups;
+  double acc = 0.0;  // group leader: sum over the group's rows of Re(conj(psi_row) (H psi)_row)
+  for (int64_t it = 0; it < iters; ++it) {
+    const int64_t row = first + it * groups;
+    const bool ok = row < rows;
+    const double2 y = csr_row<R, G>(psi, h, row, gl, ok);
+    if (ok && gl == 0) {
       const g_t<R> x = psi[row];
       acc += (double)x.x * y.x + (double)x.y * y.y;
     }
   }
-  if (lane == 0) red[warp] = acc;
+  red[threadIdx.x] = gl == 0 ? acc : 0.0;
   __syncthreads();
   if (threadIdx.x == 0) {
     double t = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    for (int i = 0; i < (int)blockDim.x; i += G) t += red[i];
     partials[blockIdx.x] = t;
   }
 }

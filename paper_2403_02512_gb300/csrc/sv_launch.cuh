@@ -217,15 +217,42 @@ cudaError_t Launch<R>::dot_partials(const void *a, const void *b, int n, double 
   return cudaGetLastError();
 }
 
+namespace detail {
+// Lanes per sparse row: the power of two >= the mean row length, 1..32.
+inline int csr_group(const SparseDev &h) {
+  const double mean = h.nnz_per_row;
+  int g = 1;
+  while (g < 32 && g < mean) g <<= 1;
+  return g;
+}
+}  // namespace detail
+
 template <typename R>
 cudaError_t Launch<R>::csr_spmv(const void *psi, const SparseDev &h, void *out, cudaStream_t st) {
-  k_csr_spmv<R><<<kNormBlocks, kBlock, 0, st>>>(reinterpret_cast<const g_t<R> *>(psi), h, reinterpret_cast<g_t<R> *>(out));
+  const g_t<R> *p = reinterpret_cast<const g_t<R> *>(psi);
+  g_t<R> *o = reinterpret_cast<g_t<R> *>(out);
+  switch (detail::csr_group(h)) {
+    case 1: k_csr_spmv<R, 1><<<kNormBlocks, kBlock, 0, st>>>(p, h, o); break;
+    case 2: k_csr_spmv<R, 2><<<kNormBlocks, kBlock, 0, st>>>(p, h, o); break;
+    case 4: k_csr_spmv<R, 4><<<kNormBlocks, kBlock, 0, st>>>(p, h, o); break;
+    case 8: k_csr_spmv<R, 8><<<kNormBlocks, kBlock, 0, st>>>(p, h, o); break;
+    case 16: k_csr_spmv<R, 16><<<kNormBlocks, kBlock, 0, st>>>(p, h, o); break;
+    default: k_csr_spmv<R, 32><<<kNormBlocks, kBlock, 0, st>>>(p, h, o); break;
+  }
   return cudaGetLastError();
 }
 
 template <typename R>
 cudaError_t Launch<R>::csr_expval_partials(const void *psi, const SparseDev &h, double *partials, cudaStream_t st) {
-  k_csr_expval_partials<R><<<kNormBlocks, kBlock, 0, st>>>(reinterpret_cast<const g_t<R> *>(psi), h, partials);
+  const g_t<R> *p = reinterpret_cast<const g_t<R> *>(psi);
+  switch (detail::csr_group(h)) {
+    case 1: k_csr_expval_partials<R, 1><<<kNormBlocks, kBlock, 0, st>>>(p, h, partials); break;
+    case 2: k_csr_expval_partials<R, 2><<<kNormBlocks, kBlock, 0, st>>>(p, h, partials); break;
+    case 4: k_csr_expval_partials<R, 4><<<kNormBlocks, kBlock, 0, st>>>(p, h, partials); break;
+    case 8: k_csr_expval_partials<R, 8><<<kNormBlocks, kBlock, 0, st>>>(p, h, partials); break;
+    case 16: k_csr_expval_partials<R, 16><<<kNormBlocks, kBlock, 0, st>>>(p, h, partials); break;
+    default: k_csr_expval_partials<R, 32><<<kNormBlocks, kBlock, 0, st>>>(p, h, partials); break;
+  }
   return cudaGetLastError();
 }
 
