@@ -774,8 +774,55 @@ void lower_fused(int n, const std::vector<HOp> &ops, const std::vector<int> &mem
 // is read as runs of >= 2^nlow_pref consecutive amplitudes (coalesced, and
 // 16-byte aligned for the paired complex64 accesses).  Each pass is then
 // lowered into micro-ops; dagger selects the adjoint sweep's U^dagger blocks.
+// Consecutive uncontrolled, untrained single-wire pair micro-ops of one pass on
+// distinct local bits become kMulti micro-ops of up to 3 members.
+void merge_multi(std::vector<OpDev> &ops, size_t begin) {
+  std::vector<OpDev> out(ops.begin(), ops.begin() + begin);
+  std::vector<OpDev> pend;
+  auto mergeable = [](const OpDev &o) {
+    return o.kind == kPair && o.k == 1 && o.cmask == 0 && o.train < 0 && o.gcode == gNone;
+  };
+  auto emit = [&]() {
+    if (pend.size() == 1) out.push_back(pend[0]);
+    if (pend.size() >= 2) {
+      OpDev m;
+      memset(&m, 0, sizeof(m));
+      m.kind = kMulti;
+      m.k = (int8_t)pend.size();
+      m.train = -1;
+      m.slot = -1;
+      m.sync_prev = 1;
+      int bits[3];
+      for (size_t j = 0; j < pend.size(); ++j) {
+        m.tl[j] = pend[j].tl[0];
+        m.mcode[j] = pend[j].code;
+        m.mmat[j] = pend[j].mat;
+        bits[j] = pend[j].tl[0];
+      }
+      std::sort(bits, bits + pend.size());
+      for (size_t j = 0; j < pend.size(); ++j) m.ts[j] = (int8_t)bits[j];
+      out.push_back(m);
+    }
+    pend.clear();
+  };
+  for (size_t i = begin; i < ops.size(); ++i) {
+    const OpDev &o = ops[i];
+    if (!mergeable(o)) {
+      emit();
+      out.push_back(o);
+      continue;
+    }
+    bool clash = pend.size() >= 3;
+    for (const OpDev &q : pend) clash |= q.tl[0] == o.tl[0];
+    if (clash) emit();
+    pend.push_back(o);
+  }
+  emit();
+  ops.swap(out);
+}
+
 Plan plan_passes(int n, const std::vector<HOp> &ops, int Tmax, int nlow_pref, int max_train, bool dagger,
-                 SlotTable &st, bool fuse = false, bool phase = false) {
+                 SlotTable &st, bool fuse = false, bool phase = false, bool multi = false) {
   Plan P;
   const std::vector<Group> groups = fuse_groups(n, ops, fuse, phase);
   const int T = std::min(Tmax, n);
@@ -823,6 +870,7 @@ Plan plan_passes(int n, const std::vector<HOp> &ops, int Tmax, int nlow_pref, in
       for (size_t q = before; q < P.ops.size(); ++q)
         if (P.ops[q].kind == kDense) pd.max_k = std::max(pd.max_k, (int)P.ops[q].k);
     }
+    if (multi) merge_multi(P.ops, (size_t)pd.op_begin);
     pd.op_end = (int)P.ops.size();
     pd.n_train = t;
     P.steps.push_back({0, (int)P.passes.size()});
@@ -893,6 +941,8 @@ sv_status check_plan(const Plan &P, int n, int nlow_pref) {
         continue;
       }
       if (op.k > kMaxTileTargets) return fail(SV_ERR_UNSUPPORTED, "internal planner error: wide op in a tile");
+      if (op.kind == kMulti && (op.k < 2 || op.k > 3))
+        return fail(SV_ERR_UNSUPPORTED, "internal planner error: multi-wire op");
       for (int j = 0; j < op.k; ++j) {
         if (op.tl[j] < 0 || op.tl[j] >= pd.T) return fail(SV_ERR_UNSUPPORTED, "internal planner error: non-local target");
         for (int q = 0; q < j; ++q)
@@ -1245,7 +1295,7 @@ sv_status build_program(sv_state *s, const sv_tape *tape, const sv_pauli_sum *ob
     expand_op(h, aops);
   }
   SlotTable st_tab;
-  p->fwd = plan_passes(n, fops, K.Tf, K.nlow_pref, 1 << 30, false, st_tab, true, true);
+  p->fwd = plan_passes(n, fops, K.Tf, K.nlow_pref, 1 << 30, false, st_tab, true, true, true);
   p->adj = plan_passes(n, aops, K.Ta, K.nlow_pref, kMaxTrainPerPass, true, st_tab, true);
   if (sv_status st = check_plan(p->fwd, n, K.nlow_pref)) {
     destroy_program(p);
@@ -1503,7 +1553,7 @@ sv_status require_params(const sv_program *p) {
 // over the amplitudes it touches (no tile, no shared memory).
 bool make_stream(int n, const PassDev &pd, const OpDev &o, bool c64, StreamDev &sd) {
   memset(&sd, 0, sizeof(sd));
-  if (o.kind == kDense || o.kind == kPhase || (o.kind == kDiag && o.k > 2)) return false;
+  if (o.kind == kDense || o.kind == kPhase || o.kind == kMulti || (o.kind == kDiag && o.k > 2)) return false;
   uint64_t fixed = o.cmask, val = o.cval;
   if (o.kind == kPair) {
     for (int j = 0; j < o.k; ++j) fixed |= 1ull << o.tg[j];
@@ -1972,7 +2022,7 @@ sv_status batch_plan(sv_batch *b, int tcap, int64_t wave) {
       hops.push_back(h);
     }
     const int T = std::min(std::min(tcap, K.Tf), n);
-    Plan P = plan_passes(n, hops, T, K.nlow_pref, 1 << 30, false, st, true, true);
+    Plan P = plan_passes(n, hops, T, K.nlow_pref, 1 << 30, false, st, true, true, true);
     if (sv_status e = check_plan(P, n, K.nlow_pref)) return e;
     const int aux_base = (int)(aux.size() / 2);
     for (OpDev &o : P.ops)
@@ -3028,7 +3078,7 @@ sv_status sv_plan_query(int n, sv_dtype dtype, const sv_tape *tape, int *n_forwa
     expand_op(h, aops);
   }
   SlotTable st_tab;
-  Plan f = plan_passes(n, fops, K.Tf, K.nlow_pref, 1 << 30, false, st_tab, true, true);
+  Plan f = plan_passes(n, fops, K.Tf, K.nlow_pref, 1 << 30, false, st_tab, true, true, true);
   Plan a = plan_passes(n, aops, K.Ta, K.nlow_pref, kMaxTrainPerPass, true, st_tab, true);
   if (sv_status st = check_plan(f, n, K.nlow_pref)) return st;
   if (sv_status st = check_plan(a, n, K.nlow_pref)) return st;

@@ -24,7 +24,11 @@ constexpr int kNormBlocks = 304;    // partial sums of a renormalisation (fixed 
 // amplitude pairs (kPair: e.g. IsingXX = blocks on |00>,|11> and |01>,|10>;
 // DoubleExcitation = one block on |0011>,|1100>), or a diagonal (kDiag), or,
 // for a user matrix on 2-4 wires, a dense block (kDense).
-enum OpKind : int8_t { kPair = 0, kDiag = 1, kDense = 2, kPhase = 3 };
+enum OpKind : int8_t { kPair = 0, kDiag = 1, kDense = 2, kPhase = 3, kMulti = 4 };
+// kMulti: k = 2..3 consecutive uncontrolled single-wire pair micro-ops on
+// distinct local bits (forward and batch plans): a thread holds the 2^k
+// amplitudes its group spans in registers and applies member j (code mcode[j],
+// 2x2 entries at mmat[j], local bit tl[j]) in order; ts[] = the bits sorted.
 // kPhase: a run of r adjacent Z-parity rotations sharing one angle (RZ,
 // IsingZZ; e.g. a QAOA cost layer) as one diagonal.  Member j multiplies by
 // exp(-i theta/2 (-1)^p_j) with p_j the parity of the index bits it acts on,
@@ -76,6 +80,9 @@ struct OpDev {
   // bits) vary inside a tile; the others are fixed per tile.
   uint32_t lcmask, lcval;
   uint64_t hcmask, hcval;
+  int8_t mcode[3];       // kMulti: member codes
+  int8_t pad2;
+  int32_t mmat[3];       // kMulti: member 2x2 entries
 };
 
 // One fused pass: a tile is the set of 2^T amplitudes that share every index

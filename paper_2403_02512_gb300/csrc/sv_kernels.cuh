@@ -663,9 +663,57 @@ __device__ void fwd_phase(c_t<R> *s, const TileGeom &tg, const OpDev &op, const 
   }
 }
 
+// Multi-wire micro-op: each thread takes groups of 2^W amplitudes (zeros
+// inserted at the W sorted bits), applies the members' 2x2 blocks in order in
+// registers, and stores the group back: one barrier for W gates.
+template <typename R, int W>
+__device__ void fwd_multi_t(c_t<R> *s, const TileGeom &tg, const OpDev &op, const c_t<R> *__restrict__ mats) {
+  using C = c_t<R>;
+  constexpr int G = 1 << W;
+  C M[W][4];
+#pragma unroll
+  for (int j = 0; j < W; ++j) {
+    const int c = op.mcode[j];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) M[j][q] = (c == mGen || c == mReal || c == mImOff) ? mats[op.mmat[j] + q] : C();
+  }
+  int off[G];
+#pragma unroll
+  for (int i = 0; i < G; ++i) {
+    int o = 0;
+#pragma unroll
+    for (int j = 0; j < W; ++j)
+      if ((i >> j) & 1) o += 1 << op.tl[j];
+    off[i] = o;
+  }
+  const int ts0 = op.ts[0], ts1 = op.ts[1], ts2 = op.ts[2];
+  const int ng = tg.A >> W;
+  for (int g = threadIdx.x; g < ng; g += blockDim.x) {
+    int l0 = insert_zero(insert_zero(g, ts0), ts1);
+    if (W > 2) l0 = insert_zero(l0, ts2);
+    C v[G];
+#pragma unroll
+    for (int i = 0; i < G; ++i) v[i] = s[l0 + off[i]];
+#pragma unroll
+    for (int j = 0; j < W; ++j)
+#pragma unroll
+      for (int i = 0; i < G; ++i)
+        if (!((i >> j) & 1)) pair_apply<R>(op.mcode[j], M[j], v[i], v[i | (1 << j)]);
+#pragma unroll
+    for (int i = 0; i < G; ++i) s[l0 + off[i]] = v[i];
+  }
+}
+
 template <typename R, int MAXK>
 __device__ __forceinline__ void apply_op(c_t<R> *s, const TileGeom &tg, const OpDev &op, const c_t<R> *mats,
                                          const uint64_t *aux) {
+  if (op.kind == kMulti) {
+    if (op.k == 2)
+      fwd_multi_t<R, 2>(s, tg, op, mats);
+    else
+      fwd_multi_t<R, 3>(s, tg, op, mats);
+    return;
+  }
   if (op.kind != kDense && !op_active(op, tg.base)) return;
   if (op.kind == kPair)
     fwd_pair<R>(s, tg, op, mats);
@@ -2033,7 +2081,7 @@ __device__ __forceinline__ unsigned long long global_ns() {
 constexpr int kBatchChunk = 8;  // work items a CTA takes from the queue at once
 
 template <typename R, int MAXK>
-__global__ void __launch_bounds__(kBlock) k_batch(g_t<R> *__restrict__ states, const BatchCircuit *__restrict__ circs,
+__global__ void __launch_bounds__(kBlock, 3) k_batch(g_t<R> *__restrict__ states, const BatchCircuit *__restrict__ circs,
                                                    const PassDev *__restrict__ passes, const OpDev *__restrict__ ops,
                                                    const c_t<R> *__restrict__ mats, const uint64_t *__restrict__ aux,
                                                    const BatchSeg *__restrict__ segs,
