@@ -250,9 +250,6 @@ struct Launch {
                            int no_publish, int grid, cudaStream_t st);
   static int batch_blocks_per_sm(int max_T, int max_terms, int max_k);
   static cudaError_t copy(void *dst, const void *src, int n, cudaStream_t st);
-  static int forward_smem(int T);
-  static int adjoint_smem(int T);
-  static int expval_smem(int T, int n_terms);
   static int max_T_forward();
   static int max_T_adjoint();
   // lambdas per adjoint CTA (largest compiled variant) and resident adjoint CTAs per SM

@@ -222,19 +222,6 @@ __device__ __forceinline__ void load_tile(const g_t<R> *__restrict__ g, c_t<R> *
   }
 }
 
-template <typename R>
-__device__ __forceinline__ void load_tile_rw(const g_t<R> *g, c_t<R> *s, const TileGeom &tg) {
-  // Same as load_tile without the read-only path (buffer is written by this kernel).
-  if constexpr (std::is_same<R, float>::value) {
-    const int nv = tg.A >> 1;
-    for (int v = threadIdx.x; v < nv; v += blockDim.x) {
-      const int l = v << 1;
-      reinterpret_cast<float4 *>(s)[v] = *reinterpret_cast<const float4 *>(g + tg.gidx(l));
-    }
-  } else {
-    for (int l = threadIdx.x; l < tg.A; l += blockDim.x) s[l] = to_c<R>(g[tg.gidx(l)]);
-  }
-}
 
 // Asynchronous tile load: every thread issues all of its 16-byte copies
 // global -> shared (cp.async, L2 only) before waiting, so a whole tile is in
@@ -430,23 +417,6 @@ __device__ __forceinline__ R pair_ip_acc(R acc, c_t<R> pa, c_t<R> pb, c_t<R> la,
   return acc;
 }
 
-__device__ __forceinline__ int diag_index(const OpDev &op, uint64_t g) {
-  int idx = 0;
-  for (int j = 0; j < op.k; ++j) idx = (idx << 1) | (int)((g >> op.tg[j]) & 1);
-  return idx;
-}
-
-template <typename R>
-__device__ __forceinline__ c_t<R> diag_mul(const OpDev &op, const c_t<R> *__restrict__ mats, int idx, c_t<R> v) {
-  if (op.code == dNeg) {
-    if (idx == (1 << op.k) - 1) {
-      v.x = -v.x;
-      v.y = -v.y;
-    }
-    return v;
-  }
-  return cmul(v, mats[op.mat + idx]);
-}
 
 // Controls on bits outside the tile decide per tile whether an op acts at all.
 __device__ __forceinline__ bool op_active(const OpDev &op, uint64_t base) {
@@ -2216,22 +2186,5 @@ __global__ void __launch_bounds__(kBlock, 3) k_batch(g_t<R> *__restrict__ states
     if (s_abort) break;
   }
 }
-
-// ---------------------------------------------------------------------------
-// Launchers
-// ---------------------------------------------------------------------------
-inline int lut_bytes(int T, int nlow_min) { return 8 << (T - nlow_min); }
-
-template <typename R>
-struct LaunchImpl {
-  using C = c_t<R>;
-  static constexpr int kNlowMin = std::is_same<R, float>::value ? 4 : 3;
-
-  static int forward_smem(int T) { return (int)(sizeof(C) << T) + lut_bytes(T, 0); }
-  static int adjoint_smem(int T) { return (int)(2 * (sizeof(C) << T)) + lut_bytes(T, 0) + 64 * 8 * 8; }
-  static int expval_smem(int T, int n_terms) {
-    return (int)(sizeof(C) << T) + lut_bytes(T, 0) + n_terms * 8 * 8;
-  }
-};
 
 }  // namespace sv

@@ -312,20 +312,8 @@ cudaError_t Launch<R>::copy(void *dst, const void *src, int n, cudaStream_t st) 
   return cudaMemcpyAsync(dst, src, sizeof(g_t<R>) << n, cudaMemcpyDeviceToDevice, st);
 }
 
-template <typename R>
-int Launch<R>::forward_smem(int T) {
-  return detail::tile_bytes(sizeof(c_t<R>), T) + (8 << T);
-}
 
-template <typename R>
-int Launch<R>::adjoint_smem(int T) {
-  return 2 * detail::tile_bytes(sizeof(c_t<R>), T) + (8 << T) + 64 * detail::kWarps * 8;
-}
 
-template <typename R>
-int Launch<R>::expval_smem(int T, int n_terms) {
-  return detail::tile_bytes(sizeof(c_t<R>), T) + (8 << T) + n_terms * detail::kWarps * 8;
-}
 
 // Tile sizes: 32 KiB of amplitudes per tile in the forward / expval kernels,
 // 2 x 16 KiB (phi + lambda) in the adjoint kernel.
