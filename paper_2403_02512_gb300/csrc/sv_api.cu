@@ -1243,7 +1243,8 @@ void adj_config(sv_program *p, const Ops &K, int n) {
   while (2 * b <= lpc) b *= 2;
   p->lam_per_cta = b;
   const int smem_a = tile_b * (1 + b) + (8 << ta) + kMaxTrainPerPass * 8 * (kBlock / 32) * b;
-  p->ctas_a = 2 * sm_count() * std::min(K.adj_cps, blocks_per_sm(smem_a));
+  const int cps = b <= 2 ? 2 : K.adj_cps;  // few lambdas per CTA: registers allow two CTAs per SM
+  p->ctas_a = 2 * sm_count() * std::min(cps, blocks_per_sm(smem_a));
   p->tiles_a = 1ull << (n - ta);
   p->cfg_compute = p->s->compute;
 }

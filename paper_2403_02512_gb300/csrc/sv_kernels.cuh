@@ -1139,7 +1139,7 @@ __device__ __forceinline__ void adj_diag(c_t<R> *sp, c_t<R> *sl, const TileGeom 
 }
 
 template <typename R, int MAXK, int B>
-__global__ void __launch_bounds__(kBlock, std::is_same<R, double>::value ? 1 : 2) k_tile_adjoint(const g_t<R> *phi_in, g_t<R> *phi_out,
+__global__ void __launch_bounds__(kBlock, (std::is_same<R, double>::value && B >= 4) ? 1 : 2) k_tile_adjoint(const g_t<R> *phi_in, g_t<R> *phi_out,
                                                              g_t<R> *__restrict__ lam_base, int n, int m,
                                                              const PassDev pass, const OpDev *__restrict__ ops,
                                                              const c_t<R> *__restrict__ mats,
