@@ -407,6 +407,17 @@ sv_status sv_batch_info(const sv_batch *b, int64_t *work_items, int *ctas, int *
 sv_status sv_plan_query(int n, sv_dtype dtype, const sv_tape *tape,
                         int *n_forward_passes, int *n_adjoint_passes);
 
+/* Host-only planner description: micro-op counts of the forward and adjoint
+ * plans (either array may be NULL), indexed by
+ *   0 pair blocks, 1 diagonals, 2 dense blocks in a tile, 3 phase runs
+ *   (adjacent RZ / IsingZZ sharing an angle), 4 fused single-wire runs,
+ *   5 multi-wire micro-ops (up to 3 single-wire gates per barrier),
+ *   6 wide dense steps outside tiles, 7 tile passes.
+ * Same argument errors as sv_plan_query. */
+#define SV_PLAN_KINDS 8
+sv_status sv_plan_describe(int n, sv_dtype dtype, const sv_tape *tape, int forward_counts[SV_PLAN_KINDS],
+                           int adjoint_counts[SV_PLAN_KINDS]);
+
 /* ---- expectation values without device allocation ------------------------------ */
 
 /* The paper has no counterpart to this call; it exists for callers that cannot

@@ -125,6 +125,7 @@ PROTOTYPES = {
     "sv_adjoint_jacobian_sparse": (ctypes.c_int, [_vp, ctypes.POINTER(SvTape), _dp, _vp, _dp, _dp]),
     "sv_program_stats": (ctypes.c_int, [_vp, _ip, _ip, _ip]),
     "sv_plan_query": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(SvTape), _ip, _ip]),
+    "sv_plan_describe": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(SvTape), _ip, _ip]),
     "sv_kernel_timing_enable": (ctypes.c_int, [ctypes.c_int]),
     "sv_kernel_timing_reset": (ctypes.c_int, []),
     "sv_kernel_timing_read": (ctypes.c_int, [_dp, ctypes.POINTER(ctypes.c_int64)]),
@@ -407,6 +408,17 @@ def sv_adjoint_jacobian_sparse(h: int, tape: "Tape", params, sp: Sparse):
     _check(load().sv_adjoint_jacobian_sparse(_vp(h), ctypes.byref(tape.struct), _dptr(p) if p.size else None,
                                              _vp(sp.handle), _dptr(e), _dptr(J)))
     return float(e[0]), J[: tape.n_params]
+
+
+PLAN_KINDS = ("pair", "diag", "dense", "phase_run", "fused_run", "multi", "wide_dense", "passes")
+
+
+def sv_plan_describe(n: int, dtype: int, tape: "Tape"):
+    """Micro-op counts of the forward and adjoint plans (host only)."""
+    f = (ctypes.c_int * 8)()
+    a = (ctypes.c_int * 8)()
+    _check(load().sv_plan_describe(int(n), int(dtype), ctypes.byref(tape.struct), f, a))
+    return dict(zip(PLAN_KINDS, list(f))), dict(zip(PLAN_KINDS, list(a)))
 
 
 def sv_program_stats(ph: int):

@@ -756,6 +756,7 @@ void lower_fused(int n, const std::vector<HOp> &ops, const std::vector<int> &mem
     ngen += g.code != gNone;
   }
   int gmat = 0;
+  o.fused = 1;
   o.mat = st.add_run(hs, gens, dagger, gmat);
   if (ngen > 0) {
     o.gcode = gHerm;
@@ -3064,7 +3065,8 @@ sv_status sv_batch_info(const sv_batch *b, int64_t *work_items, int *ctas, int *
   return SV_OK;
 }
 
-sv_status sv_plan_query(int n, sv_dtype dtype, const sv_tape *tape, int *n_forward_passes, int *n_adjoint_passes) {
+namespace {
+sv_status plan_both(int n, sv_dtype dtype, const sv_tape *tape, Plan &f, Plan &a) {
   if (n < 1 || n > SV_MAX_QUBITS) return fail(SV_ERR_ARG, "n = %d outside [1, %d]", n, SV_MAX_QUBITS);
   if (dtype != SV_C64 && dtype != SV_C128) return fail(SV_ERR_ARG, "unknown dtype");
   if (!tape || (tape->n_ops > 0 && !tape->ops)) return fail(SV_ERR_ARG, "bad tape");
@@ -3079,12 +3081,40 @@ sv_status sv_plan_query(int n, sv_dtype dtype, const sv_tape *tape, int *n_forwa
     expand_op(h, aops);
   }
   SlotTable st_tab;
-  Plan f = plan_passes(n, fops, K.Tf, K.nlow_pref, 1 << 30, false, st_tab, true, true, true);
-  Plan a = plan_passes(n, aops, K.Ta, K.nlow_pref, kMaxTrainPerPass, true, st_tab, true);
+  f = plan_passes(n, fops, K.Tf, K.nlow_pref, 1 << 30, false, st_tab, true, true, true);
+  a = plan_passes(n, aops, K.Ta, K.nlow_pref, kMaxTrainPerPass, true, st_tab, true);
   if (sv_status st = check_plan(f, n, K.nlow_pref)) return st;
-  if (sv_status st = check_plan(a, n, K.nlow_pref)) return st;
+  return check_plan(a, n, K.nlow_pref);
+}
+}  // namespace
+
+sv_status sv_plan_query(int n, sv_dtype dtype, const sv_tape *tape, int *n_forward_passes, int *n_adjoint_passes) {
+  Plan f, a;
+  if (sv_status st = plan_both(n, dtype, tape, f, a)) return st;
   if (n_forward_passes) *n_forward_passes = (int)f.steps.size();
   if (n_adjoint_passes) *n_adjoint_passes = (int)a.steps.size();
+  return SV_OK;
+}
+
+sv_status sv_plan_describe(int n, sv_dtype dtype, const sv_tape *tape, int forward_counts[SV_PLAN_KINDS],
+                           int adjoint_counts[SV_PLAN_KINDS]) {
+  Plan f, a;
+  if (sv_status st = plan_both(n, dtype, tape, f, a)) return st;
+  auto count = [](const Plan &P, int *out) {
+    if (!out) return;
+    for (int k = 0; k < SV_PLAN_KINDS; ++k) out[k] = 0;
+    for (const OpDev &o : P.ops) {
+      if (o.kind == kPair) out[o.fused ? 4 : 0]++;
+      else if (o.kind == kDiag) out[1]++;
+      else if (o.kind == kDense) out[2]++;
+      else if (o.kind == kPhase) out[3]++;
+      else if (o.kind == kMulti) out[5]++;
+    }
+    out[6] = (int)P.dk_ops.size();
+    out[7] = (int)P.passes.size();
+  };
+  count(f, forward_counts);
+  count(a, adjoint_counts);
   return SV_OK;
 }
 

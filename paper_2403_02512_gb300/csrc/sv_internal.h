@@ -81,7 +81,7 @@ struct OpDev {
   uint32_t lcmask, lcval;
   uint64_t hcmask, hcval;
   int8_t mcode[3];       // kMulti: member codes
-  int8_t pad2;
+  int8_t fused;          // kPair made from a fused run of single-wire gates (1), for plan descriptions
   int32_t mmat[3];       // kMulti: member 2x2 entries
 };
 

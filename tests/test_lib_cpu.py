@@ -84,3 +84,32 @@ def test_planner_checks_hold_for_random_circuits():
             for dt in (L.SV_C64, L.SV_C128):
                 f, a = L.sv_plan_query(n, dt, L.Tape(c.ops, c.n_params))
                 assert 1 <= f <= len(c.ops) and a >= f
+
+
+# ---- planner features, described without a GPU ------------------------------
+def test_plan_describe_qaoa_cost_layers_become_phase_runs_and_mixers_multi_ops():
+    from workloads import qaoa_maxcut
+    c = qaoa_maxcut(20, 4)
+    fwd, adj = L.sv_plan_describe(20, L.SV_C64, L.Tape(c.ops, c.n_params))
+    assert fwd["phase_run"] == 4                      # one diagonal per cost layer (30 RZZ each)
+    assert fwd["diag"] == 0                           # no RZZ left as its own micro-op
+    assert fwd["multi"] >= 4 * 20 // 3                # mixers: up to 3 RX per barrier
+    assert adj["phase_run"] == 0 and adj["multi"] == 0  # the adjoint keeps one micro-op per generator
+    assert adj["diag"] == 4 * len([o for o in c.ops if o.name == "IsingZZ"]) // 4
+
+
+def test_plan_describe_rot_runs_fuse_in_both_plans():
+    c, _ = strongly_entangling(12, 2, seed=3)
+    fwd, adj = L.sv_plan_describe(12, L.SV_C128, L.Tape(c.ops, c.n_params))
+    # the adjoint expands Rot into RZ, RY, RZ and fuses them back: one block per Rot
+    assert adj["fused_run"] == 2 * 12
+    assert fwd["dense"] == 0 and adj["dense"] == 0
+
+
+def test_plan_describe_counts_are_consistent_with_pass_counts():
+    for seed in range(5):
+        c, _ = random_circuit(10, 60, seed, max_controls=2)
+        tape = L.Tape(c.ops, c.n_params)
+        fwd, adj = L.sv_plan_describe(10, L.SV_C128, tape)
+        f, a = L.sv_plan_query(10, L.SV_C128, tape)
+        assert fwd["passes"] + fwd["wide_dense"] == f and adj["passes"] + adj["wide_dense"] == a
