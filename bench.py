@@ -300,6 +300,20 @@ def extra_qaoa():
     dt128 = (time.perf_counter() - t0) / k
     res["qaoa20_per_circuit_c128"] = {"circuits_per_s": 1.0 / dt128, "sample": k,
                                       "max_abs_diff_c64_batch_vs_c128": float(np.abs(e64[:k] - e128).max())}
+    # energy + adjoint gradient (8 parameters) of one parameter set, per precision
+    for dtype in ("c128", "c64"):
+        g_sv = StateVector(20, dtype)
+        g_prog = Program.from_circuit(g_sv, c)
+        g_prog.set_params(sets[0])
+
+        def grad_step():
+            g_prog.forward()
+            return g_prog.jacobian()
+
+        ms = _timed(grad_step, 5, torch.cuda.current_stream())
+        res[f"qaoa20_energy_and_gradient_{dtype}"] = {"ms": ms, "adjoint_passes": g_prog.stats()[1]}
+        g_prog.close()
+        g_sv.close()
     prog.close()
     sv.close()
     inst = qaoa_mixed_instances(256, 14, 22, 4)

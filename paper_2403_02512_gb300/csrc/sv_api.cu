@@ -602,11 +602,13 @@ bool fusable(const HOp &h) {
 // (same parameter and scale, or the same constant, and the same adjoint flag)
 // multiply by exp(-i theta/2 sum_j (-1)^p_j): one diagonal pass.
 bool phase_member(const HOp &h) {
-  return h.diag && h.nc == 0 && !h.train && (h.kind == SV_RZ || h.kind == SV_ISING_ZZ);
+  return h.diag && h.nc == 0 && (h.kind == SV_RZ || h.kind == SV_ISING_ZZ);
 }
 
+// Same angle source; trainable members (adjoint plans) then share one
+// Jacobian slot: their contributions all go to the same parameter column.
 bool same_angle(const HOp &a, const HOp &b) {
-  if (a.adjoint != b.adjoint || a.pidx[0] != b.pidx[0]) return false;
+  if (a.adjoint != b.adjoint || a.pidx[0] != b.pidx[0] || a.train != b.train) return false;
   return a.pidx[0] >= 0 ? a.scale == b.scale : a.cang[0] == b.cang[0];
 }
 
@@ -694,7 +696,7 @@ std::vector<Group> fuse_groups(int n, const std::vector<HOp> &ops, bool fuse, bo
 // Lower a phase run into one kPhase micro-op: member records (local-bit parity
 // mask, tile-bit parity mask) in P.aux, members with local bits first.
 void lower_phase(int n, const std::vector<HOp> &ops, const std::vector<int> &mem, const PassDev &pd, bool dagger,
-                 SlotTable &st, std::vector<OpDev> &out, std::vector<uint64_t> &aux) {
+                 int train, int slot, SlotTable &st, std::vector<OpDev> &out, std::vector<uint64_t> &aux) {
   const HOp &h0 = ops[mem[0]];
   OpDev o;
   memset(&o, 0, sizeof(o));
@@ -724,6 +726,11 @@ void lower_phase(int n, const std::vector<HOp> &ops, const std::vector<int> &mem
   o.oa = (int32_t)(aux.size() / 2);
   o.ob = (int32_t)mem.size();
   o.zmask = (int32_t)loc.size();
+  if (h0.train) {  // one slot: sum_j Im<lambda|G_j phi> = Im<lambda|(r - 2k) phi>
+    o.train = train;
+    o.slot = slot;
+    o.gcode = gDiag;
+  }
   for (auto *v : {&loc, &far})
     for (auto &rec : *v) {
       aux.push_back(rec.first);
@@ -842,7 +849,13 @@ Plan plan_passes(int n, const std::vector<HOp> &ops, int Tmax, int nlow_pref, in
       const std::vector<int> &grp = groups[gi].m;
       const size_t before = P.ops.size();
       if (groups[gi].kind == gPhaseRun) {
-        lower_phase(n, ops, grp, pd, dagger, st, P.ops, P.aux);
+        const bool tr = ops[grp[0]].train;
+        lower_phase(n, ops, grp, pd, dagger, t, tr ? P.n_train : -1, st, P.ops, P.aux);
+        if (tr) {
+          ++t;
+          ++P.n_train;
+          P.train_hop.push_back(grp[0]);
+        }
       } else if (groups[gi].kind == gRun) {
         lower_fused(n, ops, grp, pd, dagger, t, P.n_train, st, P.ops);
         for (int i : grp)
@@ -883,8 +896,10 @@ Plan plan_passes(int n, const std::vector<HOp> &ops, int Tmax, int nlow_pref, in
   for (int gi = 0; gi < (int)groups.size(); ++gi) {
     const std::vector<int> &grp = groups[gi].m;
     if (groups[gi].kind == gPhaseRun) {  // diagonal: needs no local bits
-      if (!cur_ops.empty() && cur_train > max_train) flush();
+      const int gt = ops[grp[0]].train ? 1 : 0;
+      if (!cur_ops.empty() && cur_train + gt > max_train) flush();
       cur_ops.push_back(gi);
+      cur_train += gt;
       continue;
     }
     if (groups[gi].kind == gRun) {
@@ -1180,7 +1195,8 @@ struct sv_program {
   size_t mats_entries = 0;
   // device pointers into `tables`
   OpDev *d_fwd_ops = nullptr, *d_adj_ops = nullptr, *d_tan_ops = nullptr;
-  uint64_t *d_aux = nullptr;  // phase-run member records of the forward plan
+  uint64_t *d_aux = nullptr;      // phase-run member records of the forward plan
+  uint64_t *d_adj_aux = nullptr;  // ... of the adjoint plan
   MatSlot *d_slots = nullptr;
   void *d_mats = nullptr;
   double *d_params = nullptr, *d_user = nullptr;
@@ -1298,7 +1314,7 @@ sv_status build_program(sv_state *s, const sv_tape *tape, const sv_pauli_sum *ob
   }
   SlotTable st_tab;
   p->fwd = plan_passes(n, fops, K.Tf, K.nlow_pref, 1 << 30, false, st_tab, true, true, true);
-  p->adj = plan_passes(n, aops, K.Ta, K.nlow_pref, kMaxTrainPerPass, true, st_tab, true);
+  p->adj = plan_passes(n, aops, K.Ta, K.nlow_pref, kMaxTrainPerPass, true, st_tab, true, true);
   if (sv_status st = check_plan(p->fwd, n, K.nlow_pref)) {
     destroy_program(p);
     return st;
@@ -1435,7 +1451,8 @@ sv_status build_program(sv_state *s, const sv_tape *tape, const sv_pauli_sum *ob
                  sz(umat_doubles, 8) + sz(tdev.size(), sizeof(TermDev)) + sz(obs_begin.size(), 4) +
                  sz(term_order.size(), 4) + sz(ltdev.size(), sizeof(TermDev)) + sz(lbegin.size(), 4) +
                  sz(p->coef.size(), 8) + sz(pbegin.size(), 4) + sz(pslots.size(), 4) +
-                 sz(p->vjp_host.size(), sizeof(TermDev)) + sz(vbegin.size(), 4) + sz(p->fwd.aux.size(), 8);
+                 sz(p->vjp_host.size(), sizeof(TermDev)) + sz(vbegin.size(), 4) + sz(p->fwd.aux.size(), 8) +
+                 sz(p->adj.aux.size(), 8);
   total = std::max<size_t>(total, 256);
   if (one_shot) {
     if (s->tab_bytes < total) {
@@ -1469,6 +1486,7 @@ sv_status build_program(sv_state *s, const sv_tape *tape, const sv_pauli_sum *ob
   };
   p->d_fwd_ops = (OpDev *)put(p->fwd.ops.data(), p->fwd.ops.size(), sizeof(OpDev));
   p->d_aux = (uint64_t *)put(p->fwd.aux.data(), p->fwd.aux.size(), 8);
+  p->d_adj_aux = (uint64_t *)put(p->adj.aux.data(), p->adj.aux.size(), 8);
   p->d_tan_ops = (OpDev *)put(p->tan.ops.data(), p->tan.ops.size(), sizeof(OpDev));
   p->d_adj_ops = (OpDev *)put(p->adj.ops.data(), p->adj.ops.size(), sizeof(OpDev));
   p->d_slots = (MatSlot *)put(slots.data(), slots.size(), sizeof(MatSlot));
@@ -1749,8 +1767,8 @@ sv_status run_sweep(sv_program *p, const JacWs &w, int mcc, int j0, int ldc, con
     cudaError_t e;
     {
       LaunchTimer t(s->stream, 1);
-      e = K.tile_adjoint(phi_in, phi_out, w.lam, n, mcc, p->lam_per_cta, pd, p->d_adj_ops, p->d_mats, w.partials, nb,
-                         s->stream);
+      e = K.tile_adjoint(phi_in, phi_out, w.lam, n, mcc, p->lam_per_cta, pd, p->d_adj_ops, p->d_mats, p->d_adj_aux,
+                         w.partials, nb, s->stream);
     }
     if (sv_status r = after_launch(s, e, "adjoint pass")) return r;
     ++p->launches;
@@ -3082,7 +3100,7 @@ sv_status plan_both(int n, sv_dtype dtype, const sv_tape *tape, Plan &f, Plan &a
   }
   SlotTable st_tab;
   f = plan_passes(n, fops, K.Tf, K.nlow_pref, 1 << 30, false, st_tab, true, true, true);
-  a = plan_passes(n, aops, K.Ta, K.nlow_pref, kMaxTrainPerPass, true, st_tab, true);
+  a = plan_passes(n, aops, K.Ta, K.nlow_pref, kMaxTrainPerPass, true, st_tab, true, true);
   if (sv_status st = check_plan(f, n, K.nlow_pref)) return st;
   return check_plan(a, n, K.nlow_pref);
 }

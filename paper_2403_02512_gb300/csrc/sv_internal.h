@@ -214,7 +214,7 @@ struct Launch {
                                   const void *mats, const uint64_t *aux, int grid, cudaStream_t st);
   // m lambdas, b of them per CTA (grid.x = ceil(m / b) lambda groups).
   static cudaError_t tile_adjoint(const void *phi_in, void *phi_out, void *lam, int n, int m, int b,
-                                  const PassDev &pass, const OpDev *ops, const void *mats,
+                                  const PassDev &pass, const OpDev *ops, const void *mats, const uint64_t *aux,
                                   double *partials, int grid, cudaStream_t st);
   static cudaError_t expval_pass(const void *psi, int n, const PassDev &pass, const TermDev *terms,
                                  int n_terms, double *partials, int grid, cudaStream_t st);

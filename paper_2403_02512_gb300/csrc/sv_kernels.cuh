@@ -1050,6 +1050,48 @@ __device__ __forceinline__ void adj_fused(c_t<R> *sp, c_t<R> *sl, const TileGeom
     adj_fused_c<R, B, 3>(sp, sl, tg, op, mats, bb, accs, nwarps, warp, lane);
 }
 
+// Phase run in the adjoint sweep: per amplitude k = parity count (as in the
+// forward op); a trainable run adds (r - 2k) Im(conj(lambda_j) phi) for every
+// lambda (the sum of its members' Z-parity generators) before phi and the
+// lambdas are multiplied by the stored E[k] (adjoint entries).
+template <typename R, int B>
+__device__ void adj_phase(c_t<R> *sp, c_t<R> *sl, const TileGeom &tg, const OpDev &op, const c_t<R> *__restrict__ mats,
+                          const uint64_t *__restrict__ aux, int bb, double *accs, int nwarps, int warp, int lane) {
+  using C = c_t<R>;
+  const uint64_t *m = aux + 2 * op.oa;
+  const int r = op.ob, rl = op.zmask;
+  const bool tr = op.train >= 0;
+  uint64_t flip = 0;
+  int k0 = 0;
+  for (int j = 0; j < r; ++j) {
+    const int f = __popcll(tg.base & __ldg(m + 2 * j + 1)) & 1;
+    if (j < rl)
+      flip |= (uint64_t)f << j;
+    else
+      k0 += f;
+  }
+  R acc[B];
+#pragma unroll
+  for (int jj = 0; jj < B; ++jj) acc[jj] = R(0);
+  for (int l = threadIdx.x; l < tg.A; l += blockDim.x) {
+    int k = k0;
+    for (int j = 0; j < rl; ++j)
+      k += (__popc((uint32_t)l & (uint32_t)__ldg(m + 2 * j)) + (int)(flip >> j)) & 1;
+    const C e = mats[op.mat + k];
+    const C p = sp[l];
+    const R g = R(r - 2 * k);
+    const R gpy = g * p.y, gpx = g * p.x;
+    sp[l] = cmul(p, e);
+#pragma unroll
+    for (int jj = 0; jj < B; ++jj) {
+      const C q = sl[jj * tg.A + l];
+      if (tr) acc[jj] = fma(q.x, gpy, fma(-q.y, gpx, acc[jj]));
+      sl[jj * tg.A + l] = cmul(q, e);
+    }
+  }
+  if (tr) flush_acc<R, B>(acc, bb, op.train, accs, nwarps, warp, lane, R(1));
+}
+
 // Adjoint diagonal micro-op: acc[j] += g(idx) Im(conj(lambda_j) phi) before
 // multiplying phi and every lambda by the stored (adjoint) entry.
 template <typename R, int B, int KD, bool NEG, bool CTL, bool TRAIN>
@@ -1143,6 +1185,7 @@ __global__ void __launch_bounds__(kBlock, (std::is_same<R, double>::value && B >
                                                              g_t<R> *__restrict__ lam_base, int n, int m,
                                                              const PassDev pass, const OpDev *__restrict__ ops,
                                                              const c_t<R> *__restrict__ mats,
+                                                             const uint64_t *__restrict__ aux,
                                                              double *__restrict__ partials) {
   using C = c_t<R>;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -1185,6 +1228,8 @@ __global__ void __launch_bounds__(kBlock, (std::is_same<R, double>::value && B >
       if (op.kind == kDense) {
         dense_any<R, MAXK>(sp, tg, op, mats);
         for (int jj = 0; jj < bb; ++jj) dense_any<R, MAXK>(sl + (size_t)jj * A, tg, op, mats);
+      } else if (op.kind == kPhase) {
+        adj_phase<R, B>(sp, sl, tg, op, mats, aux, bb, accs, nwarps, warp, lane);
       } else if (op.gcode == gHerm && op.train >= 0) {
         if (op_active(op, tg.base)) adj_fused<R, B>(sp, sl, tg, op, mats, bb, accs, nwarps, warp, lane);
       } else if (op_active(op, tg.base)) {

@@ -56,27 +56,29 @@ cudaError_t Launch<R>::tile_forward(void *psi, int n, const PassDev &pass, const
 namespace detail {
 template <typename R, int MAXK, int B>
 cudaError_t adjoint_b(const void *phi_in, void *phi_out, void *lam, int n, int m, const PassDev &pass,
-                      const OpDev *ops, const void *mats, double *partials, int grid, cudaStream_t st) {
+                      const OpDev *ops, const void *mats, const uint64_t *aux, double *partials, int grid,
+                      cudaStream_t st) {
   static bool attr = false;
   const int smem = (1 + B) * tile_bytes(sizeof(c_t<R>), pass.T) + lut_bytes(pass) + pass.n_train * B * kWarps * 8;
   allow_big_smem(k_tile_adjoint<R, MAXK, B>, attr);
   dim3 g((m + B - 1) / B, grid);
   k_tile_adjoint<R, MAXK, B><<<g, kBlock, smem, st>>>(
       reinterpret_cast<const g_t<R> *>(phi_in), reinterpret_cast<g_t<R> *>(phi_out), reinterpret_cast<g_t<R> *>(lam),
-      n, m, pass, ops, reinterpret_cast<const c_t<R> *>(mats), partials);
+      n, m, pass, ops, reinterpret_cast<const c_t<R> *>(mats), aux, partials);
   return cudaGetLastError();
 }
 
 template <typename R, int MAXK>
 cudaError_t adjoint_k(const void *phi_in, void *phi_out, void *lam, int n, int m, int b, const PassDev &pass,
-                      const OpDev *ops, const void *mats, double *partials, int grid, cudaStream_t st) {
+                      const OpDev *ops, const void *mats, const uint64_t *aux, double *partials, int grid,
+                      cudaStream_t st) {
   switch (b) {
-    case 1: return adjoint_b<R, MAXK, 1>(phi_in, phi_out, lam, n, m, pass, ops, mats, partials, grid, st);
-    case 2: return adjoint_b<R, MAXK, 2>(phi_in, phi_out, lam, n, m, pass, ops, mats, partials, grid, st);
-    case 4: return adjoint_b<R, MAXK, 4>(phi_in, phi_out, lam, n, m, pass, ops, mats, partials, grid, st);
+    case 1: return adjoint_b<R, MAXK, 1>(phi_in, phi_out, lam, n, m, pass, ops, mats, aux, partials, grid, st);
+    case 2: return adjoint_b<R, MAXK, 2>(phi_in, phi_out, lam, n, m, pass, ops, mats, aux, partials, grid, st);
+    case 4: return adjoint_b<R, MAXK, 4>(phi_in, phi_out, lam, n, m, pass, ops, mats, aux, partials, grid, st);
     case 8:
       if constexpr (std::is_same<R, double>::value)
-        return adjoint_b<R, MAXK, 8>(phi_in, phi_out, lam, n, m, pass, ops, mats, partials, grid, st);
+        return adjoint_b<R, MAXK, 8>(phi_in, phi_out, lam, n, m, pass, ops, mats, aux, partials, grid, st);
       return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;  // lambdas per CTA: 1, 2, 4 (8: complex128)
   }
@@ -85,11 +87,11 @@ cudaError_t adjoint_k(const void *phi_in, void *phi_out, void *lam, int n, int m
 
 template <typename R>
 cudaError_t Launch<R>::tile_adjoint(const void *phi_in, void *phi_out, void *lam, int n, int m, int b,
-                                    const PassDev &pass, const OpDev *ops, const void *mats, double *partials,
-                                    int grid, cudaStream_t st) {
+                                    const PassDev &pass, const OpDev *ops, const void *mats, const uint64_t *aux,
+                                    double *partials, int grid, cudaStream_t st) {
   if (pass.max_k <= 2)
-    return detail::adjoint_k<R, 2>(phi_in, phi_out, lam, n, m, b, pass, ops, mats, partials, grid, st);
-  return detail::adjoint_k<R, 4>(phi_in, phi_out, lam, n, m, b, pass, ops, mats, partials, grid, st);
+    return detail::adjoint_k<R, 2>(phi_in, phi_out, lam, n, m, b, pass, ops, mats, aux, partials, grid, st);
+  return detail::adjoint_k<R, 4>(phi_in, phi_out, lam, n, m, b, pass, ops, mats, aux, partials, grid, st);
 }
 
 template <typename R>
