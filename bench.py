@@ -63,8 +63,8 @@ def parse():
 # current kernel on sel22 (22 observables), scaled to sel24 by the state size
 # (x4) and the vector count (25 / 23).  Must be re-taken when the kernel changes.
 PROFILED_TRAFFIC = {
-    "c128": (3.037110e9 * 4 * 25 / 23, "profiles/k_tile_adjoint_sel22_c128.md, scaled x4 x25/23"),
-    "c64": (1.487835e9 * 4 * 25 / 23, "profiles/k_tile_adjoint_sel22_c64.md, scaled x4 x25/23"),
+    "c128": (3.042117e9 * 4 * 25 / 23, "profiles/k_tile_adjoint_sel22_c128.md, scaled x4 x25/23"),
+    "c64": (1.487015e9 * 4 * 25 / 23, "profiles/k_tile_adjoint_sel22_c64.md, scaled x4 x25/23"),
 }
 
 # FP64 pipe of a GB300: 152 SMs x 2 FMA lanes/clk x 2 flops x 2.07 GHz.
