@@ -1756,8 +1756,9 @@ sv_status run_sweep(sv_program *p, const JacWs &w, int mcc, int j0, int ldc, con
       }
       const OpDev &op = p->adj.dk_ops[st.index];
       LaunchTimer t(s->stream, 6);
-      cudaError_t e = K.dense_k((void *)phi_in, n, op, p->d_mats, 1, s->stream);
-      for (int j = 0; j < mcc && e == cudaSuccess; ++j) e = K.dense_k(w.lam + (size_t)j * V, n, op, p->d_mats, 1, s->stream);
+      // the adjoint plan's slot already holds U^dagger: apply it as stored
+      cudaError_t e = K.dense_k((void *)phi_in, n, op, p->d_mats, 0, s->stream);
+      for (int j = 0; j < mcc && e == cudaSuccess; ++j) e = K.dense_k(w.lam + (size_t)j * V, n, op, p->d_mats, 0, s->stream);
       if (sv_status r = after_launch(s, e, "dense_k adjoint")) return r;
       p->launches += 1 + mcc;
       continue;
@@ -1947,6 +1948,10 @@ sv_status sync_state(sv_state *s) {
   if (e != cudaSuccess) {
     s->latched = 1;
     return cuda_fail(e, "stream synchronize");
+  }
+  if (dense5_tc_take_error()) {
+    s->latched = 1;
+    return fail(SV_ERR_TIMEOUT, "a tensor-core dense-block wait ran out (results of the last call are invalid)");
   }
   return SV_OK;
 }
@@ -2341,6 +2346,12 @@ sv_status sv_set_renormalize(sv_state *s, int on) {
   if (!s) return fail(SV_ERR_ARG, "state is NULL");
   if (on != 0 && on != 1) return fail(SV_ERR_ARG, "renormalize flag must be 0 or 1, got %d", on);
   s->renorm = on;
+  return SV_OK;
+}
+
+sv_status sv_set_dense_tensor_cores(int on) {
+  if (on != 0 && on != 1) return fail(SV_ERR_ARG, "flag must be 0 or 1, got %d", on);
+  dense5_tc_enable(on != 0);
   return SV_OK;
 }
 
