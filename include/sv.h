@@ -189,6 +189,13 @@ sv_status sv_set_compute(sv_state *s, int compute);
  * reports).  on: 0 or 1; SV_ERR_ARG for a NULL state or another value. */
 sv_status sv_set_renormalize(sv_state *s, int on);
 
+/* Dense 5-qubit blocks on complex64 states run on the tensor cores (tcgen05,
+ * three TF32 products per FP32 product, FP32 accumulation in tensor memory)
+ * unless this library-wide switch is 0; then they run on the CUDA cores.
+ * Default 1.  A tensor-core wait that runs out (bounded at 1 s) makes the
+ * next synchronising call on the state return SV_ERR_TIMEOUT. */
+sv_status sv_set_dense_tensor_cores(int on);
+
 /* Query: n, dtype and the device pointer of the amplitudes (any may be NULL). */
 sv_status sv_info(const sv_state *s, int *n, sv_dtype *dtype, void **device_ptr);
 

@@ -93,6 +93,7 @@ PROTOTYPES = {
     "sv_info": (ctypes.c_int, [_vp, _ip, _ip, ctypes.POINTER(_vp)]),
     "sv_set_compute": (ctypes.c_int, [_vp, ctypes.c_int]),
     "sv_set_renormalize": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "sv_set_dense_tensor_cores": (ctypes.c_int, [ctypes.c_int]),
     "sv_reset": (ctypes.c_int, [_vp, ctypes.c_uint64]),
     "sv_set_state": (ctypes.c_int, [_vp, _vp]),
     "sv_get_state": (ctypes.c_int, [_vp, _vp]),
@@ -227,6 +228,10 @@ def sv_set_compute(h: int, compute: int) -> None:
 
 def sv_set_renormalize(h: int, on: bool) -> None:
     _check(load().sv_set_renormalize(_vp(h), 1 if on else 0))
+
+
+def sv_set_dense_tensor_cores(on: bool) -> None:
+    _check(load().sv_set_dense_tensor_cores(1 if on else 0))
 
 
 def sv_info(h: int):

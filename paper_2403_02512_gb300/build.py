@@ -22,7 +22,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libsv.so")
 
-SOURCES = ["sv_api.cu", "sv_kernels_f32.cu", "sv_kernels_f64.cu", "sv_kernels_df.cu", "sv_static.cu"]
+SOURCES = ["sv_api.cu", "sv_kernels_f32.cu", "sv_kernels_f64.cu", "sv_kernels_df.cu", "sv_static.cu", "sv_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 

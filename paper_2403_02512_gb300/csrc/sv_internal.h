@@ -258,6 +258,12 @@ struct Launch {
 };
 
 // Batch: out[c.out] = sum_term coeff * sum_tile partials (fixed order), one thread per circuit.
+// Tensor-core application of a dense 5-qubit block to a complex64 state (sv_tc.cu).
+cudaError_t dense5_tc(void *psi, int n, const OpDev &op, const void *mats, int adjoint, cudaStream_t st);
+int dense5_tc_take_error();  // 1 if a tensor-core wait ran out since the last call (clears it)
+void dense5_tc_enable(bool on);
+bool dense5_tc_enabled();
+
 // out[j0 + j] = 2 sum_b partials[j * nb + b], j < m (Jacobian-vector products).
 cudaError_t jvp_combine(const double *partials, int nb, int m, int j0, double *out, cudaStream_t st);
 // out[j0 + j] = sum_b partials[j * nb + b] - E[j0 + j]^2, j < m (variances).

@@ -155,6 +155,9 @@ cudaError_t Launch<R>::lambda_pass(const void *phi, void *lam, int n, const Pass
 template <typename R>
 cudaError_t Launch<R>::dense_k(void *psi, int n, const OpDev &op, const void *mats, int adjoint,
                                cudaStream_t st) {
+  if constexpr (std::is_same<R, float>::value) {
+    if (op.k == 5 && n >= 5 && dense5_tc_enabled()) return dense5_tc(psi, n, op, mats, adjoint, st);
+  }
   const uint64_t groups = 1ull << (n - op.k);
   const int gpb = kBlock >> op.k;
   uint64_t blocks = (groups + gpb - 1) / gpb;

@@ -625,3 +625,104 @@ def test_sparse_observable_validation():
     with pytest.raises(L.SvError):
         L.sv_sparse_expval(sv.handle, sp)
     sp.close()
+
+
+# ---- dense 5-qubit blocks on the tensor cores (complex64) ----------------------
+def _unitary(k, seed):
+    rng = np.random.default_rng(seed)
+    A = rng.normal(size=(1 << k, 1 << k)) + 1j * rng.normal(size=(1 << k, 1 << k))
+    U, _ = np.linalg.qr(A)
+    return U
+
+
+@pytest.mark.parametrize("n,wires", [(5, [0, 1, 2, 3, 4]), (6, [5, 1, 3, 0, 2]), (12, [7, 8, 9, 10, 11]),
+                                     (16, [15, 0, 9, 3, 12]), (17, [2, 11, 5, 16, 8])])
+def test_dense5_tensor_cores_match_oracle_and_cuda_cores(n, wires):
+    U = _unitary(5, 700 + n)
+    for adjoint in (False, True):
+        got = {}
+        for tc in (True, False):
+            L.sv_set_dense_tensor_cores(tc)
+            try:
+                sv, psi = _state(n, "c64", 700 + n)
+                sv.apply_matrix(wires, U, adjoint)
+                got[tc] = sv.to_numpy()
+                sv.close()
+            finally:
+                L.sv_set_dense_tensor_cores(True)
+        oracle.apply_matrix(psi, U.conj().T if adjoint else U, wires)
+        assert np.abs(got[True] - psi).max() <= 1e-5      # three TF32 products: FP32-level accuracy
+        assert np.abs(got[True] - got[False]).max() <= 1e-5
+
+
+class _MatrixOp:
+    """A dense user matrix on the tape (the binding's QubitUnitary)."""
+
+    def __init__(self, wires, matrix, controls=(), control_values=()):
+        self.name, self.wires, self.matrix = "QubitUnitary", tuple(wires), matrix
+        self.params, self.constants = (), ()
+        self.controls, self.control_values = tuple(controls), tuple(control_values)
+        self.adjoint, self.scale = False, 1.0
+
+
+def test_dense5_tensor_cores_with_controls_and_in_a_jacobian():
+    n = 13
+    U = _unitary(5, 720)
+    blk_wires, ctrl = (3, 9, 4, 11, 6), (0,)
+    pre = [Op("RY", (w,), (w,)) for w in range(n)]
+    post = [Op("RX", (w,), (n + w,)) for w in range(n)]
+    P = 2 * n  # one parameter per gate: the two-term shift rule is exact
+    obs = [[Term(1.0, ((3, "Z"),))], [Term(0.5, ((9, "X"), (4, "Y")))]]
+    p = np.random.default_rng(720).uniform(0, 2 * np.pi, P)
+
+    def oracle_energy(q):
+        psi = oracle.forward(Circuit(n, pre, P, []), q)
+        oracle.apply_matrix(psi, U, list(blk_wires), list(ctrl), [1])
+        psi = oracle.forward(Circuit(n, post, P, []), q, psi0=psi)
+        return oracle.expvals(psi, obs), psi
+
+    Eo, want = oracle_energy(p)
+    Jo = np.zeros((2, P))
+    for q in range(P):
+        e = np.zeros(P)
+        e[q] = 0.5 * np.pi
+        Jo[:, q] = 0.5 * (oracle_energy(p + e)[0] - oracle_energy(p - e)[0])
+    sv = StateVector(n, "c64")
+    prog = Program(sv, pre + [_MatrixOp(blk_wires, U, ctrl, (1,))] + post, P, obs)
+    prog.forward(p)
+    _assert_state(sv.to_numpy(), want, "c64")
+    E, J = prog.jacobian()  # the sweep un-applies the block with its adjoint on the tensor cores
+    _assert_rel(E.cpu().numpy(), Eo, 1e-4, "expval")
+    _assert_rel(J.cpu().numpy(), Jo, 1e-4, "jacobian")
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_wide_dense_blocks_in_a_jacobian(dtype):
+    # 6-qubit user matrix: a wide dense step outside the tiles, un-applied in the sweep
+    n = 12
+    U = _unitary(6, 730)
+    blk_wires = (1, 10, 4, 7, 2, 11)
+    pre = [Op("RY", (w,), (w,)) for w in range(n)]
+    post = [Op("RZ", (w,), (n + w,)) for w in range(n)] + [Op("RX", (w,), (2 * n + w,)) for w in range(n)]
+    P = 3 * n  # one parameter per gate: the two-term shift rule is exact
+    obs = [[Term(1.0, ((10, "Z"),))]]
+    p = np.random.default_rng(730).uniform(0, 2 * np.pi, P)
+
+    def oracle_energy(q):
+        psi = oracle.forward(Circuit(n, pre, P, []), q)
+        oracle.apply_matrix(psi, U, list(blk_wires))
+        psi = oracle.forward(Circuit(n, post, P, []), q, psi0=psi)
+        return oracle.expvals(psi, obs)
+
+    Eo = oracle_energy(p)
+    Jo = np.zeros((1, P))
+    for q in range(P):
+        e = np.zeros(P)
+        e[q] = 0.5 * np.pi
+        Jo[:, q] = 0.5 * (oracle_energy(p + e) - oracle_energy(p - e))
+    sv = StateVector(n, dtype)
+    prog = Program(sv, pre + [_MatrixOp(blk_wires, U)] + post, P, obs)
+    prog.forward(p)
+    E, J = prog.jacobian()
+    _assert_rel(E.cpu().numpy(), Eo, TOL_E[dtype], "expval")
+    _assert_rel(J.cpu().numpy(), Jo, TOL_J[dtype] * 10, "jacobian")
