@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--profile-batch", type=int, default=0, metavar="N",
                     help="profiling aid: time --steps runs of one batch of N 20-qubit QAOA p=4 parameter sets "
                          "(complex64, default launch shape, no autotuning) and print one JSON line")
+    ap.add_argument("--profile-dense", default=None, metavar="K[:cuda]",
+                    help="profiling aid: time --steps applications of a random K-qubit unitary on the lowest K "
+                         "wires' bits of a --qubits complex64 state (tensor cores for K = 5 unless ':cuda')")
     ap.add_argument("--profile-gate", default=None, metavar="GATE:WIRE",
                     help="profiling aid: time --steps passes of one gate (RX, Hadamard or CNOT, control "
                          "wire+1) on a --qubits state of --dtype and print one JSON line (not the bench line)")
@@ -262,6 +265,16 @@ def extra_gates(hbm_peak, wires_step=1):
         out[dtype] = res
         sv.close()
         torch.cuda.empty_cache()
+    # dense 5-qubit block, complex64, 28 qubits: tensor cores vs CUDA cores.  Algorithmic: 2V bytes;
+    # 32 complex multiply-adds per amplitude = 256 real flops per amplitude.
+    n = 28
+    V = 8 << n
+    dense = {}
+    for tc in (True, False):
+        ms = _dense_block_ms(n, 5, tc, 5, 2)
+        dense["tensor_cores" if tc else "cuda_cores"] = {"ms": ms, "frac_of_hbm": 2.0 * V / ms / 1e6 / hbm_peak,
+                                                         "tflops": (1 << n) * 256.0 / ms / 1e9}
+    out["dense5_n28_c64"] = dense
     return out
 
 
@@ -631,6 +644,33 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def _dense_block_ms(n, k, tensor_cores, reps, warmup):
+    import torch
+    from paper_2403_02512_gb300 import _lib as L
+    from paper_2403_02512_gb300.torch_api import StateVector
+    rng = np.random.default_rng(k)
+    U, _ = np.linalg.qr(rng.normal(size=(1 << k, 1 << k)) + 1j * rng.normal(size=(1 << k, 1 << k)))
+    wires = list(range(n - k, n))  # the lowest index bits: each group is contiguous
+    L.sv_set_dense_tensor_cores(tensor_cores)
+    try:
+        sv = StateVector(n, "c64", renormalize=False)
+        for _ in range(warmup):
+            sv.apply_matrix(wires, U)
+        ms = _timed(lambda: sv.apply_matrix(wires, U), reps, torch.cuda.current_stream())
+        sv.close()
+    finally:
+        L.sv_set_dense_tensor_cores(True)
+    return ms
+
+
+def run_profile_dense(args):
+    k, _, mode = args.profile_dense.partition(":")
+    ms = _dense_block_ms(args.qubits, int(k), mode != "cuda", args.steps, args.warmup)
+    V = 8 << args.qubits
+    print(json.dumps({"profile_dense": args.profile_dense, "n": args.qubits, "ms": ms,
+                      "gbs_algorithmic": 2.0 * V / ms / 1e6}))
+
+
 def run_profile_gate(args):
     import torch
     from paper_2403_02512_gb300.torch_api import Program, StateVector
@@ -677,7 +717,9 @@ def main():
     args = parse()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
-    if args.profile_gate:
+    if args.profile_dense:
+        run_profile_dense(args)
+    elif args.profile_gate:
         run_profile_gate(args)
     elif args.profile_batch:
         run_profile_batch(args)

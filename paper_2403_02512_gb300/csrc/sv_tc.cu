@@ -3,9 +3,15 @@
 // amplitudes that share the other index bits).
 //
 // As a real GEMM per tile of 128 groups:  D (128 x 64) = X (128 x 64) * Ur^T,
-// where row g of X holds group g's 32 real parts then 32 imaginary parts and
-// Ur (64 x 64) = [[Re U, -Im U], [Im U, Re U]] maps them to the output's real
-// and imaginary parts.  One tcgen05.mma (kind::tf32, M = 128, N = 64, K = 8)
+// where row g of X holds group g's 32 amplitudes (real and imaginary parts)
+// and Ur (64 x 64), built from Re U and Im U, maps them to the outputs' real
+// and imaginary parts.  Inputs are ordered along K as (member pair s, member
+// of the pair, re / im): k = 4 s + 2 h + c, with the pair bit pb the member bit
+// of the target on global index bit 0 when there is one.  Then each 16-byte
+// segment of a row is two amplitudes adjacent in memory, and the operand is
+// gathered with cp.async (all copies in flight) before one pass splits it
+// into TF32 halves; other target sets gather element by element.  Outputs
+// along N are (member, re / im) in member order.  One tcgen05.mma (kind::tf32, M = 128, N = 64, K = 8)
 // per 8 columns of K; FP32 accuracy from three products of TF32 halves,
 // hi*hi + hi*lo + lo*hi (x = hi + lo, each rounded to TF32), accumulated in
 // FP32 in tensor memory.  Operands sit in shared memory in the no-swizzle
@@ -68,6 +74,16 @@ __device__ __forceinline__ void split_tf32(float x, float &hi, float &lo) {
   lo = to_tf32(x - hi);
 }
 
+// K position of member m's real part (imaginary part: + 1).
+__device__ __forceinline__ int kpos(int m, int pb) {
+  const int s = ((m >> (pb + 1)) << pb) | (m & ((1 << pb) - 1));
+  return 4 * s + 2 * ((m >> pb) & 1);
+}
+
+__device__ __forceinline__ void cp_async16_zfill(uint32_t saddr, const void *gaddr, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(saddr), "l"(gaddr), "r"(src_bytes) : "memory");
+}
+
 __device__ __forceinline__ void st_shared_f32(uint32_t addr, float v) {
   asm volatile("st.shared.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
 }
@@ -116,8 +132,9 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+template <bool SEG>
 __global__ void __launch_bounds__(kTcThreads) k_dense5_tc(float2 *__restrict__ psi, int n, const OpDev op,
-                                                          const float2 *__restrict__ M, int dagger) {
+                                                          const float2 *__restrict__ M, int dagger, int pb) {
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char *a_hi = smem, *a_lo = smem + kOpBytesA;
   unsigned char *b_hi = smem + 2 * kOpBytesA, *b_lo = b_hi + kOpBytesB;
@@ -137,16 +154,21 @@ __global__ void __launch_bounds__(kTcThreads) k_dense5_tc(float2 *__restrict__ p
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
 
-  // B halves: row n (output component) of Ur, K-major.
-  for (int e = threadIdx.x; e < kTcN * kTcK; e += blockDim.x) {
-    const int nn = e / kTcK, k = e % kTcK;
-    const int r = nn & 31, c = k & 31;
-    const float2 u = dagger ? make_float2(M[c * 32 + r].x, -M[c * 32 + r].y) : M[r * 32 + c];
-    const float v = (nn < 32) ? (k < 32 ? u.x : -u.y) : (k < 32 ? u.y : u.x);
+  // B halves: row nn = 2 o + c' (output member o, re / im), column k(i, c), K-major.
+  for (int e = threadIdx.x; e < kTcN * 32; e += blockDim.x) {
+    const int nn = e >> 5, i = e & 31;
+    const int o = nn >> 1, co = nn & 1;
+    const float2 u = dagger ? make_float2(M[i * 32 + o].x, -M[i * 32 + o].y) : M[o * 32 + i];
+    const int k = kpos(i, pb);
+    const float vr = co == 0 ? u.x : u.y;   // coefficient of the input's real part
+    const float vi = co == 0 ? -u.y : u.x;  // ... of its imaginary part
     float hi, lo;
-    split_tf32(v, hi, lo);
+    split_tf32(vr, hi, lo);
     st_shared_f32(smem_u32(b_hi) + kmajor_off(nn, k), hi);
     st_shared_f32(smem_u32(b_lo) + kmajor_off(nn, k), lo);
+    split_tf32(vi, hi, lo);
+    st_shared_f32(smem_u32(b_hi) + kmajor_off(nn, k + 1), hi);
+    st_shared_f32(smem_u32(b_lo) + kmajor_off(nn, k + 1), lo);
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -171,26 +193,62 @@ __global__ void __launch_bounds__(kTcThreads) k_dense5_tc(float2 *__restrict__ p
   uint32_t phase = 0;
   bool failed = false;
   for (uint64_t tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
-    // gather: warp w loads groups 32w .. 32w + 31 of the tile, lane = member
-    for (int q = 0; q < 32; ++q) {
-      const int row = warp * 32 + q;
-      const uint64_t g = tile * kTcRows + row;
-      float2 a = make_float2(0.f, 0.f);
-      if (g < ngroups) {
-        uint64_t i0 = g;
-        for (int j = 0; j < 5; ++j) {
-          const int b = sorted[j];
-          i0 = ((i0 >> b) << (b + 1)) | (i0 & ((1ull << b) - 1));
+    if constexpr (SEG) {
+      // 512-byte chunks of the operand: 8 rows x 4 segments; lane -> (row l % 8, segment l / 8)
+      for (int chunk = warp; chunk < (kTcRows / 8) * (kTcK / 16); chunk += kTcThreads / 32) {
+        const int row = (chunk >> 2) * 8 + (lane & 7);
+        const int seg = (chunk & 3) * 4 + (lane >> 3);  // pair index s
+        const uint64_t g = tile * kTcRows + row;
+        uint64_t i0 = 0;
+        if (g < ngroups) {
+          i0 = g;
+          for (int j = 0; j < 5; ++j) {
+            const int b = sorted[j];
+            i0 = ((i0 >> b) << (b + 1)) | (i0 & ((1ull << b) - 1));
+          }
         }
-        a = __ldcs(psi + (i0 | roff));
+        // member of pair s with the pair bit clear
+        const int m = ((seg >> pb) << (pb + 1)) | (seg & ((1 << pb) - 1));
+        uint64_t off = 0;
+        for (int j = 0; j < 5; ++j)
+          if ((m >> (4 - j)) & 1) off |= 1ull << op.tg[j];
+        cp_async16_zfill(smem_u32(a_hi) + kmajor_off(row, 4 * seg), psi + (i0 | off), g < ngroups ? 16 : 0);
       }
-      float hi, lo;
-      split_tf32(a.x, hi, lo);
-      st_shared_f32(smem_u32(a_hi) + kmajor_off(row, lane), hi);
-      st_shared_f32(smem_u32(a_lo) + kmajor_off(row, lane), lo);
-      split_tf32(a.y, hi, lo);
-      st_shared_f32(smem_u32(a_hi) + kmajor_off(row, 32 + lane), hi);
-      st_shared_f32(smem_u32(a_lo) + kmajor_off(row, 32 + lane), lo);
+      asm volatile("cp.async.wait_all;" ::: "memory");
+      __syncthreads();
+      // split in place: a_hi <- TF32(x), a_lo <- TF32(x - hi); consecutive 16-byte chunks per lane
+      for (int c = threadIdx.x; c < kOpBytesA / 16; c += blockDim.x) {
+        float4 x = reinterpret_cast<const float4 *>(a_hi)[c], lo;
+        split_tf32(x.x, x.x, lo.x);
+        split_tf32(x.y, x.y, lo.y);
+        split_tf32(x.z, x.z, lo.z);
+        split_tf32(x.w, x.w, lo.w);
+        reinterpret_cast<float4 *>(a_hi)[c] = x;
+        reinterpret_cast<float4 *>(a_lo)[c] = lo;
+      }
+    } else {
+      // gather: warp w loads groups 32w .. 32w + 31 of the tile, lane = member
+      const int kl = kpos(lane, pb);
+      for (int q = 0; q < 32; ++q) {
+        const int row = warp * 32 + q;
+        const uint64_t g = tile * kTcRows + row;
+        float2 a = make_float2(0.f, 0.f);
+        if (g < ngroups) {
+          uint64_t i0 = g;
+          for (int j = 0; j < 5; ++j) {
+            const int b = sorted[j];
+            i0 = ((i0 >> b) << (b + 1)) | (i0 & ((1ull << b) - 1));
+          }
+          a = __ldcs(psi + (i0 | roff));
+        }
+        float hi, lo;
+        split_tf32(a.x, hi, lo);
+        st_shared_f32(smem_u32(a_hi) + kmajor_off(row, kl), hi);
+        st_shared_f32(smem_u32(a_lo) + kmajor_off(row, kl), lo);
+        split_tf32(a.y, hi, lo);
+        st_shared_f32(smem_u32(a_hi) + kmajor_off(row, kl + 1), hi);
+        st_shared_f32(smem_u32(a_lo) + kmajor_off(row, kl + 1), lo);
+      }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -231,7 +289,7 @@ __global__ void __launch_bounds__(kTcThreads) k_dense5_tc(float2 *__restrict__ p
     }
     const int row = warp * 32 + lane;
 #pragma unroll
-    for (int i = 0; i < 32; ++i) stage[row * 32 + i] = make_float2(d[i], d[32 + i]);
+    for (int i = 0; i < 32; ++i) stage[row * 32 + i] = make_float2(d[2 * i], d[2 * i + 1]);
     __syncwarp();
     // store: warp w writes its 32 groups, lane = member (coalesced for low target bits)
     for (int q = 0; q < 32; ++q) {
@@ -277,17 +335,30 @@ cudaError_t dense5_tc(void *psi, int n, const OpDev &op, const void *mats, int a
   static bool attr = false;
   const int smem = dense5_tc_smem();
   if (!attr) {
-    cudaFuncSetAttribute(k_dense5_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(k_dense5_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(k_dense5_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     attr = true;
   }
+  // pair bit: the member bit of the target on global index bit 0 (segments of two adjacent amplitudes)
+  int pb = 0;
+  bool seg = false;
+  for (int j = 0; j < 5; ++j)
+    if (op.tg[j] == 0) {
+      pb = 4 - j;
+      seg = true;
+    }
   int dev = 0, sms = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const uint64_t ntiles = ((1ull << (n - 5)) + kTcRows - 1) / kTcRows;
   const int grid = (int)std::min<uint64_t>(ntiles, (uint64_t)sms * 2);
   g_tc_launched = true;
-  k_dense5_tc<<<grid, kTcThreads, smem, st>>>(reinterpret_cast<float2 *>(psi), n, op,
-                                             reinterpret_cast<const float2 *>(mats) + op.mat, adjoint);
+  if (seg)
+    k_dense5_tc<true><<<grid, kTcThreads, smem, st>>>(reinterpret_cast<float2 *>(psi), n, op,
+                                                     reinterpret_cast<const float2 *>(mats) + op.mat, adjoint, pb);
+  else
+    k_dense5_tc<false><<<grid, kTcThreads, smem, st>>>(reinterpret_cast<float2 *>(psi), n, op,
+                                                      reinterpret_cast<const float2 *>(mats) + op.mat, adjoint, pb);
   return cudaGetLastError();
 }
 

@@ -636,7 +636,8 @@ def _unitary(k, seed):
 
 
 @pytest.mark.parametrize("n,wires", [(5, [0, 1, 2, 3, 4]), (6, [5, 1, 3, 0, 2]), (12, [7, 8, 9, 10, 11]),
-                                     (16, [15, 0, 9, 3, 12]), (17, [2, 11, 5, 16, 8])])
+                                     (16, [15, 0, 9, 3, 12]), (17, [2, 11, 5, 16, 8]),
+                                     (14, [0, 3, 6, 9, 12])])  # last: no target on index bit 0
 def test_dense5_tensor_cores_match_oracle_and_cuda_cores(n, wires):
     U = _unitary(5, 700 + n)
     for adjoint in (False, True):
