@@ -288,8 +288,10 @@ __global__ void __launch_bounds__(kTcThreads) k_dense5_tc(float2 *__restrict__ p
       for (int i = 0; i < 16; ++i) d[c * 16 + i] = v[i];
     }
     const int row = warp * 32 + lane;
+    // staging index row * 32 + (member ^ (row % 32)): conflict-free for these per-row
+    // writes and for the per-group reads below
 #pragma unroll
-    for (int i = 0; i < 32; ++i) stage[row * 32 + i] = make_float2(d[2 * i], d[2 * i + 1]);
+    for (int i = 0; i < 32; ++i) stage[row * 32 + (i ^ lane)] = make_float2(d[2 * i], d[2 * i + 1]);
     __syncwarp();
     // store: warp w writes its 32 groups, lane = member (coalesced for low target bits)
     for (int q = 0; q < 32; ++q) {
@@ -301,7 +303,7 @@ __global__ void __launch_bounds__(kTcThreads) k_dense5_tc(float2 *__restrict__ p
         const int b = sorted[j];
         i0 = ((i0 >> b) << (b + 1)) | (i0 & ((1ull << b) - 1));
       }
-      if ((i0 & op.cmask) == op.cval) __stcs(psi + (i0 | roff), stage[rr * 32 + lane]);
+      if ((i0 & op.cmask) == op.cval) __stcs(psi + (i0 | roff), stage[rr * 32 + (lane ^ (rr & 31))]);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();  // the stage and A are rewritten by the next tile
