@@ -196,6 +196,23 @@ def oracle_sample(sweep_steps: int = 6):
     return est_ms, sample, oracle.num_threads(), (t3 - t0)
 
 
+def max_over_ranks(value: float, world: int, device) -> float:
+    """The job's time: the slowest replica's (all-reduce MAX over the process
+    group; the replicas themselves exchange nothing)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(ms_max: float, world: int) -> float:
+    """Whole-job time per step: `world` replicas each finish one step in ms_max."""
+    return ms_max / world if world > 1 else ms_max
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -539,11 +556,7 @@ def run_ours(args):
         return out
 
     main = measure(args.dtype, args.steps, args.warmup, timing=True)
-    ms = main["ms"]
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(main["ms"], world, "cuda")
 
     # roofline of the dominant kernel (tile_adjoint).  HBM: algorithmic bytes
     # 2V(1 + m) per launch.  Arithmetic: the sweep's algorithmic flops
@@ -627,7 +640,7 @@ def run_ours(args):
                "sample_wall_s": wall}
 
     if rank == 0:
-        line = {"metric": METRIC, "value": ms / world if world > 1 else ms, "unit": "ms", "n_gpus": world,
+        line = {"metric": METRIC, "value": replica_value(ms, world), "unit": "ms", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
                 "scaling": "weak", "vs_baseline": None, "dtype": {"c128": "f64", "c64": "f32", "c128df": "df64 (f32 pairs; complex128 storage)"}[args.dtype],
                 "data": "synthetic",
