@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--profile-dense", default=None, metavar="K[:cuda]",
                     help="profiling aid: time --steps applications of a random K-qubit unitary on the lowest K "
                          "wires' bits of a --qubits complex64 state (tensor cores for K = 5 unless ':cuda')")
+    ap.add_argument("--profile-vqe", action="store_true",
+                    help="profiling aid: --steps energy + adjoint-gradient steps of the 24-qubit VQE workload "
+                         "(2000-term Hamiltonian) in --dtype; prints one JSON line")
     ap.add_argument("--profile-gate", default=None, metavar="GATE:WIRE",
                     help="profiling aid: time --steps passes of one gate (RX, Hadamard or CNOT, control "
                          "wire+1) on a --qubits state of --dtype and print one JSON line (not the bench line)")
@@ -684,6 +687,25 @@ def run_profile_dense(args):
                       "gbs_algorithmic": 2.0 * V / ms / 1e6}))
 
 
+def run_profile_vqe(args):
+    import torch
+    from paper_2403_02512_gb300.torch_api import Program, StateVector
+    from workloads import vqe_givens
+    c, p = vqe_givens(24, 12, 40, 120, 2000)
+    sv = StateVector(24, args.dtype, basis_state=c.basis_state)
+    prog = Program.from_circuit(sv, c)
+
+    def step():
+        prog.forward(p)
+        prog.expval()
+        return prog.vjp(np.ones(1))
+
+    for _ in range(args.warmup):
+        step()
+    ms = _timed(step, args.steps, torch.cuda.current_stream())
+    print(json.dumps({"profile_vqe": args.dtype, "ms_energy_and_gradient": ms}))
+
+
 def run_profile_gate(args):
     import torch
     from paper_2403_02512_gb300.torch_api import Program, StateVector
@@ -730,7 +752,9 @@ def main():
     args = parse()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
-    if args.profile_dense:
+    if args.profile_vqe:
+        run_profile_vqe(args)
+    elif args.profile_dense:
         run_profile_dense(args)
     elif args.profile_gate:
         run_profile_gate(args)
