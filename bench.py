@@ -456,7 +456,10 @@ def extra_measurements(hbm_peak):
 
 
 def extra_rycz30():
-    """30-qubit RY layers + CZ brick, <Z0 Z29>: forward + full adjoint Jacobian (600 params)."""
+    """30-qubit RY layers + CZ brick + a 5-qubit dense block after every fifth
+    layer, <Z0 Z29>: forward + full adjoint Jacobian (600 params).  The dense
+    blocks run on the tensor cores in complex64 and on the CUDA cores in
+    complex128."""
     import torch
     from paper_2403_02512_gb300.torch_api import Program, StateVector
     from workloads import ry_cz_brick

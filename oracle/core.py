@@ -279,7 +279,12 @@ def op_angles(op, params: np.ndarray) -> List[float]:
 
 
 def op_matrix(op, params: np.ndarray) -> np.ndarray:
-    M = gate_matrix(op.name, op_angles(op, params))
+    """Matrix of a base gate at its angles, or a QubitUnitary's own matrix;
+    conjugate-transposed under the op's adjoint flag (Listing 1's inverse)."""
+    if op.name == "QubitUnitary":
+        M = np.array(op.matrix, dtype=np.complex128)
+    else:
+        M = gate_matrix(op.name, op_angles(op, params))
     return M.conj().T.copy() if op.adjoint else M
 
 
@@ -397,11 +402,11 @@ def norm2(psi: np.ndarray) -> float:
 class _Step:
     """One single-angle (or angle-free) operation of the expanded tape."""
 
-    __slots__ = ("name", "wires", "controls", "cvals", "param", "scale", "adjoint")
+    __slots__ = ("name", "wires", "controls", "cvals", "param", "scale", "adjoint", "matrix")
 
-    def __init__(self, name, wires, controls, cvals, param, scale, adjoint):
+    def __init__(self, name, wires, controls, cvals, param, scale, adjoint, matrix=None):
         self.name, self.wires, self.controls, self.cvals = name, wires, controls, cvals
-        self.param, self.scale, self.adjoint = param, scale, adjoint
+        self.param, self.scale, self.adjoint, self.matrix = param, scale, adjoint, matrix
 
 
 def expand(ops) -> List[_Step]:
@@ -415,6 +420,9 @@ def expand(ops) -> List[_Step]:
                 parts = parts[::-1]
             for g, p in parts:
                 out.append(_Step(g, op.wires, op.controls, cv, p, op.scale, op.adjoint))
+        elif op.name == "QubitUnitary":
+            out.append(_Step(op.name, op.wires, op.controls, cv, None, 1.0, op.adjoint,
+                             np.array(op.matrix, dtype=np.complex128)))
         else:
             p = op.params[0] if op.params else None
             out.append(_Step(op.name, op.wires, op.controls, cv, p, op.scale, op.adjoint))
@@ -422,8 +430,11 @@ def expand(ops) -> List[_Step]:
 
 
 def _step_matrix(st: _Step, params) -> np.ndarray:
-    ang = [] if st.param is None else [st.scale * float(params[st.param])]
-    M = gate_matrix(st.name, ang)
+    if st.matrix is not None:
+        M = st.matrix
+    else:
+        ang = [] if st.param is None else [st.scale * float(params[st.param])]
+        M = gate_matrix(st.name, ang)
     return M.conj().T.copy() if st.adjoint else M
 
 

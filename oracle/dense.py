@@ -62,7 +62,10 @@ def controlled(n: int, wires, M, controls, values) -> np.ndarray:
 
 
 def op_unitary(n: int, op, params) -> np.ndarray:
-    M = gate_matrix(op.name, op_angles(op, params))
+    if op.name == "QubitUnitary":
+        M = np.array(op.matrix, dtype=np.complex128)
+    else:
+        M = gate_matrix(op.name, op_angles(op, params))
     if op.adjoint:
         M = M.conj().T
     return controlled(n, op.wires, M, op.controls, op.ctrl_values)

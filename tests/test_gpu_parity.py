@@ -277,7 +277,9 @@ def test_workload_shapes_small(dtype, maker):
     elif maker == "vqe":
         c, p = vqe_givens(12, 6, 10, 20, 150, seed=3)
     else:
-        c, p = ry_cz_brick(14, 4, seed=4)
+        # a 5-qubit dense block after every second layer: all four block windows
+        # (complex64: the tensor cores, forward and un-applied in the sweep)
+        c, p = ry_cz_brick(14, 8, seed=4, dense_every=2)
     sv = StateVector(c.n, dtype, basis_state=c.basis_state)
     prog = Program.from_circuit(sv, c)
     prog.forward(p)

@@ -1,6 +1,8 @@
 """The 30-qubit stress workload at full size: 20 layers of RY on all wires plus
-a CZ brick, observable Z_0 Z_29, forward pass plus full adjoint Jacobian
-(600 parameters), complex128 (16 GiB per vector) and complex64.
+a CZ brick, with a seeded 5-qubit dense block after every fifth layer (tensor
+cores in complex64, CUDA cores in complex128), observable Z_0 Z_29, forward
+pass plus full adjoint Jacobian (600 parameters), complex128 (16 GiB per
+vector) and complex64.
 
 No dense reference exists at this size, so the checks are:
   * parameter shift, computed with the GPU's own forward passes, on a seeded
@@ -33,7 +35,9 @@ N = 30
 
 @pytest.fixture(scope="module")
 def workload():
-    return ry_cz_brick(N, 20)
+    c, p = ry_cz_brick(N, 20)
+    assert sum(op.name == "QubitUnitary" for op in c.ops) == 4
+    return c, p
 
 
 @pytest.fixture(scope="module")
@@ -46,7 +50,7 @@ def c128_result(workload):
     E, J = E.cpu().numpy(), J.cpu().numpy()
     # parameter shift on a seeded sample of parameters, GPU forward passes
     rng = np.random.default_rng(config_seed(5) + 1)
-    sample = rng.choice(c.n_params, 4, replace=False)
+    sample = rng.choice(c.n_params, 8, replace=False)
     shift = {}
     for q in sample:
         e = []

@@ -17,8 +17,8 @@ import scipy.linalg
 
 import oracle
 from oracle import dense, enumeration
-from workloads import (Circuit, Op, Term, GATE_ARITY, GATE_NPARAMS, layered_circuit,
-                       qaoa_maxcut, random_circuit, random_hamiltonian, random_state,
+from workloads import (Circuit, MatrixOp, Op, Term, GATE_ARITY, GATE_NPARAMS, layered_circuit,
+                       dense_block_wires, random_unitary, qaoa_maxcut, random_circuit, random_hamiltonian, random_state,
                        regular_graph, strongly_entangling, vqe_givens, ry_cz_brick)
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -335,6 +335,81 @@ def test_adjoint_matches_finite_differences():
     _, J = oracle.adjoint_jacobian(c, p, obs)
     Jfd = oracle.finite_diff_jacobian(c, p, obs)
     np.testing.assert_allclose(J, Jfd, atol=1e-7)
+
+
+# ---------------------------------------------------------------------------
+# Dense blocks (QubitUnitary) on the tape
+# ---------------------------------------------------------------------------
+CNOT_TEXTBOOK = np.array([[1, 0, 0, 0], [0, 1, 0, 0], [0, 0, 0, 1], [0, 0, 1, 0]], dtype=np.complex128)
+
+
+@pytest.mark.parametrize("wires", [(0, 1), (1, 0), (2, 0), (1, 3)])
+def test_dense_block_wire_order_is_the_textbook_cnot(wires):
+    # the textbook CNOT matrix (first wire = control = most significant bit) on
+    # `wires` must equal the base gate PauliX on wires[1] controlled by wires[0]
+    n = 4
+    psi0 = random_state(n, 31)
+    a = oracle.copy(psi0)
+    oracle.apply_op(a, MatrixOp(wires, CNOT_TEXTBOOK), np.zeros(0))
+    b = oracle.copy(psi0)
+    oracle.apply_op(b, Op("PauliX", (wires[1],), controls=(wires[0],)), np.zeros(0))
+    np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("wires,controls", [((5, 0, 3, 1, 4), ()), ((0, 1, 2, 3, 4), ()), ((4, 2, 0, 5, 1), (3,))])
+def test_dense_block_forward_matches_dense_kronecker(wires, controls):
+    n = 6
+    rng = np.random.default_rng(41)
+    ops = [Op("RY", (w,), (w,)) for w in range(n)]
+    ops += [MatrixOp(wires, random_unitary(5, rng), controls)]
+    ops += [Op("RX", (w,), (n + w,)) for w in range(n)]
+    ops += [MatrixOp(wires, random_unitary(5, rng), controls, adjoint=True)]
+    c = Circuit(n, ops, 2 * n, [])
+    p = rng.uniform(0, 2 * math.pi, 2 * n)
+    np.testing.assert_allclose(oracle.forward(c, p), dense.state(c, p), atol=1e-13)
+
+
+def test_dense_block_adjoint_flag_is_the_conjugate_transpose():
+    n = 7
+    U = random_unitary(5, np.random.default_rng(43))
+    psi0 = random_state(n, 43)
+    a = oracle.copy(psi0)
+    oracle.apply_op(a, MatrixOp((6, 2, 4, 0, 3), U, adjoint=True), np.zeros(0))
+    b = oracle.copy(psi0)
+    oracle.apply_op(b, MatrixOp((6, 2, 4, 0, 3), U.conj().T.copy()), np.zeros(0))
+    np.testing.assert_array_equal(a, b)
+    oracle.apply_op(a, MatrixOp((6, 2, 4, 0, 3), U), np.zeros(0))  # U U^dagger = I
+    np.testing.assert_allclose(a, psi0, atol=1e-14)
+
+
+def test_rycz_dense_block_windows_are_distinct_wires_and_touch_bit0():
+    for n in (10, 12, 30):
+        ws = [dense_block_wires(n, b) for b in range(4)]
+        assert all(len(set(w)) == 5 and min(w) >= 0 and max(w) < n for w in ws)
+        assert any(n - 1 in w for w in ws)  # wire n-1 = global index bit 0
+
+
+def test_adjoint_through_dense_blocks_matches_parameter_shift():
+    # RY + CZ brick with a dense block after every second layer (all four windows)
+    c, p = ry_cz_brick(10, 8, seed=4, dense_every=2)
+    assert sum(op.name == "QubitUnitary" for op in c.ops) == 4
+    E, J = oracle.adjoint_jacobian(c, p)
+    Jps = oracle.param_shift_jacobian(c, p)
+    np.testing.assert_allclose(J, Jps, atol=1e-12)
+    np.testing.assert_allclose(E, oracle.expvals(oracle.forward(c, p), c.observables), atol=1e-14)
+
+
+def test_adjoint_through_a_controlled_dense_block_matches_the_exact_derivative():
+    n = 6
+    rng = np.random.default_rng(47)
+    ops = [Op("RX", (w,), (w,)) for w in range(n)]
+    ops += [MatrixOp((0, 2, 4, 5, 1), random_unitary(5, rng), (3,), (0,))]
+    ops += [Op("RY", (w,), (n + w,)) for w in range(n)]
+    obs = [[Term(1.0, ((2, "Z"),))], [Term(0.4, ((0, "X"), (5, "Y")))]]
+    c = Circuit(n, ops, 2 * n, obs)
+    p = rng.uniform(0, 2 * math.pi, 2 * n)
+    _, J = oracle.adjoint_jacobian(c, p)
+    np.testing.assert_allclose(J, dense.exact_jacobian(c, p), atol=1e-12)
 
 
 def test_vjp_is_gradient_weighted_jacobian_rows():

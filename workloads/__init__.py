@@ -3,10 +3,12 @@
 This package describes circuits and observables only as structure (gate names,
 wires, parameter indices) plus seeded random numbers.  It holds none of the
 simulation arithmetic: no gate matrices, no index arithmetic, no reductions.
+The dense unitaries of :class:`MatrixOp` are random input data.
 """
 
 from .circuits import (  # noqa: F401
     Op,
+    MatrixOp,
     Circuit,
     Term,
     GATE_ARITY,
@@ -19,6 +21,8 @@ from .circuits import (  # noqa: F401
     regular_graph,
     vqe_givens,
     ry_cz_brick,
+    dense_block_wires,
+    random_unitary,
     random_circuit,
     random_hamiltonian,
     random_state,

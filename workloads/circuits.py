@@ -12,7 +12,10 @@ not of arithmetic):
   Listing 1;
 * an observable is a list of :class:`Term` (coefficient, Pauli letters per
   wire), i.e. a Hamiltonian of coefficients and tensor-product Pauli words as
-  in Listing 2.
+  in Listing 2;
+* a :class:`MatrixOp` is a fixed dense 2^k x 2^k unitary on k wires (the
+  QubitUnitary of the gate list), given as data; its matrix index has wires[0]
+  as the most significant bit.
 
 Gate names follow the paper's gate list (Section 2.1.2): PauliX, PauliY,
 PauliZ, Hadamard, S, T, PhaseShift, RX, RY, RZ, Rot, SWAP, IsingXX, IsingXY,
@@ -71,6 +74,43 @@ class Op:
     @property
     def ctrl_values(self) -> Tuple[int, ...]:
         return self.control_values if self.control_values else (1,) * len(self.controls)
+
+
+@dataclass(frozen=True)
+class MatrixOp:
+    """A fixed dense unitary on ``wires`` (no angles): ``matrix`` is 2^k x 2^k,
+    row / column bit j (from the most significant) belongs to wires[j]."""
+    wires: Tuple[int, ...]
+    matrix: np.ndarray = field(compare=False, repr=False)
+    controls: Tuple[int, ...] = ()
+    control_values: Tuple[int, ...] = ()
+    adjoint: bool = False
+    name: str = "QubitUnitary"
+    params: Tuple[int, ...] = ()
+    scale: float = 1.0
+
+    def __post_init__(self):
+        if self.name != "QubitUnitary":
+            raise ValueError("MatrixOp is a QubitUnitary")
+        if np.shape(self.matrix) != (1 << len(self.wires), 1 << len(self.wires)):
+            raise ValueError("matrix must be 2^k x 2^k for k wires")
+        if self.control_values and len(self.control_values) != len(self.controls):
+            raise ValueError("control_values must match controls")
+
+    @property
+    def ctrl_values(self) -> Tuple[int, ...]:
+        return self.control_values if self.control_values else (1,) * len(self.controls)
+
+
+def random_unitary(k: int, rng: np.random.Generator) -> np.ndarray:
+    """Haar-distributed 2^k x 2^k unitary (input data): QR of a complex Gaussian
+    matrix with the phases of R's diagonal moved into Q (Mezzadri, Notices AMS
+    54, 2007)."""
+    d = 1 << k
+    z = (rng.normal(size=(d, d)) + 1j * rng.normal(size=(d, d))) / np.sqrt(2.0)
+    q, r = np.linalg.qr(z)
+    ph = np.diag(r) / np.abs(np.diag(r))
+    return np.ascontiguousarray(q * ph[None, :], dtype=np.complex128)
 
 
 @dataclass(frozen=True)
@@ -279,14 +319,29 @@ def vqe_givens(n: int = 24, electrons: int = 12, n_singles: int = 40, n_doubles:
 # ---------------------------------------------------------------------------
 # Workload 5: RY layers + CZ brick
 # ---------------------------------------------------------------------------
-def ry_cz_brick(n: int = 30, layers: int = 20, seed: int | None = None):
+def dense_block_wires(n: int, b: int) -> Tuple[int, ...]:
+    """Wires of the b-th 5-qubit dense block of :func:`ry_cz_brick` (n >= 10):
+    the top five wires, the bottom five (global index bit 0 among them), five
+    scattered wires in descending order, then the middle five; repeating."""
+    return [tuple(range(5)), tuple(range(n - 5, n)), (n - 2, 2 * n // 3, n // 2, n // 3, 1),
+            tuple(range(n // 2 - 2, n // 2 + 3))][b % 4]
+
+
+def ry_cz_brick(n: int = 30, layers: int = 20, seed: int | None = None, dense_every: int = 5):
     """RY on every wire then a CZ brick (even layer: CZ(2i, 2i+1); odd: CZ(2i+1, 2i+2)).
 
-    Observable Z_0 Z_{n-1}.  Angles uniform in [0, 2pi).
+    After every ``dense_every``-th layer (0: none) comes a fixed 5-qubit dense
+    block: a Haar-random unitary (a stand-in for a block fused from several
+    gates) on the wires of :func:`dense_block_wires`.  Observable
+    Z_0 Z_{n-1}.  Angles uniform in [0, 2pi); the blocks draw from a separate
+    stream, so the angles do not depend on them.
     """
-    rng = np.random.default_rng(config_seed(5) if seed is None else seed)
-    ops: List[Op] = []
+    seed = config_seed(5) if seed is None else seed
+    rng = np.random.default_rng(seed)
+    mrng = np.random.default_rng([seed, 5])
+    ops: List = []
     p = 0
+    blocks = 0
     for l in range(layers):
         for w in range(n):
             ops.append(Op("RY", (w,), (p,)))
@@ -294,6 +349,11 @@ def ry_cz_brick(n: int = 30, layers: int = 20, seed: int | None = None):
         start = 0 if l % 2 == 0 else 1
         for a in range(start, n - 1, 2):
             ops.append(Op("PauliZ", (a + 1,), controls=(a,)))
+        if dense_every > 0 and (l + 1) % dense_every == 0:
+            if n < 10:
+                raise ValueError("dense blocks need n >= 10 (or dense_every=0)")
+            ops.append(MatrixOp(dense_block_wires(n, blocks), random_unitary(5, mrng)))
+            blocks += 1
     params = rng.uniform(0.0, 2.0 * np.pi, size=p)
     obs = [[Term(1.0, ((0, "Z"), (n - 1, "Z")))]]
     return Circuit(n, ops, p, obs, name=f"rycz_n{n}_l{layers}"), params
