@@ -463,9 +463,12 @@ def extra_rycz30():
     import torch
     from paper_2403_02512_gb300.torch_api import Program, StateVector
     from workloads import ry_cz_brick
+    from paper_2403_02512_gb300 import _lib as L
     c, p = ry_cz_brick(30, 20)
     out = {}
-    for dtype in ("c128", "c64"):
+    # the last run applies the complex64 dense blocks on the CUDA cores instead
+    for key, dtype, tc in (("c128", "c128", True), ("c64", "c64", True), ("c64_dense_on_cuda_cores", "c64", False)):
+        L.sv_set_dense_tensor_cores(tc)
         sv = StateVector(30, dtype)
         prog = Program.from_circuit(sv, c)
 
@@ -473,10 +476,13 @@ def extra_rycz30():
             prog.forward(p)
             return prog.jacobian()
 
-        ms = _timed(step, 1, torch.cuda.current_stream())
-        E, J = step()
-        out[dtype] = {"ms_forward_and_jacobian": ms, "expval": float(E[0]), "forward_passes": prog.stats()[0],
-                      "adjoint_passes": prog.stats()[1], "J_sum": float(J.sum())}
+        try:
+            ms = _timed(step, 1, torch.cuda.current_stream())
+            E, J = step()
+        finally:
+            L.sv_set_dense_tensor_cores(True)
+        out[key] = {"ms_forward_and_jacobian": ms, "expval": float(E[0]), "forward_passes": prog.stats()[0],
+                    "adjoint_passes": prog.stats()[1], "J_sum": float(J.sum())}
         prog.close()
         sv.close()
         torch.cuda.empty_cache()

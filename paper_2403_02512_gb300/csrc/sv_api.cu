@@ -1072,6 +1072,7 @@ struct Ops {
   decltype(&Launch<float>::tile_forward) tile_forward;
   decltype(&Launch<float>::tile_adjoint) tile_adjoint;
   decltype(&Launch<float>::expval_pass) expval_pass;
+  decltype(&Launch<float>::expval_obs_pass) expval_obs_pass;
   decltype(&Launch<float>::lambda_pass) lambda_pass;
   decltype(&Launch<float>::dense_k) dense_k;
   decltype(&Launch<float>::set_basis) set_basis;
@@ -1084,7 +1085,8 @@ struct Ops {
 
 const Ops &ops_df() {
   static const Ops d = {Launch<df>::build_matrices, Launch<df>::tile_forward, Launch<df>::tile_adjoint,
-                        Launch<df>::expval_pass,    Launch<df>::lambda_pass,  Launch<df>::dense_k,
+                        Launch<df>::expval_pass,    Launch<df>::expval_obs_pass, Launch<df>::lambda_pass,
+                        Launch<df>::dense_k,
                         Launch<df>::set_basis,      Launch<df>::copy,
                         Launch<df>::stream_op, Launch<df>::tile_tangent,
                         16, Launch<df>::max_T_forward(), Launch<df>::max_T_adjoint(), 3,
@@ -1095,14 +1097,14 @@ const Ops &ops_df() {
 const Ops &ops_for(sv_dtype dt) {
   static const Ops f32 = {Launch<float>::build_matrices, Launch<float>::tile_forward,
                           Launch<float>::tile_adjoint,   Launch<float>::expval_pass,
-                          Launch<float>::lambda_pass,    Launch<float>::dense_k,
+                          Launch<float>::expval_obs_pass, Launch<float>::lambda_pass, Launch<float>::dense_k,
                           Launch<float>::set_basis,      Launch<float>::copy,
                           Launch<float>::stream_op, Launch<float>::tile_tangent,
                           8, Launch<float>::max_T_forward(), Launch<float>::max_T_adjoint(), 4,
                           Launch<float>::adj_lambdas_max(), Launch<float>::adj_ctas_per_sm()};
   static const Ops f64 = {Launch<double>::build_matrices, Launch<double>::tile_forward,
                           Launch<double>::tile_adjoint,   Launch<double>::expval_pass,
-                          Launch<double>::lambda_pass,    Launch<double>::dense_k,
+                          Launch<double>::expval_obs_pass, Launch<double>::lambda_pass, Launch<double>::dense_k,
                           Launch<double>::set_basis,      Launch<double>::copy,
                           Launch<double>::stream_op, Launch<double>::tile_tangent,
                           16, Launch<double>::max_T_forward(), Launch<double>::max_T_adjoint(), 3,
@@ -1645,6 +1647,21 @@ struct JacWs {
   double2 *tan_coefs;  // JVP: complex coefficient per tangent slot
 };
 
+// Expectation values by observable (one register sum of H_o psi per amplitude,
+// one reduction per observable and tile) instead of by word: complex128 (FP64
+// or double-float), all observables in one lambda chunk (its term tables), at
+// least four words per observable on average, at most 64 observables.
+bool expval_by_observable(const sv_program *p) {
+  return p->s->dt == SV_C128 && p->m > 0 && p->m <= 64 && p->n_chunks == 1 && p->terms.size() >= 4 * (size_t)p->m;
+}
+
+// Rows of the term-sum buffer: one per word, or one per (pass, observable).
+size_t term_sum_rows(const sv_program *p) {
+  size_t rows = std::max<size_t>(1, p->terms.size());
+  if (expval_by_observable(p)) rows = std::max(rows, p->tp.passes.size() * (size_t)p->m);
+  return rows;
+}
+
 sv_status jac_workspace(sv_program *p, JacWs &w) {
   sv_state *s = p->s;
   sync_adj_config(p);
@@ -1657,7 +1674,7 @@ sv_status jac_workspace(sv_program *p, JacWs &w) {
   size_t lam_rows = 1;
   for (int mcc : {p->mc, p->m % std::max(1, p->mc), 1})
     if (mcc > 0) lam_rows = std::max(lam_rows, (size_t)p->grid_a(mcc) * mcc);
-  size_t part = std::max(lam_rows * max_train, (size_t)p->grid_e * max_terms);
+  size_t part = std::max(lam_rows * max_train, (size_t)p->grid_e * std::max<size_t>(max_terms, p->m));
   if (p->want_lam) part = std::max(part, (size_t)p->mc * kNormBlocks);
   if (p->want_tan) part = std::max(part, (size_t)p->mc * kNormBlocks);
   const bool need_vec = p->adj.n_train > 0 || !p->adj.dk_ops.empty() || p->want_tan;  // phi buffers / dpsi
@@ -1665,7 +1682,7 @@ sv_status jac_workspace(sv_program *p, JacWs &w) {
   const size_t tan_bytes = p->want_tan ? align256((size_t)std::max(1, p->tan.n_train) * 16) : 0;
   const size_t bytes = tan_bytes + (need_vec ? 2 * V : 0) + (need_lam ? (size_t)p->mc * V : 0) + align256(part * 8) +
                        align256((size_t)std::max(1, p->adj.n_train) * std::max(1, p->m) * 8) +
-                       align256(std::max<size_t>(1, p->terms.size()) * 8) + align256((size_t)std::max(1, p->m) * 8) +
+                       align256(term_sum_rows(p) * 8) + align256((size_t)std::max(1, p->m) * 8) +
                        align256((size_t)std::max(1, p->m) * std::max(1, p->n_params) * 8);
   char *base = nullptr;
   if (sv_status st = get_workspace(s, bytes, &base)) return st;
@@ -1683,7 +1700,7 @@ sv_status jac_workspace(sv_program *p, JacWs &w) {
   w.contrib = (double *)(base + c);
   c += align256((size_t)std::max(1, p->adj.n_train) * std::max(1, p->m) * 8);
   w.term_sums = (double *)(base + c);
-  c += align256(std::max<size_t>(1, p->terms.size()) * 8);
+  c += align256(term_sum_rows(p) * 8);
   w.expvals = (double *)(base + c);
   c += align256((size_t)std::max(1, p->m) * 8);
   w.J = (double *)(base + c);
@@ -1693,6 +1710,33 @@ sv_status jac_workspace(sv_program *p, JacWs &w) {
 sv_status run_expval(sv_program *p, const void *psi, const JacWs &w) {
   sv_state *s = p->s;
   const Ops &K = ops_of(s);
+  if (expval_by_observable(p)) {
+    // per pass q: term_sums[q * m + o] = sum over CTAs; then expvals[o] = sum over q (fixed orders)
+    const int npass = (int)p->tp.passes.size();
+    for (int q = 0; q < npass; ++q) {
+      const int32_t *begin = (const int32_t *)p->d_lam_begin + p->lam_begin_off[q];
+      cudaError_t e;
+      {
+        LaunchTimer t(s->stream, 2);
+        e = K.expval_obs_pass(psi, s->n, p->tp.passes[q], p->d_lam_terms, begin, p->m, w.partials, p->grid_e,
+                              s->stream);
+      }
+      if (sv_status r = after_launch(s, e, "expval pass")) return r;
+      {
+        LaunchTimer t(s->stream, 4);
+        e = reduce_partials(w.partials, p->grid_e, p->m, 1, w.term_sums, p->m, q, 0, s->stream);
+      }
+      if (sv_status r = after_launch(s, e, "expval reduce")) return r;
+      p->launches += 2;
+    }
+    cudaError_t e;
+    {
+      LaunchTimer t(s->stream, 4);
+      e = reduce_partials(w.term_sums, npass, p->m, 1, w.expvals, 1, 0, 0, s->stream);
+    }
+    p->launches += 1;
+    return after_launch(s, e, "expval combine");
+  }
   for (size_t q = 0; q + 1 < p->tp.begin.size(); ++q) {
     const int b = p->tp.begin[q], cnt = p->tp.begin[q + 1] - b;
     if (cnt == 0) continue;

@@ -218,6 +218,12 @@ struct Launch {
                                   double *partials, int grid, cudaStream_t st);
   static cudaError_t expval_pass(const void *psi, int n, const PassDev &pass, const TermDev *terms,
                                  int n_terms, double *partials, int grid, cudaStream_t st);
+  // Expectation values of n_obs observables over the words placed in one pass,
+  // words grouped by observable ([obs_term_begin[o], obs_term_begin[o + 1]) of
+  // terms): FP64 partials[block * n_obs + o].
+  static cudaError_t expval_obs_pass(const void *psi, int n, const PassDev &pass, const TermDev *terms,
+                                     const int32_t *obs_term_begin, int n_obs, double *partials, int grid,
+                                     cudaStream_t st);
   static cudaError_t lambda_pass(const void *phi, void *lam, int n, const PassDev &pass,
                                  const TermDev *terms, const int32_t *obs_term_begin, int n_obs,
                                  int first, int grid, cudaStream_t st);

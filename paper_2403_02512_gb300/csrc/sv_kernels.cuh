@@ -1385,6 +1385,108 @@ __global__ void __launch_bounds__(kBlock) k_lambda(const g_t<R> *__restrict__ ph
 }
 
 // ---------------------------------------------------------------------------
+// Expectation values by observable (S5 for Hamiltonians of many words): for
+// each amplitude g of the tile, (H_o psi)_g over the words of observable o
+// placed in this pass is accumulated in registers, then Re(conj(psi_g)
+// (H_o psi)_g) is summed: one reduction per observable and tile instead of one
+// per word.  Words are the outer loop, so a word's masks and signed
+// coefficients are formed once per thread for its NA amplitudes.  The sign
+// (-1)^{popcount((g ^ x) & z)} = (-1)^{popcount(g & z)} (-1)^{popcount(x & z)}
+// is applied by flipping the sign bits of the partner amplitude.
+// partials[block * n_obs + o].
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float flip_sign(float v, uint32_t p) { return __int_as_float(__float_as_int(v) ^ (int)(p << 31)); }
+__device__ __forceinline__ double flip_sign(double v, uint32_t p) {
+  return __longlong_as_double(__double_as_longlong(v) ^ ((long long)p << 63));
+}
+__device__ __forceinline__ df flip_sign(df v, uint32_t p) { return df_make(flip_sign(v.h, p), flip_sign(v.l, p)); }
+
+template <typename R, int NA>
+__global__ void __launch_bounds__(kBlock) k_expval_obs(const g_t<R> *__restrict__ psi, int n, const PassDev pass,
+                                                        const TermDev *__restrict__ terms,
+                                                        const int32_t *__restrict__ obs_term_begin, int n_obs,
+                                                        double *__restrict__ partials) {
+  using C = c_t<R>;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int A = 1 << pass.T;
+  C *s = reinterpret_cast<C *>(smem);
+  uint64_t *lut = reinterpret_cast<uint64_t *>(s + A);
+  const int nch = 1 << (pass.T - pass.nlow);
+  double *accs = reinterpret_cast<double *>(lut + nch);  // [n_obs][nwarps]
+  const int nwarps = blockDim.x >> 5;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  build_lut(lut, pass);
+  for (int i = threadIdx.x; i < n_obs * nwarps; i += blockDim.x) accs[i] = 0.0;
+  TileGeom tg;
+  tg.T = pass.T;
+  tg.nlow = pass.nlow;
+  tg.A = A;
+  tg.lowmask = (1u << pass.nlow) - 1u;
+  tg.lut = lut;
+  __syncthreads();
+  const uint64_t ntiles = 1ull << (n - pass.T);
+  for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    tg.base = tile_base(pass, tile);
+    load_tile<R>(psi, s, tg);
+    __syncthreads();
+    uint64_t g[NA];
+#pragma unroll
+    for (int k = 0; k < NA; ++k) {
+      const int l = threadIdx.x + k * kBlock;
+      g[k] = l < A ? tg.gidx(l) : 0;
+    }
+    for (int o = 0; o < n_obs; ++o) {
+      const int t0 = obs_term_begin[o], t1 = obs_term_begin[o + 1];
+      if (t0 == t1) continue;
+      R hx[NA], hy[NA];
+#pragma unroll
+      for (int k = 0; k < NA; ++k) {
+        hx[k] = R(0);
+        hy[k] = R(0);
+      }
+      for (int t = t0; t < t1; ++t) {
+        const TermDev tm = terms[t];
+        // i^ny c b:  x += cx * (swap ? b.y : b.x),  y += cy * (swap ? b.x : b.y)
+        const int ny = tm.ny & 3;
+        const bool swap = (ny & 1) != 0;
+        const R c = R(tm.coeff);
+        const R cx = (ny == 1 || ny == 2) ? -c : c;
+        const R cy = ny >= 2 ? -c : c;
+        const uint32_t tpar = (uint32_t)__popcll(tm.xg & tm.zg) & 1u;
+#pragma unroll
+        for (int k = 0; k < NA; ++k) {
+          const int l = threadIdx.x + k * kBlock;
+          if (l < A) {
+            const C b = s[l ^ tm.xl];
+            const uint32_t par = ((uint32_t)__popcll(g[k] & tm.zg) & 1u) ^ tpar;
+            const R bx = flip_sign(b.x, par), by = flip_sign(b.y, par);
+            hx[k] = fma(cx, swap ? by : bx, hx[k]);
+            hy[k] = fma(cy, swap ? bx : by, hy[k]);
+          }
+        }
+      }
+      Acc<R> acc;
+#pragma unroll
+      for (int k = 0; k < NA; ++k) {
+        const int l = threadIdx.x + k * kBlock;
+        if (l < A) {
+          const C a = s[l];
+          acc.add(a.x * hx[k] + a.y * hy[k]);
+        }
+      }
+      const R part = warp_sum(acc.value());
+      if (lane == 0) WarpAcc<R>::add(&accs[o * nwarps + warp], part);
+    }
+    __syncthreads();
+  }
+  for (int o = threadIdx.x; o < n_obs; o += blockDim.x) {
+    double v = 0.0;
+    for (int w = 0; w < nwarps; ++w) v += WarpAcc<R>::read(&accs[o * nwarps + w]);
+    partials[(size_t)blockIdx.x * n_obs + o] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Dense k-qubit block applied straight from global memory (k = 5, 6), one
 // output amplitude per thread: CTA stages 256 / 2^k groups in shared memory.
 // ---------------------------------------------------------------------------

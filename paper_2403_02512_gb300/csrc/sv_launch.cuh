@@ -140,6 +140,29 @@ cudaError_t Launch<R>::expval_pass(const void *psi, int n, const PassDev &pass, 
 }
 
 template <typename R>
+cudaError_t Launch<R>::expval_obs_pass(const void *psi, int n, const PassDev &pass, const TermDev *terms,
+                                       const int32_t *obs_term_begin, int n_obs, double *partials, int grid,
+                                       cudaStream_t st) {
+  static bool attr[5] = {false, false, false, false, false};
+  const int smem = detail::tile_bytes(sizeof(c_t<R>), pass.T) + detail::lut_bytes(pass) + n_obs * detail::kWarps * 8;
+  const int na = pass.T > 8 ? 1 << (pass.T - 8) : 1;  // amplitudes per thread (kBlock = 256)
+  auto go = [&](auto kern, bool &done) {
+    detail::allow_big_smem(kern, done);
+    kern<<<grid, kBlock, smem, st>>>(reinterpret_cast<const g_t<R> *>(psi), n, pass, terms, obs_term_begin, n_obs,
+                                     partials);
+    return cudaGetLastError();
+  };
+  switch (na) {
+    case 1: return go(k_expval_obs<R, 1>, attr[0]);
+    case 2: return go(k_expval_obs<R, 2>, attr[1]);
+    case 4: return go(k_expval_obs<R, 4>, attr[2]);
+    case 8: return go(k_expval_obs<R, 8>, attr[3]);
+    case 16: return go(k_expval_obs<R, 16>, attr[4]);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <typename R>
 cudaError_t Launch<R>::lambda_pass(const void *phi, void *lam, int n, const PassDev &pass,
                                    const TermDev *terms, const int32_t *obs_term_begin, int n_obs,
                                    int first, int grid, cudaStream_t st) {

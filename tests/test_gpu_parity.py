@@ -139,8 +139,10 @@ def test_empty_tape_leaves_the_state():
 # S5: expectation values
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("dtype", DTYPES)
-@pytest.mark.parametrize("n", [1, 3, 8, 13, 15])
+@pytest.mark.parametrize("n", [1, 3, 8, 9, 10, 13, 15])
 def test_pauli_sum_expvals(dtype, n):
+    # 43 words over 4 observables: complex128 sums them by observable (1, 2, 4 or 8
+    # amplitudes per thread at these sizes), complex64 by word
     rng = np.random.default_rng(n)
     obs = [random_hamiltonian(n, 40, rng, weights=tuple(range(1, min(n, 4) + 1))),
            [Term(0.5, ())],                                 # identity term
