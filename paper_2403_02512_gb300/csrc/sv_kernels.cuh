@@ -1329,9 +1329,46 @@ __global__ void __launch_bounds__(kBlock) k_expval(const g_t<R> *__restrict__ ps
 // Lambda initialisation (S6): lam_o += sum_{t in o} c_t P_t phi over the terms of
 // this pass (output-stationary: each lambda amplitude written once per pass).
 //   (P phi)_g = i^{ny} (-1)^{popcount((g ^ x) & z)} phi_{g ^ x}
+// Words are the outer loop over NA register sums per thread (the word's masks
+// and signed coefficients formed once per thread), as in k_expval_obs below.
 // blockIdx.y = observable within the chunk; first != 0 overwrites lam.
 // ---------------------------------------------------------------------------
-template <typename R>
+__device__ __forceinline__ float flip_sign(float v, uint32_t p) { return __int_as_float(__float_as_int(v) ^ (int)(p << 31)); }
+__device__ __forceinline__ double flip_sign(double v, uint32_t p) {
+  return __longlong_as_double(__double_as_longlong(v) ^ ((long long)p << 63));
+}
+__device__ __forceinline__ df flip_sign(df v, uint32_t p) { return df_make(flip_sign(v.h, p), flip_sign(v.l, p)); }
+
+// h[k] += i^{ny} c (-1)^{popcount((g[k] ^ x) & z)} s[l_k ^ x_l] for the words [t0, t1).
+template <typename R, int NA>
+__device__ __forceinline__ void pauli_rows(const c_t<R> *s, int A, const uint64_t (&g)[NA],
+                                           const TermDev *__restrict__ terms, int t0, int t1, R (&hx)[NA],
+                                           R (&hy)[NA]) {
+  using C = c_t<R>;
+  for (int t = t0; t < t1; ++t) {
+    const TermDev tm = terms[t];
+    // i^ny c b:  x += cx * (swap ? b.y : b.x),  y += cy * (swap ? b.x : b.y)
+    const int ny = tm.ny & 3;
+    const bool swap = (ny & 1) != 0;
+    const R c = R(tm.coeff);
+    const R cx = (ny == 1 || ny == 2) ? -c : c;
+    const R cy = ny >= 2 ? -c : c;
+    const uint32_t tpar = (uint32_t)__popcll(tm.xg & tm.zg) & 1u;
+#pragma unroll
+    for (int k = 0; k < NA; ++k) {
+      const int l = threadIdx.x + k * kBlock;
+      if (l < A) {
+        const C b = s[l ^ tm.xl];
+        const uint32_t par = ((uint32_t)__popcll(g[k] & tm.zg) & 1u) ^ tpar;
+        const R bx = flip_sign(b.x, par), by = flip_sign(b.y, par);
+        hx[k] = fma(cx, swap ? by : bx, hx[k]);
+        hy[k] = fma(cy, swap ? bx : by, hy[k]);
+      }
+    }
+  }
+}
+
+template <typename R, int NA>
 __global__ void __launch_bounds__(kBlock) k_lambda(const g_t<R> *__restrict__ phi, g_t<R> *__restrict__ lam_base,
                                                     int n, const PassDev pass, const TermDev *__restrict__ terms,
                                                     const int32_t *__restrict__ obs_term_begin, int first) {
@@ -1356,29 +1393,31 @@ __global__ void __launch_bounds__(kBlock) k_lambda(const g_t<R> *__restrict__ ph
     tg.base = tile_base(pass, tile);
     load_tile<R>(phi, s, tg);
     __syncthreads();
-    for (int l = threadIdx.x; l < A; l += blockDim.x) {
-      const uint64_t g = tg.gidx(l);
-      C acc;
-      if (first) {
-        acc.x = R(0);
-        acc.y = R(0);
-      } else {
-        acc = to_c<R>(lam[g]);
-      }
-      for (int t = t0; t < t1; ++t) {
-        const TermDev tm = terms[t];
-        const C b = s[l ^ tm.xl];
-        const int par = __popcll((g ^ tm.xg) & tm.zg) & 1;
-        const R c = par ? R(-tm.coeff) : R(tm.coeff);
-        // i^ny * c * b
-        switch (tm.ny & 3) {
-          case 0: acc.x = fma(c, b.x, acc.x); acc.y = fma(c, b.y, acc.y); break;
-          case 1: acc.x = fma(-c, b.y, acc.x); acc.y = fma(c, b.x, acc.y); break;
-          case 2: acc.x = fma(-c, b.x, acc.x); acc.y = fma(-c, b.y, acc.y); break;
-          default: acc.x = fma(c, b.y, acc.x); acc.y = fma(-c, b.x, acc.y); break;
+    uint64_t g[NA];
+    R hx[NA], hy[NA];
+#pragma unroll
+    for (int k = 0; k < NA; ++k) {
+      const int l = threadIdx.x + k * kBlock;
+      g[k] = l < A ? tg.gidx(l) : 0;
+      hx[k] = R(0);
+      hy[k] = R(0);
+    }
+    pauli_rows<R, NA>(s, A, g, terms, t0, t1, hx, hy);
+#pragma unroll
+    for (int k = 0; k < NA; ++k) {
+      const int l = threadIdx.x + k * kBlock;
+      if (l < A) {
+        C acc;
+        if (first) {
+          acc.x = hx[k];
+          acc.y = hy[k];
+        } else {
+          acc = to_c<R>(lam[g[k]]);
+          acc.x = acc.x + hx[k];
+          acc.y = acc.y + hy[k];
         }
+        lam[g[k]] = to_g<R>(acc);
       }
-      lam[g] = to_g<R>(acc);
     }
     __syncthreads();
   }
@@ -1392,15 +1431,9 @@ __global__ void __launch_bounds__(kBlock) k_lambda(const g_t<R> *__restrict__ ph
 // per word.  Words are the outer loop, so a word's masks and signed
 // coefficients are formed once per thread for its NA amplitudes.  The sign
 // (-1)^{popcount((g ^ x) & z)} = (-1)^{popcount(g & z)} (-1)^{popcount(x & z)}
-// is applied by flipping the sign bits of the partner amplitude.
+// is applied by flipping the sign bits of the partner amplitude (pauli_rows).
 // partials[block * n_obs + o].
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float flip_sign(float v, uint32_t p) { return __int_as_float(__float_as_int(v) ^ (int)(p << 31)); }
-__device__ __forceinline__ double flip_sign(double v, uint32_t p) {
-  return __longlong_as_double(__double_as_longlong(v) ^ ((long long)p << 63));
-}
-__device__ __forceinline__ df flip_sign(df v, uint32_t p) { return df_make(flip_sign(v.h, p), flip_sign(v.l, p)); }
-
 template <typename R, int NA>
 __global__ void __launch_bounds__(kBlock) k_expval_obs(const g_t<R> *__restrict__ psi, int n, const PassDev pass,
                                                         const TermDev *__restrict__ terms,
@@ -1444,27 +1477,7 @@ __global__ void __launch_bounds__(kBlock) k_expval_obs(const g_t<R> *__restrict_
         hx[k] = R(0);
         hy[k] = R(0);
       }
-      for (int t = t0; t < t1; ++t) {
-        const TermDev tm = terms[t];
-        // i^ny c b:  x += cx * (swap ? b.y : b.x),  y += cy * (swap ? b.x : b.y)
-        const int ny = tm.ny & 3;
-        const bool swap = (ny & 1) != 0;
-        const R c = R(tm.coeff);
-        const R cx = (ny == 1 || ny == 2) ? -c : c;
-        const R cy = ny >= 2 ? -c : c;
-        const uint32_t tpar = (uint32_t)__popcll(tm.xg & tm.zg) & 1u;
-#pragma unroll
-        for (int k = 0; k < NA; ++k) {
-          const int l = threadIdx.x + k * kBlock;
-          if (l < A) {
-            const C b = s[l ^ tm.xl];
-            const uint32_t par = ((uint32_t)__popcll(g[k] & tm.zg) & 1u) ^ tpar;
-            const R bx = flip_sign(b.x, par), by = flip_sign(b.y, par);
-            hx[k] = fma(cx, swap ? by : bx, hx[k]);
-            hy[k] = fma(cy, swap ? bx : by, hy[k]);
-          }
-        }
-      }
+      pauli_rows<R, NA>(s, A, g, terms, t0, t1, hx, hy);
       Acc<R> acc;
 #pragma unroll
       for (int k = 0; k < NA; ++k) {

@@ -166,13 +166,24 @@ template <typename R>
 cudaError_t Launch<R>::lambda_pass(const void *phi, void *lam, int n, const PassDev &pass,
                                    const TermDev *terms, const int32_t *obs_term_begin, int n_obs,
                                    int first, int grid, cudaStream_t st) {
-  static bool attr = false;
-  detail::allow_big_smem(k_lambda<R>, attr);
+  static bool attr[5] = {false, false, false, false, false};
   const int smem = detail::tile_bytes(sizeof(c_t<R>), pass.T) + detail::lut_bytes(pass);
+  const int na = pass.T > 8 ? 1 << (pass.T - 8) : 1;  // amplitudes per thread (kBlock = 256)
   dim3 g(grid, n_obs);
-  k_lambda<R><<<g, kBlock, smem, st>>>(reinterpret_cast<const g_t<R> *>(phi), reinterpret_cast<g_t<R> *>(lam),
-                                        n, pass, terms, obs_term_begin, first);
-  return cudaGetLastError();
+  auto go = [&](auto kern, bool &done) {
+    detail::allow_big_smem(kern, done);
+    kern<<<g, kBlock, smem, st>>>(reinterpret_cast<const g_t<R> *>(phi), reinterpret_cast<g_t<R> *>(lam), n, pass,
+                                  terms, obs_term_begin, first);
+    return cudaGetLastError();
+  };
+  switch (na) {
+    case 1: return go(k_lambda<R, 1>, attr[0]);
+    case 2: return go(k_lambda<R, 2>, attr[1]);
+    case 4: return go(k_lambda<R, 4>, attr[2]);
+    case 8: return go(k_lambda<R, 8>, attr[3]);
+    case 16: return go(k_lambda<R, 16>, attr[4]);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 template <typename R>
