@@ -229,7 +229,9 @@ sv_status sv_apply_matrix(sv_state *s, const int *wires, int k, const double *ma
 
 /* out[j] = <psi|H_j|psi> for j < n_obs (Sec. 2.2), FP64 accumulation (complex64:
  * compensated FP32 per thread, FP64 across threads), fixed summation order:
- * repeated calls give bitwise-equal results. */
+ * repeated calls give bitwise-equal results.  complex128 Hamiltonians of many
+ * words (on average >= 4 per observable, <= 64 observables) are summed as
+ * Re<psi|(H_j psi)> with (H_j psi) formed per amplitude in FP64 registers. */
 sv_status sv_expval(sv_state *s, const sv_pauli_sum *obs, int n_obs, double *out);
 
 /* out = <psi|psi> in FP64. */
