@@ -57,7 +57,7 @@ typedef enum {
     SV_ERR_OOM = 2,          /* device allocation failed or exceeds the allocation cap */
     SV_ERR_CUDA = 3,         /* a CUDA runtime call failed */
     SV_ERR_TIMEOUT = 4,      /* a bounded device-side wait gave up */
-    SV_ERR_UNSUPPORTED = 5,  /* valid request this build does not implement */
+    SV_ERR_UNSUPPORTED = 5,  /* valid request the library does not implement */
     SV_ERR_STATE = 6         /* an earlier asynchronous device error is latched; sv_reset clears it */
 } sv_status;
 
@@ -412,7 +412,7 @@ sv_status sv_batch_info(const sv_batch *b, int64_t *work_items, int *ctas, int *
                         int *graph);
 
 /* Host-only planner query (no GPU needed): number of fused forward passes and
- * adjoint passes this build would use for a tape on n qubits and dtype. */
+ * adjoint passes the library would use for a tape on n qubits and dtype. */
 sv_status sv_plan_query(int n, sv_dtype dtype, const sv_tape *tape,
                         int *n_forward_passes, int *n_adjoint_passes);
 
