@@ -113,3 +113,14 @@ def test_plan_describe_counts_are_consistent_with_pass_counts():
         fwd, adj = L.sv_plan_describe(10, L.SV_C128, tape)
         f, a = L.sv_plan_query(10, L.SV_C128, tape)
         assert fwd["passes"] + fwd["wide_dense"] == f and adj["passes"] + adj["wide_dense"] == a
+
+
+def test_plan_describe_dense_blocks_of_the_30_qubit_workload_are_wide_steps():
+    # four 5-qubit dense blocks: steps outside the tiles in both plans; the
+    # 290 CZ gates of the brick are diagonal micro-ops; all 600 RY are trained
+    c, _ = ry_cz_brick(30, 20)
+    for dt in (L.SV_C64, L.SV_C128):
+        fwd, adj = L.sv_plan_describe(30, dt, L.Tape(c.ops, c.n_params))
+        assert fwd["wide_dense"] == 4 and adj["wide_dense"] == 4
+        assert fwd["diag"] == 290 and adj["diag"] == 290
+        assert fwd["dense"] == 0 and adj["dense"] == 0 and adj["multi"] == 0
