@@ -209,7 +209,7 @@ sv_status sv_get_state(sv_state *s, void *host_amplitudes);
 /* Wait for all work issued on the state's stream; reports latched device errors. */
 sv_status sv_synchronize(sv_state *s);
 
-/* ---- gates (S1-S3) ---------------------------------------------------------- */
+/* ---- gates ------------------------------------------------------------------ */
 
 /* Apply one base gate (Sec. 2.1.1, Alg. 1; Listing 1 inverse flag):
  * wires = its n_targets target wires, angles = its angles (NULL if none). */
@@ -225,7 +225,7 @@ sv_status sv_apply_op(sv_state *s, const sv_op *op, const double *params,
  * to the k wires (Sec. 2.1.2, generic many-qubit gate). */
 sv_status sv_apply_matrix(sv_state *s, const int *wires, int k, const double *matrix, int adjoint);
 
-/* ---- measurements (S5) -------------------------------------------------------- */
+/* ---- measurements ------------------------------------------------------------ */
 
 /* out[j] = <psi|H_j|psi> for j < n_obs (Sec. 2.2), FP64 accumulation (complex64:
  * compensated FP32 per thread, FP64 across threads), fixed summation order:
@@ -267,10 +267,10 @@ sv_status sv_probs(sv_state *s, const int *wires, int k, double *out);
  * [0, 1), bad wires or shots < 0; the state is not modified. */
 sv_status sv_sample(sv_state *s, const int *wires, int k, const double *uniforms, int64_t shots, uint64_t *out);
 
-/* ---- circuits (S4, S6-S8) ----------------------------------------------------- */
+/* ---- circuits ---------------------------------------------------------------- */
 
 /* psi <- U_N ... U_1 psi for the tape with the given parameters.  Ops are fused
- * into shared-memory passes (gate fusion, S4) without changing the result
+ * into shared-memory passes (gate fusion) without changing the result
  * beyond rounding. */
 sv_status sv_forward(sv_state *s, const sv_tape *tape, const double *params);
 
@@ -337,7 +337,7 @@ sv_status sv_program_vjp(sv_program *p, const double *grad_out, double *vjp_out,
  * parameters never set. */
 sv_status sv_program_jvp(sv_program *p, const double *tangent, double *jvp_out, int outputs_on_device);
 
-/* ---- sparse observables (NEXT-4) ----------------------------------------------
+/* ---- sparse observables -----------------------------------------------------
  * A general sparse observable in CSR form (the SparseHamiltonian the paper's
  * GPU device accepts for expectation values and the adjoint method, Sec. 2.2):
  * indptr[0..2^n] (indptr[0] = 0, non-decreasing, indptr[2^n] = nnz), column
@@ -376,7 +376,7 @@ sv_status sv_kernel_timing_enable(int enable);
 sv_status sv_kernel_timing_reset(void);
 sv_status sv_kernel_timing_read(double *total_ms, int64_t *launches);
 
-/* ---- batched circuits (S9) ---------------------------------------------------------- */
+/* ---- batched circuits ------------------------------------------------------------- */
 
 typedef struct sv_batch sv_batch; /* opaque: many circuits in one persistent launch */
 

@@ -776,7 +776,7 @@ void lower_fused(int n, const std::vector<HOp> &ops, const std::vector<int> &mem
   out.push_back(o);
 }
 
-// Greedy order-preserving fusion (S4): gates join the current pass while the
+// Greedy order-preserving fusion: gates join the current pass while the
 // union of the local bits they need (non-diagonal targets) plus the lowest
 // index bits fits in T bits.  The lowest bits are always local, so every tile
 // is read as runs of >= 2^nlow_pref consecutive amplitudes (coalesced, and
@@ -1762,7 +1762,7 @@ sv_status run_expval(sv_program *p, const void *psi, const JacWs &w) {
   return after_launch(s, e, "combine terms");
 }
 
-// One backward sweep (S6 + S7) for mcc lambdas, written into contrib columns
+// One backward sweep (lambda initialisation and reverse passes) for mcc lambdas, written into contrib columns
 // [j0, j0 + mcc) (leading dimension ldc).  lam_begin(q) gives the per-observable
 // term ranges of expectation pass q in lam_terms.
 template <typename BeginFn>
@@ -2003,7 +2003,7 @@ sv_status sync_state(sv_state *s) {
 }  // namespace
 
 
-// ---- batched circuits (S9) ----------------------------------------------------------
+// ---- batched circuits ---------------------------------------------------------------
 struct sv_batch {
   sv_dtype dt = SV_C64;
   cudaStream_t stream = nullptr;

@@ -177,7 +177,7 @@ cudaError_t inclusive_scan(double *x, int64_t m, double *scratch, cudaStream_t s
 cudaError_t probs_combine(const double *partials, int64_t bins, int per_bin, double *out, cudaStream_t st);
 cudaError_t sample_cdf(const double *cdf, int64_t m, const double *u, int64_t shots, uint64_t *out, cudaStream_t st);
 
-// ---- batched circuits (S9) --------------------------------------------------
+// ---- batched circuits -------------------------------------------------------
 // One circuit of a batch: its passes, its Z-only observable and its state slice.
 struct BatchCircuit {
   int32_t n;

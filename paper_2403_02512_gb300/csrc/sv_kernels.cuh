@@ -696,7 +696,7 @@ __device__ __forceinline__ void apply_op(c_t<R> *s, const TileGeom &tg, const Op
 }
 
 // ---------------------------------------------------------------------------
-// Forward pass kernel (S1-S4): load tile, apply the pass's micro-ops, store.
+// Forward pass kernel: load tile, apply the pass's micro-ops, store.
 // A barrier separates micro-ops whose thread-to-amplitude maps differ; runs of
 // diagonal micro-ops and the blocks of one gate need none (each thread keeps
 // the same amplitudes, or the blocks are disjoint).
@@ -875,7 +875,7 @@ __global__ void __launch_bounds__(kBlock) k_tile_tangent(g_t<R> *__restrict__ ps
 }
 
 // ---------------------------------------------------------------------------
-// Adjoint pass kernel (S7).  For the pass's micro-ops in reverse order:
+// Adjoint pass kernel.  For the pass's micro-ops in reverse order:
 //   acc[op, j] += Im <lambda_j | G phi>   (before the op is un-applied),
 //   phi <- E phi, lambda_j <- E lambda_j   (E = U^dagger, stored by the builder).
 // One CTA holds a phi tile and b lambda tiles in shared memory, so phi is
@@ -1258,7 +1258,7 @@ __global__ void __launch_bounds__(kBlock, (std::is_same<R, double>::value && B >
 }
 
 // ---------------------------------------------------------------------------
-// Expectation values (S5): for every term t placed in this pass,
+// Expectation values: for every term t placed in this pass,
 //   <P_t> partial = sum_l Re( i^{ny} (-1)^{popcount((g ^ x) & z)} conj(psi_g) psi_{g ^ x} )
 // over the tile (P|i> = i^{ny} (-1)^{popcount(i & z)} |i ^ x>).  x lies inside
 // the local bits, so both amplitudes are in the tile.  Term coefficients are
@@ -1326,7 +1326,7 @@ __global__ void __launch_bounds__(kBlock) k_expval(const g_t<R> *__restrict__ ps
 }
 
 // ---------------------------------------------------------------------------
-// Lambda initialisation (S6): lam_o += sum_{t in o} c_t P_t phi over the terms of
+// Lambda initialisation: lam_o += sum_{t in o} c_t P_t phi over the terms of
 // this pass (output-stationary: each lambda amplitude written once per pass).
 //   (P phi)_g = i^{ny} (-1)^{popcount((g ^ x) & z)} phi_{g ^ x}
 // Words are the outer loop over NA register sums per thread (the word's masks
@@ -1424,7 +1424,7 @@ __global__ void __launch_bounds__(kBlock) k_lambda(const g_t<R> *__restrict__ ph
 }
 
 // ---------------------------------------------------------------------------
-// Expectation values by observable (S5 for Hamiltonians of many words): for
+// Expectation values by observable (Hamiltonians of many words): for
 // each amplitude g of the tile, (H_o psi)_g over the words of observable o
 // placed in this pass is accumulated in registers, then Re(conj(psi_g)
 // (H_o psi)_g) is summed: one reduction per observable and tile instead of one
@@ -2183,7 +2183,7 @@ __global__ void k_set_basis(g_t<R> *psi, uint64_t N, uint64_t index) {
 }
 
 // ---------------------------------------------------------------------------
-// Batched circuits (S9): one persistent launch drains a queue of work items
+// Batched circuits: one persistent launch drains a queue of work items
 // (circuit, pass, tile).  Items are numbered so that every tile of pass p of a
 // circuit precedes every tile of its pass p + 1; a CTA holding an item of pass
 // p + 1 waits (bounded, %globaltimer) until all tiles of pass p are done.  An

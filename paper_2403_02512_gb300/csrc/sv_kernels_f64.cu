@@ -1,5 +1,5 @@
 // complex128 instantiation of the state-vector kernels, plus the
-// precision-independent deterministic reductions (S8).
+// precision-independent deterministic reductions.
 #include "sv_launch.cuh"
 
 namespace sv {

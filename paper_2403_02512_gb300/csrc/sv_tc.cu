@@ -1,6 +1,6 @@
-// Tensor-core path for a dense 5-qubit block on a complex64 state (S3: a
-// user matrix on 5 wires, 32 x 32 complex, applied to every group of 32
-// amplitudes that share the other index bits).
+// Tensor-core path for a dense 5-qubit block on a complex64 state (a user
+// matrix on 5 wires, 32 x 32 complex, applied to every group of 32 amplitudes
+// that share the other index bits; Sec. 2.1.2's generic many-qubit gate).
 //
 // As a real GEMM per tile of 128 groups:  D (128 x 64) = X (128 x 64) * Ur^T,
 // where row g of X holds group g's 32 amplitudes (real and imaginary parts)

@@ -59,7 +59,7 @@ def _assert_rel(got, want, tol, what):
 
 
 # ---------------------------------------------------------------------------
-# S1-S3: every gate, every wire, controls, adjoint flag
+# gates: every gate, every wire, controls, adjoint flag
 # ---------------------------------------------------------------------------
 GATES = [g for g in GATE_ARITY if g != "Identity"]
 
@@ -117,7 +117,7 @@ def test_dense_matrix_blocks(dtype, k):
 
 
 # ---------------------------------------------------------------------------
-# S4: fused forward passes
+# fused forward passes
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("dtype", DTYPES)
 @pytest.mark.parametrize("n,seed", [(3, 1), (7, 2), (12, 3), (14, 4)])
@@ -136,7 +136,7 @@ def test_empty_tape_leaves_the_state():
 
 
 # ---------------------------------------------------------------------------
-# S5: expectation values
+# expectation values
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("dtype", DTYPES)
 @pytest.mark.parametrize("n", [1, 3, 8, 9, 10, 13, 15])
@@ -165,7 +165,7 @@ def test_expvals_repeat_bitwise():
 
 
 # ---------------------------------------------------------------------------
-# S6-S8: adjoint Jacobian, VJP, autograd
+# adjoint Jacobian, VJP, autograd
 # ---------------------------------------------------------------------------
 def _obs_for(n, rng):
     return [random_hamiltonian(n, 5, rng, weights=tuple(range(1, min(n, 3) + 1))),

@@ -142,7 +142,7 @@ def _z(w: int) -> List[Term]:
 
 
 # ---------------------------------------------------------------------------
-# Workload 1: layered RX/RY/RZ + CNOT ladder
+# Layered RX/RY/RZ + CNOT ladder
 # ---------------------------------------------------------------------------
 def layered_circuit(n: int = 12, layers: int = 10, seed: int | None = None):
     """RX, RY, RZ on every wire then CNOT(i, i+1) per layer; O = sum_i Z_i.
@@ -165,7 +165,7 @@ def layered_circuit(n: int = 12, layers: int = 10, seed: int | None = None):
 
 
 # ---------------------------------------------------------------------------
-# Workload 2: strongly-entangling layers
+# Strongly-entangling layers
 # ---------------------------------------------------------------------------
 def strongly_entangling(n: int = 24, layers: int = 8, seed: int | None = None):
     """Rot(phi, theta, omega) per wire then CNOT(i, (i+r) mod n), r = l mod (n-1) + 1.
@@ -188,7 +188,7 @@ def strongly_entangling(n: int = 24, layers: int = 8, seed: int | None = None):
 
 
 # ---------------------------------------------------------------------------
-# Workload 3: QAOA MaxCut
+# QAOA MaxCut
 # ---------------------------------------------------------------------------
 def regular_graph(n: int, rng: np.random.Generator, degree: int = 3):
     """Seeded simple graph with every vertex of degree 3.
@@ -262,7 +262,7 @@ def qaoa_mixed_instances(count: int = 256, nmin: int = 14, nmax: int = 22, p: in
 
 
 # ---------------------------------------------------------------------------
-# Workload 4: VQE-shaped Givens ansatz
+# VQE-shaped Givens ansatz
 # ---------------------------------------------------------------------------
 def random_hamiltonian(n: int, n_terms: int, rng: np.random.Generator,
                        weights=(2, 3, 4), letters="XYZ") -> List[Term]:
@@ -317,7 +317,7 @@ def vqe_givens(n: int = 24, electrons: int = 12, n_singles: int = 40, n_doubles:
 
 
 # ---------------------------------------------------------------------------
-# Workload 5: RY layers + CZ brick
+# RY layers + CZ brick
 # ---------------------------------------------------------------------------
 def dense_block_wires(n: int, b: int) -> Tuple[int, ...]:
     """Wires of the b-th 5-qubit dense block of :func:`ry_cz_brick` (n >= 10):
