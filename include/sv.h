@@ -411,6 +411,23 @@ sv_status sv_batch_autotune(sv_batch *b, double *best_ms);
 sv_status sv_batch_info(const sv_batch *b, int64_t *work_items, int *ctas, int *tile_bits, int64_t *wave_bytes,
                         int *graph);
 
+/* ---- Hermitian observables ------------------------------------------------------ */
+
+/* Host-only (no GPU needed): the Pauli words of a Hermitian 2^k x 2^k matrix A
+ * on k wires (an observable given as a matrix, Sec. 2.2), so that sv_expval,
+ * sv_var, sv_adjoint_jacobian and the program calls measure it as the
+ * Hamiltonian sum_P c_P P.  matrix: host, row-major, interleaved re/im, its
+ * index bit k-1-j belonging to wires[j] (wires[0] most significant).
+ * c_P = Tr(P A) / 2^k over the 4^k words on the k wires; words with
+ * |c_P| <= tol are left out.  coeffs, x_masks, z_masks: caller-owned host
+ * arrays of 4^k entries, filled with *n_terms words in sv_pauli_sum form (bit w
+ * of a mask is wire w).  SV_ERR_ARG for n outside 1..63, k outside
+ * 1..SV_MAX_HERMITIAN_WIRES, wires out of range or repeated, non-finite
+ * entries, tol < 0, or A not Hermitian within 1e-12 * max(1, max |A_rc|). */
+#define SV_MAX_HERMITIAN_WIRES 5
+sv_status sv_hermitian_to_pauli(int n, const int *wires, int k, const double *matrix, double tol, double *coeffs,
+                                uint64_t *x_masks, uint64_t *z_masks, int *n_terms);
+
 /* Host-only planner query (no GPU needed): number of fused forward passes and
  * adjoint passes the library would use for a tape on n qubits and dtype. */
 sv_status sv_plan_query(int n, sv_dtype dtype, const sv_tape *tape,

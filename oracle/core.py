@@ -333,6 +333,19 @@ class CSRObservable:
         return out
 
 
+class MatrixObservable:
+    """An observable given as a Hermitian 2^k x 2^k matrix on k wires (wires[0]
+    = the matrix's most significant index bit), identity elsewhere: A psi is
+    the plain dense application of the matrix to every group of amplitudes."""
+
+    def __init__(self, wires, matrix):
+        self.wires = [int(w) for w in wires]
+        self.matrix = np.array(matrix, dtype=np.complex128)
+
+    def apply(self, psi: np.ndarray) -> np.ndarray:
+        return apply_matrix(copy(psi), self.matrix, self.wires)
+
+
 def apply_hamiltonian(psi: np.ndarray, terms) -> np.ndarray:
     """out = sum_t c_t P_t psi (or H psi for a sparse observable)."""
     if hasattr(terms, "apply"):

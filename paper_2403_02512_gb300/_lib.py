@@ -11,7 +11,7 @@ from __future__ import annotations
 
 import ctypes
 import os
-from typing import Optional, Sequence
+from typing import NamedTuple, Optional, Sequence, Tuple
 
 import numpy as np
 
@@ -127,6 +127,8 @@ PROTOTYPES = {
     "sv_program_stats": (ctypes.c_int, [_vp, _ip, _ip, _ip]),
     "sv_plan_query": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(SvTape), _ip, _ip]),
     "sv_plan_describe": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(SvTape), _ip, _ip]),
+    "sv_hermitian_to_pauli": (ctypes.c_int, [ctypes.c_int, _ip, ctypes.c_int, _dp, ctypes.c_double, _dp,
+                                             ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64), _ip]),
     "sv_kernel_timing_enable": (ctypes.c_int, [ctypes.c_int]),
     "sv_kernel_timing_reset": (ctypes.c_int, []),
     "sv_kernel_timing_read": (ctypes.c_int, [_dp, ctypes.POINTER(ctypes.c_int64)]),
@@ -424,6 +426,43 @@ def sv_plan_describe(n: int, dtype: int, tape: "Tape"):
     a = (ctypes.c_int * 8)()
     _check(load().sv_plan_describe(int(n), int(dtype), ctypes.byref(tape.struct), f, a))
     return dict(zip(PLAN_KINDS, list(f))), dict(zip(PLAN_KINDS, list(a)))
+
+
+SV_MAX_HERMITIAN_WIRES = 5
+
+
+class PauliTerm(NamedTuple):
+    """One word of a Hamiltonian: coeff * prod over (wire, letter) of the Pauli letter."""
+    coeff: float
+    paulis: Tuple[Tuple[int, str], ...]
+
+
+def sv_hermitian_to_pauli(n: int, wires, matrix, tol: float = 0.0):
+    """The Pauli words of a Hermitian matrix on ``wires`` (host only): a list of
+    PauliTerm usable wherever a Hamiltonian (list of terms) is accepted."""
+    w = np.ascontiguousarray(list(wires), dtype=np.int32)
+    k = int(w.size)
+    m = np.ascontiguousarray(np.asarray(matrix, dtype=np.complex128))
+    if k < 1 or m.shape != (1 << k, 1 << k):
+        raise SvError(1, "matrix must be 2^k x 2^k for k wires")
+    cap = 1 << (2 * k)
+    c = np.zeros(cap, dtype=np.float64)
+    x = np.zeros(cap, dtype=np.uint64)
+    z = np.zeros(cap, dtype=np.uint64)
+    cnt = ctypes.c_int()
+    _check(load().sv_hermitian_to_pauli(int(n), w.ctypes.data_as(_ip), k, m.view(np.float64).ctypes.data_as(_dp),
+                                        float(tol), c.ctypes.data_as(_dp),
+                                        x.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                        z.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), ctypes.byref(cnt)))
+    out = []
+    for t in range(cnt.value):
+        letters = []
+        for wire in range(n):
+            xb, zb = (int(x[t]) >> wire) & 1, (int(z[t]) >> wire) & 1
+            if xb or zb:
+                letters.append((wire, "Y" if xb and zb else ("X" if xb else "Z")))
+        out.append(PauliTerm(float(c[t]), tuple(letters)))
+    return out
 
 
 def sv_program_stats(ph: int):

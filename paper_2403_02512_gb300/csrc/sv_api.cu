@@ -3169,6 +3169,71 @@ sv_status sv_plan_query(int n, sv_dtype dtype, const sv_tape *tape, int *n_forwa
   return SV_OK;
 }
 
+// Pauli words of a Hermitian matrix on k wires.  Local index j of the matrix
+// has wires[0] as its most significant bit; a word with local flip mask x, sign
+// mask z and nY = popcount(x & z) acts as P|j> = i^nY (-1)^popcount(j & z) |j ^ x>,
+// so Tr(P A) = i^nY sum_j (-1)^popcount(j & z) A[j][j ^ x] and A = sum_P c_P P
+// with c_P = Tr(P A) / 2^k (the Pauli matrices are an orthogonal basis under
+// the trace inner product).
+sv_status sv_hermitian_to_pauli(int n, const int *wires, int k, const double *matrix, double tol, double *coeffs,
+                                uint64_t *x_masks, uint64_t *z_masks, int *n_terms) {
+  if (n < 1 || n > 63) return fail(SV_ERR_ARG, "n = %d out of range 1..63", n);
+  if (k < 1 || k > SV_MAX_HERMITIAN_WIRES)
+    return fail(SV_ERR_ARG, "a Hermitian observable takes 1..%d wires, got %d", SV_MAX_HERMITIAN_WIRES, k);
+  if (!wires || !matrix || !coeffs || !x_masks || !z_masks || !n_terms) return fail(SV_ERR_ARG, "NULL argument");
+  if (!(tol >= 0.0)) return fail(SV_ERR_ARG, "tol must be >= 0");
+  for (int j = 0; j < k; ++j) {
+    if (wires[j] < 0 || wires[j] >= n) return fail(SV_ERR_ARG, "wire %d out of range for %d qubits", wires[j], n);
+    for (int i = 0; i < j; ++i)
+      if (wires[i] == wires[j]) return fail(SV_ERR_ARG, "wire %d used twice", wires[j]);
+  }
+  const int D = 1 << k;
+  double amax = 0.0;
+  for (int e = 0; e < 2 * D * D; ++e) {
+    if (!std::isfinite(matrix[e])) return fail(SV_ERR_ARG, "matrix entry %d is not finite", e / 2);
+    amax = std::max(amax, std::fabs(matrix[e]));
+  }
+  for (int r = 0; r < D; ++r)
+    for (int c = 0; c <= r; ++c) {
+      const double *a = matrix + 2 * (r * D + c), *b = matrix + 2 * (c * D + r);
+      if (std::fabs(a[0] - b[0]) > 1e-12 * std::max(1.0, amax) || std::fabs(a[1] + b[1]) > 1e-12 * std::max(1.0, amax))
+        return fail(SV_ERR_ARG, "matrix is not Hermitian (entries (%d,%d) and (%d,%d))", r, c, c, r);
+    }
+  int cnt = 0;
+  for (int x = 0; x < D; ++x)
+    for (int z = 0; z < D; ++z) {
+      double re = 0.0, im = 0.0;  // sum_j (-1)^popcount(j & z) A[j][j ^ x]
+      for (int j = 0; j < D; ++j) {
+        const double *a = matrix + 2 * (j * D + (j ^ x));
+        const double sg = (popc((uint64_t)(j & z)) & 1) ? -1.0 : 1.0;
+        re += sg * a[0];
+        im += sg * a[1];
+      }
+      // times i^nY: the real part of the (real) coefficient
+      double c;
+      switch (popc((uint64_t)(x & z)) & 3) {
+        case 0: c = re; break;
+        case 1: c = -im; break;
+        case 2: c = -re; break;
+        default: c = im; break;
+      }
+      c /= (double)D;
+      if (std::fabs(c) <= tol) continue;
+      uint64_t xm = 0, zm = 0;
+      for (int j = 0; j < k; ++j) {
+        const int bit = k - 1 - j;  // local bit of wires[j]
+        if ((x >> bit) & 1) xm |= 1ull << wires[j];
+        if ((z >> bit) & 1) zm |= 1ull << wires[j];
+      }
+      coeffs[cnt] = c;
+      x_masks[cnt] = xm;
+      z_masks[cnt] = zm;
+      ++cnt;
+    }
+  *n_terms = cnt;
+  return SV_OK;
+}
+
 sv_status sv_plan_describe(int n, sv_dtype dtype, const sv_tape *tape, int forward_counts[SV_PLAN_KINDS],
                            int adjoint_counts[SV_PLAN_KINDS]) {
   Plan f, a;

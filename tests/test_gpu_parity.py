@@ -446,6 +446,31 @@ def test_variance_matches_oracle(dtype, n):
     assert np.array_equal(got, again)             # fixed-order reductions repeat bitwise
 
 
+# ---- observables given as Hermitian matrices ------------------------------------
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("n,wires", [(6, (2,)), (9, (8, 0)), (11, (3, 10, 5)), (12, (11, 6, 0, 2)),
+                                     (13, (12, 1, 7, 4, 0))])
+def test_hermitian_observables_as_pauli_words(dtype, n, wires):
+    # the matrix's Pauli words (host decomposition) through the Pauli-sum
+    # kernels, against the oracle applying the matrix itself
+    rng = np.random.default_rng(800 + n)
+    k = len(wires)
+    a = rng.normal(size=(1 << k, 1 << k)) + 1j * rng.normal(size=(1 << k, 1 << k))
+    A = (a + a.conj().T) / 2
+    H = L.sv_hermitian_to_pauli(n, wires, A)
+    want_obs = oracle.MatrixObservable(wires, A)
+    c, p = random_circuit(n, 30, 800 + n)
+    sv = StateVector(n, dtype)
+    prog = Program(sv, c.ops, c.n_params, [H])
+    prog.forward(p)
+    E, J = prog.jacobian()
+    Eo, Jo = oracle.adjoint_jacobian(c, p, [want_obs])
+    _assert_rel(E.cpu().numpy(), Eo, TOL_E[dtype], "expval")
+    _assert_rel(J.cpu().numpy(), Jo, TOL_J[dtype], "jacobian")
+    psi = oracle.forward(c, p)
+    _assert_rel(sv.var([H]), [oracle.variance(psi, want_obs)], TOL_E[dtype] * 10, "variance")
+
+
 # ---- probabilities and samples -----------------------------------------------
 def _wire_sets(n, rng):
     sets = [[], [0], [n - 1], list(range(n)), list(range(n))[::-1]]

@@ -5,6 +5,7 @@ without a GPU."""
 import os
 import re
 
+import numpy as np
 import pytest
 
 import paper_2403_02512_gb300 as svlib
@@ -124,3 +125,65 @@ def test_plan_describe_dense_blocks_of_the_30_qubit_workload_are_wide_steps():
         assert fwd["wide_dense"] == 4 and adj["wide_dense"] == 4
         assert fwd["diag"] == 290 and adj["diag"] == 290
         assert fwd["dense"] == 0 and adj["dense"] == 0 and adj["multi"] == 0
+
+
+# ---------------------------------------------------------------------------
+# Hermitian observables as Pauli words (host only)
+# ---------------------------------------------------------------------------
+def _terms_matrix(n, terms):
+    # sum_t c_t (x)_w P_w over all n wires, wire 0 leftmost (independent of the library)
+    pauli = {"I": np.eye(2), "X": np.array([[0, 1], [1, 0]]), "Y": np.array([[0, -1j], [1j, 0]]),
+             "Z": np.diag([1.0, -1.0])}
+    out = np.zeros((1 << n, 1 << n), dtype=np.complex128)
+    for t in terms:
+        letters = dict(t.paulis)
+        m = np.ones((1, 1))
+        for w in range(n):
+            m = np.kron(m, pauli[letters.get(w, "I")])
+        out += t.coeff * m
+    return out
+
+
+@pytest.mark.parametrize("n,wires,seed", [(3, (0,), 1), (4, (2, 0), 2), (5, (1, 4, 3), 3), (6, (5, 0, 2, 3), 4),
+                                          (5, (4, 2, 0, 3, 1), 5)])
+def test_hermitian_to_pauli_reconstructs_the_matrix(n, wires, seed):
+    from oracle import dense
+    rng = np.random.default_rng(seed)
+    k = len(wires)
+    a = rng.normal(size=(1 << k, 1 << k)) + 1j * rng.normal(size=(1 << k, 1 << k))
+    A = (a + a.conj().T) / 2
+    terms = L.sv_hermitian_to_pauli(n, wires, A)
+    assert 1 <= len(terms) <= 4 ** k
+    np.testing.assert_allclose(_terms_matrix(n, terms), dense.embed(n, list(wires), A), atol=1e-13)
+
+
+def test_hermitian_to_pauli_known_matrices():
+    proj1 = np.diag([0.0, 1.0])                                   # |1><1| = (I - Z) / 2
+    t = sorted(L.sv_hermitian_to_pauli(4, [2], proj1), key=lambda t: len(t.paulis))
+    assert [(x.coeff, x.paulis) for x in t] == [(0.5, ()), (-0.5, ((2, "Z"),))]
+    zx = np.kron(np.diag([1.0, -1.0]), np.array([[0, 1], [1, 0]]))  # Z on wire 3, X on wire 1
+    t = L.sv_hermitian_to_pauli(4, [3, 1], zx)
+    assert [(x.coeff, x.paulis) for x in t] == [(1.0, ((1, "X"), (3, "Z")))]
+    y = np.array([[0, -1j], [1j, 0]])
+    t = L.sv_hermitian_to_pauli(2, [0], y)
+    assert [(x.coeff, x.paulis) for x in t] == [(1.0, ((0, "Y"),))]
+
+
+def test_hermitian_to_pauli_rejects_bad_input():
+    with pytest.raises(L.SvError) as ei:
+        L.sv_hermitian_to_pauli(3, [0], np.array([[0, 1], [0, 0]]))   # not Hermitian
+    assert ei.value.status == 1 and "Hermitian" in str(ei.value)
+    for wires in ([0, 0], [3], [-1]):
+        with pytest.raises(L.SvError):
+            L.sv_hermitian_to_pauli(3, wires, np.eye(1 << len(wires)))
+    with pytest.raises(L.SvError):
+        L.sv_hermitian_to_pauli(8, list(range(6)), np.eye(64))       # more than 5 wires
+    with pytest.raises(L.SvError):
+        L.sv_hermitian_to_pauli(3, [0], np.eye(2), tol=-1.0)
+
+
+def test_hermitian_to_pauli_drops_words_at_or_below_tol():
+    A = np.diag([1.0, 1.0 + 1e-9])   # I (1 + 5e-10) - 5e-10 Z
+    assert len(L.sv_hermitian_to_pauli(2, [1], A)) == 2
+    t = L.sv_hermitian_to_pauli(2, [1], A, tol=1e-8)
+    assert len(t) == 1 and t[0].paulis == ()

@@ -412,6 +412,57 @@ def test_adjoint_through_a_controlled_dense_block_matches_the_exact_derivative()
     np.testing.assert_allclose(J, dense.exact_jacobian(c, p), atol=1e-12)
 
 
+# ---------------------------------------------------------------------------
+# Observables given as Hermitian matrices
+# ---------------------------------------------------------------------------
+def _random_hermitian(k, rng):
+    a = rng.normal(size=(1 << k, 1 << k)) + 1j * rng.normal(size=(1 << k, 1 << k))
+    return (a + a.conj().T) / 2
+
+
+@pytest.mark.parametrize("theta", [0.0, 0.4, 2.2, -1.3])
+def test_matrix_observable_projector_after_rx_closed_form(theta):
+    # |1><1| on wire 1 after RX(theta) there: probability sin^2(theta / 2)
+    c = Circuit(3, [Op("RX", (1,), (0,))], 1, [])
+    psi = oracle.forward(c, np.array([theta]))
+    proj = oracle.MatrixObservable([1], np.diag([0.0, 1.0]))
+    assert oracle.expval(psi, proj) == pytest.approx(math.sin(theta / 2) ** 2, abs=1e-15)
+
+
+def test_matrix_observable_of_a_pauli_word_equals_the_pauli_path():
+    # the Kronecker matrix of X (x) Y (x) Z on wires (4, 0, 2) against the
+    # per-wire Pauli application of the same word
+    n = 5
+    psi = random_state(n, 61)
+    m = np.kron(np.kron(oracle.PAULI["X"], oracle.PAULI["Y"]), oracle.PAULI["Z"])
+    word = [Term(1.0, ((4, "X"), (0, "Y"), (2, "Z")))]
+    got = oracle.expval(psi, oracle.MatrixObservable([4, 0, 2], m))
+    assert got == pytest.approx(oracle.expval(psi, word), abs=1e-14)
+    np.testing.assert_allclose(oracle.MatrixObservable([4, 0, 2], m).apply(psi),
+                               oracle.apply_hamiltonian(psi, word), atol=1e-15)
+
+
+def test_matrix_observable_expval_and_variance_match_dense_algebra():
+    n = 5
+    rng = np.random.default_rng(62)
+    A = _random_hermitian(3, rng)
+    wires = [3, 1, 4]
+    psi = random_state(n, 62)
+    full = dense.embed(n, wires, A)
+    obs = oracle.MatrixObservable(wires, A)
+    e = np.vdot(psi, full @ psi).real
+    assert oracle.expval(psi, obs) == pytest.approx(e, abs=1e-13)
+    assert oracle.variance(psi, obs) == pytest.approx(np.vdot(psi, full @ full @ psi).real - e * e, abs=1e-12)
+
+
+def test_adjoint_with_a_matrix_observable_matches_parameter_shift():
+    c, p = layered_circuit(5, 2, seed=63)
+    A = _random_hermitian(2, np.random.default_rng(63))
+    obs = [oracle.MatrixObservable([2, 0], A)]
+    _, J = oracle.adjoint_jacobian(c, p, obs)
+    np.testing.assert_allclose(J, oracle.param_shift_jacobian(c, p, obs), atol=1e-12)
+
+
 def test_vjp_is_gradient_weighted_jacobian_rows():
     c, p = strongly_entangling(4, 2, seed=5)
     g = np.random.default_rng(1).normal(size=len(c.observables))
