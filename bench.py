@@ -455,6 +455,31 @@ def extra_measurements(hbm_peak):
     return out
 
 
+def extra_layered12():
+    """12-qubit layered RX/RY/RZ + CNOT ladder, O = sum_i Z_i, complex128:
+    forward + expval + full adjoint Jacobian (360 parameters).  The state is
+    64 KiB, so the step is bound by launch and pass latency, not HBM: reported
+    in microseconds per step (its parity with the oracle is a test case)."""
+    import torch
+    from paper_2403_02512_gb300.torch_api import Program, StateVector
+    from workloads import layered_circuit
+    c, p = layered_circuit(12, 10)
+    sv = StateVector(12, "c128")
+    prog = Program.from_circuit(sv, c)
+
+    def step():
+        prog.forward(p)
+        return prog.jacobian()
+
+    for _ in range(3):
+        step()
+    ms = _timed(step, 50, torch.cuda.current_stream())
+    out = {"us_forward_and_jacobian": ms * 1e3, "forward_passes": prog.stats()[0], "adjoint_passes": prog.stats()[1]}
+    prog.close()
+    sv.close()
+    return out
+
+
 def extra_rycz30():
     """30-qubit RY layers + CZ brick + a 5-qubit dense block after every fifth
     layer, <Z0 Z29>: forward + full adjoint Jacobian (600 params).  The dense
@@ -643,6 +668,10 @@ def run_ours(args):
             extras["qaoa_batched"] = extra_qaoa()
             extras["vqe24_2000_terms"] = extra_vqe()
             extras["rycz30"] = extra_rycz30()
+            try:
+                extras["layered12"] = extra_layered12()
+            except Exception as exc:  # an extra never takes the bench line down
+                extras["layered12"] = {"error": repr(exc)}
             extras["measurements_sel24"] = extra_measurements(hbm_peak)
 
     cpu = None
