@@ -33,6 +33,7 @@ from __future__ import annotations
 
 import ctypes
 import math
+import time
 from typing import List, Sequence, Tuple
 
 import numpy as np
@@ -451,13 +452,24 @@ def _step_matrix(st: _Step, params) -> np.ndarray:
     return M.conj().T.copy() if st.adjoint else M
 
 
-def adjoint_jacobian(circuit, params: np.ndarray, observables=None, psi_final=None):
-    """(E, J): E[j] = <psi|O_j|psi>, J[j, p] = dE_j / dparams[p]  (adjoint method)."""
+def adjoint_jacobian(circuit, params: np.ndarray, observables=None, psi_final=None, clock=None):
+    """(E, J): E[j] = <psi|O_j|psi>, J[j, p] = dE_j / dparams[p]  (adjoint method).
+
+    ``clock``: an optional dict; wall seconds are added under "forward",
+    "lambda" (lambda_j = O_j phi and E), "phi" (mu = G phi and phi's
+    un-apply: the work done once) and "rows" (inner products and the lambdas'
+    un-apply: the work done once per observable)."""
     obs = circuit.observables if observables is None else observables
     steps = expand(circuit.ops)
+    t = {"forward": 0.0, "lambda": 0.0, "phi": 0.0, "rows": 0.0}
+    t0 = time.perf_counter()
     phi = forward(circuit, params) if psi_final is None else copy(psi_final)
+    t1 = time.perf_counter()
+    t["forward"] += t1 - t0
     lams = [apply_hamiltonian(phi, H) for H in obs]
     E = np.array([inner(phi, lam).real for lam in lams])
+    t0 = time.perf_counter()
+    t["lambda"] += t0 - t1
     J = np.zeros((len(obs), circuit.n_params))
     for st in reversed(steps):
         M = _step_matrix(st, params)
@@ -469,12 +481,24 @@ def adjoint_jacobian(circuit, params: np.ndarray, observables=None, psi_final=No
             apply_matrix(mu, G, st.wires, st.controls, st.cvals)
             if st.controls:
                 project_controls(mu, st.controls, st.cvals)
+            t1 = time.perf_counter()
+            t["phi"] += t1 - t0
             for j, lam in enumerate(lams):
                 J[j, st.param] += st.scale * (-2.0 * s) * inner(lam, mu).imag
+            del mu  # three vectors at a time (phi, lambda, mu), not four
+            t0 = time.perf_counter()
+            t["rows"] += t0 - t1
         Md = M.conj().T.copy()
         apply_matrix(phi, Md, st.wires, st.controls, st.cvals)
+        t1 = time.perf_counter()
+        t["phi"] += t1 - t0
         for lam in lams:
             apply_matrix(lam, Md, st.wires, st.controls, st.cvals)
+        t0 = time.perf_counter()
+        t["rows"] += t0 - t1
+    if clock is not None:
+        for k, v in t.items():
+            clock[k] = clock.get(k, 0.0) + v
     return E, J
 
 
