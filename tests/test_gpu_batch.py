@@ -3,8 +3,8 @@
 Mixed qubit counts, repeated tapes with different parameter sets (QAOA
 MaxCut), basis-state starts, empty tapes, and the bounded-wait failure path
 (a pass whose completion is never published must end in SV_ERR_TIMEOUT, not a
-hang).  Tolerances as in test_gpu_parity: 1e-10 relative (complex128),
-1e-4 (complex64 gate arithmetic with FP64 reductions).
+hang).  Bars as in tests/bars.py: complex128 1e-10 entry-wise relative with a
+1e-3 floor, complex64 1e-4 normwise.
 """
 
 import dataclasses
@@ -15,6 +15,7 @@ import sys
 import numpy as np
 import pytest
 
+import bars
 import oracle
 from workloads import Circuit, Op, Term, qaoa_maxcut, qaoa_mixed_instances, random_circuit
 
@@ -26,7 +27,7 @@ if not torch.cuda.is_available():  # pragma: no cover
 
 from paper_2403_02512_gb300 import _lib as L  # noqa: E402
 
-TOL = {L.SV_C128: 1e-10, L.SV_C64: 1e-4}
+NAME = {L.SV_C128: "c128", L.SV_C64: "c64"}
 
 
 def _z_observable(n, rng, k=6):
@@ -54,7 +55,7 @@ def test_mixed_random_circuits_match_oracle(dtype):
     for _ in range(2):  # second run replays the captured graph
         got = b.run()
         want = np.array([oracle.expval(oracle.forward(c, p), c.observables[0]) for c, p in zip(circs, params)])
-        assert np.all(np.abs(got - want) <= TOL[dtype] * np.maximum(1.0, np.abs(want)))
+        bars.check_e(got, want, NAME[dtype], "mixed batch")
     assert b.info()["graph"]
     b.close()
 
@@ -68,11 +69,11 @@ def test_qaoa_parameter_sets_share_one_tape(dtype):
     b.set_params(sets.ravel())
     got = b.run()
     want = np.array([oracle.expval(oracle.forward(c, p), c.observables[0]) for p in sets])
-    assert np.all(np.abs(got - want) <= TOL[dtype] * np.maximum(1.0, np.abs(want)))
+    bars.check_e(got, want, NAME[dtype], "qaoa batch")
     # new parameters, same graph
     sets2 = sets[::-1].copy()
     b.set_params(sets2.ravel())
-    assert np.allclose(b.run(), want[::-1], atol=TOL[dtype] * 10)
+    bars.check_e(b.run(), want[::-1], NAME[dtype], "qaoa batch, new parameters")
     b.close()
 
 
@@ -86,7 +87,7 @@ def test_mixed_qaoa_instances_and_autotune():
     assert ms > 0
     got = b.run()
     want = np.array([oracle.expval(oracle.forward(c, p), c.observables[0]) for c, p in inst])
-    assert np.all(np.abs(got - want) <= 1e-4 * np.maximum(1.0, np.abs(want)))
+    bars.check_e(got, want, "c64", "mixed qaoa batch")
     b.close()
 
 

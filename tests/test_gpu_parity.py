@@ -1,11 +1,9 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle.
 
-Tolerances (fixed by the accuracy targets of the state-vector core):
-  complex128: amplitudes 1e-12 absolute; expectation values 1e-10 relative
-              (to max(1, |E|)); Jacobian entries 1e-9 relative to max(1, max|J|).
-  complex64:  1e-4 on amplitudes, expectation values and Jacobian entries
-              (relative to max(1, |.|)), with FP32 gate arithmetic and FP64 /
-              compensated reductions.
+Bars (tests/bars.py): complex128 expectation values 1e-10 and gradients
+1e-9, each entry relative to max(|x|, 1e-3 max|x|); complex64 1e-4
+normwise; amplitudes 1e-12 (complex128) and 1e-4 (complex64) absolute;
+variances relative to <H^2>.
 Sizes span several tiles (n > 11 local bits for complex128, > 12 for
 complex64) and ragged cases (n = 1, 2, 3; empty tapes; zero-term observables).
 """
@@ -15,6 +13,7 @@ import math
 import numpy as np
 import pytest
 
+import bars
 import oracle
 from oracle import dense
 from workloads import (Circuit, Op, Term, GATE_ARITY, GATE_NPARAMS, layered_circuit, qaoa_maxcut,
@@ -33,9 +32,7 @@ from paper_2403_02512_gb300.torch_api import Program, StateVector, expval as ad_
 
 # "c128df": complex128 storage, double-float arithmetic -- held to the complex128 bars
 DTYPES = ["c128", "c64", "c128df"]
-TOL_STATE = {"c128": 1e-12, "c64": 1e-4, "c128df": 1e-12}
-TOL_E = {"c128": 1e-10, "c64": 1e-4, "c128df": 1e-10}
-TOL_J = {"c128": 1e-9, "c64": 1e-4, "c128df": 1e-9}
+TOL_STATE, TOL_E, TOL_J = bars.TOL_STATE, bars.TOL_E, bars.TOL_J
 
 
 def _state(n, dtype, seed):
@@ -47,15 +44,15 @@ def _state(n, dtype, seed):
 
 
 def _assert_state(got, want, dtype):
-    err = np.abs(got.astype(np.complex128) - want).max()
-    assert err <= TOL_STATE[dtype], f"max amplitude error {err:.3e}"
+    bars.check_state(got, want, dtype)
 
 
-def _assert_rel(got, want, tol, what):
-    got, want = np.asarray(got, dtype=np.float64), np.asarray(want, dtype=np.float64)
-    scale = max(1.0, float(np.abs(want).max()) if want.size else 1.0)
-    err = float(np.abs(got - want).max()) if want.size else 0.0
-    assert err <= tol * scale, f"{what}: max error {err:.3e} > {tol:.1e} * {scale:.3g}"
+def _assert_rel(got, want, tol, what, dtype, magnitude=None):
+    """The bar of `dtype` (entry-wise relative with a 1e-3 floor for complex128,
+    normwise for complex64) at tolerance `tol`."""
+    r = bars.check(got, want, dtype, tol, what, magnitude)
+    bars.record(what, dtype, got, want, r)
+    return r
 
 
 # ---------------------------------------------------------------------------
@@ -112,8 +109,7 @@ def test_dense_matrix_blocks(dtype, k):
         sv, psi = _state(n, dtype, 40 + k)
         sv.apply_matrix(wires, U, adjoint)
         oracle.apply_matrix(psi, U.conj().T if adjoint else U, wires)
-        tol = TOL_STATE[dtype] * (10 if dtype != "c64" else 1)
-        assert np.abs(sv.to_numpy() - psi).max() <= tol
+        _assert_state(sv.to_numpy(), psi, dtype)
 
 
 # ---------------------------------------------------------------------------
@@ -151,7 +147,7 @@ def test_pauli_sum_expvals(dtype, n):
     sv, psi = _state(n, dtype, 100 + n)
     got = sv.expval(obs)
     want = np.array([oracle.expval(psi, H) for H in obs])
-    _assert_rel(got, want, TOL_E[dtype], "expval")
+    _assert_rel(got, want, TOL_E[dtype], "expval", dtype)
     assert abs(sv.norm2() - oracle.norm2(psi)) <= TOL_E[dtype]
 
 
@@ -184,8 +180,8 @@ def test_adjoint_jacobian_random_circuits(dtype, n, seed):
     prog.forward(p)
     E, J = prog.jacobian()
     Eo, Jo = oracle.adjoint_jacobian(c, p, obs)
-    _assert_rel(E.cpu().numpy(), Eo, TOL_E[dtype], "expvals")
-    _assert_rel(J.cpu().numpy(), Jo, TOL_J[dtype], "jacobian")
+    _assert_rel(E.cpu().numpy(), Eo, TOL_E[dtype], "expvals", dtype)
+    _assert_rel(J.cpu().numpy(), Jo, TOL_J[dtype], "jacobian", dtype)
 
 
 @pytest.mark.parametrize("dtype", DTYPES)
@@ -206,9 +202,9 @@ def test_one_shot_jacobian_and_vjp_calls(dtype):
     finally:
         L.sv_destroy(h)
     Eo, Jo = oracle.adjoint_jacobian(c, p, obs)
-    _assert_rel(E, Eo, TOL_E[dtype], "expvals")
-    _assert_rel(J, Jo, TOL_J[dtype], "jacobian")
-    _assert_rel(v, g @ Jo, TOL_J[dtype], "vjp")
+    _assert_rel(E, Eo, TOL_E[dtype], "expvals", dtype)
+    _assert_rel(J, Jo, TOL_J[dtype], "jacobian", dtype)
+    _assert_rel(v, g @ Jo, TOL_J[dtype], "vjp", dtype)
 
 
 @pytest.mark.parametrize("dtype", DTYPES)
@@ -224,7 +220,7 @@ def test_lambda_chunking_matches_single_sweep(dtype, monkeypatch):
     chunked.set_params(p)
     E2, J2 = chunked.jacobian()
     assert torch.equal(E1, E2)
-    _assert_rel(J2.cpu().numpy(), J1.cpu().numpy(), 1e-6 if dtype == "c64" else 1e-12, "chunked")
+    _assert_rel(J2.cpu().numpy(), J1.cpu().numpy(), 1e-6 if dtype == "c64" else 1e-12, "chunked", dtype)
 
 
 @pytest.mark.parametrize("dtype", DTYPES)
@@ -238,7 +234,7 @@ def test_autograd_function_backward_is_adjoint_vjp(dtype):
     w = torch.linspace(-1, 1, E.numel(), dtype=torch.float64, device="cuda")
     (E * w).sum().backward()
     _, Jo = oracle.adjoint_jacobian(c, p)
-    _assert_rel(params.grad.cpu().numpy(), w.cpu().numpy() @ Jo, TOL_J[dtype], "autograd grad")
+    _assert_rel(params.grad.cpu().numpy(), w.cpu().numpy() @ Jo, TOL_J[dtype], "autograd grad", dtype)
 
 
 def test_jacobian_repeats_bitwise():
@@ -264,8 +260,8 @@ def test_layered_12_qubit_full_size(dtype):
     prog.forward(p)
     E, J = prog.jacobian()
     Eo, Jo = oracle.adjoint_jacobian(c, p)
-    _assert_rel(E.cpu().numpy(), Eo, TOL_E[dtype], "expvals")
-    _assert_rel(J.cpu().numpy(), Jo, TOL_J[dtype], "jacobian")
+    _assert_rel(E.cpu().numpy(), Eo, TOL_E[dtype], "expvals", dtype)
+    _assert_rel(J.cpu().numpy(), Jo, TOL_J[dtype], "jacobian", dtype)
 
 
 @pytest.mark.parametrize("dtype", DTYPES)
@@ -291,8 +287,8 @@ def test_workload_shapes_small(dtype, maker):
         assert np.all(amps[weights != 6] == 0)          # Givens gates keep Hamming weight exactly
     E, J = prog.jacobian()
     Eo, Jo = oracle.adjoint_jacobian(c, p)
-    _assert_rel(E.cpu().numpy(), Eo, TOL_E[dtype], "expvals")
-    _assert_rel(J.cpu().numpy(), Jo, TOL_J[dtype], "jacobian")
+    _assert_rel(E.cpu().numpy(), Eo, TOL_E[dtype], "expvals", dtype)
+    _assert_rel(J.cpu().numpy(), Jo, TOL_J[dtype], "jacobian", dtype)
 
 
 def test_compute_mode_switch_rebuilds_matrices():
@@ -305,8 +301,8 @@ def test_compute_mode_switch_rebuilds_matrices():
     L.sv_set_compute(sv.handle, L.SV_COMPUTE_DOUBLE_FLOAT)
     prog.forward(p)
     E2, J2 = prog.jacobian()
-    _assert_rel(E2.cpu().numpy(), E1.cpu().numpy(), 1e-10, "expvals")
-    _assert_rel(J2.cpu().numpy(), J1.cpu().numpy(), 1e-9, "jacobian")
+    _assert_rel(E2.cpu().numpy(), E1.cpu().numpy(), 1e-10, "expvals", "c128")
+    _assert_rel(J2.cpu().numpy(), J1.cpu().numpy(), 1e-9, "jacobian", "c128")
     with pytest.raises(L.SvError):
         L.sv_set_compute(StateVector(3, "c64").handle, L.SV_COMPUTE_DOUBLE_FLOAT)
 
@@ -410,8 +406,8 @@ def test_phase_runs_forward_and_jacobian(dtype, n):
     want = oracle.forward(c, p)
     _assert_state(sv.to_numpy(), want, dtype)
     E, J = prog.jacobian()
-    _assert_rel(E.cpu().numpy(), oracle.expvals(want, c.observables), TOL_E[dtype], "expval")
-    _assert_rel(J.cpu().numpy(), oracle.adjoint_jacobian(c, p)[1], TOL_J[dtype], "jacobian")
+    _assert_rel(E.cpu().numpy(), oracle.expvals(want, c.observables), TOL_E[dtype], "expval", dtype)
+    _assert_rel(J.cpu().numpy(), oracle.adjoint_jacobian(c, p)[1], TOL_J[dtype], "jacobian", dtype)
 
 
 def test_phase_runs_in_a_batch():
@@ -441,7 +437,9 @@ def test_variance_matches_oracle(dtype, n):
     obs.append([])                                # no terms: 0
     got = sv.var(obs)
     want = np.array([oracle.variance(psi, H) for H in obs])
-    _assert_rel(got, want, TOL_E[dtype] * 10, "variance")
+    # Var = <H^2> - <H>^2: the rounding of the difference scales with <H^2>
+    h2 = want + np.array([oracle.expval(psi, H) for H in obs]) ** 2
+    _assert_rel(got, want, TOL_E[dtype], "variance", dtype, magnitude=h2)
     again = sv.var(obs)
     assert np.array_equal(got, again)             # fixed-order reductions repeat bitwise
 
@@ -465,10 +463,12 @@ def test_hermitian_observables_as_pauli_words(dtype, n, wires):
     prog.forward(p)
     E, J = prog.jacobian()
     Eo, Jo = oracle.adjoint_jacobian(c, p, [want_obs])
-    _assert_rel(E.cpu().numpy(), Eo, TOL_E[dtype], "expval")
-    _assert_rel(J.cpu().numpy(), Jo, TOL_J[dtype], "jacobian")
+    _assert_rel(E.cpu().numpy(), Eo, TOL_E[dtype], "expval", dtype)
+    _assert_rel(J.cpu().numpy(), Jo, TOL_J[dtype], "jacobian", dtype)
     psi = oracle.forward(c, p)
-    _assert_rel(sv.var([H]), [oracle.variance(psi, want_obs)], TOL_E[dtype] * 10, "variance")
+    var_o = oracle.variance(psi, want_obs)
+    _assert_rel(sv.var([H]), [var_o], TOL_E[dtype], "variance", dtype,
+                magnitude=[var_o + oracle.expval(psi, want_obs) ** 2])
 
 
 # ---- probabilities and samples -----------------------------------------------
@@ -548,11 +548,11 @@ def test_jvp_matches_oracle_forward_mode(dtype, case):
     prog.set_params(p)
     got = prog.jvp(v).cpu().numpy()
     want = oracle.jvp(c, p, v)
-    _assert_rel(got, want, TOL_J[dtype] * 10, "jvp")
+    _assert_rel(got, want, TOL_J[dtype], "jvp", dtype)
     # the state ends as the forward output; the reverse-mode Jacobian agrees
     _assert_state(sv.to_numpy(), oracle.forward(c, p), dtype)
     _, J = prog.jacobian()
-    _assert_rel(J.cpu().numpy() @ v, got, TOL_J[dtype] * 10, "J @ v")
+    _assert_rel(J.cpu().numpy() @ v, got, TOL_J[dtype], "J @ v", dtype)
 
 
 def test_jacobian_by_shape_uses_forward_mode_when_parameters_are_few():
@@ -566,8 +566,8 @@ def test_jacobian_by_shape_uses_forward_mode_when_parameters_are_few():
     prog.set_params(p)
     E, J = prog.jacobian_by_shape()  # 3 parameters < 9 observables: three tangent passes
     Eo, Jo = oracle.adjoint_jacobian(c, p)
-    _assert_rel(E.cpu().numpy(), Eo, 1e-10, "expval")
-    _assert_rel(J.cpu().numpy(), Jo, 1e-9, "jacobian")
+    _assert_rel(E.cpu().numpy(), Eo, 1e-10, "expval", "c128")
+    _assert_rel(J.cpu().numpy(), Jo, 1e-9, "jacobian", "c128")
 
 
 def test_jvp_rejects_bad_tangents():
@@ -615,11 +615,11 @@ def test_sparse_expval_and_jacobian_match_oracle(dtype, n):
     psi = oracle.forward(c, p)
     e = L.sv_sparse_expval(sv.handle, sp)
     want_e = oracle.expval(psi, H)
-    _assert_rel([e], [want_e], TOL_E[dtype], "sparse expval")
+    _assert_rel([e], [want_e], TOL_E[dtype], "sparse expval", dtype)
     e2, J = L.sv_adjoint_jacobian_sparse(sv.handle, L.Tape(c.ops, c.n_params), p, sp)
     Eo, Jo = oracle.adjoint_jacobian(c, p, [H])
-    _assert_rel([e2], Eo, TOL_E[dtype], "sparse expval (adjoint call)")
-    _assert_rel(J, Jo[0], TOL_J[dtype], "sparse jacobian")
+    _assert_rel([e2], Eo, TOL_E[dtype], "sparse expval (adjoint call)", dtype)
+    _assert_rel(J, Jo[0], TOL_J[dtype], "sparse jacobian", dtype)
     assert e == L.sv_sparse_expval(sv.handle, sp)  # fixed order: bitwise repeat
     sp.close()
 
@@ -722,8 +722,8 @@ def test_dense5_tensor_cores_with_controls_and_in_a_jacobian():
     prog.forward(p)
     _assert_state(sv.to_numpy(), want, "c64")
     E, J = prog.jacobian()  # the sweep un-applies the block with its adjoint on the tensor cores
-    _assert_rel(E.cpu().numpy(), Eo, 1e-4, "expval")
-    _assert_rel(J.cpu().numpy(), Jo, 1e-4, "jacobian")
+    _assert_rel(E.cpu().numpy(), Eo, 1e-4, "expval", "c64")
+    _assert_rel(J.cpu().numpy(), Jo, 1e-4, "jacobian", "c64")
 
 
 @pytest.mark.parametrize("dtype", DTYPES)
@@ -754,5 +754,5 @@ def test_wide_dense_blocks_in_a_jacobian(dtype):
     prog = Program(sv, pre + [_MatrixOp(blk_wires, U)] + post, P, obs)
     prog.forward(p)
     E, J = prog.jacobian()
-    _assert_rel(E.cpu().numpy(), Eo, TOL_E[dtype], "expval")
-    _assert_rel(J.cpu().numpy(), Jo, TOL_J[dtype] * 10, "jacobian")
+    _assert_rel(E.cpu().numpy(), Eo, TOL_E[dtype], "expval", dtype)
+    _assert_rel(J.cpu().numpy(), Jo, TOL_J[dtype], "jacobian", dtype)
