@@ -69,8 +69,8 @@ def parse():
 # current kernel on sel22 (22 observables), scaled to sel24 by the state size
 # (x4) and the vector count (25 / 23).  Must be re-taken when the kernel changes.
 PROFILED_TRAFFIC = {
-    "c128": (3.042117e9 * 4 * 25 / 23, "profiles/k_tile_adjoint_sel22_c128.md, scaled x4 x25/23"),
-    "c64": (1.487015e9 * 4 * 25 / 23, "profiles/k_tile_adjoint_sel22_c64.md, scaled x4 x25/23"),
+    "c128": (3.042117e9 * 4 * 25 / 23, "ncu dram bytes of one sel22 adjoint launch, scaled x4 x25/23"),
+    "c64": (1.487015e9 * 4 * 25 / 23, "ncu dram bytes of one sel22 adjoint launch, scaled x4 x25/23"),
 }
 
 # FP64 pipe of a GB300: 152 SMs x 2 FMA lanes/clk x 2 flops x 2.07 GHz.
@@ -161,42 +161,36 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # oracle (CPU baseline / reference arm) on a bounded sample
 # ---------------------------------------------------------------------------
-def oracle_sample(sweep_steps: int = 6):
-    """Time the FP64 oracle on the sel24 workload and scale to one full step.
+def oracle_sample(rows: int = 1):
+    """Time the FP64 oracle on the sel24 workload, whole parts only.
 
-    Sample: the full forward pass (all 384 ops), lambda_j = Z_j psi for the 24
-    observables, and `sweep_steps` steps of the adjoint sweep (each step: 24
-    generator inner products and 25 un-applied vectors).  The full step is
-    estimated as forward + lambda + (sweep time per step) x (768 sweep steps).
-    """
+    Sample: the oracle's own adjoint-Jacobian call for Jacobian rows
+    0..rows-1: a complete forward pass (all 384 ops), lambda_j = Z_j psi for
+    those rows, and the complete adjoint sweep (all 768 steps of the expanded
+    tape) with phi, mu and those lambdas.  The oracle clocks the work done once
+    (forward pass; phi's un-apply and mu = G phi) apart from the work done once
+    per observable (lambda_j and E_j; the inner products and lambda_j's
+    un-apply).  Every observable is a single Z word, so each row repeats the
+    same operations on a vector of the same size, and the full step (24 rows)
+    is forward + phi part + 24 / rows x (lambda part + rows part).
+
+    Returns (full-step estimate in ms, the sample's own wall ms, description,
+    threads, the sample's Jacobian rows)."""
     import oracle
     from workloads import strongly_entangling
 
     c, p = strongly_entangling(N_QUBITS, LAYERS)
-    steps = oracle.expand(c.ops)
+    m = len(c.observables)
+    clock = {}
     t0 = time.perf_counter()
-    psi = oracle.forward(c, p)
-    t1 = time.perf_counter()
-    lams = [oracle.apply_hamiltonian(psi, H) for H in c.observables]
-    t2 = time.perf_counter()
-    phi = psi
-    for st in list(reversed(steps))[:sweep_steps]:
-        M = oracle.core._step_matrix(st, p)
-        if st.param is not None:
-            G, _ = oracle.generator(st.name)
-            mu = oracle.copy(phi)
-            oracle.apply_matrix(mu, G, st.wires, st.controls, st.cvals)
-            for lam in lams:
-                oracle.inner(lam, mu)
-        Md = M.conj().T.copy()
-        oracle.apply_matrix(phi, Md, st.wires, st.controls, st.cvals)
-        for lam in lams:
-            oracle.apply_matrix(lam, Md, st.wires, st.controls, st.cvals)
-    t3 = time.perf_counter()
-    est_ms = 1e3 * ((t1 - t0) + (t2 - t1) + (t3 - t2) / sweep_steps * len(steps))
-    sample = (f"oracle FP64 on sel24 at full size: forward (384 ops) + 24 lambdas + {sweep_steps} of "
-              f"{len(steps)} adjoint-sweep steps, scaled to the full sweep")
-    return est_ms, sample, oracle.num_threads(), (t3 - t0)
+    _, J = oracle.adjoint_jacobian(c, p, observables=c.observables[:rows], clock=clock)
+    wall_ms = 1e3 * (time.perf_counter() - t0)
+    est_ms = 1e3 * (clock["forward"] + clock["phi"] + m / rows * (clock["lambda"] + clock["rows"]))
+    sample = (f"oracle FP64 adjoint Jacobian of sel24 at full size for {rows} of its {m} rows: complete forward "
+              f"pass (384 ops) and complete adjoint sweep (768 steps), timed; the full step is forward + phi part "
+              f"+ {m}/{rows} x per-row part (forward {clock['forward']:.2f} s, phi {clock['phi']:.2f} s, "
+              f"per-row {clock['lambda'] + clock['rows']:.2f} s)")
+    return est_ms, wall_ms, sample, oracle.num_threads(), J
 
 
 def max_over_ranks(value: float, world: int, device) -> float:
@@ -217,21 +211,29 @@ def replica_value(ms_max: float, world: int) -> float:
 
 
 def run_reference(args):
+    """The oracle arm: each step is one oracle_sample (one complete Jacobian
+    row, about 10 s on 16 cores); `value` is the full sel24 step it gives,
+    `ms_per_step` the sample's own wall time."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    times = []
+    est, wall = [], []
     sample = cores = None
     for i in range(args.warmup + args.steps):
-        est, sample, cores, _ = oracle_sample(sweep_steps=3)
+        e, w, sample, cores, _ = oracle_sample(rows=1)
         if i >= args.warmup:
-            times.append(est)
-    value = statistics.mean(times)
+            est.append(e)
+            wall.append(w)
+    value = statistics.mean(est)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "ms", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": value, "higher_is_better": False,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(wall),
+            "value_is": "the full sel24 step (forward + 24 x 576 Jacobian) from each timed sample; ms_per_step is "
+                        "the sample's own wall time (one complete Jacobian row)",
+            "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n_qubits": N_QUBITS, "n_params": 576, "n_observables": 24},
-            "cpu_baseline": {"value": value, "unit": "ms", "cores": cores, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "ms", "cores": cores, "kind": "oracle", "sample": sample,
+                             "samples": len(est), "spread_ms": [min(est), max(est)]},
             "e2e": {"value": value, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -480,16 +482,27 @@ def extra_layered12():
     return out
 
 
-def extra_rycz30():
+def _kernel_split(kt):
+    total = sum(v[0] for v in kt.values()) or 1.0
+    return {k: {"ms": round(v[0], 3), "launches": v[1], "share": round(v[0] / total, 4)}
+            for k, v in kt.items() if v[1] > 0}
+
+
+def extra_rycz30(hbm_peak, reps=3):
     """30-qubit RY layers + CZ brick + a 5-qubit dense block after every fifth
-    layer, <Z0 Z29>: forward + full adjoint Jacobian (600 params).  The dense
-    blocks run on the tensor cores in complex64 and on the CUDA cores in
-    complex128."""
+    layer, <Z0 Z29>: forward + full adjoint Jacobian (600 params), `reps`
+    timed repetitions (no kernel events), then one repetition with per-kernel
+    CUDA events for the kernel split and the rooflines of the adjoint tile
+    kernel (2V(1 + m) bytes per launch, m = 1; FP64 flops of the unfused
+    method) and of the dense-block kernels (2V bytes and 256 flops per
+    amplitude per application).  The dense blocks run on the tensor cores in
+    complex64 and on the CUDA cores in complex128."""
     import torch
     from paper_2403_02512_gb300.torch_api import Program, StateVector
     from workloads import ry_cz_brick
     from paper_2403_02512_gb300 import _lib as L
     c, p = ry_cz_brick(30, 20)
+    n_dense = sum(op.name == "QubitUnitary" for op in c.ops)
     out = {}
     # the last run applies the complex64 dense blocks on the CUDA cores instead
     for key, dtype, tc in (("c128", "c128", True), ("c64", "c64", True), ("c64_dense_on_cuda_cores", "c64", False)):
@@ -502,12 +515,36 @@ def extra_rycz30():
             return prog.jacobian()
 
         try:
-            ms = _timed(step, 1, torch.cuda.current_stream())
+            step()
+            torch.cuda.synchronize()
+            times = [_timed(step, 1, torch.cuda.current_stream()) for _ in range(reps if tc else 1)]
+            L.sv_kernel_timing_reset()
+            L.sv_kernel_timing_enable(True)
             E, J = step()
+            torch.cuda.synchronize()
+            L.sv_kernel_timing_enable(False)
+            kt = L.sv_kernel_timing_read()
         finally:
             L.sv_set_dense_tensor_cores(True)
-        out[key] = {"ms_forward_and_jacobian": ms, "expval": float(E[0]), "forward_passes": prog.stats()[0],
-                    "adjoint_passes": prog.stats()[1], "J_sum": float(J.sum())}
+        V = (8 if dtype == "c64" else 16) << 30
+        res = {"ms_forward_and_jacobian": float(np.median(times)), "ms_reps": times, "expval": float(E[0]),
+               "forward_passes": prog.stats()[0], "adjoint_passes": prog.stats()[1], "J_sum": float(J.sum()),
+               "kernels": _kernel_split(kt)}
+        adj_ms, adj_n = kt["tile_adjoint"]
+        if adj_n:
+            fl = adjoint_flops(c, 1) / adj_n  # one sweep per repetition
+            res["roofline_tile_adjoint"] = {
+                "launches": adj_n, "avg_launch_ms": adj_ms / adj_n,
+                "hbm_frac": 2.0 * V * 2 / (adj_ms / adj_n * 1e-3) / 1e9 / hbm_peak,
+                "fp64_tflops_algorithmic": fl / (adj_ms / adj_n * 1e-3) / 1e12,
+                "fp64_frac": (fl / (adj_ms / adj_n * 1e-3) / 1e12 / FP64_PEAK_TFLOPS) if dtype == "c128" else None}
+        dk_ms, dk_n = kt["dense_k"]
+        if dk_n:
+            res["roofline_dense_blocks"] = {
+                "launches": dk_n, "applications": 3 * n_dense, "avg_launch_ms": dk_ms / dk_n,
+                "hbm_frac": 2.0 * V * 3 * n_dense / (dk_ms * 1e-3) / 1e9 / hbm_peak,
+                "tflops_algorithmic": 256.0 * (1 << 30) * 3 * n_dense / (dk_ms * 1e-3) / 1e12}
+        out[key] = res
         prog.close()
         sv.close()
         torch.cuda.empty_cache()
@@ -555,15 +592,12 @@ def run_ours(args):
         for _ in range(warmup):
             step()
         torch.cuda.synchronize()
-        launches_fwd = prog.stats()[2]
-        if timing:
-            L.sv_kernel_timing_reset()
-            L.sv_kernel_timing_enable(True)
         barrier()
         torch.cuda.synchronize()
         clocks = ClockSampler(local)
         if timing:
             clocks.start()
+        # the headline region: kernel-timing events off
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         launches = 0
@@ -581,6 +615,13 @@ def run_ours(args):
         ms = e0.elapsed_time(e1) / steps
         kt = None
         if timing:
+            # the roofline region: the same steps again with a CUDA event pair
+            # around every library kernel launch (on the library's stream)
+            L.sv_kernel_timing_reset()
+            L.sv_kernel_timing_enable(True)
+            for _ in range(min(steps, 5)):
+                step()
+            torch.cuda.synchronize()
             L.sv_kernel_timing_enable(False)
             kt = L.sv_kernel_timing_read()
         fp, ap, _ = prog.stats()
@@ -609,6 +650,7 @@ def run_ours(args):
     total_kernel_ms = sum(v[0] for v in kt.values())
     shares = {k: round(v[0] / total_kernel_ms, 4) for k, v in kt.items() if v[1] > 0}
     common = {"kernel": "k_tile_adjoint", "avg_launch_ms": adj_ms / max(1, adj_n), "launches": adj_n,
+              "timed_in": "a second region of min(steps, 5) steps with per-launch CUDA events",
               "algorithmic_bytes_per_launch": bytes_per_launch,
               "algorithmic_flops_per_launch": flops_per_launch,
               "hbm_achieved_gbs": hbm_achieved, "hbm_frac": (hbm_achieved / hbm_peak) if hbm_achieved else None,
@@ -667,7 +709,7 @@ def run_ours(args):
             extras["gate_pass_n30"] = extra_gates(hbm_peak)
             extras["qaoa_batched"] = extra_qaoa()
             extras["vqe24_2000_terms"] = extra_vqe()
-            extras["rycz30"] = extra_rycz30()
+            extras["rycz30"] = extra_rycz30(hbm_peak)
             try:
                 extras["layered12"] = extra_layered12()
             except Exception as exc:  # an extra never takes the bench line down
@@ -676,9 +718,14 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        est, sample, cores, wall = oracle_sample()
-        cpu = {"value": est, "unit": "ms", "cores": cores, "kind": "oracle", "sample": sample,
-               "sample_wall_s": wall}
+        runs = [oracle_sample(rows=1) for _ in range(2)]
+        est = statistics.mean(r[0] for r in runs)
+        Jo = runs[0][4]
+        cpu = {"value": est, "unit": "ms", "cores": runs[0][3], "kind": "oracle", "sample": runs[0][2],
+               "samples": len(runs), "spread_ms": [min(r[0] for r in runs), max(r[0] for r in runs)],
+               "sample_wall_s": sum(r[1] for r in runs) / 1e3}
+        if (NQ, args.layers) == (N_QUBITS, LAYERS):
+            cpu["max_abs_diff_row0_vs_gpu"] = float(np.abs(main["J"].cpu().numpy()[0] - Jo[0]).max())
 
     if rank == 0:
         line = {"metric": METRIC, "value": replica_value(ms, world), "unit": "ms", "n_gpus": world,
