@@ -452,23 +452,30 @@ sv_status sv_plan_describe(int n, sv_dtype dtype, const sv_tape *tape, int forwa
  * device synchronisation of cudaFree are not allowed, or a framework whose
  * allocator must not see foreign allocations).
  *
- * Same values as sv_expval (same kernels and summation order), computed for a
+ * The values of sv_expval, equal within rounding (the same term kernel; the
+ * grid, and so the order of the partial sums, may differ), computed for a
  * state given by its device pointer psi (2^n amplitudes of dtype, 16-byte
  * aligned, read only) on cuda_stream (NULL = legacy default stream); results go
- * to the host array out[n_obs] and the call synchronises the stream.  Every
+ * to the host array out[n_obs] and the call synchronises the stream.  psi must
+ * be device (or managed) memory of the current device whose allocation holds
+ * 2^n amplitudes from psi on; anything else (a host pointer, another device's
+ * memory, a short buffer) is rejected with SV_ERR_ARG before any launch.  Every
  * temporary lives in one array compiled into the library
  * (SV_STATIC_SCRATCH_BYTES on every GPU that loads it, until exit); the call
  * makes no cudaMalloc / cudaFree or other allocation.
  *
  * Limits, rejected with SV_ERR_ARG and a message in sv_last_error(): at most
  * SV_STATIC_MAX_OBSERVABLES observables and SV_STATIC_MAX_TERMS Pauli terms in
- * total per call.
+ * total per call.  A Pauli word that flips more wires than one tile holds
+ * (11 for complex128, 12 for complex64, less 3 or 4 always-local low bits) is
+ * rejected with SV_ERR_UNSUPPORTED.
  *
  * The first call on each device looks up the array's device address (with
- * that device current) and keeps it: make that first call before any stream
- * capture.  All calls share the array; calls whose GPU work overlaps race and
- * must be serialised by the caller.  The per-term totals are cleared at the
- * start of every call. */
+ * that device current) and keeps it.  The call copies host tables and
+ * synchronises its stream, so it must not be called while that stream, or any
+ * stream in global capture mode, is capturing.  All calls share the array;
+ * calls whose GPU work overlaps race and must be serialised by the caller.
+ * The per-term totals are cleared at the start of every call. */
 #define SV_STATIC_SCRATCH_BYTES (2u << 20)
 #define SV_STATIC_MAX_TERMS 4096
 #define SV_STATIC_MAX_OBSERVABLES 1024

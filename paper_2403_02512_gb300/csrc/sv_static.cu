@@ -4,17 +4,27 @@
 // measurement: an application that reserved the whole GPU up front and hands
 // memory to nobody, code running where cudaMalloc / cudaFree would stall the
 // device (cudaFree synchronises it), or a framework whose allocator must not
-// see foreign allocations.  For them sv_expval_static computes the same values
-// as sv_expval with every temporary (the term table, the per-block partial
-// sums and the per-term totals) in one fixed array compiled into the library.
+// see foreign allocations.  For them sv_expval_static computes the values of
+// sv_expval (the same term kernel; equal within rounding, since the grid and
+// so the order of the partial sums may differ) with every temporary (the term
+// table, the per-block partial sums and the per-term totals) in one fixed
+// array compiled into the library.
 //
 // The array is a file-scope __device__ variable: every GPU that loads the
 // library holds its SV_STATIC_SCRATCH_BYTES until the process exits.  Host
 // code cannot use the array's name as a device address, so the first call on
 // each device looks the address up with cudaGetSymbolAddress (with that device
-// current) and keeps it; make that first call before any stream capture.
-// All calls share the array, so calls whose GPU work overlaps (on different
-// streams, or from several threads) race; serialise them.
+// current) and keeps it.  The call copies its term tables from host memory and
+// synchronises its stream, so it must not be called while that stream, or any
+// stream in global capture mode, is capturing.  All calls share the array, so
+// calls whose GPU work overlaps (on different streams, or from several
+// threads) race; serialise them.
+//
+// Before any launch the call checks that psi is device memory of the current
+// device and that its allocation holds 2^n amplitudes from psi on
+// (cudaPointerGetAttributes, and the driver's cuMemGetAddressRange looked up
+// through the runtime so that the library does not link libcuda); neither
+// check allocates.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -22,6 +32,8 @@
 #include <mutex>
 #include <string>
 #include <vector>
+
+#include <cuda.h>
 
 #include "sv.h"
 #include "sv_internal.h"
@@ -78,6 +90,50 @@ sv_status scratch_address(char **out) {
   return SV_OK;
 }
 
+// The driver's cuMemGetAddressRange (base and size of the allocation holding an
+// address), through the runtime's entry-point lookup: no link-time libcuda.
+typedef CUresult (*AddressRangeFn)(CUdeviceptr *base, size_t *size, CUdeviceptr dptr);
+std::once_flag g_range_once;
+AddressRangeFn g_range_fn = nullptr;
+
+// psi must be device (or managed) memory of the current device, with
+// `bytes` bytes of its allocation from psi on.
+sv_status check_state_memory(const void *psi, size_t bytes) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(SV_ERR_CUDA, "sv_expval_static: no current CUDA device");
+  }
+  cudaPointerAttributes a;
+  memset(&a, 0, sizeof(a));
+  if (cudaPointerGetAttributes(&a, psi) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(SV_ERR_ARG, "sv_expval_static: psi is not an address CUDA knows");
+  }
+  if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
+    return fail(SV_ERR_ARG, "sv_expval_static: psi is not device memory");
+  if (a.type == cudaMemoryTypeDevice && a.device != dev)
+    return fail(SV_ERR_ARG, "sv_expval_static: psi is memory of another device than the current one");
+  std::call_once(g_range_once, [] {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuMemGetAddressRange", &fn, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_range_fn = (AddressRangeFn)fn;
+    cudaGetLastError();
+  });
+  if (!g_range_fn) return fail(SV_ERR_CUDA, "sv_expval_static: cuMemGetAddressRange is unavailable");
+  CUdeviceptr base = 0;
+  size_t size = 0;
+  if (g_range_fn(&base, &size, (CUdeviceptr)(uintptr_t)psi) != CUDA_SUCCESS)
+    return fail(SV_ERR_ARG, "sv_expval_static: psi lies in no device allocation");
+  const uint64_t p = (uint64_t)(uintptr_t)psi;
+  if (p < base || bytes > size || p - base > size - bytes)
+    return fail(SV_ERR_ARG, "sv_expval_static: psi's allocation holds fewer than 2^n amplitudes from psi on");
+  return SV_OK;
+}
+
 struct Term {
   int obs;
   double coeff;
@@ -127,6 +183,7 @@ sv_status sv_expval_static(const void *psi, int n, sv_dtype dtype, const sv_paul
     return fail(SV_ERR_ARG, "sv_expval_static: more observables than SV_STATIC_MAX_OBSERVABLES");
   if (n_obs == 0) return SV_OK;
   cudaStream_t st = (cudaStream_t)cuda_stream;
+  if (sv_status s = check_state_memory(psi, (size_t)(dtype == SV_C64 ? 8 : 16) << n)) return s;
 
   // terms in index-bit form
   std::vector<Term> terms;

@@ -187,3 +187,20 @@ def test_hermitian_to_pauli_drops_words_at_or_below_tol():
     assert len(L.sv_hermitian_to_pauli(2, [1], A)) == 2
     t = L.sv_hermitian_to_pauli(2, [1], A, tol=1e-8)
     assert len(t) == 1 and t[0].paulis == ()
+
+
+def test_static_expval_rejects_bad_arguments_before_touching_a_device():
+    # argument checks come before any CUDA call, so they hold without a GPU
+    from workloads import Term
+    ps = L.PauliSums([[Term(1.0, ((0, "Z"),))]])
+    host = np.zeros(16, dtype=np.complex128)
+    for ptr, n, dt, msg in ((0, 4, L.SV_C128, "NULL"), (host.ctypes.data + 8, 4, L.SV_C128, "aligned"),
+                            (host.ctypes.data, 0, L.SV_C128, "n out of range"),
+                            (host.ctypes.data, 4, 7, "dtype")):
+        with pytest.raises(L.SvError) as ei:
+            L.sv_expval_static(ptr, n, dt, ps)
+        assert ei.value.status == 1 and msg in str(ei.value)
+    # a host pointer never reaches a kernel: without a GPU the call ends in an error status
+    with pytest.raises(L.SvError) as ei:
+        L.sv_expval_static(host.ctypes.data, 4, L.SV_C128, ps)
+    assert ei.value.status in (1, 3)
