@@ -59,6 +59,12 @@ def parse():
     ap.add_argument("--profile-vqe", action="store_true",
                     help="profiling aid: --steps energy + adjoint-gradient steps of the 24-qubit VQE workload "
                          "(2000-term Hamiltonian) in --dtype; prints one JSON line")
+    ap.add_argument("--profile-expval", action="store_true",
+                    help="profiling aid: time --steps expectation values of the 24 single-Z observables on the "
+                         "--qubits strongly-entangling output state in --dtype; prints one JSON line")
+    ap.add_argument("--profile-rycz30", action="store_true",
+                    help="profiling aid: --steps forward + adjoint-Jacobian steps of the 30-qubit RY + CZ-brick "
+                         "workload (four 5-qubit dense blocks) in --dtype; prints one JSON line")
     ap.add_argument("--profile-gate", default=None, metavar="GATE:WIRE",
                     help="profiling aid: time --steps passes of one gate (RX, Hadamard or CNOT, control "
                          "wire+1) on a --qubits state of --dtype and print one JSON line (not the bench line)")
@@ -791,6 +797,46 @@ def run_profile_vqe(args):
     print(json.dumps({"profile_vqe": args.dtype, "ms_energy_and_gradient": ms}))
 
 
+def run_profile_expval(args):
+    import torch
+    from paper_2403_02512_gb300.torch_api import Program, StateVector
+    from workloads import strongly_entangling
+    c, p = strongly_entangling(args.qubits, args.layers)
+    sv = StateVector(args.qubits, args.dtype)
+    prog = Program.from_circuit(sv, c)
+    prog.forward(p)
+    for _ in range(args.warmup):
+        sv.expval(c.observables)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sv.expval(c.observables)
+    torch.cuda.synchronize()
+    ms = (time.perf_counter() - t0) / args.steps * 1e3
+    V = (8 if args.dtype == "c64" else 16) << args.qubits
+    print(json.dumps({"profile_expval": args.dtype, "n": args.qubits, "words": len(c.observables), "ms": ms,
+                      "gbs_algorithmic": V / ms / 1e6}))
+
+
+def run_profile_rycz30(args):
+    import torch
+    from paper_2403_02512_gb300.torch_api import Program, StateVector
+    from workloads import ry_cz_brick
+    c, p = ry_cz_brick(30, 20)
+    sv = StateVector(30, args.dtype)
+    prog = Program.from_circuit(sv, c)
+
+    def step():
+        prog.forward(p)
+        return prog.jacobian()
+
+    for _ in range(args.warmup):
+        step()
+    ms = _timed(step, args.steps, torch.cuda.current_stream())
+    print(json.dumps({"profile_rycz30": args.dtype, "ms_forward_and_jacobian": ms,
+                      "adjoint_passes": prog.stats()[1]}))
+
+
 def run_profile_gate(args):
     import torch
     from paper_2403_02512_gb300.torch_api import Program, StateVector
@@ -843,6 +889,10 @@ def main():
         run_profile_dense(args)
     elif args.profile_gate:
         run_profile_gate(args)
+    elif args.profile_expval:
+        run_profile_expval(args)
+    elif args.profile_rycz30:
+        run_profile_rycz30(args)
     elif args.profile_batch:
         run_profile_batch(args)
     elif args.impl == "reference":

@@ -221,6 +221,34 @@ DF_HD df::df(double x) {
   l = n.l;
 }
 
+// Lean conversions for single-op streams, where conversion dominates the
+// work.  Split: the top 24 significant bits by truncation, the next 29 rounded
+// to a float, then one Fast2Sum; magnitudes below 2^-126 become zero and the
+// low part is dropped below 2^-74 (never the case that matters for an
+// amplitude of a normalised state).  Join: each float re-encoded as a double
+// with integer operations (subnormal floats flush to zero), then one FP64
+// addition.
+DF_HD df df_split_fast(double x) {
+  const uint64_t b = df_d2u(x);
+  const uint32_t sign = (uint32_t)(b >> 32) & 0x80000000u;
+  const int fe = (int)((b >> 52) & 0x7FF) - 896;  // float biased exponent of x
+  const float h = df_u2f(fe > 0 ? (sign | ((uint32_t)fe << 23) | (uint32_t)((b >> 29) & 0x7FFFFFu)) : sign);
+  // remainder r * 2^(E - 52): float biased exponent of the scale is fe - 52
+  float l = df_u32_to_f((uint32_t)b & 0x1FFFFFFFu) * df_u2f((uint32_t)(fe > 52 ? fe - 52 : 1) << 23);
+  l = df_u2f(df_f2u(l) | sign);
+  return df_fast_two_sum(h, fe > 52 ? l : 0.f);
+}
+
+DF_HD double df_f2d_normal(float f) {
+  const uint32_t u = df_f2u(f);
+  const uint64_t sign = (uint64_t)(u & 0x80000000u) << 32;
+  const uint32_t e = (u >> 23) & 0xFFu;
+  if (e == 0) return df_u2d(sign);
+  return df_u2d(sign | ((uint64_t)(e + 896) << 52) | ((uint64_t)(u & 0x7FFFFFu) << 29));
+}
+
+DF_HD double df_join_fast(df v) { return df_f2d_normal(v.h) + df_f2d_normal(v.l); }
+
 struct __align__(16) dfc {
   df x, y;  // real, imaginary
 };

@@ -736,6 +736,15 @@ void lower_phase(int n, const std::vector<HOp> &ops, const std::vector<int> &mem
       aux.push_back(rec.first);
       aux.push_back(rec.second);
     }
+  // the local masks transposed: word b has bit j set when local member j's mask
+  // has local bit b, so the parities of all members over a local index l are
+  // the bits of the XOR of the words of l's set bits (padded to an even count)
+  for (int b = 0; b < pd.T + (pd.T & 1); ++b) {
+    uint64_t w = 0;
+    for (size_t j = 0; j < loc.size() && b < pd.T; ++j)
+      if (loc[j].first >> b & 1) w |= 1ull << j;
+    aux.push_back(w);
+  }
   out.push_back(o);
 }
 
@@ -829,8 +838,64 @@ void merge_multi(std::vector<OpDev> &ops, size_t begin) {
   ops.swap(out);
 }
 
+// Adjoint plans: up to `wmax` consecutive uncontrolled single-wire pair
+// micro-ops on distinct local bits (trainable ones with an X, Y or fused
+// Hermitian generator) are grouped: the members stay in place, marked
+// in_multi, and a kMulti header with the count and the sorted bits follows
+// them.  The adjoint kernel meets the header first (it walks the pass
+// backwards) and applies the members together (one load and store of phi and
+// each lambda per group, one barrier).
+void merge_multi_adj(std::vector<OpDev> &ops, size_t begin, int wmax) {
+  std::vector<OpDev> out(ops.begin(), ops.begin() + begin);
+  std::vector<OpDev> pend;
+  auto mergeable = [](const OpDev &o) {
+    if (o.kind != kPair || o.k != 1 || o.cmask != 0 || o.hcmask != 0 || o.lcmask != 0) return false;
+    if (o.oa != 0 || o.ob != (1 << o.tl[0])) return false;
+    return o.train < 0 || o.gcode == gX || o.gcode == gY || (o.gcode == gHerm && o.ngen >= 1 && o.ngen <= 3);
+  };
+  auto emit = [&]() {
+    if (pend.size() == 1) out.push_back(pend[0]);
+    if (pend.size() >= 2) {
+      OpDev m;
+      memset(&m, 0, sizeof(m));
+      m.kind = kMulti;
+      m.k = (int8_t)pend.size();
+      m.train = -1;
+      m.slot = -1;
+      m.sync_prev = 1;
+      int bits[3];
+      for (size_t j = 0; j < pend.size(); ++j) {
+        OpDev mj = pend[j];
+        mj.in_multi = 1;
+        mj.sync_prev = 0;
+        out.push_back(mj);
+        m.tl[j] = pend[j].tl[0];
+        bits[j] = pend[j].tl[0];
+      }
+      std::sort(bits, bits + pend.size());
+      for (size_t j = 0; j < pend.size(); ++j) m.ts[j] = (int8_t)bits[j];
+      out.push_back(m);
+    }
+    pend.clear();
+  };
+  for (size_t i = begin; i < ops.size(); ++i) {
+    const OpDev &o = ops[i];
+    if (!mergeable(o)) {
+      emit();
+      out.push_back(o);
+      continue;
+    }
+    bool clash = (int)pend.size() >= wmax;
+    for (const OpDev &q : pend) clash |= q.tl[0] == o.tl[0];
+    if (clash) emit();
+    pend.push_back(o);
+  }
+  emit();
+  ops.swap(out);
+}
+
 Plan plan_passes(int n, const std::vector<HOp> &ops, int Tmax, int nlow_pref, int max_train, bool dagger,
-                 SlotTable &st, bool fuse = false, bool phase = false, bool multi = false) {
+                 SlotTable &st, bool fuse = false, bool phase = false, bool multi = false, int multi_adj = 0) {
   Plan P;
   const std::vector<Group> groups = fuse_groups(n, ops, fuse, phase);
   const int T = std::min(Tmax, n);
@@ -885,6 +950,7 @@ Plan plan_passes(int n, const std::vector<HOp> &ops, int Tmax, int nlow_pref, in
         if (P.ops[q].kind == kDense) pd.max_k = std::max(pd.max_k, (int)P.ops[q].k);
     }
     if (multi) merge_multi(P.ops, (size_t)pd.op_begin);
+    if (multi_adj > 1) merge_multi_adj(P.ops, (size_t)pd.op_begin, multi_adj);
     pd.op_end = (int)P.ops.size();
     pd.n_train = t;
     P.steps.push_back({0, (int)P.passes.size()});
@@ -952,13 +1018,21 @@ sv_status check_plan(const Plan &P, int n, int nlow_pref) {
       if (op.kind == kDiag) continue;
       if (op.kind == kPhase) {
         if (op.ob < 2 || op.ob > kMaxPhaseMembers || op.zmask < 0 || op.zmask > op.ob || op.oa < 0 ||
-            2 * (size_t)(op.oa + op.ob) > P.aux.size())
+            2 * (size_t)(op.oa + op.ob) + pd.T > P.aux.size())
           return fail(SV_ERR_UNSUPPORTED, "internal planner error: phase run");
         continue;
       }
       if (op.k > kMaxTileTargets) return fail(SV_ERR_UNSUPPORTED, "internal planner error: wide op in a tile");
       if (op.kind == kMulti && (op.k < 2 || op.k > 3))
         return fail(SV_ERR_UNSUPPORTED, "internal planner error: multi-wire op");
+      if (op.kind == kMulti && o > pd.op_begin && P.ops[o - 1].in_multi) {  // adjoint: members precede it
+        if (o - op.k < pd.op_begin) return fail(SV_ERR_UNSUPPORTED, "internal planner error: multi-wire members");
+        for (int j = 0; j < op.k; ++j) {
+          const OpDev &mj = P.ops[o - op.k + j];
+          if (!mj.in_multi || mj.kind != kPair || mj.k != 1 || mj.tl[0] != op.tl[j] || mj.ob != (1 << mj.tl[0]))
+            return fail(SV_ERR_UNSUPPORTED, "internal planner error: multi-wire members");
+        }
+      }
       for (int j = 0; j < op.k; ++j) {
         if (op.tl[j] < 0 || op.tl[j] >= pd.T) return fail(SV_ERR_UNSUPPORTED, "internal planner error: non-local target");
         for (int q = 0; q < j; ++q)
@@ -1021,14 +1095,33 @@ struct TermPlan {
 constexpr int kMaxTermsPerPass = 512;
 
 // Cover the terms' flip masks by passes: a term joins a pass when its X/Y wires
-// fit into the pass's T local bits; Z-only terms fit everywhere.  A pass starts
-// from the lowest index bits (coalesced tiles) unless its first term needs them.
+// fit into the pass's T local bits.  A pass starts from the lowest index bits
+// (coalesced tiles) unless its first term needs them.  Words with Z letters
+// only (x = 0) go to passes of their own, marked zonly, which the expectation
+// kernels sum with one transform of |psi|^2 per thread and tile.
 sv_status plan_terms(int n, const std::vector<HTerm> &terms, int Tmax, int nlow_pref, TermPlan &tp) {
   const int T = std::min(Tmax, n);
   std::vector<char> done(terms.size(), 0);
   size_t left = terms.size();
   tp.begin.assign(1, 0);
-  do {
+  {
+    std::vector<int> zonly;
+    for (size_t t = 0; t < terms.size(); ++t)
+      if (terms[t].x == 0) zonly.push_back((int)t);
+    for (size_t z0 = 0; z0 < zonly.size(); z0 += kMaxTermsPerPass) {
+      const size_t z1 = std::min(zonly.size(), z0 + kMaxTermsPerPass);
+      for (size_t i = z0; i < z1; ++i) {
+        tp.placed.push_back(zonly[i]);
+        done[zonly[i]] = 1;
+        --left;
+      }
+      PassDev pd = make_pass(n, fill_bits(0, n, T, nlow_pref));
+      pd.zonly = 1;
+      tp.passes.push_back(pd);
+      tp.begin.push_back((int)tp.placed.size());
+    }
+  }
+  while (left > 0) {
     uint64_t bits = fill_bits(0, n, std::min(T, nlow_pref), nlow_pref);
     int cnt = 0;
     for (size_t t = 0; t < terms.size() && cnt < kMaxTermsPerPass; ++t) {
@@ -1047,7 +1140,11 @@ sv_status plan_terms(int n, const std::vector<HTerm> &terms, int Tmax, int nlow_
     }
     tp.passes.push_back(make_pass(n, fill_bits(bits, n, T, nlow_pref)));
     tp.begin.push_back((int)tp.placed.size());
-  } while (left > 0);
+  }
+  if (tp.passes.empty()) {  // no terms: one empty pass, as before
+    tp.passes.push_back(make_pass(n, fill_bits(0, n, T, nlow_pref)));
+    tp.begin.push_back(0);
+  }
   return SV_OK;
 }
 
@@ -1065,6 +1162,11 @@ TermDev make_termdev(const HTerm &h, const PassDev &p) {
   t.coeff = h.coeff;
   return t;
 }
+
+// Members per adjoint multi-wire micro-op: complex64 only (three, one group of
+// eight amplitudes per thread at 2^11-amplitude tiles).  The complex128 modes
+// are bound by FP64 or double-float arithmetic, which grouping does not cut.
+int adjoint_multi_width(sv_dtype dt) { return dt == SV_C64 ? 3 : 0; }
 
 // ---- precision dispatch ---------------------------------------------------------
 struct Ops {
@@ -1316,7 +1418,8 @@ sv_status build_program(sv_state *s, const sv_tape *tape, const sv_pauli_sum *ob
   }
   SlotTable st_tab;
   p->fwd = plan_passes(n, fops, K.Tf, K.nlow_pref, 1 << 30, false, st_tab, true, true, true);
-  p->adj = plan_passes(n, aops, K.Ta, K.nlow_pref, kMaxTrainPerPass, true, st_tab, true, true);
+  p->adj = plan_passes(n, aops, K.Ta, K.nlow_pref, kMaxTrainPerPass, true, st_tab, true, true, false,
+                       adjoint_multi_width(s->dt));
   if (sv_status st = check_plan(p->fwd, n, K.nlow_pref)) {
     destroy_program(p);
     return st;
@@ -1652,7 +1755,11 @@ struct JacWs {
 // or double-float), all observables in one lambda chunk (its term tables), at
 // least four words per observable on average, at most 64 observables.
 bool expval_by_observable(const sv_program *p) {
-  return p->s->dt == SV_C128 && p->m > 0 && p->m <= 64 && p->n_chunks == 1 && p->terms.size() >= 4 * (size_t)p->m;
+  if (!(p->s->dt == SV_C128 && p->m > 0 && p->m <= 64 && p->n_chunks == 1 && p->terms.size() >= 4 * (size_t)p->m))
+    return false;
+  for (const PassDev &pd : p->tp.passes)  // Z-only words are summed faster word by word
+    if (!pd.zonly) return true;
+  return false;
 }
 
 // Rows of the term-sum buffer: one per word, or one per (pass, observable).
@@ -3155,7 +3262,8 @@ sv_status plan_both(int n, sv_dtype dtype, const sv_tape *tape, Plan &f, Plan &a
   }
   SlotTable st_tab;
   f = plan_passes(n, fops, K.Tf, K.nlow_pref, 1 << 30, false, st_tab, true, true, true);
-  a = plan_passes(n, aops, K.Ta, K.nlow_pref, kMaxTrainPerPass, true, st_tab, true, true);
+  a = plan_passes(n, aops, K.Ta, K.nlow_pref, kMaxTrainPerPass, true, st_tab, true, true, false,
+                  adjoint_multi_width(dtype));
   if (sv_status st = check_plan(f, n, K.nlow_pref)) return st;
   return check_plan(a, n, K.nlow_pref);
 }
@@ -3242,6 +3350,7 @@ sv_status sv_plan_describe(int n, sv_dtype dtype, const sv_tape *tape, int forwa
     if (!out) return;
     for (int k = 0; k < SV_PLAN_KINDS; ++k) out[k] = 0;
     for (const OpDev &o : P.ops) {
+      if (o.in_multi) continue;  // counted once, under its kMulti header
       if (o.kind == kPair) out[o.fused ? 4 : 0]++;
       else if (o.kind == kDiag) out[1]++;
       else if (o.kind == kDense) out[2]++;

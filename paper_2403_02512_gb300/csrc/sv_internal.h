@@ -82,6 +82,7 @@ struct OpDev {
   uint64_t hcmask, hcval;
   int8_t mcode[3];       // kMulti: member codes
   int8_t fused;          // kPair made from a fused run of single-wire gates (1), for plan descriptions
+  int8_t in_multi;       // adjoint plans: member of the kMulti whose header follows its k members
   int32_t mmat[3];       // kMulti: member 2x2 entries
 };
 
@@ -97,6 +98,7 @@ struct PassDev {
   int32_t n_train;                 // trainable ops in this pass
   int32_t train_base;              // row of the first trainable op in the pass's partial block
   int32_t max_k;                   // widest kDense op in the pass (selects the kernel variant)
+  int32_t zonly;                   // expectation pass whose words all have x = 0 (Z letters only)
 };
 
 // One Pauli term placed in an expectation / lambda pass.

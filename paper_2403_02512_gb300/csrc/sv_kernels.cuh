@@ -176,6 +176,55 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+__device__ __forceinline__ float shfl_x(float v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ double shfl_x(double v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ df shfl_x(df v, int o) {
+  return df_make(__shfl_xor_sync(0xffffffffu, v.h, o), __shfl_xor_sync(0xffffffffu, v.l, o));
+}
+
+// Warp sums of P per-lane values of W components each (P a power of two up
+// to 32), by reduce-scatter.  At exchange offset o = 16 >> K a lane holding
+// c > 1 values keeps one half (the upper half when bit o of its lane is set),
+// sends the other half to lane ^ o and adds what that lane sends for its kept
+// half; once one value is left, plain exchanges over the remaining offsets
+// finish the sum.  On return v[0] is the warp total of value `slot`, held by
+// the 32 / P lanes that differ only in their low log2(32 / P) bits.  The cost
+// is W (P - 1 + 5 - log2 P) additions, against 5 W P for P separate warp sums.
+template <typename R, int P, int W, int K>
+__device__ __forceinline__ void reduce_scatter_step(R (&v)[P][W], int lane, int &slot) {
+  if constexpr (K < 5) {
+    constexpr int o = 16 >> K;
+    constexpr int c = P >> K;
+    if constexpr (c > 1) {
+      constexpr int h = c / 2;
+      const bool up = (lane & o) != 0;
+#pragma unroll
+      for (int i = 0; i < h; ++i)
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+          const R send = up ? v[i][w] : v[i + h][w];
+          const R keep = up ? v[i + h][w] : v[i][w];
+          v[i][w] = keep + shfl_x(send, o);
+        }
+      if (up) slot += h;
+    } else {
+#pragma unroll
+      for (int w = 0; w < W; ++w) v[0][w] = v[0][w] + shfl_x(v[0][w], o);
+    }
+    reduce_scatter_step<R, P, W, K + 1>(v, lane, slot);
+  }
+}
+
+template <typename R, int P, int W>
+__device__ __forceinline__ bool warp_reduce_scatter(R (&v)[P][W], int lane, int &slot) {
+  static_assert(P >= 1 && P <= 32 && (P & (P - 1)) == 0, "P must be a power of two up to 32");
+  slot = 0;
+  reduce_scatter_step<R, P, W, 0>(v, lane, slot);
+  return (lane & (32 / P - 1)) == 0;  // this lane writes slot's total
+}
+
+__host__ __device__ constexpr int pow2_at_least(int v) { return v <= 1 ? 1 : 2 * pow2_at_least((v + 1) / 2); }
+
 // ---------------------------------------------------------------------------
 // Tile geometry
 // ---------------------------------------------------------------------------
@@ -609,28 +658,48 @@ __device__ __forceinline__ void dense_any(c_t<R> *s, const TileGeom &tg, const O
   }
 }
 
+// Parity count of a phase run at the local indices l = threadIdx.x + kBlock i:
+// bit j of the word is member j's parity over l's local bits and the tile bits
+// (the XOR of the transposed-mask words of l's set bits and the tile's flip
+// word), so k = k0 + popcount(word): one popcount per amplitude for all members.
+struct PhaseCount {
+  const uint64_t *xw;  // transposed local masks, one word per local bit
+  uint64_t pu;         // flip word XOR the words of the thread's bits (l's low 8 bits)
+  int k0, T;
+  __device__ __forceinline__ PhaseCount(const OpDev &op, const TileGeom &tg, const uint64_t *__restrict__ aux) {
+    const uint64_t *m = aux + 2 * op.oa;
+    const int r = op.ob, rl = op.zmask;
+    xw = m + 2 * r;
+    T = tg.T;
+    uint64_t flip = 0;  // member j's parity over the tile bits (j < rl)
+    k0 = 0;             // members without local bits: constant for the tile
+    for (int j = 0; j < r; ++j) {
+      const int f = __popcll(tg.base & __ldg(m + 2 * j + 1)) & 1;
+      if (j < rl)
+        flip |= (uint64_t)f << j;
+      else
+        k0 += f;
+    }
+    pu = flip;
+    for (int b = 0; b < 8 && b < T; ++b)
+      if ((threadIdx.x >> b) & 1) pu ^= __ldg(xw + b);
+  }
+  // k for l = threadIdx.x + kBlock * i
+  __device__ __forceinline__ int at(int i) const {
+    uint64_t w = pu;
+    for (int b = 8; b < T; ++b)
+      if ((i >> (b - 8)) & 1) w ^= __ldg(xw + b);
+    return k0 + __popcll(w);
+  }
+};
+
 // Phase run: k(l) = parities of the members over the tile's fixed bits (once
 // per tile) plus their parities over the local bits of l; then one table entry.
 template <typename R>
 __device__ void fwd_phase(c_t<R> *s, const TileGeom &tg, const OpDev &op, const c_t<R> *__restrict__ mats,
                           const uint64_t *__restrict__ aux) {
-  const uint64_t *m = aux + 2 * op.oa;
-  const int r = op.ob, rl = op.zmask;
-  uint64_t flip = 0;  // member j's parity over the tile bits (j < rl)
-  int k0 = 0;         // members without local bits: constant for the tile
-  for (int j = 0; j < r; ++j) {
-    const int f = __popcll(tg.base & __ldg(m + 2 * j + 1)) & 1;
-    if (j < rl)
-      flip |= (uint64_t)f << j;
-    else
-      k0 += f;
-  }
-  for (int l = threadIdx.x; l < tg.A; l += blockDim.x) {
-    int k = k0;
-    for (int j = 0; j < rl; ++j)
-      k += (__popc((uint32_t)l & (uint32_t)__ldg(m + 2 * j)) + (int)(flip >> j)) & 1;
-    s[l] = cmul(s[l], mats[op.mat + k]);
-  }
+  const PhaseCount pc(op, tg, aux);
+  for (int l = threadIdx.x, i = 0; l < tg.A; l += kBlock, ++i) s[l] = cmul(s[l], mats[op.mat + pc.at(i)]);
 }
 
 // Multi-wire micro-op: each thread takes groups of 2^W amplitudes (zeros
@@ -886,16 +955,26 @@ __global__ void __launch_bounds__(kBlock) k_tile_tangent(g_t<R> *__restrict__ ps
 // and written by one CTA and phi_out may equal phi_in.
 // Partial layout: partials[(blockIdx.y * m + j) * n_train + t].
 // ---------------------------------------------------------------------------
+// The warp's partial sums of NG x B accumulators (generator g, lambda jj)
+// go to their per-warp slots accs[((train + g) * B + jj) * nwarps + warp],
+// summed over the warp by one reduce-scatter.
+template <typename R, int NG, int B>
+__device__ __forceinline__ void flush_acc(const R (&acc)[NG][B], int bb, int train, double *accs, int nwarps,
+                                          int warp, int lane, R scale) {
+  constexpr int P = pow2_at_least(NG * B);
+  R v[P][1];
+#pragma unroll
+  for (int i = 0; i < P; ++i) v[i][0] = i < NG * B ? acc[i / B][i % B] : R(0);
+  int slot;
+  const bool writer = warp_reduce_scatter<R, P, 1>(v, lane, slot);
+  const int g = slot / B, jj = slot % B;
+  if (writer && g < NG && jj < bb) WarpAcc<R>::add(&accs[((train + g) * B + jj) * nwarps + warp], scale * v[0][0]);
+}
+
 template <typename R, int B>
 __device__ __forceinline__ void flush_acc(const R (&acc)[B], int bb, int train, double *accs, int nwarps, int warp,
                                           int lane, R scale) {
-#pragma unroll
-  for (int jj = 0; jj < B; ++jj) {
-    if (jj < bb) {
-      const R v = scale * warp_sum(acc[jj]);
-      if (lane == 0) WarpAcc<R>::add(&accs[(train * B + jj) * nwarps + warp], v);
-    }
-  }
+  flush_acc<R, 1, B>(reinterpret_cast<const R(&)[1][B]>(acc), bb, train, accs, nwarps, warp, lane, scale);
 }
 
 // Adjoint pair micro-op on phi and B lambda tiles (slots past the CTA's last
@@ -965,10 +1044,21 @@ __device__ __forceinline__ void adj_pair(c_t<R> *sp, c_t<R> *sl, const TileGeom 
 }
 
 // Fused run in the adjoint sweep: phi and B lambdas on pairs (a, b); for each
-// of NG generators G' (Hermitian: G00, G11 real, G10 = conj(G01)) the phi-side
-// products w = G' phi are formed once per pair and every lambda adds
-// Im(conj(l_a) w_a + conj(l_b) w_b) before the run's U^dagger is applied.
-template <typename R, int B, int NG, bool CTL>
+// of NG generators G' (Hermitian: G00, G11 real, G10 = conj(G01)) the
+// contribution Im <lambda | G' phi> is taken before the run's U^dagger is
+// applied.  Two ways to form it:
+//  * products: w = G' phi once per pair, then every lambda adds
+//    Im(conj(l_a) w_a + conj(l_b) w_b) (4 FMA per generator and lambda);
+//  * moments (MOM): every lambda accumulates four real bilinear moments of
+//    (lambda, phi) over its pairs,
+//      D0 = Im(conj(l_a) p_a), D1 = Im(conj(l_b) p_b),
+//      SY = Im(conj(l_a) p_b) + Im(conj(l_b) p_a),
+//      SX = Re(conj(l_a) p_b) - Re(conj(l_b) p_a)   (12 FMA per lambda),
+//    and after the warp reduction each generator's contribution is
+//      G00 D0 + G11 D1 + Re(G01) SY + Im(G01) SX,
+//    which equals the sum over pairs of Im(conj(l_a)(G' p)_a + conj(l_b)(G' p)_b).
+//    No w = G' phi products are formed.
+template <typename R, int B, int NG, bool CTL, bool MOM>
 __device__ void adj_fused_t(c_t<R> *sp, c_t<R> *sl, const TileGeom &tg, const OpDev &op,
                             const c_t<R> *__restrict__ mats, int bb, double *accs, int nwarps, int warp, int lane) {
   using C = c_t<R>;
@@ -983,9 +1073,10 @@ __device__ void adj_fused_t(c_t<R> *sp, c_t<R> *sl, const TileGeom &tg, const Op
     g01[g] = mats[op.gmat + 4 * g + 1];
     g11[g] = mats[op.gmat + 4 * g + 3].x;
   }
-  R acc[NG][B];
+  constexpr int NA = MOM ? 4 : NG;  // accumulators per lambda
+  R acc[NA][B];
 #pragma unroll
-  for (int g = 0; g < NG; ++g)
+  for (int g = 0; g < NA; ++g)
 #pragma unroll
     for (int jj = 0; jj < B; ++jj) acc[g][jj] = R(0);
   const OpRegs o(op);
@@ -996,47 +1087,84 @@ __device__ void adj_fused_t(c_t<R> *sp, c_t<R> *sl, const TileGeom &tg, const Op
     if (CTL && (((uint32_t)l0 & lcm) != lcv)) continue;
     const int ia = l0 + o.oa, ib = l0 + o.ob;
     C pa = sp[ia], pb = sp[ib];
-    C wa[NG], wb[NG];
+    if constexpr (MOM) {
+      const C qa = pa, qb = pb;  // phi before the un-apply
+      pair_apply<R>(mGen, Mr, pa, pb);
+      sp[ia] = pa;
+      sp[ib] = pb;
 #pragma unroll
-    for (int g = 0; g < NG; ++g) {
-      // wa = g00 pa + g01 pb ; wb = conj(g01) pa + g11 pb
-      wa[g].x = fma(g01[g].x, pb.x, fma(-g01[g].y, pb.y, g00[g] * pa.x));
-      wa[g].y = fma(g01[g].x, pb.y, fma(g01[g].y, pb.x, g00[g] * pa.y));
-      wb[g].x = fma(g01[g].x, pa.x, fma(g01[g].y, pa.y, g11[g] * pb.x));
-      wb[g].y = fma(g01[g].x, pa.y, fma(-g01[g].y, pa.x, g11[g] * pb.y));
-    }
-    pair_apply<R>(mGen, Mr, pa, pb);
-    sp[ia] = pa;
-    sp[ib] = pb;
-#pragma unroll
-    for (int jj = 0; jj < B; ++jj) {
-      C la = sl[jj * tg.A + ia], lb = sl[jj * tg.A + ib];
+      for (int jj = 0; jj < B; ++jj) {
+        C la = sl[jj * tg.A + ia], lb = sl[jj * tg.A + ib];
+        acc[0][jj] = fma(la.x, qa.y, fma(-la.y, qa.x, acc[0][jj]));
+        acc[1][jj] = fma(lb.x, qb.y, fma(-lb.y, qb.x, acc[1][jj]));
+        acc[2][jj] = fma(la.x, qb.y, fma(-la.y, qb.x, fma(lb.x, qa.y, fma(-lb.y, qa.x, acc[2][jj]))));
+        acc[3][jj] = fma(la.x, qb.x, fma(la.y, qb.y, fma(-lb.x, qa.x, fma(-lb.y, qa.y, acc[3][jj]))));
+        pair_apply<R>(mGen, Mr, la, lb);
+        sl[jj * tg.A + ia] = la;
+        sl[jj * tg.A + ib] = lb;
+      }
+    } else {
+      C wa[NG], wb[NG];
 #pragma unroll
       for (int g = 0; g < NG; ++g) {
-        R a = acc[g][jj];
-        a = fma(la.x, wa[g].y, a);
-        a = fma(-la.y, wa[g].x, a);
-        a = fma(lb.x, wb[g].y, a);
-        a = fma(-lb.y, wb[g].x, a);
-        acc[g][jj] = a;
+        // wa = g00 pa + g01 pb ; wb = conj(g01) pa + g11 pb
+        wa[g].x = fma(g01[g].x, pb.x, fma(-g01[g].y, pb.y, g00[g] * pa.x));
+        wa[g].y = fma(g01[g].x, pb.y, fma(g01[g].y, pb.x, g00[g] * pa.y));
+        wb[g].x = fma(g01[g].x, pa.x, fma(g01[g].y, pa.y, g11[g] * pb.x));
+        wb[g].y = fma(g01[g].x, pa.y, fma(-g01[g].y, pa.x, g11[g] * pb.y));
       }
-      pair_apply<R>(mGen, Mr, la, lb);
-      sl[jj * tg.A + ia] = la;
-      sl[jj * tg.A + ib] = lb;
+      pair_apply<R>(mGen, Mr, pa, pb);
+      sp[ia] = pa;
+      sp[ib] = pb;
+#pragma unroll
+      for (int jj = 0; jj < B; ++jj) {
+        C la = sl[jj * tg.A + ia], lb = sl[jj * tg.A + ib];
+#pragma unroll
+        for (int g = 0; g < NG; ++g) {
+          R a = acc[g][jj];
+          a = fma(la.x, wa[g].y, a);
+          a = fma(-la.y, wa[g].x, a);
+          a = fma(lb.x, wb[g].y, a);
+          a = fma(-lb.y, wb[g].x, a);
+          acc[g][jj] = a;
+        }
+        pair_apply<R>(mGen, Mr, la, lb);
+        sl[jj * tg.A + ia] = la;
+        sl[jj * tg.A + ib] = lb;
+      }
     }
   }
+  if constexpr (MOM) {
+    // reduce-scatter over the lambdas with the four moments as one value
+    R v[B][4];
 #pragma unroll
-  for (int g = 0; g < NG; ++g) flush_acc<R, B>(acc[g], bb, op.train + g, accs, nwarps, warp, lane, R(1));
+    for (int jj = 0; jj < B; ++jj)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) v[jj][q] = acc[q][jj];
+    int jj;
+    const bool writer = warp_reduce_scatter<R, B, 4>(v, lane, jj);
+    if (writer && jj < bb)
+#pragma unroll
+      for (int g = 0; g < NG; ++g) {
+        const R val = g00[g] * v[0][0] + g11[g] * v[0][1] + g01[g].x * v[0][2] + g01[g].y * v[0][3];
+        WarpAcc<R>::add(&accs[((op.train + g) * B + jj) * nwarps + warp], val);
+      }
+  } else {
+    flush_acc<R, NG, B>(acc, bb, op.train, accs, nwarps, warp, lane, R(1));
+  }
 }
 
 template <typename R, int B, int NG>
 __device__ __forceinline__ void adj_fused_c(c_t<R> *sp, c_t<R> *sl, const TileGeom &tg, const OpDev &op,
                                             const c_t<R> *mats, int bb, double *accs, int nwarps, int warp,
                                             int lane) {
+  // moments when they cost fewer operations than the products (three
+  // generators; two with at most two lambdas)
+  constexpr bool MOM = NG == 3 || (NG == 2 && B <= 2);
   if (op.lcmask)
-    adj_fused_t<R, B, NG, true>(sp, sl, tg, op, mats, bb, accs, nwarps, warp, lane);
+    adj_fused_t<R, B, NG, true, MOM>(sp, sl, tg, op, mats, bb, accs, nwarps, warp, lane);
   else
-    adj_fused_t<R, B, NG, false>(sp, sl, tg, op, mats, bb, accs, nwarps, warp, lane);
+    adj_fused_t<R, B, NG, false, MOM>(sp, sl, tg, op, mats, bb, accs, nwarps, warp, lane);
 }
 
 template <typename R, int B>
@@ -1058,25 +1186,14 @@ template <typename R, int B>
 __device__ void adj_phase(c_t<R> *sp, c_t<R> *sl, const TileGeom &tg, const OpDev &op, const c_t<R> *__restrict__ mats,
                           const uint64_t *__restrict__ aux, int bb, double *accs, int nwarps, int warp, int lane) {
   using C = c_t<R>;
-  const uint64_t *m = aux + 2 * op.oa;
-  const int r = op.ob, rl = op.zmask;
+  const int r = op.ob;
   const bool tr = op.train >= 0;
-  uint64_t flip = 0;
-  int k0 = 0;
-  for (int j = 0; j < r; ++j) {
-    const int f = __popcll(tg.base & __ldg(m + 2 * j + 1)) & 1;
-    if (j < rl)
-      flip |= (uint64_t)f << j;
-    else
-      k0 += f;
-  }
+  const PhaseCount pc(op, tg, aux);
   R acc[B];
 #pragma unroll
   for (int jj = 0; jj < B; ++jj) acc[jj] = R(0);
-  for (int l = threadIdx.x; l < tg.A; l += blockDim.x) {
-    int k = k0;
-    for (int j = 0; j < rl; ++j)
-      k += (__popc((uint32_t)l & (uint32_t)__ldg(m + 2 * j)) + (int)(flip >> j)) & 1;
+  for (int l = threadIdx.x, i = 0; l < tg.A; l += kBlock, ++i) {
+    const int k = pc.at(i);
     const C e = mats[op.mat + k];
     const C p = sp[l];
     const R g = R(r - 2 * k);
@@ -1180,6 +1297,118 @@ __device__ __forceinline__ void adj_diag(c_t<R> *sp, c_t<R> *sl, const TileGeom 
   }
 }
 
+// Adjoint multi-wire micro-op: W uncontrolled single-wire pair micro-ops on
+// distinct local bits, stored (in forward order) as mem[0 .. W) before their
+// header.  A thread takes the 2^W amplitudes of a group that share every
+// other local bit, for phi and then for each lambda in turn: the
+// contributions of the trainable members come first, all from the group's
+// values before any member is un-applied (the members act on distinct wires,
+// so each member's generator commutes with the other members' blocks and the
+// inner product is the same as right after that member), then every member's
+// block E = U^dagger is applied in registers.  Contributions are kept as the
+// four moments of the fused runs (D0, D1, SY, SX per member and lambda) and
+// contracted after the warp reduction: a fused run with its generators, an X
+// generator as gs SY, a Y generator as -gs SX.
+template <typename R, int B, int W>
+__device__ void adj_multi_t(c_t<R> *sp, c_t<R> *sl, const TileGeom &tg, const OpDev *__restrict__ mem,
+                            const OpDev &hd, const c_t<R> *__restrict__ mats, int bb, double *accs, int nwarps,
+                            int warp, int lane) {
+  using C = c_t<R>;
+  constexpr int G = 1 << W;
+  C U[W][4];
+  int code[W], off[G];
+  bool tr[W];
+#pragma unroll
+  for (int j = 0; j < W; ++j) {
+    code[j] = mem[j].code;
+    tr[j] = mem[j].train >= 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      U[j][q] = (code[j] == mGen || code[j] == mReal || code[j] == mImOff) ? mats[mem[j].mat + q] : C();
+  }
+#pragma unroll
+  for (int i = 0; i < G; ++i) {
+    int o = 0;
+#pragma unroll
+    for (int j = 0; j < W; ++j)
+      if ((i >> j) & 1) o += 1 << mem[j].tl[0];
+    off[i] = o;
+  }
+  R acc[B][W][4];
+#pragma unroll
+  for (int jj = 0; jj < B; ++jj)
+#pragma unroll
+    for (int j = 0; j < W; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[jj][j][q] = R(0);
+  const int ts0 = hd.ts[0], ts1 = hd.ts[1], ts2 = hd.ts[2];
+  const int ng = tg.A >> W;
+  for (int g = threadIdx.x; g < ng; g += blockDim.x) {
+    int l0 = insert_zero(insert_zero(g, ts0), ts1);
+    if (W > 2) l0 = insert_zero(l0, ts2);
+    C p[G];
+#pragma unroll
+    for (int i = 0; i < G; ++i) p[i] = sp[l0 + off[i]];
+#pragma unroll
+    for (int jj = 0; jj < B; ++jj) {
+      C v[G];
+#pragma unroll
+      for (int i = 0; i < G; ++i) v[i] = sl[jj * tg.A + l0 + off[i]];
+#pragma unroll
+      for (int j = 0; j < W; ++j) {
+        if (!tr[j]) continue;
+#pragma unroll
+        for (int i = 0; i < G; ++i) {
+          if ((i >> j) & 1) continue;
+          const C qa = p[i], qb = p[i | (1 << j)], la = v[i], lb = v[i | (1 << j)];
+          acc[jj][j][0] = fma(la.x, qa.y, fma(-la.y, qa.x, acc[jj][j][0]));
+          acc[jj][j][1] = fma(lb.x, qb.y, fma(-lb.y, qb.x, acc[jj][j][1]));
+          acc[jj][j][2] = fma(la.x, qb.y, fma(-la.y, qb.x, fma(lb.x, qa.y, fma(-lb.y, qa.x, acc[jj][j][2]))));
+          acc[jj][j][3] = fma(la.x, qb.x, fma(la.y, qb.y, fma(-lb.x, qa.x, fma(-lb.y, qa.y, acc[jj][j][3]))));
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < W; ++j)
+#pragma unroll
+        for (int i = 0; i < G; ++i)
+          if (!((i >> j) & 1)) pair_apply<R>(code[j], U[j], v[i], v[i | (1 << j)]);
+#pragma unroll
+      for (int i = 0; i < G; ++i) sl[jj * tg.A + l0 + off[i]] = v[i];
+    }
+#pragma unroll
+    for (int j = 0; j < W; ++j)
+#pragma unroll
+      for (int i = 0; i < G; ++i)
+        if (!((i >> j) & 1)) pair_apply<R>(code[j], U[j], p[i], p[i | (1 << j)]);
+#pragma unroll
+    for (int i = 0; i < G; ++i) sp[l0 + off[i]] = p[i];
+  }
+  // warp sums of the moments of every (lambda, member): slot s = jj * W + j
+  constexpr int P = pow2_at_least(B * W);
+  R v[P][4];
+#pragma unroll
+  for (int s = 0; s < P; ++s)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[s][q] = s < B * W ? acc[s / W][s % W][q] : R(0);
+  int slot;
+  const bool writer = warp_reduce_scatter<R, P, 4>(v, lane, slot);
+  const int jj = slot / W, j = slot % W;
+  if (!writer || slot >= B * W || jj >= bb) return;
+  const OpDev &mj = mem[j];
+  if (mj.train < 0) return;
+  if (mj.gcode == gHerm) {
+    for (int gi = 0; gi < mj.ngen; ++gi) {
+      const R g00 = mats[mj.gmat + 4 * gi].x, g11 = mats[mj.gmat + 4 * gi + 3].x;
+      const C g01 = mats[mj.gmat + 4 * gi + 1];
+      const R val = g00 * v[0][0] + g11 * v[0][1] + g01.x * v[0][2] + g01.y * v[0][3];
+      WarpAcc<R>::add(&accs[((mj.train + gi) * B + jj) * nwarps + warp], val);
+    }
+  } else {
+    const R val = (R)mj.gs * (mj.gcode == gX ? v[0][2] : -v[0][3]);
+    WarpAcc<R>::add(&accs[(mj.train * B + jj) * nwarps + warp], val);
+  }
+}
+
 template <typename R, int MAXK, int B>
 __global__ void __launch_bounds__(kBlock, (std::is_same<R, double>::value && B >= 4) ? 1 : 2) k_tile_adjoint(const g_t<R> *phi_in, g_t<R> *phi_out,
                                                              g_t<R> *__restrict__ lam_base, int n, int m,
@@ -1225,6 +1454,17 @@ __global__ void __launch_bounds__(kBlock, (std::is_same<R, double>::value && B >
     tile_async_convert<R>(sp, A * (1 + bb));  // sp and the lambda tiles are contiguous
     for (int o = pass.op_end - 1; o >= pass.op_begin; --o) {
       const OpDev &op = ops[o];
+      if constexpr (std::is_same<R, float>::value) {
+        if (op.kind == kMulti) {  // header after its members ops[o - k .. o)
+          if (op.k == 2)
+            adj_multi_t<R, B, 2>(sp, sl, tg, ops + o - 2, op, mats, bb, accs, nwarps, warp, lane);
+          else
+            adj_multi_t<R, B, 3>(sp, sl, tg, ops + o - 3, op, mats, bb, accs, nwarps, warp, lane);
+          o -= op.k;
+          if (o > pass.op_begin) __syncthreads();
+          continue;
+        }
+      }
       if (op.kind == kDense) {
         dense_any<R, MAXK>(sp, tg, op, mats);
         for (int jj = 0; jj < bb; ++jj) dense_any<R, MAXK>(sl + (size_t)jj * A, tg, op, mats);
@@ -1326,6 +1566,139 @@ __global__ void __launch_bounds__(kBlock) k_expval(const g_t<R> *__restrict__ ps
 }
 
 // ---------------------------------------------------------------------------
+// Expectation pass for Pauli words with only Z letters (x = 0):
+//   <P_t> = sum_g (-1)^{popcount(g & z_t)} |psi_g|^2.
+// Thread u of the CTA owns the tile's local indices l = u + 256 i, i < NA =
+// 2^NB (NB = T - 8).  Over those the sign factors: popcount(g & z) =
+// popcount(tile base & z) + popcount(u & z_l) + popcount(i & (z_l >> 8)), with
+// z_l the word's mask in local bits.  One Walsh-Hadamard transform of the
+// thread's NA values p_i = |psi|^2, W[k] = sum_i (-1)^{popcount(i & k)} p_i,
+// therefore gives every Z word's signed sum over the thread's amplitudes:
+// (+-) W[z_l >> 8], the sign from the tile base and the thread bits.  Each
+// thread accumulates its words over all its tiles in registers (words in
+// chunks of 32, one read of the state per chunk), then one reduce-scatter per
+// warp and fixed-order sums give partials[b * n_terms + t].
+// ---------------------------------------------------------------------------
+// v with its sign bit flipped when p is 1.
+__device__ __forceinline__ float flip_sign(float v, uint32_t p) { return __int_as_float(__float_as_int(v) ^ (int)(p << 31)); }
+__device__ __forceinline__ double flip_sign(double v, uint32_t p) {
+  return __longlong_as_double(__double_as_longlong(v) ^ ((long long)p << 63));
+}
+__device__ __forceinline__ df flip_sign(df v, uint32_t p) { return df_make(flip_sign(v.h, p), flip_sign(v.l, p)); }
+
+template <typename R>
+struct ZSum;  // per-thread running sum of a word over tiles
+template <>
+struct ZSum<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double v) { s += v; }
+  __device__ __forceinline__ double value() const { return s; }
+};
+template <>
+struct ZSum<float> {  // compensated (TwoSum): no FP64 instruction per tile
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float v) {
+    float t, e;
+    two_sum(s, v, t, e);
+    s = t;
+    c += e;
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+template <>
+struct ZSum<df> {
+  df s = df(0.f);
+  __device__ __forceinline__ void add(df v) { s = s + v; }
+  __device__ __forceinline__ double value() const { return (double)s; }
+};
+
+constexpr int kZChunk = 32;
+
+template <typename R, int NB>
+__global__ void __launch_bounds__(kBlock) k_expval_z(const g_t<R> *__restrict__ psi, int n, const PassDev pass,
+                                                      const TermDev *__restrict__ terms, int n_terms,
+                                                      double *__restrict__ partials) {
+  constexpr int NA = 1 << NB;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int nch = 1 << (pass.T - pass.nlow);
+  uint64_t *lut = reinterpret_cast<uint64_t *>(smem);
+  R *sw = reinterpret_cast<R *>(lut + nch);                        // W[k] of thread u at sw[k * kBlock + u]
+  uint64_t *zg = reinterpret_cast<uint64_t *>(sw + NA * kBlock);    // chunk words' global z masks
+  int *zk = reinterpret_cast<int *>(zg + kZChunk);                  // ... their upper local z bits
+  double *accs = reinterpret_cast<double *>(zk + kZChunk);          // [n_terms][nwarps]
+  const int nwarps = blockDim.x >> 5;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int u = threadIdx.x;
+  build_lut(lut, pass);
+  for (int i = threadIdx.x; i < n_terms * nwarps; i += blockDim.x) accs[i] = 0.0;
+  TileGeom tg;
+  tg.T = pass.T;
+  tg.nlow = pass.nlow;
+  tg.A = 1 << pass.T;
+  tg.lowmask = (1u << pass.nlow) - 1u;
+  tg.lut = lut;
+  const uint64_t ntiles = 1ull << (n - pass.T);
+  for (int t0 = 0; t0 < n_terms; t0 += kZChunk) {
+    const int nt = min(kZChunk, n_terms - t0);
+    __syncthreads();  // the previous chunk's words are no longer read
+    uint32_t par_thread = 0;  // bit t: parity of the thread bits under word t
+    for (int t = 0; t < nt; ++t) {
+      const uint64_t z = terms[t0 + t].zg;
+      uint32_t zl = 0;  // z in local bits
+      for (int b = 0; b < pass.T; ++b)
+        if (z >> pass.pos[b] & 1) zl |= 1u << b;
+      par_thread |= (uint32_t)(__popc(zl & (uint32_t)u & 0xFFu) & 1) << t;
+      if (threadIdx.x == 0) {
+        zg[t] = z;
+        zk[t] = (int)(zl >> 8);
+      }
+    }
+    __syncthreads();  // zg / zk written (each thread reads only its own column of sw)
+    ZSum<R> acc[kZChunk];
+    for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+      tg.base = tile_base(pass, tile);
+      R w[NA];
+#pragma unroll
+      for (int i = 0; i < NA; ++i) {
+        const c_t<R> a = to_c<R>(__ldcs(psi + tg.gidx(u + i * kBlock)));
+        w[i] = a.x * a.x + a.y * a.y;
+      }
+#pragma unroll
+      for (int b = 0; b < NB; ++b)
+#pragma unroll
+        for (int i = 0; i < NA; ++i)
+          if (!(i >> b & 1)) {
+            const R x = w[i], y = w[i | (1 << b)];
+            w[i] = x + y;
+            w[i | (1 << b)] = x - y;
+          }
+#pragma unroll
+      for (int i = 0; i < NA; ++i) sw[i * kBlock + u] = w[i];
+#pragma unroll
+      for (int t = 0; t < kZChunk; ++t) {
+        if (t < nt) {
+          const uint32_t neg = ((par_thread >> t) & 1u) ^ (uint32_t)(__popcll(tg.base & zg[t]) & 1);
+          acc[t].add(flip_sign(sw[zk[t] * kBlock + u], neg));
+        }
+      }
+    }
+    // per-warp sums of the chunk's words
+    double v[kZChunk][1];
+#pragma unroll
+    for (int t = 0; t < kZChunk; ++t) v[t][0] = t < nt ? acc[t].value() : 0.0;
+    int slot;
+    const bool writer = warp_reduce_scatter<double, kZChunk, 1>(v, lane, slot);
+    if (writer && slot < nt) accs[(t0 + slot) * nwarps + warp] += v[0][0];
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < n_terms; t += blockDim.x) {
+    double s = 0.0;
+    for (int wi = 0; wi < nwarps; ++wi) s += accs[t * nwarps + wi];
+    partials[(size_t)blockIdx.x * n_terms + t] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Lambda initialisation: lam_o += sum_{t in o} c_t P_t phi over the terms of
 // this pass (output-stationary: each lambda amplitude written once per pass).
 //   (P phi)_g = i^{ny} (-1)^{popcount((g ^ x) & z)} phi_{g ^ x}
@@ -1333,12 +1706,6 @@ __global__ void __launch_bounds__(kBlock) k_expval(const g_t<R> *__restrict__ ps
 // and signed coefficients formed once per thread), as in k_expval_obs below.
 // blockIdx.y = observable within the chunk; first != 0 overwrites lam.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float flip_sign(float v, uint32_t p) { return __int_as_float(__float_as_int(v) ^ (int)(p << 31)); }
-__device__ __forceinline__ double flip_sign(double v, uint32_t p) {
-  return __longlong_as_double(__double_as_longlong(v) ^ ((long long)p << 63));
-}
-__device__ __forceinline__ df flip_sign(df v, uint32_t p) { return df_make(flip_sign(v.h, p), flip_sign(v.l, p)); }
-
 // h[k] += i^{ny} c (-1)^{popcount((g[k] ^ x) & z)} s[l_k ^ x_l] for the words [t0, t1).
 template <typename R, int NA>
 __device__ __forceinline__ void pauli_rows(const c_t<R> *s, int A, const uint64_t (&g)[NA],
@@ -1796,29 +2163,45 @@ __device__ __forceinline__ uint64_t stream_index(const StreamDev &sd, uint64_t u
   return u | sd.fixval;
 }
 
-// Streams of a double-float state use FP64 arithmetic on the stored complex128
-// amplitudes: one pass does a few operations per amplitude, fewer than the
-// conversions to and from double-float would cost.
-template <typename R>
-using stream_t = typename std::conditional<std::is_same<R, df>::value, double, R>::type;
+// Streams of a double-float state compute in double-float like its tile
+// passes: the stored complex128 amplitudes are split into float pairs with
+// integer operations, and the result costs one FP64 addition per real value
+// on the way back (two per amplitude, where FP64 gate arithmetic takes four
+// to eight).  Permutations and sign flips (swap, Y, the all-ones negation)
+// move the stored doubles as they are.
+template <typename R, bool PERM>
+using stream_r = typename std::conditional<std::is_same<R, df>::value && PERM, double, R>::type;
 
 template <typename R>
-__device__ __forceinline__ c_t<stream_t<R>> stream_entry(const c_t<R> &e) {
+__device__ __forceinline__ c_t<R> stream_in(g_t<R> v) {
+  if constexpr (std::is_same<R, df>::value) {
+    dfc r;
+    r.x = df_split_fast(v.x);
+    r.y = df_split_fast(v.y);
+    return r;
+  } else {
+    return v;
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ g_t<R> stream_out(c_t<R> v) {
   if constexpr (std::is_same<R, df>::value)
-    return make_double2((double)e.x, (double)e.y);
+    return make_double2(df_join_fast(v.x), df_join_fast(v.y));
   else
-    return e;
+    return v;
 }
 
 template <typename R0, int CODE>
 __global__ void __launch_bounds__(kBlock) k_stream_pair(g_t<R0> *__restrict__ psi, uint64_t units, const StreamDev sd,
                                                         const c_t<R0> *__restrict__ mats) {
-  using R = stream_t<R0>;
+  using R = stream_r<R0, CODE == mSwap || CODE == mY>;
   using C = c_t<R>;
   C M[4];
-  if (CODE == mGen || CODE == mReal || CODE == mImOff)
+  if constexpr (std::is_same<R, R0>::value)
+    if (CODE == mGen || CODE == mReal || CODE == mImOff)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) M[q] = stream_entry<R0>(mats[sd.mat + q]);
+      for (int q = 0; q < 4; ++q) M[q] = mats[sd.mat + q];
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   if constexpr (std::is_same<R, float>::value) {
     if (sd.vec2) {  // units 2v, 2v + 1 are adjacent amplitudes in both members
@@ -1887,10 +2270,10 @@ __global__ void __launch_bounds__(kBlock) k_stream_pair(g_t<R0> *__restrict__ ps
 #pragma unroll
     for (int r = 0; r < kStreamUnroll; ++r) {
       if (u0 + r * stride >= units) break;
-      C va = to_c<R>(a[r]), vb = to_c<R>(b[r]);
+      C va = stream_in<R>(a[r]), vb = stream_in<R>(b[r]);
       pair_apply<R>(CODE, M, va, vb);
-      __stcs(psi + ia[r] + sd.oa, to_g<R>(va));
-      __stcs(psi + ia[r] + sd.ob, to_g<R>(vb));
+      __stcs(psi + ia[r] + sd.oa, stream_out<R>(va));
+      __stcs(psi + ia[r] + sd.ob, stream_out<R>(vb));
     }
   }
 }
@@ -1910,12 +2293,12 @@ __device__ __forceinline__ c_t<R> stream_diag_mul(const StreamDev &sd, const c_t
 template <typename R0, int KD, bool NEG>
 __global__ void __launch_bounds__(kBlock) k_stream_diag(g_t<R0> *__restrict__ psi, uint64_t units, const StreamDev sd,
                                                         const c_t<R0> *__restrict__ mats) {
-  using R = stream_t<R0>;
+  using R = stream_r<R0, NEG>;
   using C = c_t<R>;
   C d[4];
-  if (!NEG)
+  if constexpr (!NEG)
 #pragma unroll
-    for (int e = 0; e < 4; ++e) d[e] = e < (1 << KD) ? stream_entry<R0>(mats[sd.mat + e]) : C();
+    for (int e = 0; e < 4; ++e) d[e] = e < (1 << KD) ? mats[sd.mat + e] : C();
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   if constexpr (std::is_same<R, float>::value) {
     if (sd.vec2) {
@@ -1953,7 +2336,7 @@ __global__ void __launch_bounds__(kBlock) k_stream_diag(g_t<R0> *__restrict__ ps
 #pragma unroll
     for (int r = 0; r < kStreamUnroll; ++r) {
       if (u0 + r * stride >= units) break;
-      __stcs(psi + ia[r], to_g<R>(stream_diag_mul<R, KD, NEG>(sd, d, ia[r], to_c<R>(a[r]))));
+      __stcs(psi + ia[r], stream_out<R>(stream_diag_mul<R, KD, NEG>(sd, d, ia[r], stream_in<R>(a[r]))));
     }
   }
 }
@@ -2210,6 +2593,57 @@ __device__ __forceinline__ unsigned long long global_ns() {
 
 constexpr int kBatchChunk = 8;  // work items a CTA takes from the queue at once
 
+// Z-word partials of a batch tile in its last pass (as in k_expval_z): thread
+// u holds p_i = |psi|^2 at l = u + kBlock i (i < 2^NB, NB = T - 8), one
+// Walsh-Hadamard transform gives every word's signed sum over them, written to
+// the thread's own column of sw; zs[t] holds word t's local mask (low 32 bits)
+// and its parity over the tile bits (bit 32).  Per-warp sums go to accs.
+template <typename R, int NB>
+__device__ __forceinline__ void batch_zsums(const R (&p)[1 << NB], R *sw, const uint64_t *zs, int n_terms,
+                                            double *accs, int nwarps, int warp, int lane) {
+  constexpr int NA = 1 << NB;
+  R w[NA];
+#pragma unroll
+  for (int i = 0; i < NA; ++i) w[i] = p[i];
+#pragma unroll
+  for (int b = 0; b < NB; ++b)
+#pragma unroll
+    for (int i = 0; i < NA; ++i)
+      if (!(i >> b & 1)) {
+        const R x = w[i], y = w[i | (1 << b)];
+        w[i] = x + y;
+        w[i | (1 << b)] = x - y;
+      }
+  const int u = threadIdx.x;
+#pragma unroll
+  for (int i = 0; i < NA; ++i) sw[i * kBlock + u] = w[i];
+  for (int t0 = 0; t0 < n_terms; t0 += 32) {
+    R v[32][1];
+#pragma unroll
+    for (int t = 0; t < 32; ++t) {
+      v[t][0] = R(0);
+      if (t0 + t < n_terms) {
+        const uint64_t z = zs[t0 + t];
+        const uint32_t zl = (uint32_t)z;
+        const uint32_t neg = (uint32_t)(z >> 32 & 1) ^ (uint32_t)(__popc(zl & (uint32_t)u & 0xFFu) & 1);
+        v[t][0] = flip_sign(sw[((zl >> 8) & (NA - 1)) * kBlock + u], neg);
+      }
+    }
+    int slot;
+    const bool writer = warp_reduce_scatter<R, 32, 1>(v, lane, slot);
+    if (writer && t0 + slot < n_terms) accs[(t0 + slot) * nwarps + warp] = (double)v[0][0];
+  }
+}
+
+template <typename R, int NB>
+__device__ __forceinline__ void batch_load_p(const c_t<R> *s, R (&p)[1 << NB]) {
+#pragma unroll
+  for (int i = 0; i < (1 << NB); ++i) {
+    const c_t<R> a = s[threadIdx.x + kBlock * i];
+    p[i] = a.x * a.x + a.y * a.y;
+  }
+}
+
 template <typename R, int MAXK>
 __global__ void __launch_bounds__(kBlock, 3) k_batch(g_t<R> *__restrict__ states, const BatchCircuit *__restrict__ circs,
                                                    const PassDev *__restrict__ passes, const OpDev *__restrict__ ops,
@@ -2225,6 +2659,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_batch(g_t<R> *__restrict__ states
   C *s = reinterpret_cast<C *>(smem);
   uint64_t *lut = reinterpret_cast<uint64_t *>(s + (1 << max_T));
   double *accs = reinterpret_cast<double *>(lut + (1 << max_T));  // [max_terms][nwarps]
+  uint64_t *zs = reinterpret_cast<uint64_t *>(accs + max_terms * (blockDim.x >> 5));  // [max_terms]
   __shared__ long long s_first;
   __shared__ int s_seg, s_abort, s_new_seg;
   __shared__ PassDev s_pass;
@@ -2316,7 +2751,40 @@ __global__ void __launch_bounds__(kBlock, 3) k_batch(g_t<R> *__restrict__ states
       }
       __syncthreads();
       const bool last = sg.pass == cc.n_pass - 1;
-      if (last && cc.n_terms > 0) {
+      if (last && cc.n_terms > 0 && pass.T >= 8 && pass.T <= 12) {
+        // <Z word> partials of this tile, sum_l (-1)^popcount(g & z) |psi_l|^2, by one
+        // Walsh-Hadamard transform per thread (the tile buffer holds the transforms)
+        for (int t = threadIdx.x; t < cc.n_terms; t += blockDim.x) {
+          const uint64_t z = terms[cc.term_begin + t].z;
+          uint32_t zl = 0;
+          for (int b = 0; b < pass.T; ++b)
+            if (z >> pass.pos[b] & 1) zl |= 1u << b;
+          zs[t] = zl | ((uint64_t)(__popcll(tg.base & z) & 1) << 32);
+        }
+        R pr[16];
+        if (pass.T == 12) batch_load_p<R, 4>(s, reinterpret_cast<R(&)[16]>(pr));
+        else if (pass.T == 11) batch_load_p<R, 3>(s, reinterpret_cast<R(&)[8]>(pr));
+        else if (pass.T == 10) batch_load_p<R, 2>(s, reinterpret_cast<R(&)[4]>(pr));
+        else if (pass.T == 9) batch_load_p<R, 1>(s, reinterpret_cast<R(&)[2]>(pr));
+        else batch_load_p<R, 0>(s, reinterpret_cast<R(&)[1]>(pr));
+        __syncthreads();  // the words' masks are in place; every thread has read its amplitudes
+        if (store_final) {
+          store_tile<R>(psi, s, tg);
+          __syncthreads();
+        }
+        R *sw = reinterpret_cast<R *>(s);
+        if (pass.T == 12) batch_zsums<R, 4>(reinterpret_cast<R(&)[16]>(pr), sw, zs, cc.n_terms, accs, nwarps, warp, lane);
+        else if (pass.T == 11) batch_zsums<R, 3>(reinterpret_cast<R(&)[8]>(pr), sw, zs, cc.n_terms, accs, nwarps, warp, lane);
+        else if (pass.T == 10) batch_zsums<R, 2>(reinterpret_cast<R(&)[4]>(pr), sw, zs, cc.n_terms, accs, nwarps, warp, lane);
+        else if (pass.T == 9) batch_zsums<R, 1>(reinterpret_cast<R(&)[2]>(pr), sw, zs, cc.n_terms, accs, nwarps, warp, lane);
+        else batch_zsums<R, 0>(reinterpret_cast<R(&)[1]>(pr), sw, zs, cc.n_terms, accs, nwarps, warp, lane);
+        __syncthreads();
+        for (int t = threadIdx.x; t < cc.n_terms; t += blockDim.x) {
+          double v = 0.0;
+          for (int w = 0; w < nwarps; ++w) v += accs[t * nwarps + w];
+          partials[cc.part_begin + (int64_t)t * sg.ntiles + (int64_t)tile] = v;
+        }
+      } else if (last && cc.n_terms > 0) {
         // <Z word> partial of this tile: sum_l (-1)^popcount(g & z) |psi_l|^2
         for (int t = 0; t < cc.n_terms; ++t) {
           const uint64_t z = terms[cc.term_begin + t].z;
@@ -2336,7 +2804,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_batch(g_t<R> *__restrict__ states
           partials[cc.part_begin + (int64_t)t * sg.ntiles + (int64_t)tile] = v;
         }
       }
-      if (!last || store_final) store_tile<R>(psi, s, tg);
+      if (!last || (store_final && !(cc.n_terms > 0 && pass.T >= 8 && pass.T <= 12))) store_tile<R>(psi, s, tg);
       __syncthreads();
       if (threadIdx.x == 0 && pidx != no_publish) {  // no_publish >= 0 only in failure-path tests
         __threadfence();

@@ -127,9 +127,32 @@ cudaError_t Launch<R>::stream_op(void *psi, int n, const StreamDev &sd, const vo
   return cudaGetLastError();
 }
 
+namespace detail {
+template <typename R, int NB>
+cudaError_t expval_z(const void *psi, int n, const PassDev &pass, const TermDev *terms, int n_terms,
+                     double *partials, int grid, cudaStream_t st) {
+  static bool attr = false;
+  allow_big_smem(k_expval_z<R, NB>, attr);
+  const int smem = lut_bytes(pass) + (int)sizeof(R) * (kBlock << NB) + kZChunk * (8 + 4) + n_terms * kWarps * 8;
+  k_expval_z<R, NB><<<grid, kBlock, smem, st>>>(reinterpret_cast<const g_t<R> *>(psi), n, pass, terms, n_terms,
+                                                 partials);
+  return cudaGetLastError();
+}
+}  // namespace detail
+
 template <typename R>
 cudaError_t Launch<R>::expval_pass(const void *psi, int n, const PassDev &pass, const TermDev *terms,
                                    int n_terms, double *partials, int grid, cudaStream_t st) {
+  if (pass.zonly) {  // words with Z letters only: one transform of |psi|^2 per thread and tile
+    switch (pass.T) {
+      case 8: return detail::expval_z<R, 0>(psi, n, pass, terms, n_terms, partials, grid, st);
+      case 9: return detail::expval_z<R, 1>(psi, n, pass, terms, n_terms, partials, grid, st);
+      case 10: return detail::expval_z<R, 2>(psi, n, pass, terms, n_terms, partials, grid, st);
+      case 11: return detail::expval_z<R, 3>(psi, n, pass, terms, n_terms, partials, grid, st);
+      case 12: return detail::expval_z<R, 4>(psi, n, pass, terms, n_terms, partials, grid, st);
+      default: break;  // tiles of fewer than 256 amplitudes: the general kernel
+    }
+  }
   static bool attr = false;
   detail::allow_big_smem(k_expval<R>, attr);
   const int smem = detail::tile_bytes(sizeof(c_t<R>), pass.T) + detail::lut_bytes(pass) +
@@ -305,7 +328,7 @@ cudaError_t Launch<R>::probs_small(const void *psi, const ProbsDev &pd, double *
 
 template <typename R>
 int Launch<R>::batch_blocks_per_sm(int max_T, int max_terms, int max_k) {
-  const int smem = (int)((sizeof(c_t<R>) + 8) << max_T) + max_terms * detail::kWarps * 8;
+  const int smem = (int)((sizeof(c_t<R>) + 8) << max_T) + max_terms * (detail::kWarps + 1) * 8;
   // the occupancy query honours the dynamic shared-memory opt-in: set it first
   static bool attr2 = false, attr4 = false;
   if (max_k <= 2)
@@ -329,7 +352,7 @@ cudaError_t Launch<R>::batch(void *states, const BatchCircuit *circs, const Pass
                              int store_final, unsigned long long timeout_ns, int max_T, int max_terms, int max_k,
                              int no_publish, int grid, cudaStream_t st) {
   static bool attr2 = false, attr4 = false;
-  const int smem = (int)((sizeof(c_t<R>) + 8) << max_T) + max_terms * detail::kWarps * 8;
+  const int smem = (int)((sizeof(c_t<R>) + 8) << max_T) + max_terms * (detail::kWarps + 1) * 8;
   if (max_k <= 2) {
     detail::allow_big_smem(k_batch<R, 2>, attr2);
     k_batch<R, 2><<<grid, kBlock, smem, st>>>(reinterpret_cast<g_t<R> *>(states), circs, passes, ops,

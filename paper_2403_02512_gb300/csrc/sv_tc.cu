@@ -132,27 +132,80 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Group base index of group g: g's bits dealt, in order, to the index bits that
+// are not targets (zeros inserted at the ascending target bits).  Linear over
+// disjoint bit sets, so the base of tile * 128 + row is D(tile << 7) | D(row).
+__device__ __forceinline__ uint64_t deposit(uint64_t x, const int (&sorted)[5]) {
+#pragma unroll
+  for (int j = 0; j < 5; ++j) {
+    const int b = sorted[j];
+    x = ((x >> b) << (b + 1)) | (x & ((1ull << b) - 1));
+  }
+  return x;
+}
+
+__device__ __forceinline__ void cp_async8_zfill(uint32_t saddr, const void *gaddr, int src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(saddr), "l"(gaddr), "r"(src_bytes) : "memory");
+}
+
+// Shared memory of the kernel (bytes from the 1024-aligned base).
+constexpr int kOffRaw = 0;                          // two raw operand buffers (cp.async targets)
+constexpr int kOffAhi = kOffRaw + 2 * kOpBytesA;    // TF32 halves of the operand
+constexpr int kOffAlo = kOffAhi + kOpBytesA;
+constexpr int kOffBhi = kOffAlo + kOpBytesA;        // TF32 halves of the matrix
+constexpr int kOffBlo = kOffBhi + kOpBytesB;
+constexpr int kOffStage = kOffBlo + kOpBytesB;      // outputs [group][member], float2
+constexpr int kOffOffs = kOffStage + kTcRows * 32 * 8;   // member offsets (global index bits), 32 x u64
+constexpr int kOffDrow = kOffOffs + 32 * 8;              // group-base deposits of the tile's rows, 128 x u64
+constexpr int kOffMbar = kOffDrow + kTcRows * 8;
+constexpr int kSmemBytes = kOffMbar + 16;
+
+// Pipelined over the CTA's tiles (one CTA per SM, persistent): while tile i is
+// split into TF32 halves and its MMAs run, tile i + 1 is in flight to the
+// other raw buffer (cp.async) and tile i - 1 is read back from the other
+// accumulator (two 64-column TMEM buffers), staged and stored.  SEG: a target
+// is on global index bit 0, so members pair up in 16-byte segments (gather in
+// 16-byte copies, store with lane = member); otherwise consecutive groups are
+// adjacent in memory and gather and store run with lane = group.
 template <bool SEG>
-__global__ void __launch_bounds__(kTcThreads) k_dense5_tc(float2 *__restrict__ psi, int n, const OpDev op,
-                                                          const float2 *__restrict__ M, int dagger, int pb) {
+__global__ void __launch_bounds__(kTcThreads, 1) k_dense5_tc(float2 *__restrict__ psi, int n, const OpDev op,
+                                                             const float2 *__restrict__ M, int dagger, int pb) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  unsigned char *a_hi = smem, *a_lo = smem + kOpBytesA;
-  unsigned char *b_hi = smem + 2 * kOpBytesA, *b_lo = b_hi + kOpBytesB;
-  uint64_t *mbar = reinterpret_cast<uint64_t *>(b_lo + kOpBytesB);
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mbar + 1);
-  float2 *stage = reinterpret_cast<float2 *>(a_hi);  // outputs [group][32], after the MMAs read A
+  const uint32_t sbase = smem_u32(smem);
+  const uint32_t raw[2] = {sbase + kOffRaw, sbase + kOffRaw + kOpBytesA};
+  const uint32_t a_hi = sbase + kOffAhi, a_lo = sbase + kOffAlo, b_hi = sbase + kOffBhi, b_lo = sbase + kOffBlo;
+  float2 *stage = reinterpret_cast<float2 *>(smem + kOffStage);
+  uint64_t *offs = reinterpret_cast<uint64_t *>(smem + kOffOffs);
+  uint64_t *drow = reinterpret_cast<uint64_t *>(smem + kOffDrow);
+  const uint32_t mbar = sbase + kOffMbar;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + kOffMbar + 8);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(kTcN)
+                 "r"(2 * kTcN)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (threadIdx.x == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  int sorted[5];
+  for (int j = 0; j < 5; ++j) sorted[j] = op.tg[j];
+  for (int i = 1; i < 5; ++i)
+    for (int j = i; j > 0 && sorted[j - 1] > sorted[j]; --j) {
+      const int t = sorted[j];
+      sorted[j] = sorted[j - 1];
+      sorted[j - 1] = t;
+    }
+  if (threadIdx.x < 32) {  // member m (wire order: bit 4 - j of m is target j)
+    uint64_t o = 0;
+    for (int j = 0; j < 5; ++j)
+      if ((threadIdx.x >> (4 - j)) & 1) o |= 1ull << op.tg[j];
+    offs[threadIdx.x] = o;
+  }
+  drow[threadIdx.x] = deposit((uint64_t)threadIdx.x, sorted);  // kTcThreads == kTcRows
 
   // B halves: row nn = 2 o + c' (output member o, re / im), column k(i, c), K-major.
   for (int e = threadIdx.x; e < kTcN * 32; e += blockDim.x) {
@@ -164,11 +217,11 @@ __global__ void __launch_bounds__(kTcThreads) k_dense5_tc(float2 *__restrict__ p
     const float vi = co == 0 ? -u.y : u.x;  // ... of its imaginary part
     float hi, lo;
     split_tf32(vr, hi, lo);
-    st_shared_f32(smem_u32(b_hi) + kmajor_off(nn, k), hi);
-    st_shared_f32(smem_u32(b_lo) + kmajor_off(nn, k), lo);
+    st_shared_f32(b_hi + kmajor_off(nn, k), hi);
+    st_shared_f32(b_lo + kmajor_off(nn, k), lo);
     split_tf32(vi, hi, lo);
-    st_shared_f32(smem_u32(b_hi) + kmajor_off(nn, k + 1), hi);
-    st_shared_f32(smem_u32(b_lo) + kmajor_off(nn, k + 1), lo);
+    st_shared_f32(b_hi + kmajor_off(nn, k + 1), hi);
+    st_shared_f32(b_lo + kmajor_off(nn, k + 1), lo);
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -176,145 +229,139 @@ __global__ void __launch_bounds__(kTcThreads) k_dense5_tc(float2 *__restrict__ p
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
 
-  int sorted[5];
-  for (int j = 0; j < 5; ++j) sorted[j] = op.tg[j];
-  for (int i = 1; i < 5; ++i)
-    for (int j = i; j > 0 && sorted[j - 1] > sorted[j]; --j) {
-      const int t = sorted[j];
-      sorted[j] = sorted[j - 1];
-      sorted[j - 1] = t;
-    }
-  uint64_t roff = 0;  // this lane's member of a group (row index r = lane, wire order)
-  for (int j = 0; j < 5; ++j)
-    if ((lane >> (4 - j)) & 1) roff |= 1ull << op.tg[j];
-
   const uint64_t ngroups = 1ull << (n - 5);
   const uint64_t ntiles = (ngroups + kTcRows - 1) / kTcRows;
+  const int niter = blockIdx.x < ntiles ? (int)((ntiles - 1 - blockIdx.x) / gridDim.x + 1) : 0;
+
+  // Issue the copies of tile `tile` into raw buffer `dst` (all asynchronous).
+  auto gather = [&](uint64_t tile, uint32_t dst) {
+    const uint64_t dt = deposit(tile << 7, sorted);
+    if constexpr (SEG) {
+      // 16-byte segment seg (members m, m + 2^pb) of rows c * 8 + (lane % 8), c < 16
+      const int seg = warp * 4 + (lane >> 3);
+      const int m = ((seg >> pb) << (pb + 1)) | (seg & ((1 << pb) - 1));
+      const uint64_t om = offs[m];
+#pragma unroll 4
+      for (int c = 0; c < kTcRows / 8; ++c) {
+        const int row = c * 8 + (lane & 7);
+        const bool ok = tile * kTcRows + row < ngroups;
+        cp_async16_zfill(dst + kmajor_off(row, 4 * seg), psi + (ok ? (dt | drow[row] | om) : 0), ok ? 16 : 0);
+      }
+    } else {
+      // lane = group (row warp * 32 + lane): member m of 32 consecutive groups per instruction
+      const int row = warp * 32 + lane;
+      const bool ok = tile * kTcRows + row < ngroups;
+      const uint64_t base = dt | drow[row];
+#pragma unroll 4
+      for (int m = 0; m < 32; ++m)
+        cp_async8_zfill(dst + kmajor_off(row, 2 * m), psi + (ok ? (base | offs[m]) : 0), ok ? 8 : 0);
+    }
+  };
+
+  if (niter > 0) gather(blockIdx.x, raw[0]);
+  asm volatile("cp.async.commit_group;" ::: "memory");
   uint32_t phase = 0;
   bool failed = false;
-  for (uint64_t tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
-    if constexpr (SEG) {
-      // 512-byte chunks of the operand: 8 rows x 4 segments; lane -> (row l % 8, segment l / 8)
-      for (int chunk = warp; chunk < (kTcRows / 8) * (kTcK / 16); chunk += kTcThreads / 32) {
-        const int row = (chunk >> 2) * 8 + (lane & 7);
-        const int seg = (chunk & 3) * 4 + (lane >> 3);  // pair index s
-        const uint64_t g = tile * kTcRows + row;
-        uint64_t i0 = 0;
-        if (g < ngroups) {
-          i0 = g;
-          for (int j = 0; j < 5; ++j) {
-            const int b = sorted[j];
-            i0 = ((i0 >> b) << (b + 1)) | (i0 & ((1ull << b) - 1));
-          }
+  for (int it = 0; it <= niter; ++it) {
+    const bool cur = it < niter, prev = it > 0;
+    if (it + 1 < niter) gather(blockIdx.x + (uint64_t)(it + 1) * gridDim.x, raw[(it + 1) & 1]);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("cp.async.wait_group 1;" ::: "memory");  // tile it has landed
+    __syncthreads();
+    if (prev) {  // tile it - 1's MMAs: A may be overwritten, its accumulator read
+      const unsigned long long t0 = global_ns_tc();
+      while (!mbar_try_wait(mbar, phase)) {
+        if (global_ns_tc() - t0 > kWaitNs) {
+          failed = true;
+          break;
         }
-        // member of pair s with the pair bit clear
-        const int m = ((seg >> pb) << (pb + 1)) | (seg & ((1 << pb) - 1));
-        uint64_t off = 0;
-        for (int j = 0; j < 5; ++j)
-          if ((m >> (4 - j)) & 1) off |= 1ull << op.tg[j];
-        cp_async16_zfill(smem_u32(a_hi) + kmajor_off(row, 4 * seg), psi + (i0 | off), g < ngroups ? 16 : 0);
       }
-      asm volatile("cp.async.wait_all;" ::: "memory");
-      __syncthreads();
-      // split in place: a_hi <- TF32(x), a_lo <- TF32(x - hi); consecutive 16-byte chunks per lane
+      phase ^= 1;
+      if (__syncthreads_or(failed)) {
+        if (threadIdx.x == 0) atomicExch(&g_tc_error, 1);
+        failed = true;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    }
+    if (cur) {
+      // split: a_hi <- TF32(x), a_lo <- TF32(x - hi), element by element in the K-major layout
+      const float4 *src = reinterpret_cast<const float4 *>(smem + kOffRaw + (it & 1) * kOpBytesA);
+      float4 *hi4 = reinterpret_cast<float4 *>(smem + kOffAhi), *lo4 = reinterpret_cast<float4 *>(smem + kOffAlo);
+#pragma unroll 4
       for (int c = threadIdx.x; c < kOpBytesA / 16; c += blockDim.x) {
-        float4 x = reinterpret_cast<const float4 *>(a_hi)[c], lo;
+        float4 x = src[c], lo;
         split_tf32(x.x, x.x, lo.x);
         split_tf32(x.y, x.y, lo.y);
         split_tf32(x.z, x.z, lo.z);
         split_tf32(x.w, x.w, lo.w);
-        reinterpret_cast<float4 *>(a_hi)[c] = x;
-        reinterpret_cast<float4 *>(a_lo)[c] = lo;
+        hi4[c] = x;
+        lo4[c] = lo;
       }
-    } else {
-      // gather: warp w loads groups 32w .. 32w + 31 of the tile, lane = member
-      const int kl = kpos(lane, pb);
-      for (int q = 0; q < 32; ++q) {
-        const int row = warp * 32 + q;
-        const uint64_t g = tile * kTcRows + row;
-        float2 a = make_float2(0.f, 0.f);
-        if (g < ngroups) {
-          uint64_t i0 = g;
-          for (int j = 0; j < 5; ++j) {
-            const int b = sorted[j];
-            i0 = ((i0 >> b) << (b + 1)) | (i0 & ((1ull << b) - 1));
-          }
-          a = __ldcs(psi + (i0 | roff));
-        }
-        float hi, lo;
-        split_tf32(a.x, hi, lo);
-        st_shared_f32(smem_u32(a_hi) + kmajor_off(row, kl), hi);
-        st_shared_f32(smem_u32(a_lo) + kmajor_off(row, kl), lo);
-        split_tf32(a.y, hi, lo);
-        st_shared_f32(smem_u32(a_hi) + kmajor_off(row, kl + 1), hi);
-        st_shared_f32(smem_u32(a_lo) + kmajor_off(row, kl + 1), lo);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t as[3] = {a_hi, a_hi, a_lo}, bs[3] = {b_hi, b_lo, b_hi};
+        const uint32_t dcol = tmem + (uint32_t)((it & 1) * kTcN);
+        for (int pr = 0; pr < 3; ++pr)
+          for (int ks = 0; ks < kTcK / 8; ++ks)  // K = 8 per MMA: two core matrices along K
+            mma_tf32(dcol, mat_desc(as[pr] + ks * 2 * kLBO), mat_desc(bs[pr] + ks * 2 * kLBO), (pr | ks) != 0);
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                     : "memory");
       }
     }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    if (threadIdx.x == 0) {
+    if (prev) {
+      // epilogue of tile it - 1: each warp reads its 32 rows (TMEM lanes 32w ..) x 64 columns
+      const uint64_t tile = blockIdx.x + (uint64_t)(it - 1) * gridDim.x;
+      const uint32_t scol = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(((it - 1) & 1) * kTcN);
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t ah = smem_u32(a_hi), al = smem_u32(a_lo), bh = smem_u32(b_hi), bl = smem_u32(b_lo);
-      const uint32_t as[3] = {ah, ah, al}, bs[3] = {bh, bl, bh};
-      for (int pr = 0; pr < 3; ++pr)
-        for (int ks = 0; ks < kTcK / 8; ++ks)  // K = 8 per MMA: two core matrices along K
-          mma_tf32(tmem, mat_desc(as[pr] + ks * 2 * kLBO), mat_desc(bs[pr] + ks * 2 * kLBO), (pr | ks) != 0);
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                       smem_u32(mbar))
-                   : "memory");
-    }
-    const unsigned long long t0 = global_ns_tc();
-    while (!mbar_try_wait(smem_u32(mbar), phase)) {
-      if (global_ns_tc() - t0 > kWaitNs) {
-        failed = true;
-        break;
+      float d[kTcN];
+#pragma unroll
+      for (int c = 0; c < kTcN / 16; ++c) {
+        float v[16];
+        tmem_ld16(scol + (uint32_t)(c * 16), v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) d[c * 16 + i] = v[i];
       }
-    }
-    phase ^= 1;
-    if (__syncthreads_or(failed)) {
-      if (threadIdx.x == 0) atomicExch(&g_tc_error, 1);
-      failed = true;
-      break;
-    }
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // each warp reads its 32 rows (TMEM lanes 32w ..) x 64 columns
-    float d[kTcN];
+      const int row = warp * 32 + lane;
+      // staging index row * 32 + (member ^ (row % 32)): conflict-free for the per-row
+      // writes and for the per-group and per-member reads below
 #pragma unroll
-    for (int c = 0; c < kTcN / 16; ++c) {
-      float v[16];
-      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 16), v);
-#pragma unroll
-      for (int i = 0; i < 16; ++i) d[c * 16 + i] = v[i];
-    }
-    const int row = warp * 32 + lane;
-    // staging index row * 32 + (member ^ (row % 32)): conflict-free for these per-row
-    // writes and for the per-group reads below
-#pragma unroll
-    for (int i = 0; i < 32; ++i) stage[row * 32 + (i ^ lane)] = make_float2(d[2 * i], d[2 * i + 1]);
-    __syncwarp();
-    // store: warp w writes its 32 groups, lane = member (coalesced for low target bits)
-    for (int q = 0; q < 32; ++q) {
-      const int rr = warp * 32 + q;
-      const uint64_t g = tile * kTcRows + rr;
-      if (g >= ngroups) break;
-      uint64_t i0 = g;
-      for (int j = 0; j < 5; ++j) {
-        const int b = sorted[j];
-        i0 = ((i0 >> b) << (b + 1)) | (i0 & ((1ull << b) - 1));
+      for (int i = 0; i < 32; ++i) stage[row * 32 + (i ^ lane)] = make_float2(d[2 * i], d[2 * i + 1]);
+      __syncwarp();
+      const uint64_t dt = deposit(tile << 7, sorted);
+      if constexpr (SEG) {
+        // lane = member, one group per step (32 consecutive amplitudes for low target bits)
+        const uint64_t om = offs[lane];
+        for (int q = 0; q < 32; ++q) {
+          const int rr = warp * 32 + q;
+          if (tile * kTcRows + rr >= ngroups) break;
+          const uint64_t i0 = dt | drow[rr];
+          if ((i0 & op.cmask) == op.cval) __stcs(psi + (i0 | om), stage[rr * 32 + (lane ^ q)]);
+        }
+      } else {
+        // lane = group, one member per step (consecutive groups are adjacent)
+        const uint64_t i0 = dt | drow[row];
+        if (tile * kTcRows + row < ngroups && (i0 & op.cmask) == op.cval) {
+#pragma unroll 4
+          for (int m = 0; m < 32; ++m) __stcs(psi + (i0 | offs[m]), stage[row * 32 + (m ^ lane)]);
+        }
       }
-      if ((i0 & op.cmask) == op.cval) __stcs(psi + (i0 | roff), stage[rr * 32 + (lane ^ (rr & 31))]);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();  // the stage and A are rewritten by the next tile
+    __syncthreads();  // buffers of this iteration are free for the next
   }
+  asm volatile("cp.async.wait_all;" ::: "memory");  // no copy outlives the kernel, on every path
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcN) : "memory");
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kTcN) : "memory");
 }
 
 }  // namespace
 
-int dense5_tc_smem() { return 2 * kOpBytesA + 2 * kOpBytesB + 64; }
+int dense5_tc_smem() { return kSmemBytes; }
 
 namespace {
 std::atomic<bool> g_tc_launched{false};
@@ -353,7 +400,7 @@ cudaError_t dense5_tc(void *psi, int n, const OpDev &op, const void *mats, int a
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const uint64_t ntiles = ((1ull << (n - 5)) + kTcRows - 1) / kTcRows;
-  const int grid = (int)std::min<uint64_t>(ntiles, (uint64_t)sms * 2);
+  const int grid = (int)std::min<uint64_t>(ntiles, (uint64_t)sms);  // one persistent CTA per SM
   g_tc_launched = true;
   if (seg)
     k_dense5_tc<true><<<grid, kTcThreads, smem, st>>>(reinterpret_cast<float2 *>(psi), n, op,

@@ -44,8 +44,21 @@ int main() {
     const float f = std::ldexp((float)u(rng), -std::uniform_int_distribution<int>(0, 149)(rng));
     if (sv::df_f2d_exact(f) != (double)f) e_conv = 1.0;
   }
+  // lean stream conversions: amplitudes down to 2^-70 keep ~47 bits; below
+  // 2^-126 they become zero
+  double e_fast = 0;
+  for (int i = 0; i < 200000; ++i) {
+    const double a = std::ldexp(0.5 + 0.5 * std::fabs(u(rng)), -std::uniform_int_distribution<int>(-4, 70)(rng)) *
+                     (u(rng) < 0 ? -1 : 1);
+    const df F = sv::df_split_fast(a);
+    e_fast = std::fmax(e_fast, rel(sv::df_join_fast(F), a, std::fabs(a)));
+    e_fast = std::fmax(e_fast, rel((double)F, a, std::fabs(a)));
+    if (std::fabs(F.l) > 0.5f * std::ldexp(1.0f, std::ilogb(F.h) - 23)) e_fast = 1.0;  // canonical pair
+  }
+  if (sv::df_join_fast(sv::df_split_fast(std::ldexp(1.0, -130))) != 0.0) e_fast = 1.0;
+  if (sv::df_join_fast(sv::df_split_fast(0.0)) != 0.0) e_fast = 1.0;
   const double z = (double)df(0.0), nz = (double)df(-0.0);
-  std::printf("conv %.3e add %.3e mul %.3e fma %.3e rot %.3e zero %g %g\n", e_conv, e_add, e_mul, e_fma, e_rot, z,
-              nz);
+  std::printf("conv %.3e add %.3e mul %.3e fma %.3e rot %.3e fastconv %.3e zero %g %g\n", e_conv, e_add, e_mul,
+              e_fma, e_rot, e_fast, z, nz);
   return 0;
 }

@@ -26,4 +26,5 @@ def test_df64_conversion_and_arithmetic_error_bounds(tmp_path):
     assert float(vals["mul"]) < 2.0 ** -45
     assert float(vals["fma"]) < 2.0 ** -44
     assert float(vals["rot"]) < 2.0 ** -44
+    assert float(vals["fastconv"]) < 2.0 ** -46     # stream conversions (split, join)
     assert float(vals["zero"]) == 0.0
