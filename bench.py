@@ -488,6 +488,51 @@ def extra_layered12():
     return out
 
 
+def extra_dense_fusion_layer30(hbm_peak):
+    """Dense-block fusion measured per layer of the 30-qubit RY + CZ-brick
+    workload (complex64): (a) one layer as the planner runs it, RY on all 30
+    wires plus the layer's CZ brick in tile passes; (b) the same layer fused
+    into 5-wire windows, i.e. six 5-qubit dense blocks on the tensor cores
+    (wires 5w .. 5w + 4) plus the CZ gates that cross a window boundary.  The
+    kernels' time does not depend on the matrices' entries, so (b) uses seeded
+    unitaries."""
+    import torch
+    from paper_2403_02512_gb300 import _lib as L
+    from paper_2403_02512_gb300.torch_api import Program, StateVector
+    from workloads import Op
+    n = 30
+    out = {}
+    sv = StateVector(n, "c64", renormalize=False)
+    for parity in (0, 1):
+        layer = [Op("RY", (w,), (w,)) for w in range(n)]
+        layer += [Op("PauliZ", (a + 1,), controls=(a,)) for a in range(parity, n - 1, 2)]
+        prog = Program(sv, layer, n)
+        prog.set_params(np.linspace(0.1, 3.0, n))
+        ms_tiles = _timed(lambda: prog.forward(reset=False), 5, torch.cuda.current_stream())
+        passes = prog.stats()[0]
+        prog.close()
+        cross = [Op("PauliZ", (a + 1,), controls=(a,)) for a in range(parity, n - 1, 2) if (a + 1) % 5 == 0]
+        pc = Program(sv, cross, 0)
+        pc.set_params([])
+        rng = np.random.default_rng(parity)
+        mats = [np.linalg.qr(rng.normal(size=(32, 32)) + 1j * rng.normal(size=(32, 32)))[0] for _ in range(6)]
+
+        def fused():
+            for w in range(6):
+                sv.apply_matrix(list(range(5 * w, 5 * w + 5)), mats[w])
+            if cross:
+                pc.forward(reset=False)
+
+        ms_fused = _timed(fused, 3, torch.cuda.current_stream())
+        pc.close()
+        out["even_layer" if parity == 0 else "odd_layer"] = {
+            "tile_passes_ms": ms_tiles, "tile_passes": passes, "fused_dense_ms": ms_fused,
+            "fused_blocks": 6, "boundary_cz": len(cross)}
+    sv.close()
+    torch.cuda.empty_cache()
+    return out
+
+
 def _kernel_split(kt):
     total = sum(v[0] for v in kt.values()) or 1.0
     return {k: {"ms": round(v[0], 3), "launches": v[1], "share": round(v[0] / total, 4)}
@@ -716,6 +761,7 @@ def run_ours(args):
             extras["qaoa_batched"] = extra_qaoa()
             extras["vqe24_2000_terms"] = extra_vqe()
             extras["rycz30"] = extra_rycz30(hbm_peak)
+            extras["dense_fusion_layer30_c64"] = extra_dense_fusion_layer30(hbm_peak)
             try:
                 extras["layered12"] = extra_layered12()
             except Exception as exc:  # an extra never takes the bench line down

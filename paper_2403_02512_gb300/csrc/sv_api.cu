@@ -1163,10 +1163,12 @@ TermDev make_termdev(const HTerm &h, const PassDev &p) {
   return t;
 }
 
-// Members per adjoint multi-wire micro-op: complex64 only (three, one group of
-// eight amplitudes per thread at 2^11-amplitude tiles).  The complex128 modes
-// are bound by FP64 or double-float arithmetic, which grouping does not cut.
-int adjoint_multi_width(sv_dtype dt) { return dt == SV_C64 ? 3 : 0; }
+// Members per adjoint multi-wire micro-op: one group of 2^(T - 8) amplitudes
+// per thread (three for complex64's 2^11-amplitude tiles, two for complex128's
+// 2^10).  complex128 kernels group them only with one lambda per CTA (the
+// registers of more lambdas' moments would spill); otherwise they apply the
+// members one by one.
+int adjoint_multi_width(sv_dtype dt) { return dt == SV_C64 ? 3 : 2; }
 
 // ---- precision dispatch ---------------------------------------------------------
 struct Ops {
@@ -2127,6 +2129,7 @@ struct sv_batch {
   // plan
   int tile_cap = 0;          // tile bits cap (autotuned)
   int64_t wave_bytes = 64ll << 20;
+  int ctas_per_sm_cap = 0;   // CTAs per SM at most (0: as many as fit; autotuned)
   int n_segs = 0, n_pass = 0, n_slots = 0, max_T = 1, max_terms = 1, max_k = 1, grid = 1;
   int64_t total_items = 0, n_partials = 0;
   int no_publish = -1;
@@ -2280,7 +2283,8 @@ sv_status batch_plan(sv_batch *b, int tcap, int64_t wave) {
   const int sms = sm_count();
   const int per_sm = b->dt == SV_C64 ? Launch<float>::batch_blocks_per_sm(max_T, max_terms, max_k)
                                      : Launch<double>::batch_blocks_per_sm(max_T, max_terms, max_k);
-  b->grid = (int)std::max<int64_t>(1, std::min<int64_t>(items, (int64_t)sms * per_sm));
+  const int per_sm_used = b->ctas_per_sm_cap > 0 ? std::min(per_sm, b->ctas_per_sm_cap) : per_sm;
+  b->grid = (int)std::max<int64_t>(1, std::min<int64_t>(items, (int64_t)sms * per_sm_used));
   if (const char *e = getenv("SV_BATCH_DEBUG_NO_PUBLISH")) b->no_publish = atoi(e);
   if (const char *e = getenv("SV_BATCH_TIMEOUT_MS")) b->timeout_ns = 1000000ull * (unsigned long long)atoll(e);
 
@@ -3200,12 +3204,15 @@ sv_status sv_batch_autotune(sv_batch *b, double *best_ms) {
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   double best = 1e300;
-  int best_t = K.Tf;
+  int best_t = K.Tf, best_cap = 0;
   int64_t best_w = b->wave_bytes;
   const int64_t waves[4] = {16ll << 20, 32ll << 20, 64ll << 20, 128ll << 20};
   sv_status result = SV_OK;
   for (int t = K.Tf - 2; t <= K.Tf && !result; ++t) {
-    for (int64_t w : waves) {
+    for (int64_t w : waves)
+    for (int cap : {0, 2}) {  // CTAs per SM: as many as fit, or two
+      if (result) break;      // a failed configuration ends the search
+      b->ctas_per_sm_cap = cap;
       if ((result = batch_plan(b, t, w))) break;
       if ((result = sv_batch_set_params(b, params.data(), 0))) break;
       b->use_graph = false;
@@ -3221,12 +3228,14 @@ sv_status sv_batch_autotune(sv_batch *b, double *best_ms) {
         best = ms / 2;
         best_t = t;
         best_w = w;
+        best_cap = cap;
       }
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (result) return result;
+  b->ctas_per_sm_cap = best_cap;
   if (sv_status st = batch_plan(b, best_t, best_w)) return st;
   b->use_graph = true;
   if (sv_status st = sv_batch_set_params(b, params.data(), 0)) return st;
@@ -3350,7 +3359,6 @@ sv_status sv_plan_describe(int n, sv_dtype dtype, const sv_tape *tape, int forwa
     if (!out) return;
     for (int k = 0; k < SV_PLAN_KINDS; ++k) out[k] = 0;
     for (const OpDev &o : P.ops) {
-      if (o.in_multi) continue;  // counted once, under its kMulti header
       if (o.kind == kPair) out[o.fused ? 4 : 0]++;
       else if (o.kind == kDiag) out[1]++;
       else if (o.kind == kDense) out[2]++;

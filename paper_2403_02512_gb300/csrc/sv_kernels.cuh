@@ -1308,7 +1308,8 @@ __device__ __forceinline__ void adj_diag(c_t<R> *sp, c_t<R> *sl, const TileGeom 
 // block E = U^dagger is applied in registers.  Contributions are kept as the
 // four moments of the fused runs (D0, D1, SY, SX per member and lambda) and
 // contracted after the warp reduction: a fused run with its generators, an X
-// generator as gs SY, a Y generator as -gs SX.
+// generator as gs SY, a Y generator as -gs SX (those two take only the moment
+// they need, 4 FMA per pair and lambda).
 template <typename R, int B, int W>
 __device__ void adj_multi_t(c_t<R> *sp, c_t<R> *sl, const TileGeom &tg, const OpDev *__restrict__ mem,
                             const OpDev &hd, const c_t<R> *__restrict__ mats, int bb, double *accs, int nwarps,
@@ -1317,11 +1318,13 @@ __device__ void adj_multi_t(c_t<R> *sp, c_t<R> *sl, const TileGeom &tg, const Op
   constexpr int G = 1 << W;
   C U[W][4];
   int code[W], off[G];
-  bool tr[W];
+  bool tr[W], herm[W], gy[W];  // trainable; fused-run generators (four moments); a Y generator (SX only)
 #pragma unroll
   for (int j = 0; j < W; ++j) {
     code[j] = mem[j].code;
     tr[j] = mem[j].train >= 0;
+    herm[j] = mem[j].gcode == gHerm;
+    gy[j] = mem[j].gcode == gY;
 #pragma unroll
     for (int q = 0; q < 4; ++q)
       U[j][q] = (code[j] == mGen || code[j] == mReal || code[j] == mImOff) ? mats[mem[j].mat + q] : C();
@@ -1361,10 +1364,14 @@ __device__ void adj_multi_t(c_t<R> *sp, c_t<R> *sl, const TileGeom &tg, const Op
         for (int i = 0; i < G; ++i) {
           if ((i >> j) & 1) continue;
           const C qa = p[i], qb = p[i | (1 << j)], la = v[i], lb = v[i | (1 << j)];
-          acc[jj][j][0] = fma(la.x, qa.y, fma(-la.y, qa.x, acc[jj][j][0]));
-          acc[jj][j][1] = fma(lb.x, qb.y, fma(-lb.y, qb.x, acc[jj][j][1]));
-          acc[jj][j][2] = fma(la.x, qb.y, fma(-la.y, qb.x, fma(lb.x, qa.y, fma(-lb.y, qa.x, acc[jj][j][2]))));
-          acc[jj][j][3] = fma(la.x, qb.x, fma(la.y, qb.y, fma(-lb.x, qa.x, fma(-lb.y, qa.y, acc[jj][j][3]))));
+          if (herm[j]) {
+            acc[jj][j][0] = fma(la.x, qa.y, fma(-la.y, qa.x, acc[jj][j][0]));
+            acc[jj][j][1] = fma(lb.x, qb.y, fma(-lb.y, qb.x, acc[jj][j][1]));
+          }
+          if (herm[j] || !gy[j])  // SY: an X generator's contribution
+            acc[jj][j][2] = fma(la.x, qb.y, fma(-la.y, qb.x, fma(lb.x, qa.y, fma(-lb.y, qa.x, acc[jj][j][2]))));
+          if (herm[j] || gy[j])   // SX: a Y generator's contribution (negated)
+            acc[jj][j][3] = fma(la.x, qb.x, fma(la.y, qb.y, fma(-lb.x, qa.x, fma(-lb.y, qa.y, acc[jj][j][3]))));
         }
       }
 #pragma unroll
@@ -1454,16 +1461,18 @@ __global__ void __launch_bounds__(kBlock, (std::is_same<R, double>::value && B >
     tile_async_convert<R>(sp, A * (1 + bb));  // sp and the lambda tiles are contiguous
     for (int o = pass.op_end - 1; o >= pass.op_begin; --o) {
       const OpDev &op = ops[o];
-      if constexpr (std::is_same<R, float>::value) {
-        if (op.kind == kMulti) {  // header after its members ops[o - k .. o)
+      if (op.kind == kMulti) {  // header after its members ops[o - k .. o)
+        // grouped in registers for complex64, and for complex128 with one lambda per
+        // CTA (registers); otherwise the members follow one by one, each with a barrier
+        if constexpr (std::is_same<R, float>::value || B == 1) {
           if (op.k == 2)
             adj_multi_t<R, B, 2>(sp, sl, tg, ops + o - 2, op, mats, bb, accs, nwarps, warp, lane);
           else
             adj_multi_t<R, B, 3>(sp, sl, tg, ops + o - 3, op, mats, bb, accs, nwarps, warp, lane);
           o -= op.k;
           if (o > pass.op_begin) __syncthreads();
-          continue;
         }
+        continue;
       }
       if (op.kind == kDense) {
         dense_any<R, MAXK>(sp, tg, op, mats);
@@ -1482,7 +1491,7 @@ __global__ void __launch_bounds__(kBlock, (std::is_same<R, double>::value && B >
           adj_diag<R, B>(sp, sl, tg, op, mats, acc);
         if (op.train >= 0) flush_acc<R, B>(acc, bb, op.train, accs, nwarps, warp, lane, op.kind == kPair ? (R)op.gs : R(1));
       }
-      if (op.sync_prev && o > pass.op_begin) __syncthreads();
+      if ((op.sync_prev || op.in_multi) && o > pass.op_begin) __syncthreads();
     }
     __syncthreads();
     for (int jj = 0; jj < bb; ++jj) store_tile<R>(lam_base + ((size_t)(j0 + jj) << n), sl + (size_t)jj * A, tg);

@@ -756,3 +756,63 @@ def test_wide_dense_blocks_in_a_jacobian(dtype):
     E, J = prog.jacobian()
     _assert_rel(E.cpu().numpy(), Eo, TOL_E[dtype], "expval", dtype)
     _assert_rel(J.cpu().numpy(), Jo, TOL_J[dtype], "jacobian", dtype)
+
+
+# ---- Z-only words: one Walsh-Hadamard transform of |psi|^2 per thread and tile ----------
+def _z_words(n, rng, count, max_weight=4):
+    terms = []
+    for _ in range(count):
+        k = int(rng.integers(1, min(n, max_weight) + 1))
+        wires = sorted(int(w) for w in rng.choice(n, size=k, replace=False))
+        terms.append(Term(float(rng.normal()), tuple((w, "Z") for w in wires)))
+    return terms
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("n", [7, 8, 9, 12, 13, 17, 20])
+def test_z_only_observables(dtype, n):
+    # tile sizes T = min(n, 11 or 12) cover every transform width 2^(T - 8) (and the
+    # general kernel below T = 8); 40 words exceed one chunk of 32, 600 exceed one pass
+    rng = np.random.default_rng(900 + n)
+    obs = [[Term(1.0, ((w, "Z"),))] for w in (0, n // 2, n - 1)]        # single Z on high, middle, low bits
+    obs.append(_z_words(n, rng, 40))
+    obs.append(_z_words(n, rng, 600))
+    obs.append(_z_words(n, rng, 12) + random_hamiltonian(n, 12, rng, weights=tuple(range(1, min(n, 3) + 1))))
+    obs.append([Term(0.7, ())] + _z_words(n, rng, 5))                   # identity word among Z words
+    sv, psi = _state(n, dtype, 900 + n)
+    got = sv.expval(obs)
+    want = np.array([oracle.expval(psi, H) for H in obs])
+    _assert_rel(got, want, TOL_E[dtype], "z-only expval", dtype)
+    assert np.array_equal(got, sv.expval(obs))  # fixed-order sums repeat bitwise
+
+
+# ---- single-wire trainable layers: grouped adjoint micro-ops -----------------------------
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("n_obs", [1, 3])
+def test_single_wire_layers_jacobian(dtype, n_obs):
+    # consecutive single-wire gates on distinct wires are grouped in the adjoint sweep
+    # (complex64; complex128 with one lambda per CTA), the rest are walked one by one
+    n = 13
+    rng = np.random.default_rng(950 + n_obs)
+    names = ["RX", "RY", "RZ", "PhaseShift", "Rot", "Hadamard"]
+    ops, p = [], 0
+    for layer in range(4):
+        for w in rng.permutation(n):
+            g = names[int(rng.integers(0, len(names)))]
+            npar = GATE_NPARAMS[g]
+            ops.append(Op(g, (int(w),), tuple(range(p, p + npar)), adjoint=bool(rng.integers(0, 2))))
+            p += npar
+        ops += [Op("PauliX", ((w + 1 + layer) % n,), controls=(w,)) for w in range(0, n, 3)]
+    obs = [[Term(1.0, ((int(rng.integers(0, n)), "Z"),))] for _ in range(n_obs - 1)]
+    obs.insert(0, random_hamiltonian(n, 6, rng, weights=(1, 2)))
+    c = Circuit(n, ops, p, obs)
+    params = rng.uniform(0, 2 * np.pi, p)
+    sv = StateVector(n, dtype)
+    prog = Program.from_circuit(sv, c)
+    prog.forward(params)
+    E, J = prog.jacobian()
+    Eo, Jo = oracle.adjoint_jacobian(c, params)
+    _assert_rel(E.cpu().numpy(), Eo, TOL_E[dtype], "expvals", dtype)
+    _assert_rel(J.cpu().numpy(), Jo, TOL_J[dtype], "jacobian", dtype)
+    g = rng.normal(size=n_obs)
+    _assert_rel(prog.vjp(g).cpu().numpy(), g @ Jo, TOL_J[dtype], "vjp", dtype)
