@@ -793,7 +793,7 @@ void lower_fused(int n, const std::vector<HOp> &ops, const std::vector<int> &mem
 // lowered into micro-ops; dagger selects the adjoint sweep's U^dagger blocks.
 // Consecutive uncontrolled, untrained single-wire pair micro-ops of one pass on
 // distinct local bits become kMulti micro-ops of up to 3 members.
-void merge_multi(std::vector<OpDev> &ops, size_t begin) {
+void merge_multi(std::vector<OpDev> &ops, size_t begin, int lowbits) {
   std::vector<OpDev> out(ops.begin(), ops.begin() + begin);
   std::vector<OpDev> pend;
   auto mergeable = [](const OpDev &o) {
@@ -829,8 +829,8 @@ void merge_multi(std::vector<OpDev> &ops, size_t begin) {
       out.push_back(o);
       continue;
     }
-    bool clash = pend.size() >= 3;
-    for (const OpDev &q : pend) clash |= q.tl[0] == o.tl[0];
+    bool clash = pend.size() >= 3;  // at most one member on the lowest bits (bank conflicts, as below)
+    for (const OpDev &q : pend) clash |= q.tl[0] == o.tl[0] || (q.tl[0] < lowbits && o.tl[0] < lowbits);
     if (clash) emit();
     pend.push_back(o);
   }
@@ -845,7 +845,11 @@ void merge_multi(std::vector<OpDev> &ops, size_t begin) {
 // them.  The adjoint kernel meets the header first (it walks the pass
 // backwards) and applies the members together (one load and store of phi and
 // each lambda per group, one barrier).
-void merge_multi_adj(std::vector<OpDev> &ops, size_t begin, int wmax) {
+// At most one member sits on the lowest `lowbits` local bits: a group's
+// amplitudes for one member index are 2^(member bits below lowbits) elements
+// apart across a warp, so two low members would give 4-way shared-memory bank
+// conflicts (one gives the 2-way of a single op on such a bit).
+void merge_multi_adj(std::vector<OpDev> &ops, size_t begin, int wmax, int lowbits) {
   std::vector<OpDev> out(ops.begin(), ops.begin() + begin);
   std::vector<OpDev> pend;
   auto mergeable = [](const OpDev &o) {
@@ -886,7 +890,7 @@ void merge_multi_adj(std::vector<OpDev> &ops, size_t begin, int wmax) {
       continue;
     }
     bool clash = (int)pend.size() >= wmax;
-    for (const OpDev &q : pend) clash |= q.tl[0] == o.tl[0];
+    for (const OpDev &q : pend) clash |= q.tl[0] == o.tl[0] || (q.tl[0] < lowbits && o.tl[0] < lowbits);
     if (clash) emit();
     pend.push_back(o);
   }
@@ -949,8 +953,8 @@ Plan plan_passes(int n, const std::vector<HOp> &ops, int Tmax, int nlow_pref, in
       for (size_t q = before; q < P.ops.size(); ++q)
         if (P.ops[q].kind == kDense) pd.max_k = std::max(pd.max_k, (int)P.ops[q].k);
     }
-    if (multi) merge_multi(P.ops, (size_t)pd.op_begin);
-    if (multi_adj > 1) merge_multi_adj(P.ops, (size_t)pd.op_begin, multi_adj);
+    if (multi) merge_multi(P.ops, (size_t)pd.op_begin, nlow_pref);
+    if (multi_adj > 1) merge_multi_adj(P.ops, (size_t)pd.op_begin, multi_adj, nlow_pref);
     pd.op_end = (int)P.ops.size();
     pd.n_train = t;
     P.steps.push_back({0, (int)P.passes.size()});
@@ -1785,6 +1789,7 @@ sv_status jac_workspace(sv_program *p, JacWs &w) {
     if (mcc > 0) lam_rows = std::max(lam_rows, (size_t)p->grid_a(mcc) * mcc);
   size_t part = std::max(lam_rows * max_train, (size_t)p->grid_e * std::max<size_t>(max_terms, p->m));
   if (p->want_lam) part = std::max(part, (size_t)p->mc * kNormBlocks);
+  if (expval_by_observable(p)) part = std::max(part, (size_t)p->m * kNormBlocks);  // expvals from lambdas
   if (p->want_tan) part = std::max(part, (size_t)p->mc * kNormBlocks);
   const bool need_vec = p->adj.n_train > 0 || !p->adj.dk_ops.empty() || p->want_tan;  // phi buffers / dpsi
   const bool need_lam = need_vec || p->want_lam;
@@ -1939,16 +1944,52 @@ sv_status run_sweep(sv_program *p, const JacWs &w, int mcc, int j0, int ldc, con
 
 bool needs_sweep(const sv_program *p) { return p->adj.n_train > 0 || !p->adj.dk_ops.empty(); }
 
+// Expectation values from lambda_j = H_j psi already in w.lam: E_j = Re <psi|lambda_j>
+// (fixed-order partials), instead of a second application of the words.
+sv_status expvals_from_lambdas(sv_program *p, const JacWs &w) {
+  sv_state *s = p->s;
+  for (int j = 0; j < p->m; ++j) {
+    LaunchTimer t(s->stream, 2);
+    const void *lam = w.lam + (size_t)j * s->bytes;
+    const cudaError_t e = s->dt == SV_C64
+                              ? Launch<float>::dot_partials(lam, s->psi, s->n, w.partials + (size_t)j * kNormBlocks, s->stream)
+                              : Launch<double>::dot_partials(lam, s->psi, s->n, w.partials + (size_t)j * kNormBlocks, s->stream);
+    if (sv_status r = after_launch(s, e, "expval dot")) return r;
+    ++p->launches;
+  }
+  LaunchTimer t(s->stream, 4);
+  ++p->launches;
+  return after_launch(s, jvp_combine(w.partials, kNormBlocks, p->m, 0, w.expvals, s->stream, 1.0), "expval combine");
+}
+
 sv_status run_jacobian(sv_program *p, const JacWs &w) {
   sv_state *s = p->s;
   if (sv_status r = ensure_mats(p)) return r;
-  if (sv_status r = run_expval(p, s->psi, w)) return r;
+  // Hamiltonians of many words: the lambdas H_j psi are formed first and give the
+  // expectation values by one dot product each (one application of the words, not two)
+  const bool lam_first = expval_by_observable(p) && needs_sweep(p) && p->n_chunks == 1;
+  if (!lam_first)
+    if (sv_status r = run_expval(p, s->psi, w)) return r;
   if (needs_sweep(p)) {
     const int npass_e = (int)p->tp.passes.size();
     for (int c = 0; c < p->n_chunks; ++c) {
       const int j0 = c * p->mc, mcc = std::min(p->m, j0 + p->mc) - j0;
       auto begin = [&](int q) { return (const int32_t *)p->d_lam_begin + p->lam_begin_off[c * npass_e + q]; };
-      if (sv_status r = run_sweep(p, w, mcc, j0, p->m, p->d_lam_terms, begin)) return r;
+      if (lam_first) {
+        const Ops &K = ops_of(s);
+        for (int q = 0; q < npass_e; ++q) {
+          cudaError_t e;
+          {
+            LaunchTimer t(s->stream, 3);
+            e = K.lambda_pass(s->psi, w.lam, s->n, p->tp.passes[q], p->d_lam_terms, begin(q), mcc, q == 0,
+                              p->grid_l(mcc), s->stream);
+          }
+          if (sv_status r = after_launch(s, e, "lambda pass")) return r;
+          ++p->launches;
+        }
+        if (sv_status r = expvals_from_lambdas(p, w)) return r;
+      }
+      if (sv_status r = run_sweep(p, w, mcc, j0, p->m, p->d_lam_terms, begin, lam_first)) return r;
     }
   }
   cudaError_t e;

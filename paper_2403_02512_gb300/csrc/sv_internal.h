@@ -273,7 +273,9 @@ void dense5_tc_enable(bool on);
 bool dense5_tc_enabled();
 
 // out[j0 + j] = 2 sum_b partials[j * nb + b], j < m (Jacobian-vector products).
-cudaError_t jvp_combine(const double *partials, int nb, int m, int j0, double *out, cudaStream_t st);
+// out[j0 + j] = scale * sum over b < nb of partials[j * nb + b] (fixed order).
+cudaError_t jvp_combine(const double *partials, int nb, int m, int j0, double *out, cudaStream_t st,
+                        double scale = 2.0);
 // out[j0 + j] = sum_b partials[j * nb + b] - E[j0 + j]^2, j < m (variances).
 cudaError_t var_combine(const double *partials, int nb, int m, const double *E, int j0, double *out, cudaStream_t st);
 cudaError_t batch_reduce(const BatchCircuit *circs, int n_circ, const ZTerm *terms, const double *partials,

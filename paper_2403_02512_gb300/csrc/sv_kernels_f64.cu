@@ -84,17 +84,18 @@ cudaError_t assemble_jacobian(const double *contrib, const double *coef, const i
 }
 
 // Jacobian-vector products: out = 2 Re <lambda_j | dpsi>, partials ascending.
-__global__ void k_jvp_combine(const double *__restrict__ partials, int nb, int m, int j0, double *__restrict__ out) {
+__global__ void k_jvp_combine(const double *__restrict__ partials, int nb, int m, int j0, double scale,
+                              double *__restrict__ out) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= m) return;
   double t = 0.0;
   for (int b = 0; b < nb; ++b) t += partials[(size_t)j * nb + b];
-  out[j0 + j] = 2.0 * t;
+  out[j0 + j] = scale * t;
 }
 
-cudaError_t jvp_combine(const double *partials, int nb, int m, int j0, double *out, cudaStream_t st) {
+cudaError_t jvp_combine(const double *partials, int nb, int m, int j0, double *out, cudaStream_t st, double scale) {
   if (m <= 0) return cudaSuccess;
-  k_jvp_combine<<<(m + 127) / 128, 128, 0, st>>>(partials, nb, m, j0, out);
+  k_jvp_combine<<<(m + 127) / 128, 128, 0, st>>>(partials, nb, m, j0, scale, out);
   return cudaGetLastError();
 }
 

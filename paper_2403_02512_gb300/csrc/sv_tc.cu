@@ -33,7 +33,7 @@ namespace {
 constexpr int kTcRows = 128;              // groups per tile (MMA M)
 constexpr int kTcK = 64;                  // 32 real + 32 imaginary inputs
 constexpr int kTcN = 64;                  // 32 real + 32 imaginary outputs
-constexpr int kTcThreads = 128;           // four warps: TMEM lanes 32w .. 32w + 31
+constexpr int kTcThreads = 256;           // eight warps; warps w and w + 4 read TMEM lanes 32(w % 4) ..
 constexpr int kOpBytesA = kTcRows * kTcK * 4;  // 32 KB per TF32 operand half
 constexpr int kOpBytesB = kTcN * kTcK * 4;     // 16 KB
 constexpr int kSBO = (kTcK / 4) * 128;         // bytes between 8-row core-matrix blocks
@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dense5_tc(float2 *__restrict_
       if ((threadIdx.x >> (4 - j)) & 1) o |= 1ull << op.tg[j];
     offs[threadIdx.x] = o;
   }
-  drow[threadIdx.x] = deposit((uint64_t)threadIdx.x, sorted);  // kTcThreads == kTcRows
+  if (threadIdx.x < kTcRows) drow[threadIdx.x] = deposit((uint64_t)threadIdx.x, sorted);
 
   // B halves: row nn = 2 o + c' (output member o, re / im), column k(i, c), K-major.
   for (int e = threadIdx.x; e < kTcN * 32; e += blockDim.x) {
@@ -237,23 +237,24 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dense5_tc(float2 *__restrict_
   auto gather = [&](uint64_t tile, uint32_t dst) {
     const uint64_t dt = deposit(tile << 7, sorted);
     if constexpr (SEG) {
-      // 16-byte segment seg (members m, m + 2^pb) of rows c * 8 + (lane % 8), c < 16
-      const int seg = warp * 4 + (lane >> 3);
+      // 16-byte segment seg (members m, m + 2^pb) of rows c * 8 + (lane % 8), c in this warp half's 8
+      const int seg = (warp & 3) * 4 + (lane >> 3);
       const int m = ((seg >> pb) << (pb + 1)) | (seg & ((1 << pb) - 1));
       const uint64_t om = offs[m];
 #pragma unroll 4
-      for (int c = 0; c < kTcRows / 8; ++c) {
+      for (int c = (warp >> 2) * 8; c < (warp >> 2) * 8 + 8; ++c) {
         const int row = c * 8 + (lane & 7);
         const bool ok = tile * kTcRows + row < ngroups;
         cp_async16_zfill(dst + kmajor_off(row, 4 * seg), psi + (ok ? (dt | drow[row] | om) : 0), ok ? 16 : 0);
       }
     } else {
-      // lane = group (row warp * 32 + lane): member m of 32 consecutive groups per instruction
-      const int row = warp * 32 + lane;
+      // lane = group (row (warp % 4) * 32 + lane): member m of 32 consecutive groups per
+      // instruction, members split between the two warps of a row quarter
+      const int row = (warp & 3) * 32 + lane;
       const bool ok = tile * kTcRows + row < ngroups;
       const uint64_t base = dt | drow[row];
 #pragma unroll 4
-      for (int m = 0; m < 32; ++m)
+      for (int m = (warp >> 2) * 16; m < (warp >> 2) * 16 + 16; ++m)
         cp_async8_zfill(dst + kmajor_off(row, 2 * m), psi + (ok ? (base | offs[m]) : 0), ok ? 8 : 0);
     }
   };
@@ -313,30 +314,35 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dense5_tc(float2 *__restrict_
       }
     }
     if (prev) {
-      // epilogue of tile it - 1: each warp reads its 32 rows (TMEM lanes 32w ..) x 64 columns
+      // epilogue of tile it - 1: warp w reads rows 32(w % 4) .. (its TMEM lane quarter),
+      // columns 32(w / 4) .. + 31 (outputs 16(w / 4) .. + 15)
       const uint64_t tile = blockIdx.x + (uint64_t)(it - 1) * gridDim.x;
-      const uint32_t scol = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(((it - 1) & 1) * kTcN);
+      const int half = warp >> 2;
+      const uint32_t scol = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(((it - 1) & 1) * kTcN + half * 32);
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      float d[kTcN];
+      float d[kTcN / 2];
 #pragma unroll
-      for (int c = 0; c < kTcN / 16; ++c) {
+      for (int c = 0; c < kTcN / 32; ++c) {
         float v[16];
         tmem_ld16(scol + (uint32_t)(c * 16), v);
 #pragma unroll
         for (int i = 0; i < 16; ++i) d[c * 16 + i] = v[i];
       }
-      const int row = warp * 32 + lane;
+      const int row = (warp & 3) * 32 + lane;
       // staging index row * 32 + (member ^ (row % 32)): conflict-free for the per-row
       // writes and for the per-group and per-member reads below
 #pragma unroll
-      for (int i = 0; i < 32; ++i) stage[row * 32 + (i ^ lane)] = make_float2(d[2 * i], d[2 * i + 1]);
-      __syncwarp();
+      for (int i = 0; i < 16; ++i) {
+        const int mi = half * 16 + i;
+        stage[row * 32 + (mi ^ lane)] = make_float2(d[2 * i], d[2 * i + 1]);
+      }
+      __syncthreads();  // a row's outputs come from two warps
       const uint64_t dt = deposit(tile << 7, sorted);
       if constexpr (SEG) {
         // lane = member, one group per step (32 consecutive amplitudes for low target bits)
         const uint64_t om = offs[lane];
-        for (int q = 0; q < 32; ++q) {
-          const int rr = warp * 32 + q;
+        for (int q = half * 16; q < half * 16 + 16; ++q) {
+          const int rr = (warp & 3) * 32 + q;
           if (tile * kTcRows + rr >= ngroups) break;
           const uint64_t i0 = dt | drow[rr];
           if ((i0 & op.cmask) == op.cval) __stcs(psi + (i0 | om), stage[rr * 32 + (lane ^ q)]);
@@ -346,7 +352,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dense5_tc(float2 *__restrict_
         const uint64_t i0 = dt | drow[row];
         if (tile * kTcRows + row < ngroups && (i0 & op.cmask) == op.cval) {
 #pragma unroll 4
-          for (int m = 0; m < 32; ++m) __stcs(psi + (i0 | offs[m]), stage[row * 32 + (m ^ lane)]);
+          for (int m = half * 16; m < half * 16 + 16; ++m) __stcs(psi + (i0 | offs[m]), stage[row * 32 + (m ^ lane)]);
         }
       }
     }
