@@ -437,8 +437,7 @@ sv_status sv_plan_query(int n, sv_dtype dtype, const sv_tape *tape,
  * plans (either array may be NULL), indexed by
  *   0 pair blocks, 1 diagonals, 2 dense blocks in a tile, 3 phase runs
  *   (adjacent RZ / IsingZZ sharing an angle), 4 fused single-wire runs,
- *   5 multi-wire micro-ops (up to 3 single-wire gates per barrier; in adjoint
- *   plans their members are also counted under their own kinds),
+ *   5 multi-wire micro-ops (up to 3 single-wire gates per barrier),
  *   6 wide dense steps outside tiles, 7 tile passes.
  * Same argument errors as sv_plan_query. */
 #define SV_PLAN_KINDS 8

@@ -838,68 +838,8 @@ void merge_multi(std::vector<OpDev> &ops, size_t begin, int lowbits) {
   ops.swap(out);
 }
 
-// Adjoint plans: up to `wmax` consecutive uncontrolled single-wire pair
-// micro-ops on distinct local bits (trainable ones with an X, Y or fused
-// Hermitian generator) are grouped: the members stay in place, marked
-// in_multi, and a kMulti header with the count and the sorted bits follows
-// them.  The adjoint kernel meets the header first (it walks the pass
-// backwards) and applies the members together (one load and store of phi and
-// each lambda per group, one barrier).
-// At most one member sits on the lowest `lowbits` local bits: a group's
-// amplitudes for one member index are 2^(member bits below lowbits) elements
-// apart across a warp, so two low members would give 4-way shared-memory bank
-// conflicts (one gives the 2-way of a single op on such a bit).
-void merge_multi_adj(std::vector<OpDev> &ops, size_t begin, int wmax, int lowbits) {
-  std::vector<OpDev> out(ops.begin(), ops.begin() + begin);
-  std::vector<OpDev> pend;
-  auto mergeable = [](const OpDev &o) {
-    if (o.kind != kPair || o.k != 1 || o.cmask != 0 || o.hcmask != 0 || o.lcmask != 0) return false;
-    if (o.oa != 0 || o.ob != (1 << o.tl[0])) return false;
-    return o.train < 0 || o.gcode == gX || o.gcode == gY || (o.gcode == gHerm && o.ngen >= 1 && o.ngen <= 3);
-  };
-  auto emit = [&]() {
-    if (pend.size() == 1) out.push_back(pend[0]);
-    if (pend.size() >= 2) {
-      OpDev m;
-      memset(&m, 0, sizeof(m));
-      m.kind = kMulti;
-      m.k = (int8_t)pend.size();
-      m.train = -1;
-      m.slot = -1;
-      m.sync_prev = 1;
-      int bits[3];
-      for (size_t j = 0; j < pend.size(); ++j) {
-        OpDev mj = pend[j];
-        mj.in_multi = 1;
-        mj.sync_prev = 0;
-        out.push_back(mj);
-        m.tl[j] = pend[j].tl[0];
-        bits[j] = pend[j].tl[0];
-      }
-      std::sort(bits, bits + pend.size());
-      for (size_t j = 0; j < pend.size(); ++j) m.ts[j] = (int8_t)bits[j];
-      out.push_back(m);
-    }
-    pend.clear();
-  };
-  for (size_t i = begin; i < ops.size(); ++i) {
-    const OpDev &o = ops[i];
-    if (!mergeable(o)) {
-      emit();
-      out.push_back(o);
-      continue;
-    }
-    bool clash = (int)pend.size() >= wmax;
-    for (const OpDev &q : pend) clash |= q.tl[0] == o.tl[0] || (q.tl[0] < lowbits && o.tl[0] < lowbits);
-    if (clash) emit();
-    pend.push_back(o);
-  }
-  emit();
-  ops.swap(out);
-}
-
 Plan plan_passes(int n, const std::vector<HOp> &ops, int Tmax, int nlow_pref, int max_train, bool dagger,
-                 SlotTable &st, bool fuse = false, bool phase = false, bool multi = false, int multi_adj = 0) {
+                 SlotTable &st, bool fuse = false, bool phase = false, bool multi = false) {
   Plan P;
   const std::vector<Group> groups = fuse_groups(n, ops, fuse, phase);
   const int T = std::min(Tmax, n);
@@ -954,7 +894,6 @@ Plan plan_passes(int n, const std::vector<HOp> &ops, int Tmax, int nlow_pref, in
         if (P.ops[q].kind == kDense) pd.max_k = std::max(pd.max_k, (int)P.ops[q].k);
     }
     if (multi) merge_multi(P.ops, (size_t)pd.op_begin, nlow_pref);
-    if (multi_adj > 1) merge_multi_adj(P.ops, (size_t)pd.op_begin, multi_adj, nlow_pref);
     pd.op_end = (int)P.ops.size();
     pd.n_train = t;
     P.steps.push_back({0, (int)P.passes.size()});
@@ -1029,14 +968,6 @@ sv_status check_plan(const Plan &P, int n, int nlow_pref) {
       if (op.k > kMaxTileTargets) return fail(SV_ERR_UNSUPPORTED, "internal planner error: wide op in a tile");
       if (op.kind == kMulti && (op.k < 2 || op.k > 3))
         return fail(SV_ERR_UNSUPPORTED, "internal planner error: multi-wire op");
-      if (op.kind == kMulti && o > pd.op_begin && P.ops[o - 1].in_multi) {  // adjoint: members precede it
-        if (o - op.k < pd.op_begin) return fail(SV_ERR_UNSUPPORTED, "internal planner error: multi-wire members");
-        for (int j = 0; j < op.k; ++j) {
-          const OpDev &mj = P.ops[o - op.k + j];
-          if (!mj.in_multi || mj.kind != kPair || mj.k != 1 || mj.tl[0] != op.tl[j] || mj.ob != (1 << mj.tl[0]))
-            return fail(SV_ERR_UNSUPPORTED, "internal planner error: multi-wire members");
-        }
-      }
       for (int j = 0; j < op.k; ++j) {
         if (op.tl[j] < 0 || op.tl[j] >= pd.T) return fail(SV_ERR_UNSUPPORTED, "internal planner error: non-local target");
         for (int q = 0; q < j; ++q)
@@ -1167,12 +1098,6 @@ TermDev make_termdev(const HTerm &h, const PassDev &p) {
   return t;
 }
 
-// Members per adjoint multi-wire micro-op: one group of 2^(T - 8) amplitudes
-// per thread (three for complex64's 2^11-amplitude tiles, two for complex128's
-// 2^10).  complex128 kernels group them only with one lambda per CTA (the
-// registers of more lambdas' moments would spill); otherwise they apply the
-// members one by one.
-int adjoint_multi_width(sv_dtype dt) { return dt == SV_C64 ? 3 : 2; }
 
 // ---- precision dispatch ---------------------------------------------------------
 struct Ops {
@@ -1424,8 +1349,7 @@ sv_status build_program(sv_state *s, const sv_tape *tape, const sv_pauli_sum *ob
   }
   SlotTable st_tab;
   p->fwd = plan_passes(n, fops, K.Tf, K.nlow_pref, 1 << 30, false, st_tab, true, true, true);
-  p->adj = plan_passes(n, aops, K.Ta, K.nlow_pref, kMaxTrainPerPass, true, st_tab, true, true, false,
-                       adjoint_multi_width(s->dt));
+  p->adj = plan_passes(n, aops, K.Ta, K.nlow_pref, kMaxTrainPerPass, true, st_tab, true, true);
   if (sv_status st = check_plan(p->fwd, n, K.nlow_pref)) {
     destroy_program(p);
     return st;
@@ -3312,8 +3236,7 @@ sv_status plan_both(int n, sv_dtype dtype, const sv_tape *tape, Plan &f, Plan &a
   }
   SlotTable st_tab;
   f = plan_passes(n, fops, K.Tf, K.nlow_pref, 1 << 30, false, st_tab, true, true, true);
-  a = plan_passes(n, aops, K.Ta, K.nlow_pref, kMaxTrainPerPass, true, st_tab, true, true, false,
-                  adjoint_multi_width(dtype));
+  a = plan_passes(n, aops, K.Ta, K.nlow_pref, kMaxTrainPerPass, true, st_tab, true, true);
   if (sv_status st = check_plan(f, n, K.nlow_pref)) return st;
   return check_plan(a, n, K.nlow_pref);
 }

@@ -82,7 +82,6 @@ struct OpDev {
   uint64_t hcmask, hcval;
   int8_t mcode[3];       // kMulti: member codes
   int8_t fused;          // kPair made from a fused run of single-wire gates (1), for plan descriptions
-  int8_t in_multi;       // adjoint plans: member of the kMulti whose header follows its k members
   int32_t mmat[3];       // kMulti: member 2x2 entries
 };
 

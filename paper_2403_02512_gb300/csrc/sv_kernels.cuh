@@ -1297,125 +1297,6 @@ __device__ __forceinline__ void adj_diag(c_t<R> *sp, c_t<R> *sl, const TileGeom 
   }
 }
 
-// Adjoint multi-wire micro-op: W uncontrolled single-wire pair micro-ops on
-// distinct local bits, stored (in forward order) as mem[0 .. W) before their
-// header.  A thread takes the 2^W amplitudes of a group that share every
-// other local bit, for phi and then for each lambda in turn: the
-// contributions of the trainable members come first, all from the group's
-// values before any member is un-applied (the members act on distinct wires,
-// so each member's generator commutes with the other members' blocks and the
-// inner product is the same as right after that member), then every member's
-// block E = U^dagger is applied in registers.  Contributions are kept as the
-// four moments of the fused runs (D0, D1, SY, SX per member and lambda) and
-// contracted after the warp reduction: a fused run with its generators, an X
-// generator as gs SY, a Y generator as -gs SX (those two take only the moment
-// they need, 4 FMA per pair and lambda).
-template <typename R, int B, int W>
-__device__ void adj_multi_t(c_t<R> *sp, c_t<R> *sl, const TileGeom &tg, const OpDev *__restrict__ mem,
-                            const OpDev &hd, const c_t<R> *__restrict__ mats, int bb, double *accs, int nwarps,
-                            int warp, int lane) {
-  using C = c_t<R>;
-  constexpr int G = 1 << W;
-  C U[W][4];
-  int code[W], off[G];
-  bool tr[W], herm[W], gy[W];  // trainable; fused-run generators (four moments); a Y generator (SX only)
-#pragma unroll
-  for (int j = 0; j < W; ++j) {
-    code[j] = mem[j].code;
-    tr[j] = mem[j].train >= 0;
-    herm[j] = mem[j].gcode == gHerm;
-    gy[j] = mem[j].gcode == gY;
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-      U[j][q] = (code[j] == mGen || code[j] == mReal || code[j] == mImOff) ? mats[mem[j].mat + q] : C();
-  }
-#pragma unroll
-  for (int i = 0; i < G; ++i) {
-    int o = 0;
-#pragma unroll
-    for (int j = 0; j < W; ++j)
-      if ((i >> j) & 1) o += 1 << mem[j].tl[0];
-    off[i] = o;
-  }
-  R acc[B][W][4];
-#pragma unroll
-  for (int jj = 0; jj < B; ++jj)
-#pragma unroll
-    for (int j = 0; j < W; ++j)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) acc[jj][j][q] = R(0);
-  const int ts0 = hd.ts[0], ts1 = hd.ts[1], ts2 = hd.ts[2];
-  const int ng = tg.A >> W;
-  for (int g = threadIdx.x; g < ng; g += blockDim.x) {
-    int l0 = insert_zero(insert_zero(g, ts0), ts1);
-    if (W > 2) l0 = insert_zero(l0, ts2);
-    C p[G];
-#pragma unroll
-    for (int i = 0; i < G; ++i) p[i] = sp[l0 + off[i]];
-#pragma unroll
-    for (int jj = 0; jj < B; ++jj) {
-      C v[G];
-#pragma unroll
-      for (int i = 0; i < G; ++i) v[i] = sl[jj * tg.A + l0 + off[i]];
-#pragma unroll
-      for (int j = 0; j < W; ++j) {
-        if (!tr[j]) continue;
-#pragma unroll
-        for (int i = 0; i < G; ++i) {
-          if ((i >> j) & 1) continue;
-          const C qa = p[i], qb = p[i | (1 << j)], la = v[i], lb = v[i | (1 << j)];
-          if (herm[j]) {
-            acc[jj][j][0] = fma(la.x, qa.y, fma(-la.y, qa.x, acc[jj][j][0]));
-            acc[jj][j][1] = fma(lb.x, qb.y, fma(-lb.y, qb.x, acc[jj][j][1]));
-          }
-          if (herm[j] || !gy[j])  // SY: an X generator's contribution
-            acc[jj][j][2] = fma(la.x, qb.y, fma(-la.y, qb.x, fma(lb.x, qa.y, fma(-lb.y, qa.x, acc[jj][j][2]))));
-          if (herm[j] || gy[j])   // SX: a Y generator's contribution (negated)
-            acc[jj][j][3] = fma(la.x, qb.x, fma(la.y, qb.y, fma(-lb.x, qa.x, fma(-lb.y, qa.y, acc[jj][j][3]))));
-        }
-      }
-#pragma unroll
-      for (int j = 0; j < W; ++j)
-#pragma unroll
-        for (int i = 0; i < G; ++i)
-          if (!((i >> j) & 1)) pair_apply<R>(code[j], U[j], v[i], v[i | (1 << j)]);
-#pragma unroll
-      for (int i = 0; i < G; ++i) sl[jj * tg.A + l0 + off[i]] = v[i];
-    }
-#pragma unroll
-    for (int j = 0; j < W; ++j)
-#pragma unroll
-      for (int i = 0; i < G; ++i)
-        if (!((i >> j) & 1)) pair_apply<R>(code[j], U[j], p[i], p[i | (1 << j)]);
-#pragma unroll
-    for (int i = 0; i < G; ++i) sp[l0 + off[i]] = p[i];
-  }
-  // warp sums of the moments of every (lambda, member): slot s = jj * W + j
-  constexpr int P = pow2_at_least(B * W);
-  R v[P][4];
-#pragma unroll
-  for (int s = 0; s < P; ++s)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) v[s][q] = s < B * W ? acc[s / W][s % W][q] : R(0);
-  int slot;
-  const bool writer = warp_reduce_scatter<R, P, 4>(v, lane, slot);
-  const int jj = slot / W, j = slot % W;
-  if (!writer || slot >= B * W || jj >= bb) return;
-  const OpDev &mj = mem[j];
-  if (mj.train < 0) return;
-  if (mj.gcode == gHerm) {
-    for (int gi = 0; gi < mj.ngen; ++gi) {
-      const R g00 = mats[mj.gmat + 4 * gi].x, g11 = mats[mj.gmat + 4 * gi + 3].x;
-      const C g01 = mats[mj.gmat + 4 * gi + 1];
-      const R val = g00 * v[0][0] + g11 * v[0][1] + g01.x * v[0][2] + g01.y * v[0][3];
-      WarpAcc<R>::add(&accs[((mj.train + gi) * B + jj) * nwarps + warp], val);
-    }
-  } else {
-    const R val = (R)mj.gs * (mj.gcode == gX ? v[0][2] : -v[0][3]);
-    WarpAcc<R>::add(&accs[(mj.train * B + jj) * nwarps + warp], val);
-  }
-}
-
 template <typename R, int MAXK, int B>
 __global__ void __launch_bounds__(kBlock, (std::is_same<R, double>::value && B >= 4) ? 1 : 2) k_tile_adjoint(const g_t<R> *phi_in, g_t<R> *phi_out,
                                                              g_t<R> *__restrict__ lam_base, int n, int m,
@@ -1461,19 +1342,6 @@ __global__ void __launch_bounds__(kBlock, (std::is_same<R, double>::value && B >
     tile_async_convert<R>(sp, A * (1 + bb));  // sp and the lambda tiles are contiguous
     for (int o = pass.op_end - 1; o >= pass.op_begin; --o) {
       const OpDev &op = ops[o];
-      if (op.kind == kMulti) {  // header after its members ops[o - k .. o)
-        // grouped in registers for complex64, and for complex128 with one lambda per
-        // CTA (registers); otherwise the members follow one by one, each with a barrier
-        if constexpr (std::is_same<R, float>::value || B == 1) {
-          if (op.k == 2)
-            adj_multi_t<R, B, 2>(sp, sl, tg, ops + o - 2, op, mats, bb, accs, nwarps, warp, lane);
-          else
-            adj_multi_t<R, B, 3>(sp, sl, tg, ops + o - 3, op, mats, bb, accs, nwarps, warp, lane);
-          o -= op.k;
-          if (o > pass.op_begin) __syncthreads();
-        }
-        continue;
-      }
       if (op.kind == kDense) {
         dense_any<R, MAXK>(sp, tg, op, mats);
         for (int jj = 0; jj < bb; ++jj) dense_any<R, MAXK>(sl + (size_t)jj * A, tg, op, mats);
@@ -1491,7 +1359,7 @@ __global__ void __launch_bounds__(kBlock, (std::is_same<R, double>::value && B >
           adj_diag<R, B>(sp, sl, tg, op, mats, acc);
         if (op.train >= 0) flush_acc<R, B>(acc, bb, op.train, accs, nwarps, warp, lane, op.kind == kPair ? (R)op.gs : R(1));
       }
-      if ((op.sync_prev || op.in_multi) && o > pass.op_begin) __syncthreads();
+      if (op.sync_prev && o > pass.op_begin) __syncthreads();
     }
     __syncthreads();
     for (int jj = 0; jj < bb; ++jj) store_tile<R>(lam_base + ((size_t)(j0 + jj) << n), sl + (size_t)jj * A, tg);

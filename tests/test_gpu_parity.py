@@ -786,12 +786,11 @@ def test_z_only_observables(dtype, n):
     assert np.array_equal(got, sv.expval(obs))  # fixed-order sums repeat bitwise
 
 
-# ---- single-wire trainable layers: grouped adjoint micro-ops -----------------------------
+# ---- single-wire trainable layers of every kind, adjoint flags, CNOT layers --------------
 @pytest.mark.parametrize("dtype", DTYPES)
 @pytest.mark.parametrize("n_obs", [1, 3])
 def test_single_wire_layers_jacobian(dtype, n_obs):
-    # consecutive single-wire gates on distinct wires are grouped in the adjoint sweep
-    # (complex64; complex128 with one lambda per CTA), the rest are walked one by one
+    # one and three observables: one lambda per CTA (the VJP shape) and several
     n = 13
     rng = np.random.default_rng(950 + n_obs)
     names = ["RX", "RY", "RZ", "PhaseShift", "Rot", "Hadamard"]
