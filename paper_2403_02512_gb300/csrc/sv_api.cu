@@ -1713,7 +1713,7 @@ sv_status jac_workspace(sv_program *p, JacWs &w) {
     if (mcc > 0) lam_rows = std::max(lam_rows, (size_t)p->grid_a(mcc) * mcc);
   size_t part = std::max(lam_rows * max_train, (size_t)p->grid_e * std::max<size_t>(max_terms, p->m));
   if (p->want_lam) part = std::max(part, (size_t)p->mc * kNormBlocks);
-  if (expval_by_observable(p)) part = std::max(part, (size_t)p->m * kNormBlocks);  // expvals from lambdas
+  part = std::max(part, (size_t)std::min(std::max(p->m, 1), 64) * kNormBlocks);  // expvals from lambdas
   if (p->want_tan) part = std::max(part, (size_t)p->mc * kNormBlocks);
   const bool need_vec = p->adj.n_train > 0 || !p->adj.dk_ops.empty() || p->want_tan;  // phi buffers / dpsi
   const bool need_lam = need_vec || p->want_lam;
@@ -1886,12 +1886,23 @@ sv_status expvals_from_lambdas(sv_program *p, const JacWs &w) {
   return after_launch(s, jvp_combine(w.partials, kNormBlocks, p->m, 0, w.expvals, s->stream, 1.0), "expval combine");
 }
 
+// Hamiltonians of several words per observable (any precision): the lambdas
+// H_j psi, which the sweep needs anyway, are formed first and give the
+// expectation values by one dot product each (2V per observable against a
+// pass over the state per word group).  Z-only observables keep their
+// transform pass, which reads the state once for all of them.
+bool lambda_first(const sv_program *p) {
+  if (!(p->m > 0 && p->m <= 64 && p->n_chunks == 1 && p->terms.size() >= 4 * (size_t)p->m && needs_sweep(p)))
+    return false;
+  for (const PassDev &pd : p->tp.passes)
+    if (!pd.zonly) return true;
+  return false;
+}
+
 sv_status run_jacobian(sv_program *p, const JacWs &w) {
   sv_state *s = p->s;
   if (sv_status r = ensure_mats(p)) return r;
-  // Hamiltonians of many words: the lambdas H_j psi are formed first and give the
-  // expectation values by one dot product each (one application of the words, not two)
-  const bool lam_first = expval_by_observable(p) && needs_sweep(p) && p->n_chunks == 1;
+  const bool lam_first = lambda_first(p);
   if (!lam_first)
     if (sv_status r = run_expval(p, s->psi, w)) return r;
   if (needs_sweep(p)) {
