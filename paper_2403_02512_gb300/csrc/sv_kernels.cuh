@@ -1082,6 +1082,51 @@ __device__ void adj_fused_t(c_t<R> *sp, c_t<R> *sl, const TileGeom &tg, const Op
   const OpRegs o(op);
   const uint32_t lcm = op.lcmask, lcv = op.lcval;
   const int ng = tg.A >> 1;
+  if constexpr (MOM && std::is_same<R, float>::value) {
+    // complex64: two pairs per step, every load of a step issued before its stores
+    // (the compiler cannot move a later pair's loads above an earlier pair's stores)
+    auto moments = [&](int jj, const C &la, const C &lb, const C &qa, const C &qb) {
+      acc[0][jj] = fma(la.x, qa.y, fma(-la.y, qa.x, acc[0][jj]));
+      acc[1][jj] = fma(lb.x, qb.y, fma(-lb.y, qb.x, acc[1][jj]));
+      acc[2][jj] = fma(la.x, qb.y, fma(-la.y, qb.x, fma(lb.x, qa.y, fma(-lb.y, qa.x, acc[2][jj]))));
+      acc[3][jj] = fma(la.x, qb.x, fma(la.y, qb.y, fma(-lb.x, qa.x, fma(-lb.y, qa.y, acc[3][jj]))));
+    };
+    for (int gi = threadIdx.x; gi < ng; gi += 2 * blockDim.x) {
+      const int gj = gi + blockDim.x;
+      const int l0 = o.base(gi), l1 = gj < ng ? o.base(gj) : l0;
+      const bool a0 = !CTL || (((uint32_t)l0 & lcm) == lcv);
+      const bool a1 = gj < ng && (!CTL || (((uint32_t)l1 & lcm) == lcv));
+      const int ia0 = l0 + o.oa, ib0 = l0 + o.ob, ia1 = l1 + o.oa, ib1 = l1 + o.ob;
+      C pa0 = sp[ia0], pb0 = sp[ib0], pa1 = sp[ia1], pb1 = sp[ib1];
+      const C qa0 = pa0, qb0 = pb0, qa1 = pa1, qb1 = pb1;  // phi before the un-apply
+      pair_apply<R>(mGen, Mr, pa0, pb0);
+      pair_apply<R>(mGen, Mr, pa1, pb1);
+      if (a0) {
+        sp[ia0] = pa0;
+        sp[ib0] = pb0;
+      }
+      if (a1) {
+        sp[ia1] = pa1;
+        sp[ib1] = pb1;
+      }
+#pragma unroll
+      for (int jj = 0; jj < B; ++jj) {
+        C la0 = sl[jj * tg.A + ia0], lb0 = sl[jj * tg.A + ib0], la1 = sl[jj * tg.A + ia1], lb1 = sl[jj * tg.A + ib1];
+        if (a0) moments(jj, la0, lb0, qa0, qb0);
+        if (a1) moments(jj, la1, lb1, qa1, qb1);
+        pair_apply<R>(mGen, Mr, la0, lb0);
+        pair_apply<R>(mGen, Mr, la1, lb1);
+        if (a0) {
+          sl[jj * tg.A + ia0] = la0;
+          sl[jj * tg.A + ib0] = lb0;
+        }
+        if (a1) {
+          sl[jj * tg.A + ia1] = la1;
+          sl[jj * tg.A + ib1] = lb1;
+        }
+      }
+    }
+  } else
   for (int gi = threadIdx.x; gi < ng; gi += blockDim.x) {
     const int l0 = o.base(gi);
     if (CTL && (((uint32_t)l0 & lcm) != lcv)) continue;
