@@ -1088,10 +1088,13 @@ TermDev make_termdev(const HTerm &h, const PassDev &p) {
   memset(&t, 0, sizeof(t));
   t.xg = h.x;
   t.zg = h.z;
-  uint32_t xl = 0;
-  for (int i = 0; i < p.T; ++i)
+  uint32_t xl = 0, zl = 0;
+  for (int i = 0; i < p.T; ++i) {
     if (h.x >> p.pos[i] & 1) xl |= 1u << i;
+    if (h.z >> p.pos[i] & 1) zl |= 1u << i;
+  }
   t.xl = xl;
+  t.zl = zl;
   t.ny = h.ny;
   t.obs = h.obs;
   t.coeff = h.coeff;

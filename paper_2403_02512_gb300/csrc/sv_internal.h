@@ -106,7 +106,7 @@ struct TermDev {
   uint32_t xl;       // the flip mask in local bits of the pass
   int32_t ny;        // number of Y letters mod 4
   int32_t obs;       // observable (row) index
-  int32_t pad;
+  uint32_t zl;       // the sign mask in local bits of the pass
   double coeff;
 };
 

@@ -1469,9 +1469,13 @@ __global__ void __launch_bounds__(kBlock) k_expval(const g_t<R> *__restrict__ ps
     for (int t = 0; t < n_terms; ++t) {
       const TermDev tm = terms[t];
       Acc<R> acc;
-      for (int l = threadIdx.x; l < A; l += blockDim.x) {
-        const uint64_t g = tg.gidx(l);
-        const int par = __popcll((g ^ tm.xg) & tm.zg) & 1;
+      // sign (-1)^popcount((g ^ x) & z) with g = tile base | local bits of l and
+      // l = threadIdx.x + kBlock i: a per-thread part and the parity of i's bits
+      const int s0 = (__popcll(tg.base & tm.zg) + __popcll(tm.xg & tm.zg) +
+                      __popc((uint32_t)threadIdx.x & tm.zl & 0xFFu)) & 1;
+      const uint32_t zh = tm.zl >> 8;
+      for (int l = threadIdx.x, i = 0; l < A; l += kBlock, ++i) {
+        const int par = s0 ^ (__popc((uint32_t)i & zh) & 1);
         R v = pauli_re<R>(s[l], s[l ^ tm.xl], tm.ny);
         acc.add(par ? -v : v);
       }

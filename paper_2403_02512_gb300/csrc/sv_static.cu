@@ -239,8 +239,10 @@ sv_status sv_expval_static(const void *psi, int n, sv_dtype dtype, const sv_paul
       memset(&t, 0, sizeof(t));
       t.xg = h.x;
       t.zg = h.z;
-      for (int b = 0; b < passes[q].T; ++b)
+      for (int b = 0; b < passes[q].T; ++b) {
         if (h.x >> passes[q].pos[b] & 1) t.xl |= 1u << b;
+        if (h.z >> passes[q].pos[b] & 1) t.zl |= 1u << b;
+      }
       t.ny = h.ny;
       t.obs = h.obs;
       t.coeff = h.coeff;
