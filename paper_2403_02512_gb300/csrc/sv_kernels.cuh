@@ -1058,7 +1058,7 @@ __device__ __forceinline__ void adj_pair(c_t<R> *sp, c_t<R> *sl, const TileGeom 
 //      G00 D0 + G11 D1 + Re(G01) SY + Im(G01) SX,
 //    which equals the sum over pairs of Im(conj(l_a)(G' p)_a + conj(l_b)(G' p)_b).
 //    No w = G' phi products are formed.
-template <typename R, int B, int NG, bool CTL, bool MOM>
+template <typename R, int B, int NG, bool CTL, bool MOM, bool SWZ = false>
 __device__ void adj_fused_t(c_t<R> *sp, c_t<R> *sl, const TileGeom &tg, const OpDev &op,
                             const c_t<R> *__restrict__ mats, int bb, double *accs, int nwarps, int warp, int lane) {
   using C = c_t<R>;
@@ -1091,16 +1091,33 @@ __device__ void adj_fused_t(c_t<R> *sp, c_t<R> *sl, const TileGeom &tg, const Op
       acc[2][jj] = fma(la.x, qb.y, fma(-la.y, qb.x, fma(lb.x, qa.y, fma(-lb.y, qa.x, acc[2][jj]))));
       acc[3][jj] = fma(la.x, qb.x, fma(la.y, qb.y, fma(-lb.x, qa.x, fma(-lb.y, qa.y, acc[3][jj]))));
     };
+    // SWZ (pair bit below 4): lanes 8..15 of each half-warp take their pair's b member
+    // first.  A half-warp's a members then share no bank pair with its b members
+    // (bit t of the index differs), so each access is conflict-free instead of 2-way.
+    const bool sw = SWZ && ((threadIdx.x >> 3) & 1);
+    const int oa = sw ? o.ob : o.oa, ob = sw ? o.oa : o.ob;
     for (int gi = threadIdx.x; gi < ng; gi += 2 * blockDim.x) {
       const int gj = gi + blockDim.x;
       const int l0 = o.base(gi), l1 = gj < ng ? o.base(gj) : l0;
       const bool a0 = !CTL || (((uint32_t)l0 & lcm) == lcv);
       const bool a1 = gj < ng && (!CTL || (((uint32_t)l1 & lcm) == lcv));
-      const int ia0 = l0 + o.oa, ib0 = l0 + o.ob, ia1 = l1 + o.oa, ib1 = l1 + o.ob;
+      // first / second member in memory-access order (a, b unless swapped)
+      const int ia0 = l0 + oa, ib0 = l0 + ob, ia1 = l1 + oa, ib1 = l1 + ob;
+      auto order = [&](C &x, C &y) {  // (first, second) <-> (a, b)
+        if (sw) {
+          const C t = x;
+          x = y;
+          y = t;
+        }
+      };
       C pa0 = sp[ia0], pb0 = sp[ib0], pa1 = sp[ia1], pb1 = sp[ib1];
+      order(pa0, pb0);
+      order(pa1, pb1);
       const C qa0 = pa0, qb0 = pb0, qa1 = pa1, qb1 = pb1;  // phi before the un-apply
       pair_apply<R>(mGen, Mr, pa0, pb0);
       pair_apply<R>(mGen, Mr, pa1, pb1);
+      order(pa0, pb0);
+      order(pa1, pb1);
       if (a0) {
         sp[ia0] = pa0;
         sp[ib0] = pb0;
@@ -1112,10 +1129,14 @@ __device__ void adj_fused_t(c_t<R> *sp, c_t<R> *sl, const TileGeom &tg, const Op
 #pragma unroll
       for (int jj = 0; jj < B; ++jj) {
         C la0 = sl[jj * tg.A + ia0], lb0 = sl[jj * tg.A + ib0], la1 = sl[jj * tg.A + ia1], lb1 = sl[jj * tg.A + ib1];
+        order(la0, lb0);
+        order(la1, lb1);
         if (a0) moments(jj, la0, lb0, qa0, qb0);
         if (a1) moments(jj, la1, lb1, qa1, qb1);
         pair_apply<R>(mGen, Mr, la0, lb0);
         pair_apply<R>(mGen, Mr, la1, lb1);
+        order(la0, lb0);
+        order(la1, lb1);
         if (a0) {
           sl[jj * tg.A + ia0] = la0;
           sl[jj * tg.A + ib0] = lb0;
@@ -1206,6 +1227,16 @@ __device__ __forceinline__ void adj_fused_c(c_t<R> *sp, c_t<R> *sl, const TileGe
   // moments when they cost fewer operations than the products (three
   // generators; two with at most two lambdas)
   constexpr bool MOM = NG == 3 || (NG == 2 && B <= 2);
+  // complex64 pairs on the lowest four bits: access order that avoids bank conflicts
+  if constexpr (MOM && std::is_same<R, float>::value) {
+    if (op.ts[0] < 4) {
+      if (op.lcmask)
+        adj_fused_t<R, B, NG, true, MOM, true>(sp, sl, tg, op, mats, bb, accs, nwarps, warp, lane);
+      else
+        adj_fused_t<R, B, NG, false, MOM, true>(sp, sl, tg, op, mats, bb, accs, nwarps, warp, lane);
+      return;
+    }
+  }
   if (op.lcmask)
     adj_fused_t<R, B, NG, true, MOM>(sp, sl, tg, op, mats, bb, accs, nwarps, warp, lane);
   else
