@@ -154,7 +154,8 @@ constexpr int kOffAhi = kOffRaw + 2 * kOpBytesA;    // TF32 halves of the operan
 constexpr int kOffAlo = kOffAhi + kOpBytesA;
 constexpr int kOffBhi = kOffAlo + kOpBytesA;        // TF32 halves of the matrix
 constexpr int kOffBlo = kOffBhi + kOpBytesB;
-constexpr int kOffOffs = kOffBlo + kOpBytesB;            // member offsets (global index bits), 32 x u64
+constexpr int kOffStage = kOffBlo + kOpBytesB;      // outputs [group][member], float2 (SEG layout)
+constexpr int kOffOffs = kOffStage + kTcRows * 32 * 8;   // member offsets (global index bits), 32 x u64
 constexpr int kOffDrow = kOffOffs + 32 * 8;              // group-base deposits of the tile's rows, 128 x u64
 constexpr int kOffMbar = kOffDrow + kTcRows * 8;
 constexpr int kSmemBytes = kOffMbar + 16;
@@ -162,10 +163,11 @@ constexpr int kSmemBytes = kOffMbar + 16;
 // Pipelined over the CTA's tiles (one CTA per SM, persistent): while tile i is
 // split into TF32 halves and its MMAs run, tile i + 1 is in flight to the
 // other raw buffer (cp.async) and tile i - 1 is read back from the other
-// accumulator (two 64-column TMEM buffers) and stored from registers.  SEG: a
-// target is on global index bit 0, so members pair up in 16-byte segments
-// (gathered in 16-byte copies); otherwise consecutive groups are adjacent in
-// memory and the gather runs with lane = group.
+// accumulator (two 64-column TMEM buffers) and stored.  SEG: a target is on
+// global index bit 0, so members pair up in 16-byte segments (gathered in
+// 16-byte copies, outputs staged and stored with lane = member); otherwise
+// consecutive groups are adjacent in memory and gather and store run with
+// lane = group (the store straight from registers).
 template <bool SEG>
 __global__ void __launch_bounds__(kTcThreads, 1) k_dense5_tc(float2 *__restrict__ psi, int n, const OpDev op,
                                                              const float2 *__restrict__ M, int dagger, int pb) {
@@ -173,6 +175,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dense5_tc(float2 *__restrict_
   const uint32_t sbase = smem_u32(smem);
   const uint32_t raw[2] = {sbase + kOffRaw, sbase + kOffRaw + kOpBytesA};
   const uint32_t a_hi = sbase + kOffAhi, a_lo = sbase + kOffAlo, b_hi = sbase + kOffBhi, b_lo = sbase + kOffBlo;
+  float2 *stage = reinterpret_cast<float2 *>(smem + kOffStage);
   uint64_t *offs = reinterpret_cast<uint64_t *>(smem + kOffOffs);
   uint64_t *drow = reinterpret_cast<uint64_t *>(smem + kOffDrow);
   const uint32_t mbar = sbase + kOffMbar;
@@ -326,15 +329,32 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dense5_tc(float2 *__restrict_
 #pragma unroll
         for (int i = 0; i < 16; ++i) d[c * 16 + i] = v[i];
       }
-      // stores straight from registers: lane = group, 16 members each.  For high
-      // target bits a member's store is coalesced across the warp (consecutive
-      // groups are adjacent); for low target bits a lane's members are one
-      // contiguous run.
       const int row = (warp & 3) * 32 + lane;
-      const uint64_t i0 = deposit(tile << 7, sorted) | drow[row];
-      if (tile * kTcRows + row < ngroups && (i0 & op.cmask) == op.cval) {
+      const uint64_t dt = deposit(tile << 7, sorted);
+      if constexpr (SEG) {
+        // members adjacent in memory: staged (index row * 32 + (member ^ (row % 32)),
+        // conflict-free both ways), then stored lane = member, one group per step
 #pragma unroll
-        for (int i = 0; i < 16; ++i) __stcs(psi + (i0 | offs[half * 16 + i]), make_float2(d[2 * i], d[2 * i + 1]));
+        for (int i = 0; i < 16; ++i) {
+          const int mi = half * 16 + i;
+          stage[row * 32 + (mi ^ lane)] = make_float2(d[2 * i], d[2 * i + 1]);
+        }
+        __syncthreads();  // a row's outputs come from two warps
+        const uint64_t om = offs[lane];
+        for (int q = half * 16; q < half * 16 + 16; ++q) {
+          const int rr = (warp & 3) * 32 + q;
+          if (tile * kTcRows + rr >= ngroups) break;
+          const uint64_t i0 = dt | drow[rr];
+          if ((i0 & op.cmask) == op.cval) __stcs(psi + (i0 | om), stage[rr * 32 + (lane ^ q)]);
+        }
+      } else {
+        // consecutive groups adjacent in memory: stored straight from registers,
+        // lane = group, each member's store coalesced across the warp
+        const uint64_t i0 = dt | drow[row];
+        if (tile * kTcRows + row < ngroups && (i0 & op.cmask) == op.cval) {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) __stcs(psi + (i0 | offs[half * 16 + i]), make_float2(d[2 * i], d[2 * i + 1]));
+        }
       }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
