@@ -1082,90 +1082,42 @@ __device__ void adj_fused_t(c_t<R> *sp, c_t<R> *sl, const TileGeom &tg, const Op
   const OpRegs o(op);
   const uint32_t lcm = op.lcmask, lcv = op.lcval;
   const int ng = tg.A >> 1;
-  if constexpr (MOM && std::is_same<R, float>::value) {
-    // complex64: two pairs per step, every load of a step issued before its stores
-    // (the compiler cannot move a later pair's loads above an earlier pair's stores)
-    auto moments = [&](int jj, const C &la, const C &lb, const C &qa, const C &qb) {
-      acc[0][jj] = fma(la.x, qa.y, fma(-la.y, qa.x, acc[0][jj]));
-      acc[1][jj] = fma(lb.x, qb.y, fma(-lb.y, qb.x, acc[1][jj]));
-      acc[2][jj] = fma(la.x, qb.y, fma(-la.y, qb.x, fma(lb.x, qa.y, fma(-lb.y, qa.x, acc[2][jj]))));
-      acc[3][jj] = fma(la.x, qb.x, fma(la.y, qb.y, fma(-lb.x, qa.x, fma(-lb.y, qa.y, acc[3][jj]))));
-    };
-    // SWZ (pair bit below 4): lanes 8..15 of each half-warp take their pair's b member
-    // first.  A half-warp's a members then share no bank pair with its b members
-    // (bit t of the index differs), so each access is conflict-free instead of 2-way.
-    const bool sw = SWZ && ((threadIdx.x >> 3) & 1);
-    const int oa = sw ? o.ob : o.oa, ob = sw ? o.oa : o.ob;
-    for (int gi = threadIdx.x; gi < ng; gi += 2 * blockDim.x) {
-      const int gj = gi + blockDim.x;
-      const int l0 = o.base(gi), l1 = gj < ng ? o.base(gj) : l0;
-      const bool a0 = !CTL || (((uint32_t)l0 & lcm) == lcv);
-      const bool a1 = gj < ng && (!CTL || (((uint32_t)l1 & lcm) == lcv));
-      // first / second member in memory-access order (a, b unless swapped)
-      const int ia0 = l0 + oa, ib0 = l0 + ob, ia1 = l1 + oa, ib1 = l1 + ob;
-      auto order = [&](C &x, C &y) {  // (first, second) <-> (a, b)
-        if (sw) {
-          const C t = x;
-          x = y;
-          y = t;
-        }
-      };
-      C pa0 = sp[ia0], pb0 = sp[ib0], pa1 = sp[ia1], pb1 = sp[ib1];
-      order(pa0, pb0);
-      order(pa1, pb1);
-      const C qa0 = pa0, qb0 = pb0, qa1 = pa1, qb1 = pb1;  // phi before the un-apply
-      pair_apply<R>(mGen, Mr, pa0, pb0);
-      pair_apply<R>(mGen, Mr, pa1, pb1);
-      order(pa0, pb0);
-      order(pa1, pb1);
-      if (a0) {
-        sp[ia0] = pa0;
-        sp[ib0] = pb0;
-      }
-      if (a1) {
-        sp[ia1] = pa1;
-        sp[ib1] = pb1;
-      }
-#pragma unroll
-      for (int jj = 0; jj < B; ++jj) {
-        C la0 = sl[jj * tg.A + ia0], lb0 = sl[jj * tg.A + ib0], la1 = sl[jj * tg.A + ia1], lb1 = sl[jj * tg.A + ib1];
-        order(la0, lb0);
-        order(la1, lb1);
-        if (a0) moments(jj, la0, lb0, qa0, qb0);
-        if (a1) moments(jj, la1, lb1, qa1, qb1);
-        pair_apply<R>(mGen, Mr, la0, lb0);
-        pair_apply<R>(mGen, Mr, la1, lb1);
-        order(la0, lb0);
-        order(la1, lb1);
-        if (a0) {
-          sl[jj * tg.A + ia0] = la0;
-          sl[jj * tg.A + ib0] = lb0;
-        }
-        if (a1) {
-          sl[jj * tg.A + ia1] = la1;
-          sl[jj * tg.A + ib1] = lb1;
-        }
-      }
+  // SWZ (complex64 pair bit below 4): lanes 8..15 of each half-warp access their
+  // pair's b member first.  A half-warp's a members then share no bank pair with
+  // its b members (bit t of the index differs), so each access is conflict-free
+  // instead of 2-way; `order` puts the values back in (a, b) order.
+  static_assert(!SWZ || MOM, "the swapped access order is written for the moment path");
+  const bool sw = SWZ && ((threadIdx.x >> 3) & 1);
+  const int oa = sw ? o.ob : o.oa, ob = sw ? o.oa : o.ob;
+  auto order = [&](C &x, C &y) {
+    if (SWZ && sw) {
+      const C t = x;
+      x = y;
+      y = t;
     }
-  } else
+  };
   for (int gi = threadIdx.x; gi < ng; gi += blockDim.x) {
     const int l0 = o.base(gi);
     if (CTL && (((uint32_t)l0 & lcm) != lcv)) continue;
-    const int ia = l0 + o.oa, ib = l0 + o.ob;
+    const int ia = l0 + oa, ib = l0 + ob;  // first / second member in access order
     C pa = sp[ia], pb = sp[ib];
+    order(pa, pb);
     if constexpr (MOM) {
       const C qa = pa, qb = pb;  // phi before the un-apply
       pair_apply<R>(mGen, Mr, pa, pb);
+      order(pa, pb);
       sp[ia] = pa;
       sp[ib] = pb;
 #pragma unroll
       for (int jj = 0; jj < B; ++jj) {
         C la = sl[jj * tg.A + ia], lb = sl[jj * tg.A + ib];
+        order(la, lb);
         acc[0][jj] = fma(la.x, qa.y, fma(-la.y, qa.x, acc[0][jj]));
         acc[1][jj] = fma(lb.x, qb.y, fma(-lb.y, qb.x, acc[1][jj]));
         acc[2][jj] = fma(la.x, qb.y, fma(-la.y, qb.x, fma(lb.x, qa.y, fma(-lb.y, qa.x, acc[2][jj]))));
         acc[3][jj] = fma(la.x, qb.x, fma(la.y, qb.y, fma(-lb.x, qa.x, fma(-lb.y, qa.y, acc[3][jj]))));
         pair_apply<R>(mGen, Mr, la, lb);
+        order(la, lb);
         sl[jj * tg.A + ia] = la;
         sl[jj * tg.A + ib] = lb;
       }
