@@ -76,7 +76,7 @@ def parse():
 # (x4) and the vector count (25 / 23).  Must be re-taken when the kernel changes.
 PROFILED_TRAFFIC = {
     "c128": (3.028316e9 * 4 * 25 / 23, "ncu dram bytes of one sel22 adjoint launch, scaled x4 x25/23"),
-    "c64": (1.487015e9 * 4 * 25 / 23, "ncu dram bytes of one sel22 adjoint launch, scaled x4 x25/23"),
+    "c64": (1.483159e9 * 4 * 25 / 23, "ncu dram bytes of one sel22 adjoint launch, scaled x4 x25/23"),
 }
 
 # FP64 pipe of a GB300: 152 SMs x 2 FMA lanes/clk x 2 flops x 2.07 GHz.
