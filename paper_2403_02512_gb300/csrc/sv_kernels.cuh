@@ -395,11 +395,44 @@ struct DiagRegs {
   }
 };
 
+// Packed FP32 arithmetic for complex64 (the sm_100 family's two-lane FMA:
+// one instruction for both components of a float2).  A complex product is
+// formed from the vector's components: m v = vx (mr, mi) + vy (-mi, mr).
+// (The other split, (mr, mr) v + (-mi, mi) (vy, vx), measured slower: its
+// swapped copies cost extra moves.)
+__device__ __forceinline__ float2 pk_swap(float2 v) { return make_float2(v.y, v.x); }
+__device__ __forceinline__ float2 pk_re(float2 m) { return make_float2(m.x, m.x); }
+
+// m0 a + m1 b for complex m0, m1, a, b (four packed instructions).
+__device__ __forceinline__ float2 pk_cmv2(float2 m0, float2 a, float2 m1, float2 b) {
+  return __ffma2_rn(make_float2(a.x, a.x), m0,
+                    __ffma2_rn(make_float2(a.y, a.y), make_float2(-m0.y, m0.x),
+                               __ffma2_rn(make_float2(b.x, b.x), m1, __fmul2_rn(make_float2(b.y, b.y), make_float2(-m1.y, m1.x)))));
+}
+
 // (va, vb) <- E (va, vb) for a 2x2 block E stored row-major in M.
-template <typename R>
+// PK: complex64 general and real blocks in packed FP32 (where the kernel has
+// registers to spare for the packed coefficients).
+template <typename R, bool PK = false>
 __device__ __forceinline__ void pair_apply(int code, const c_t<R> *M, c_t<R> &va, c_t<R> &vb) {
   using C = c_t<R>;
   C na, nb;
+  if constexpr (PK && std::is_same<R, float>::value) {
+    if (code == mReal) {
+      na = __ffma2_rn(pk_re(M[0]), va, __fmul2_rn(pk_re(M[1]), vb));
+      nb = __ffma2_rn(pk_re(M[2]), va, __fmul2_rn(pk_re(M[3]), vb));
+      va = na;
+      vb = nb;
+      return;
+    }
+    if (code == mGen) {
+      na = pk_cmv2(M[0], va, M[1], vb);
+      nb = pk_cmv2(M[2], va, M[3], vb);
+      va = na;
+      vb = nb;
+      return;
+    }
+  }
   switch (code) {
     case mSwap:
       na = vb;
@@ -486,7 +519,7 @@ __device__ void fwd_pair_t(c_t<R> *s, const TileGeom &tg, const OpDev &op, const
     const int l0 = o.base(g);
     if (CTL && (((uint32_t)l0 & lcm) != lcv)) continue;
     C va = s[l0 + o.oa], vb = s[l0 + o.ob];
-    pair_apply<R>(CODE, Mr, va, vb);
+    pair_apply<R, true>(CODE, Mr, va, vb);
     s[l0 + o.oa] = va;
     s[l0 + o.ob] = vb;
   }
@@ -996,14 +1029,14 @@ __device__ void adj_pair_t(c_t<R> *sp, c_t<R> *sl, const TileGeom &tg, const OpD
     const int ia = l0 + o.oa, ib = l0 + o.ob;
     C pa = sp[ia], pb = sp[ib];
     const C qa = pa, qb = pb;  // phi before the un-apply
-    pair_apply<R>(CODE, Mr, pa, pb);
+    pair_apply<R, true>(CODE, Mr, pa, pb);
     sp[ia] = pa;
     sp[ib] = pb;
 #pragma unroll
     for (int jj = 0; jj < B; ++jj) {
       C la = sl[jj * tg.A + ia], lb = sl[jj * tg.A + ib];
       if (GCODE != gNone) acc[jj] = pair_ip_acc<R, GCODE>(acc[jj], qa, qb, la, lb);
-      pair_apply<R>(CODE, Mr, la, lb);
+      pair_apply<R, true>(CODE, Mr, la, lb);
       sl[jj * tg.A + ia] = la;
       sl[jj * tg.A + ib] = lb;
     }
@@ -1074,50 +1107,78 @@ __device__ void adj_fused_t(c_t<R> *sp, c_t<R> *sl, const TileGeom &tg, const Op
     g11[g] = mats[op.gmat + 4 * g + 3].x;
   }
   constexpr int NA = MOM ? 4 : NG;  // accumulators per lambda
+  constexpr bool PK = MOM && std::is_same<R, float>::value;
   R acc[NA][B];
+  float2 pm[PK ? 4 : 1][PK ? B : 1];  // packed moment halves (complex64)
 #pragma unroll
   for (int g = 0; g < NA; ++g)
 #pragma unroll
     for (int jj = 0; jj < B; ++jj) acc[g][jj] = R(0);
+  if constexpr (PK)
+#pragma unroll
+    for (int g = 0; g < 4; ++g)
+#pragma unroll
+      for (int jj = 0; jj < B; ++jj) pm[g][jj] = make_float2(0.f, 0.f);
   const OpRegs o(op);
   const uint32_t lcm = op.lcmask, lcv = op.lcval;
   const int ng = tg.A >> 1;
   // SWZ (complex64 pair bit below 4): lanes 8..15 of each half-warp access their
   // pair's b member first.  A half-warp's a members then share no bank pair with
   // its b members (bit t of the index differs), so each access is conflict-free
-  // instead of 2-way; `order` puts the values back in (a, b) order.
+  // instead of 2-way.  Such a thread holds (b, a): it applies P U P (P the
+  // member swap, i.e. the block's entries mirrored) and its moments come out
+  // as (D1, D0, SY, -SX), put back in order before the reduction.
   static_assert(!SWZ || MOM, "the swapped access order is written for the moment path");
   const bool sw = SWZ && ((threadIdx.x >> 3) & 1);
   const int oa = sw ? o.ob : o.oa, ob = sw ? o.oa : o.ob;
-  auto order = [&](C &x, C &y) {
-    if (SWZ && sw) {
-      const C t = x;
-      x = y;
-      y = t;
-    }
-  };
+  if (SWZ && sw) {
+    const C t0 = Mr[0], t1 = Mr[1];
+    Mr[0] = Mr[3];
+    Mr[1] = Mr[2];
+    Mr[2] = t1;
+    Mr[3] = t0;
+  }
   for (int gi = threadIdx.x; gi < ng; gi += blockDim.x) {
     const int l0 = o.base(gi);
     if (CTL && (((uint32_t)l0 & lcm) != lcv)) continue;
     const int ia = l0 + oa, ib = l0 + ob;  // first / second member in access order
     C pa = sp[ia], pb = sp[ib];
-    order(pa, pb);
-    if constexpr (MOM) {
-      const C qa = pa, qb = pb;  // phi before the un-apply
-      pair_apply<R>(mGen, Mr, pa, pb);
-      order(pa, pb);
+    if constexpr (MOM && std::is_same<R, float>::value) {
+      // Packed moments: each float2 accumulator holds two partial products
+      // whose sum (or difference) is one moment, resolved after the loop:
+      //   pm[0] = (sum la.x qa.y, sum la.y qa.x)            D0 = x - y
+      //   pm[1] = (sum lb.x qb.y, sum lb.y qb.x)            D1 = x - y
+      //   pm[2] = la (qb.y, qb.x) + lb (qa.y, qa.x)         SY = x - y
+      //   pm[3] = la (qb.x, qb.y) - lb (qa.x, qa.y)         SX = x + y
+      const C qa = pa, qb = pb;
+      const C qas = pk_swap(qa), qbs = pk_swap(qb), nqa = make_float2(-qa.x, -qa.y);
+      pair_apply<R, true>(mGen, Mr, pa, pb);
       sp[ia] = pa;
       sp[ib] = pb;
 #pragma unroll
       for (int jj = 0; jj < B; ++jj) {
         C la = sl[jj * tg.A + ia], lb = sl[jj * tg.A + ib];
-        order(la, lb);
+        pm[0][jj] = __ffma2_rn(la, qas, pm[0][jj]);
+        pm[1][jj] = __ffma2_rn(lb, qbs, pm[1][jj]);
+        pm[2][jj] = __ffma2_rn(lb, qas, __ffma2_rn(la, qbs, pm[2][jj]));
+        pm[3][jj] = __ffma2_rn(lb, nqa, __ffma2_rn(la, qb, pm[3][jj]));
+        pair_apply<R, true>(mGen, Mr, la, lb);
+        sl[jj * tg.A + ia] = la;
+        sl[jj * tg.A + ib] = lb;
+      }
+    } else if constexpr (MOM) {
+      const C qa = pa, qb = pb;  // phi before the un-apply
+      pair_apply<R, true>(mGen, Mr, pa, pb);
+      sp[ia] = pa;
+      sp[ib] = pb;
+#pragma unroll
+      for (int jj = 0; jj < B; ++jj) {
+        C la = sl[jj * tg.A + ia], lb = sl[jj * tg.A + ib];
         acc[0][jj] = fma(la.x, qa.y, fma(-la.y, qa.x, acc[0][jj]));
         acc[1][jj] = fma(lb.x, qb.y, fma(-lb.y, qb.x, acc[1][jj]));
         acc[2][jj] = fma(la.x, qb.y, fma(-la.y, qb.x, fma(lb.x, qa.y, fma(-lb.y, qa.x, acc[2][jj]))));
         acc[3][jj] = fma(la.x, qb.x, fma(la.y, qb.y, fma(-lb.x, qa.x, fma(-lb.y, qa.y, acc[3][jj]))));
-        pair_apply<R>(mGen, Mr, la, lb);
-        order(la, lb);
+        pair_apply<R, true>(mGen, Mr, la, lb);
         sl[jj * tg.A + ia] = la;
         sl[jj * tg.A + ib] = lb;
       }
@@ -1131,7 +1192,7 @@ __device__ void adj_fused_t(c_t<R> *sp, c_t<R> *sl, const TileGeom &tg, const Op
         wb[g].x = fma(g01[g].x, pa.x, fma(g01[g].y, pa.y, g11[g] * pb.x));
         wb[g].y = fma(g01[g].x, pa.y, fma(-g01[g].y, pa.x, g11[g] * pb.y));
       }
-      pair_apply<R>(mGen, Mr, pa, pb);
+      pair_apply<R, true>(mGen, Mr, pa, pb);
       sp[ia] = pa;
       sp[ib] = pb;
 #pragma unroll
@@ -1146,11 +1207,29 @@ __device__ void adj_fused_t(c_t<R> *sp, c_t<R> *sl, const TileGeom &tg, const Op
           a = fma(-lb.y, wb[g].x, a);
           acc[g][jj] = a;
         }
-        pair_apply<R>(mGen, Mr, la, lb);
+        pair_apply<R, true>(mGen, Mr, la, lb);
         sl[jj * tg.A + ia] = la;
         sl[jj * tg.A + ib] = lb;
       }
     }
+  }
+  if constexpr (PK)
+#pragma unroll
+    for (int jj = 0; jj < B; ++jj) {
+      acc[0][jj] = pm[0][jj].x - pm[0][jj].y;
+      acc[1][jj] = pm[1][jj].x - pm[1][jj].y;
+      acc[2][jj] = pm[2][jj].x - pm[2][jj].y;
+      acc[3][jj] = pm[3][jj].x + pm[3][jj].y;
+    }
+  if constexpr (SWZ) {
+    if (sw)
+#pragma unroll
+      for (int jj = 0; jj < B; ++jj) {
+        const R d0 = acc[0][jj];
+        acc[0][jj] = acc[1][jj];
+        acc[1][jj] = d0;
+        acc[3][jj] = -acc[3][jj];
+      }
   }
   if constexpr (MOM) {
     // reduce-scatter over the lambdas with the four moments as one value
