@@ -73,10 +73,11 @@ def parse():
 
 # DRAM bytes (read + write) per adjoint launch from one ncu capture of the
 # current kernel on sel22 (22 observables), scaled to sel24 by the state size
-# (x4) and the vector count (25 / 23).  Must be re-taken when the kernel changes.
+# (x4) and the vector count (25 / 23).  Must be re-taken when the kernel changes:
+# a precision whose kernel changed after its capture has no entry (traffic null).
+# The complex64 kernel's arithmetic changed to packed FP32 after its capture.
 PROFILED_TRAFFIC = {
     "c128": (3.028316e9 * 4 * 25 / 23, "ncu dram bytes of one sel22 adjoint launch, scaled x4 x25/23"),
-    "c64": (1.483159e9 * 4 * 25 / 23, "ncu dram bytes of one sel22 adjoint launch, scaled x4 x25/23"),
 }
 
 # FP64 pipe of a GB300: 152 SMs x 2 FMA lanes/clk x 2 flops x 2.07 GHz.
