@@ -22,7 +22,10 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libsv.so")
 
-SOURCES = ["sv_api.cu", "sv_kernels_f32.cu", "sv_kernels_f64.cu", "sv_kernels_df.cu", "sv_static.cu", "sv_tc.cu"]
+# One precision's launchers compile as two units (the adjoint kernel's variants
+# apart from the rest), longest first, all in parallel.
+SOURCES = ["sv_kernels_df_adjoint.cu", "sv_kernels_df.cu", "sv_kernels_f64_adjoint.cu", "sv_kernels_f32_adjoint.cu",
+           "sv_kernels_f64.cu", "sv_kernels_f32.cu", "sv_api.cu", "sv_static.cu", "sv_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 

@@ -204,7 +204,8 @@ struct ZTerm {
   double coeff;
 };
 
-// Launchers (defined once per precision in sv_kernels_f32.cu / sv_kernels_f64.cu).
+// Launchers (defined once per precision in sv_kernels_{f32,f64,df}.cu, the adjoint
+// launcher in sv_kernels_{f32,f64,df}_adjoint.cu).
 // R = float (complex64) or double (complex128).  Every launcher returns the
 // cudaError_t of its launch.
 template <typename R>

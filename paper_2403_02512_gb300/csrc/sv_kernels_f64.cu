@@ -1,5 +1,6 @@
 // complex128 instantiation of the state-vector kernels, plus the
 // precision-independent deterministic reductions.
+#define SV_LAUNCH_PART 1  // tile_adjoint: sv_kernels_f64_adjoint.cu
 #include "sv_launch.cuh"
 
 namespace sv {

@@ -1,5 +1,16 @@
 // Launcher definitions of Launch<R>; included once per precision.
+//
+// SV_LAUNCH_PART selects which launchers a translation unit defines, so that
+// one precision compiles as two units in parallel (an explicit instantiation
+// of Launch<R> instantiates only the members defined before it):
+//   0 (default)  every launcher;
+//   1            every launcher but tile_adjoint;
+//   2            tile_adjoint alone (the adjoint kernel's variants).
 #pragma once
+
+#ifndef SV_LAUNCH_PART
+#define SV_LAUNCH_PART 0
+#endif
 
 #include "sv_kernels.cuh"
 
@@ -26,6 +37,7 @@ inline void allow_big_smem(Kern k, bool &done) {
 }
 }  // namespace detail
 
+#if SV_LAUNCH_PART != 2
 template <typename R>
 cudaError_t Launch<R>::build_matrices(const MatSlot *slots, int n_slots, const double *params,
                                       const double *user_mats, void *mats, cudaStream_t st) {
@@ -53,6 +65,9 @@ cudaError_t Launch<R>::tile_forward(void *psi, int n, const PassDev &pass, const
   return cudaGetLastError();
 }
 
+#endif  // SV_LAUNCH_PART != 2
+
+#if SV_LAUNCH_PART != 1
 namespace detail {
 template <typename R, int MAXK, int B>
 cudaError_t adjoint_b(const void *phi_in, void *phi_out, void *lam, int n, int m, const PassDev &pass,
@@ -94,6 +109,9 @@ cudaError_t Launch<R>::tile_adjoint(const void *phi_in, void *phi_out, void *lam
   return detail::adjoint_k<R, 4>(phi_in, phi_out, lam, n, m, b, pass, ops, mats, aux, partials, grid, st);
 }
 
+#endif  // SV_LAUNCH_PART != 1
+
+#if SV_LAUNCH_PART != 2
 template <typename R>
 cudaError_t Launch<R>::stream_op(void *psi, int n, const StreamDev &sd, const void *mats, cudaStream_t st) {
   static int sms = 0;
@@ -374,9 +392,6 @@ cudaError_t Launch<R>::copy(void *dst, const void *src, int n, cudaStream_t st) 
   return cudaMemcpyAsync(dst, src, sizeof(g_t<R>) << n, cudaMemcpyDeviceToDevice, st);
 }
 
-
-
-
 // Tile sizes: 32 KiB of amplitudes per tile in the forward / expval kernels,
 // 2 x 16 KiB (phi + lambda) in the adjoint kernel.
 template <typename R>
@@ -401,5 +416,6 @@ template <typename R>
 int Launch<R>::adj_ctas_per_sm() {
   return std::is_same<R, double>::value ? 1 : 2;
 }
+#endif  // SV_LAUNCH_PART != 2
 
 }  // namespace sv
