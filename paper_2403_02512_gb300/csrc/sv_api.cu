@@ -180,7 +180,7 @@ sv_status validate_op(int n, const sv_op &op, int n_params, const double *matric
     if (op.n_targets < 1 || op.n_targets > SV_MAX_TARGETS)
       return fail(SV_ERR_ARG, "SV_MATRIX takes 1..%d targets, got %d", SV_MAX_TARGETS, op.n_targets);
     const int64_t need = (int64_t)1 << (2 * op.n_targets);
-    if (!matrices || op.matrix_offset < 0 || op.matrix_offset + need > n_mat)
+    if (!matrices || op.matrix_offset < 0 || op.matrix_offset > n_mat - need)  // no overflow in the sum
       return fail(SV_ERR_ARG, "SV_MATRIX data out of range (offset %lld, %lld entries needed)",
                   (long long)op.matrix_offset, (long long)need);
     for (int64_t e = 0; e < 2 * need; ++e)
@@ -2529,8 +2529,10 @@ sv_status sv_apply_op(sv_state *s, const sv_op *op, const double *params, const 
   if (!op) return fail(SV_ERR_ARG, "op is NULL");
   int np = 0;
   for (int a = 0; a < 3; ++a) np = std::max(np, op->param_index[a] + 1);
-  int64_t nm = 0;
-  if (op->kind == SV_MATRIX) nm = op->matrix_offset + ((int64_t)1 << (2 * op->n_targets));
+  int64_t nm = 0;  // entries the matrix data must hold; out-of-range sizes are rejected by the op check
+  if (op->kind == SV_MATRIX && op->n_targets >= 1 && op->n_targets <= SV_MAX_TARGETS && op->matrix_offset >= 0 &&
+      op->matrix_offset < ((int64_t)1 << 48))
+    nm = op->matrix_offset + ((int64_t)1 << (2 * op->n_targets));
   sv_tape tape = {1, op, np, matrices, nm};
   sv_program *p = nullptr;
   if (sv_status st = build_program(s, &tape, nullptr, 0, params, true, &p)) return st;
@@ -2873,6 +2875,7 @@ sv_status sv_adjoint_vjp(sv_state *s, const sv_tape *tape, const double *params,
   std::vector<uint64_t> x, z;
   for (int j = 0; j < n_obs; ++j) {
     if (!std::isfinite(grad_out[j])) return fail(SV_ERR_ARG, "grad_out[%d] is not finite", j);
+    if (obs[j].n_terms < 0) return fail(SV_ERR_ARG, "observable %d: n_terms < 0", j);
     if (obs[j].n_terms > 0 && (!obs[j].coeffs || !obs[j].x_mask || !obs[j].z_mask))
       return fail(SV_ERR_ARG, "observable %d: NULL term arrays", j);
     for (int t = 0; t < obs[j].n_terms; ++t) {
