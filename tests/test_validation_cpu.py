@@ -190,3 +190,25 @@ def test_sparse_observables_are_checked_on_the_host():
         with pytest.raises(L.SvError) as ei:
             L.Sparse(N, bad_ip, bad_ix, bad_v)
         assert ei.value.status == 1 and msg in str(ei.value)
+
+
+def test_batches_are_checked_on_the_host():
+    from workloads import Circuit
+
+    def circ(n, ops, n_params=0, obs=None, basis=0):
+        return Circuit(n, ops, n_params, [obs if obs is not None else [Term(1.0, ((0, "Z"),))]], basis)
+
+    good = circ(3, [Op("Hadamard", (0,))])
+    for bad, status, msg in (
+            (circ(31, [Op("Hadamard", (0,))]), 1, "outside [1, 30]"),
+            (circ(3, [Op("RX", (3,), (0,))], 1), 1, "batch circuit 1 op 0: target wire 3 out of range"),
+            (circ(3, [Op("Hadamard", (0,))], obs=[Term(1.0, ((1, "X"),))]), 5, "Z-only"),
+            (circ(3, [Op("Hadamard", (0,))], obs=[Term(1.0, ((3, "Z"),))]), 1, "bad Z word"),
+            (circ(3, [Op("Hadamard", (0,))], obs=[Term(math.nan, ((0, "Z"),))]), 1, "bad Z word"),
+            (circ(3, [Op("Hadamard", (0,))], basis=8), 1, "basis state out of range")):
+        with pytest.raises(L.SvError) as ei:
+            L.Batch([good, bad], L.SV_C64)
+        assert ei.value.status == status and msg in str(ei.value), str(ei.value)
+    with pytest.raises(L.SvError) as ei:
+        L.Batch([good], 3)
+    assert ei.value.status == 1 and "unknown dtype" in str(ei.value)
