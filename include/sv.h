@@ -370,7 +370,9 @@ sv_status sv_program_stats(const sv_program *p, int *n_forward_passes, int *n_ad
  * (all deterministic reductions), 5 build_matrices, 6 dense_k, 7 other.
  * sv_kernel_timing_read synchronises the device, adds the elapsed times of the
  * completed launches to per-class totals and reports them (ms, launches).
- * SV_KERNEL_CLASSES entries each; NULL outputs are skipped.  Reset clears totals. */
+ * SV_KERNEL_CLASSES entries each; NULL outputs are skipped.  Reset clears totals.
+ * The totals are process-wide: launches of every state and host thread are
+ * recorded (under a lock, so concurrent threads may launch while timing). */
 #define SV_KERNEL_CLASSES 8
 sv_status sv_kernel_timing_enable(int enable);
 sv_status sv_kernel_timing_reset(void);

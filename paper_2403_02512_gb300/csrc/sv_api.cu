@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -83,11 +84,13 @@ struct TimedLaunch {
   int cls;
 };
 std::atomic<bool> g_timing{false};
+std::mutex g_timing_mu;  // guards the four below: launches may come from several host threads
 std::vector<TimedLaunch> g_pending;
 std::vector<cudaEvent_t> g_event_pool;
 double g_class_ms[SV_KERNEL_CLASSES] = {0};
 int64_t g_class_n[SV_KERNEL_CLASSES] = {0};
 
+// An event from the pool (or a new one); the caller holds g_timing_mu.
 cudaEvent_t take_event() {
   if (!g_event_pool.empty()) {
     cudaEvent_t e = g_event_pool.back();
@@ -106,12 +109,14 @@ struct LaunchTimer {
   cudaEvent_t a = nullptr;
   LaunchTimer(cudaStream_t s_, int c) : st(s_), cls(c) {
     if (g_timing.load()) {
+      std::lock_guard<std::mutex> lk(g_timing_mu);
       a = take_event();
       cudaEventRecord(a, st);
     }
   }
   ~LaunchTimer() {
     if (a) {
+      std::lock_guard<std::mutex> lk(g_timing_mu);
       cudaEvent_t b = take_event();
       cudaEventRecord(b, st);
       g_pending.push_back({a, b, cls});
@@ -3003,6 +3008,7 @@ sv_status sv_kernel_timing_enable(int enable) {
 
 sv_status sv_kernel_timing_reset(void) {
   cudaError_t e = cudaDeviceSynchronize();
+  std::lock_guard<std::mutex> lk(g_timing_mu);
   for (TimedLaunch &t : g_pending) {
     g_event_pool.push_back(t.a);
     g_event_pool.push_back(t.b);
@@ -3018,6 +3024,7 @@ sv_status sv_kernel_timing_reset(void) {
 sv_status sv_kernel_timing_read(double *total_ms, int64_t *launches) {
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return cuda_fail(e, "sv_kernel_timing_read");
+  std::lock_guard<std::mutex> lk(g_timing_mu);
   for (TimedLaunch &t : g_pending) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) {
