@@ -200,6 +200,35 @@ def oracle_sample(rows: int = 1):
     return est_ms, wall_ms, sample, oracle.num_threads(), J
 
 
+def oracle_layered12(reps: int = 3):
+    """The oracle on the 12-qubit layered workload (10 layers of RX, RY, RZ on
+    every wire plus a CNOT ladder, O = sum_i Z_i, 360 parameters): forward pass
+    plus full adjoint Jacobian, median ms over `reps` calls with all host
+    threads and with one thread (the thread count is restored afterwards)."""
+    import oracle
+    from workloads import layered_circuit
+
+    c, p = layered_circuit(12, 10)
+    threads = oracle.num_threads()
+
+    def med():
+        ts = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            oracle.adjoint_jacobian(c, p)
+            ts.append(1e3 * (time.perf_counter() - t0))
+        return statistics.median(ts)
+
+    try:
+        all_ms = med()
+        oracle.set_num_threads(1)
+        one_ms = med()
+    finally:
+        oracle.set_num_threads(threads)
+    return {"workload": "layered12: forward + 360-parameter adjoint Jacobian of sum_i Z_i, oracle FP64",
+            "ms_all_threads": all_ms, "threads": threads, "ms_one_thread": one_ms, "reps": reps}
+
+
 def max_over_ranks(value: float, world: int, device) -> float:
     """The job's time: the slowest replica's (all-reduce MAX over the process
     group; the replicas themselves exchange nothing)."""
@@ -785,6 +814,10 @@ def run_ours(args):
                "sample_wall_s": sum(r[1] for r in runs) / 1e3}
         if (NQ, args.layers) == (N_QUBITS, LAYERS):
             cpu["max_abs_diff_row0_vs_gpu"] = float(np.abs(main["J"].cpu().numpy()[0] - Jo[0]).max())
+        try:  # a side figure never takes the bench line down
+            cpu["layered12"] = oracle_layered12()
+        except Exception as exc:
+            cpu["layered12"] = {"error": repr(exc)}
 
     if rank == 0:
         line = {"metric": METRIC, "value": replica_value(ms, world), "unit": "ms", "n_gpus": world,

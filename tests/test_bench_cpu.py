@@ -36,3 +36,11 @@ def test_controls_halve_the_flops_and_constant_gates_add_no_inner_product():
 def test_fp64_peak_is_the_pipe_arithmetic():
     # 152 SMs x 2 FP64 FMA per clock x 2 flops x 2070 MHz
     assert bench.FP64_PEAK_TFLOPS == pytest.approx(1.25856, rel=1e-5)
+
+
+def test_oracle_layered12_timing_restores_the_thread_count():
+    import oracle
+    before = oracle.num_threads()
+    r = bench.oracle_layered12(reps=1)
+    assert oracle.num_threads() == before
+    assert r["threads"] == before and r["ms_all_threads"] > 0 and r["ms_one_thread"] > 0
