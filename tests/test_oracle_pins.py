@@ -329,6 +329,32 @@ def test_adjoint_matches_parameter_shift(maker):
     np.testing.assert_allclose(J, Jps, atol=1e-12)
 
 
+@pytest.mark.parametrize("maker", ["layered", "sel", "qaoa", "vqe", "rycz"])
+def test_workload_miniatures_match_the_dense_reference(maker):
+    # each benchmark workload's own generator at a size the Kronecker reference
+    # can hold: forward amplitudes, expectation values and the exact Jacobian
+    # (dU/dtheta = i s G U), which also covers the Givens gates that the
+    # two-term shift rule cannot
+    if maker == "layered":
+        c, p = layered_circuit(6, 3, seed=11)
+    elif maker == "sel":
+        c, p = strongly_entangling(6, 6, seed=12)  # CNOT ranges 1..5 (l mod 5 + 1)
+    elif maker == "qaoa":
+        c = qaoa_maxcut(6, 2, seed=13)
+        p = np.random.default_rng(13).uniform(0, math.pi, size=4)
+    elif maker == "vqe":
+        c, p = vqe_givens(8, 4, 3, 4, 20, seed=14)
+        p = p + np.random.default_rng(14).normal(0.0, 0.5, size=p.size)  # away from the HF point
+    else:
+        c, p = ry_cz_brick(8, 4, seed=15, dense_every=0)
+    psi0 = dense.initial(c)
+    np.testing.assert_allclose(oracle.forward(c, p, psi0), dense.state(c, p), atol=1e-13)
+    E, J = oracle.adjoint_jacobian(c, p)
+    np.testing.assert_allclose(E, dense.expvals(c, p), atol=1e-13)
+    np.testing.assert_allclose(J, dense.exact_jacobian(c, p), atol=1e-12)
+    assert np.abs(J).max() > 1e-3  # a nontrivial gradient
+
+
 def test_adjoint_matches_finite_differences():
     c, p = random_circuit(4, 14, 77)
     obs = [[Term(0.7, ((0, "Z"), (2, "X"))), Term(-1.1, ((1, "Y"),))]]
