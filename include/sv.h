@@ -157,7 +157,8 @@ sv_status sv_create(int n, sv_dtype dtype, sv_state **out);
  * must outlive the state. */
 sv_status sv_create_from_device_ptr(int n, sv_dtype dtype, void *device_ptr, sv_state **out);
 
-/* Release the state, its workspace and any library-owned buffer.  NULL is a no-op. */
+/* Release the state, its workspace and any library-owned buffer.  NULL is a no-op.
+ * Programs created for the state refer to it: destroy them first. */
 sv_status sv_destroy(sv_state *s);
 
 /* Issue all further work for s on this CUDA stream (cudaStream_t; NULL = legacy default). */
@@ -292,7 +293,8 @@ sv_status sv_adjoint_vjp(sv_state *s, const sv_tape *tape, const double *params,
 
 /* Plan a tape and observables once for state s: fusion passes, device tables and
  * workspace are built here; later calls only move parameters.  The program keeps
- * copies of everything it needs; tape and obs may be freed after the call. */
+ * copies of everything it needs; tape and obs may be freed after the call.  The
+ * program runs on s (its buffer and stream) and must be destroyed before s. */
 sv_status sv_program_create(sv_state *s, const sv_tape *tape, const sv_pauli_sum *obs,
                             int n_obs, sv_program **out);
 sv_status sv_program_destroy(sv_program *p);

@@ -14,6 +14,7 @@ the stream; every arithmetic step runs in the library's CUDA kernels.
 
 from __future__ import annotations
 
+import weakref
 from typing import Optional, Sequence
 
 import numpy as np
@@ -53,6 +54,7 @@ class StateVector:
             self.handle = L.sv_create_from_device_ptr(self.n, self.sv_dtype, self.tensor.data_ptr())
         self.device = dev
         self.generation = 0
+        self._programs = weakref.WeakSet()  # programs on this state: closed before it
         if dtype == "c128df":
             L.sv_set_compute(self.handle, L.SV_COMPUTE_DOUBLE_FLOAT)
         if renormalize is not None:
@@ -104,6 +106,8 @@ class StateVector:
 
     def close(self) -> None:
         if getattr(self, "handle", None):
+            for prog in list(getattr(self, "_programs", ())):
+                prog.close()  # a program refers to its state's handle
             L.sv_destroy(self.handle)
             self.handle = None
 
@@ -124,7 +128,10 @@ class Program:
         self.m = self.obs.count if self.obs else 0
         self.n_params = int(n_params)
         self.basis_state = int(basis_state)
+        if not getattr(sv, "handle", None):
+            raise RuntimeError("the state vector is closed")
         self.handle = L.sv_program_create(sv.handle, self.tape, self.obs)
+        sv._programs.add(self)
         self._params = torch.zeros(max(1, self.n_params), dtype=torch.float64, device=sv.device)
         self._forward_generation = None
 
