@@ -39,7 +39,7 @@ def _replica(rank, world, port, out):
 
 def test_max_over_ranks_with_two_gloo_replicas():
     world = 2
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()  # no fork of a process that may hold CUDA state
     out = mgr.dict()
     mp.spawn(_replica, args=(world, _free_port(), out), nprocs=world, join=True)
     assert out[0] == out[1] == (17.25, 17.25 / 2)
