@@ -164,9 +164,13 @@ sv_status sv_destroy(sv_state *s);
 /* Issue all further work for s on this CUDA stream (cudaStream_t; NULL = legacy default). */
 sv_status sv_set_stream(sv_state *s, void *cuda_stream);
 
-/* Optional caller-owned device workspace used instead of library allocations
- * while it is large enough (bytes >= sv_workspace_bytes for the request).
- * NULL / 0 returns to library-owned workspace. */
+/* Optional caller-owned device workspace (256-byte aligned, `bytes` long): a
+ * call whose temporaries fit in it uses it instead of library allocations; a
+ * call that needs more allocates its own, as if none were set.  A Jacobian or
+ * VJP needs about (2 + m_c) state vectors (phi buffers and m_c lambda
+ * vectors) plus small tables; probabilities, samples and sparse expectation
+ * values need a few partial-sum arrays.  NULL / 0 returns to library-owned
+ * workspace.  The buffer must outlive every call that uses it. */
 sv_status sv_set_workspace(sv_state *s, void *device_ptr, size_t bytes);
 
 /* Arithmetic of a complex128 state (its storage stays IEEE complex128):
