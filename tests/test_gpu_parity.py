@@ -815,3 +815,18 @@ def test_single_wire_layers_jacobian(dtype, n_obs):
     _assert_rel(J.cpu().numpy(), Jo, TOL_J[dtype], "jacobian", dtype)
     g = rng.normal(size=n_obs)
     _assert_rel(prog.vjp(g).cpu().numpy(), g @ Jo, TOL_J[dtype], "vjp", dtype)
+
+
+def test_closing_a_state_first_closes_its_programs():
+    # a program refers to its state: closing the state closes the program with it
+    c, p = strongly_entangling(6, 1, seed=3)
+    sv = StateVector(6, "c128")
+    prog = Program.from_circuit(sv, c)
+    prog.forward(p)
+    E, _ = prog.jacobian()
+    _assert_rel(E.cpu().numpy(), oracle.adjoint_jacobian(c, p)[0], TOL_E["c128"], "expvals", "c128")
+    sv.close()
+    assert sv.handle is None and prog.handle is None
+    prog.close()  # already closed: a no-op
+    with pytest.raises(RuntimeError):
+        Program.from_circuit(sv, c)
