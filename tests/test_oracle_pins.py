@@ -622,6 +622,33 @@ def test_sampling_by_inverse_transform():
     assert np.all(np.abs(freq - p) <= 5 * np.sqrt(p * (1 - p) / shots) + 1e-12)
 
 
+def test_sampling_stratified_uniforms_give_exact_counts():
+    # K evenly spaced uniforms (k + 1/2) / K: outcome b takes the grid points in
+    # [CDF_{b-1}, CDF_b), i.e. K p_b of them up to one at each end
+    psi = random_state(5, 21)
+    for wires in ([1, 4], [0, 2, 3], [4]):
+        p = oracle.probabilities(psi, wires)
+        K = 100003
+        s = oracle.sample(psi, wires, (np.arange(K) + 0.5) / K)
+        counts = np.bincount(s.astype(np.int64), minlength=p.size)
+        assert counts.sum() == K and np.all(np.abs(counts - K * p) <= 1.0 + 1e-9)
+        assert np.all(np.diff(s.astype(np.int64)) >= 0)  # monotone in u
+
+
+def test_probabilities_agree_with_z_expectations():
+    # <Z_w> = p_w(0) - p_w(1), and <Z_a Z_b> = sum_b (-1)^(b_a + b_b) p_ab(b):
+    # the marginal sums against the Pauli-word path
+    n = 5
+    psi = random_state(n, 22)
+    for w in range(n):
+        p = oracle.probabilities(psi, [w])
+        assert abs(oracle.expval(psi, [Term(1.0, ((w, "Z"),))]) - (p[0] - p[1])) < 1e-14
+    for a, b in ((0, 4), (3, 1), (2, 3)):
+        p = oracle.probabilities(psi, [a, b])
+        want = p[0] - p[1] - p[2] + p[3]
+        assert abs(oracle.expval(psi, [Term(1.0, ((a, "Z"), (b, "Z")))]) - want) < 1e-14
+
+
 # ---- forward-mode Jacobian-vector product -----------------------------------
 @pytest.mark.parametrize("seed", [1, 2, 3])
 def test_jvp_matches_dense_exact_jacobian(seed):
