@@ -36,6 +36,17 @@ N_QUBITS, LAYERS = 24, 8
 FALLBACK_HBM_GBS = 6800.0
 
 
+def bench_config(n_qubits: int, layers: int, dtype: str, world: int, n_params: int, n_obs: int) -> dict:
+    """The `config` of the JSON line, the same dict in both arms for the same
+    workload (the plan's pass counts are reported beside it, not in it)."""
+    full = (n_qubits, layers) == (N_QUBITS, LAYERS)
+    return {"workload": WORKLOAD if full else f"sel{n_qubits} ({layers} layers; reduced size for profiling)",
+            "precision": dtype, "n_qubits": n_qubits, "layers": layers, "n_params": n_params,
+            "n_observables": n_obs, "parallelism": "replicas" if world > 1 else "single",
+            "l2": "inputs larger than L2 (129 MB): c128 state 268 MB and 24 lambda vectors 6.4 GB per step"
+            if full else "reduced size"}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -267,7 +278,7 @@ def run_reference(args):
                         "the sample's own wall time (one complete Jacobian row)",
             "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_qubits": N_QUBITS, "n_params": 576, "n_observables": 24},
+            "config": bench_config(N_QUBITS, LAYERS, "c128", int(os.environ.get("WORLD_SIZE", "1")), 576, 24),
             "cpu_baseline": {"value": value, "unit": "ms", "cores": cores, "kind": "oracle", "sample": sample,
                              "samples": len(est), "spread_ms": [min(est), max(est)]},
             "e2e": {"value": value, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -824,12 +835,8 @@ def run_ours(args):
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
                 "scaling": "weak", "vs_baseline": None, "dtype": {"c128": "f64", "c64": "f32", "c128df": "df64 (f32 pairs; complex128 storage)"}[args.dtype],
                 "data": "synthetic",
-                "config": {"workload": WORKLOAD if (NQ, args.layers) == (N_QUBITS, LAYERS) else
-                           f"sel{NQ} ({args.layers} layers; reduced size for profiling)",
-                           "precision": args.dtype, "n_qubits": NQ, "layers": args.layers,
-                           "n_params": P, "n_observables": m, "parallelism": "replicas" if world > 1 else "single",
-                           "l2": "inputs larger than L2 (129 MB): c128 state 268 MB and 24 lambda vectors 6.4 GB per step",
-                           "forward_passes": main["fwd_passes"], "adjoint_passes": main["adj_passes"]},
+                "config": bench_config(NQ, args.layers, args.dtype, world, P, m),
+                "plan": {"forward_passes": main["fwd_passes"], "adjoint_passes": main["adj_passes"]},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": main["launches"],
                 "clocks": main["clocks"], "extras": extras}
         print(json.dumps(line), flush=True)

@@ -44,3 +44,11 @@ def test_oracle_layered12_timing_restores_the_thread_count():
     r = bench.oracle_layered12(reps=1)
     assert oracle.num_threads() == before
     assert r["threads"] == before and r["ms_all_threads"] > 0 and r["ms_one_thread"] > 0
+
+
+def test_both_arms_print_the_same_config():
+    # the reference arm hard-codes the workload's sizes; our arm derives them from the workload
+    c, _ = strongly_entangling(bench.N_QUBITS, bench.LAYERS)
+    ours = bench.bench_config(bench.N_QUBITS, bench.LAYERS, "c128", 1, c.n_params, len(c.observables))
+    ref = bench.bench_config(bench.N_QUBITS, bench.LAYERS, "c128", 1, 576, 24)
+    assert ours == ref and ours["workload"] == bench.WORKLOAD
