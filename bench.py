@@ -47,6 +47,18 @@ def bench_config(n_qubits: int, layers: int, dtype: str, world: int, n_params: i
             if full else "reduced size"}
 
 
+DTYPE_NAMES = {"c128": "f64", "c64": "f32", "c128df": "df64 (f32 pairs; complex128 storage)"}
+
+
+def bench_line(ms, world, steps, warmup, dtype, config, plan, roofline, cpu, e2e, launches, clocks, extras) -> dict:
+    """The GPU arm's JSON line: ms is the slowest replica's time per step."""
+    return {"metric": METRIC, "value": replica_value(ms, world), "unit": "ms", "n_gpus": world,
+            "steps": steps, "warmup": warmup, "ms_per_step": ms, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_NAMES[dtype], "data": "synthetic",
+            "config": config, "plan": plan, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches, "clocks": clocks, "extras": extras}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -831,14 +843,10 @@ def run_ours(args):
             cpu["layered12"] = {"error": repr(exc)}
 
     if rank == 0:
-        line = {"metric": METRIC, "value": replica_value(ms, world), "unit": "ms", "n_gpus": world,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
-                "scaling": "weak", "vs_baseline": None, "dtype": {"c128": "f64", "c64": "f32", "c128df": "df64 (f32 pairs; complex128 storage)"}[args.dtype],
-                "data": "synthetic",
-                "config": bench_config(NQ, args.layers, args.dtype, world, P, m),
-                "plan": {"forward_passes": main["fwd_passes"], "adjoint_passes": main["adj_passes"]},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": main["launches"],
-                "clocks": main["clocks"], "extras": extras}
+        line = bench_line(ms, world, args.steps, args.warmup, args.dtype,
+                          bench_config(NQ, args.layers, args.dtype, world, P, m),
+                          {"forward_passes": main["fwd_passes"], "adjoint_passes": main["adj_passes"]},
+                          roofline, cpu, e2e, main["launches"], main["clocks"], extras)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

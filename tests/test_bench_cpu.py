@@ -52,3 +52,34 @@ def test_both_arms_print_the_same_config():
     ours = bench.bench_config(bench.N_QUBITS, bench.LAYERS, "c128", 1, c.n_params, len(c.observables))
     ref = bench.bench_config(bench.N_QUBITS, bench.LAYERS, "c128", 1, 576, 24)
     assert ours == ref and ours["workload"] == bench.WORKLOAD
+
+
+def test_json_lines_carry_the_contract_keys(monkeypatch, capsys):
+    import argparse
+    import json
+
+    cfg = bench.bench_config(bench.N_QUBITS, bench.LAYERS, "c128", 1, 576, 24)
+    roofline = {"bound": "alu", "achieved": 1.0, "peak": bench.FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": 1.0 / bench.FP64_PEAK_TFLOPS, "traffic": 1.0}
+    cpu = {"value": 1.4e5, "unit": "ms", "cores": 16, "kind": "oracle", "sample": "s"}
+    e2e = {"value": 2401.0, "unit": "ms", "h2d_bytes_per_step": 9216, "d2h_bytes_per_step": 110784}
+    clocks = {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": []}
+    ours = bench.bench_line(2400.0, 1, 20, 5, "c128", cfg, {"forward_passes": 41}, roofline, cpu, e2e, 2400,
+                            clocks, {})
+    need = {"metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+            "vs_baseline", "dtype", "data", "config", "roofline", "cpu_baseline", "e2e", "gpu_launches", "clocks"}
+    assert need <= set(ours)
+    assert ours["value"] == 2400.0 and ours["higher_is_better"] is False and ours["dtype"] == "f64"
+    assert bench.bench_line(2400.0, 4, 20, 5, "c128", cfg, {}, roofline, cpu, e2e, 1, clocks, {})["value"] == 600.0
+    # the reference arm (the oracle), with a stand-in for its timed sample
+    monkeypatch.delenv("RANK", raising=False)
+    monkeypatch.delenv("WORLD_SIZE", raising=False)
+    monkeypatch.setattr(bench, "oracle_sample", lambda rows=1: (1.4e5, 1.5e4, "one row", 16, None))
+    bench.run_reference(argparse.Namespace(gpus=1, steps=2, warmup=1))
+    ref = json.loads(capsys.readouterr().out)
+    assert ref["impl"] == "reference" and need - {"roofline", "gpu_launches", "clocks"} <= set(ref)
+    for k in ("metric", "unit", "higher_is_better", "config", "dtype", "scaling"):
+        assert ref[k] == ours[k], k
+    assert ref["steps"] == 2 and ref["warmup"] == 1 and ref["ms_per_step"] == 1.5e4 and ref["value"] == 1.4e5
+    assert ref["e2e"] == {"value": 1.4e5, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert ref["cpu_baseline"]["kind"] == "oracle" and ref["cpu_baseline"]["cores"] == 16
