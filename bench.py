@@ -252,6 +252,23 @@ def oracle_layered12(reps: int = 3):
             "ms_all_threads": all_ms, "threads": threads, "ms_one_thread": one_ms, "reps": reps}
 
 
+def oracle_qaoa20(count: int = 4, n: int = 20):
+    """The oracle on the batched QAOA workload: energies of the first `count`
+    of the 512 parameter sets of the 20-node p = 4 MaxCut circuit (forward
+    pass plus <H_C>, all host threads), as circuits per second."""
+    import oracle
+    from workloads import qaoa_maxcut, qaoa_param_sets
+
+    c = qaoa_maxcut(n, 4)
+    sets = qaoa_param_sets(512, 4)[:count]
+    t0 = time.perf_counter()
+    for p in sets:
+        oracle.expval(oracle.forward(c, p), c.observables[0])
+    dt = time.perf_counter() - t0
+    return {"workload": f"QAOA MaxCut, {n} nodes, p = 4: energy of {count} parameter sets, oracle FP64",
+            "circuits_per_s": count / dt, "threads": oracle.num_threads()}
+
+
 def max_over_ranks(value: float, world: int, device) -> float:
     """The job's time: the slowest replica's (all-reduce MAX over the process
     group; the replicas themselves exchange nothing)."""
@@ -837,10 +854,11 @@ def run_ours(args):
                "sample_wall_s": sum(r[1] for r in runs) / 1e3}
         if (NQ, args.layers) == (N_QUBITS, LAYERS):
             cpu["max_abs_diff_row0_vs_gpu"] = float(np.abs(main["J"].cpu().numpy()[0] - Jo[0]).max())
-        try:  # a side figure never takes the bench line down
-            cpu["layered12"] = oracle_layered12()
-        except Exception as exc:
-            cpu["layered12"] = {"error": repr(exc)}
+        for key, fn in (("layered12", oracle_layered12), ("qaoa20", oracle_qaoa20)):
+            try:  # a side figure never takes the bench line down
+                cpu[key] = fn()
+            except Exception as exc:
+                cpu[key] = {"error": repr(exc)}
 
     if rank == 0:
         line = bench_line(ms, world, args.steps, args.warmup, args.dtype,

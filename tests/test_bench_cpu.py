@@ -83,3 +83,8 @@ def test_json_lines_carry_the_contract_keys(monkeypatch, capsys):
     assert ref["steps"] == 2 and ref["warmup"] == 1 and ref["ms_per_step"] == 1.5e4 and ref["value"] == 1.4e5
     assert ref["e2e"] == {"value": 1.4e5, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert ref["cpu_baseline"]["kind"] == "oracle" and ref["cpu_baseline"]["cores"] == 16
+
+
+def test_oracle_qaoa_throughput_is_reported():
+    r = bench.oracle_qaoa20(count=2, n=10)
+    assert r["circuits_per_s"] > 0 and r["threads"] >= 1
