@@ -126,6 +126,26 @@ def test_rotations_are_exp_minus_i_theta_p_over_2():
                                        scipy.linalg.expm(-0.5j * t * P), atol=1e-14)
 
 
+def test_two_qubit_rotations_from_textbook_pauli_products():
+    # Paulis written out here (not the oracle's tables); first wire = left factor
+    X = np.array([[0, 1], [1, 0]], dtype=np.complex128)
+    Y = np.array([[0, -1j], [1j, 0]], dtype=np.complex128)
+    Z = np.array([[1, 0], [0, -1]], dtype=np.complex128)
+    XX, YY, ZZ = np.kron(X, X), np.kron(Y, Y), np.kron(Z, Z)
+    for t in (0.35, -1.4, 2.9):
+        for name, H in (("IsingXX", -0.5 * XX), ("IsingYY", -0.5 * YY), ("IsingZZ", -0.5 * ZZ),
+                        ("IsingXY", 0.25 * (XX + YY))):
+            np.testing.assert_allclose(oracle.gate_matrix(name, [t]), scipy.linalg.expm(1j * t * H), atol=1e-14,
+                                       err_msg=name)
+        # controlled rotations: |1><1| (x) R on the target, identity where the control is 0
+        out = oracle.apply_op(np.eye(4, dtype=np.complex128)[:, 1].copy(), Op("RY", (1,), (0,), controls=(0,)),
+                              np.array([t]))
+        np.testing.assert_allclose(out, [0, 1, 0, 0], atol=1e-15)  # |01>: control 0, untouched
+        out = oracle.apply_op(np.eye(4, dtype=np.complex128)[:, 2].copy(), Op("RY", (1,), (0,), controls=(0,)),
+                              np.array([t]))
+        np.testing.assert_allclose(out, [0, 0, math.cos(t / 2), math.sin(t / 2)], atol=1e-15)
+
+
 def test_rot_closed_form():
     for (phi, th, om) in [(0.1, 0.2, 0.3), (-1.0, 2.0, 4.0), (3.0, -0.7, 1.9)]:
         c, s = math.cos(th / 2), math.sin(th / 2)
